@@ -1,0 +1,502 @@
+/*
+ * Plain FP64 CPU oracle for the sub-structured Conjugate Gradient.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * definition that the CUDA path is checked against.  Only the tests, the
+ * smoke check and the CPU-baseline leg of the benchmark may build or call it.
+ * It shares no code, header or table with the CUDA library, and it must be
+ * compiled with -ffp-contract=off so that every a*b+c rounds twice, the same
+ * way on x86-64 and aarch64.
+ *
+ * What it computes, by paper section:
+ *   or_spmv          global CSR product y = A x, rows in order, each row summed
+ *                    left to right (CSR storage, Section 2.2).
+ *   or_cg            Algorithm 3 (Conjugate Gradient) with M = I on the global
+ *                    CSR, x1 = x0, stopping on the recursive residual.
+ *   or_partition     the sub-structure data of Section 2.4: local matrices S_i
+ *                    (Eq. mat_subdomains) whose interface blocks sum to S_33
+ *                    (Eq. interface_summation), local-to-global maps and the
+ *                    per-node interface lists (Section 3.4.2), with the
+ *                    entry-ownership reading for assembled matrices.
+ *   or_sub_spmv      the two-step sub-structured SpMV of Section 3.4.1: local
+ *                    products, then assembly of interface contributions
+ *                    (Algorithms 4 and 5, every copy receives the same sum).
+ *   or_wdot          the interface-weighted dot of Section 3.4.2, w = 1/m.
+ *   or_sub_cg        Algorithm 3 with the sub-structured SpMV and weighted dots.
+ *   or_cholesky_solve  textbook dense Cholesky (second opinion on tiny systems).
+ *
+ * Readings where the paper is silent (no tolerance, no initial guess, no
+ * weights, no rule for splitting an assembled S_33) are stated at each function.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_INVALID 1
+#define OR_OOM 2
+#define OR_BREAKDOWN 4
+#define OR_NOT_CONVERGED 5
+
+/* ------------------------------------------------------------------ */
+/* Global CSR product (Section 2.2).                                   */
+/* ------------------------------------------------------------------ */
+void or_spmv(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, const double *x,
+             double *y) {
+    for (int32_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += val[k] * x[colidx[k]];
+        y[i] = s;
+    }
+}
+
+static double dot_plain(int64_t n, const double *u, const double *v) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += u[i] * v[i];
+    return s;
+}
+
+/*
+ * Algorithm 3 with M = I (z_k = r_k), on the assembled matrix.
+ * Reading: x1 = x (input, the initial guess); the loop stops after the first
+ * iteration k whose recursive residual satisfies sqrt(rho_k) <= rtol*||b||, or
+ * when max_iter iterations are done.  A zero right-hand side with x = 0 is
+ * converged at iteration 0.  (S p_k, p_k) <= 0 or non-finite is a breakdown.
+ * hist_alpha/hist_beta (may be NULL) receive alpha_k and beta_k per iteration
+ * (length >= max_iter); hist_res (may be NULL) receives sqrt(rho)/||b|| after
+ * each iteration.
+ */
+int or_cg(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, const double *b, double *x,
+          double rtol, int32_t max_iter, int32_t *iters_out, double *relres_out, double *hist_alpha,
+          double *hist_beta, double *hist_res) {
+    double *r = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *p = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *q = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!r || !p || !q) {
+        free(r); free(p); free(q);
+        return OR_OOM;
+    }
+    int status = OR_NOT_CONVERGED;
+    or_spmv(n, rowptr, colidx, val, x, q);
+    for (int32_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    for (int32_t i = 0; i < n; ++i) p[i] = r[i];
+    double rho = dot_plain(n, r, r);
+    double bnorm = sqrt(dot_plain(n, b, b));
+    int32_t k = 0;
+    double relres = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;
+    if (sqrt(rho) <= rtol * bnorm) status = OR_OK;
+    while (status == OR_NOT_CONVERGED && k < max_iter) {
+        or_spmv(n, rowptr, colidx, val, p, q);
+        double pq = dot_plain(n, q, p);
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            status = OR_BREAKDOWN;
+            break;
+        }
+        double alpha = rho / pq;
+        for (int32_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+        for (int32_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
+        double rho_new = dot_plain(n, r, r);
+        double beta = rho_new / rho;
+        for (int32_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+        if (hist_alpha) hist_alpha[k] = alpha;
+        if (hist_beta) hist_beta[k] = beta;
+        rho = rho_new;
+        ++k;
+        relres = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;
+        if (hist_res) hist_res[k - 1] = relres;
+        if (sqrt(rho) <= rtol * bnorm) status = OR_OK;
+    }
+    *iters_out = k;
+    *relres_out = relres;
+    free(r); free(p); free(q);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sub-structure data (Section 2.4, Section 3.4).                      */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t n, P;
+    int64_t nnz;
+    int64_t nloc;    /* sum over s of |V_s| */
+    int32_t ngamma;  /* number of interface nodes */
+    int64_t ncopies; /* sum of multiplicities over interface nodes */
+    int32_t *off;    /* [P+1] first concatenated local index of each subdomain */
+    int32_t *nint;   /* [P] number of interior (m = 1) nodes of each subdomain */
+    int32_t *l2g;    /* [nloc] global node of each concatenated local index */
+    int32_t *mult;   /* [n] multiplicity m_i */
+    int32_t *lrowptr;/* [nloc+1] concatenated local CSR row pointers */
+    int32_t *lcol;   /* [nnz] local column index inside its subdomain */
+    double *lval;    /* [nnz] values, copied unchanged from A */
+    int32_t *gamma;  /* [ngamma] interface nodes, ascending global id */
+    int32_t *iptr;   /* [ngamma+1] */
+    int32_t *icopy;  /* [ncopies] concatenated local index of each copy, ascending s */
+    int32_t *own;    /* [n] concatenated local index of the copy in subdomain part(i) */
+    double *w;       /* [nloc] weight 1/m of each local entry */
+} or_part;
+
+static int find_col(const int32_t *colidx, int32_t lo, int32_t hi, int32_t c) {
+    while (lo < hi) {
+        int32_t mid = lo + (hi - lo) / 2;
+        if (colidx[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+void or_part_free(or_part *h) {
+    if (!h) return;
+    free(h->off); free(h->nint); free(h->l2g); free(h->mult); free(h->lrowptr); free(h->lcol);
+    free(h->lval); free(h->gamma); free(h->iptr); free(h->icopy); free(h->own); free(h->w);
+    free(h);
+}
+
+/* owner subdomain of stored entry (i, j): the diagonal goes to part(i), an
+ * off-diagonal entry to min(part(i), part(j)) (reading for an assembled S). */
+static int32_t owner_of(const int32_t *part, int32_t i, int32_t j) {
+    if (i == j) return part[i];
+    return part[i] < part[j] ? part[i] : part[j];
+}
+
+typedef struct { int32_t key; int32_t a; double v; } triple;
+static int cmp_triple(const void *x, const void *y) {
+    const triple *p = (const triple *)x, *q = (const triple *)y;
+    return (p->key > q->key) - (p->key < q->key);
+}
+static int cmp_int(const void *x, const void *y) {
+    int32_t a = *(const int32_t *)x, b = *(const int32_t *)y;
+    return (a > b) - (a < b);
+}
+
+/*
+ * Build the sub-structures from a global CSR matrix and a node partition.
+ * Returns NULL with *status set on invalid input.  Checks: shapes, sorted and
+ * unique columns, part ids in [0, P), structural and value symmetry.
+ *
+ * V_s     = {i : part(i) = s}  U  {j : some i with part(i) = s < part(j) has A_ij stored}
+ * m_j     = number of subdomains whose V_s holds j; interface = {j : m_j >= 2}
+ * order   = in each V_s, nodes with m = 1 first, then interface nodes, each ascending by global id
+ *           ("interior then interface" numbering of Eq. 2.4:eqn0)
+ * A^(s)   = the stored entries owned by s, rows in local order, columns sorted by local id
+ * copies  = for each interface node (ascending id), its local copies in ascending s
+ */
+or_part *or_partition(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                      const int32_t *part, int32_t P, int *status) {
+    *status = OR_INVALID;
+    if (n <= 0 || P <= 0 || rowptr[0] != 0) return NULL;
+    for (int32_t i = 0; i < n; ++i) {
+        if (rowptr[i + 1] < rowptr[i]) return NULL;
+        if (part[i] < 0 || part[i] >= P) return NULL;
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            if (colidx[k] < 0 || colidx[k] >= n) return NULL;
+            if (k > rowptr[i] && colidx[k] <= colidx[k - 1]) return NULL;
+        }
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            int32_t j = colidx[k];
+            int32_t t = find_col(colidx, rowptr[j], rowptr[j + 1], i);
+            if (t >= rowptr[j + 1] || colidx[t] != i) return NULL;
+            if (val[t] != val[k]) return NULL;
+        }
+    }
+    *status = OR_OOM;
+    or_part *h = (or_part *)calloc(1, sizeof(or_part));
+    if (!h) return NULL;
+    h->n = n;
+    h->P = P;
+    h->nnz = rowptr[n];
+
+    /* membership: subdomain list of every node (sorted, unique) */
+    int32_t *mem_ptr = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    int32_t *cand = (int32_t *)malloc(sizeof(int32_t) * (size_t)(h->nnz + n));
+    int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)(h->nnz + n));
+    if (!mem_ptr || !cand || !mem) goto oom;
+    {
+        int64_t w = 0;
+        for (int32_t j = 0; j < n; ++j) {
+            int64_t c0 = 0;
+            cand[c0++] = part[j];
+            for (int32_t k = rowptr[j]; k < rowptr[j + 1]; ++k) {
+                int32_t i = colidx[k];
+                if (part[i] < part[j]) cand[c0++] = part[i];
+            }
+            qsort(cand, (size_t)c0, sizeof(int32_t), cmp_int);
+            for (int64_t t = 0; t < c0; ++t)
+                if (t == 0 || cand[t] != cand[t - 1]) mem[w++] = cand[t];
+            mem_ptr[j + 1] = (int32_t)w;
+        }
+    }
+    h->mult = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!h->mult) goto oom;
+    for (int32_t j = 0; j < n; ++j) h->mult[j] = mem_ptr[j + 1] - mem_ptr[j];
+
+    /* sizes and local numbering */
+    h->off = (int32_t *)calloc((size_t)P + 1, sizeof(int32_t));
+    h->nint = (int32_t *)calloc((size_t)P, sizeof(int32_t));
+    int32_t *cnt = (int32_t *)calloc((size_t)P, sizeof(int32_t));
+    if (!h->off || !h->nint || !cnt) { free(cnt); goto oom; }
+    for (int32_t j = 0; j < n; ++j)
+        for (int32_t t = mem_ptr[j]; t < mem_ptr[j + 1]; ++t) {
+            cnt[mem[t]]++;
+            if (h->mult[j] == 1) h->nint[mem[t]]++;
+        }
+    for (int32_t s = 0; s < P; ++s) h->off[s + 1] = h->off[s] + cnt[s];
+    h->nloc = h->off[P];
+    /* local index of node j inside each subdomain of its membership list */
+    int32_t *memloc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(mem_ptr[n] > 0 ? mem_ptr[n] : 1));
+    h->l2g = (int32_t *)malloc(sizeof(int32_t) * (size_t)(h->nloc > 0 ? h->nloc : 1));
+    if (!memloc || !h->l2g) { free(cnt); free(memloc); goto oom; }
+    for (int32_t s = 0; s < P; ++s) cnt[s] = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        /* pass 0: interior nodes (m = 1), pass 1: interface nodes, each ascending by id */
+        for (int32_t j = 0; j < n; ++j) {
+            int is_iface = h->mult[j] >= 2;
+            if (is_iface != pass) continue;
+            for (int32_t t = mem_ptr[j]; t < mem_ptr[j + 1]; ++t) {
+                int32_t s = mem[t];
+                memloc[t] = cnt[s]++;
+                h->l2g[h->off[s] + memloc[t]] = j;
+            }
+        }
+    }
+    free(cnt);
+
+    /* owner copy */
+    h->own = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!h->own) { free(memloc); goto oom; }
+    for (int32_t j = 0; j < n; ++j)
+        for (int32_t t = mem_ptr[j]; t < mem_ptr[j + 1]; ++t)
+            if (mem[t] == part[j]) h->own[j] = h->off[part[j]] + memloc[t];
+
+    /* local CSR */
+    h->lrowptr = (int32_t *)calloc((size_t)h->nloc + 1, sizeof(int32_t));
+    h->lcol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(h->nnz > 0 ? h->nnz : 1));
+    h->lval = (double *)malloc(sizeof(double) * (size_t)(h->nnz > 0 ? h->nnz : 1));
+    if (!h->lrowptr || !h->lcol || !h->lval) { free(memloc); goto oom; }
+    {
+        triple *row = (triple *)malloc(sizeof(triple) * (size_t)(n > 0 ? n : 1));
+        if (!row) { free(memloc); goto oom; }
+        int64_t wpos = 0;
+        for (int32_t s = 0; s < P; ++s) {
+            for (int32_t li = 0; li < h->off[s + 1] - h->off[s]; ++li) {
+                int32_t i = h->l2g[h->off[s] + li];
+                int32_t c = 0;
+                for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+                    int32_t j = colidx[k];
+                    if (owner_of(part, i, j) != s) continue;
+                    /* local id of j in s */
+                    int32_t lj = -1;
+                    for (int32_t t = mem_ptr[j]; t < mem_ptr[j + 1]; ++t)
+                        if (mem[t] == s) lj = memloc[t];
+                    if (lj < 0) { free(row); free(memloc); *status = OR_INVALID; goto fail; }
+                    row[c].key = lj;
+                    row[c].v = val[k];
+                    row[c].a = 0;
+                    ++c;
+                }
+                qsort(row, (size_t)c, sizeof(triple), cmp_triple);
+                for (int32_t t = 0; t < c; ++t) {
+                    h->lcol[wpos] = row[t].key;
+                    h->lval[wpos] = row[t].v;
+                    ++wpos;
+                }
+                h->lrowptr[h->off[s] + li + 1] = (int32_t)wpos;
+            }
+        }
+        free(row);
+        if (wpos != h->nnz) { free(memloc); *status = OR_INVALID; goto fail; }
+    }
+
+    /* interface lists */
+    h->ngamma = 0;
+    h->ncopies = 0;
+    for (int32_t j = 0; j < n; ++j)
+        if (h->mult[j] >= 2) { h->ngamma++; h->ncopies += h->mult[j]; }
+    h->gamma = (int32_t *)malloc(sizeof(int32_t) * (size_t)(h->ngamma > 0 ? h->ngamma : 1));
+    h->iptr = (int32_t *)calloc((size_t)h->ngamma + 1, sizeof(int32_t));
+    h->icopy = (int32_t *)malloc(sizeof(int32_t) * (size_t)(h->ncopies > 0 ? h->ncopies : 1));
+    if (!h->gamma || !h->iptr || !h->icopy) { free(memloc); goto oom; }
+    {
+        int32_t g = 0;
+        int64_t c = 0;
+        for (int32_t j = 0; j < n; ++j) {
+            if (h->mult[j] < 2) continue;
+            h->gamma[g] = j;
+            for (int32_t t = mem_ptr[j]; t < mem_ptr[j + 1]; ++t) h->icopy[c++] = h->off[mem[t]] + memloc[t];
+            h->iptr[++g] = (int32_t)c;
+        }
+    }
+    /* weights w = 1/m per local entry */
+    h->w = (double *)malloc(sizeof(double) * (size_t)(h->nloc > 0 ? h->nloc : 1));
+    if (!h->w) { free(memloc); goto oom; }
+    for (int64_t k = 0; k < h->nloc; ++k) h->w[k] = 1.0 / (double)h->mult[h->l2g[k]];
+    free(memloc);
+    free(mem_ptr); free(cand); free(mem);
+    *status = OR_OK;
+    return h;
+oom:
+    *status = OR_OOM;
+fail:
+    free(mem_ptr); free(cand); free(mem);
+    or_part_free(h);
+    return NULL;
+}
+
+void or_part_sizes(const or_part *h, int64_t *out) {
+    out[0] = h->n;
+    out[1] = h->P;
+    out[2] = h->nnz;
+    out[3] = h->nloc;
+    out[4] = h->ngamma;
+    out[5] = h->ncopies;
+}
+
+void or_part_copy(const or_part *h, int32_t *off, int32_t *nint, int32_t *l2g, int32_t *mult, int32_t *lrowptr,
+                  int32_t *lcol, double *lval, int32_t *gamma, int32_t *iptr, int32_t *icopy, int32_t *own,
+                  double *w) {
+    memcpy(off, h->off, sizeof(int32_t) * (size_t)(h->P + 1));
+    memcpy(nint, h->nint, sizeof(int32_t) * (size_t)h->P);
+    memcpy(l2g, h->l2g, sizeof(int32_t) * (size_t)h->nloc);
+    memcpy(mult, h->mult, sizeof(int32_t) * (size_t)h->n);
+    memcpy(lrowptr, h->lrowptr, sizeof(int32_t) * (size_t)(h->nloc + 1));
+    memcpy(lcol, h->lcol, sizeof(int32_t) * (size_t)h->nnz);
+    memcpy(lval, h->lval, sizeof(double) * (size_t)h->nnz);
+    memcpy(gamma, h->gamma, sizeof(int32_t) * (size_t)h->ngamma);
+    memcpy(iptr, h->iptr, sizeof(int32_t) * (size_t)(h->ngamma + 1));
+    memcpy(icopy, h->icopy, sizeof(int32_t) * (size_t)h->ncopies);
+    memcpy(own, h->own, sizeof(int32_t) * (size_t)h->n);
+    memcpy(w, h->w, sizeof(double) * (size_t)h->nloc);
+}
+
+/* global -> local: every copy of node i receives x_glob[i] */
+void or_scatter(const or_part *h, const double *xg, double *xl) {
+    for (int64_t k = 0; k < h->nloc; ++k) xl[k] = xg[h->l2g[k]];
+}
+
+/* local -> global: node i takes the value of its copy in subdomain part(i) */
+void or_gather(const or_part *h, const double *xl, double *xg) {
+    for (int32_t i = 0; i < h->n; ++i) xg[i] = xl[h->own[i]];
+}
+
+/*
+ * Section 3.4.1: y_s = A^(s) x_s for every subdomain (rows in local order,
+ * each row summed left to right), then, for every interface node in ascending
+ * global id, the sum of its copies' values taken in ascending s is written back
+ * to every copy (the collect/send and receive/update of Algorithms 4 and 5 with
+ * one fixed summation order).
+ */
+void or_sub_spmv(const or_part *h, const double *xl, double *yl) {
+    for (int32_t s = 0; s < h->P; ++s) {
+        const int32_t o = h->off[s];
+        for (int32_t li = 0; li < h->off[s + 1] - o; ++li) {
+            double acc = 0.0;
+            for (int32_t k = h->lrowptr[o + li]; k < h->lrowptr[o + li + 1]; ++k)
+                acc += h->lval[k] * xl[o + h->lcol[k]];
+            yl[o + li] = acc;
+        }
+    }
+    for (int32_t g = 0; g < h->ngamma; ++g) {
+        double S = 0.0;
+        for (int32_t c = h->iptr[g]; c < h->iptr[g + 1]; ++c) S += yl[h->icopy[c]];
+        for (int32_t c = h->iptr[g]; c < h->iptr[g + 1]; ++c) yl[h->icopy[c]] = S;
+    }
+}
+
+/* Section 3.4.2 weighted dot: sum over concatenated local entries of w*u*v,
+ * w = 1/m (reading: the paper does not give the weights). */
+double or_wdot(const or_part *h, const double *u, const double *v) {
+    double s = 0.0;
+    for (int64_t k = 0; k < h->nloc; ++k) s += h->w[k] * u[k] * v[k];
+    return s;
+}
+
+/*
+ * Algorithm 3 (M = I) with the sub-structured SpMV and weighted dots, on the
+ * concatenated local vectors; b and x are global (length n).  x is the
+ * initial guess on input.  Same stopping rule and outputs as or_cg.
+ */
+int or_sub_cg(const or_part *h, const double *b, double *x, double rtol, int32_t max_iter, int32_t *iters_out,
+              double *relres_out, double *hist_alpha, double *hist_beta, double *hist_res) {
+    size_t N = (size_t)(h->nloc > 0 ? h->nloc : 1);
+    double *bl = (double *)malloc(sizeof(double) * N);
+    double *xl = (double *)malloc(sizeof(double) * N);
+    double *r = (double *)malloc(sizeof(double) * N);
+    double *p = (double *)malloc(sizeof(double) * N);
+    double *q = (double *)malloc(sizeof(double) * N);
+    if (!bl || !xl || !r || !p || !q) {
+        free(bl); free(xl); free(r); free(p); free(q);
+        return OR_OOM;
+    }
+    const int64_t L = h->nloc;
+    or_scatter(h, b, bl);
+    or_scatter(h, x, xl);
+    or_sub_spmv(h, xl, q);
+    for (int64_t k = 0; k < L; ++k) r[k] = bl[k] - q[k];
+    for (int64_t k = 0; k < L; ++k) p[k] = r[k];
+    double rho = or_wdot(h, r, r);
+    double bnorm = sqrt(or_wdot(h, bl, bl));
+    int status = OR_NOT_CONVERGED;
+    int32_t it = 0;
+    double relres = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;
+    if (sqrt(rho) <= rtol * bnorm) status = OR_OK;
+    while (status == OR_NOT_CONVERGED && it < max_iter) {
+        or_sub_spmv(h, p, q);
+        double pq = or_wdot(h, q, p);
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            status = OR_BREAKDOWN;
+            break;
+        }
+        double alpha = rho / pq;
+        for (int64_t k = 0; k < L; ++k) xl[k] = xl[k] + alpha * p[k];
+        for (int64_t k = 0; k < L; ++k) r[k] = r[k] - alpha * q[k];
+        double rho_new = or_wdot(h, r, r);
+        double beta = rho_new / rho;
+        for (int64_t k = 0; k < L; ++k) p[k] = r[k] + beta * p[k];
+        if (hist_alpha) hist_alpha[it] = alpha;
+        if (hist_beta) hist_beta[it] = beta;
+        rho = rho_new;
+        ++it;
+        relres = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;
+        if (hist_res) hist_res[it - 1] = relres;
+        if (sqrt(rho) <= rtol * bnorm) status = OR_OK;
+    }
+    or_gather(h, xl, x);
+    *iters_out = it;
+    *relres_out = relres;
+    free(bl); free(xl); free(r); free(p); free(q);
+    return status;
+}
+
+/* Textbook dense Cholesky A = L L^T (row-major n x n), then two triangular
+ * solves.  Returns OR_BREAKDOWN if a pivot is not positive. */
+int or_cholesky_solve(int32_t n, const double *A, const double *b, double *x) {
+    double *L = (double *)calloc((size_t)n * (size_t)n, sizeof(double));
+    double *y = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!L || !y) { free(L); free(y); return OR_OOM; }
+    for (int32_t j = 0; j < n; ++j) {
+        double d = A[(size_t)j * n + j];
+        for (int32_t k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        if (!(d > 0.0)) { free(L); free(y); return OR_BREAKDOWN; }
+        double ljj = sqrt(d);
+        L[(size_t)j * n + j] = ljj;
+        for (int32_t i = j + 1; i < n; ++i) {
+            double s = A[(size_t)i * n + j];
+            for (int32_t k = 0; k < j; ++k) s -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            L[(size_t)i * n + j] = s / ljj;
+        }
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int32_t k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * y[k];
+        y[i] = s / L[(size_t)i * n + i];
+    }
+    for (int32_t i = n - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int32_t k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * x[k];
+        x[i] = s / L[(size_t)i * n + i];
+    }
+    free(L); free(y);
+    return OR_OK;
+}
