@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""Benchmark: sub-structured CG time-to-1e-8 on the 128^3 finite-volume system.
+
+Workload: 3D 7-point variable-coefficient diffusion on 128^3 cells
+(kappa = exp(g), g ~ N(0,1) per cell, harmonic-mean faces), 4x4x4 box split
+into 64 subdomains, b = A x* with x* ~ U[-1,1], seeded.  One step = one
+complete solve (Algorithm 3, M = I) from x = 0 to a recursive relative
+residual of 1e-8, with b already resident on the device.
+
+Prints one JSON line.  Besides the time per solve it reports the roofline of
+the dominant kernel (fused sub-structured SpMV + interface assembly) measured
+live with CUDA events, the end-to-end time through the host-buffer C ABI
+call, the SM clocks sampled during the timed region, and (rank 0, one GPU)
+the FP64 CPU oracle timed on a bounded sample of the same solve.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own replica of the workload (the
+path has no cross-GPU exchange on one node: "replicas only"); the reported
+time is the maximum over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sub-structured CG time-to-1e-8 rel residual; SpMV+assembly HBM GB/s vs peak"
+UNIT = "s"
+RTOL = 1e-8
+WORKLOAD = "fv3d_7pt_128^3_kappa=exp(N(0,1))_4x4x4_subdomains"
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_RECORD = os.path.join(ROOT, "profiles", "spmv_asm_fp64_fv3d128.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2108_13162_gb300", "csrc", "kernels.cuh")
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_fv3d_128_4x4x4.json")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--spmv-reps", type=int, default=30)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU time budget of the oracle sample")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------- distributed helpers
+class Dist:
+    """Rank bookkeeping for torchrun launches; a no-op for one process."""
+
+    def __init__(self, backend=None):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = False
+        if self.world > 1:
+            import torch.distributed as dist
+
+            if backend is None:
+                import torch
+
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                import torch
+
+                torch.cuda.set_device(self.local_rank)
+            dist.init_process_group(backend=backend)
+            self.pg = True
+            self.backend = backend
+
+    def barrier(self):
+        if self.pg:
+            import torch.distributed as dist
+
+            if self.backend == "nccl":
+                import torch
+
+                dist.barrier(device_ids=[self.local_rank])
+            else:
+                dist.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return float(v)
+        import torch
+        import torch.distributed as dist
+
+        dev = "cuda:%d" % self.local_rank if self.backend == "nccl" else "cpu"
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if not self.pg:
+            return float(v)
+        import torch
+        import torch.distributed as dist
+
+        dev = "cuda:%d" % self.local_rank if self.backend == "nccl" else "cpu"
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) of SM clocks and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = str(device_index)
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.dev, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.remove(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": reasons,
+            "samples": len(rows),
+        }
+
+
+def _device_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+# ----------------------------------------------------------------------------- workload
+def make_workload():
+    from synth import config_problem
+
+    return config_problem(2)
+
+
+def spmv_algorithmic_bytes(sizes) -> int:
+    """Bytes the fused sub-structured SpMV must move once per launch (FP64
+    values, int32 indices, each x and y entry once): matrix 12*nnz, row
+    pointers 4*(nloc+1), x 8*nloc, y 8*nloc, interface lists
+    4*ncopies + 4*(ngamma+1)."""
+    return (12 * sizes.nnz + 4 * (sizes.nloc + 1) + 16 * sizes.nloc + 4 * sizes.ncopies + 4 * (sizes.ngamma + 1))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic():
+    """Per-launch DRAM bytes from the committed ncu summary, only if the
+    kernel source is unchanged since the counters were taken."""
+    try:
+        text = open(PROFILE_RECORD).read()
+        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    rec = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            rec[k.strip()] = v.strip().strip("`")
+    if rec.get("kernel_source_sha256") != src:
+        return None
+    try:
+        return int(rec["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def golden_iters():
+    try:
+        with open(GOLDEN) as f:
+            return int(json.load(f)["iters"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(prob, iters_full, seconds):
+    """Time the FP64 oracle's sub-structured CG on a bounded number of
+    iterations of the same solve; returns (seconds per full solve, sample text)."""
+    import oracle
+
+    part = oracle.Partition(prob.A, prob.part, prob.P)
+    b = prob.b[:, 0]
+    t0 = time.perf_counter()
+    part.cg(b, 0.0, 3)
+    t_probe = (time.perf_counter() - t0) / 3
+    m = int(max(5, min(iters_full, seconds / max(t_probe, 1e-6))))
+    t0 = time.perf_counter()
+    r = part.cg(b, 0.0, m)
+    dt = time.perf_counter() - t0
+    per_iter = dt / max(r.iters, 1)
+    sample = ("oracle sub-structured CG (plain C, FP64, one thread): first %d of %d iterations of the same "
+              "128^3 solve, %.1f s, scaled to %d iterations" % (r.iters, iters_full, dt, iters_full))
+    return per_iter * iters_full, sample, r.iters, dt
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return 0
+    prob = make_workload()
+    iters_full = golden_iters() or 1065
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, sample, m, dt = oracle_sample(prob, iters_full, per_step)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": value * 1e3,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": prob.A.n, "nnz": prob.A.nnz, "rtol": RTOL, "mode": "fp64",
+                   "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, dist):
+    import numpy as np
+    import torch
+
+    from paper_2108_13162_gb300 import build as ssg_build
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import Context, System
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    ssg_build.build()
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    prob = make_workload()
+    ctx = Context(dev, stream)
+    S = System(ctx, prob.A, prob.part, prob.P)
+    b = torch.from_numpy(prob.b[:, 0].copy()).to("cuda:%d" % dev)
+    x = torch.zeros_like(b)
+
+    def solve():
+        x.zero_()
+        rc, st = ssg.ssg_solve(S.h, 1, b, x, False, RTOL, 0, ssg.SSG_FP64)
+        if rc != ssg.SSG_OK:
+            raise RuntimeError("solve did not converge: %r" % st)
+        return st[0]
+
+    for _ in range(max(args.warmup, 0)):
+        solve()
+    clocks = ClockSampler(_device_index(dev))
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches = 0
+    iters = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = solve()
+        launches += st["kernel_launches"]
+        iters.append(st["iters"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    ms_step = dist.max(elapsed_ms / args.steps)
+    true_res = st["true_relres"]
+
+    # end to end through the host-buffer C ABI call (pinned host memory)
+    bh = torch.from_numpy(prob.b[:, 0].copy()).pin_memory().numpy()
+    xh = torch.zeros(prob.A.n, dtype=torch.float64).pin_memory().numpy()
+    ssg.ssg_solve_host(S.h, 1, bh, xh, False, RTOL, 0, ssg.SSG_FP64)
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rc, _ = ssg.ssg_solve_host(S.h, 1, bh, xh, False, RTOL, 0, ssg.SSG_FP64)
+    e2e_s = dist.max((time.perf_counter() - t0) / args.steps)
+
+    # roofline of the dominant kernel: fused SpMV + interface assembly, CUDA
+    # events on the launching stream, inputs (175 MB of matrix) larger than L2
+    xl = S.scatter(b)
+    y = torch.empty_like(xl)
+    for _ in range(3):
+        S.spmv(xl, y)
+    torch.cuda.synchronize()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(args.spmv_reps):
+        S.spmv(xl, y)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    spmv_s = k0.elapsed_time(k1) / 1e3 / args.spmv_reps
+    nbytes = spmv_algorithmic_bytes(S.sizes)
+    peak, peak_src = measured_peaks()
+    achieved = nbytes / spmv_s / 1e9
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        v, sample, m, dt = oracle_sample(prob, int(statistics.median(iters)), args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    value = ms_step / 1e3
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": dist.world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD,
+            "n": prob.A.n,
+            "nnz": prob.A.nnz,
+            "nloc": S.sizes.nloc,
+            "interface_nodes": S.sizes.ngamma,
+            "subdomains": prob.P,
+            "rtol": RTOL,
+            "mode": "fp64",
+            "iters": int(statistics.median(iters)),
+            "true_relres": true_res,
+            "us_per_iter": ms_step * 1e3 / statistics.median(iters),
+            "l2": "inputs larger than L2 (175 MB matrix + 5 x 18 MB vectors > 129 MB)",
+            "parallelism": "replicas" if dist.world > 1 else "single",
+        },
+        "roofline": {
+            "kernel": "k_spmv_asm (fused local CSR SpMV + interface assembly + (p,Sp)_w partials)",
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": peak,
+            "peak_source": peak_src,
+            "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": profiled_traffic(),
+            "algorithmic_bytes": nbytes,
+            "launch_us": spmv_s * 1e6,
+        },
+        "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * prob.A.n, "d2h_bytes_per_step": 8 * prob.A.n},
+        "gpu_launches": int(dist.sum(launches)),
+        "clocks": ck,
+        "cpu_baseline": cpu,
+    }
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    S.close()
+    ctx.close()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        # rank 0 alone times the CPU oracle; other ranks exit without work
+        dist = Dist.__new__(Dist)
+        dist.world = int(os.environ.get("WORLD_SIZE", "1"))
+        dist.rank = int(os.environ.get("RANK", "0"))
+        dist.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        dist.pg = False
+        return run_reference(args, dist)
+    dist = Dist()
+    try:
+        return run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * ssg.h - sub-structured Conjugate Gradient on one GPU (C ABI).
+ *
+ * Cheik Ahamed & Magoules, "Parallel Sub-Structuring Methods for solving
+ * Sparse Linear Systems on a cluster of GPU".  The problem statement the ABI
+ * follows: a sparse symmetric positive-definite system S u = f in CSR form
+ * (Section 2.2, Section 2.4 Eq. linear_systems) is split into sub-structures
+ * (Section 2.4: local matrices S_i whose interface blocks sum to S_33,
+ * Eq. mat_subdomains / interface_summation) and solved with the Conjugate
+ * Gradient (Algorithm 3) whose SpMV is the two-step local product plus
+ * interface assembly (Section 3.4.1, Algorithms 4 and 5) and whose dot
+ * products are interface-weighted (Section 3.4.2).  All subdomains live on
+ * one GPU; the interface exchange is an on-device gather-sum-scatter.
+ *
+ * Conventions for every call:
+ *   - Return value: SSG_OK (0) or one of the SSG_E_* codes below.  No C++
+ *     exception crosses the ABI.  ssg_last_error() gives a thread-local
+ *     message for the last failing call on the calling thread.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory on the context's device.  The library never takes
+ *     ownership of caller memory; it owns (and frees in *_destroy) every
+ *     buffer it allocates.
+ *   - Device work is ordered on the context's stream (ssg_create).  Calls
+ *     that return host results (ssg_solve*, ssg_copy_maps) synchronise that
+ *     stream before returning; the others are asynchronous, and caller device
+ *     buffers must stay valid until the stream has passed them.
+ *   - Integer types are fixed width; all indices are 0-based int32.
+ *   - Local vectors ("x_loc") are the concatenation over subdomains
+ *     s = 0..P-1 of the local vectors of V_s (length nloc, ssg_sizes).  Every
+ *     interface node has one entry per subdomain holding it; a vector is
+ *     "consistent" when all copies of a node are equal.
+ */
+#ifndef SSG_H
+#define SSG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SSG_OK 0
+#define SSG_E_INVALID 1       /* bad argument, shape, index, partition id or asymmetric matrix */
+#define SSG_E_OOM 2           /* host or device allocation failed */
+#define SSG_E_CUDA 3          /* a CUDA runtime call failed (message in ssg_last_error) */
+#define SSG_E_BREAKDOWN 4     /* (S p, p) <= 0 or not finite: matrix not SPD (Algorithm 3 line 3) */
+#define SSG_E_NOT_CONVERGED 5 /* max_iter reached; x and stats hold the last iterate */
+#define SSG_E_TIMEOUT 6       /* reserved: a bounded device wait expired */
+
+/* solve modes */
+#define SSG_FP64 0  /* Algorithm 3 in FP64 throughout */
+#define SSG_MIXED 1 /* FP32 inner CG inside FP64 iterative refinement */
+
+/* driver modes (ssg_set_driver) */
+#define SSG_DRIVER_GRAPH 0 /* one CUDA-graph launch per solve, device-side while loop */
+#define SSG_DRIVER_HOST 1  /* host loop of direct launches, done-flag polled every 32 iterations */
+
+typedef struct ssg_ctx ssg_ctx;
+typedef struct ssg_system ssg_system;
+
+typedef struct {
+    int32_t n;        /* global unknowns */
+    int32_t P;        /* subdomains */
+    int64_t nnz;      /* stored nonzeros of S (= sum of local nonzeros) */
+    int64_t nloc;     /* sum over s of |V_s| (length of local vectors) */
+    int32_t ngamma;   /* interface nodes (multiplicity >= 2) */
+    int32_t max_mult; /* largest multiplicity */
+    int64_t ncopies;  /* sum of multiplicities over interface nodes */
+} ssg_sizes;
+
+typedef struct {
+    int32_t status;          /* SSG_OK, SSG_E_BREAKDOWN or SSG_E_NOT_CONVERGED for this right-hand side */
+    int32_t iters;           /* CG iterations (mixed mode: inner iterations summed over refinements) */
+    int32_t outer;           /* refinement steps (mixed mode); 1 in FP64 mode */
+    int32_t reserved;
+    double relres;           /* final recursive residual sqrt((r,r)_w) / sqrt((b,b)_w) */
+    double true_relres;      /* ||b - S x|| / ||b|| recomputed in FP64 after the solve */
+    double solve_ms;         /* device time of this solve (CUDA events on the context stream) */
+    int64_t kernel_launches; /* kernels executed on the device for this solve */
+} ssg_stats;
+
+/*
+ * Create a context on CUDA device `device`; work is issued on `stream`
+ * (a cudaStream_t, or NULL for the legacy default stream).  The stream is
+ * borrowed and must outlive the context.
+ */
+int ssg_create(ssg_ctx **ctx, int device, void *stream);
+/* Change the stream later calls on this context use (borrowed). */
+int ssg_set_stream(ssg_ctx *ctx, void *stream);
+/* Pick how ssg_solve drives the iteration (SSG_DRIVER_*); default GRAPH. */
+int ssg_set_driver(ssg_ctx *ctx, int driver);
+int ssg_destroy(ssg_ctx *ctx);
+
+/*
+ * Sub-structuring of Section 2.4 (Eq. 2.4:eqn0, mat_subdomains,
+ * interface_summation) for an assembled matrix, plus the interface lists of
+ * Section 3.4.2 ("the list of nodes along the interface and the number of
+ * neighboring sub-domains").
+ *
+ * Inputs (host, copied): S in 0-based CSR (rowptr[n+1], colidx[nnz],
+ * val[nnz]); columns sorted and unique in each row; the pattern and the values
+ * symmetric (exactly); part[n] gives the subdomain 0..P-1 of every node.
+ * Rules (where the paper only treats finite-element assembly, the reading for
+ * an assembled matrix):
+ *   V_s = {i : part(i) = s} U {j : A_ij stored for some i with part(i) = s < part(j)}
+ *   m_j = number of V_s holding j; interface nodes have m_j >= 2 (m_j <= 255)
+ *   local order in V_s: nodes with m = 1 ascending by id, then interface nodes
+ *   ascending by id (interior first, interface last, as in Eq. 2.4:eqn0)
+ *   entry (i,i) belongs to S^(part(i)); entry (i,j), i != j, to
+ *   S^(min(part(i), part(j))), so the local matrices sum exactly to S.
+ *   Interface copies of a node are listed in ascending subdomain order.
+ * With ctx == NULL only the host maps are built (ssg_get_sizes and
+ * ssg_copy_maps work; device calls return SSG_E_INVALID).  Otherwise the
+ * device arena is allocated and filled on the context stream.
+ * Errors: SSG_E_INVALID for any malformed input, SSG_E_OOM, SSG_E_CUDA.
+ */
+int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                  const int32_t *part, int32_t P, ssg_system **sys);
+
+int ssg_get_sizes(const ssg_system *sys, ssg_sizes *out);
+
+/*
+ * Copy the sub-structure maps into caller host buffers (any pointer may be
+ * NULL to skip it).  Sizes from ssg_sizes:
+ *   off[P+1]      first concatenated local index of each subdomain
+ *   nint[P]       interior (m = 1) nodes of each subdomain (they come first)
+ *   l2g[nloc]     global node of each local entry (the local-to-global map, Section 2)
+ *   mult[n]       multiplicity of every global node
+ *   lrowptr[nloc+1], lcol[nnz], lval[nnz]
+ *                 local matrices, concatenated; lcol holds the column's local
+ *                 index inside its own subdomain; values copied unchanged
+ *   gamma[ngamma] interface nodes, ascending global id
+ *   iptr[ngamma+1], icopy[ncopies]
+ *                 concatenated local indices of each interface node's copies,
+ *                 ascending subdomain
+ *   own[n]        local index of node i's copy in subdomain part(i)
+ */
+int ssg_copy_maps(const ssg_system *sys, int32_t *off, int32_t *nint, int32_t *l2g, int32_t *mult,
+                  int32_t *lrowptr, int32_t *lcol, double *lval, int32_t *gamma, int32_t *iptr, int32_t *icopy,
+                  int32_t *own);
+
+/* Global -> local: x_loc[k] = x_glob[l2g[k]] (device pointers, n and nloc long). */
+int ssg_scatter(ssg_system *sys, const double *x_glob, double *x_loc);
+/* Local -> global: x_glob[i] = x_loc[own[i]] (device pointers). */
+int ssg_gather(ssg_system *sys, const double *x_loc, double *x_glob);
+
+/*
+ * The sub-structured SpMV of Section 3.4.1: local products y_s = S_s x_s for
+ * every subdomain, then assembly of the interface contributions (the
+ * collect/send and receive/update of Algorithms 4 and 5, done on the device):
+ * every copy of an interface node receives the sum of its copies' local
+ * values, summed in ascending subdomain order.  x_loc must be consistent for
+ * y_loc to be the global product.  Device pointers, nloc long, must not
+ * overlap.  If xSx_dev is not NULL it receives (x, S x)_w on the device.
+ */
+int ssg_spmv_assembled(ssg_system *sys, const double *x_loc, double *y_loc, double *xSx_dev);
+
+/*
+ * Interface-weighted dot of Section 3.4.2: result = sum_k w_k u_k v_k over the
+ * nloc local entries with w_k = 1/m of the entry's node (equals the global dot
+ * for consistent vectors).  Device pointers; *result_dev is written on the
+ * device.  Deterministic for a given system.
+ */
+int ssg_wdot(ssg_system *sys, const double *u_loc, const double *v_loc, double *result_dev);
+
+/*
+ * Solve S x = b for k right-hand sides with Algorithm 3 (M = I) on the
+ * sub-structured operator.  b and x are device pointers to n*k doubles,
+ * right-hand side j at offset j*n.  If x_is_guess is nonzero x holds the
+ * initial guess x_1, else the iteration starts from 0.  Readings where the
+ * paper is silent: stop after the first iteration with
+ * sqrt((r,r)_w) <= rtol * sqrt((b,b)_w) (recursive residual) or after
+ * max_iter iterations (max_iter <= 0 means n).  mode = SSG_FP64 or SSG_MIXED.
+ * stats (host, may be NULL) receives k entries.  Blocks until done.
+ * Returns SSG_OK when every right-hand side converged, else the first
+ * non-OK per-RHS status (x still holds the last iterates).
+ */
+int ssg_solve(ssg_system *sys, int32_t k, const double *b, double *x, int32_t x_is_guess, double rtol,
+              int32_t max_iter, int32_t mode, ssg_stats *stats);
+
+/* Same as ssg_solve with b and x in host memory (copied in and out on the
+ * context stream inside the call). */
+int ssg_solve_host(ssg_system *sys, int32_t k, const double *b_host, double *x_host, int32_t x_is_guess,
+                   double rtol, int32_t max_iter, int32_t mode, ssg_stats *stats);
+
+int ssg_system_destroy(ssg_system *sys);
+
+const char *ssg_error_string(int status);
+const char *ssg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSG_H */

@@ -1,0 +1,598 @@
+// C ABI of the sub-structured CG library: contexts, device upload of the
+// sub-structures, the SpMV/dot entry points and the solve driver.
+//
+// The solve runs Algorithm 3 (M = I) with the whole iteration on the device:
+// one CUDA graph holds the setup kernel and a conditional WHILE node whose
+// body is {sub-structured SpMV + alpha, residual update + beta, x/p update};
+// the kernels decide convergence and clear the loop condition themselves, so
+// the host synchronises once per solve.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "ssg_internal.h"
+
+namespace ssg {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+}  // namespace ssg
+
+using namespace ssg;
+
+struct ssg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int driver = SSG_DRIVER_GRAPH;
+    int num_sms = 0;
+};
+
+struct ssg_system {
+    ssg_ctx *ctx = nullptr;
+    HostMaps maps;
+    bool on_device = false;
+    // device arena
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    DevOp op{};
+    int32_t *d_l2g = nullptr;
+    int32_t *d_own = nullptr;
+    // solver state
+    double *d_bl = nullptr, *d_xl = nullptr, *d_r = nullptr, *d_p = nullptr, *d_q = nullptr;
+    double *d_partials = nullptr;
+    int32_t n_partials = 0;
+    Scal *d_scal = nullptr;     // CG state
+    Scal *d_scal_op = nullptr;  // state for the stand-alone SpMV / dot calls
+    double *d_xg = nullptr, *d_bg = nullptr;  // global staging for ssg_solve_host
+    int grid_spmv = 0;
+    int grid_vec = 0;
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+#define SSG_CUDA_TRY(call)                                                                      \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) {                                                                \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+            return e_ == cudaErrorMemoryAllocation ? SSG_E_OOM : SSG_E_CUDA;                    \
+        }                                                                                       \
+    } while (0)
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Greedy interior tiles: consecutive interior rows of one subdomain, at most
+// kTileRows rows and kTileNnz nonzeros; a longer row gets a tile of its own.
+std::vector<int2> make_tiles(const HostMaps &M) {
+    std::vector<int2> t;
+    for (int32_t s = 0; s < M.P; ++s) {
+        int32_t r = M.off[s];
+        const int32_t rend = M.off[s] + M.nint[s];
+        while (r < rend) {
+            int32_t r1 = r;
+            const int32_t e0 = M.lrowptr[r];
+            while (r1 < rend && r1 - r < kTileRows && M.lrowptr[r1 + 1] - e0 <= kTileNnz) ++r1;
+            if (r1 == r) r1 = r + 1;  // single long row
+            t.push_back(make_int2(r, r1));
+            r = r1;
+        }
+    }
+    return t;
+}
+
+int launch_body(ssg_system *S, cudaStream_t st, int use_cond) {
+    const int64_t N = S->maps.nloc;
+    k_spmv_asm<kEpiAlpha><<<S->grid_spmv, kBlock, 0, st>>>(S->op, S->d_p, S->d_q, S->d_partials, S->d_scal,
+                                                           nullptr, S->cond, use_cond);
+    k_update_r<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_r, S->d_q, S->op.mult, S->op.wtab, S->d_partials,
+                                               S->d_scal);
+    k_update_xp<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_xl, S->d_p, S->d_r, S->d_partials, S->d_scal, S->cond,
+                                                use_cond);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int launch_init(ssg_system *S, cudaStream_t st, int use_cond) {
+    k_cg_init<<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_bl, S->d_q, S->d_r, S->d_p, S->op.mult,
+                                              S->op.wtab, S->d_partials, S->d_scal, S->cond, use_cond);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int build_graph(ssg_system *S) {
+    if (S->exec) return SSG_OK;
+    SSG_CUDA_TRY(cudaGraphCreate(&S->graph, 0));
+    SSG_CUDA_TRY(cudaGraphConditionalHandleCreate(&S->cond, S->graph, 0u, cudaGraphCondAssignDefault));
+    cudaStream_t cap;
+    SSG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int rc = SSG_OK;
+    // setup kernel
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cap, S->graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        rc = launch_init(S, cap, 1);
+        cudaGraph_t g2 = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g2);
+        if (rc == SSG_OK && e2 != cudaSuccess) e = e2;
+    }
+    cudaGraphNode_t init_node = nullptr;
+    if (e == cudaSuccess && rc == SSG_OK) {
+        size_t nn = 0;
+        e = cudaGraphGetNodes(S->graph, nullptr, &nn);
+        if (e == cudaSuccess && nn == 1) e = cudaGraphGetNodes(S->graph, &init_node, &nn);
+    }
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess && rc == SSG_OK) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = S->cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        e = cudaGraphAddNode(&cnode, S->graph, &init_node, nullptr, 1, &cp);
+        if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess && rc == SSG_OK) {
+        e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            rc = launch_body(S, cap, 1);
+            cudaGraph_t g3 = nullptr;
+            cudaError_t e3 = cudaStreamEndCapture(cap, &g3);
+            if (rc == SSG_OK && e3 != cudaSuccess) e = e3;
+        }
+    }
+    if (e == cudaSuccess && rc == SSG_OK) e = cudaGraphInstantiate(&S->exec, S->graph, 0);
+    cudaStreamDestroy(cap);
+    if (rc != SSG_OK) return rc;
+    if (e != cudaSuccess) {
+        set_error(std::string("building the CG graph: ") + cudaGetErrorString(e));
+        if (S->graph) cudaGraphDestroy(S->graph);
+        S->graph = nullptr;
+        S->exec = nullptr;
+        return SSG_E_CUDA;
+    }
+    return SSG_OK;
+}
+
+int upload(ssg_system *S) {
+    const HostMaps &M = S->maps;
+    ssg_ctx *C = S->ctx;
+    SSG_CUDA_TRY(cudaSetDevice(C->device));
+    std::vector<int2> tiles = make_tiles(M);
+    const int64_t N = M.nloc;
+    // concatenated column ids
+    std::vector<int32_t> gcol(static_cast<size_t>(M.nnz));
+    for (int32_t s = 0; s < M.P; ++s)
+        for (int64_t r = M.off[s]; r < M.off[s + 1]; ++r)
+            for (int32_t k = M.lrowptr[r]; k < M.lrowptr[r + 1]; ++k) gcol[k] = M.off[s] + M.lcol[k];
+    std::vector<uint8_t> mloc(static_cast<size_t>(N));
+    for (int64_t k = 0; k < N; ++k) mloc[k] = static_cast<uint8_t>(M.mult[M.l2g[k]]);
+    std::vector<double> wtab(256, 0.0);
+    for (int m = 1; m < 256; ++m) wtab[m] = 1.0 / static_cast<double>(m);
+
+    const int niface_blocks = (M.ngamma + kBlock - 1) / kBlock;
+    S->grid_spmv = niface_blocks + static_cast<int>(tiles.size());
+    S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N + kBlock - 1) / kBlock), C->num_sms * 8));
+    S->n_partials = 2 * std::max(S->grid_spmv, S->grid_vec);
+
+    struct Piece {
+        const void *src;
+        size_t bytes;
+        size_t off;
+    };
+    std::vector<Piece> pieces;
+    size_t total = 0;
+    auto add = [&](const void *src, size_t bytes) {
+        pieces.push_back({src, bytes, total});
+        total = align_up(total + std::max<size_t>(bytes, 1), 256);
+        return pieces.size() - 1;
+    };
+    size_t i_rowptr = add(M.lrowptr.data(), sizeof(int32_t) * (N + 1));
+    size_t i_col = add(gcol.data(), sizeof(int32_t) * M.nnz);
+    size_t i_val = add(M.lval.data(), sizeof(double) * M.nnz);
+    size_t i_tiles = add(tiles.data(), sizeof(int2) * tiles.size());
+    size_t i_iptr = add(M.iptr.data(), sizeof(int32_t) * (M.ngamma + 1));
+    size_t i_icopy = add(M.icopy.data(), sizeof(int32_t) * M.ncopies);
+    size_t i_mult = add(mloc.data(), N);
+    size_t i_wtab = add(wtab.data(), sizeof(double) * 256);
+    size_t i_l2g = add(M.l2g.data(), sizeof(int32_t) * N);
+    size_t i_own = add(M.own.data(), sizeof(int32_t) * M.n);
+    size_t i_bl = add(nullptr, sizeof(double) * N);
+    size_t i_xl = add(nullptr, sizeof(double) * N);
+    size_t i_r = add(nullptr, sizeof(double) * N);
+    size_t i_p = add(nullptr, sizeof(double) * N);
+    size_t i_q = add(nullptr, sizeof(double) * N);
+    size_t i_part = add(nullptr, sizeof(double) * S->n_partials);
+    size_t i_scal = add(nullptr, sizeof(Scal));
+    size_t i_scal2 = add(nullptr, sizeof(Scal));
+    size_t i_xg = add(nullptr, sizeof(double) * M.n);
+    size_t i_bg = add(nullptr, sizeof(double) * M.n);
+
+    cudaError_t e = cudaMalloc(&S->arena, total);
+    if (e != cudaSuccess) {
+        set_error(std::string("device arena of ") + std::to_string(total) + " bytes: " + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? SSG_E_OOM : SSG_E_CUDA;
+    }
+    S->arena_bytes = total;
+    char *base = static_cast<char *>(S->arena);
+    for (const Piece &p : pieces)
+        if (p.src && p.bytes) SSG_CUDA_TRY(cudaMemcpyAsync(base + p.off, p.src, p.bytes, cudaMemcpyHostToDevice, C->stream));
+    auto at = [&](size_t i) { return static_cast<void *>(base + pieces[i].off); };
+    S->op.rowptr = static_cast<const int32_t *>(at(i_rowptr));
+    S->op.col = static_cast<const int32_t *>(at(i_col));
+    S->op.val = static_cast<const double *>(at(i_val));
+    S->op.tiles = static_cast<const int2 *>(at(i_tiles));
+    S->op.ntiles = static_cast<int32_t>(tiles.size());
+    S->op.iptr = static_cast<const int32_t *>(at(i_iptr));
+    S->op.icopy = static_cast<const int32_t *>(at(i_icopy));
+    S->op.ngamma = M.ngamma;
+    S->op.niface_blocks = niface_blocks;
+    S->op.mult = static_cast<const uint8_t *>(at(i_mult));
+    S->op.wtab = static_cast<const double *>(at(i_wtab));
+    S->d_l2g = static_cast<int32_t *>(at(i_l2g));
+    S->d_own = static_cast<int32_t *>(at(i_own));
+    S->d_bl = static_cast<double *>(at(i_bl));
+    S->d_xl = static_cast<double *>(at(i_xl));
+    S->d_r = static_cast<double *>(at(i_r));
+    S->d_p = static_cast<double *>(at(i_p));
+    S->d_q = static_cast<double *>(at(i_q));
+    S->d_partials = static_cast<double *>(at(i_part));
+    S->d_scal = static_cast<Scal *>(at(i_scal));
+    S->d_scal_op = static_cast<Scal *>(at(i_scal2));
+    S->d_xg = static_cast<double *>(at(i_xg));
+    S->d_bg = static_cast<double *>(at(i_bg));
+    SSG_CUDA_TRY(cudaMemsetAsync(S->d_scal, 0, sizeof(Scal), C->stream));
+    SSG_CUDA_TRY(cudaMemsetAsync(S->d_scal_op, 0, sizeof(Scal), C->stream));
+    SSG_CUDA_TRY(cudaEventCreate(&S->ev0));
+    SSG_CUDA_TRY(cudaEventCreate(&S->ev1));
+    // the host vectors above are freed when this function returns
+    SSG_CUDA_TRY(cudaStreamSynchronize(C->stream));
+    S->on_device = true;
+    return SSG_OK;
+}
+
+int check_dev(const ssg_system *S) {
+    if (!S) {
+        set_error("null system");
+        return SSG_E_INVALID;
+    }
+    if (!S->on_device) {
+        set_error("system has host maps only (built without a context)");
+        return SSG_E_INVALID;
+    }
+    return SSG_OK;
+}
+
+int grid_for(int64_t n, int num_sms) {
+    return std::max(1, std::min<int>(static_cast<int>((n + kBlock - 1) / kBlock), num_sms * 8));
+}
+
+// One right-hand side: b_glob/x_glob are device pointers (length n).
+int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, double rtol, int32_t max_iter,
+              ssg_stats *st) {
+    ssg_ctx *C = S->ctx;
+    cudaStream_t s = C->stream;
+    const int64_t N = S->maps.nloc;
+    int64_t launches = 0;
+    SSG_CUDA_TRY(cudaEventRecord(S->ev0, s));
+    k_scatter<<<grid_for(N, C->num_sms), kBlock, 0, s>>>(N, S->d_l2g, b_glob, S->d_bl);
+    ++launches;
+    if (guess) {
+        k_scatter<<<grid_for(N, C->num_sms), kBlock, 0, s>>>(N, S->d_l2g, x_glob, S->d_xl);
+        k_spmv_asm<kEpiStore><<<S->grid_spmv, kBlock, 0, s>>>(S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op,
+                                                               nullptr, 0, 0);
+        launches += 2;
+    } else {
+        SSG_CUDA_TRY(cudaMemsetAsync(S->d_xl, 0, sizeof(double) * N, s));
+    }
+    k_set_params<<<1, 32, 0, s>>>(S->d_scal, rtol, max_iter, guess);
+    ++launches;
+    SSG_CUDA_TRY(cudaGetLastError());
+    Scal h{};
+    if (C->driver == SSG_DRIVER_GRAPH) {
+        int rc = build_graph(S);
+        if (rc != SSG_OK) return rc;
+        SSG_CUDA_TRY(cudaGraphLaunch(S->exec, s));
+    } else {
+        int rc = launch_init(S, s, 0);
+        if (rc != SSG_OK) return rc;
+        ++launches;
+        for (;;) {
+            for (int i = 0; i < kHostChunk; ++i) {
+                rc = launch_body(S, s, 0);
+                if (rc != SSG_OK) return rc;
+            }
+            launches += 3 * kHostChunk;
+            SSG_CUDA_TRY(cudaMemcpyAsync(&h, S->d_scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
+            SSG_CUDA_TRY(cudaStreamSynchronize(s));
+            if (h.done) break;
+        }
+    }
+    k_gather<<<grid_for(S->maps.n, C->num_sms), kBlock, 0, s>>>(S->maps.n, S->d_own, S->d_xl, x_glob);
+    // true residual ||b - S x||_w in FP64
+    k_spmv_asm<kEpiStore><<<S->grid_spmv, kBlock, 0, s>>>(S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op,
+                                                           nullptr, 0, 0);
+    k_wdot<true><<<S->grid_vec, kBlock, 0, s>>>(N, S->d_bl, S->d_q, S->op.mult, S->op.wtab, S->d_partials,
+                                                S->d_scal_op, &S->d_scal->aux);
+    launches += 3;
+    SSG_CUDA_TRY(cudaGetLastError());
+    SSG_CUDA_TRY(cudaEventRecord(S->ev1, s));
+    SSG_CUDA_TRY(cudaMemcpyAsync(&h, S->d_scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
+    SSG_CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
+    if (C->driver == SSG_DRIVER_GRAPH) launches += 1 + 3 * static_cast<int64_t>(h.iter) +
+                                                   (h.status == SSG_E_BREAKDOWN ? 1 : 0);
+    if (st) {
+        st->status = h.status;
+        st->iters = h.iter;
+        st->outer = 1;
+        st->reserved = 0;
+        st->relres = h.relres;
+        st->true_relres = h.bnorm > 0.0 ? std::sqrt(h.aux) / h.bnorm : std::sqrt(h.aux);
+        st->solve_ms = ms;
+        st->kernel_launches = launches;
+    }
+    return h.status;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ssg_error_string(int status) {
+    switch (status) {
+        case SSG_OK: return "ok";
+        case SSG_E_INVALID: return "invalid argument";
+        case SSG_E_OOM: return "out of memory";
+        case SSG_E_CUDA: return "CUDA error";
+        case SSG_E_BREAKDOWN: return "CG breakdown: (Sp, p) <= 0 or not finite (matrix not SPD)";
+        case SSG_E_NOT_CONVERGED: return "not converged within max_iter";
+        case SSG_E_TIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char *ssg_last_error(void) { return g_last_error.c_str(); }
+
+int ssg_create(ssg_ctx **ctx, int device, void *stream) {
+    if (!ctx) {
+        set_error("ctx is null");
+        return SSG_E_INVALID;
+    }
+    *ctx = nullptr;
+    int ndev = 0;
+    SSG_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) {
+        set_error("device " + std::to_string(device) + " out of range");
+        return SSG_E_INVALID;
+    }
+    SSG_CUDA_TRY(cudaSetDevice(device));
+    ssg_ctx *c = new (std::nothrow) ssg_ctx();
+    if (!c) return SSG_E_OOM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete c;
+        set_error(std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+        return SSG_E_CUDA;
+    }
+    *ctx = c;
+    return SSG_OK;
+}
+
+int ssg_set_stream(ssg_ctx *ctx, void *stream) {
+    if (!ctx) return SSG_E_INVALID;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return SSG_OK;
+}
+
+int ssg_set_driver(ssg_ctx *ctx, int driver) {
+    if (!ctx || (driver != SSG_DRIVER_GRAPH && driver != SSG_DRIVER_HOST)) {
+        set_error("bad context or driver");
+        return SSG_E_INVALID;
+    }
+    ctx->driver = driver;
+    return SSG_OK;
+}
+
+int ssg_destroy(ssg_ctx *ctx) {
+    delete ctx;
+    return SSG_OK;
+}
+
+int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                  const int32_t *part, int32_t P, ssg_system **sys) {
+    if (!sys) {
+        set_error("sys is null");
+        return SSG_E_INVALID;
+    }
+    *sys = nullptr;
+    ssg_system *S = new (std::nothrow) ssg_system();
+    if (!S) return SSG_E_OOM;
+    std::string err;
+    int rc = build_host_maps(n, rowptr, colidx, val, part, P, S->maps, &err);
+    if (rc != SSG_OK) {
+        set_error(err);
+        delete S;
+        return rc;
+    }
+    S->ctx = ctx;
+    if (ctx) {
+        rc = upload(S);
+        if (rc != SSG_OK) {
+            ssg_system_destroy(S);
+            return rc;
+        }
+    }
+    *sys = S;
+    return SSG_OK;
+}
+
+int ssg_get_sizes(const ssg_system *S, ssg_sizes *o) {
+    if (!S || !o) {
+        set_error("null argument");
+        return SSG_E_INVALID;
+    }
+    o->n = S->maps.n;
+    o->P = S->maps.P;
+    o->nnz = S->maps.nnz;
+    o->nloc = S->maps.nloc;
+    o->ngamma = S->maps.ngamma;
+    o->max_mult = S->maps.max_mult;
+    o->ncopies = S->maps.ncopies;
+    return SSG_OK;
+}
+
+int ssg_copy_maps(const ssg_system *S, int32_t *off, int32_t *nint, int32_t *l2g, int32_t *mult, int32_t *lrowptr,
+                  int32_t *lcol, double *lval, int32_t *gamma, int32_t *iptr, int32_t *icopy, int32_t *own) {
+    if (!S) {
+        set_error("null system");
+        return SSG_E_INVALID;
+    }
+    const HostMaps &M = S->maps;
+    auto cp = [](void *dst, const void *src, size_t bytes) {
+        if (dst && bytes) memcpy(dst, src, bytes);
+    };
+    cp(off, M.off.data(), sizeof(int32_t) * (M.P + 1));
+    cp(nint, M.nint.data(), sizeof(int32_t) * M.P);
+    cp(l2g, M.l2g.data(), sizeof(int32_t) * M.nloc);
+    cp(mult, M.mult.data(), sizeof(int32_t) * M.n);
+    cp(lrowptr, M.lrowptr.data(), sizeof(int32_t) * (M.nloc + 1));
+    cp(lcol, M.lcol.data(), sizeof(int32_t) * M.nnz);
+    cp(lval, M.lval.data(), sizeof(double) * M.nnz);
+    cp(gamma, M.gamma.data(), sizeof(int32_t) * M.ngamma);
+    cp(iptr, M.iptr.data(), sizeof(int32_t) * (M.ngamma + 1));
+    cp(icopy, M.icopy.data(), sizeof(int32_t) * M.ncopies);
+    cp(own, M.own.data(), sizeof(int32_t) * M.n);
+    return SSG_OK;
+}
+
+int ssg_scatter(ssg_system *S, const double *x_glob, double *x_loc) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (!x_glob || !x_loc) {
+        set_error("null vector");
+        return SSG_E_INVALID;
+    }
+    k_scatter<<<grid_for(S->maps.nloc, S->ctx->num_sms), kBlock, 0, S->ctx->stream>>>(S->maps.nloc, S->d_l2g,
+                                                                                       x_glob, x_loc);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int ssg_gather(ssg_system *S, const double *x_loc, double *x_glob) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (!x_glob || !x_loc) {
+        set_error("null vector");
+        return SSG_E_INVALID;
+    }
+    k_gather<<<grid_for(S->maps.n, S->ctx->num_sms), kBlock, 0, S->ctx->stream>>>(S->maps.n, S->d_own, x_loc,
+                                                                                   x_glob);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int ssg_spmv_assembled(ssg_system *S, const double *x_loc, double *y_loc, double *xSx_dev) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (!x_loc || !y_loc || x_loc == y_loc) {
+        set_error("x_loc and y_loc must be distinct non-null device vectors");
+        return SSG_E_INVALID;
+    }
+    k_spmv_asm<kEpiStore><<<S->grid_spmv, kBlock, 0, S->ctx->stream>>>(S->op, x_loc, y_loc, S->d_partials,
+                                                                        S->d_scal_op, xSx_dev, 0, 0);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int ssg_wdot(ssg_system *S, const double *u, const double *v, double *result_dev) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (!u || !v || !result_dev) {
+        set_error("null argument");
+        return SSG_E_INVALID;
+    }
+    k_wdot<false><<<S->grid_vec, kBlock, 0, S->ctx->stream>>>(S->maps.nloc, u, v, S->op.mult, S->op.wtab,
+                                                               S->d_partials, S->d_scal_op, result_dev);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int ssg_solve(ssg_system *S, int32_t k, const double *b, double *x, int32_t x_is_guess, double rtol,
+              int32_t max_iter, int32_t mode, ssg_stats *stats) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (k <= 0 || !b || !x || !(rtol >= 0.0)) {
+        set_error("bad k, null b/x, or negative rtol");
+        return SSG_E_INVALID;
+    }
+    if (mode != SSG_FP64) {
+        set_error("mode not available in this build");
+        return SSG_E_INVALID;
+    }
+    if (max_iter <= 0) max_iter = S->maps.n;
+    SSG_CUDA_TRY(cudaSetDevice(S->ctx->device));
+    int first_bad = SSG_OK;
+    for (int32_t j = 0; j < k; ++j) {
+        const size_t o = static_cast<size_t>(j) * S->maps.n;
+        rc = solve_one(S, b + o, x + o, x_is_guess, rtol, max_iter, stats ? stats + j : nullptr);
+        if (rc == SSG_E_CUDA || rc == SSG_E_OOM || rc == SSG_E_INVALID) return rc;
+        if (rc != SSG_OK && first_bad == SSG_OK) first_bad = rc;
+    }
+    if (first_bad != SSG_OK) set_error(ssg_error_string(first_bad));
+    return first_bad;
+}
+
+int ssg_solve_host(ssg_system *S, int32_t k, const double *b_host, double *x_host, int32_t x_is_guess, double rtol,
+                   int32_t max_iter, int32_t mode, ssg_stats *stats) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (k <= 0 || !b_host || !x_host) {
+        set_error("bad k or null b/x");
+        return SSG_E_INVALID;
+    }
+    cudaStream_t s = S->ctx->stream;
+    const size_t nb = sizeof(double) * S->maps.n;
+    int first_bad = SSG_OK;
+    for (int32_t j = 0; j < k; ++j) {
+        const size_t o = static_cast<size_t>(j) * S->maps.n;
+        SSG_CUDA_TRY(cudaMemcpyAsync(S->d_bg, b_host + o, nb, cudaMemcpyHostToDevice, s));
+        if (x_is_guess) SSG_CUDA_TRY(cudaMemcpyAsync(S->d_xg, x_host + o, nb, cudaMemcpyHostToDevice, s));
+        rc = ssg_solve(S, 1, S->d_bg, S->d_xg, x_is_guess, rtol, max_iter, mode, stats ? stats + j : nullptr);
+        if (rc == SSG_E_CUDA || rc == SSG_E_OOM || rc == SSG_E_INVALID) return rc;
+        if (rc != SSG_OK && first_bad == SSG_OK) first_bad = rc;
+        SSG_CUDA_TRY(cudaMemcpyAsync(x_host + o, S->d_xg, nb, cudaMemcpyDeviceToHost, s));
+    }
+    SSG_CUDA_TRY(cudaStreamSynchronize(s));
+    return first_bad;
+}
+
+int ssg_system_destroy(ssg_system *S) {
+    if (!S) return SSG_OK;
+    if (S->ctx) cudaSetDevice(S->ctx->device);
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    if (S->ev0) cudaEventDestroy(S->ev0);
+    if (S->ev1) cudaEventDestroy(S->ev1);
+    if (S->arena) {
+        if (S->ctx && S->ctx->stream) cudaStreamSynchronize(S->ctx->stream);
+        cudaFree(S->arena);
+    }
+    delete S;
+    return SSG_OK;
+}
+
+}  // extern "C"

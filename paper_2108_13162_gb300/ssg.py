@@ -1,0 +1,376 @@
+"""ctypes binding of libssg.so (include/ssg.h), same names as the C ABI.
+
+Argument marshalling only: every step of the sub-structured CG runs in the
+library's CUDA kernels.  Device vectors are passed as ``torch.Tensor``
+(float64, CUDA, contiguous) through ``data_ptr()``; host arrays as numpy
+arrays.  The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_2108_13162_gb300.build``): there is no fallback, a missing
+library raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+SSG_OK = 0
+SSG_E_INVALID = 1
+SSG_E_OOM = 2
+SSG_E_CUDA = 3
+SSG_E_BREAKDOWN = 4
+SSG_E_NOT_CONVERGED = 5
+SSG_E_TIMEOUT = 6
+SSG_FP64 = 0
+SSG_MIXED = 1
+SSG_DRIVER_GRAPH = 0
+SSG_DRIVER_HOST = 1
+
+# every entry point declared in include/ssg.h
+EXPORTS = (
+    "ssg_create",
+    "ssg_set_stream",
+    "ssg_set_driver",
+    "ssg_destroy",
+    "ssg_partition",
+    "ssg_get_sizes",
+    "ssg_copy_maps",
+    "ssg_scatter",
+    "ssg_gather",
+    "ssg_spmv_assembled",
+    "ssg_wdot",
+    "ssg_solve",
+    "ssg_solve_host",
+    "ssg_system_destroy",
+    "ssg_error_string",
+    "ssg_last_error",
+)
+
+
+class ssg_sizes(C.Structure):
+    _fields_ = [
+        ("n", C.c_int32),
+        ("P", C.c_int32),
+        ("nnz", C.c_int64),
+        ("nloc", C.c_int64),
+        ("ngamma", C.c_int32),
+        ("max_mult", C.c_int32),
+        ("ncopies", C.c_int64),
+    ]
+
+
+class ssg_stats(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32),
+        ("iters", C.c_int32),
+        ("outer", C.c_int32),
+        ("reserved", C.c_int32),
+        ("relres", C.c_double),
+        ("true_relres", C.c_double),
+        ("solve_ms", C.c_double),
+        ("kernel_launches", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class SSGError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s failed: %s (%s)" % (where, _lib_or_none_str(status), last_error()))
+
+
+_lib = None
+
+
+def _lib_or_none_str(status):
+    try:
+        return lib().ssg_error_string(status).decode()
+    except Exception:  # noqa: BLE001
+        return "status %d" % status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libssg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libssg.so is not built (%s); run __graft_entry__.build()" % path)
+        L = C.CDLL(path)
+        vp = C.c_void_p
+        i32 = C.c_int32
+        L.ssg_create.argtypes = [C.POINTER(vp), C.c_int, vp]
+        L.ssg_set_stream.argtypes = [vp, vp]
+        L.ssg_set_driver.argtypes = [vp, C.c_int]
+        L.ssg_destroy.argtypes = [vp]
+        L.ssg_partition.argtypes = [vp, i32, vp, vp, vp, vp, i32, C.POINTER(vp)]
+        L.ssg_get_sizes.argtypes = [vp, C.POINTER(ssg_sizes)]
+        L.ssg_copy_maps.argtypes = [vp] * 12
+        L.ssg_scatter.argtypes = [vp, vp, vp]
+        L.ssg_gather.argtypes = [vp, vp, vp]
+        L.ssg_spmv_assembled.argtypes = [vp, vp, vp, vp]
+        L.ssg_wdot.argtypes = [vp, vp, vp, vp]
+        L.ssg_solve.argtypes = [vp, i32, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
+        L.ssg_solve_host.argtypes = [vp, i32, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
+        L.ssg_system_destroy.argtypes = [vp]
+        L.ssg_error_string.argtypes = [C.c_int]
+        L.ssg_error_string.restype = C.c_char_p
+        L.ssg_last_error.argtypes = []
+        L.ssg_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("ssg_error_string", "ssg_last_error"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().ssg_last_error().decode(errors="replace")
+
+
+def _check(rc, where, ok=(SSG_OK,)):
+    if rc not in ok:
+        raise SSGError(rc, where)
+    return rc
+
+
+def _ptr(t):
+    """Device (torch) or host (numpy) buffer -> address; None -> NULL."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return t.ctypes.data
+    assert t.is_contiguous(), "tensors passed to the library must be contiguous"
+    return t.data_ptr()
+
+
+def _dev_f64(t):
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+# ------------------------------------------------------------------ thin wrappers (same names)
+def ssg_create(device: int = 0, stream=None):
+    h = C.c_void_p()
+    _check(lib().ssg_create(C.byref(h), device, stream), "ssg_create")
+    return h
+
+
+def ssg_set_stream(ctx, stream):
+    return _check(lib().ssg_set_stream(ctx, stream), "ssg_set_stream")
+
+
+def ssg_set_driver(ctx, driver: int):
+    return _check(lib().ssg_set_driver(ctx, driver), "ssg_set_driver")
+
+
+def ssg_destroy(ctx):
+    return lib().ssg_destroy(ctx)
+
+
+def ssg_partition(ctx, n, rowptr, colidx, val, part, P):
+    rowptr = np.ascontiguousarray(rowptr, np.int32)
+    colidx = np.ascontiguousarray(colidx, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    part = np.ascontiguousarray(part, np.int32)
+    if rowptr.size != n + 1 or part.size != n or colidx.size != val.size or colidx.size < rowptr[-1]:
+        raise ValueError("CSR/partition arrays have inconsistent sizes")
+    h = C.c_void_p()
+    _check(
+        lib().ssg_partition(ctx, n, _ptr(rowptr), _ptr(colidx), _ptr(val), _ptr(part), P, C.byref(h)),
+        "ssg_partition",
+    )
+    return h
+
+
+def ssg_get_sizes(sys):
+    s = ssg_sizes()
+    _check(lib().ssg_get_sizes(sys, C.byref(s)), "ssg_get_sizes")
+    return s
+
+
+def ssg_copy_maps(sys):
+    s = ssg_get_sizes(sys)
+    out = {
+        "off": np.zeros(s.P + 1, np.int32),
+        "nint": np.zeros(s.P, np.int32),
+        "l2g": np.zeros(s.nloc, np.int32),
+        "mult": np.zeros(s.n, np.int32),
+        "lrowptr": np.zeros(s.nloc + 1, np.int32),
+        "lcol": np.zeros(s.nnz, np.int32),
+        "lval": np.zeros(s.nnz, np.float64),
+        "gamma": np.zeros(s.ngamma, np.int32),
+        "iptr": np.zeros(s.ngamma + 1, np.int32),
+        "icopy": np.zeros(s.ncopies, np.int32),
+        "own": np.zeros(s.n, np.int32),
+    }
+    keys = ("off", "nint", "l2g", "mult", "lrowptr", "lcol", "lval", "gamma", "iptr", "icopy", "own")
+    _check(lib().ssg_copy_maps(sys, *[_ptr(out[k]) for k in keys]), "ssg_copy_maps")
+    return out
+
+
+def ssg_scatter(sys, x_glob, x_loc):
+    return _check(lib().ssg_scatter(sys, _dev_f64(x_glob), _dev_f64(x_loc)), "ssg_scatter")
+
+
+def ssg_gather(sys, x_loc, x_glob):
+    return _check(lib().ssg_gather(sys, _dev_f64(x_loc), _dev_f64(x_glob)), "ssg_gather")
+
+
+def ssg_spmv_assembled(sys, x_loc, y_loc, xSx=None):
+    return _check(
+        lib().ssg_spmv_assembled(sys, _dev_f64(x_loc), _dev_f64(y_loc), None if xSx is None else _dev_f64(xSx)),
+        "ssg_spmv_assembled",
+    )
+
+
+def ssg_wdot(sys, u_loc, v_loc, out):
+    return _check(lib().ssg_wdot(sys, _dev_f64(u_loc), _dev_f64(v_loc), _dev_f64(out)), "ssg_wdot")
+
+
+def ssg_solve(sys, k, b, x, x_is_guess=False, rtol=1e-8, max_iter=0, mode=SSG_FP64):
+    """Device solve; returns (status, [stats per RHS])."""
+    st = (ssg_stats * k)()
+    rc = lib().ssg_solve(sys, k, _dev_f64(b), _dev_f64(x), int(bool(x_is_guess)), rtol, max_iter, mode, st)
+    _check(rc, "ssg_solve", ok=(SSG_OK, SSG_E_BREAKDOWN, SSG_E_NOT_CONVERGED))
+    return rc, [st[i].as_dict() for i in range(k)]
+
+
+def ssg_solve_host(sys, k, b_host, x_host, x_is_guess=False, rtol=1e-8, max_iter=0, mode=SSG_FP64):
+    """Host-buffer solve (copies inside the call); returns (status, stats)."""
+    assert b_host.dtype == np.float64 and x_host.dtype == np.float64
+    st = (ssg_stats * k)()
+    rc = lib().ssg_solve_host(sys, k, _ptr(b_host), _ptr(x_host), int(bool(x_is_guess)), rtol, max_iter, mode, st)
+    _check(rc, "ssg_solve_host", ok=(SSG_OK, SSG_E_BREAKDOWN, SSG_E_NOT_CONVERGED))
+    return rc, [st[i].as_dict() for i in range(k)]
+
+
+def ssg_system_destroy(sys):
+    return lib().ssg_system_destroy(sys)
+
+
+def ssg_error_string(status: int) -> str:
+    return lib().ssg_error_string(status).decode()
+
+
+def ssg_last_error() -> str:
+    return last_error()
+
+
+# ------------------------------------------------------------------ convenience object
+@dataclass
+class Sizes:
+    n: int
+    P: int
+    nnz: int
+    nloc: int
+    ngamma: int
+    max_mult: int
+    ncopies: int
+
+
+class Context:
+    """Owns an ssg_ctx on a CUDA device; work goes to the given torch stream
+    (default: the current stream at creation)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the sub-structured CG library needs a CUDA device")
+        torch.cuda.set_device(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self.device = device
+        self.h = ssg_create(device, C.c_void_p(stream.cuda_stream))
+
+    def set_driver(self, driver: int):
+        ssg_set_driver(self.h, driver)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ssg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+class System:
+    """A partitioned system (ssg_partition) with device-side operators."""
+
+    def __init__(self, ctx: Context | None, A, part, P):
+        self.ctx = ctx
+        self.h = ssg_partition(None if ctx is None else ctx.h, A.n, A.rowptr, A.colidx, A.val, part, P)
+        s = ssg_get_sizes(self.h)
+        self.sizes = Sizes(s.n, s.P, s.nnz, s.nloc, s.ngamma, s.max_mult, s.ncopies)
+
+    def maps(self):
+        return ssg_copy_maps(self.h)
+
+    def _empty_loc(self):
+        import torch
+
+        return torch.empty(self.sizes.nloc, dtype=torch.float64, device="cuda:%d" % self.ctx.device)
+
+    def scatter(self, x_glob, out=None):
+        out = self._empty_loc() if out is None else out
+        ssg_scatter(self.h, x_glob, out)
+        return out
+
+    def gather(self, x_loc, out=None):
+        import torch
+
+        out = torch.empty(self.sizes.n, dtype=torch.float64, device=x_loc.device) if out is None else out
+        ssg_gather(self.h, x_loc, out)
+        return out
+
+    def spmv(self, x_loc, out=None, xSx=None):
+        out = self._empty_loc() if out is None else out
+        ssg_spmv_assembled(self.h, x_loc, out, xSx)
+        return out
+
+    def wdot(self, u, v, out=None):
+        import torch
+
+        out = torch.empty(1, dtype=torch.float64, device=u.device) if out is None else out
+        ssg_wdot(self.h, u, v, out)
+        return out
+
+    def solve(self, b, x=None, rtol=1e-8, max_iter=0, mode=SSG_FP64):
+        """b: CUDA float64 (n,) or (k, n) tensor; returns (x, status, stats)."""
+        import torch
+
+        bb = b.reshape(-1, self.sizes.n).contiguous()
+        k = bb.shape[0]
+        guess = x is not None
+        xx = torch.zeros_like(bb) if x is None else x.reshape(-1, self.sizes.n).contiguous()
+        rc, st = ssg_solve(self.h, k, bb, xx, guess, rtol, max_iter, mode)
+        return xx.reshape(b.shape), rc, st
+
+    def solve_host(self, b_host, x_host, rtol=1e-8, max_iter=0, mode=SSG_FP64, x_is_guess=False):
+        k = b_host.size // self.sizes.n
+        return ssg_solve_host(self.h, k, b_host, x_host, x_is_guess, rtol, max_iter, mode)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ssg_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

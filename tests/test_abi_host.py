@@ -1,0 +1,135 @@
+"""CPU-side checks of the C ABI (no GPU): the library loads, exports every
+entry point include/ssg.h declares, and its host partitioner produces maps
+bit-identical to the oracle's (Section 2.4 sub-structures, Section 3.4.2
+interface lists).  Device entry points are not called here except on a
+host-only system, where they must refuse with SSG_E_INVALID."""
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import CSR, config_problem, poisson2d_5pt, random_spd
+from paper_2108_13162_gb300 import build as ssg_build
+from paper_2108_13162_gb300 import ssg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ssg_build.build()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "ssg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ssg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol():
+    names = _declared()
+    assert len(names) >= 14
+    assert set(names) == set(ssg.EXPORTS)
+    L = C.CDLL(ssg.library_path())
+    for n in names:
+        assert hasattr(L, n), "missing export %s" % n
+
+
+def _cases():
+    rng = np.random.default_rng(21)
+    out = []
+    p = config_problem(1)
+    out.append(("config1", p.A, p.part, p.P))
+    p = config_problem(2, scale=24)
+    out.append(("fv3d_24", p.A, p.part, p.P))
+    p = config_problem(3, scale=40)
+    out.append(("fe_40", p.A, p.part, p.P))
+    A = random_spd(300, 7.0, rng)
+    out.append(("rand300", A, rng.integers(0, 9, 300).astype(np.int32), 9))
+    A = poisson2d_5pt(9, 7)
+    out.append(("p2d_P1", A, np.zeros(A.n, np.int32), 1))
+    return out
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_host_maps_bit_exact_vs_oracle(case):
+    _, A, part, P = case
+    sys_ = ssg.ssg_partition(None, A.n, A.rowptr, A.colidx, A.val, part, P)
+    try:
+        got = ssg.ssg_copy_maps(sys_)
+        sz = ssg.ssg_get_sizes(sys_)
+    finally:
+        ssg.ssg_system_destroy(sys_)
+    ref = oracle.Partition(A, part, P).maps
+    assert (sz.n, sz.P, sz.nnz, sz.nloc, sz.ngamma, sz.ncopies) == (
+        ref.n, ref.P, ref.nnz, ref.nloc, ref.ngamma, ref.ncopies)
+    assert sz.max_mult == int(ref.mult.max())
+    for k in ("off", "nint", "l2g", "mult", "lrowptr", "lcol", "gamma", "iptr", "icopy", "own"):
+        assert np.array_equal(got[k], getattr(ref, k)), k
+    assert np.array_equal(got["lval"].view(np.int64), ref.lval.view(np.int64))
+
+
+def test_full_size_maps_bit_exact():
+    """The 128^3 / 4x4x4 workload: counts and maps identical to the oracle's."""
+    p = config_problem(2)
+    sys_ = ssg.ssg_partition(None, p.A.n, p.A.rowptr, p.A.colidx, p.A.val, p.part, p.P)
+    try:
+        got = ssg.ssg_copy_maps(sys_)
+    finally:
+        ssg.ssg_system_destroy(sys_)
+    ref = oracle.Partition(p.A, p.part, p.P).maps
+    assert ref.nloc == 2244608 and ref.ngamma == 144027 and ref.ncopies == 291483
+    for k in ("off", "nint", "l2g", "lrowptr", "lcol", "iptr", "icopy", "own"):
+        assert np.array_equal(got[k], getattr(ref, k)), k
+
+
+def test_invalid_inputs():
+    A = poisson2d_5pt(6, 6)
+    part = np.zeros(A.n, np.int32)
+    bad = part.copy()
+    bad[5] = 3
+    with pytest.raises(ssg.SSGError) as e:
+        ssg.ssg_partition(None, A.n, A.rowptr, A.colidx, A.val, bad, 2)
+    assert e.value.status == ssg.SSG_E_INVALID and "part id" in str(e.value)
+    v = A.val.copy()
+    v[1] = 7.0
+    with pytest.raises(ssg.SSGError) as e:
+        ssg.ssg_partition(None, A.n, A.rowptr, A.colidx, v, part, 1)
+    assert "symmetric" in str(e.value)
+    c = A.colidx.copy()
+    c[0], c[1] = c[1], c[0]
+    with pytest.raises(ssg.SSGError):
+        ssg.ssg_partition(None, A.n, A.rowptr, c, A.val, part, 1)
+    with pytest.raises(ssg.SSGError):
+        ssg.ssg_partition(None, A.n, A.rowptr, A.colidx, A.val, part, 0)
+    # the non-symmetric worked example of Section 2.2
+    ex = CSR(5, np.array([0, 2, 4, 6, 9, 11], np.int32), np.array([0, 1, 1, 2, 0, 2, 1, 3, 4, 2, 4], np.int32),
+             np.array([-5, 14, 8, 1, 2, 10, 4, 2, 9, 15, 7], np.float64))
+    with pytest.raises(ssg.SSGError):
+        ssg.ssg_partition(None, 5, ex.rowptr, ex.colidx, ex.val, np.zeros(5, np.int32), 1)
+
+
+def test_host_only_system_refuses_device_calls():
+    A = poisson2d_5pt(4, 4)
+    sys_ = ssg.ssg_partition(None, A.n, A.rowptr, A.colidx, A.val, np.zeros(A.n, np.int32), 1)
+    try:
+        L = ssg.lib()
+        assert L.ssg_spmv_assembled(sys_, None, None, None) == ssg.SSG_E_INVALID
+        assert L.ssg_solve(sys_, 1, None, None, 0, 1e-8, 10, 0, None) == ssg.SSG_E_INVALID
+        assert L.ssg_wdot(sys_, None, None, None) == ssg.SSG_E_INVALID
+        assert "host maps only" in ssg.last_error()
+    finally:
+        ssg.ssg_system_destroy(sys_)
+
+
+def test_error_strings():
+    for code in range(7):
+        assert ssg.ssg_error_string(code)
+    assert "breakdown" in ssg.ssg_error_string(ssg.SSG_E_BREAKDOWN).lower()

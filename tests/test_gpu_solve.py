@@ -1,0 +1,240 @@
+"""GPU sub-structured CG (Algorithm 3, M = I) against the FP64 oracle.
+
+Parity readings (the paper gives no tolerance):
+  (i)  at the same fixed iteration count (rtol = 0, max_iter = k) the GPU
+       iterate matches the oracle's to <= 1e-10 relative;
+  (ii) run to rtol, the iteration count matches the oracle's within one
+       iteration, the solution matches the oracle's to <= 1e-10 relative and
+       the manufactured solution is recovered within 2 kappa rtol;
+  edge cases: b = 0, A = I, exact initial guess, max_iter reached, an
+  indefinite matrix (breakdown), several right-hand sides, the host-loop
+  driver, host buffers.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import CSR, config_problem, laplace1d, poisson2d_5pt, random_spd
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    from paper_2108_13162_gb300 import build as ssg_build
+    from paper_2108_13162_gb300.ssg import Context
+
+    ssg_build.build()
+    c = Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def _t(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _sys(ctx, A, part, P):
+    from paper_2108_13162_gb300.ssg import System
+
+    return System(ctx, A, part, P)
+
+
+SOLVE_CASES = [
+    ("config1", lambda: config_problem(1), 1e-10),
+    ("fv3d_24", lambda: config_problem(2, scale=24), 1e-8),
+    ("fe2d_64", lambda: config_problem(3, scale=64), 1e-8),
+]
+
+
+@pytest.mark.parametrize("name,mk,rtol", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
+def test_fixed_iterations_match_oracle(ctx, name, mk, rtol):
+    from paper_2108_13162_gb300 import ssg
+
+    p = mk()
+    S = _sys(ctx, p.A, p.part, p.P)
+    ref = oracle.Partition(p.A, p.part, p.P)
+    b = p.b[:, 0]
+    for k in (1, 7, 40):
+        r = ref.cg(b, 0.0, k)
+        x, rc, st = S.solve(_t(b), rtol=0.0, max_iter=k)
+        assert rc == ssg.SSG_E_NOT_CONVERGED and st[0]["iters"] == k
+        assert _rel(x.cpu().numpy(), r.x) <= 1e-10
+        assert abs(st[0]["relres"] - r.relres) <= 1e-8 * r.relres
+
+
+@pytest.mark.parametrize("name,mk,rtol", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
+def test_solve_to_tolerance(ctx, name, mk, rtol):
+    from paper_2108_13162_gb300 import ssg
+
+    p = mk()
+    S = _sys(ctx, p.A, p.part, p.P)
+    ref = oracle.Partition(p.A, p.part, p.P)
+    b = p.b[:, 0]
+    r = ref.cg(b, rtol, 20 * p.A.n)
+    assert r.status == oracle.OK
+    x, rc, st = S.solve(_t(b), rtol=rtol)
+    assert rc == ssg.SSG_OK
+    assert abs(st[0]["iters"] - r.iters) <= 1
+    xg = x.cpu().numpy()
+    assert _rel(xg, r.x) <= 1e-10 if st[0]["iters"] == r.iters else _rel(xg, r.x) <= 10 * rtol
+    kap = oracle.cond_from_lanczos(r.alpha, r.beta)
+    assert _rel(xg, p.xstar[:, 0]) <= 2 * kap * rtol
+    tr = np.linalg.norm(b - p.A.to_scipy() @ xg) / np.linalg.norm(b)
+    assert abs(st[0]["true_relres"] - tr) <= 1e-6 * tr + 1e-15
+    assert st[0]["relres"] <= rtol
+    assert st[0]["kernel_launches"] >= 3 * st[0]["iters"]
+
+
+def test_deterministic_and_drivers_agree(ctx):
+    from paper_2108_13162_gb300 import ssg
+
+    p = config_problem(2, scale=20)
+    S = _sys(ctx, p.A, p.part, p.P)
+    b = _t(p.b[:, 0])
+    x1, _, s1 = S.solve(b, rtol=1e-8)
+    x2, _, s2 = S.solve(b, rtol=1e-8)
+    assert np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
+    ctx.set_driver(ssg.SSG_DRIVER_HOST)
+    try:
+        x3, rc3, s3 = S.solve(b, rtol=1e-8)
+    finally:
+        ctx.set_driver(ssg.SSG_DRIVER_GRAPH)
+    assert rc3 == ssg.SSG_OK and s3[0]["iters"] == s1[0]["iters"]
+    assert np.array_equal(x3.cpu().numpy(), x1.cpu().numpy())
+
+
+def test_host_buffers_match_device(ctx):
+    p = config_problem(1)
+    S = _sys(ctx, p.A, p.part, p.P)
+    b = p.b[:, 0].copy()
+    xd, _, sd = S.solve(_t(b), rtol=1e-10)
+    xh = np.zeros_like(b)
+    rc, sh = S.solve_host(b, xh, rtol=1e-10)
+    assert rc == 0 and sh[0]["iters"] == sd[0]["iters"]
+    assert np.array_equal(xh, xd.cpu().numpy())
+
+
+def test_multiple_rhs(ctx):
+    p = config_problem(2, scale=16)
+    rng = np.random.default_rng(8)
+    xs = rng.uniform(-1, 1, (3, p.A.n))
+    B = np.stack([p.A.to_scipy() @ xs[j] for j in range(3)])
+    S = _sys(ctx, p.A, p.part, p.P)
+    X, rc, st = S.solve(_t(B), rtol=1e-10)
+    assert rc == 0 and len(st) == 3
+    ref = oracle.Partition(p.A, p.part, p.P)
+    for j in range(3):
+        r = ref.cg(B[j], 1e-10, 10000)
+        assert abs(st[j]["iters"] - r.iters) <= 1
+        assert _rel(X[j].cpu().numpy(), xs[j]) <= 1e-6
+
+
+def test_zero_rhs_and_exact_guess(ctx):
+    p = config_problem(1)
+    S = _sys(ctx, p.A, p.part, p.P)
+    import torch
+
+    x, rc, st = S.solve(torch.zeros(p.A.n, dtype=torch.float64, device="cuda"), rtol=1e-10)
+    assert rc == 0 and st[0]["iters"] == 0 and float(x.abs().max()) == 0.0
+    # an exact guess: residual already zero up to rounding, so no iteration
+    b = _t(p.b[:, 0])
+    x0 = _t(p.xstar[:, 0])
+    x, rc, st = S.solve(b, x=x0.clone(), rtol=1e-10)
+    assert rc == 0 and st[0]["iters"] == 0
+    assert np.array_equal(x.cpu().numpy(), p.xstar[:, 0])
+
+
+def test_identity_one_iteration(ctx):
+    n = 1000
+    A = CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
+    part = (np.arange(n) % 7).astype(np.int32)
+    S = _sys(ctx, A, part, 7)
+    b = np.random.default_rng(1).uniform(-1, 1, n)
+    x, rc, st = S.solve(_t(b), rtol=1e-12)
+    assert rc == 0 and st[0]["iters"] == 1
+    assert _rel(x.cpu().numpy(), b) <= 1e-15
+
+
+def test_laplace1d_finite_termination(ctx):
+    n = 64
+    A = laplace1d(n)
+    S = _sys(ctx, A, (np.arange(n) * 4 // n).astype(np.int32), 4)
+    b = np.random.default_rng(2).uniform(-1, 1, n)
+    x, rc, st = S.solve(_t(b), rtol=1e-10)
+    assert rc == 0 and st[0]["iters"] <= n
+
+
+def test_max_iter_not_converged(ctx):
+    from paper_2108_13162_gb300 import ssg
+
+    p = config_problem(1)
+    S = _sys(ctx, p.A, p.part, p.P)
+    x, rc, st = S.solve(_t(p.b[:, 0]), rtol=1e-12, max_iter=5)
+    assert rc == ssg.SSG_E_NOT_CONVERGED and st[0]["iters"] == 5
+    r = oracle.Partition(p.A, p.part, p.P).cg(p.b[:, 0], 1e-12, 5)
+    assert _rel(x.cpu().numpy(), r.x) <= 1e-10
+
+
+def test_breakdown_indefinite(ctx):
+    from paper_2108_13162_gb300 import ssg
+
+    A = poisson2d_5pt(10, 10)
+    An = CSR(A.n, A.rowptr, A.colidx, -A.val)
+    S = _sys(ctx, An, (np.arange(A.n) % 3).astype(np.int32), 3)
+    b = np.ones(A.n)
+    x, rc, st = S.solve(_t(b), rtol=1e-10)
+    assert rc == ssg.SSG_E_BREAKDOWN and st[0]["status"] == ssg.SSG_E_BREAKDOWN
+    assert st[0]["iters"] == 0 and float(x.abs().max()) == 0.0
+
+
+def test_random_spd_uneven_partition(ctx):
+    rng = np.random.default_rng(4)
+    A = random_spd(20000, 8.0, rng, shift=0.05)
+    part = np.minimum((rng.random(A.n) ** 2 * 11).astype(np.int32), 10)
+    S = _sys(ctx, A, part, 11)
+    b = rng.uniform(-1, 1, A.n)
+    r = oracle.Partition(A, part, 11).cg(b, 1e-10, 10000)
+    x, rc, st = S.solve(_t(b), rtol=1e-10)
+    assert rc == 0 and abs(st[0]["iters"] - r.iters) <= 1
+    assert _rel(x.cpu().numpy(), r.x) <= 1e-9
+
+
+def test_full_size_solve_128cube(ctx):
+    """The benchmark workload: 128^3 FV, 64 subdomains, FP64 to 1e-8.
+
+    The oracle needs ~1000 iterations (a minute of CPU), so parity is checked
+    at a fixed 30 iterations (<= 1e-10 relative) and the full solve against
+    the manufactured solution and the FP64 true residual."""
+    p = config_problem(2)
+    S = _sys(ctx, p.A, p.part, p.P)
+    b = p.b[:, 0]
+    r = oracle.Partition(p.A, p.part, p.P).cg(b, 0.0, 30)
+    x, rc, st = S.solve(_t(b), rtol=0.0, max_iter=30)
+    assert _rel(x.cpu().numpy(), r.x) <= 1e-10
+    x, rc, st = S.solve(_t(b), rtol=1e-8)
+    assert rc == 0
+    assert st[0]["true_relres"] <= 2e-8
+    xg = x.cpu().numpy()
+    assert _rel(xg, p.xstar[:, 0]) <= 1e-4
+    # against the stored full oracle solve (tests/golden/make_oracle_golden.py)
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_fv3d_128_4x4x4.json")))
+    assert abs(st[0]["iters"] - g["iters"]) <= 1
+    idx = np.array(g["sample_idx"])
+    xs = np.array(g["sample_x"])
+    rel = _rel(xg[idx], xs)
+    print("full-size sampled rel diff vs oracle: %.3e (iters %d vs %d)" % (rel, st[0]["iters"], g["iters"]))
+    assert rel <= (1e-10 if st[0]["iters"] == g["iters"] else 1e-7)
