@@ -231,11 +231,15 @@ def profiled_traffic():
 
 
 def golden_iters():
+    """Iterations the oracle needs for this solve at rtol 1e-8 (stored)."""
     try:
         with open(GOLDEN) as f:
-            return int(json.load(f)["iters"])
+            for rec in json.load(f)["solves"]:
+                if rec["rtol"] == RTOL:
+                    return int(rec["iters"])
     except (OSError, KeyError, ValueError):
-        return None
+        pass
+    return None
 
 
 # ----------------------------------------------------------------------------- CPU oracle

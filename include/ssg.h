@@ -90,6 +90,8 @@ int ssg_create(ssg_ctx **ctx, int device, void *stream);
 int ssg_set_stream(ssg_ctx *ctx, void *stream);
 /* Pick how ssg_solve drives the iteration (SSG_DRIVER_*); default GRAPH. */
 int ssg_set_driver(ssg_ctx *ctx, int driver);
+/* Free a context.  Refused with SSG_E_INVALID (nothing freed) while systems
+ * created on it are still alive: destroy those first. */
 int ssg_destroy(ssg_ctx *ctx);
 
 /*

@@ -31,6 +31,7 @@ struct ssg_ctx {
     cudaStream_t stream = nullptr;
     int driver = SSG_DRIVER_GRAPH;
     int num_sms = 0;
+    int live_systems = 0;  // systems created on this context and not yet destroyed
 };
 
 struct ssg_system {
@@ -408,6 +409,11 @@ int ssg_set_driver(ssg_ctx *ctx, int driver) {
 }
 
 int ssg_destroy(ssg_ctx *ctx) {
+    if (!ctx) return SSG_OK;
+    if (ctx->live_systems > 0) {
+        set_error("context still has " + std::to_string(ctx->live_systems) + " live system(s); destroy them first");
+        return SSG_E_INVALID;
+    }
     delete ctx;
     return SSG_OK;
 }
@@ -430,6 +436,7 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
     }
     S->ctx = ctx;
     if (ctx) {
+        ctx->live_systems++;
         rc = upload(S);
         if (rc != SSG_OK) {
             ssg_system_destroy(S);
@@ -591,6 +598,7 @@ int ssg_system_destroy(ssg_system *S) {
         if (S->ctx && S->ctx->stream) cudaStreamSynchronize(S->ctx->stream);
         cudaFree(S->arena);
     }
+    if (S->ctx) S->ctx->live_systems--;
     delete S;
     return SSG_OK;
 }

@@ -303,9 +303,11 @@ class Context:
         ssg_set_driver(self.h, driver)
 
     def close(self):
+        """Free the context once no System created on it is alive (the C
+        library refuses earlier; a System keeps its Context referenced)."""
         if getattr(self, "h", None):
-            ssg_destroy(self.h)
-            self.h = None
+            if ssg_destroy(self.h) == SSG_OK:
+                self.h = None
 
     def __del__(self):
         self.close()
