@@ -188,6 +188,31 @@ int ssg_solve_host(ssg_system *sys, int32_t k, const double *b_host, double *x_h
 
 int ssg_system_destroy(ssg_system *sys);
 
+/*
+ * Interface-weighted dot, (u, v)_w = sum_k w_k u_k v_k with w_k = 1/mult_loc[k],
+ * for callers that cannot let a library allocate device memory (this call
+ * has no counterpart in the paper).  Such callers: code running while a CUDA
+ * graph is being captured, where cudaMalloc is not allowed; programs whose
+ * own allocator owns the device memory under a fixed budget; loops that must
+ * not take the implicit device synchronisation cudaMalloc/cudaFree can cause.
+ *
+ * No system is needed.  All arguments are device pointers owned by the
+ * caller: u_loc, v_loc (nloc doubles), mult_loc (nloc bytes, the multiplicity
+ * 1..255 of each local entry's node, i.e. mult[l2g[k]] from ssg_copy_maps),
+ * result_dev (one double, written on the device).  Work goes to `stream`
+ * (cudaStream_t or NULL) on the calling thread's current device.
+ * Scratch: a 64 KB static __device__ array that every GPU loading this
+ * library keeps until the process exits; nothing is allocated or freed.
+ * Limit: nloc <= 33,554,432 (8192 partial sums of 4096 entries); larger
+ * nloc, a negative nloc or a null pointer returns SSG_E_INVALID.
+ * The first call on a device looks up the scratch address on that device;
+ * make that first call before any stream capture.  Every call shares the one
+ * scratch array: calls that can overlap on the GPU (different streams, or
+ * threads) race and must be serialised by the caller.
+ */
+int ssg_wdot_noalloc(const double *u_loc, const double *v_loc, const uint8_t *mult_loc, int64_t nloc,
+                     double *result_dev, void *stream);
+
 const char *ssg_error_string(int status);
 const char *ssg_last_error(void);
 

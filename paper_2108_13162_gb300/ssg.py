@@ -48,6 +48,7 @@ EXPORTS = (
     "ssg_system_destroy",
     "ssg_error_string",
     "ssg_last_error",
+    "ssg_wdot_noalloc",
 )
 
 
@@ -123,6 +124,7 @@ def lib():
         L.ssg_solve.argtypes = [vp, i32, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
         L.ssg_solve_host.argtypes = [vp, i32, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
         L.ssg_system_destroy.argtypes = [vp]
+        L.ssg_wdot_noalloc.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
         L.ssg_error_string.argtypes = [C.c_int]
         L.ssg_error_string.restype = C.c_char_p
         L.ssg_last_error.argtypes = []
@@ -257,6 +259,19 @@ def ssg_solve_host(sys, k, b_host, x_host, x_is_guess=False, rtol=1e-8, max_iter
     rc = lib().ssg_solve_host(sys, k, _ptr(b_host), _ptr(x_host), int(bool(x_is_guess)), rtol, max_iter, mode, st)
     _check(rc, "ssg_solve_host", ok=(SSG_OK, SSG_E_BREAKDOWN, SSG_E_NOT_CONVERGED))
     return rc, [st[i].as_dict() for i in range(k)]
+
+
+def ssg_wdot_noalloc(u_loc, v_loc, mult_loc, out, stream=None):
+    """Weighted dot with no device allocation in the library (see ssg.h)."""
+    import torch
+
+    if not (isinstance(mult_loc, torch.Tensor) and mult_loc.is_cuda and mult_loc.dtype == torch.uint8):
+        raise TypeError("mult_loc must be a uint8 CUDA tensor")
+    return _check(
+        lib().ssg_wdot_noalloc(_dev_f64(u_loc), _dev_f64(v_loc), mult_loc.data_ptr(), u_loc.numel(),
+                               _dev_f64(out), stream),
+        "ssg_wdot_noalloc",
+    )
 
 
 def ssg_system_destroy(sys):
