@@ -40,7 +40,8 @@ UNIT = "s"
 RTOL = 1e-8
 WORKLOAD = "fv3d_7pt_128^3_kappa=exp(N(0,1))_4x4x4_subdomains"
 FALLBACK_HBM_GBS = 6800.0
-PROFILE_RECORD = os.path.join(ROOT, "profiles", "spmv_asm_fp64_fv3d128.md")
+PROFILE_RECORDS = {"fp64": os.path.join(ROOT, "profiles", "spmv_asm_fp64_fv3d128.md"),
+                   "fp32": os.path.join(ROOT, "profiles", "spmv_asm_fp32_fv3d128.md")}
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2108_13162_gb300", "csrc", "kernels.cuh")
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_fv3d_128_4x4x4.json")
 
@@ -54,6 +55,12 @@ def parse_args(argv=None):
     ap.add_argument("--spmv-reps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU time budget of the oracle sample")
+    ap.add_argument("--mode", choices=("mixed", "fp64"), default="mixed",
+                    help="mixed: FP32 inner CG inside FP64 iterative refinement; fp64: Algorithm 3 in FP64. "
+                         "Both stop on an FP64 relative residual of 1e-8; the other mode is timed too and reported")
+    ap.add_argument("--driver", choices=("graph", "host"), default="graph",
+                    help="graph: one CUDA graph per solve (timed default); host: same kernels launched from a "
+                         "host loop (for profilers that cannot see kernels inside conditional graphs)")
     return ap.parse_args(argv)
 
 
@@ -191,12 +198,33 @@ def make_workload():
     return config_problem(2)
 
 
-def spmv_algorithmic_bytes(sizes) -> int:
-    """Bytes the fused sub-structured SpMV must move once per launch (FP64
-    values, int32 indices, each x and y entry once): matrix 12*nnz, row
-    pointers 4*(nloc+1), x 8*nloc, y 8*nloc, interface lists
-    4*ncopies + 4*(ngamma+1)."""
-    return (12 * sizes.nnz + 4 * (sizes.nloc + 1) + 16 * sizes.nloc + 4 * sizes.ncopies + 4 * (sizes.ngamma + 1))
+def spmv_algorithmic_bytes(sizes, vb: int = 8) -> int:
+    """Bytes the fused sub-structured SpMV must move once per launch with
+    vb-byte values and vectors (8: FP64, 4: FP32), int32 indices, each x and
+    y entry once: matrix (vb+4)*nnz, row pointers 4*(nloc+1), x and y
+    vb*nloc each, interface lists 4*ncopies + 4*(ngamma+1)."""
+    return ((vb + 4) * sizes.nnz + 4 * (sizes.nloc + 1) + 2 * vb * sizes.nloc + 4 * sizes.ncopies
+            + 4 * (sizes.ngamma + 1))
+
+
+def time_spmv(S, prec, stream, reps):
+    """Average duration of one SpMV launch (CUDA events on its stream)."""
+    import torch
+
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    xl = torch.rand(S.sizes.nloc, dtype=torch.float64, device="cuda").to(dt)
+    y = torch.empty_like(xl)
+    for _ in range(3):
+        S.spmv_prec(xl, y, prec)
+    torch.cuda.synchronize()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        S.spmv_prec(xl, y, prec)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    return k0.elapsed_time(k1) / 1e3 / reps
 
 
 def measured_peaks():
@@ -209,11 +237,11 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic():
+def profiled_traffic(prec="fp64"):
     """Per-launch DRAM bytes from the committed ncu summary, only if the
     kernel source is unchanged since the counters were taken."""
     try:
-        text = open(PROFILE_RECORD).read()
+        text = open(PROFILE_RECORDS[prec]).read()
         src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
     except OSError:
         return None
@@ -315,75 +343,92 @@ def run_ours(args, dist):
     stream = torch.cuda.current_stream(dev)
     prob = make_workload()
     ctx = Context(dev, stream)
+    if args.driver == "host":
+        ctx.set_driver(ssg.SSG_DRIVER_HOST)
     S = System(ctx, prob.A, prob.part, prob.P)
     b = torch.from_numpy(prob.b[:, 0].copy()).to("cuda:%d" % dev)
     x = torch.zeros_like(b)
+    modes = {"fp64": ssg.SSG_FP64, "mixed": ssg.SSG_MIXED}
 
-    def solve():
+    def solve(mode):
         x.zero_()
-        rc, st = ssg.ssg_solve(S.h, 1, b, x, False, RTOL, 0, ssg.SSG_FP64)
+        rc, st = ssg.ssg_solve(S.h, 1, b, x, False, RTOL, 0, modes[mode])
         if rc != ssg.SSG_OK:
             raise RuntimeError("solve did not converge: %r" % st)
         return st[0]
 
+    def timed(mode, steps, clocks=None):
+        """K solves bracketed by a barrier and a device sync on both sides,
+        CUDA events on the solve stream; returns (ms per step, stats list)."""
+        if clocks:
+            clocks.start()
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sts = []
+        e0.record(stream)
+        for _ in range(steps):
+            sts.append(solve(mode))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        ck = clocks.stop() if clocks else None
+        return dist.max(e0.elapsed_time(e1) / steps), sts, ck
+
+    other = "fp64" if args.mode == "mixed" else "mixed"
     for _ in range(max(args.warmup, 0)):
-        solve()
-    clocks = ClockSampler(_device_index(dev))
-    clocks.start()
-    dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    launches = 0
-    iters = []
-    e0.record(stream)
-    for _ in range(args.steps):
-        st = solve()
-        launches += st["kernel_launches"]
-        iters.append(st["iters"])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    dist.barrier()
-    elapsed_ms = e0.elapsed_time(e1)
-    ck = clocks.stop()
-    ms_step = dist.max(elapsed_ms / args.steps)
+        solve(args.mode)
+    ms_step, sts, ck = timed(args.mode, args.steps, ClockSampler(_device_index(dev)))
+    launches = sum(s["kernel_launches"] for s in sts)
+    iters = [s["iters"] for s in sts]
+    st = sts[-1]
     true_res = st["true_relres"]
+    # the other mode on the same system, same protocol (reported, not the value)
+    for _ in range(max(args.warmup, 0)):
+        solve(other)
+    ms_other, sts_other, _ = timed(other, args.steps)
 
     # end to end through the host-buffer C ABI call (pinned host memory)
     bh = torch.from_numpy(prob.b[:, 0].copy()).pin_memory().numpy()
     xh = torch.zeros(prob.A.n, dtype=torch.float64).pin_memory().numpy()
-    ssg.ssg_solve_host(S.h, 1, bh, xh, False, RTOL, 0, ssg.SSG_FP64)
+    ssg.ssg_solve_host(S.h, 1, bh, xh, False, RTOL, 0, modes[args.mode])
     dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        rc, _ = ssg.ssg_solve_host(S.h, 1, bh, xh, False, RTOL, 0, ssg.SSG_FP64)
+        rc, _ = ssg.ssg_solve_host(S.h, 1, bh, xh, False, RTOL, 0, modes[args.mode])
     e2e_s = dist.max((time.perf_counter() - t0) / args.steps)
 
-    # roofline of the dominant kernel: fused SpMV + interface assembly, CUDA
-    # events on the launching stream, inputs (175 MB of matrix) larger than L2
-    xl = S.scatter(b)
-    y = torch.empty_like(xl)
-    for _ in range(3):
-        S.spmv(xl, y)
-    torch.cuda.synchronize()
-    k0 = torch.cuda.Event(enable_timing=True)
-    k1 = torch.cuda.Event(enable_timing=True)
-    k0.record(stream)
-    for _ in range(args.spmv_reps):
-        S.spmv(xl, y)
-    k1.record(stream)
-    torch.cuda.synchronize()
-    spmv_s = k0.elapsed_time(k1) / 1e3 / args.spmv_reps
-    nbytes = spmv_algorithmic_bytes(S.sizes)
+    # roofline of the dominant kernel: the fused SpMV + interface assembly,
+    # CUDA events on the launching stream, matrix larger than L2
     peak, peak_src = measured_peaks()
-    achieved = nbytes / spmv_s / 1e9
+    roof = {}
+    for prec in ("fp64", "fp32"):
+        spmv_s = time_spmv(S, prec, stream, args.spmv_reps)
+        nbytes = spmv_algorithmic_bytes(S.sizes, 4 if prec == "fp32" else 8)
+        achieved = nbytes / spmv_s / 1e9
+        roof[prec] = {
+            "kernel": "k_spmv_asm<%s> (fused local CSR SpMV + interface assembly + (p,Sp)_w partials)"
+                      % ("float" if prec == "fp32" else "double"),
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": peak,
+            "peak_source": peak_src,
+            "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": profiled_traffic(prec),
+            "algorithmic_bytes": nbytes,
+            "launch_us": spmv_s * 1e6,
+        }
+    dominant = "fp32" if args.mode == "mixed" else "fp64"
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        v, sample, m, dt = oracle_sample(prob, int(statistics.median(iters)), args.cpu_seconds)
+        v, sample, m, dt = oracle_sample(prob, golden_iters() or int(statistics.median(iters)), args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
     value = ms_step / 1e3
+    fp64_iters = iters if args.mode == "fp64" else [s["iters"] for s in sts_other]
     line = {
         "metric": METRIC,
         "value": value,
@@ -395,7 +440,7 @@ def run_ours(args, dist):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f32+f64" if args.mode == "mixed" else "f64",
         "data": "synthetic",
         "config": {
             "workload": WORKLOAD,
@@ -405,25 +450,21 @@ def run_ours(args, dist):
             "interface_nodes": S.sizes.ngamma,
             "subdomains": prob.P,
             "rtol": RTOL,
-            "mode": "fp64",
+            "mode": args.mode,
             "iters": int(statistics.median(iters)),
+            "outer": st["outer"],
             "true_relres": true_res,
             "us_per_iter": ms_step * 1e3 / statistics.median(iters),
+            other + "_s": ms_other / 1e3,
+            other + "_iters": sts_other[-1]["iters"],
+            other + "_true_relres": sts_other[-1]["true_relres"],
+            "fp64_us_per_iter": (ms_step if args.mode == "fp64" else ms_other) * 1e3 / statistics.median(fp64_iters),
             "l2": "inputs larger than L2 (175 MB matrix + 5 x 18 MB vectors > 129 MB)",
             "parallelism": "replicas" if dist.world > 1 else "single",
+            "driver": args.driver,
         },
-        "roofline": {
-            "kernel": "k_spmv_asm (fused local CSR SpMV + interface assembly + (p,Sp)_w partials)",
-            "bound": "hbm",
-            "achieved": achieved,
-            "peak": peak,
-            "peak_source": peak_src,
-            "unit": "GB/s",
-            "frac": achieved / peak,
-            "traffic": profiled_traffic(),
-            "algorithmic_bytes": nbytes,
-            "launch_us": spmv_s * 1e6,
-        },
+        "roofline": roof[dominant],
+        "roofline_other": roof["fp64" if dominant == "fp32" else "fp32"],
         "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * prob.A.n, "d2h_bytes_per_step": 8 * prob.A.n},
         "gpu_launches": int(dist.sum(launches)),
         "clocks": ck,

@@ -90,6 +90,14 @@ int ssg_create(ssg_ctx **ctx, int device, void *stream);
 int ssg_set_stream(ssg_ctx *ctx, void *stream);
 /* Pick how ssg_solve drives the iteration (SSG_DRIVER_*); default GRAPH. */
 int ssg_set_driver(ssg_ctx *ctx, int driver);
+/*
+ * Parameters of SSG_MIXED solves on this context (not a method of the paper;
+ * its experiments are FP64 only): the inner FP32 CG stops when its residual
+ * has dropped by inner_rtol (or by the factor the outer test still needs, if
+ * that is larger), and at most max_outer refinements run.  Defaults 1e-4, 30.
+ * SSG_E_INVALID unless 0 < inner_rtol < 1 and max_outer >= 1.
+ */
+int ssg_set_mixed(ssg_ctx *ctx, double inner_rtol, int32_t max_outer);
 /* Free a context.  Refused with SSG_E_INVALID (nothing freed) while systems
  * created on it are still alive: destroy those first. */
 int ssg_destroy(ssg_ctx *ctx);
@@ -159,6 +167,16 @@ int ssg_gather(ssg_system *sys, const double *x_loc, double *x_glob);
 int ssg_spmv_assembled(ssg_system *sys, const double *x_loc, double *y_loc, double *xSx_dev);
 
 /*
+ * The same sub-structured SpMV with the values rounded to FP32 and FP32
+ * vectors and arithmetic (the inner operator of SSG_MIXED solves; the paper
+ * itself computes in FP64).  Rows summed in CSR order with FP32 FMAs,
+ * interface copies summed in ascending subdomain order in FP32; xSx_dev (may
+ * be NULL) receives (x, S x)_w summed in FP64.  Device pointers, nloc floats,
+ * must not overlap.
+ */
+int ssg_spmv_assembled_f32(ssg_system *sys, const float *x_loc, float *y_loc, double *xSx_dev);
+
+/*
  * Interface-weighted dot of Section 3.4.2: result = sum_k w_k u_k v_k over the
  * nloc local entries with w_k = 1/m of the entry's node (equals the global dot
  * for consistent vectors).  Device pointers; *result_dev is written on the
@@ -174,6 +192,12 @@ int ssg_wdot(ssg_system *sys, const double *u_loc, const double *v_loc, double *
  * paper is silent: stop after the first iteration with
  * sqrt((r,r)_w) <= rtol * sqrt((b,b)_w) (recursive residual) or after
  * max_iter iterations (max_iter <= 0 means n).  mode = SSG_FP64 or SSG_MIXED.
+ * SSG_MIXED: iterative refinement in FP64 (r = b - S x with the FP64
+ * sub-structured SpMV, x += d, the stopping test on that true residual)
+ * around an inner Algorithm 3 in FP32 (values, vectors and SpMV in FP32, dot
+ * products summed in FP64) on S d = r; max_iter then caps the inner
+ * iterations summed over refinements (ssg_set_mixed sets the inner tolerance
+ * and the refinement cap).
  * stats (host, may be NULL) receives k entries.  Blocks until done.
  * Returns SSG_OK when every right-hand side converged, else the first
  * non-OK per-RHS status (x still holds the last iterates).

@@ -110,6 +110,11 @@ def _bind(L):
         L.or_sub_cg.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int32, C.POINTER(C.c_int32),
                                 C.POINTER(C.c_double), dp, dp, dp]
         L.or_sub_cg.restype = C.c_int
+        L.or_sub_spmv32.argtypes = [C.c_void_p, np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS"),
+                                    np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")]
+        L.or_sub_cg_mixed.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int32, C.c_double, C.c_int32,
+                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+        L.or_sub_cg_mixed.restype = C.c_int
         L.or_cholesky_solve.argtypes = [C.c_int32, _f64p, _f64p, _f64p]
         L.or_cholesky_solve.restype = C.c_int
     return L
@@ -248,6 +253,40 @@ class Partition:
         st = self._L.or_sub_cg(self.h, b, x, rtol, max_iter, C.byref(it), C.byref(rr), pa, pb, pr)
         k = it.value
         return CGResult(x, st, k, rr.value, ha[:k].copy(), hb[:k].copy(), hr[:k].copy())
+
+
+@dataclass
+class MixedResult:
+    x: np.ndarray
+    status: int
+    iters: int
+    outer: int
+    relres: float
+
+
+def _mixed(self, b, rtol, max_iter, inner_rtol=1e-4, max_outer=30, x0=None) -> MixedResult:
+    """FP32 inner CG inside FP64 iterative refinement (ssg_oracle.c: or_sub_cg_mixed)."""
+    b = _c(b, np.float64).ravel()
+    x = np.zeros(self.maps.n) if x0 is None else _c(x0, np.float64).ravel().copy()
+    it = C.c_int32()
+    ou = C.c_int32()
+    rr = C.c_double()
+    st = self._L.or_sub_cg_mixed(self.h, b, x, rtol, max_iter, inner_rtol, max_outer, C.byref(it), C.byref(ou),
+                                 C.byref(rr))
+    return MixedResult(x, st, it.value, ou.value, rr.value)
+
+
+Partition.cg_mixed = _mixed
+
+
+def _spmv32(self, xl):
+    """FP32 sub-structured SpMV (values rounded to FP32, FP32 arithmetic)."""
+    out = np.empty(self.maps.nloc, np.float32)
+    self._L.or_sub_spmv32(self.h, np.ascontiguousarray(xl, np.float32), out)
+    return out
+
+
+Partition.spmv32 = _spmv32
 
 
 def cholesky_solve(Adense, b):

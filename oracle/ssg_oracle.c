@@ -500,3 +500,122 @@ int or_cholesky_solve(int32_t n, const double *A, const double *b, double *x) {
     free(L); free(y);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Mixed precision: FP32 inner CG inside FP64 iterative refinement.    */
+/* ------------------------------------------------------------------ */
+/*
+ * Not a method of the paper (its experiments are FP64 only); the reading
+ * this oracle fixes for the library's SSG_MIXED mode:
+ *   outer (FP64): r = b - S x with the sub-structured SpMV of Section 3.4.1,
+ *     stop when sqrt((r,r)_w) <= rtol * sqrt((b,b)_w), after max_outer
+ *     refinements, or when the inner iterations reach max_iter;
+ *   inner (FP32): Algorithm 3 (M = I) on S32 d = r32 with S32 = (float)S,
+ *     r32 = (float)r, d = 0, every product, sum and update in float (the
+ *     local row products and the interface sums included); the dot
+ *     products multiply in float and accumulate in double; alpha and beta
+ *     are the double ratios rounded to float; stop when
+ *     sqrt(rho_k) <= tau * sqrt(rho_0), tau = max(inner_rtol,
+ *     rtol * ||b|| / ||r||) (the last refinement is not over-solved);
+ *   update: x += (double) d.
+ */
+static void sub_spmv32(const or_part *h, const float *val32, const float *xl, float *yl) {
+    for (int32_t s = 0; s < h->P; ++s) {
+        const int32_t o = h->off[s];
+        for (int32_t li = 0; li < h->off[s + 1] - o; ++li) {
+            float acc = 0.0f;
+            for (int32_t k = h->lrowptr[o + li]; k < h->lrowptr[o + li + 1]; ++k) acc += val32[k] * xl[o + h->lcol[k]];
+            yl[o + li] = acc;
+        }
+    }
+    for (int32_t g = 0; g < h->ngamma; ++g) {
+        float S = 0.0f;
+        for (int32_t c = h->iptr[g]; c < h->iptr[g + 1]; ++c) S += yl[h->icopy[c]];
+        for (int32_t c = h->iptr[g]; c < h->iptr[g + 1]; ++c) yl[h->icopy[c]] = S;
+    }
+}
+
+/* sub_spmv32 with the FP32 value copy made here (for tests) */
+void or_sub_spmv32(const or_part *h, const float *xl, float *yl) {
+    float *val32 = (float *)malloc(sizeof(float) * (size_t)(h->nnz > 0 ? h->nnz : 1));
+    if (!val32) return;
+    for (int64_t k = 0; k < h->nnz; ++k) val32[k] = (float)h->lval[k];
+    sub_spmv32(h, val32, xl, yl);
+    free(val32);
+}
+
+static double wdot32(const or_part *h, const float *u, const float *v) {
+    double s = 0.0;
+    for (int64_t k = 0; k < h->nloc; ++k) s += (double)((float)h->w[k] * u[k] * v[k]);
+    return s;
+}
+
+int or_sub_cg_mixed(const or_part *h, const double *b, double *x, double rtol, int32_t max_iter, double inner_rtol,
+                    int32_t max_outer, int32_t *iters_out, int32_t *outer_out, double *relres_out) {
+    size_t N = (size_t)(h->nloc > 0 ? h->nloc : 1);
+    const int64_t L = h->nloc;
+    double *bl = (double *)malloc(sizeof(double) * N);
+    double *xl = (double *)malloc(sizeof(double) * N);
+    double *r = (double *)malloc(sizeof(double) * N);
+    double *q = (double *)malloc(sizeof(double) * N);
+    float *val32 = (float *)malloc(sizeof(float) * (size_t)(h->nnz > 0 ? h->nnz : 1));
+    float *r32 = (float *)malloc(sizeof(float) * N);
+    float *p32 = (float *)malloc(sizeof(float) * N);
+    float *q32 = (float *)malloc(sizeof(float) * N);
+    float *d32 = (float *)malloc(sizeof(float) * N);
+    if (!bl || !xl || !r || !q || !val32 || !r32 || !p32 || !q32 || !d32) {
+        free(bl); free(xl); free(r); free(q); free(val32); free(r32); free(p32); free(q32); free(d32);
+        return OR_OOM;
+    }
+    for (int64_t k = 0; k < h->nnz; ++k) val32[k] = (float)h->lval[k];
+    or_scatter(h, b, bl);
+    or_scatter(h, x, xl);
+    or_sub_spmv(h, xl, q);
+    for (int64_t k = 0; k < L; ++k) r[k] = bl[k] - q[k];
+    double rho = or_wdot(h, r, r);
+    const double bnorm = sqrt(or_wdot(h, bl, bl));
+    int32_t outer = 0, total = 0;
+    int status = OR_NOT_CONVERGED;
+    if (sqrt(rho) <= rtol * bnorm) status = OR_OK;
+    while (status == OR_NOT_CONVERGED && outer < max_outer && total < max_iter) {
+        double tau = rtol * bnorm / sqrt(rho);
+        if (tau < inner_rtol) tau = inner_rtol;
+        for (int64_t k = 0; k < L; ++k) {
+            r32[k] = (float)r[k];
+            p32[k] = r32[k];
+            d32[k] = 0.0f;
+        }
+        double rho32 = wdot32(h, r32, r32);
+        const double rho0 = rho32;
+        int broke = 0;
+        while (sqrt(rho32) > tau * sqrt(rho0) && total < max_iter) {
+            sub_spmv32(h, val32, p32, q32);
+            const double pq = wdot32(h, p32, q32);
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                broke = 1;
+                break;
+            }
+            const float alpha = (float)(rho32 / pq);
+            for (int64_t k = 0; k < L; ++k) d32[k] = d32[k] + alpha * p32[k];
+            for (int64_t k = 0; k < L; ++k) r32[k] = r32[k] - alpha * q32[k];
+            const double rho_new = wdot32(h, r32, r32);
+            const float beta = (float)(rho_new / rho32);
+            for (int64_t k = 0; k < L; ++k) p32[k] = r32[k] + beta * p32[k];
+            rho32 = rho_new;
+            ++total;
+        }
+        for (int64_t k = 0; k < L; ++k) xl[k] = xl[k] + (double)d32[k];
+        or_sub_spmv(h, xl, q);
+        for (int64_t k = 0; k < L; ++k) r[k] = bl[k] - q[k];
+        rho = or_wdot(h, r, r);
+        ++outer;
+        if (sqrt(rho) <= rtol * bnorm) status = OR_OK;
+        else if (broke) status = OR_BREAKDOWN;
+    }
+    or_gather(h, xl, x);
+    *iters_out = total;
+    *outer_out = outer;
+    *relres_out = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;
+    free(bl); free(xl); free(r); free(q); free(val32); free(r32); free(p32); free(q32); free(d32);
+    return status;
+}

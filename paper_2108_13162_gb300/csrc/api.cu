@@ -32,6 +32,8 @@ struct ssg_ctx {
     int driver = SSG_DRIVER_GRAPH;
     int num_sms = 0;
     int live_systems = 0;  // systems created on this context and not yet destroyed
+    double inner_rtol = 1e-4;  // SSG_MIXED: inner FP32 CG tolerance
+    int32_t max_outer = 30;    // SSG_MIXED: refinement steps cap
 };
 
 struct ssg_system {
@@ -46,6 +48,8 @@ struct ssg_system {
     int32_t *d_own = nullptr;
     // solver state
     double *d_bl = nullptr, *d_xl = nullptr, *d_r = nullptr, *d_p = nullptr, *d_q = nullptr;
+    float *d_r32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr, *d_d32 = nullptr;  // SSG_MIXED inner vectors
+    Scal *d_scal_in = nullptr;  // SSG_MIXED inner CG state
     double *d_partials = nullptr;
     int32_t n_partials = 0;
     Scal *d_scal = nullptr;     // CG state
@@ -57,6 +61,9 @@ struct ssg_system {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle cond = 0;
+    cudaGraph_t graph_m = nullptr;  // SSG_MIXED: nested refinement / inner loops
+    cudaGraphExec_t exec_m = nullptr;
+    cudaGraphConditionalHandle cond_out = 0, cond_in = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -73,10 +80,36 @@ namespace {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Greedy interior tiles: consecutive interior rows of one subdomain, at most
-// kTileRows rows and kTileNnz nonzeros; a longer row gets a tile of its own.
-std::vector<int2> make_tiles(const HostMaps &M) {
-    std::vector<int2> t;
+// SpMV work list (see WorkItem in kernels.cuh).  Interior items: greedy runs
+// of consecutive interior rows of one subdomain, at most kTileRows rows and
+// kTileNnz nonzeros; a longer row is an item of its own.  Interface items:
+// greedy runs of consecutive interface nodes with at most kTileRows nodes,
+// kTileRows copies and kTileNnz copy-row nonzeros.  Interface items are
+// spread evenly among the interior ones.
+struct WorkPlan {
+    std::vector<int32_t> irp, icol;
+    std::vector<double> ival;
+    std::vector<WorkItem> items;
+    std::vector<int2> block_range;
+};
+
+WorkPlan make_plan(const HostMaps &M, int grid_cap) {
+    WorkPlan W;
+    // interface copy rows in (node, copy) order, columns as concatenated index
+    std::vector<int32_t> sub_of(static_cast<size_t>(M.nloc));
+    for (int32_t s = 0; s < M.P; ++s)
+        for (int64_t r = M.off[s]; r < M.off[s + 1]; ++r) sub_of[r] = s;
+    W.irp.assign(static_cast<size_t>(M.ncopies) + 1, 0);
+    for (int64_t c = 0; c < M.ncopies; ++c) {
+        const int32_t row = M.icopy[c];
+        const int32_t o = M.off[sub_of[row]];
+        for (int32_t k = M.lrowptr[row]; k < M.lrowptr[row + 1]; ++k) {
+            W.icol.push_back(o + M.lcol[k]);
+            W.ival.push_back(M.lval[k]);
+        }
+        W.irp[c + 1] = static_cast<int32_t>(W.icol.size());
+    }
+    std::vector<WorkItem> rows, iface;
     for (int32_t s = 0; s < M.P; ++s) {
         int32_t r = M.off[s];
         const int32_t rend = M.off[s] + M.nint[s];
@@ -84,20 +117,67 @@ std::vector<int2> make_tiles(const HostMaps &M) {
             int32_t r1 = r;
             const int32_t e0 = M.lrowptr[r];
             while (r1 < rend && r1 - r < kTileRows && M.lrowptr[r1 + 1] - e0 <= kTileNnz) ++r1;
-            if (r1 == r) r1 = r + 1;  // single long row
-            t.push_back(make_int2(r, r1));
-            r = r1;
+            if (r1 == r) {
+                rows.push_back({kItemLongRow, r, r + 1, e0, M.lrowptr[r + 1], 0, 0, 0});
+                r = r + 1;
+            } else {
+                rows.push_back({kItemRows, r, r1, e0, M.lrowptr[r1], 0, 0, 0});
+                r = r1;
+            }
         }
     }
-    return t;
+    int32_t g = 0;
+    while (g < M.ngamma) {
+        int32_t g1 = g;
+        const int32_t c0 = M.iptr[g];
+        const int32_t e0 = W.irp[c0];
+        while (g1 < M.ngamma && g1 - g < kTileRows && M.iptr[g1 + 1] - c0 <= kTileRows &&
+               W.irp[M.iptr[g1 + 1]] - e0 <= kTileNnz)
+            ++g1;
+        if (g1 == g) {
+            iface.push_back({kItemLongIface, g, g + 1, e0, W.irp[M.iptr[g + 1]], c0, M.iptr[g + 1], 0});
+            g = g + 1;
+        } else {
+            iface.push_back({kItemIface, g, g1, e0, W.irp[M.iptr[g1]], c0, M.iptr[g1], 0});
+            g = g1;
+        }
+    }
+    // interleave: interface item j goes after interior item floor((j+1) * nrows / (niface+1))
+    const size_t nr = rows.size(), ni = iface.size();
+    size_t j = 0;
+    for (size_t i = 0; i <= nr; ++i) {
+        while (j < ni && (j + 1) * nr <= i * (ni + 1)) W.items.push_back(iface[j++]);
+        if (i < nr) W.items.push_back(rows[i]);
+    }
+    while (j < ni) W.items.push_back(iface[j++]);
+    // contiguous slices of about equal cost (nonzeros + 4 per row or copy)
+    const int n = static_cast<int>(W.items.size());
+    const int G = std::max(1, std::min(n, grid_cap));
+    std::vector<double> prefix(static_cast<size_t>(n) + 1, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const WorkItem &w = W.items[i];
+        const double rowsn = (w.kind == kItemIface || w.kind == kItemLongIface) ? (w.c1 - w.c0) : (w.b - w.a);
+        prefix[i + 1] = prefix[i] + (w.e1 - w.e0) + 4.0 * rowsn;
+    }
+    W.block_range.resize(G);
+    int lo = 0;
+    for (int b = 0; b < G; ++b) {
+        const double target = prefix[n] * (b + 1) / G;
+        int hi = lo;
+        while (hi < n && (prefix[hi + 1] <= target || hi == lo)) ++hi;
+        if (b == G - 1) hi = n;
+        W.block_range[b] = make_int2(lo, hi);
+        lo = hi;
+    }
+    return W;
 }
 
 int launch_body(ssg_system *S, cudaStream_t st, int use_cond) {
     const int64_t N = S->maps.nloc;
-    k_spmv_asm<kEpiAlpha><<<S->grid_spmv, kBlock, 0, st>>>(S->op, S->d_p, S->d_q, S->d_partials, S->d_scal,
-                                                           nullptr, S->cond, use_cond);
-    k_update_r<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_r, S->d_q, S->op.mult, S->op.wtab, S->d_partials,
-                                               S->d_scal);
+    k_spmv_asm<kEpiAlpha, double><<<S->grid_spmv, kBlock, spmv_smem<double>(), st>>>(
+        S->op, S->d_p, S->d_q, S->d_partials, S->d_scal, nullptr, S->cond, use_cond);
+    k_update_r<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_r, S->d_q, S->op.mult, S->op.wtab, S->op.gflag,
+                                               S->d_partials, S->d_scal);
     k_update_xp<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_xl, S->d_p, S->d_r, S->d_partials, S->d_scal, S->cond,
                                                 use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
@@ -165,11 +245,130 @@ int build_graph(ssg_system *S) {
     return SSG_OK;
 }
 
+
+int launch_mixed_init(ssg_system *S, cudaStream_t st, int use_cond) {
+    k_cg_init<<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_bl, S->d_q, S->d_r, nullptr, S->op.mult, S->op.wtab,
+                                              S->d_partials, S->d_scal, S->cond_out, use_cond);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int launch_inner_init(ssg_system *S, cudaStream_t st, int use_cond) {
+    k_inner_init<<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_r, S->d_r32, S->d_p32, S->d_d32, S->op.mult,
+                                                 S->op.wtab, S->d_partials, S->d_scal_in, S->d_scal, S->cond_in,
+                                                 use_cond);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond) {
+    const int64_t N = S->maps.nloc;
+    k_spmv_asm<kEpiAlpha, float><<<S->grid_spmv, kBlock, spmv_smem<float>(), st>>>(
+        S->op, S->d_p32, S->d_q32, S->d_partials, S->d_scal_in, nullptr, S->cond_in, use_cond);
+    k_update_r32<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_r32, S->d_q32, S->op.mult, S->op.wtab, S->op.gflag,
+                                                 S->d_partials, S->d_scal_in, S->d_scal);
+    k_update_dp32<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_d32, S->d_p32, S->d_r32, S->d_partials, S->d_scal_in,
+                                                  S->cond_in, use_cond);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int launch_outer_tail(ssg_system *S, cudaStream_t st, int use_cond) {
+    const int64_t N = S->maps.nloc;
+    k_ir_correct<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_xl, S->d_d32);
+    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kBlock, spmv_smem<double>(), st>>>(
+        S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
+    k_ir_residual<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_bl, S->d_q, S->d_r, S->op.mult, S->op.wtab, S->d_partials,
+                                                  S->d_scal, S->d_scal_in, S->cond_out, use_cond);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+// Capture `fn` into `g` after `deps`; returns the nodes `g` holds afterwards
+// that have no dependents (the capture's sink).
+template <typename F>
+cudaError_t capture_into(cudaStream_t cap, cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, F fn, int *rc) {
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cap, g, deps, nullptr, ndeps, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    *rc = fn(cap);
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &out);
+    return e2;
+}
+
+cudaError_t last_node(cudaGraph_t g, cudaGraphNode_t *out) {
+    size_t nn = 0;
+    cudaError_t e = cudaGraphGetNodes(g, nullptr, &nn);
+    if (e != cudaSuccess) return e;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    e = cudaGraphGetNodes(g, nodes.data(), &nn);
+    if (e != cudaSuccess) return e;
+    for (cudaGraphNode_t n : nodes) {
+        size_t nd = 0;
+        e = cudaGraphNodeGetDependentNodes(n, nullptr, nullptr, &nd);
+        if (e != cudaSuccess) return e;
+        if (nd == 0) {
+            *out = n;
+            return cudaSuccess;
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t add_while(cudaGraph_t g, const cudaGraphNode_t *dep, cudaGraphConditionalHandle h, cudaGraphNode_t *node,
+                      cudaGraph_t *body) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaError_t e = cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &cp);
+    if (e == cudaSuccess) *body = cp.conditional.phGraph_out[0];
+    return e;
+}
+
+// SSG_MIXED graph: init -> WHILE(outer) { inner_init -> WHILE(inner) { FP32
+// SpMV, r update, d/p update } -> x += d -> FP64 SpMV -> residual + test }.
+int build_graph_mixed(ssg_system *S) {
+    if (S->exec_m) return SSG_OK;
+    SSG_CUDA_TRY(cudaGraphCreate(&S->graph_m, 0));
+    SSG_CUDA_TRY(cudaGraphConditionalHandleCreate(&S->cond_out, S->graph_m, 0u, cudaGraphCondAssignDefault));
+    cudaStream_t cap;
+    SSG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int rc = SSG_OK;
+    cudaError_t e = capture_into(cap, S->graph_m, nullptr, 0, [&](cudaStream_t c) { return launch_mixed_init(S, c, 1); }, &rc);
+    cudaGraphNode_t n_init = nullptr, n_outer = nullptr, n_iinit = nullptr, n_inner = nullptr;
+    cudaGraph_t body_out = nullptr, body_in = nullptr;
+    if (e == cudaSuccess && rc == SSG_OK) e = last_node(S->graph_m, &n_init);
+    if (e == cudaSuccess && rc == SSG_OK) e = add_while(S->graph_m, &n_init, S->cond_out, &n_outer, &body_out);
+    if (e == cudaSuccess && rc == SSG_OK)
+        e = capture_into(cap, body_out, nullptr, 0, [&](cudaStream_t c) { return launch_inner_init(S, c, 1); }, &rc);
+    if (e == cudaSuccess && rc == SSG_OK) e = last_node(body_out, &n_iinit);
+    if (e == cudaSuccess && rc == SSG_OK)
+        e = cudaGraphConditionalHandleCreate(&S->cond_in, body_out, 0u, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess && rc == SSG_OK) e = add_while(body_out, &n_iinit, S->cond_in, &n_inner, &body_in);
+    if (e == cudaSuccess && rc == SSG_OK)
+        e = capture_into(cap, body_in, nullptr, 0, [&](cudaStream_t c) { return launch_inner_body(S, c, 1); }, &rc);
+    if (e == cudaSuccess && rc == SSG_OK)
+        e = capture_into(cap, body_out, &n_inner, 1, [&](cudaStream_t c) { return launch_outer_tail(S, c, 1); }, &rc);
+    if (e == cudaSuccess && rc == SSG_OK) e = cudaGraphInstantiate(&S->exec_m, S->graph_m, 0);
+    cudaStreamDestroy(cap);
+    if (rc != SSG_OK) return rc;
+    if (e != cudaSuccess) {
+        set_error(std::string("building the mixed-precision graph: ") + cudaGetErrorString(e));
+        if (S->graph_m) cudaGraphDestroy(S->graph_m);
+        S->graph_m = nullptr;
+        S->exec_m = nullptr;
+        return SSG_E_CUDA;
+    }
+    return SSG_OK;
+}
+
 int upload(ssg_system *S) {
     const HostMaps &M = S->maps;
     ssg_ctx *C = S->ctx;
     SSG_CUDA_TRY(cudaSetDevice(C->device));
-    std::vector<int2> tiles = make_tiles(M);
+    WorkPlan plan = make_plan(M, C->num_sms * kSpmvBlocksPerSM);
     const int64_t N = M.nloc;
     // concatenated column ids
     std::vector<int32_t> gcol(static_cast<size_t>(M.nnz));
@@ -178,13 +377,24 @@ int upload(ssg_system *S) {
             for (int32_t k = M.lrowptr[r]; k < M.lrowptr[r + 1]; ++k) gcol[k] = M.off[s] + M.lcol[k];
     std::vector<uint8_t> mloc(static_cast<size_t>(N));
     for (int64_t k = 0; k < N; ++k) mloc[k] = static_cast<uint8_t>(M.mult[M.l2g[k]]);
+    // group flags: 1 when any of the 64 entries of a group is an interface copy
+    std::vector<uint8_t> gflag(static_cast<size_t>((N + 63) / 64), 0);
+    for (int64_t k = 0; k < N; ++k)
+        if (mloc[k] > 1) gflag[k >> 6] = 1;
     std::vector<double> wtab(256, 0.0);
     for (int m = 1; m < 256; ++m) wtab[m] = 1.0 / static_cast<double>(m);
 
-    const int niface_blocks = (M.ngamma + kBlock - 1) / kBlock;
-    S->grid_spmv = niface_blocks + static_cast<int>(tiles.size());
-    S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N + kBlock - 1) / kBlock), C->num_sms * 8));
+    S->grid_spmv = static_cast<int>(plan.block_range.size());
+    S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N / 2 + kBlock - 1) / kBlock), C->num_sms * kVecBlocksPerSM));
     S->n_partials = 2 * std::max(S->grid_spmv, S->grid_vec);
+    SSG_CUDA_TRY(cudaFuncSetAttribute(k_spmv_asm<kEpiStore, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(spmv_smem<double>())));
+    SSG_CUDA_TRY(cudaFuncSetAttribute(k_spmv_asm<kEpiAlpha, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(spmv_smem<double>())));
+    SSG_CUDA_TRY(cudaFuncSetAttribute(k_spmv_asm<kEpiStore, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(spmv_smem<float>())));
+    SSG_CUDA_TRY(cudaFuncSetAttribute(k_spmv_asm<kEpiAlpha, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(spmv_smem<float>())));
 
     struct Piece {
         const void *src;
@@ -193,21 +403,38 @@ int upload(ssg_system *S) {
     };
     std::vector<Piece> pieces;
     size_t total = 0;
+    // every piece starts 256-byte aligned and keeps >= 64 bytes of slack after
+    // its end (the SpMV stages tiles with 16-byte copies that may overrun the
+    // last nonzero by up to 12 bytes)
     auto add = [&](const void *src, size_t bytes) {
         pieces.push_back({src, bytes, total});
-        total = align_up(total + std::max<size_t>(bytes, 1), 256);
+        total = align_up(total + bytes + 64, 256);
         return pieces.size() - 1;
     };
     size_t i_rowptr = add(M.lrowptr.data(), sizeof(int32_t) * (N + 1));
     size_t i_col = add(gcol.data(), sizeof(int32_t) * M.nnz);
     size_t i_val = add(M.lval.data(), sizeof(double) * M.nnz);
-    size_t i_tiles = add(tiles.data(), sizeof(int2) * tiles.size());
+    size_t i_irp = add(plan.irp.data(), sizeof(int32_t) * plan.irp.size());
+    size_t i_icol = add(plan.icol.data(), sizeof(int32_t) * plan.icol.size());
+    size_t i_ival = add(plan.ival.data(), sizeof(double) * plan.ival.size());
+    size_t i_items = add(plan.items.data(), sizeof(WorkItem) * plan.items.size());
+    size_t i_brange = add(plan.block_range.data(), sizeof(int2) * plan.block_range.size());
     size_t i_iptr = add(M.iptr.data(), sizeof(int32_t) * (M.ngamma + 1));
     size_t i_icopy = add(M.icopy.data(), sizeof(int32_t) * M.ncopies);
     size_t i_mult = add(mloc.data(), N);
     size_t i_wtab = add(wtab.data(), sizeof(double) * 256);
+    size_t i_gflag = add(gflag.data(), gflag.size());
     size_t i_l2g = add(M.l2g.data(), sizeof(int32_t) * N);
     size_t i_own = add(M.own.data(), sizeof(int32_t) * M.n);
+    std::vector<float> val32(M.lval.begin(), M.lval.end());
+    std::vector<float> ival32(plan.ival.begin(), plan.ival.end());
+    size_t i_val32 = add(val32.data(), sizeof(float) * val32.size());
+    size_t i_ival32 = add(ival32.data(), sizeof(float) * ival32.size());
+    size_t i_r32 = add(nullptr, sizeof(float) * N);
+    size_t i_p32 = add(nullptr, sizeof(float) * N);
+    size_t i_q32 = add(nullptr, sizeof(float) * N);
+    size_t i_d32 = add(nullptr, sizeof(float) * N);
+    size_t i_scal_in = add(nullptr, sizeof(Scal));
     size_t i_bl = add(nullptr, sizeof(double) * N);
     size_t i_xl = add(nullptr, sizeof(double) * N);
     size_t i_r = add(nullptr, sizeof(double) * N);
@@ -226,20 +453,30 @@ int upload(ssg_system *S) {
     }
     S->arena_bytes = total;
     char *base = static_cast<char *>(S->arena);
+    SSG_CUDA_TRY(cudaMemsetAsync(S->arena, 0, total, C->stream));  // slack bytes read by the tile copies
     for (const Piece &p : pieces)
         if (p.src && p.bytes) SSG_CUDA_TRY(cudaMemcpyAsync(base + p.off, p.src, p.bytes, cudaMemcpyHostToDevice, C->stream));
     auto at = [&](size_t i) { return static_cast<void *>(base + pieces[i].off); };
     S->op.rowptr = static_cast<const int32_t *>(at(i_rowptr));
     S->op.col = static_cast<const int32_t *>(at(i_col));
     S->op.val = static_cast<const double *>(at(i_val));
-    S->op.tiles = static_cast<const int2 *>(at(i_tiles));
-    S->op.ntiles = static_cast<int32_t>(tiles.size());
+    S->op.val32 = static_cast<const float *>(at(i_val32));
+    S->op.ival32 = static_cast<const float *>(at(i_ival32));
+    S->d_r32 = static_cast<float *>(at(i_r32));
+    S->d_p32 = static_cast<float *>(at(i_p32));
+    S->d_q32 = static_cast<float *>(at(i_q32));
+    S->d_d32 = static_cast<float *>(at(i_d32));
+    S->d_scal_in = static_cast<Scal *>(at(i_scal_in));
+    S->op.irp = static_cast<const int32_t *>(at(i_irp));
+    S->op.icol = static_cast<const int32_t *>(at(i_icol));
+    S->op.ival = static_cast<const double *>(at(i_ival));
+    S->op.items = static_cast<const WorkItem *>(at(i_items));
+    S->op.block_range = static_cast<const int2 *>(at(i_brange));
     S->op.iptr = static_cast<const int32_t *>(at(i_iptr));
     S->op.icopy = static_cast<const int32_t *>(at(i_icopy));
-    S->op.ngamma = M.ngamma;
-    S->op.niface_blocks = niface_blocks;
     S->op.mult = static_cast<const uint8_t *>(at(i_mult));
     S->op.wtab = static_cast<const double *>(at(i_wtab));
+    S->op.gflag = static_cast<const uint8_t *>(at(i_gflag));
     S->d_l2g = static_cast<int32_t *>(at(i_l2g));
     S->d_own = static_cast<int32_t *>(at(i_own));
     S->d_bl = static_cast<double *>(at(i_bl));
@@ -279,8 +516,64 @@ int grid_for(int64_t n, int num_sms) {
 }
 
 // One right-hand side: b_glob/x_glob are device pointers (length n).
+int read_scal(ssg_system *S, const Scal *src, Scal *dst) {
+    SSG_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(Scal), cudaMemcpyDeviceToHost, S->ctx->stream));
+    SSG_CUDA_TRY(cudaStreamSynchronize(S->ctx->stream));
+    return SSG_OK;
+}
+
+// Host-loop drivers (SSG_DRIVER_HOST): the same kernels, launched directly,
+// the done flags read back every kHostChunk iterations.
+int run_host_fp64(ssg_system *S, int64_t *launches) {
+    cudaStream_t s = S->ctx->stream;
+    int rc = launch_init(S, s, 0);
+    if (rc != SSG_OK) return rc;
+    *launches += 1;
+    Scal h{};
+    for (;;) {
+        rc = read_scal(S, S->d_scal, &h);
+        if (rc != SSG_OK) return rc;
+        if (h.done) return SSG_OK;
+        for (int i = 0; i < kHostChunk; ++i) {
+            rc = launch_body(S, s, 0);
+            if (rc != SSG_OK) return rc;
+        }
+        *launches += 3 * kHostChunk;
+    }
+}
+
+int run_host_mixed(ssg_system *S, int64_t *launches) {
+    cudaStream_t s = S->ctx->stream;
+    int rc = launch_mixed_init(S, s, 0);
+    if (rc != SSG_OK) return rc;
+    *launches += 1;
+    Scal ho{}, hi{};
+    for (;;) {
+        rc = read_scal(S, S->d_scal, &ho);
+        if (rc != SSG_OK) return rc;
+        if (ho.done) return SSG_OK;
+        rc = launch_inner_init(S, s, 0);
+        if (rc != SSG_OK) return rc;
+        *launches += 1;
+        for (;;) {
+            rc = read_scal(S, S->d_scal_in, &hi);
+            if (rc != SSG_OK) return rc;
+            if (hi.done) break;
+            for (int i = 0; i < kHostChunk; ++i) {
+                rc = launch_inner_body(S, s, 0);
+                if (rc != SSG_OK) return rc;
+            }
+            *launches += 3 * kHostChunk;
+        }
+        rc = launch_outer_tail(S, s, 0);
+        if (rc != SSG_OK) return rc;
+        *launches += 3;
+    }
+}
+
+// One right-hand side: b_glob/x_glob are device pointers (length n).
 int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, double rtol, int32_t max_iter,
-              ssg_stats *st) {
+              int mode, ssg_stats *st) {
     ssg_ctx *C = S->ctx;
     cudaStream_t s = C->stream;
     const int64_t N = S->maps.nloc;
@@ -290,54 +583,52 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     ++launches;
     if (guess) {
         k_scatter<<<grid_for(N, C->num_sms), kBlock, 0, s>>>(N, S->d_l2g, x_glob, S->d_xl);
-        k_spmv_asm<kEpiStore><<<S->grid_spmv, kBlock, 0, s>>>(S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op,
-                                                               nullptr, 0, 0);
+        k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kBlock, spmv_smem<double>(), s>>>(
+            S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
         launches += 2;
     } else {
         SSG_CUDA_TRY(cudaMemsetAsync(S->d_xl, 0, sizeof(double) * N, s));
     }
     k_set_params<<<1, 32, 0, s>>>(S->d_scal, rtol, max_iter, guess);
     ++launches;
-    SSG_CUDA_TRY(cudaGetLastError());
-    Scal h{};
-    if (C->driver == SSG_DRIVER_GRAPH) {
-        int rc = build_graph(S);
-        if (rc != SSG_OK) return rc;
-        SSG_CUDA_TRY(cudaGraphLaunch(S->exec, s));
-    } else {
-        int rc = launch_init(S, s, 0);
-        if (rc != SSG_OK) return rc;
+    if (mode == SSG_MIXED) {
+        k_set_mixed<<<1, 32, 0, s>>>(S->d_scal, C->inner_rtol, C->max_outer);
         ++launches;
-        for (;;) {
-            for (int i = 0; i < kHostChunk; ++i) {
-                rc = launch_body(S, s, 0);
-                if (rc != SSG_OK) return rc;
-            }
-            launches += 3 * kHostChunk;
-            SSG_CUDA_TRY(cudaMemcpyAsync(&h, S->d_scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
-            SSG_CUDA_TRY(cudaStreamSynchronize(s));
-            if (h.done) break;
-        }
+    }
+    SSG_CUDA_TRY(cudaGetLastError());
+    int rc = SSG_OK;
+    if (C->driver == SSG_DRIVER_GRAPH) {
+        rc = mode == SSG_MIXED ? build_graph_mixed(S) : build_graph(S);
+        if (rc != SSG_OK) return rc;
+        SSG_CUDA_TRY(cudaGraphLaunch(mode == SSG_MIXED ? S->exec_m : S->exec, s));
+    } else {
+        rc = mode == SSG_MIXED ? run_host_mixed(S, &launches) : run_host_fp64(S, &launches);
+        if (rc != SSG_OK) return rc;
     }
     k_gather<<<grid_for(S->maps.n, C->num_sms), kBlock, 0, s>>>(S->maps.n, S->d_own, S->d_xl, x_glob);
     // true residual ||b - S x||_w in FP64
-    k_spmv_asm<kEpiStore><<<S->grid_spmv, kBlock, 0, s>>>(S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op,
-                                                           nullptr, 0, 0);
+    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kBlock, spmv_smem<double>(), s>>>(
+        S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
     k_wdot<true><<<S->grid_vec, kBlock, 0, s>>>(N, S->d_bl, S->d_q, S->op.mult, S->op.wtab, S->d_partials,
                                                 S->d_scal_op, &S->d_scal->aux);
     launches += 3;
     SSG_CUDA_TRY(cudaGetLastError());
     SSG_CUDA_TRY(cudaEventRecord(S->ev1, s));
-    SSG_CUDA_TRY(cudaMemcpyAsync(&h, S->d_scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
-    SSG_CUDA_TRY(cudaStreamSynchronize(s));
+    Scal h{};
+    rc = read_scal(S, S->d_scal, &h);
+    if (rc != SSG_OK) return rc;
     float ms = 0.f;
     SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
-    if (C->driver == SSG_DRIVER_GRAPH) launches += 1 + 3 * static_cast<int64_t>(h.iter) +
-                                                   (h.status == SSG_E_BREAKDOWN ? 1 : 0);
+    if (C->driver == SSG_DRIVER_GRAPH) {
+        if (mode == SSG_MIXED)  // init, per refinement: inner init + 3 tail kernels, 3 per inner iteration
+            launches += 1 + 4 * static_cast<int64_t>(h.iter) + 3 * static_cast<int64_t>(h.total);
+        else
+            launches += 1 + 3 * static_cast<int64_t>(h.iter) + (h.status == SSG_E_BREAKDOWN ? 1 : 0);
+    }
     if (st) {
         st->status = h.status;
-        st->iters = h.iter;
-        st->outer = 1;
+        st->iters = mode == SSG_MIXED ? h.total : h.iter;
+        st->outer = mode == SSG_MIXED ? h.iter : 1;
         st->reserved = 0;
         st->relres = h.relres;
         st->true_relres = h.bnorm > 0.0 ? std::sqrt(h.aux) / h.bnorm : std::sqrt(h.aux);
@@ -405,6 +696,16 @@ int ssg_set_driver(ssg_ctx *ctx, int driver) {
         return SSG_E_INVALID;
     }
     ctx->driver = driver;
+    return SSG_OK;
+}
+
+int ssg_set_mixed(ssg_ctx *ctx, double inner_rtol, int32_t max_outer) {
+    if (!ctx || !(inner_rtol > 0.0 && inner_rtol < 1.0) || max_outer < 1) {
+        set_error("ssg_set_mixed: need 0 < inner_rtol < 1 and max_outer >= 1");
+        return SSG_E_INVALID;
+    }
+    ctx->inner_rtol = inner_rtol;
+    ctx->max_outer = max_outer;
     return SSG_OK;
 }
 
@@ -519,8 +820,21 @@ int ssg_spmv_assembled(ssg_system *S, const double *x_loc, double *y_loc, double
         set_error("x_loc and y_loc must be distinct non-null device vectors");
         return SSG_E_INVALID;
     }
-    k_spmv_asm<kEpiStore><<<S->grid_spmv, kBlock, 0, S->ctx->stream>>>(S->op, x_loc, y_loc, S->d_partials,
-                                                                        S->d_scal_op, xSx_dev, 0, 0);
+    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kBlock, spmv_smem<double>(), S->ctx->stream>>>(
+        S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int ssg_spmv_assembled_f32(ssg_system *S, const float *x_loc, float *y_loc, double *xSx_dev) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (!x_loc || !y_loc || x_loc == y_loc) {
+        set_error("x_loc and y_loc must be distinct non-null device vectors");
+        return SSG_E_INVALID;
+    }
+    k_spmv_asm<kEpiStore, float><<<S->grid_spmv, kBlock, spmv_smem<float>(), S->ctx->stream>>>(
+        S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
@@ -546,8 +860,8 @@ int ssg_solve(ssg_system *S, int32_t k, const double *b, double *x, int32_t x_is
         set_error("bad k, null b/x, or negative rtol");
         return SSG_E_INVALID;
     }
-    if (mode != SSG_FP64) {
-        set_error("mode not available in this build");
+    if (mode != SSG_FP64 && mode != SSG_MIXED) {
+        set_error("mode must be SSG_FP64 or SSG_MIXED");
         return SSG_E_INVALID;
     }
     if (max_iter <= 0) max_iter = S->maps.n;
@@ -555,7 +869,7 @@ int ssg_solve(ssg_system *S, int32_t k, const double *b, double *x, int32_t x_is
     int first_bad = SSG_OK;
     for (int32_t j = 0; j < k; ++j) {
         const size_t o = static_cast<size_t>(j) * S->maps.n;
-        rc = solve_one(S, b + o, x + o, x_is_guess, rtol, max_iter, stats ? stats + j : nullptr);
+        rc = solve_one(S, b + o, x + o, x_is_guess, rtol, max_iter, mode, stats ? stats + j : nullptr);
         if (rc == SSG_E_CUDA || rc == SSG_E_OOM || rc == SSG_E_INVALID) return rc;
         if (rc != SSG_OK && first_bad == SSG_OK) first_bad = rc;
     }
@@ -592,6 +906,8 @@ int ssg_system_destroy(ssg_system *S) {
     if (S->ctx) cudaSetDevice(S->ctx->device);
     if (S->exec) cudaGraphExecDestroy(S->exec);
     if (S->graph) cudaGraphDestroy(S->graph);
+    if (S->exec_m) cudaGraphExecDestroy(S->exec_m);
+    if (S->graph_m) cudaGraphDestroy(S->graph_m);
     if (S->ev0) cudaEventDestroy(S->ev0);
     if (S->ev1) cudaEventDestroy(S->ev1);
     if (S->arena) {

@@ -6,10 +6,14 @@
 // interface rows last (Eq. 2.4:eqn0), so the interior rows of all subdomains
 // form contiguous ranges that the SpMV tiles stream through.
 //
-// Reductions are deterministic: every block reduces its values with a fixed
-// warp-shuffle tree, writes one partial, and the last block to arrive (an
-// atomic ticket, no waiting) sums the partials in a fixed order and applies
-// the scalar step of Algorithm 3 (alpha, beta, the stopping test).
+// Reductions are deterministic: every block reduces its values in a fixed
+// order, writes one partial, and the last block to arrive (an atomic ticket,
+// no waiting) sums the partials in a fixed order and applies the scalar step
+// of Algorithm 3 (alpha, beta, the stopping test).
+//
+// GB300 executes 2 FP64 FMAs per clock per SM, so every FP64 instruction
+// counts: the block reduction runs its adds in one warp (12 warp-level adds
+// per block) and interior entries (weight 1) skip the weight multiply.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,10 +23,13 @@
 
 namespace ssg {
 
-constexpr int kBlock = 256;      // threads per block, every kernel
-constexpr int kTileRows = 256;   // max rows of one interior SpMV tile
-constexpr int kTileNnz = 3072;   // max nonzeros staged in shared memory per tile
-constexpr int kHostChunk = 32;   // iterations per host-loop chunk (SSG_DRIVER_HOST)
+constexpr int kBlock = 256;       // threads per block, every kernel
+constexpr int kTileRows = 256;    // max rows of one interior SpMV tile (one per thread)
+constexpr int kTileNnz = 2048;    // max nonzeros staged in shared memory per tile
+static_assert(kTileRows == kBlock, "an interior item holds at most one row per thread");
+constexpr int kSpmvBlocksPerSM = 3;
+constexpr int kVecBlocksPerSM = 4;
+constexpr int kHostChunk = 32;    // iterations per host-loop chunk (SSG_DRIVER_HOST)
 
 // Scalar state of one CG solve, resident on the device.
 struct Scal {
@@ -41,23 +48,46 @@ struct Scal {
     int32_t stop_after_xp;  // set by the residual update, applied after the x/p update
     int32_t guess;   // x holds an initial guess
     unsigned int ticket[4];
+    // iterative refinement (SSG_MIXED): outer state uses iter as the
+    // refinement count and total for the inner iterations summed; the inner
+    // state stops at sqrt(rho) <= tau * sqrt(rho0)
+    double rho0;
+    double tau;
+    double inner_rtol;
+    int32_t total;
+    int32_t max_outer;
 };
 
 enum { kTicketSpmv = 0, kTicketR = 1, kTicketXP = 2, kTicketMisc = 3 };
+
+// One unit of SpMV work (precomputed on the host, 32 bytes).
+//   kind 0: interior rows [a, b) of the local CSR, nonzeros [e0, e1)
+//   kind 1: interface nodes [a, b), copies [c0, c1), copy-row nonzeros [e0, e1)
+//   kind 2: one interior row a longer than a tile (read from global memory)
+//   kind 3: one interface node a whose copy rows exceed a tile
+struct WorkItem {
+    int32_t kind, a, b, e0, e1, c0, c1, pad;
+};
+
+enum { kItemRows = 0, kItemIface = 1, kItemLongRow = 2, kItemLongIface = 3 };
 
 // Matrix-side arrays on the device (one arena, see api.cu).
 struct DevOp {
     const int32_t *rowptr;  // [nloc+1] concatenated local CSR row pointers
     const int32_t *col;     // [nnz] concatenated column index (subdomain offset + local column)
     const double *val;      // [nnz]
-    const int2 *tiles;      // [ntiles] interior row ranges [x, y)
-    int32_t ntiles;
-    const int32_t *iptr;    // [ngamma+1]
-    const int32_t *icopy;   // [ncopies]
-    int32_t ngamma;
-    int32_t niface_blocks;  // ceil(ngamma / kBlock)
+    const float *val32;     // [nnz] values rounded to FP32 (mixed mode)
+    const int32_t *irp;     // [ncopies+1] row pointers of the interface copy rows, (node, copy) order
+    const int32_t *icol;    // copy-row columns (concatenated local index)
+    const double *ival;     // copy-row values
+    const float *ival32;    // copy-row values rounded to FP32
+    const int32_t *iptr;    // [ngamma+1] copies of each interface node
+    const int32_t *icopy;   // [ncopies] concatenated local index of each copy
+    const WorkItem *items;  // SpMV work list
+    const int2 *block_range;  // [grid] contiguous item range of each block
     const uint8_t *mult;    // [nloc] multiplicity of each local entry's node
     const double *wtab;     // [256] wtab[m] = 1/m
+    const uint8_t *gflag;   // [ceil(nloc / 64)] 1 if entries [64 g, 64 g + 64) hold an interface copy
 };
 
 enum { kEpiStore = 0, kEpiAlpha = 1 };
@@ -68,17 +98,17 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Fixed-order block sum; the result is valid in thread 0.
+// Fixed-order block sum, adds done by warp 0 only; result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v) {
-    __shared__ double ws[kBlock / 32];
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) ws[wid] = v;
+    __shared__ double red[kBlock];
+    __syncthreads();  // protects red[] against a previous call
+    red[threadIdx.x] = v;
     __syncthreads();
     double t = 0.0;
-    if (wid == 0) {
-        t = lane < kBlock / 32 ? ws[lane] : 0.0;
+    if (threadIdx.x < 32) {
+        t = red[threadIdx.x];
+#pragma unroll
+        for (int i = 1; i < kBlock / 32; ++i) t += red[threadIdx.x + 32 * i];
         t = warp_sum(t);
     }
     return t;
@@ -110,73 +140,224 @@ __device__ __forceinline__ void stop_loop(Scal *s, cudaGraphConditionalHandle h,
     if (use_cond) cudaGraphSetConditional(h, 0);
 }
 
-// ---------------------------------------------------------------------------
-// Sub-structured SpMV (Section 3.4.1) with the interface assembly of
-// Algorithms 4 and 5 fused in: blocks [0, niface_blocks) take one interface
-// node per thread, compute the local row product of each of its copies, sum
-// them in ascending subdomain order and write the sum to every copy; the
-// remaining blocks stream interior tiles (values and columns staged in shared
-// memory with coalesced loads, one thread per row).  Interior rows have
-// m = 1, so no assembly touches them.  Every block also accumulates its share
-// of (x, y)_w for the alpha step.
-// ---------------------------------------------------------------------------
-template <int EPI>
-__global__ void __launch_bounds__(kBlock) k_spmv_asm(DevOp A, const double *__restrict__ x, double *__restrict__ y,
-                                                     double *partials, Scal *s, double *out,
-                                                     cudaGraphConditionalHandle h, int use_cond) {
-    if (EPI == kEpiAlpha && s->done) return;
-    __shared__ double sval[kTileNnz];
-    __shared__ int32_t scol[kTileNnz];
-    double dot = 0.0;
-    if ((int)blockIdx.x < A.niface_blocks) {
-        const int g = blockIdx.x * kBlock + threadIdx.x;
-        if (g < A.ngamma) {
-            const int c0 = A.iptr[g], c1 = A.iptr[g + 1];
-            double S = 0.0;
-            for (int c = c0; c < c1; ++c) {
-                const int row = A.icopy[c];
-                double acc = 0.0;
-                const int k1 = A.rowptr[row + 1];
-                for (int k = A.rowptr[row]; k < k1; ++k) acc = fma(A.val[k], __ldg(x + A.col[k]), acc);
-                S += acc;
-            }
-            const double w = A.wtab[c1 - c0];
-            for (int c = c0; c < c1; ++c) {
-                const int row = A.icopy[c];
-                y[row] = S;
-                dot = fma(w * __ldg(x + row), S, dot);
-            }
-        }
+// ---- asynchronous global -> shared copies (16 bytes, L2 evict-first) -------
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, uint64_t policy) {
+    const unsigned int s = static_cast<unsigned int>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "l"(policy)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shared-memory stage of one work item: values, columns and the row/copy
+// pointers it needs, each copied from a 16-byte aligned start at or below its
+// first element.
+template <typename T>
+struct TileStage {
+    T val[kTileNnz + 8];
+    int32_t col[kTileNnz + 8];
+    int32_t rp[kTileRows + 8];  // row pointers (kind 0) or copy-row pointers (kind 1)
+    int32_t ip[kTileRows + 8];  // copy ranges of the nodes (kind 1)
+};
+
+__device__ __forceinline__ void stage_ints(int32_t *dst, const int32_t *src, int lo, int hi, uint64_t pol) {
+    const int a = lo & ~3, b = (hi + 3) & ~3;
+    for (int i = threadIdx.x; i < (b - a) >> 2; i += kBlock) cp_async16(dst + 4 * i, src + a + 4 * i, pol);
+}
+
+template <typename T>
+__device__ __forceinline__ const T *row_vals(const DevOp &A);
+template <>
+__device__ __forceinline__ const double *row_vals<double>(const DevOp &A) { return A.val; }
+template <>
+__device__ __forceinline__ const float *row_vals<float>(const DevOp &A) { return A.val32; }
+template <typename T>
+__device__ __forceinline__ const T *copy_vals(const DevOp &A);
+template <>
+__device__ __forceinline__ const double *copy_vals<double>(const DevOp &A) { return A.ival; }
+template <>
+__device__ __forceinline__ const float *copy_vals<float>(const DevOp &A) { return A.ival32; }
+
+// Issue the copies of work item W into `st` (nothing for the long kinds,
+// which read global memory directly).  Each array is read at most 12 bytes
+// past its last element; the arena pads every array for that.
+template <typename T>
+__device__ __forceinline__ void issue_item(const DevOp &A, const WorkItem &W, TileStage<T> &st, uint64_t pol) {
+    if (W.kind >= kItemLongRow) return;
+    const T *vsrc = W.kind == kItemRows ? row_vals<T>(A) : copy_vals<T>(A);
+    const int32_t *csrc = W.kind == kItemRows ? A.col : A.icol;
+    constexpr int V = 16 / sizeof(T);  // values per 16 bytes
+    const int a0 = W.e0 & ~(V - 1), a1 = (W.e1 + V - 1) & ~(V - 1);
+    for (int i = threadIdx.x; i < (a1 - a0) / V; i += kBlock) cp_async16(st.val + V * i, vsrc + a0 + V * i, pol);
+    stage_ints(st.col, csrc, W.e0, W.e1, pol);
+    if (W.kind == kItemRows) {
+        stage_ints(st.rp, A.rowptr, W.a, W.b + 1, pol);
     } else {
-        const int2 tl = A.tiles[blockIdx.x - A.niface_blocks];
-        const int r0 = tl.x, r1 = tl.y;
-        const int e0 = A.rowptr[r0], e1 = A.rowptr[r1];
-        const int ne = e1 - e0;
-        if (ne <= kTileNnz) {
-            for (int e = threadIdx.x; e < ne; e += kBlock) {
-                sval[e] = __ldcs(A.val + e0 + e);
-                scol[e] = __ldcs(A.col + e0 + e);
-            }
-            __syncthreads();
-            for (int r = r0 + threadIdx.x; r < r1; r += kBlock) {
-                const int a = A.rowptr[r] - e0, b = A.rowptr[r + 1] - e0;
-                double acc = 0.0;
-                for (int k = a; k < b; ++k) acc = fma(sval[k], __ldg(x + scol[k]), acc);
-                y[r] = acc;
-                dot = fma(__ldg(x + r), acc, dot);
-            }
-        } else {
-            // a single row longer than a tile: block-strided partial sums, fixed tree
-            double acc = 0.0;
-            for (int k = e0 + threadIdx.x; k < e1; k += kBlock) acc = fma(A.val[k], __ldg(x + A.col[k]), acc);
-            acc = block_sum(acc);
-            if (threadIdx.x == 0) {
-                y[r0] = acc;
-                dot = __ldg(x + r0) * acc;
-            }
+        stage_ints(st.rp, A.irp, W.c0, W.c1 + 1, pol);
+        stage_ints(st.ip, A.iptr, W.a, W.b + 1, pol);
+    }
+}
+
+template <int N, typename T>
+__device__ __forceinline__ T fma_chain(const T *vv, const T *xv) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc = fma(vv[j], xv[j], acc);
+    return acc;
+}
+
+// Row product over nonzeros [k0, k1) (values/columns read through sv/sc at
+// index k - base), summed in CSR order.  Called by all 32 lanes of a warp
+// (len = 0 for lanes without a row).  On this part a predicated-off FP64
+// instruction still takes its issue slot, so the FMA chain runs exactly the
+// warp's longest row length (a warp-uniform switch), shorter rows padded with
+// 0 * 0 terms, which leave the sum unchanged.
+template <typename T>
+__device__ __forceinline__ T row_dot(const T *sv, const int32_t *sc, int vbase, int cbase, int k0, int len,
+                                     const T *__restrict__ x) {
+    const int wlen = __reduce_max_sync(0xffffffffu, len);
+    if (wlen > 8) {
+        T acc = T(0);
+        for (int k = k0; k < k0 + len; ++k) acc = fma(sv[k - vbase], __ldg(x + sc[k - cbase]), acc);
+        return acc;
+    }
+    T vv[8], xv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        vv[j] = T(0);
+        xv[j] = T(0);
+        if (j < len) {
+            vv[j] = sv[k0 + j - vbase];
+            xv[j] = __ldg(x + sc[k0 + j - cbase]);
         }
     }
-    const double bs = block_sum(dot);
+    switch (wlen) {
+        case 0: return T(0);
+        case 1: return fma_chain<1>(vv, xv);
+        case 2: return fma_chain<2>(vv, xv);
+        case 3: return fma_chain<3>(vv, xv);
+        case 4: return fma_chain<4>(vv, xv);
+        case 5: return fma_chain<5>(vv, xv);
+        case 6: return fma_chain<6>(vv, xv);
+        case 7: return fma_chain<7>(vv, xv);
+        default: return fma_chain<8>(vv, xv);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sub-structured SpMV (Section 3.4.1) with the interface assembly of
+// Algorithms 4 and 5 fused in.  Persistent blocks each walk a fixed,
+// contiguous slice of a precomputed work list (the same rows in the same
+// order on every run, so the (x, y)_w partials are deterministic).  Interior
+// items stream <= 256 rows / <= 2048 nonzeros; interface items stream the
+// copy rows of <= 256 interface nodes, stored contiguously in (node, copy)
+// order: one thread per node forms each copy's local row product, sums them in
+// ascending subdomain order and writes the sum to every copy.  Values,
+// columns and pointers of the next item are staged in shared memory by
+// cp.async (L2 evict-first) while the current item computes.
+// ---------------------------------------------------------------------------
+template <int EPI, typename T>
+__global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSM)
+    k_spmv_asm(DevOp A, const T *__restrict__ x, T *__restrict__ y, double *partials, Scal *s, double *out,
+               cudaGraphConditionalHandle h, int use_cond) {
+    if (EPI == kEpiAlpha && s->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileStage<T> *stage = reinterpret_cast<TileStage<T> *>(smem_raw);
+    const uint64_t pol = policy_evict_first();
+    const int2 range = A.block_range[blockIdx.x];
+    const T *__restrict__ val = row_vals<T>(A);
+    const T *__restrict__ ival = copy_vals<T>(A);
+    constexpr int V = 16 / sizeof(T);
+    T dot = T(0);
+
+    int buf = 0;
+    if (range.x < range.y) issue_item(A, A.items[range.x], stage[0], pol);
+    cp_async_commit();
+    for (int it = range.x; it < range.y; ++it) {
+        if (it + 1 < range.y) issue_item(A, A.items[it + 1], stage[buf ^ 1], pol);
+        cp_async_commit();
+        const WorkItem W = A.items[it];
+        if (W.kind == kItemRows || W.kind == kItemIface) {
+            cp_async_wait<1>();
+            __syncthreads();
+            const TileStage<T> &st = stage[buf];
+            const int vbase = W.e0 & ~(V - 1), cbase = W.e0 & ~3;
+            if (W.kind == kItemRows) {
+                // one row per thread (an item has at most kTileRows == kBlock rows)
+                const int rbase = W.a & ~3;
+                const int r = W.a + threadIdx.x;
+                const bool valid = r < W.b;
+                const int k0 = valid ? st.rp[r - rbase] : 0;
+                const int len = valid ? st.rp[r + 1 - rbase] - k0 : 0;
+                const T acc = row_dot<T>(st.val, st.col, vbase, cbase, k0, len, x);
+                if (valid) {
+                    y[r] = acc;
+                    dot = fma(__ldg(x + r), acc, dot);
+                }
+            } else {
+                const int gbase = W.a & ~3, pbase = W.c0 & ~3;
+                for (int g = W.a + threadIdx.x; g < W.b; g += kBlock) {
+                    const int c0 = st.ip[g - gbase], c1 = st.ip[g + 1 - gbase];
+                    T S = T(0);
+                    for (int c = c0; c < c1; ++c) {
+                        T acc = T(0);
+                        const int k1 = st.rp[c + 1 - pbase];
+                        for (int k = st.rp[c - pbase]; k < k1; ++k)
+                            acc = fma(st.val[k - vbase], __ldg(x + st.col[k - cbase]), acc);
+                        S += acc;
+                    }
+                    const T w = T(__ldg(A.wtab + (c1 - c0)));
+                    for (int c = c0; c < c1; ++c) {
+                        const int row = __ldg(A.icopy + c);
+                        y[row] = S;
+                        dot = fma(w * __ldg(x + row), S, dot);
+                    }
+                }
+            }
+        } else if (W.kind == kItemLongRow) {
+            // one row longer than a stage: block-strided partial sums, fixed tree
+            T acc = T(0);
+            for (int k = W.e0 + threadIdx.x; k < W.e1; k += kBlock) acc = fma(val[k], __ldg(x + A.col[k]), acc);
+            const T racc = T(block_sum(double(acc)));
+            if (threadIdx.x == 0) {
+                y[W.a] = racc;
+                dot = fma(__ldg(x + W.a), racc, dot);
+            }
+        } else {
+            // one interface node whose copy rows exceed a stage: each copy row
+            // reduced by the block (fixed tree), copies summed in ascending s
+            T S = T(0);
+            for (int c = W.c0; c < W.c1; ++c) {
+                T acc = T(0);
+                for (int k = A.irp[c] + threadIdx.x; k < A.irp[c + 1]; k += kBlock)
+                    acc = fma(ival[k], __ldg(x + A.icol[k]), acc);
+                S += T(block_sum(double(acc)));  // valid in thread 0
+            }
+            if (threadIdx.x == 0) {
+                const T w = T(A.wtab[W.c1 - W.c0]);
+                for (int c = W.c0; c < W.c1; ++c) {
+                    const int row = A.icopy[c];
+                    y[row] = S;
+                    dot = fma(w * __ldg(x + row), S, dot);
+                }
+            }
+        }
+        __syncthreads();  // stage[buf] is refilled by the next iteration's prefetch
+        buf ^= 1;
+    }
+    cp_async_wait<0>();
+    const double bs = block_sum(double(dot));
     if (publish_and_check_last(partials, bs, &s->ticket[kTicketSpmv])) {
         const double tot = sum_partials(partials, gridDim.x);
         if (threadIdx.x == 0) {
@@ -196,19 +377,50 @@ __global__ void __launch_bounds__(kBlock) k_spmv_asm(DevOp A, const double *__re
     }
 }
 
+template <typename T>
+constexpr size_t spmv_smem() {
+    return 2 * sizeof(TileStage<T>);
+}
+
+__device__ __forceinline__ double wsq(double r, unsigned int m, const double *__restrict__ wtab, double acc) {
+    return m == 1u ? fma(r, r, acc) : fma(__ldg(wtab + m) * r, r, acc);
+}
+
 // r <- r - alpha q and (r, r)_w; the last block forms beta (Algorithm 3 lines
 // 5 and 7, M = I) and the stopping decision, applied after the x/p update.
 __global__ void __launch_bounds__(kBlock) k_update_r(int64_t N, double *__restrict__ r, const double *__restrict__ q,
                                                      const uint8_t *__restrict__ mult, const double *__restrict__ wtab,
-                                                     double *partials, Scal *s) {
+                                                     const uint8_t *__restrict__ gflag, double *partials, Scal *s) {
     if (s->done) return;
     const double alpha = s->alpha;
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N; i += stride) {
-        const double ri = fma(-alpha, __ldcs(q + i), r[i]);
-        r[i] = ri;
-        acc = fma(__ldg(wtab + mult[i]) * ri, ri, acc);
+    const int64_t N2 = N >> 1;
+    double2 *__restrict__ r2 = reinterpret_cast<double2 *>(r);
+    const double2 *__restrict__ q2 = reinterpret_cast<const double2 *>(q);
+    const uchar2 *__restrict__ m2 = reinterpret_cast<const uchar2 *>(mult);
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N2; i += stride) {
+        double2 rv = r2[i];
+        const double2 qv = __ldcs(q2 + i);
+        rv.x = fma(-alpha, qv.x, rv.x);
+        rv.y = fma(-alpha, qv.y, rv.y);
+        r2[i] = rv;
+        // a warp covers the 64 entries of group i >> 5; groups without an
+        // interface copy have weight 1 everywhere and skip the weight lookup
+        // (1.0 * r == r, so both forms give the same bits)
+        if (__ldg(gflag + (i >> 5)) == 0) {
+            acc = fma(rv.x, rv.x, acc);
+            acc = fma(rv.y, rv.y, acc);
+        } else {
+            const uchar2 mv = m2[i];
+            acc = fma(__ldg(wtab + mv.x) * rv.x, rv.x, acc);
+            acc = fma(__ldg(wtab + mv.y) * rv.y, rv.y, acc);
+        }
+    }
+    if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const double ri = fma(-alpha, q[N - 1], r[N - 1]);
+        r[N - 1] = ri;
+        acc = fma(__ldg(wtab + mult[N - 1]) * ri, ri, acc);
     }
     const double bs = block_sum(acc);
     if (publish_and_check_last(partials, bs, &s->ticket[kTicketR])) {
@@ -237,10 +449,23 @@ __global__ void __launch_bounds__(kBlock) k_update_xp(int64_t N, double *__restr
     if (s->done) return;
     const double alpha = s->alpha, beta = s->beta;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N; i += stride) {
-        const double pi = p[i];
-        x[i] = fma(alpha, pi, x[i]);
-        p[i] = fma(beta, pi, __ldcs(r + i));
+    const int64_t N2 = N >> 1;
+    double2 *x2 = reinterpret_cast<double2 *>(x);
+    double2 *p2 = reinterpret_cast<double2 *>(p);
+    const double2 *r2 = reinterpret_cast<const double2 *>(r);
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N2; i += stride) {
+        const double2 pv = p2[i];
+        double2 xv = __ldcs(x2 + i);
+        const double2 rv = r2[i];
+        xv.x = fma(alpha, pv.x, xv.x);
+        xv.y = fma(alpha, pv.y, xv.y);
+        __stcs(x2 + i, xv);
+        p2[i] = make_double2(fma(beta, pv.x, rv.x), fma(beta, pv.y, rv.y));
+    }
+    if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const double pi = p[N - 1];
+        x[N - 1] = fma(alpha, pi, x[N - 1]);
+        p[N - 1] = fma(beta, pi, r[N - 1]);
     }
     if (publish_and_check_last(partials, 0.0, &s->ticket[kTicketXP])) {
         if (threadIdx.x == 0) {
@@ -265,10 +490,10 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t N, const double *__r
         const double bi = b[i];
         const double ri = guess ? bi - q[i] : bi;
         r[i] = ri;
-        p[i] = ri;
-        const double w = __ldg(wtab + mult[i]);
-        arr = fma(w * ri, ri, arr);
-        abb = fma(w * bi, bi, abb);
+        if (p) p[i] = ri;
+        const unsigned int m = mult[i];
+        arr = wsq(ri, m, wtab, arr);
+        abb = wsq(bi, m, wtab, abb);
     }
     const double srr = block_sum(arr);
     const double sbb = block_sum(abb);
@@ -281,6 +506,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t N, const double *__r
             s->rho = rr;
             s->bnorm = sqrt(bb);
             s->iter = 0;
+            s->total = 0;
             s->done = 0;
             s->stop_after_xp = 0;
             s->alpha = 0.0;
@@ -318,12 +544,11 @@ __global__ void __launch_bounds__(kBlock) k_wdot(int64_t N, const double *__rest
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N; i += stride) {
-        const double w = __ldg(wtab + mult[i]);
+        const unsigned int m = mult[i];
         if (DIFF) {
-            const double d = u[i] - v[i];
-            acc = fma(w * d, d, acc);
+            acc = wsq(u[i] - v[i], m, wtab, acc);
         } else {
-            acc = fma(w * u[i], v[i], acc);
+            acc = m == 1u ? fma(u[i], v[i], acc) : fma(__ldg(wtab + m) * u[i], v[i], acc);
         }
     }
     const double bs = block_sum(acc);
@@ -346,6 +571,188 @@ __global__ void __launch_bounds__(kBlock) k_gather(int64_t n, const int32_t *__r
                                                    const double *__restrict__ xl, double *__restrict__ xg) {
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += stride) xg[i] = __ldg(xl + own[i]);
+}
+
+// ===========================================================================
+// Mixed precision (SSG_MIXED): FP32 inner CG inside FP64 iterative
+// refinement.  Outer state `so` (FP64 residual r64, refinement count in
+// so->iter, inner iterations summed in so->total); inner state `si`.
+// ===========================================================================
+
+// Inner setup: r32 = (float) r64, p32 = r32, d32 = 0, rho0 = (r32, r32)_w and
+// the inner tolerance tau = max(inner_rtol, rtol ||b|| / ||r64||), so the last
+// refinement is not solved further than the outer test needs.
+__global__ void __launch_bounds__(kBlock) k_inner_init(int64_t N, const double *__restrict__ r64,
+                                                       float *__restrict__ r32, float *__restrict__ p32,
+                                                       float *__restrict__ d32, const uint8_t *__restrict__ mult,
+                                                       const double *__restrict__ wtab, double *partials, Scal *si,
+                                                       const Scal *so, cudaGraphConditionalHandle h, int use_cond) {
+    float acc = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N; i += stride) {
+        const float ri = float(r64[i]);
+        r32[i] = ri;
+        p32[i] = ri;
+        d32[i] = 0.f;
+        const unsigned int m = mult[i];
+        acc = m == 1u ? fmaf(ri, ri, acc) : fmaf(float(__ldg(wtab + m)) * ri, ri, acc);
+    }
+    const double bs = block_sum(double(acc));
+    if (publish_and_check_last(partials, bs, &si->ticket[kTicketMisc])) {
+        const double tot = sum_partials(partials, gridDim.x);
+        if (threadIdx.x == 0) {
+            si->ticket[kTicketMisc] = 0;
+            si->rho = tot;
+            si->rho0 = tot;
+            double tau = so->bnorm > 0.0 && so->rho > 0.0 ? so->rtol * so->bnorm / sqrt(so->rho) : 0.0;
+            si->tau = tau > so->inner_rtol ? tau : so->inner_rtol;
+            si->iter = 0;
+            si->alpha = 0.0;
+            si->beta = 0.0;
+            si->status = SSG_OK;
+            si->stop_after_xp = 0;
+            const int stop = !(tot > 0.0) || so->total >= so->max_iter;
+            si->done = stop;
+            if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
+        }
+    }
+}
+
+// r32 <- r32 - alpha q32 and (r32, r32)_w (products in FP32, block sums in
+// FP64); the last block forms beta and the inner stopping decision.
+__global__ void __launch_bounds__(kBlock) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
+                                                       const uint8_t *__restrict__ mult,
+                                                       const double *__restrict__ wtab,
+                                                       const uint8_t *__restrict__ gflag, double *partials, Scal *si,
+                                                       Scal *so) {
+    if (si->done) return;
+    const float alpha = float(si->alpha);
+    float acc = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    const int64_t N2 = N >> 1;
+    float2 *__restrict__ r2 = reinterpret_cast<float2 *>(r);
+    const float2 *__restrict__ q2 = reinterpret_cast<const float2 *>(q);
+    const uchar2 *__restrict__ m2 = reinterpret_cast<const uchar2 *>(mult);
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N2; i += stride) {
+        float2 rv = r2[i];
+        const float2 qv = __ldcs(q2 + i);
+        rv.x = fmaf(-alpha, qv.x, rv.x);
+        rv.y = fmaf(-alpha, qv.y, rv.y);
+        r2[i] = rv;
+        if (__ldg(gflag + (i >> 5)) == 0) {
+            acc = fmaf(rv.x, rv.x, acc);
+            acc = fmaf(rv.y, rv.y, acc);
+        } else {
+            const uchar2 mv = m2[i];
+            acc = fmaf(float(__ldg(wtab + mv.x)) * rv.x, rv.x, acc);
+            acc = fmaf(float(__ldg(wtab + mv.y)) * rv.y, rv.y, acc);
+        }
+    }
+    if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const float ri = fmaf(-alpha, q[N - 1], r[N - 1]);
+        r[N - 1] = ri;
+        acc = fmaf(float(__ldg(wtab + mult[N - 1])) * ri, ri, acc);
+    }
+    const double bs = block_sum(double(acc));
+    if (publish_and_check_last(partials, bs, &si->ticket[kTicketR])) {
+        const double tot = sum_partials(partials, gridDim.x);
+        if (threadIdx.x == 0) {
+            si->ticket[kTicketR] = 0;
+            si->beta = tot / si->rho;
+            si->rho = tot;
+            si->iter += 1;
+            so->total += 1;
+            if (sqrt(tot) <= si->tau * sqrt(si->rho0) || so->total >= so->max_iter) si->stop_after_xp = 1;
+        }
+    }
+}
+
+// d32 <- d32 + alpha p32; p32 <- r32 + beta p32.
+__global__ void __launch_bounds__(kBlock) k_update_dp32(int64_t N, float *__restrict__ d, float *__restrict__ p,
+                                                        const float *__restrict__ r, double *partials, Scal *si,
+                                                        cudaGraphConditionalHandle h, int use_cond) {
+    if (si->done) return;
+    const float alpha = float(si->alpha), beta = float(si->beta);
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    const int64_t N4 = N >> 2;
+    float4 *__restrict__ d4 = reinterpret_cast<float4 *>(d);
+    float4 *__restrict__ p4 = reinterpret_cast<float4 *>(p);
+    const float4 *__restrict__ r4 = reinterpret_cast<const float4 *>(r);
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N4; i += stride) {
+        const float4 pv = p4[i];
+        float4 dv = d4[i];
+        const float4 rv = r4[i];
+        dv.x = fmaf(alpha, pv.x, dv.x);
+        dv.y = fmaf(alpha, pv.y, dv.y);
+        dv.z = fmaf(alpha, pv.z, dv.z);
+        dv.w = fmaf(alpha, pv.w, dv.w);
+        d4[i] = dv;
+        p4[i] = make_float4(fmaf(beta, pv.x, rv.x), fmaf(beta, pv.y, rv.y), fmaf(beta, pv.z, rv.z),
+                            fmaf(beta, pv.w, rv.w));
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (N & 3)) {
+        const int64_t i = (N & ~int64_t(3)) + threadIdx.x;
+        const float pi = p[i];
+        d[i] = fmaf(alpha, pi, d[i]);
+        p[i] = fmaf(beta, pi, r[i]);
+    }
+    if (publish_and_check_last(partials, 0.0, &si->ticket[kTicketXP])) {
+        if (threadIdx.x == 0) {
+            si->ticket[kTicketXP] = 0;
+            if (si->stop_after_xp) stop_loop(si, h, use_cond);
+        }
+    }
+}
+
+// x64 <- x64 + (double) d32 (the refinement update).
+__global__ void __launch_bounds__(kBlock) k_ir_correct(int64_t N, double *__restrict__ x, const float *__restrict__ d) {
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N; i += stride) x[i] += double(d[i]);
+}
+
+// r64 = b - q64 (q64 = S x64 from the FP64 SpMV), (r64, r64)_w, and the outer
+// decision: converged, inner breakdown, refinement or iteration cap.
+__global__ void __launch_bounds__(kBlock) k_ir_residual(int64_t N, const double *__restrict__ b,
+                                                        const double *__restrict__ q, double *__restrict__ r,
+                                                        const uint8_t *__restrict__ mult,
+                                                        const double *__restrict__ wtab, double *partials, Scal *so,
+                                                        const Scal *si, cudaGraphConditionalHandle h, int use_cond) {
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N; i += stride) {
+        const double ri = b[i] - q[i];
+        r[i] = ri;
+        acc = wsq(ri, mult[i], wtab, acc);
+    }
+    const double bs = block_sum(acc);
+    if (publish_and_check_last(partials, bs, &so->ticket[kTicketMisc])) {
+        const double tot = sum_partials(partials, gridDim.x);
+        if (threadIdx.x == 0) {
+            so->ticket[kTicketMisc] = 0;
+            so->rho = tot;
+            so->iter += 1;
+            so->relres = so->bnorm > 0.0 ? sqrt(tot) / so->bnorm : 0.0;
+            int stop = 1;
+            if (sqrt(tot) <= so->rtol * so->bnorm) {
+                so->status = SSG_OK;
+            } else if (si->status == SSG_E_BREAKDOWN) {
+                so->status = SSG_E_BREAKDOWN;
+            } else if (so->iter >= so->max_outer || so->total >= so->max_iter) {
+                so->status = SSG_E_NOT_CONVERGED;
+            } else {
+                stop = 0;
+            }
+            so->done = stop;
+            if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
+        }
+    }
+}
+
+__global__ void k_set_mixed(Scal *s, double inner_rtol, int32_t max_outer) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        s->inner_rtol = inner_rtol;
+        s->max_outer = max_outer;
+    }
 }
 
 }  // namespace ssg

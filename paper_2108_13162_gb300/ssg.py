@@ -35,6 +35,7 @@ EXPORTS = (
     "ssg_create",
     "ssg_set_stream",
     "ssg_set_driver",
+    "ssg_set_mixed",
     "ssg_destroy",
     "ssg_partition",
     "ssg_get_sizes",
@@ -42,6 +43,7 @@ EXPORTS = (
     "ssg_scatter",
     "ssg_gather",
     "ssg_spmv_assembled",
+    "ssg_spmv_assembled_f32",
     "ssg_wdot",
     "ssg_solve",
     "ssg_solve_host",
@@ -113,6 +115,7 @@ def lib():
         L.ssg_create.argtypes = [C.POINTER(vp), C.c_int, vp]
         L.ssg_set_stream.argtypes = [vp, vp]
         L.ssg_set_driver.argtypes = [vp, C.c_int]
+        L.ssg_set_mixed.argtypes = [vp, C.c_double, C.c_int32]
         L.ssg_destroy.argtypes = [vp]
         L.ssg_partition.argtypes = [vp, i32, vp, vp, vp, vp, i32, C.POINTER(vp)]
         L.ssg_get_sizes.argtypes = [vp, C.POINTER(ssg_sizes)]
@@ -120,6 +123,7 @@ def lib():
         L.ssg_scatter.argtypes = [vp, vp, vp]
         L.ssg_gather.argtypes = [vp, vp, vp]
         L.ssg_spmv_assembled.argtypes = [vp, vp, vp, vp]
+        L.ssg_spmv_assembled_f32.argtypes = [vp, vp, vp, vp]
         L.ssg_wdot.argtypes = [vp, vp, vp, vp]
         L.ssg_solve.argtypes = [vp, i32, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
         L.ssg_solve_host.argtypes = [vp, i32, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
@@ -180,6 +184,10 @@ def ssg_set_driver(ctx, driver: int):
     return _check(lib().ssg_set_driver(ctx, driver), "ssg_set_driver")
 
 
+def ssg_set_mixed(ctx, inner_rtol: float, max_outer: int):
+    return _check(lib().ssg_set_mixed(ctx, inner_rtol, max_outer), "ssg_set_mixed")
+
+
 def ssg_destroy(ctx):
     return lib().ssg_destroy(ctx)
 
@@ -237,6 +245,21 @@ def ssg_spmv_assembled(sys, x_loc, y_loc, xSx=None):
     return _check(
         lib().ssg_spmv_assembled(sys, _dev_f64(x_loc), _dev_f64(y_loc), None if xSx is None else _dev_f64(xSx)),
         "ssg_spmv_assembled",
+    )
+
+
+def _dev_f32(t):
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    return t.data_ptr()
+
+
+def ssg_spmv_assembled_f32(sys, x_loc, y_loc, xSx=None):
+    return _check(
+        lib().ssg_spmv_assembled_f32(sys, _dev_f32(x_loc), _dev_f32(y_loc), None if xSx is None else _dev_f64(xSx)),
+        "ssg_spmv_assembled_f32",
     )
 
 
@@ -317,6 +340,9 @@ class Context:
     def set_driver(self, driver: int):
         ssg_set_driver(self.h, driver)
 
+    def set_mixed(self, inner_rtol: float = 1e-4, max_outer: int = 30):
+        ssg_set_mixed(self.h, inner_rtol, max_outer)
+
     def close(self):
         """Free the context once no System created on it is alive (the C
         library refuses earlier; a System keeps its Context referenced)."""
@@ -360,6 +386,14 @@ class System:
     def spmv(self, x_loc, out=None, xSx=None):
         out = self._empty_loc() if out is None else out
         ssg_spmv_assembled(self.h, x_loc, out, xSx)
+        return out
+
+    def spmv_prec(self, x_loc, out, prec="fp64", xSx=None):
+        """Sub-structured SpMV in FP64 (prec="fp64") or FP32 ("fp32")."""
+        if prec == "fp32":
+            ssg_spmv_assembled_f32(self.h, x_loc, out, xSx)
+        else:
+            ssg_spmv_assembled(self.h, x_loc, out, xSx)
         return out
 
     def wdot(self, u, v, out=None):

@@ -2,7 +2,8 @@
 
 The full 128^3 finite-volume workload (4x4x4 boxes, kappa = exp(g),
 g ~ N(0,1), x* ~ U[-1,1], b = A x*) solved by the oracle's sub-structured CG
-(Algorithm 3, M = I) to a recursive relative residual of 1e-8 and of 1e-12.  Stored
+(Algorithm 3, M = I) to a recursive relative residual of 1e-8 and of 1e-12, plus the
+mixed-precision refinement (FP32 inner CG, FP64 residuals) to 1e-8.  Stored
 per solve: the iteration count, final residuals, the Lanczos condition
 estimate and the solution at 4096 seeded sample indices.  Calls only oracle/
 and synth/; takes about three minutes of one CPU core.
@@ -50,6 +51,22 @@ def main():
             "oracle_seconds_one_core": dt,
         })
         print("rtol %g: %d iterations, %.1f s" % (rtol, r.iters, dt))
+    # mixed precision: FP32 inner CG (tolerance 1e-4) inside FP64 refinement to 1e-8
+    t0 = time.time()
+    r = part.cg_mixed(b, 1e-8, 100000, 1e-4, 30)
+    dt = time.time() - t0
+    assert r.status == oracle.OK
+    rec["mixed"] = {
+        "rtol": 1e-8,
+        "inner_rtol": 1e-4,
+        "iters": r.iters,
+        "outer": r.outer,
+        "relres": r.relres,
+        "err_vs_xstar": float(np.linalg.norm(r.x - p.xstar[:, 0]) / np.linalg.norm(p.xstar[:, 0])),
+        "sample_x": [float(v) for v in r.x[idx]],
+        "oracle_seconds_one_core": dt,
+    }
+    print("mixed: %d inner iterations, %d refinements, %.1f s" % (r.iters, r.outer, dt))
     with open(OUT, "w") as f:
         json.dump(rec, f)
     print("wrote %s" % OUT)

@@ -1,0 +1,154 @@
+"""GPU mixed-precision solve (SSG_MIXED: FP32 inner CG inside FP64 iterative
+refinement) against the oracle's or_sub_cg_mixed, through the C ABI.
+
+Checks (the refinement has no exact counterpart to compare bit for bit: the
+inner FP32 sums are ordered differently on each side):
+  * converged, and the FP64 true residual ||b - S x|| / ||b|| recomputed on
+    the CPU with the oracle's global product is <= rtol;
+  * the refinement count equals the oracle's (+-1) and the summed inner
+    iterations are within max(3, 5 %) of the oracle's;
+  * the solution is within 2 kappa rtol of x* and of the oracle's solution
+    (kappa from the Lanczos coefficients of the FP64 oracle run);
+  * both drivers (graph, host loop) give the same bits; the parameters are
+    validated; a one-refinement cap stops with SSG_E_NOT_CONVERGED.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import CSR, config_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    from paper_2108_13162_gb300 import build as ssg_build
+    from paper_2108_13162_gb300.ssg import Context
+
+    ssg_build.build()
+    c = Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def _t(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+CASES = [
+    ("config1", lambda: config_problem(1), 1e-10),
+    ("fv3d_24", lambda: config_problem(2, scale=24), 1e-8),
+    ("fv3d_40", lambda: config_problem(2, scale=40), 1e-8),
+    ("fe2d_64", lambda: config_problem(3, scale=64), 1e-8),
+]
+
+
+@pytest.mark.parametrize("name,mk,rtol", CASES, ids=[c[0] for c in CASES])
+def test_mixed_matches_oracle(ctx, name, mk, rtol):
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    p = mk()
+    b = p.b[:, 0]
+    S = System(ctx, p.A, p.part, p.P)
+    ref = oracle.Partition(p.A, p.part, p.P)
+    rm = ref.cg_mixed(b, rtol, 100000, 1e-4, 30)
+    r64 = ref.cg(b, rtol, 100000)
+    x, rc, st = S.solve(_t(b), rtol=rtol, max_iter=100000, mode=ssg.SSG_MIXED)
+    assert rc == ssg.SSG_OK and rm.status == oracle.OK
+    xg = x.cpu().numpy()
+    tr = np.linalg.norm(b - oracle.spmv(p.A, xg)) / np.linalg.norm(b)
+    assert tr <= 1.0001 * rtol
+    assert abs(st[0]["true_relres"] - tr) <= 1e-6 * tr + 1e-16
+    assert abs(st[0]["outer"] - rm.outer) <= 1
+    assert abs(st[0]["iters"] - rm.iters) <= max(3, 0.05 * rm.iters)
+    kap = oracle.cond_from_lanczos(r64.alpha, r64.beta)
+    assert _rel(xg, p.xstar[:, 0]) <= 2 * kap * rtol
+    assert _rel(xg, rm.x) <= 2 * kap * rtol
+
+
+def test_mixed_drivers_agree_and_deterministic(ctx):
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    p = config_problem(2, scale=20)
+    S = System(ctx, p.A, p.part, p.P)
+    b = _t(p.b[:, 0])
+    x1, rc1, s1 = S.solve(b, rtol=1e-8, mode=ssg.SSG_MIXED)
+    x2, rc2, s2 = S.solve(b, rtol=1e-8, mode=ssg.SSG_MIXED)
+    assert np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
+    ctx.set_driver(ssg.SSG_DRIVER_HOST)
+    try:
+        x3, rc3, s3 = S.solve(b, rtol=1e-8, mode=ssg.SSG_MIXED)
+    finally:
+        ctx.set_driver(ssg.SSG_DRIVER_GRAPH)
+    assert rc1 == rc3 == ssg.SSG_OK
+    assert (s3[0]["iters"], s3[0]["outer"]) == (s1[0]["iters"], s1[0]["outer"])
+    assert np.array_equal(x3.cpu().numpy(), x1.cpu().numpy())
+
+
+def test_mixed_parameters_and_caps(ctx):
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    with pytest.raises(ssg.SSGError):
+        ctx.set_mixed(0.0, 30)
+    with pytest.raises(ssg.SSGError):
+        ctx.set_mixed(1e-4, 0)
+    p = config_problem(2, scale=16)
+    S = System(ctx, p.A, p.part, p.P)
+    ctx.set_mixed(1e-4, 1)
+    try:
+        x, rc, st = S.solve(_t(p.b[:, 0]), rtol=1e-10, mode=ssg.SSG_MIXED)
+    finally:
+        ctx.set_mixed(1e-4, 30)
+    assert rc == ssg.SSG_E_NOT_CONVERGED and st[0]["outer"] == 1
+    # identity: each refinement's inner solve ends after one iteration (its
+    # alpha is 1 up to the FP32 rounding of two differently ordered sums)
+    n = 500
+    eye = CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
+    S2 = System(ctx, eye, (np.arange(n) % 5).astype(np.int32), 5)
+    bb = np.float32(np.random.default_rng(1).uniform(-1, 1, n)).astype(np.float64)
+    x, rc, st = S2.solve(_t(bb), rtol=1e-12, mode=ssg.SSG_MIXED)
+    assert rc == 0 and st[0]["outer"] <= 3 and st[0]["iters"] == st[0]["outer"]
+    assert _rel(x.cpu().numpy(), bb) <= 1e-12
+
+
+def test_mixed_full_size_128cube(ctx):
+    """The benchmark workload in mixed mode against the stored oracle run."""
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_fv3d_128_4x4x4.json")) as f:
+        g = json.load(f)
+    gm = g["mixed"]
+    kap = [s for s in g["solves"] if s["rtol"] == 1e-8][0]["kappa_lanczos"]
+    p = config_problem(2)
+    b = p.b[:, 0]
+    S = System(ctx, p.A, p.part, p.P)
+    x, rc, st = S.solve(_t(b), rtol=1e-8, max_iter=100000, mode=ssg.SSG_MIXED)
+    assert rc == 0
+    xg = x.cpu().numpy()
+    tr = np.linalg.norm(b - oracle.spmv(p.A, xg)) / np.linalg.norm(b)
+    print("mixed 128^3: inner %d (oracle %d), outer %d (oracle %d), true relres %.3e" % (
+        st[0]["iters"], gm["iters"], st[0]["outer"], gm["outer"], tr))
+    assert tr <= 1.0001e-8
+    assert abs(st[0]["outer"] - gm["outer"]) <= 1
+    assert abs(st[0]["iters"] - gm["iters"]) <= max(3, 0.05 * gm["iters"])
+    idx = np.array(g["sample_idx"])
+    assert _rel(xg[idx], np.array(gm["sample_x"])) <= 2 * kap * 1e-8
+    assert _rel(xg, p.xstar[:, 0]) <= 2 * kap * 1e-8

@@ -143,6 +143,31 @@ def test_wdot_parity(ctx, case):
     assert out.item() == out2.item()
 
 
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_spmv_f32_parity(ctx, case):
+    """FP32 SpMV (mixed mode's inner operator): both sides round values and x
+    to FP32 the same way; |dy_i| <= 4 (L_i + m_i) u32 (|A||x|)_i, u32 = 2^-24."""
+    import torch
+
+    from paper_2108_13162_gb300.ssg import System
+
+    _, A, part, P = case
+    S = System(ctx, A, part, P)
+    ref = oracle.Partition(A, part, P)
+    m = ref.maps
+    x = np.random.default_rng(9).uniform(-1, 1, A.n)
+    xl32 = ref.scatter(x).astype(np.float32)
+    y_ref = ref.spmv32(xl32).astype(np.float64)
+    y = torch.empty(m.nloc, dtype=torch.float32, device="cuda")
+    S.spmv_prec(torch.from_numpy(xl32).cuda(), y, "fp32")
+    yg = y.cpu().numpy().astype(np.float64)
+    absAx = abs(A.to_scipy()) @ np.abs(x)
+    L = np.diff(A.rowptr)
+    bound = 4.0 * (L[m.l2g] + m.mult[m.l2g]) * 2.0**-24 * absAx[m.l2g] * 1.0001
+    assert np.all(np.abs(yg - y_ref) <= bound)
+    assert np.array_equal(yg, yg[m.own][m.l2g])  # copies consistent
+
+
 def test_spmv_full_size_128cube(ctx):
     """The 128^3, 64-subdomain workload the benchmark times: every output checked."""
     p = config_problem(2)

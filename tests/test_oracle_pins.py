@@ -361,8 +361,8 @@ def test_breakdown_on_indefinite():
 # ---------------------------------------------------------------- planted mistakes
 MUTATIONS = {
     # interface assembly keeps only the last copy instead of the sum
-    "no_assembly_sum": ("for (int32_t c = h->iptr[g]; c < h->iptr[g + 1]; ++c) S += yl[h->icopy[c]];",
-                        "for (int32_t c = h->iptr[g]; c < h->iptr[g + 1]; ++c) S = yl[h->icopy[c]];"),
+    "no_assembly_sum": ("double S = 0.0;\n        for (int32_t c = h->iptr[g]; c < h->iptr[g + 1]; ++c) S += yl[h->icopy[c]];",
+                        "double S = 0.0;\n        for (int32_t c = h->iptr[g]; c < h->iptr[g + 1]; ++c) S = yl[h->icopy[c]];"),
     # unweighted dot (w = 1 on every copy)
     "unit_weights": ("h->w[k] = 1.0 / (double)h->mult[h->l2g[k]];", "h->w[k] = 1.0;"),
     # off-diagonal entries owned by the higher subdomain, interface entries counted twice
@@ -412,3 +412,60 @@ def test_planted_mistake_is_caught(name):
     finally:
         os.remove(path)
     assert failures, "planted mistake %s slipped through every pin" % name
+
+
+# ---------------------------------------------------------------- mixed precision (library mode SSG_MIXED)
+def test_mixed_identity_one_step():
+    """A = I with b exactly representable in FP32: one inner iteration gives
+    d = b exactly, so one refinement reaches a zero residual."""
+    n = 64
+    eye = CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
+    b = np.float32(np.random.default_rng(3).uniform(-1, 1, n)).astype(np.float64)
+    r = oracle.Partition(eye, (np.arange(n) % 3).astype(np.int32), 3).cg_mixed(b, 1e-12, 100, 1e-4, 10)
+    assert r.status == oracle.OK and r.outer == 1 and r.iters == 1
+    assert np.array_equal(r.x, b)
+
+
+@pytest.mark.parametrize("scale", [16, 24])
+def test_mixed_true_residual_and_manufactured(scale):
+    """The refinement stops on the FP64 true residual: recomputed with the
+    global FP64 product it is <= rtol, and x* is recovered within 2 kappa rtol."""
+    p = config_problem(2, scale=scale)
+    b = p.b[:, 0]
+    Pt = oracle.Partition(p.A, p.part, p.P)
+    r = Pt.cg_mixed(b, 1e-8, 100000, 1e-4, 30)
+    assert r.status == oracle.OK and r.outer >= 2
+    tr = np.linalg.norm(b - oracle.spmv(p.A, r.x)) / np.linalg.norm(b)
+    assert tr <= 1.0001e-8
+    r64 = Pt.cg(b, 1e-8, 100000)
+    kap = oracle.cond_from_lanczos(r64.alpha, r64.beta)
+    assert np.linalg.norm(r.x - p.xstar[:, 0]) / np.linalg.norm(p.xstar[:, 0]) <= 2 * kap * 1e-8
+    # FP32 inner solves cost only a few more iterations than one FP64 solve
+    assert r.iters <= 1.5 * r64.iters
+
+
+MIXED_MUTATIONS = {
+    # the outer residual is not recomputed after the correction
+    "stale_outer_residual": ("        or_sub_spmv(h, xl, q);\n        for (int64_t k = 0; k < L; ++k) r[k] = bl[k] - q[k];\n        rho = or_wdot(h, r, r);\n        ++outer;",
+                             "        ++outer;"),
+    # the correction is dropped
+    "no_correction": ("for (int64_t k = 0; k < L; ++k) xl[k] = xl[k] + (double)d32[k];", ""),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MIXED_MUTATIONS))
+def test_mixed_planted_mistake_is_caught(name):
+    old, new = MIXED_MUTATIONS[name]
+    src = oracle.source_text()
+    assert src.count(old) == 1, name
+    path = oracle.compile_variant(src.replace(old, new), name)
+    caught = False
+    try:
+        with oracle.use_library(path):
+            try:
+                test_mixed_true_residual_and_manufactured(16)
+            except AssertionError:
+                caught = True
+    finally:
+        os.remove(path)
+    assert caught, "planted mistake %s slipped through" % name
