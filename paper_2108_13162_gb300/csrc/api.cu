@@ -81,16 +81,18 @@ namespace {
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // SpMV work list (see WorkItem in kernels.cuh).  Interior items: greedy runs
-// of consecutive interior rows of one subdomain, at most kTileRows rows and
-// kTileNnz nonzeros; a longer row is an item of its own.  Interface items:
-// greedy runs of consecutive interface nodes with at most kTileRows nodes,
-// kTileRows copies and kTileNnz copy-row nonzeros.  Interface items are
-// spread evenly among the interior ones.
+// of consecutive interior rows of one subdomain, at most kWarpRows rows and
+// kWarpNnz nonzeros; a longer row is an item of its own.  Interface items:
+// greedy runs of consecutive interface nodes with at most kWarpRows nodes,
+// kWarpCopies copies and kWarpNnz copy-row nonzeros.  Interface items are
+// spread evenly among the interior ones, and the list is cut into one
+// contiguous slice of about equal cost per warp.
 struct WorkPlan {
     std::vector<int32_t> irp, icol;
     std::vector<double> ival;
     std::vector<WorkItem> items;
-    std::vector<int2> block_range;
+    std::vector<int2> warp_range;
+    int grid = 0;
 };
 
 WorkPlan make_plan(const HostMaps &M, int grid_cap) {
@@ -116,7 +118,7 @@ WorkPlan make_plan(const HostMaps &M, int grid_cap) {
         while (r < rend) {
             int32_t r1 = r;
             const int32_t e0 = M.lrowptr[r];
-            while (r1 < rend && r1 - r < kTileRows && M.lrowptr[r1 + 1] - e0 <= kTileNnz) ++r1;
+            while (r1 < rend && r1 - r < kWarpRows && M.lrowptr[r1 + 1] - e0 <= kWarpNnz) ++r1;
             if (r1 == r) {
                 rows.push_back({kItemLongRow, r, r + 1, e0, M.lrowptr[r + 1], 0, 0, 0});
                 r = r + 1;
@@ -131,8 +133,8 @@ WorkPlan make_plan(const HostMaps &M, int grid_cap) {
         int32_t g1 = g;
         const int32_t c0 = M.iptr[g];
         const int32_t e0 = W.irp[c0];
-        while (g1 < M.ngamma && g1 - g < kTileRows && M.iptr[g1 + 1] - c0 <= kTileRows &&
-               W.irp[M.iptr[g1 + 1]] - e0 <= kTileNnz)
+        while (g1 < M.ngamma && g1 - g < kWarpRows && M.iptr[g1 + 1] - c0 <= kWarpCopies &&
+               W.irp[M.iptr[g1 + 1]] - e0 <= kWarpNnz)
             ++g1;
         if (g1 == g) {
             iface.push_back({kItemLongIface, g, g + 1, e0, W.irp[M.iptr[g + 1]], c0, M.iptr[g + 1], 0});
@@ -150,23 +152,26 @@ WorkPlan make_plan(const HostMaps &M, int grid_cap) {
         if (i < nr) W.items.push_back(rows[i]);
     }
     while (j < ni) W.items.push_back(iface[j++]);
-    // contiguous slices of about equal cost (nonzeros + 4 per row or copy)
+    // contiguous slices of about equal cost (nonzeros + 4 per row or copy),
+    // one per warp of the launch
     const int n = static_cast<int>(W.items.size());
-    const int G = std::max(1, std::min(n, grid_cap));
+    const int blocks = std::max(1, std::min((n + kSpmvWarps - 1) / kSpmvWarps, grid_cap));
+    const int G = blocks * kSpmvWarps;
+    W.grid = blocks;
     std::vector<double> prefix(static_cast<size_t>(n) + 1, 0.0);
     for (int i = 0; i < n; ++i) {
         const WorkItem &w = W.items[i];
         const double rowsn = (w.kind == kItemIface || w.kind == kItemLongIface) ? (w.c1 - w.c0) : (w.b - w.a);
         prefix[i + 1] = prefix[i] + (w.e1 - w.e0) + 4.0 * rowsn;
     }
-    W.block_range.resize(G);
+    W.warp_range.resize(G);
     int lo = 0;
     for (int b = 0; b < G; ++b) {
         const double target = prefix[n] * (b + 1) / G;
         int hi = lo;
         while (hi < n && (prefix[hi + 1] <= target || hi == lo)) ++hi;
         if (b == G - 1) hi = n;
-        W.block_range[b] = make_int2(lo, hi);
+        W.warp_range[b] = make_int2(lo, hi);
         lo = hi;
     }
     return W;
@@ -174,7 +179,7 @@ WorkPlan make_plan(const HostMaps &M, int grid_cap) {
 
 int launch_body(ssg_system *S, cudaStream_t st, int use_cond) {
     const int64_t N = S->maps.nloc;
-    k_spmv_asm<kEpiAlpha, double><<<S->grid_spmv, kBlock, spmv_smem<double>(), st>>>(
+    k_spmv_asm<kEpiAlpha, double><<<S->grid_spmv, kSpmvThreads, spmv_smem<double>(), st>>>(
         S->op, S->d_p, S->d_q, S->d_partials, S->d_scal, nullptr, S->cond, use_cond);
     k_update_r<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_r, S->d_q, S->op.mult, S->op.wtab, S->op.gflag,
                                                S->d_partials, S->d_scal);
@@ -263,7 +268,7 @@ int launch_inner_init(ssg_system *S, cudaStream_t st, int use_cond) {
 
 int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond) {
     const int64_t N = S->maps.nloc;
-    k_spmv_asm<kEpiAlpha, float><<<S->grid_spmv, kBlock, spmv_smem<float>(), st>>>(
+    k_spmv_asm<kEpiAlpha, float><<<S->grid_spmv, kSpmvThreads, spmv_smem<float>(), st>>>(
         S->op, S->d_p32, S->d_q32, S->d_partials, S->d_scal_in, nullptr, S->cond_in, use_cond);
     k_update_r32<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_r32, S->d_q32, S->op.mult, S->op.wtab, S->op.gflag,
                                                  S->d_partials, S->d_scal_in, S->d_scal);
@@ -276,7 +281,7 @@ int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond) {
 int launch_outer_tail(ssg_system *S, cudaStream_t st, int use_cond) {
     const int64_t N = S->maps.nloc;
     k_ir_correct<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_xl, S->d_d32);
-    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kBlock, spmv_smem<double>(), st>>>(
+    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, spmv_smem<double>(), st>>>(
         S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
     k_ir_residual<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_bl, S->d_q, S->d_r, S->op.mult, S->op.wtab, S->d_partials,
                                                   S->d_scal, S->d_scal_in, S->cond_out, use_cond);
@@ -341,11 +346,12 @@ int build_graph_mixed(ssg_system *S) {
     cudaGraph_t body_out = nullptr, body_in = nullptr;
     if (e == cudaSuccess && rc == SSG_OK) e = last_node(S->graph_m, &n_init);
     if (e == cudaSuccess && rc == SSG_OK) e = add_while(S->graph_m, &n_init, S->cond_out, &n_outer, &body_out);
+    // the inner handle must exist before the kernels that set it are captured
+    if (e == cudaSuccess && rc == SSG_OK)
+        e = cudaGraphConditionalHandleCreate(&S->cond_in, body_out, 0u, cudaGraphCondAssignDefault);
     if (e == cudaSuccess && rc == SSG_OK)
         e = capture_into(cap, body_out, nullptr, 0, [&](cudaStream_t c) { return launch_inner_init(S, c, 1); }, &rc);
     if (e == cudaSuccess && rc == SSG_OK) e = last_node(body_out, &n_iinit);
-    if (e == cudaSuccess && rc == SSG_OK)
-        e = cudaGraphConditionalHandleCreate(&S->cond_in, body_out, 0u, cudaGraphCondAssignDefault);
     if (e == cudaSuccess && rc == SSG_OK) e = add_while(body_out, &n_iinit, S->cond_in, &n_inner, &body_in);
     if (e == cudaSuccess && rc == SSG_OK)
         e = capture_into(cap, body_in, nullptr, 0, [&](cudaStream_t c) { return launch_inner_body(S, c, 1); }, &rc);
@@ -384,7 +390,7 @@ int upload(ssg_system *S) {
     std::vector<double> wtab(256, 0.0);
     for (int m = 1; m < 256; ++m) wtab[m] = 1.0 / static_cast<double>(m);
 
-    S->grid_spmv = static_cast<int>(plan.block_range.size());
+    S->grid_spmv = plan.grid;
     S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N / 2 + kBlock - 1) / kBlock), C->num_sms * kVecBlocksPerSM));
     S->n_partials = 2 * std::max(S->grid_spmv, S->grid_vec);
     SSG_CUDA_TRY(cudaFuncSetAttribute(k_spmv_asm<kEpiStore, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -418,7 +424,7 @@ int upload(ssg_system *S) {
     size_t i_icol = add(plan.icol.data(), sizeof(int32_t) * plan.icol.size());
     size_t i_ival = add(plan.ival.data(), sizeof(double) * plan.ival.size());
     size_t i_items = add(plan.items.data(), sizeof(WorkItem) * plan.items.size());
-    size_t i_brange = add(plan.block_range.data(), sizeof(int2) * plan.block_range.size());
+    size_t i_brange = add(plan.warp_range.data(), sizeof(int2) * plan.warp_range.size());
     size_t i_iptr = add(M.iptr.data(), sizeof(int32_t) * (M.ngamma + 1));
     size_t i_icopy = add(M.icopy.data(), sizeof(int32_t) * M.ncopies);
     size_t i_mult = add(mloc.data(), N);
@@ -471,7 +477,7 @@ int upload(ssg_system *S) {
     S->op.icol = static_cast<const int32_t *>(at(i_icol));
     S->op.ival = static_cast<const double *>(at(i_ival));
     S->op.items = static_cast<const WorkItem *>(at(i_items));
-    S->op.block_range = static_cast<const int2 *>(at(i_brange));
+    S->op.warp_range = static_cast<const int2 *>(at(i_brange));
     S->op.iptr = static_cast<const int32_t *>(at(i_iptr));
     S->op.icopy = static_cast<const int32_t *>(at(i_icopy));
     S->op.mult = static_cast<const uint8_t *>(at(i_mult));
@@ -583,7 +589,7 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     ++launches;
     if (guess) {
         k_scatter<<<grid_for(N, C->num_sms), kBlock, 0, s>>>(N, S->d_l2g, x_glob, S->d_xl);
-        k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kBlock, spmv_smem<double>(), s>>>(
+        k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, spmv_smem<double>(), s>>>(
             S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
         launches += 2;
     } else {
@@ -607,7 +613,7 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     }
     k_gather<<<grid_for(S->maps.n, C->num_sms), kBlock, 0, s>>>(S->maps.n, S->d_own, S->d_xl, x_glob);
     // true residual ||b - S x||_w in FP64
-    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kBlock, spmv_smem<double>(), s>>>(
+    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, spmv_smem<double>(), s>>>(
         S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
     k_wdot<true><<<S->grid_vec, kBlock, 0, s>>>(N, S->d_bl, S->d_q, S->op.mult, S->op.wtab, S->d_partials,
                                                 S->d_scal_op, &S->d_scal->aux);
@@ -820,7 +826,7 @@ int ssg_spmv_assembled(ssg_system *S, const double *x_loc, double *y_loc, double
         set_error("x_loc and y_loc must be distinct non-null device vectors");
         return SSG_E_INVALID;
     }
-    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kBlock, spmv_smem<double>(), S->ctx->stream>>>(
+    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, spmv_smem<double>(), S->ctx->stream>>>(
         S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
@@ -833,7 +839,7 @@ int ssg_spmv_assembled_f32(ssg_system *S, const float *x_loc, float *y_loc, doub
         set_error("x_loc and y_loc must be distinct non-null device vectors");
         return SSG_E_INVALID;
     }
-    k_spmv_asm<kEpiStore, float><<<S->grid_spmv, kBlock, spmv_smem<float>(), S->ctx->stream>>>(
+    k_spmv_asm<kEpiStore, float><<<S->grid_spmv, kSpmvThreads, spmv_smem<float>(), S->ctx->stream>>>(
         S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;

@@ -24,10 +24,12 @@
 namespace ssg {
 
 constexpr int kBlock = 256;       // threads per block, every kernel
-constexpr int kTileRows = 256;    // max rows of one interior SpMV tile (one per thread)
-constexpr int kTileNnz = 2048;    // max nonzeros staged in shared memory per tile
-static_assert(kTileRows == kBlock, "an interior item holds at most one row per thread");
-constexpr int kSpmvBlocksPerSM = 3;
+constexpr int kSpmvWarps = 4;               // warps per SpMV block
+constexpr int kSpmvThreads = 32 * kSpmvWarps;
+constexpr int kWarpRows = 32;               // rows (or interface nodes) per warp item: one per lane
+constexpr int kWarpNnz = 256;               // nonzeros staged per warp item
+constexpr int kWarpCopies = 64;             // interface copies staged per warp item
+constexpr int kSpmvBlocksPerSM = 6;
 constexpr int kVecBlocksPerSM = 4;
 constexpr int kHostChunk = 32;    // iterations per host-loop chunk (SSG_DRIVER_HOST)
 
@@ -84,7 +86,7 @@ struct DevOp {
     const int32_t *iptr;    // [ngamma+1] copies of each interface node
     const int32_t *icopy;   // [ncopies] concatenated local index of each copy
     const WorkItem *items;  // SpMV work list
-    const int2 *block_range;  // [grid] contiguous item range of each block
+    const int2 *warp_range;  // [grid * kSpmvWarps] contiguous item range of each warp
     const uint8_t *mult;    // [nloc] multiplicity of each local entry's node
     const double *wtab;     // [256] wtab[m] = 1/m
     const uint8_t *gflag;   // [ceil(nloc / 64)] 1 if entries [64 g, 64 g + 64) hold an interface copy
@@ -98,9 +100,11 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Fixed-order block sum, adds done by warp 0 only; result valid in thread 0.
+// Fixed-order block sum over NT threads, adds done by warp 0 only; result
+// valid in thread 0.
+template <int NT = kBlock>
 __device__ __forceinline__ double block_sum(double v) {
-    __shared__ double red[kBlock];
+    __shared__ double red[NT];
     __syncthreads();  // protects red[] against a previous call
     red[threadIdx.x] = v;
     __syncthreads();
@@ -108,7 +112,7 @@ __device__ __forceinline__ double block_sum(double v) {
     if (threadIdx.x < 32) {
         t = red[threadIdx.x];
 #pragma unroll
-        for (int i = 1; i < kBlock / 32; ++i) t += red[threadIdx.x + 32 * i];
+        for (int i = 1; i < NT / 32; ++i) t += red[threadIdx.x + 32 * i];
         t = warp_sum(t);
     }
     return t;
@@ -128,11 +132,12 @@ __device__ __forceinline__ bool publish_and_check_last(double *partials, double 
     return last != 0;
 }
 
+template <int NT = kBlock>
 __device__ __forceinline__ double sum_partials(const double *partials, int G) {
     __threadfence();
     double v = 0.0;
-    for (int i = threadIdx.x; i < G; i += kBlock) v += __ldcg(partials + i);
-    return block_sum(v);
+    for (int i = threadIdx.x; i < G; i += NT) v += __ldcg(partials + i);
+    return block_sum<NT>(v);
 }
 
 __device__ __forceinline__ void stop_loop(Scal *s, cudaGraphConditionalHandle h, int use_cond) {
@@ -160,20 +165,20 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Shared-memory stage of one work item: values, columns and the row/copy
-// pointers it needs, each copied from a 16-byte aligned start at or below its
-// first element.
+// Shared-memory stage of one warp's work item: values, columns and the
+// row/copy pointers it needs, each copied from a 16-byte aligned start at or
+// below its first element.
 template <typename T>
-struct TileStage {
-    T val[kTileNnz + 8];
-    int32_t col[kTileNnz + 8];
-    int32_t rp[kTileRows + 8];  // row pointers (kind 0) or copy-row pointers (kind 1)
-    int32_t ip[kTileRows + 8];  // copy ranges of the nodes (kind 1)
+struct WarpStage {
+    T val[kWarpNnz + 8];
+    int32_t col[kWarpNnz + 8];
+    int32_t rp[kWarpCopies + 8];  // row pointers (kind 0) or copy-row pointers (kind 1)
+    int32_t ip[kWarpRows + 8];    // copy ranges of the nodes (kind 1)
 };
 
-__device__ __forceinline__ void stage_ints(int32_t *dst, const int32_t *src, int lo, int hi, uint64_t pol) {
+__device__ __forceinline__ void stage_ints(int32_t *dst, const int32_t *src, int lo, int hi, uint64_t pol, int lane) {
     const int a = lo & ~3, b = (hi + 3) & ~3;
-    for (int i = threadIdx.x; i < (b - a) >> 2; i += kBlock) cp_async16(dst + 4 * i, src + a + 4 * i, pol);
+    for (int i = lane; i < (b - a) >> 2; i += 32) cp_async16(dst + 4 * i, src + a + 4 * i, pol);
 }
 
 template <typename T>
@@ -189,23 +194,24 @@ __device__ __forceinline__ const double *copy_vals<double>(const DevOp &A) { ret
 template <>
 __device__ __forceinline__ const float *copy_vals<float>(const DevOp &A) { return A.ival32; }
 
-// Issue the copies of work item W into `st` (nothing for the long kinds,
-// which read global memory directly).  Each array is read at most 12 bytes
-// past its last element; the arena pads every array for that.
+// The warp issues the copies of work item W into `st` (nothing for the long
+// kinds, which read global memory directly).  Each array is read at most 12
+// bytes past its last element; the arena pads every array for that.
 template <typename T>
-__device__ __forceinline__ void issue_item(const DevOp &A, const WorkItem &W, TileStage<T> &st, uint64_t pol) {
+__device__ __forceinline__ void issue_item(const DevOp &A, const WorkItem &W, WarpStage<T> &st, uint64_t pol,
+                                           int lane) {
     if (W.kind >= kItemLongRow) return;
     const T *vsrc = W.kind == kItemRows ? row_vals<T>(A) : copy_vals<T>(A);
     const int32_t *csrc = W.kind == kItemRows ? A.col : A.icol;
     constexpr int V = 16 / sizeof(T);  // values per 16 bytes
     const int a0 = W.e0 & ~(V - 1), a1 = (W.e1 + V - 1) & ~(V - 1);
-    for (int i = threadIdx.x; i < (a1 - a0) / V; i += kBlock) cp_async16(st.val + V * i, vsrc + a0 + V * i, pol);
-    stage_ints(st.col, csrc, W.e0, W.e1, pol);
+    for (int i = lane; i < (a1 - a0) / V; i += 32) cp_async16(st.val + V * i, vsrc + a0 + V * i, pol);
+    stage_ints(st.col, csrc, W.e0, W.e1, pol, lane);
     if (W.kind == kItemRows) {
-        stage_ints(st.rp, A.rowptr, W.a, W.b + 1, pol);
+        stage_ints(st.rp, A.rowptr, W.a, W.b + 1, pol, lane);
     } else {
-        stage_ints(st.rp, A.irp, W.c0, W.c1 + 1, pol);
-        stage_ints(st.ip, A.iptr, W.a, W.b + 1, pol);
+        stage_ints(st.rp, A.irp, W.c0, W.c1 + 1, pol, lane);
+        stage_ints(st.ip, A.iptr, W.a, W.b + 1, pol, lane);
     }
 }
 
@@ -257,46 +263,47 @@ __device__ __forceinline__ T row_dot(const T *sv, const int32_t *sc, int vbase, 
 
 // ---------------------------------------------------------------------------
 // Sub-structured SpMV (Section 3.4.1) with the interface assembly of
-// Algorithms 4 and 5 fused in.  Persistent blocks each walk a fixed,
-// contiguous slice of a precomputed work list (the same rows in the same
-// order on every run, so the (x, y)_w partials are deterministic).  Interior
-// items stream <= 256 rows / <= 2048 nonzeros; interface items stream the
-// copy rows of <= 256 interface nodes, stored contiguously in (node, copy)
-// order: one thread per node forms each copy's local row product, sums them in
-// ascending subdomain order and writes the sum to every copy.  Values,
-// columns and pointers of the next item are staged in shared memory by
-// cp.async (L2 evict-first) while the current item computes.
+// Algorithms 4 and 5 fused in.  Every warp walks its own fixed, contiguous
+// slice of a precomputed work list (the same rows in the same order on every
+// run, so the (x, y)_w partials are deterministic), with no block-wide
+// barrier on the way: interior items are <= 32 consecutive rows
+// (<= 256 nonzeros), one row per lane; interface items are <= 32 interface
+// nodes whose copy rows are stored contiguously in (node, copy) order, one
+// node per lane: each copy's local row product, summed in ascending
+// subdomain order, written to every copy.  A warp stages the values, columns
+// and pointers of its next item in its own shared-memory buffer by cp.async
+// (L2 evict-first) while it computes the current one.
 // ---------------------------------------------------------------------------
 template <int EPI, typename T>
-__global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSM)
+__global__ void __launch_bounds__(kSpmvThreads, kSpmvBlocksPerSM)
     k_spmv_asm(DevOp A, const T *__restrict__ x, T *__restrict__ y, double *partials, Scal *s, double *out,
                cudaGraphConditionalHandle h, int use_cond) {
     if (EPI == kEpiAlpha && s->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileStage<T> *stage = reinterpret_cast<TileStage<T> *>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpStage<T> *stage = reinterpret_cast<WarpStage<T> *>(smem_raw) + 2 * warp;
     const uint64_t pol = policy_evict_first();
-    const int2 range = A.block_range[blockIdx.x];
+    const int2 range = A.warp_range[blockIdx.x * kSpmvWarps + warp];
     const T *__restrict__ val = row_vals<T>(A);
     const T *__restrict__ ival = copy_vals<T>(A);
     constexpr int V = 16 / sizeof(T);
     T dot = T(0);
 
     int buf = 0;
-    if (range.x < range.y) issue_item(A, A.items[range.x], stage[0], pol);
+    if (range.x < range.y) issue_item(A, A.items[range.x], stage[0], pol, lane);
     cp_async_commit();
     for (int it = range.x; it < range.y; ++it) {
-        if (it + 1 < range.y) issue_item(A, A.items[it + 1], stage[buf ^ 1], pol);
+        if (it + 1 < range.y) issue_item(A, A.items[it + 1], stage[buf ^ 1], pol, lane);
         cp_async_commit();
         const WorkItem W = A.items[it];
         if (W.kind == kItemRows || W.kind == kItemIface) {
             cp_async_wait<1>();
-            __syncthreads();
-            const TileStage<T> &st = stage[buf];
+            __syncwarp();
+            const WarpStage<T> &st = stage[buf];
             const int vbase = W.e0 & ~(V - 1), cbase = W.e0 & ~3;
             if (W.kind == kItemRows) {
-                // one row per thread (an item has at most kTileRows == kBlock rows)
                 const int rbase = W.a & ~3;
-                const int r = W.a + threadIdx.x;
+                const int r = W.a + lane;
                 const bool valid = r < W.b;
                 const int k0 = valid ? st.rp[r - rbase] : 0;
                 const int len = valid ? st.rp[r + 1 - rbase] - k0 : 0;
@@ -307,7 +314,8 @@ __global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSM)
                 }
             } else {
                 const int gbase = W.a & ~3, pbase = W.c0 & ~3;
-                for (int g = W.a + threadIdx.x; g < W.b; g += kBlock) {
+                const int g = W.a + lane;
+                if (g < W.b) {
                     const int c0 = st.ip[g - gbase], c1 = st.ip[g + 1 - gbase];
                     T S = T(0);
                     for (int c = c0; c < c1; ++c) {
@@ -325,26 +333,26 @@ __global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSM)
                     }
                 }
             }
+            __syncwarp();  // stage[buf] is refilled by the next iteration's prefetch
         } else if (W.kind == kItemLongRow) {
-            // one row longer than a stage: block-strided partial sums, fixed tree
+            // one row longer than a stage: lane-strided partial sums, fixed warp tree
             T acc = T(0);
-            for (int k = W.e0 + threadIdx.x; k < W.e1; k += kBlock) acc = fma(val[k], __ldg(x + A.col[k]), acc);
-            const T racc = T(block_sum(double(acc)));
-            if (threadIdx.x == 0) {
+            for (int k = W.e0 + lane; k < W.e1; k += 32) acc = fma(val[k], __ldg(x + A.col[k]), acc);
+            const T racc = T(warp_sum(double(acc)));
+            if (lane == 0) {
                 y[W.a] = racc;
                 dot = fma(__ldg(x + W.a), racc, dot);
             }
         } else {
             // one interface node whose copy rows exceed a stage: each copy row
-            // reduced by the block (fixed tree), copies summed in ascending s
+            // reduced by the warp (fixed tree), copies summed in ascending s
             T S = T(0);
             for (int c = W.c0; c < W.c1; ++c) {
                 T acc = T(0);
-                for (int k = A.irp[c] + threadIdx.x; k < A.irp[c + 1]; k += kBlock)
-                    acc = fma(ival[k], __ldg(x + A.icol[k]), acc);
-                S += T(block_sum(double(acc)));  // valid in thread 0
+                for (int k = A.irp[c] + lane; k < A.irp[c + 1]; k += 32) acc = fma(ival[k], __ldg(x + A.icol[k]), acc);
+                S += T(warp_sum(double(acc)));  // valid in lane 0
             }
-            if (threadIdx.x == 0) {
+            if (lane == 0) {
                 const T w = T(A.wtab[W.c1 - W.c0]);
                 for (int c = W.c0; c < W.c1; ++c) {
                     const int row = A.icopy[c];
@@ -353,13 +361,22 @@ __global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSM)
                 }
             }
         }
-        __syncthreads();  // stage[buf] is refilled by the next iteration's prefetch
         buf ^= 1;
     }
     cp_async_wait<0>();
-    const double bs = block_sum(double(dot));
+    // fixed-order reduction: lanes of each warp, then the block's warps in order
+    __shared__ double wsum[kSpmvWarps];
+    const double wv = warp_sum(double(dot));
+    if (lane == 0) wsum[warp] = wv;
+    __syncthreads();
+    double bs = 0.0;
+    if (threadIdx.x == 0) {
+        bs = wsum[0];
+#pragma unroll
+        for (int w = 1; w < kSpmvWarps; ++w) bs += wsum[w];
+    }
     if (publish_and_check_last(partials, bs, &s->ticket[kTicketSpmv])) {
-        const double tot = sum_partials(partials, gridDim.x);
+        const double tot = sum_partials<kSpmvThreads>(partials, gridDim.x);
         if (threadIdx.x == 0) {
             s->ticket[kTicketSpmv] = 0;
             if (EPI == kEpiStore) {
@@ -379,7 +396,7 @@ __global__ void __launch_bounds__(kBlock, kSpmvBlocksPerSM)
 
 template <typename T>
 constexpr size_t spmv_smem() {
-    return 2 * sizeof(TileStage<T>);
+    return 2 * kSpmvWarps * sizeof(WarpStage<T>);
 }
 
 __device__ __forceinline__ double wsq(double r, unsigned int m, const double *__restrict__ wtab, double acc) {
