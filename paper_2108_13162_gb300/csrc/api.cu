@@ -80,16 +80,21 @@ namespace {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// SpMV work list (see WorkItem in kernels.cuh).  Interior items: greedy runs
-// of consecutive interior rows of one subdomain, at most kWarpRows rows and
-// kWarpNnz nonzeros; a longer row is an item of its own.  Interface items:
-// greedy runs of consecutive interface nodes with at most kWarpRows nodes,
-// kWarpCopies copies and kWarpNnz copy-row nonzeros.  Interface items are
-// spread evenly among the interior ones, and the list is cut into one
-// contiguous slice of about equal cost per warp.
+// SpMV work list (see WorkItem in kernels.cuh) and the sliced-ELL copy of
+// the local matrices it streams.  Interior slices: up to 32 consecutive
+// interior rows of one subdomain, width = their longest row; a row longer
+// than kSliceMaxWidth is an item of its own (read from the CSR arrays).
+// Interface slices: whole interface nodes, up to 32 copy rows in (node,
+// copy) order; a node with more than 32 copies or a copy row longer than
+// kSliceMaxWidth is an item of its own.  Padding entries have value 0 and a
+// column inside the same subdomain.  Interface items are spread evenly among
+// the interior ones, and the list is cut into one contiguous slice of about
+// equal cost per warp.
 struct WorkPlan {
-    std::vector<int32_t> irp, icol;
+    std::vector<int32_t> irp, icol;  // interface copy rows in CSR form (long nodes)
     std::vector<double> ival;
+    std::vector<double> sval;        // sliced-ELL values
+    std::vector<int32_t> scol, sseg;
     std::vector<WorkItem> items;
     std::vector<int2> warp_range;
     int grid = 0;
@@ -97,10 +102,11 @@ struct WorkPlan {
 
 WorkPlan make_plan(const HostMaps &M, int grid_cap) {
     WorkPlan W;
-    // interface copy rows in (node, copy) order, columns as concatenated index
     std::vector<int32_t> sub_of(static_cast<size_t>(M.nloc));
     for (int32_t s = 0; s < M.P; ++s)
         for (int64_t r = M.off[s]; r < M.off[s + 1]; ++r) sub_of[r] = s;
+    auto rlen = [&](int32_t r) { return M.lrowptr[r + 1] - M.lrowptr[r]; };
+    // interface copy rows in (node, copy) order, columns as concatenated index
     W.irp.assign(static_cast<size_t>(M.ncopies) + 1, 0);
     for (int64_t c = 0; c < M.ncopies; ++c) {
         const int32_t row = M.icopy[c];
@@ -111,38 +117,77 @@ WorkPlan make_plan(const HostMaps &M, int grid_cap) {
         }
         W.irp[c + 1] = static_cast<int32_t>(W.icol.size());
     }
+    W.sseg.assign(static_cast<size_t>(M.ncopies), 0);
     std::vector<WorkItem> rows, iface;
+    // interior slices
     for (int32_t s = 0; s < M.P; ++s) {
         int32_t r = M.off[s];
         const int32_t rend = M.off[s] + M.nint[s];
+        const int32_t o = M.off[s];
         while (r < rend) {
-            int32_t r1 = r;
-            const int32_t e0 = M.lrowptr[r];
-            while (r1 < rend && r1 - r < kWarpRows && M.lrowptr[r1 + 1] - e0 <= kWarpNnz) ++r1;
-            if (r1 == r) {
-                rows.push_back({kItemLongRow, r, r + 1, e0, M.lrowptr[r + 1], 0, 0, 0});
-                r = r + 1;
-            } else {
-                rows.push_back({kItemRows, r, r1, e0, M.lrowptr[r1], 0, 0, 0});
-                r = r1;
+            if (rlen(r) > kSliceMaxWidth) {
+                rows.push_back({kItemLongRow, r, r + 1, M.lrowptr[r], M.lrowptr[r + 1], 0, 0, 0});
+                ++r;
+                continue;
             }
+            int32_t r1 = r, w = 0;
+            while (r1 < rend && r1 - r < kSliceRows && rlen(r1) <= kSliceMaxWidth) w = std::max(w, rlen(r1++));
+            const int32_t off = static_cast<int32_t>(W.sval.size());
+            for (int32_t k = 0; k < w; ++k)
+                for (int32_t lane = 0; lane < kSliceRows; ++lane) {
+                    const int32_t row = r + lane;
+                    if (row < r1 && k < rlen(row)) {
+                        const int32_t e = M.lrowptr[row] + k;
+                        W.sval.push_back(M.lval[e]);
+                        W.scol.push_back(o + M.lcol[e]);
+                    } else {
+                        W.sval.push_back(0.0);
+                        W.scol.push_back(row < r1 ? row : r);
+                    }
+                }
+            rows.push_back({kItemSlice, r, r1, off, w, 0, 0, 0});
+            r = r1;
         }
     }
+    // interface slices (whole nodes)
     int32_t g = 0;
     while (g < M.ngamma) {
-        int32_t g1 = g;
-        const int32_t c0 = M.iptr[g];
-        const int32_t e0 = W.irp[c0];
-        while (g1 < M.ngamma && g1 - g < kWarpRows && M.iptr[g1 + 1] - c0 <= kWarpCopies &&
-               W.irp[M.iptr[g1 + 1]] - e0 <= kWarpNnz)
-            ++g1;
-        if (g1 == g) {
-            iface.push_back({kItemLongIface, g, g + 1, e0, W.irp[M.iptr[g + 1]], c0, M.iptr[g + 1], 0});
-            g = g + 1;
-        } else {
-            iface.push_back({kItemIface, g, g1, e0, W.irp[M.iptr[g1]], c0, M.iptr[g1], 0});
-            g = g1;
+        auto long_node = [&](int32_t gg) {
+            if (M.iptr[gg + 1] - M.iptr[gg] > kSliceRows) return true;
+            for (int32_t c = M.iptr[gg]; c < M.iptr[gg + 1]; ++c)
+                if (W.irp[c + 1] - W.irp[c] > kSliceMaxWidth) return true;
+            return false;
+        };
+        if (long_node(g)) {
+            const int32_t c0 = M.iptr[g], c1 = M.iptr[g + 1];
+            iface.push_back({kItemLongIface, g, g + 1, W.irp[c0], W.irp[c1], c0, c1, 0});
+            ++g;
+            continue;
         }
+        const int32_t c0 = M.iptr[g];
+        int32_t g1 = g, w = 0;
+        while (g1 < M.ngamma && !long_node(g1) && M.iptr[g1 + 1] - c0 <= kSliceRows) {
+            for (int32_t c = M.iptr[g1]; c < M.iptr[g1 + 1]; ++c) w = std::max(w, W.irp[c + 1] - W.irp[c]);
+            ++g1;
+        }
+        const int32_t c1 = M.iptr[g1];
+        for (int32_t gg = g; gg < g1; ++gg)
+            for (int32_t c = M.iptr[gg]; c < M.iptr[gg + 1]; ++c)
+                W.sseg[c] = (M.iptr[gg] - c0) | ((M.iptr[gg + 1] - M.iptr[gg]) << 8);
+        const int32_t off = static_cast<int32_t>(W.sval.size());
+        for (int32_t k = 0; k < w; ++k)
+            for (int32_t lane = 0; lane < kSliceRows; ++lane) {
+                const int32_t c = c0 + lane;
+                if (c < c1 && k < W.irp[c + 1] - W.irp[c]) {
+                    W.sval.push_back(W.ival[W.irp[c] + k]);
+                    W.scol.push_back(W.icol[W.irp[c] + k]);
+                } else {
+                    W.sval.push_back(0.0);
+                    W.scol.push_back(M.icopy[c < c1 ? c : c0]);
+                }
+            }
+        iface.push_back({kItemIfaceSlice, c0, c1, off, w, 0, 0, 0});
+        g = g1;
     }
     // interleave: interface item j goes after interior item floor((j+1) * nrows / (niface+1))
     const size_t nr = rows.size(), ni = iface.size();
@@ -152,8 +197,7 @@ WorkPlan make_plan(const HostMaps &M, int grid_cap) {
         if (i < nr) W.items.push_back(rows[i]);
     }
     while (j < ni) W.items.push_back(iface[j++]);
-    // contiguous slices of about equal cost (nonzeros + 4 per row or copy),
-    // one per warp of the launch
+    // contiguous slices of about equal cost, one per warp of the launch
     const int n = static_cast<int>(W.items.size());
     const int blocks = std::max(1, std::min((n + kSpmvWarps - 1) / kSpmvWarps, grid_cap));
     const int G = blocks * kSpmvWarps;
@@ -161,8 +205,10 @@ WorkPlan make_plan(const HostMaps &M, int grid_cap) {
     std::vector<double> prefix(static_cast<size_t>(n) + 1, 0.0);
     for (int i = 0; i < n; ++i) {
         const WorkItem &w = W.items[i];
-        const double rowsn = (w.kind == kItemIface || w.kind == kItemLongIface) ? (w.c1 - w.c0) : (w.b - w.a);
-        prefix[i + 1] = prefix[i] + (w.e1 - w.e0) + 4.0 * rowsn;
+        double cost = 64.0;
+        if (w.kind == kItemSlice || w.kind == kItemIfaceSlice) cost += 32.0 * w.e1;
+        else cost += 4.0 * (w.e1 - w.e0);
+        prefix[i + 1] = prefix[i] + cost;
     }
     W.warp_range.resize(G);
     int lo = 0;
@@ -179,7 +225,7 @@ WorkPlan make_plan(const HostMaps &M, int grid_cap) {
 
 int launch_body(ssg_system *S, cudaStream_t st, int use_cond) {
     const int64_t N = S->maps.nloc;
-    k_spmv_asm<kEpiAlpha, double><<<S->grid_spmv, kSpmvThreads, spmv_smem<double>(), st>>>(
+    k_spmv_asm<kEpiAlpha, double><<<S->grid_spmv, kSpmvThreads, 0, st>>>(
         S->op, S->d_p, S->d_q, S->d_partials, S->d_scal, nullptr, S->cond, use_cond);
     k_update_r<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_r, S->d_q, S->op.mult, S->op.wtab, S->op.gflag,
                                                S->d_partials, S->d_scal);
@@ -268,7 +314,7 @@ int launch_inner_init(ssg_system *S, cudaStream_t st, int use_cond) {
 
 int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond) {
     const int64_t N = S->maps.nloc;
-    k_spmv_asm<kEpiAlpha, float><<<S->grid_spmv, kSpmvThreads, spmv_smem<float>(), st>>>(
+    k_spmv_asm<kEpiAlpha, float><<<S->grid_spmv, kSpmvThreads, 0, st>>>(
         S->op, S->d_p32, S->d_q32, S->d_partials, S->d_scal_in, nullptr, S->cond_in, use_cond);
     k_update_r32<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_r32, S->d_q32, S->op.mult, S->op.wtab, S->op.gflag,
                                                  S->d_partials, S->d_scal_in, S->d_scal);
@@ -281,7 +327,7 @@ int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond) {
 int launch_outer_tail(ssg_system *S, cudaStream_t st, int use_cond) {
     const int64_t N = S->maps.nloc;
     k_ir_correct<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_xl, S->d_d32);
-    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, spmv_smem<double>(), st>>>(
+    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, 0, st>>>(
         S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
     k_ir_residual<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_bl, S->d_q, S->d_r, S->op.mult, S->op.wtab, S->d_partials,
                                                   S->d_scal, S->d_scal_in, S->cond_out, use_cond);
@@ -393,14 +439,6 @@ int upload(ssg_system *S) {
     S->grid_spmv = plan.grid;
     S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N / 2 + kBlock - 1) / kBlock), C->num_sms * kVecBlocksPerSM));
     S->n_partials = 2 * std::max(S->grid_spmv, S->grid_vec);
-    SSG_CUDA_TRY(cudaFuncSetAttribute(k_spmv_asm<kEpiStore, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(spmv_smem<double>())));
-    SSG_CUDA_TRY(cudaFuncSetAttribute(k_spmv_asm<kEpiAlpha, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(spmv_smem<double>())));
-    SSG_CUDA_TRY(cudaFuncSetAttribute(k_spmv_asm<kEpiStore, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(spmv_smem<float>())));
-    SSG_CUDA_TRY(cudaFuncSetAttribute(k_spmv_asm<kEpiAlpha, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(spmv_smem<float>())));
 
     struct Piece {
         const void *src;
@@ -423,6 +461,15 @@ int upload(ssg_system *S) {
     size_t i_irp = add(plan.irp.data(), sizeof(int32_t) * plan.irp.size());
     size_t i_icol = add(plan.icol.data(), sizeof(int32_t) * plan.icol.size());
     size_t i_ival = add(plan.ival.data(), sizeof(double) * plan.ival.size());
+    if (plan.sval.size() > static_cast<size_t>(INT32_MAX)) {
+        set_error("sliced matrix larger than 2^31 entries");
+        return SSG_E_INVALID;
+    }
+    std::vector<float> sval32(plan.sval.begin(), plan.sval.end());
+    size_t i_sval = add(plan.sval.data(), sizeof(double) * plan.sval.size());
+    size_t i_sval32 = add(sval32.data(), sizeof(float) * sval32.size());
+    size_t i_scol = add(plan.scol.data(), sizeof(int32_t) * plan.scol.size());
+    size_t i_sseg = add(plan.sseg.data(), sizeof(int32_t) * plan.sseg.size());
     size_t i_items = add(plan.items.data(), sizeof(WorkItem) * plan.items.size());
     size_t i_brange = add(plan.warp_range.data(), sizeof(int2) * plan.warp_range.size());
     size_t i_iptr = add(M.iptr.data(), sizeof(int32_t) * (M.ngamma + 1));
@@ -476,6 +523,10 @@ int upload(ssg_system *S) {
     S->op.irp = static_cast<const int32_t *>(at(i_irp));
     S->op.icol = static_cast<const int32_t *>(at(i_icol));
     S->op.ival = static_cast<const double *>(at(i_ival));
+    S->op.sval = static_cast<const double *>(at(i_sval));
+    S->op.sval32 = static_cast<const float *>(at(i_sval32));
+    S->op.scol = static_cast<const int32_t *>(at(i_scol));
+    S->op.sseg = static_cast<const int32_t *>(at(i_sseg));
     S->op.items = static_cast<const WorkItem *>(at(i_items));
     S->op.warp_range = static_cast<const int2 *>(at(i_brange));
     S->op.iptr = static_cast<const int32_t *>(at(i_iptr));
@@ -589,7 +640,7 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     ++launches;
     if (guess) {
         k_scatter<<<grid_for(N, C->num_sms), kBlock, 0, s>>>(N, S->d_l2g, x_glob, S->d_xl);
-        k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, spmv_smem<double>(), s>>>(
+        k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, 0, s>>>(
             S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
         launches += 2;
     } else {
@@ -613,7 +664,7 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     }
     k_gather<<<grid_for(S->maps.n, C->num_sms), kBlock, 0, s>>>(S->maps.n, S->d_own, S->d_xl, x_glob);
     // true residual ||b - S x||_w in FP64
-    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, spmv_smem<double>(), s>>>(
+    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, 0, s>>>(
         S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
     k_wdot<true><<<S->grid_vec, kBlock, 0, s>>>(N, S->d_bl, S->d_q, S->op.mult, S->op.wtab, S->d_partials,
                                                 S->d_scal_op, &S->d_scal->aux);
@@ -826,7 +877,7 @@ int ssg_spmv_assembled(ssg_system *S, const double *x_loc, double *y_loc, double
         set_error("x_loc and y_loc must be distinct non-null device vectors");
         return SSG_E_INVALID;
     }
-    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, spmv_smem<double>(), S->ctx->stream>>>(
+    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, 0, S->ctx->stream>>>(
         S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
@@ -839,7 +890,7 @@ int ssg_spmv_assembled_f32(ssg_system *S, const float *x_loc, float *y_loc, doub
         set_error("x_loc and y_loc must be distinct non-null device vectors");
         return SSG_E_INVALID;
     }
-    k_spmv_asm<kEpiStore, float><<<S->grid_spmv, kSpmvThreads, spmv_smem<float>(), S->ctx->stream>>>(
+    k_spmv_asm<kEpiStore, float><<<S->grid_spmv, kSpmvThreads, 0, S->ctx->stream>>>(
         S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;

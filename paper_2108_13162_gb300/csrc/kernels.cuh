@@ -24,12 +24,11 @@
 namespace ssg {
 
 constexpr int kBlock = 256;       // threads per block, every kernel
-constexpr int kSpmvWarps = 4;               // warps per SpMV block
+constexpr int kSpmvWarps = 8;               // warps per SpMV block
 constexpr int kSpmvThreads = 32 * kSpmvWarps;
-constexpr int kWarpRows = 32;               // rows (or interface nodes) per warp item: one per lane
-constexpr int kWarpNnz = 256;               // nonzeros staged per warp item
-constexpr int kWarpCopies = 64;             // interface copies staged per warp item
-constexpr int kSpmvBlocksPerSM = 6;
+constexpr int kSliceRows = 32;              // rows (or interface copy rows) per slice: one per lane
+constexpr int kSliceMaxWidth = 64;          // longer rows are handled one per warp from the CSR arrays
+constexpr int kSpmvBlocksPerSM = 4;
 constexpr int kVecBlocksPerSM = 4;
 constexpr int kHostChunk = 32;    // iterations per host-loop chunk (SSG_DRIVER_HOST)
 
@@ -63,15 +62,18 @@ struct Scal {
 enum { kTicketSpmv = 0, kTicketR = 1, kTicketXP = 2, kTicketMisc = 3 };
 
 // One unit of SpMV work (precomputed on the host, 32 bytes).
-//   kind 0: interior rows [a, b) of the local CSR, nonzeros [e0, e1)
-//   kind 1: interface nodes [a, b), copies [c0, c1), copy-row nonzeros [e0, e1)
-//   kind 2: one interior row a longer than a tile (read from global memory)
-//   kind 3: one interface node a whose copy rows exceed a tile
+//   kind 0: slice of interior rows [a, b) (b - a <= 32), sliced-ELL data at
+//           e0, width e1 (entries [e0 + k*32, e0 + k*32 + 32) are the k-th
+//           nonzeros of the slice's rows, padded with zero values)
+//   kind 1: slice of interface copy rows [a, b) in (node, copy) order, whole
+//           nodes only, sliced-ELL data at e0, width e1
+//   kind 2: one interior row a longer than kSliceMaxWidth, CSR nonzeros [e0, e1)
+//   kind 3: one interface node a, copies [c0, c1), whose copy rows are too long
 struct WorkItem {
     int32_t kind, a, b, e0, e1, c0, c1, pad;
 };
 
-enum { kItemRows = 0, kItemIface = 1, kItemLongRow = 2, kItemLongIface = 3 };
+enum { kItemSlice = 0, kItemIfaceSlice = 1, kItemLongRow = 2, kItemLongIface = 3 };
 
 // Matrix-side arrays on the device (one arena, see api.cu).
 struct DevOp {
@@ -85,6 +87,10 @@ struct DevOp {
     const float *ival32;    // copy-row values rounded to FP32
     const int32_t *iptr;    // [ngamma+1] copies of each interface node
     const int32_t *icopy;   // [ncopies] concatenated local index of each copy
+    const double *sval;     // sliced-ELL values: slice k-th entries of its 32 rows contiguous
+    const float *sval32;    // the same rounded to FP32
+    const int32_t *scol;    // sliced-ELL columns (concatenated local index)
+    const int32_t *sseg;    // interface slices, per copy: (lane of the node's first copy) | (m << 8)
     const WorkItem *items;  // SpMV work list
     const int2 *warp_range;  // [grid * kSpmvWarps] contiguous item range of each warp
     const uint8_t *mult;    // [nloc] multiplicity of each local entry's node
@@ -145,42 +151,12 @@ __device__ __forceinline__ void stop_loop(Scal *s, cudaGraphConditionalHandle h,
     if (use_cond) cudaGraphSetConditional(h, 0);
 }
 
-// ---- asynchronous global -> shared copies (16 bytes, L2 evict-first) -------
-__device__ __forceinline__ uint64_t policy_evict_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, uint64_t policy) {
-    const unsigned int s = static_cast<unsigned int>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "l"(policy)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Shared-memory stage of one warp's work item: values, columns and the
-// row/copy pointers it needs, each copied from a 16-byte aligned start at or
-// below its first element.
 template <typename T>
-struct WarpStage {
-    T val[kWarpNnz + 8];
-    int32_t col[kWarpNnz + 8];
-    int32_t rp[kWarpCopies + 8];  // row pointers (kind 0) or copy-row pointers (kind 1)
-    int32_t ip[kWarpRows + 8];    // copy ranges of the nodes (kind 1)
-};
-
-__device__ __forceinline__ void stage_ints(int32_t *dst, const int32_t *src, int lo, int hi, uint64_t pol, int lane) {
-    const int a = lo & ~3, b = (hi + 3) & ~3;
-    for (int i = lane; i < (b - a) >> 2; i += 32) cp_async16(dst + 4 * i, src + a + 4 * i, pol);
-}
-
+__device__ __forceinline__ const T *slice_vals(const DevOp &A);
+template <>
+__device__ __forceinline__ const double *slice_vals<double>(const DevOp &A) { return A.sval; }
+template <>
+__device__ __forceinline__ const float *slice_vals<float>(const DevOp &A) { return A.sval32; }
 template <typename T>
 __device__ __forceinline__ const T *row_vals(const DevOp &A);
 template <>
@@ -194,148 +170,103 @@ __device__ __forceinline__ const double *copy_vals<double>(const DevOp &A) { ret
 template <>
 __device__ __forceinline__ const float *copy_vals<float>(const DevOp &A) { return A.ival32; }
 
-// The warp issues the copies of work item W into `st` (nothing for the long
-// kinds, which read global memory directly).  Each array is read at most 12
-// bytes past its last element; the arena pads every array for that.
-template <typename T>
-__device__ __forceinline__ void issue_item(const DevOp &A, const WorkItem &W, WarpStage<T> &st, uint64_t pol,
-                                           int lane) {
-    if (W.kind >= kItemLongRow) return;
-    const T *vsrc = W.kind == kItemRows ? row_vals<T>(A) : copy_vals<T>(A);
-    const int32_t *csrc = W.kind == kItemRows ? A.col : A.icol;
-    constexpr int V = 16 / sizeof(T);  // values per 16 bytes
-    const int a0 = W.e0 & ~(V - 1), a1 = (W.e1 + V - 1) & ~(V - 1);
-    for (int i = lane; i < (a1 - a0) / V; i += 32) cp_async16(st.val + V * i, vsrc + a0 + V * i, pol);
-    stage_ints(st.col, csrc, W.e0, W.e1, pol, lane);
-    if (W.kind == kItemRows) {
-        stage_ints(st.rp, A.rowptr, W.a, W.b + 1, pol, lane);
-    } else {
-        stage_ints(st.rp, A.irp, W.c0, W.c1 + 1, pol, lane);
-        stage_ints(st.ip, A.iptr, W.a, W.b + 1, pol, lane);
-    }
-}
-
+// N consecutive entries (k0 .. k0+N-1) of a lane's sliced-ELL row: all
+// loads first (the value and column loads of a warp are contiguous and
+// coalesced, streamed with L2 evict-first), then the FMA chain in order.
 template <int N, typename T>
-__device__ __forceinline__ T fma_chain(const T *vv, const T *xv) {
-    T acc = T(0);
+__device__ __forceinline__ T slice_chunk(const T *__restrict__ sv, const int32_t *__restrict__ sc,
+                                         const T *__restrict__ x, int base, int k0, T acc) {
+    T vv[N], xv[N];
+    int cc[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        vv[j] = __ldcs(sv + base + (k0 + j) * kSliceRows);
+        cc[j] = __ldcs(sc + base + (k0 + j) * kSliceRows);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) xv[j] = __ldg(x + cc[j]);
 #pragma unroll
     for (int j = 0; j < N; ++j) acc = fma(vv[j], xv[j], acc);
     return acc;
 }
 
-// Row product over nonzeros [k0, k1) (values/columns read through sv/sc at
-// index k - base), summed in CSR order.  Called by all 32 lanes of a warp
-// (len = 0 for lanes without a row).  On this part a predicated-off FP64
-// instruction still takes its issue slot, so the FMA chain runs exactly the
-// warp's longest row length (a warp-uniform switch), shorter rows padded with
-// 0 * 0 terms, which leave the sum unchanged.
+// Row product of lane `lane` of a slice (sliced-ELL data at `off`, width w,
+// the same for the whole warp): the row's nonzeros in CSR order, then the
+// zero-valued padding, which leaves the sum unchanged.  Every lane runs
+// exactly w FMAs: on this part a predicated-off FP64 instruction still takes
+// its issue slot, so nothing here is predicated.
 template <typename T>
-__device__ __forceinline__ T row_dot(const T *sv, const int32_t *sc, int vbase, int cbase, int k0, int len,
-                                     const T *__restrict__ x) {
-    const int wlen = __reduce_max_sync(0xffffffffu, len);
-    if (wlen > 8) {
-        T acc = T(0);
-        for (int k = k0; k < k0 + len; ++k) acc = fma(sv[k - vbase], __ldg(x + sc[k - cbase]), acc);
-        return acc;
-    }
-    T vv[8], xv[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        vv[j] = T(0);
-        xv[j] = T(0);
-        if (j < len) {
-            vv[j] = sv[k0 + j - vbase];
-            xv[j] = __ldg(x + sc[k0 + j - cbase]);
-        }
-    }
-    switch (wlen) {
-        case 0: return T(0);
-        case 1: return fma_chain<1>(vv, xv);
-        case 2: return fma_chain<2>(vv, xv);
-        case 3: return fma_chain<3>(vv, xv);
-        case 4: return fma_chain<4>(vv, xv);
-        case 5: return fma_chain<5>(vv, xv);
-        case 6: return fma_chain<6>(vv, xv);
-        case 7: return fma_chain<7>(vv, xv);
-        default: return fma_chain<8>(vv, xv);
+__device__ __forceinline__ T slice_row(const T *__restrict__ sv, const int32_t *__restrict__ sc,
+                                       const T *__restrict__ x, int off, int w, int lane) {
+    const int base = off + lane;
+    T acc = T(0);
+    int k = 0;
+    for (; k + 8 <= w; k += 8) acc = slice_chunk<8>(sv, sc, x, base, k, acc);
+    switch (w - k) {
+        case 1: return slice_chunk<1>(sv, sc, x, base, k, acc);
+        case 2: return slice_chunk<2>(sv, sc, x, base, k, acc);
+        case 3: return slice_chunk<3>(sv, sc, x, base, k, acc);
+        case 4: return slice_chunk<4>(sv, sc, x, base, k, acc);
+        case 5: return slice_chunk<5>(sv, sc, x, base, k, acc);
+        case 6: return slice_chunk<6>(sv, sc, x, base, k, acc);
+        case 7: return slice_chunk<7>(sv, sc, x, base, k, acc);
+        default: return acc;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Sub-structured SpMV (Section 3.4.1) with the interface assembly of
-// Algorithms 4 and 5 fused in.  Every warp walks its own fixed, contiguous
-// slice of a precomputed work list (the same rows in the same order on every
-// run, so the (x, y)_w partials are deterministic), with no block-wide
-// barrier on the way: interior items are <= 32 consecutive rows
-// (<= 256 nonzeros), one row per lane; interface items are <= 32 interface
-// nodes whose copy rows are stored contiguously in (node, copy) order, one
-// node per lane: each copy's local row product, summed in ascending
-// subdomain order, written to every copy.  A warp stages the values, columns
-// and pointers of its next item in its own shared-memory buffer by cp.async
-// (L2 evict-first) while it computes the current one.
+// Algorithms 4 and 5 fused in, on a sliced-ELL copy of the local matrices
+// (slices of 32 consecutive rows, k-th nonzeros of the 32 rows contiguous).
+// Every warp walks its own fixed, contiguous slice of a precomputed work
+// list (the same rows in the same order on every run, so the (x, y)_w
+// partials are deterministic), with no block-wide barrier:
+//   interior slice: one row per lane, y[r] = its row product;
+//   interface slice: one copy row per lane ((node, copy) order, whole nodes),
+//     then each node's copies are summed in ascending subdomain order with
+//     warp shuffles and every copy receives the sum;
+//   long row / long interface node: the warp strides over the CSR entries.
 // ---------------------------------------------------------------------------
 template <int EPI, typename T>
 __global__ void __launch_bounds__(kSpmvThreads, kSpmvBlocksPerSM)
     k_spmv_asm(DevOp A, const T *__restrict__ x, T *__restrict__ y, double *partials, Scal *s, double *out,
                cudaGraphConditionalHandle h, int use_cond) {
     if (EPI == kEpiAlpha && s->done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpStage<T> *stage = reinterpret_cast<WarpStage<T> *>(smem_raw) + 2 * warp;
-    const uint64_t pol = policy_evict_first();
     const int2 range = A.warp_range[blockIdx.x * kSpmvWarps + warp];
+    const T *__restrict__ sv = slice_vals<T>(A);
     const T *__restrict__ val = row_vals<T>(A);
     const T *__restrict__ ival = copy_vals<T>(A);
-    constexpr int V = 16 / sizeof(T);
     T dot = T(0);
 
-    int buf = 0;
-    if (range.x < range.y) issue_item(A, A.items[range.x], stage[0], pol, lane);
-    cp_async_commit();
     for (int it = range.x; it < range.y; ++it) {
-        if (it + 1 < range.y) issue_item(A, A.items[it + 1], stage[buf ^ 1], pol, lane);
-        cp_async_commit();
         const WorkItem W = A.items[it];
-        if (W.kind == kItemRows || W.kind == kItemIface) {
-            cp_async_wait<1>();
-            __syncwarp();
-            const WarpStage<T> &st = stage[buf];
-            const int vbase = W.e0 & ~(V - 1), cbase = W.e0 & ~3;
-            if (W.kind == kItemRows) {
-                const int rbase = W.a & ~3;
-                const int r = W.a + lane;
-                const bool valid = r < W.b;
-                const int k0 = valid ? st.rp[r - rbase] : 0;
-                const int len = valid ? st.rp[r + 1 - rbase] - k0 : 0;
-                const T acc = row_dot<T>(st.val, st.col, vbase, cbase, k0, len, x);
-                if (valid) {
-                    y[r] = acc;
-                    dot = fma(__ldg(x + r), acc, dot);
-                }
-            } else {
-                const int gbase = W.a & ~3, pbase = W.c0 & ~3;
-                const int g = W.a + lane;
-                if (g < W.b) {
-                    const int c0 = st.ip[g - gbase], c1 = st.ip[g + 1 - gbase];
-                    T S = T(0);
-                    for (int c = c0; c < c1; ++c) {
-                        T acc = T(0);
-                        const int k1 = st.rp[c + 1 - pbase];
-                        for (int k = st.rp[c - pbase]; k < k1; ++k)
-                            acc = fma(st.val[k - vbase], __ldg(x + st.col[k - cbase]), acc);
-                        S += acc;
-                    }
-                    const T w = T(__ldg(A.wtab + (c1 - c0)));
-                    for (int c = c0; c < c1; ++c) {
-                        const int row = __ldg(A.icopy + c);
-                        y[row] = S;
-                        dot = fma(w * __ldg(x + row), S, dot);
-                    }
-                }
+        if (W.kind == kItemSlice) {
+            const T acc = slice_row<T>(sv, A.scol, x, W.e0, W.e1, lane);
+            const int r = W.a + lane;
+            if (r < W.b) {
+                y[r] = acc;
+                dot = fma(__ldg(x + r), acc, dot);
             }
-            __syncwarp();  // stage[buf] is refilled by the next iteration's prefetch
+        } else if (W.kind == kItemIfaceSlice) {
+            const T acc = slice_row<T>(sv, A.scol, x, W.e0, W.e1, lane);
+            const int c = W.a + lane;
+            const bool valid = c < W.b;
+            const int seg = valid ? __ldg(A.sseg + c) : 0;
+            const int l0 = seg & 0xff, m = seg >> 8;
+            const int mmax = __reduce_max_sync(0xffffffffu, m);
+            T S = T(0);
+            for (int t = 0; t < mmax; ++t) {
+                const T v = __shfl_sync(0xffffffffu, acc, (l0 + t) & 31);
+                if (t < m) S += v;
+            }
+            if (valid) {
+                const int row = __ldg(A.icopy + c);
+                y[row] = S;
+                dot = fma(T(__ldg(A.wtab + m)) * __ldg(x + row), S, dot);
+            }
         } else if (W.kind == kItemLongRow) {
-            // one row longer than a stage: lane-strided partial sums, fixed warp tree
+            // one long row: lane-strided partial sums, fixed warp tree
             T acc = T(0);
             for (int k = W.e0 + lane; k < W.e1; k += 32) acc = fma(val[k], __ldg(x + A.col[k]), acc);
             const T racc = T(warp_sum(double(acc)));
@@ -344,8 +275,8 @@ __global__ void __launch_bounds__(kSpmvThreads, kSpmvBlocksPerSM)
                 dot = fma(__ldg(x + W.a), racc, dot);
             }
         } else {
-            // one interface node whose copy rows exceed a stage: each copy row
-            // reduced by the warp (fixed tree), copies summed in ascending s
+            // one interface node with long copy rows: each copy row reduced by
+            // the warp (fixed tree), copies summed in ascending s
             T S = T(0);
             for (int c = W.c0; c < W.c1; ++c) {
                 T acc = T(0);
@@ -361,9 +292,7 @@ __global__ void __launch_bounds__(kSpmvThreads, kSpmvBlocksPerSM)
                 }
             }
         }
-        buf ^= 1;
     }
-    cp_async_wait<0>();
     // fixed-order reduction: lanes of each warp, then the block's warps in order
     __shared__ double wsum[kSpmvWarps];
     const double wv = warp_sum(double(dot));
@@ -392,11 +321,6 @@ __global__ void __launch_bounds__(kSpmvThreads, kSpmvBlocksPerSM)
             }
         }
     }
-}
-
-template <typename T>
-constexpr size_t spmv_smem() {
-    return 2 * kSpmvWarps * sizeof(WarpStage<T>);
 }
 
 __device__ __forceinline__ double wsq(double r, unsigned int m, const double *__restrict__ wtab, double acc) {
