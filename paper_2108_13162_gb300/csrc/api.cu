@@ -306,7 +306,7 @@ int launch_mixed_init(ssg_system *S, cudaStream_t st, int use_cond) {
 
 int launch_inner_init(ssg_system *S, cudaStream_t st, int use_cond) {
     k_inner_init<<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_r, S->d_r32, S->d_p32, S->d_d32, S->op.mult,
-                                                 S->op.wtab, S->d_partials, S->d_scal_in, S->d_scal, S->cond_in,
+                                                 S->op.wtab32, S->d_partials, S->d_scal_in, S->d_scal, S->cond_in,
                                                  use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
@@ -316,7 +316,7 @@ int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond) {
     const int64_t N = S->maps.nloc;
     k_spmv_asm<kEpiAlpha, float><<<S->grid_spmv, kSpmvThreads, 0, st>>>(
         S->op, S->d_p32, S->d_q32, S->d_partials, S->d_scal_in, nullptr, S->cond_in, use_cond);
-    k_update_r32<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_r32, S->d_q32, S->op.mult, S->op.wtab, S->op.gflag,
+    k_update_r32<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_r32, S->d_q32, S->op.mult, S->op.wtab32, S->op.gflag128,
                                                  S->d_partials, S->d_scal_in, S->d_scal);
     k_update_dp32<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_d32, S->d_p32, S->d_r32, S->d_partials, S->d_scal_in,
                                                   S->cond_in, use_cond);
@@ -433,8 +433,15 @@ int upload(ssg_system *S) {
     std::vector<uint8_t> gflag(static_cast<size_t>((N + 63) / 64), 0);
     for (int64_t k = 0; k < N; ++k)
         if (mloc[k] > 1) gflag[k >> 6] = 1;
+    std::vector<uint8_t> gflag128(static_cast<size_t>((N + 127) / 128), 0);
+    for (int64_t k = 0; k < N; ++k)
+        if (mloc[k] > 1) gflag128[k >> 7] = 1;
     std::vector<double> wtab(256, 0.0);
-    for (int m = 1; m < 256; ++m) wtab[m] = 1.0 / static_cast<double>(m);
+    std::vector<float> wtab32(256, 0.f);
+    for (int m = 1; m < 256; ++m) {
+        wtab[m] = 1.0 / static_cast<double>(m);
+        wtab32[m] = static_cast<float>(wtab[m]);
+    }
 
     S->grid_spmv = plan.grid;
     S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N / 2 + kBlock - 1) / kBlock), C->num_sms * kVecBlocksPerSM));
@@ -477,6 +484,8 @@ int upload(ssg_system *S) {
     size_t i_mult = add(mloc.data(), N);
     size_t i_wtab = add(wtab.data(), sizeof(double) * 256);
     size_t i_gflag = add(gflag.data(), gflag.size());
+    size_t i_gflag128 = add(gflag128.data(), gflag128.size());
+    size_t i_wtab32 = add(wtab32.data(), sizeof(float) * 256);
     size_t i_l2g = add(M.l2g.data(), sizeof(int32_t) * N);
     size_t i_own = add(M.own.data(), sizeof(int32_t) * M.n);
     std::vector<float> val32(M.lval.begin(), M.lval.end());
@@ -534,6 +543,8 @@ int upload(ssg_system *S) {
     S->op.mult = static_cast<const uint8_t *>(at(i_mult));
     S->op.wtab = static_cast<const double *>(at(i_wtab));
     S->op.gflag = static_cast<const uint8_t *>(at(i_gflag));
+    S->op.gflag128 = static_cast<const uint8_t *>(at(i_gflag128));
+    S->op.wtab32 = static_cast<const float *>(at(i_wtab32));
     S->d_l2g = static_cast<int32_t *>(at(i_l2g));
     S->d_own = static_cast<int32_t *>(at(i_own));
     S->d_bl = static_cast<double *>(at(i_bl));

@@ -57,6 +57,8 @@ struct Scal {
     double inner_rtol;
     int32_t total;
     int32_t max_outer;
+    float alpha32;   // alpha and beta rounded to FP32 once (FP32 kernels read these:
+    float beta32;    // a double-to-float conversion per thread costs FP64 pipe time)
 };
 
 enum { kTicketSpmv = 0, kTicketR = 1, kTicketXP = 2, kTicketMisc = 3 };
@@ -95,7 +97,9 @@ struct DevOp {
     const int2 *warp_range;  // [grid * kSpmvWarps] contiguous item range of each warp
     const uint8_t *mult;    // [nloc] multiplicity of each local entry's node
     const double *wtab;     // [256] wtab[m] = 1/m
+    const float *wtab32;    // [256] 1/m rounded to FP32
     const uint8_t *gflag;   // [ceil(nloc / 64)] 1 if entries [64 g, 64 g + 64) hold an interface copy
+    const uint8_t *gflag128;  // [ceil(nloc / 128)] the same for groups of 128 entries
 };
 
 enum { kEpiStore = 0, kEpiAlpha = 1 };
@@ -120,6 +124,28 @@ __device__ __forceinline__ double block_sum(double v) {
 #pragma unroll
         for (int i = 1; i < NT / 32; ++i) t += red[threadIdx.x + 32 * i];
         t = warp_sum(t);
+    }
+    return t;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// FP32 version for the FP32 kernels (one conversion to double per block).
+__device__ __forceinline__ float block_sumf(float v) {
+    __shared__ float redf[kBlock];
+    __syncthreads();
+    redf[threadIdx.x] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x < 32) {
+        t = redf[threadIdx.x];
+#pragma unroll
+        for (int i = 1; i < kBlock / 32; ++i) t += redf[threadIdx.x + 32 * i];
+        t = warp_sumf(t);
     }
     return t;
 }
@@ -169,6 +195,13 @@ template <>
 __device__ __forceinline__ const double *copy_vals<double>(const DevOp &A) { return A.ival; }
 template <>
 __device__ __forceinline__ const float *copy_vals<float>(const DevOp &A) { return A.ival32; }
+
+template <typename T>
+__device__ __forceinline__ T wtab_of(const DevOp &A, int m);
+template <>
+__device__ __forceinline__ double wtab_of<double>(const DevOp &A, int m) { return __ldg(A.wtab + m); }
+template <>
+__device__ __forceinline__ float wtab_of<float>(const DevOp &A, int m) { return __ldg(A.wtab32 + m); }
 
 // N consecutive entries (k0 .. k0+N-1) of a lane's sliced-ELL row: all
 // loads first (the value and column loads of a warp are contiguous and
@@ -263,7 +296,7 @@ __global__ void __launch_bounds__(kSpmvThreads, kSpmvBlocksPerSM)
             if (valid) {
                 const int row = __ldg(A.icopy + c);
                 y[row] = S;
-                dot = fma(T(__ldg(A.wtab + m)) * __ldg(x + row), S, dot);
+                dot = fma(wtab_of<T>(A, m) * __ldg(x + row), S, dot);
             }
         } else if (W.kind == kItemLongRow) {
             // one long row: lane-strided partial sums, fixed warp tree
@@ -284,7 +317,7 @@ __global__ void __launch_bounds__(kSpmvThreads, kSpmvBlocksPerSM)
                 S += T(warp_sum(double(acc)));  // valid in lane 0
             }
             if (lane == 0) {
-                const T w = T(A.wtab[W.c1 - W.c0]);
+                const T w = wtab_of<T>(A, W.c1 - W.c0);
                 for (int c = W.c0; c < W.c1; ++c) {
                     const int row = A.icopy[c];
                     y[row] = S;
@@ -317,6 +350,7 @@ __global__ void __launch_bounds__(kSpmvThreads, kSpmvBlocksPerSM)
                     stop_loop(s, h, use_cond);
                 } else {
                     s->alpha = s->rho / tot;
+                    s->alpha32 = float(s->alpha);
                 }
             }
         }
@@ -526,7 +560,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(int64_t n, const int32_t *__r
 __global__ void __launch_bounds__(kBlock) k_inner_init(int64_t N, const double *__restrict__ r64,
                                                        float *__restrict__ r32, float *__restrict__ p32,
                                                        float *__restrict__ d32, const uint8_t *__restrict__ mult,
-                                                       const double *__restrict__ wtab, double *partials, Scal *si,
+                                                       const float *__restrict__ wtab, double *partials, Scal *si,
                                                        const Scal *so, cudaGraphConditionalHandle h, int use_cond) {
     float acc = 0.f;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
@@ -536,9 +570,9 @@ __global__ void __launch_bounds__(kBlock) k_inner_init(int64_t N, const double *
         p32[i] = ri;
         d32[i] = 0.f;
         const unsigned int m = mult[i];
-        acc = m == 1u ? fmaf(ri, ri, acc) : fmaf(float(__ldg(wtab + m)) * ri, ri, acc);
+        acc = fmaf(__ldg(wtab + m) * ri, ri, acc);
     }
-    const double bs = block_sum(double(acc));
+    const double bs = double(block_sumf(acc));
     if (publish_and_check_last(partials, bs, &si->ticket[kTicketMisc])) {
         const double tot = sum_partials(partials, gridDim.x);
         if (threadIdx.x == 0) {
@@ -550,6 +584,8 @@ __global__ void __launch_bounds__(kBlock) k_inner_init(int64_t N, const double *
             si->iter = 0;
             si->alpha = 0.0;
             si->beta = 0.0;
+            si->alpha32 = 0.f;
+            si->beta32 = 0.f;
             si->status = SSG_OK;
             si->stop_after_xp = 0;
             const int stop = !(tot > 0.0) || so->total >= so->max_iter;
@@ -559,47 +595,57 @@ __global__ void __launch_bounds__(kBlock) k_inner_init(int64_t N, const double *
     }
 }
 
-// r32 <- r32 - alpha q32 and (r32, r32)_w (products in FP32, block sums in
-// FP64); the last block forms beta and the inner stopping decision.
+// r32 <- r32 - alpha q32 and (r32, r32)_w (products and block sums in
+// FP32, grid sum in FP64); the last block forms beta and the inner stopping
+// decision.  A warp covers the 128 entries of flag group i >> 5 (float4 per
+// lane); groups without interface copies skip the weights.
 __global__ void __launch_bounds__(kBlock) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
                                                        const uint8_t *__restrict__ mult,
-                                                       const double *__restrict__ wtab,
-                                                       const uint8_t *__restrict__ gflag, double *partials, Scal *si,
-                                                       Scal *so) {
+                                                       const float *__restrict__ wtab,
+                                                       const uint8_t *__restrict__ gflag128, double *partials,
+                                                       Scal *si, Scal *so) {
     if (si->done) return;
-    const float alpha = float(si->alpha);
+    const float alpha = si->alpha32;
     float acc = 0.f;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
-    const int64_t N2 = N >> 1;
-    float2 *__restrict__ r2 = reinterpret_cast<float2 *>(r);
-    const float2 *__restrict__ q2 = reinterpret_cast<const float2 *>(q);
-    const uchar2 *__restrict__ m2 = reinterpret_cast<const uchar2 *>(mult);
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N2; i += stride) {
-        float2 rv = r2[i];
-        const float2 qv = __ldcs(q2 + i);
+    const int64_t N4 = N >> 2;
+    float4 *__restrict__ r4 = reinterpret_cast<float4 *>(r);
+    const float4 *__restrict__ q4 = reinterpret_cast<const float4 *>(q);
+    const uchar4 *__restrict__ m4 = reinterpret_cast<const uchar4 *>(mult);
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N4; i += stride) {
+        float4 rv = r4[i];
+        const float4 qv = __ldcs(q4 + i);
         rv.x = fmaf(-alpha, qv.x, rv.x);
         rv.y = fmaf(-alpha, qv.y, rv.y);
-        r2[i] = rv;
-        if (__ldg(gflag + (i >> 5)) == 0) {
+        rv.z = fmaf(-alpha, qv.z, rv.z);
+        rv.w = fmaf(-alpha, qv.w, rv.w);
+        r4[i] = rv;
+        if (__ldg(gflag128 + (i >> 5)) == 0) {
             acc = fmaf(rv.x, rv.x, acc);
             acc = fmaf(rv.y, rv.y, acc);
+            acc = fmaf(rv.z, rv.z, acc);
+            acc = fmaf(rv.w, rv.w, acc);
         } else {
-            const uchar2 mv = m2[i];
-            acc = fmaf(float(__ldg(wtab + mv.x)) * rv.x, rv.x, acc);
-            acc = fmaf(float(__ldg(wtab + mv.y)) * rv.y, rv.y, acc);
+            const uchar4 mv = m4[i];
+            acc = fmaf(__ldg(wtab + mv.x) * rv.x, rv.x, acc);
+            acc = fmaf(__ldg(wtab + mv.y) * rv.y, rv.y, acc);
+            acc = fmaf(__ldg(wtab + mv.z) * rv.z, rv.z, acc);
+            acc = fmaf(__ldg(wtab + mv.w) * rv.w, rv.w, acc);
         }
     }
-    if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-        const float ri = fmaf(-alpha, q[N - 1], r[N - 1]);
-        r[N - 1] = ri;
-        acc = fmaf(float(__ldg(wtab + mult[N - 1])) * ri, ri, acc);
+    if (blockIdx.x == 0 && threadIdx.x < (N & 3)) {
+        const int64_t i = (N & ~int64_t(3)) + threadIdx.x;
+        const float ri = fmaf(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc = fmaf(__ldg(wtab + mult[i]) * ri, ri, acc);
     }
-    const double bs = block_sum(double(acc));
+    const double bs = double(block_sumf(acc));
     if (publish_and_check_last(partials, bs, &si->ticket[kTicketR])) {
         const double tot = sum_partials(partials, gridDim.x);
         if (threadIdx.x == 0) {
             si->ticket[kTicketR] = 0;
             si->beta = tot / si->rho;
+            si->beta32 = float(si->beta);
             si->rho = tot;
             si->iter += 1;
             so->total += 1;
@@ -613,7 +659,7 @@ __global__ void __launch_bounds__(kBlock) k_update_dp32(int64_t N, float *__rest
                                                         const float *__restrict__ r, double *partials, Scal *si,
                                                         cudaGraphConditionalHandle h, int use_cond) {
     if (si->done) return;
-    const float alpha = float(si->alpha), beta = float(si->beta);
+    const float alpha = si->alpha32, beta = si->beta32;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N4 = N >> 2;
     float4 *__restrict__ d4 = reinterpret_cast<float4 *>(d);
