@@ -58,6 +58,8 @@ def parse_args(argv=None):
     ap.add_argument("--mode", choices=("mixed", "fp64"), default="mixed",
                     help="mixed: FP32 inner CG inside FP64 iterative refinement; fp64: Algorithm 3 in FP64. "
                          "Both stop on an FP64 relative residual of 1e-8; the other mode is timed too and reported")
+    ap.add_argument("--pdl", choices=("on", "off"), default="off",
+                    help="programmatic dependent launch for the per-iteration update kernels")
     ap.add_argument("--driver", choices=("graph", "host"), default="graph",
                     help="graph: one CUDA graph per solve (timed default); host: same kernels launched from a "
                          "host loop (for profilers that cannot see kernels inside conditional graphs)")
@@ -345,6 +347,7 @@ def run_ours(args, dist):
     ctx = Context(dev, stream)
     if args.driver == "host":
         ctx.set_driver(ssg.SSG_DRIVER_HOST)
+    ctx.set_pdl(args.pdl == "on")
     S = System(ctx, prob.A, prob.part, prob.P)
     b = torch.from_numpy(prob.b[:, 0].copy()).to("cuda:%d" % dev)
     x = torch.zeros_like(b)
@@ -462,6 +465,7 @@ def run_ours(args, dist):
             "l2": "inputs larger than L2 (175 MB matrix + 5 x 18 MB vectors > 129 MB)",
             "parallelism": "replicas" if dist.world > 1 else "single",
             "driver": args.driver,
+            "pdl": args.pdl,
         },
         "roofline": roof[dominant],
         "roofline_other": roof["fp64" if dominant == "fp32" else "fp32"],

@@ -90,6 +90,12 @@ int ssg_create(ssg_ctx **ctx, int device, void *stream);
 int ssg_set_stream(ssg_ctx *ctx, void *stream);
 /* Pick how ssg_solve drives the iteration (SSG_DRIVER_*); default GRAPH. */
 int ssg_set_driver(ssg_ctx *ctx, int driver);
+/* Launch the residual and direction updates of each iteration with
+ * programmatic dependent launch (their launch overlaps the previous kernel's
+ * tail; results are unchanged).  enable != 0: on; default off (measured on
+ * GB300: no gain in SSG_MIXED, 13 us per iteration lost in SSG_FP64).
+ * Applies to systems partitioned on this context afterwards. */
+int ssg_set_pdl(ssg_ctx *ctx, int enable);
 /*
  * Parameters of SSG_MIXED solves on this context (not a method of the paper;
  * its experiments are FP64 only): the inner FP32 CG stops when its residual

@@ -32,6 +32,7 @@ struct ssg_ctx {
     int driver = SSG_DRIVER_GRAPH;
     int num_sms = 0;
     int live_systems = 0;  // systems created on this context and not yet destroyed
+    int pdl = 0;               // programmatic dependent launch inside the loop bodies (measured: off is faster)
     double inner_rtol = 1e-4;  // SSG_MIXED: inner FP32 CG tolerance
     int32_t max_outer = 30;    // SSG_MIXED: refinement steps cap
 };
@@ -43,7 +44,8 @@ struct ssg_system {
     // device arena
     void *arena = nullptr;
     size_t arena_bytes = 0;
-    DevOp op{};
+    DevOp op{};    // FP64 SpMV launch (warp ranges for grid_spmv blocks)
+    DevOp op32{};  // FP32 SpMV launch (warp ranges for grid_spmv32 blocks)
     int32_t *d_l2g = nullptr;
     int32_t *d_own = nullptr;
     // solver state
@@ -55,7 +57,9 @@ struct ssg_system {
     Scal *d_scal = nullptr;     // CG state
     Scal *d_scal_op = nullptr;  // state for the stand-alone SpMV / dot calls
     double *d_xg = nullptr, *d_bg = nullptr;  // global staging for ssg_solve_host
+    bool pdl = false;  // loop-body kernels use programmatic dependent launch
     int grid_spmv = 0;
+    int grid_spmv32 = 0;
     int grid_vec = 0;
     // graph
     cudaGraph_t graph = nullptr;
@@ -80,6 +84,23 @@ namespace {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Launch with or without programmatic stream serialization (the kernel may
+// begin while its predecessor finishes; it waits in pdl_enter()).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // SpMV work list (see WorkItem in kernels.cuh) and the sliced-ELL copy of
 // the local matrices it streams.  Interior slices: up to 32 consecutive
 // interior rows of one subdomain, width = their longest row; a row longer
@@ -96,11 +117,37 @@ struct WorkPlan {
     std::vector<double> sval;        // sliced-ELL values
     std::vector<int32_t> scol, sseg;
     std::vector<WorkItem> items;
-    std::vector<int2> warp_range;
-    int grid = 0;
+    std::vector<int2> warp_range64, warp_range32;  // per warp of the FP64 / FP32 launch
+    int grid64 = 0, grid32 = 0;
 };
 
-WorkPlan make_plan(const HostMaps &M, int grid_cap) {
+// Cut the item list into one contiguous range of about equal cost per warp
+// of a launch of `blocks` blocks.
+std::vector<int2> cut_ranges(const std::vector<WorkItem> &items, int blocks) {
+    const int n = static_cast<int>(items.size());
+    const int G = blocks * kSpmvWarps;
+    std::vector<double> prefix(static_cast<size_t>(n) + 1, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const WorkItem &w = items[i];
+        double cost = 64.0;
+        if (w.kind == kItemSlice || w.kind == kItemIfaceSlice) cost += 32.0 * w.e1;
+        else cost += 4.0 * (w.e1 - w.e0);
+        prefix[i + 1] = prefix[i] + cost;
+    }
+    std::vector<int2> R(G);
+    int lo = 0;
+    for (int b = 0; b < G; ++b) {
+        const double target = prefix[n] * (b + 1) / G;
+        int hi = lo;
+        while (hi < n && (prefix[hi + 1] <= target || hi == lo)) ++hi;
+        if (b == G - 1) hi = n;
+        R[b] = make_int2(lo, hi);
+        lo = hi;
+    }
+    return R;
+}
+
+WorkPlan make_plan(const HostMaps &M, int num_sms) {
     WorkPlan W;
     std::vector<int32_t> sub_of(static_cast<size_t>(M.nloc));
     for (int32_t s = 0; s < M.P; ++s)
@@ -197,41 +244,23 @@ WorkPlan make_plan(const HostMaps &M, int grid_cap) {
         if (i < nr) W.items.push_back(rows[i]);
     }
     while (j < ni) W.items.push_back(iface[j++]);
-    // contiguous slices of about equal cost, one per warp of the launch
     const int n = static_cast<int>(W.items.size());
-    const int blocks = std::max(1, std::min((n + kSpmvWarps - 1) / kSpmvWarps, grid_cap));
-    const int G = blocks * kSpmvWarps;
-    W.grid = blocks;
-    std::vector<double> prefix(static_cast<size_t>(n) + 1, 0.0);
-    for (int i = 0; i < n; ++i) {
-        const WorkItem &w = W.items[i];
-        double cost = 64.0;
-        if (w.kind == kItemSlice || w.kind == kItemIfaceSlice) cost += 32.0 * w.e1;
-        else cost += 4.0 * (w.e1 - w.e0);
-        prefix[i + 1] = prefix[i] + cost;
-    }
-    W.warp_range.resize(G);
-    int lo = 0;
-    for (int b = 0; b < G; ++b) {
-        const double target = prefix[n] * (b + 1) / G;
-        int hi = lo;
-        while (hi < n && (prefix[hi + 1] <= target || hi == lo)) ++hi;
-        if (b == G - 1) hi = n;
-        W.warp_range[b] = make_int2(lo, hi);
-        lo = hi;
-    }
+    const int per = (n + kSpmvWarps - 1) / kSpmvWarps;
+    W.grid64 = std::max(1, std::min(per, num_sms * SpmvTraits<double>::kBlocksPerSM));
+    W.grid32 = std::max(1, std::min(per, num_sms * SpmvTraits<float>::kBlocksPerSM));
+    W.warp_range64 = cut_ranges(W.items, W.grid64);
+    W.warp_range32 = cut_ranges(W.items, W.grid32);
     return W;
 }
 
 int launch_body(ssg_system *S, cudaStream_t st, int use_cond) {
     const int64_t N = S->maps.nloc;
-    k_spmv_asm<kEpiAlpha, double><<<S->grid_spmv, kSpmvThreads, 0, st>>>(
-        S->op, S->d_p, S->d_q, S->d_partials, S->d_scal, nullptr, S->cond, use_cond);
-    k_update_r<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_r, S->d_q, S->op.mult, S->op.wtab, S->op.gflag,
-                                               S->d_partials, S->d_scal);
-    k_update_xp<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_xl, S->d_p, S->d_r, S->d_partials, S->d_scal, S->cond,
-                                                use_cond);
-    SSG_CUDA_TRY(cudaGetLastError());
+    SSG_CUDA_TRY(launch_k(false, k_spmv_asm<kEpiAlpha, double>, S->grid_spmv, kSpmvThreads, st, S->op, S->d_p, S->d_q,
+                          S->d_partials, S->d_scal, (double *)nullptr, S->cond, use_cond));
+    SSG_CUDA_TRY(launch_k(S->pdl, k_update_r, S->grid_vec, kBlock, st, N, S->d_r, S->d_q, S->op.mult, S->op.wtab,
+                          S->op.gflag, S->d_partials, S->d_scal));
+    SSG_CUDA_TRY(launch_k(S->pdl, k_update_xp, S->grid_vec, kBlock, st, N, S->d_xl, S->d_p, S->d_r, S->d_partials,
+                          S->d_scal, S->cond, use_cond));
     return SSG_OK;
 }
 
@@ -242,8 +271,21 @@ int launch_init(ssg_system *S, cudaStream_t st, int use_cond) {
     return SSG_OK;
 }
 
+int build_graph_once(ssg_system *S);
+
+// Build the FP64 graph; if the driver refuses programmatic edges inside the
+// conditional body, rebuild it with plain launches.
 int build_graph(ssg_system *S) {
     if (S->exec) return SSG_OK;
+    int rc = build_graph_once(S);
+    if (rc != SSG_OK && S->pdl) {
+        S->pdl = false;
+        rc = build_graph_once(S);
+    }
+    return rc;
+}
+
+int build_graph_once(ssg_system *S) {
     SSG_CUDA_TRY(cudaGraphCreate(&S->graph, 0));
     SSG_CUDA_TRY(cudaGraphConditionalHandleCreate(&S->cond, S->graph, 0u, cudaGraphCondAssignDefault));
     cudaStream_t cap;
@@ -314,13 +356,12 @@ int launch_inner_init(ssg_system *S, cudaStream_t st, int use_cond) {
 
 int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond) {
     const int64_t N = S->maps.nloc;
-    k_spmv_asm<kEpiAlpha, float><<<S->grid_spmv, kSpmvThreads, 0, st>>>(
-        S->op, S->d_p32, S->d_q32, S->d_partials, S->d_scal_in, nullptr, S->cond_in, use_cond);
-    k_update_r32<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_r32, S->d_q32, S->op.mult, S->op.wtab32, S->op.gflag128,
-                                                 S->d_partials, S->d_scal_in, S->d_scal);
-    k_update_dp32<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_d32, S->d_p32, S->d_r32, S->d_partials, S->d_scal_in,
-                                                  S->cond_in, use_cond);
-    SSG_CUDA_TRY(cudaGetLastError());
+    SSG_CUDA_TRY(launch_k(false, k_spmv_asm<kEpiAlpha, float>, S->grid_spmv32, kSpmvThreads, st, S->op32, S->d_p32,
+                          S->d_q32, S->d_partials, S->d_scal_in, (double *)nullptr, S->cond_in, use_cond));
+    SSG_CUDA_TRY(launch_k(S->pdl, k_update_r32, S->grid_vec, kBlock, st, N, S->d_r32, S->d_q32, S->op.mult,
+                          S->op.wtab32, S->op.gflag128, S->d_partials, S->d_scal_in, S->d_scal));
+    SSG_CUDA_TRY(launch_k(S->pdl, k_update_dp32, S->grid_vec, kBlock, st, N, S->d_d32, S->d_p32, S->d_r32,
+                          S->d_partials, S->d_scal_in, S->cond_in, use_cond));
     return SSG_OK;
 }
 
@@ -380,8 +421,19 @@ cudaError_t add_while(cudaGraph_t g, const cudaGraphNode_t *dep, cudaGraphCondit
 
 // SSG_MIXED graph: init -> WHILE(outer) { inner_init -> WHILE(inner) { FP32
 // SpMV, r update, d/p update } -> x += d -> FP64 SpMV -> residual + test }.
+int build_graph_mixed_once(ssg_system *S);
+
 int build_graph_mixed(ssg_system *S) {
     if (S->exec_m) return SSG_OK;
+    int rc = build_graph_mixed_once(S);
+    if (rc != SSG_OK && S->pdl) {
+        S->pdl = false;
+        rc = build_graph_mixed_once(S);
+    }
+    return rc;
+}
+
+int build_graph_mixed_once(ssg_system *S) {
     SSG_CUDA_TRY(cudaGraphCreate(&S->graph_m, 0));
     SSG_CUDA_TRY(cudaGraphConditionalHandleCreate(&S->cond_out, S->graph_m, 0u, cudaGraphCondAssignDefault));
     cudaStream_t cap;
@@ -420,7 +472,7 @@ int upload(ssg_system *S) {
     const HostMaps &M = S->maps;
     ssg_ctx *C = S->ctx;
     SSG_CUDA_TRY(cudaSetDevice(C->device));
-    WorkPlan plan = make_plan(M, C->num_sms * kSpmvBlocksPerSM);
+    WorkPlan plan = make_plan(M, C->num_sms);
     const int64_t N = M.nloc;
     // concatenated column ids
     std::vector<int32_t> gcol(static_cast<size_t>(M.nnz));
@@ -443,9 +495,10 @@ int upload(ssg_system *S) {
         wtab32[m] = static_cast<float>(wtab[m]);
     }
 
-    S->grid_spmv = plan.grid;
+    S->grid_spmv = plan.grid64;
+    S->grid_spmv32 = plan.grid32;
     S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N / 2 + kBlock - 1) / kBlock), C->num_sms * kVecBlocksPerSM));
-    S->n_partials = 2 * std::max(S->grid_spmv, S->grid_vec);
+    S->n_partials = 2 * std::max(std::max(S->grid_spmv, S->grid_spmv32), S->grid_vec);
 
     struct Piece {
         const void *src;
@@ -478,7 +531,8 @@ int upload(ssg_system *S) {
     size_t i_scol = add(plan.scol.data(), sizeof(int32_t) * plan.scol.size());
     size_t i_sseg = add(plan.sseg.data(), sizeof(int32_t) * plan.sseg.size());
     size_t i_items = add(plan.items.data(), sizeof(WorkItem) * plan.items.size());
-    size_t i_brange = add(plan.warp_range.data(), sizeof(int2) * plan.warp_range.size());
+    size_t i_brange = add(plan.warp_range64.data(), sizeof(int2) * plan.warp_range64.size());
+    size_t i_brange32 = add(plan.warp_range32.data(), sizeof(int2) * plan.warp_range32.size());
     size_t i_iptr = add(M.iptr.data(), sizeof(int32_t) * (M.ngamma + 1));
     size_t i_icopy = add(M.icopy.data(), sizeof(int32_t) * M.ncopies);
     size_t i_mult = add(mloc.data(), N);
@@ -538,6 +592,7 @@ int upload(ssg_system *S) {
     S->op.sseg = static_cast<const int32_t *>(at(i_sseg));
     S->op.items = static_cast<const WorkItem *>(at(i_items));
     S->op.warp_range = static_cast<const int2 *>(at(i_brange));
+    S->op32 = S->op;  // filled below once the op is complete
     S->op.iptr = static_cast<const int32_t *>(at(i_iptr));
     S->op.icopy = static_cast<const int32_t *>(at(i_icopy));
     S->op.mult = static_cast<const uint8_t *>(at(i_mult));
@@ -557,6 +612,8 @@ int upload(ssg_system *S) {
     S->d_scal_op = static_cast<Scal *>(at(i_scal2));
     S->d_xg = static_cast<double *>(at(i_xg));
     S->d_bg = static_cast<double *>(at(i_bg));
+    S->op32 = S->op;
+    S->op32.warp_range = static_cast<const int2 *>(at(i_brange32));
     SSG_CUDA_TRY(cudaMemsetAsync(S->d_scal, 0, sizeof(Scal), C->stream));
     SSG_CUDA_TRY(cudaMemsetAsync(S->d_scal_op, 0, sizeof(Scal), C->stream));
     SSG_CUDA_TRY(cudaEventCreate(&S->ev0));
@@ -767,6 +824,15 @@ int ssg_set_driver(ssg_ctx *ctx, int driver) {
     return SSG_OK;
 }
 
+int ssg_set_pdl(ssg_ctx *ctx, int enable) {
+    if (!ctx) {
+        set_error("null context");
+        return SSG_E_INVALID;
+    }
+    ctx->pdl = enable ? 1 : 0;
+    return SSG_OK;
+}
+
 int ssg_set_mixed(ssg_ctx *ctx, double inner_rtol, int32_t max_outer) {
     if (!ctx || !(inner_rtol > 0.0 && inner_rtol < 1.0) || max_outer < 1) {
         set_error("ssg_set_mixed: need 0 < inner_rtol < 1 and max_outer >= 1");
@@ -806,6 +872,7 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
     S->ctx = ctx;
     if (ctx) {
         ctx->live_systems++;
+        S->pdl = ctx->pdl != 0;
         rc = upload(S);
         if (rc != SSG_OK) {
             ssg_system_destroy(S);
@@ -901,8 +968,8 @@ int ssg_spmv_assembled_f32(ssg_system *S, const float *x_loc, float *y_loc, doub
         set_error("x_loc and y_loc must be distinct non-null device vectors");
         return SSG_E_INVALID;
     }
-    k_spmv_asm<kEpiStore, float><<<S->grid_spmv, kSpmvThreads, 0, S->ctx->stream>>>(
-        S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
+    k_spmv_asm<kEpiStore, float><<<S->grid_spmv32, kSpmvThreads, 0, S->ctx->stream>>>(
+        S->op32, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }

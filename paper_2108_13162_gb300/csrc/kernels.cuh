@@ -28,7 +28,18 @@ constexpr int kSpmvWarps = 8;               // warps per SpMV block
 constexpr int kSpmvThreads = 32 * kSpmvWarps;
 constexpr int kSliceRows = 32;              // rows (or interface copy rows) per slice: one per lane
 constexpr int kSliceMaxWidth = 64;          // longer rows are handled one per warp from the CSR arrays
-constexpr int kSpmvBlocksPerSM = 4;
+template <typename T>
+struct SpmvTraits;  // resident blocks per SM; whether column indices are loaded a slice ahead
+template <>
+struct SpmvTraits<double> {
+    static constexpr int kBlocksPerSM = 4;  // measured: 4 blocks without prefetch beat 3 with it
+    static constexpr bool kPrefetch = false;
+};
+template <>
+struct SpmvTraits<float> {
+    static constexpr int kBlocksPerSM = 4;
+    static constexpr bool kPrefetch = true;
+};
 constexpr int kVecBlocksPerSM = 4;
 constexpr int kHostChunk = 32;    // iterations per host-loop chunk (SSG_DRIVER_HOST)
 
@@ -172,6 +183,15 @@ __device__ __forceinline__ double sum_partials(const double *partials, int G) {
     return block_sum<NT>(v);
 }
 
+// Programmatic dependent launch: wait until the preceding kernel in the
+// stream has completed and its writes are visible (a no-op when this kernel
+// was launched without the attribute), then let the next kernel start its
+// launch so its scheduling overlaps this kernel's tail.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void stop_loop(Scal *s, cudaGraphConditionalHandle h, int use_cond) {
     s->done = 1;
     if (use_cond) cudaGraphSetConditional(h, 0);
@@ -247,23 +267,94 @@ __device__ __forceinline__ T slice_row(const T *__restrict__ sv, const int32_t *
     }
 }
 
-// ---------------------------------------------------------------------------
-// Sub-structured SpMV (Section 3.4.1) with the interface assembly of
-// Algorithms 4 and 5 fused in, on a sliced-ELL copy of the local matrices
-// (slices of 32 consecutive rows, k-th nonzeros of the 32 rows contiguous).
-// Every warp walks its own fixed, contiguous slice of a precomputed work
-// list (the same rows in the same order on every run, so the (x, y)_w
-// partials are deterministic), with no block-wide barrier:
-//   interior slice: one row per lane, y[r] = its row product;
-//   interface slice: one copy row per lane ((node, copy) order, whole nodes),
-//     then each node's copies are summed in ascending subdomain order with
-//     warp shuffles and every copy receives the sum;
-//   long row / long interface node: the warp strides over the CSR entries.
-// ---------------------------------------------------------------------------
+// Column indices of one lane's row in a slice of width <= 8, loaded one
+// slice ahead: the current slice's value loads (DRAM) then go out together
+// with its x gathers (which only need the columns), so the two latencies
+// overlap instead of adding up.
+struct SliceCols {
+    int32_t c[8];
+};
+
+__device__ __forceinline__ bool short_slice(const WorkItem &W) {
+    return (W.kind == kItemSlice || W.kind == kItemIfaceSlice) && W.e1 <= 8;
+}
+
+__device__ __forceinline__ void load_cols(SliceCols &R, const int32_t *__restrict__ sc, const WorkItem &W, int lane) {
+    const int base = W.e0 + lane;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if (j < W.e1) R.c[j] = __ldcs(sc + base + j * kSliceRows);
+}
+
+template <int N, typename T>
+__device__ __forceinline__ T fma_regs(const T *v, const T *xv) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc = fma(v[j], xv[j], acc);
+    return acc;
+}
+
+// Row product with the columns already in registers: value loads and x
+// gathers issued together, then exactly w FMAs in CSR order.
+template <typename T>
+__device__ __forceinline__ T cols_row(const SliceCols &R, const T *__restrict__ sv, const WorkItem &W, int lane,
+                                      const T *__restrict__ x) {
+    const int base = W.e0 + lane, w = W.e1;
+    T v[8], xv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if (j < w) {
+            v[j] = __ldcs(sv + base + j * kSliceRows);
+            xv[j] = __ldg(x + R.c[j]);
+        }
+    switch (w) {
+        case 1: return fma_regs<1>(v, xv);
+        case 2: return fma_regs<2>(v, xv);
+        case 3: return fma_regs<3>(v, xv);
+        case 4: return fma_regs<4>(v, xv);
+        case 5: return fma_regs<5>(v, xv);
+        case 6: return fma_regs<6>(v, xv);
+        case 7: return fma_regs<7>(v, xv);
+        case 8: return fma_regs<8>(v, xv);
+        default: return T(0);
+    }
+}
+
+// Writes of one slice's results: interior rows, or interface copy rows whose
+// node sums are formed by shuffles in ascending subdomain order.
+template <typename T>
+__device__ __forceinline__ void finish_slice(const DevOp &A, const WorkItem &W, T acc, const T *__restrict__ x,
+                                             T *__restrict__ y, int lane, T &dot) {
+    if (W.kind == kItemSlice) {
+        const int r = W.a + lane;
+        if (r < W.b) {
+            y[r] = acc;
+            dot = fma(__ldg(x + r), acc, dot);
+        }
+    } else {
+        const int c = W.a + lane;
+        const bool valid = c < W.b;
+        const int seg = valid ? __ldg(A.sseg + c) : 0;
+        const int l0 = seg & 0xff, m = seg >> 8;
+        const int mmax = __reduce_max_sync(0xffffffffu, m);
+        T S = T(0);
+        for (int t = 0; t < mmax; ++t) {
+            const T v = __shfl_sync(0xffffffffu, acc, (l0 + t) & 31);
+            if (t < m) S += v;
+        }
+        if (valid) {
+            const int row = __ldg(A.icopy + c);
+            y[row] = S;
+            dot = fma(wtab_of<T>(A, m) * __ldg(x + row), S, dot);
+        }
+    }
+}
+
 template <int EPI, typename T>
-__global__ void __launch_bounds__(kSpmvThreads, kSpmvBlocksPerSM)
+__global__ void __launch_bounds__(kSpmvThreads, SpmvTraits<T>::kBlocksPerSM)
     k_spmv_asm(DevOp A, const T *__restrict__ x, T *__restrict__ y, double *partials, Scal *s, double *out,
                cudaGraphConditionalHandle h, int use_cond) {
+    pdl_enter();
     if (EPI == kEpiAlpha && s->done) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 range = A.warp_range[blockIdx.x * kSpmvWarps + warp];
@@ -272,59 +363,53 @@ __global__ void __launch_bounds__(kSpmvThreads, kSpmvBlocksPerSM)
     const T *__restrict__ ival = copy_vals<T>(A);
     T dot = T(0);
 
+    constexpr bool kPF = SpmvTraits<T>::kPrefetch;
+    SliceCols cur, nxt;
+    WorkItem W = range.x < range.y ? A.items[range.x] : WorkItem{};
+    if (kPF && range.x < range.y && short_slice(W)) load_cols(cur, A.scol, W, lane);
     for (int it = range.x; it < range.y; ++it) {
-        const WorkItem W = A.items[it];
-        if (W.kind == kItemSlice) {
-            const T acc = slice_row<T>(sv, A.scol, x, W.e0, W.e1, lane);
-            const int r = W.a + lane;
-            if (r < W.b) {
-                y[r] = acc;
-                dot = fma(__ldg(x + r), acc, dot);
-            }
-        } else if (W.kind == kItemIfaceSlice) {
-            const T acc = slice_row<T>(sv, A.scol, x, W.e0, W.e1, lane);
-            const int c = W.a + lane;
-            const bool valid = c < W.b;
-            const int seg = valid ? __ldg(A.sseg + c) : 0;
-            const int l0 = seg & 0xff, m = seg >> 8;
-            const int mmax = __reduce_max_sync(0xffffffffu, m);
-            T S = T(0);
-            for (int t = 0; t < mmax; ++t) {
-                const T v = __shfl_sync(0xffffffffu, acc, (l0 + t) & 31);
-                if (t < m) S += v;
-            }
-            if (valid) {
-                const int row = __ldg(A.icopy + c);
-                y[row] = S;
-                dot = fma(wtab_of<T>(A, m) * __ldg(x + row), S, dot);
-            }
-        } else if (W.kind == kItemLongRow) {
-            // one long row: lane-strided partial sums, fixed warp tree
-            T acc = T(0);
-            for (int k = W.e0 + lane; k < W.e1; k += 32) acc = fma(val[k], __ldg(x + A.col[k]), acc);
-            const T racc = T(warp_sum(double(acc)));
-            if (lane == 0) {
-                y[W.a] = racc;
-                dot = fma(__ldg(x + W.a), racc, dot);
-            }
+        const bool has_next = it + 1 < range.y;
+        const WorkItem Wn = has_next ? A.items[it + 1] : WorkItem{};
+        if (kPF && short_slice(W)) {
+            if (has_next && short_slice(Wn)) load_cols(nxt, A.scol, Wn, lane);
+            const T acc = cols_row<T>(cur, sv, W, lane, x);
+            finish_slice(A, W, acc, x, y, lane, dot);
+            cur = nxt;
         } else {
-            // one interface node with long copy rows: each copy row reduced by
-            // the warp (fixed tree), copies summed in ascending s
-            T S = T(0);
-            for (int c = W.c0; c < W.c1; ++c) {
+            if (W.kind == kItemSlice || W.kind == kItemIfaceSlice) {
+                const T acc = slice_row<T>(sv, A.scol, x, W.e0, W.e1, lane);
+                finish_slice(A, W, acc, x, y, lane, dot);
+            } else if (W.kind == kItemLongRow) {
+                // one long row: lane-strided partial sums, fixed warp tree
                 T acc = T(0);
-                for (int k = A.irp[c] + lane; k < A.irp[c + 1]; k += 32) acc = fma(ival[k], __ldg(x + A.icol[k]), acc);
-                S += T(warp_sum(double(acc)));  // valid in lane 0
-            }
-            if (lane == 0) {
-                const T w = wtab_of<T>(A, W.c1 - W.c0);
+                for (int k = W.e0 + lane; k < W.e1; k += 32) acc = fma(val[k], __ldg(x + A.col[k]), acc);
+                const T racc = T(warp_sum(double(acc)));
+                if (lane == 0) {
+                    y[W.a] = racc;
+                    dot = fma(__ldg(x + W.a), racc, dot);
+                }
+            } else {
+                // one interface node with long copy rows: each copy row reduced by
+                // the warp (fixed tree), copies summed in ascending s
+                T S = T(0);
                 for (int c = W.c0; c < W.c1; ++c) {
-                    const int row = A.icopy[c];
-                    y[row] = S;
-                    dot = fma(w * __ldg(x + row), S, dot);
+                    T acc = T(0);
+                    for (int k = A.irp[c] + lane; k < A.irp[c + 1]; k += 32)
+                        acc = fma(ival[k], __ldg(x + A.icol[k]), acc);
+                    S += T(warp_sum(double(acc)));  // valid in lane 0
+                }
+                if (lane == 0) {
+                    const T w = wtab_of<T>(A, W.c1 - W.c0);
+                    for (int c = W.c0; c < W.c1; ++c) {
+                        const int row = A.icopy[c];
+                        y[row] = S;
+                        dot = fma(w * __ldg(x + row), S, dot);
+                    }
                 }
             }
+            if (kPF && has_next && short_slice(Wn)) load_cols(cur, A.scol, Wn, lane);
         }
+        W = Wn;
     }
     // fixed-order reduction: lanes of each warp, then the block's warps in order
     __shared__ double wsum[kSpmvWarps];
@@ -366,6 +451,7 @@ __device__ __forceinline__ double wsq(double r, unsigned int m, const double *__
 __global__ void __launch_bounds__(kBlock) k_update_r(int64_t N, double *__restrict__ r, const double *__restrict__ q,
                                                      const uint8_t *__restrict__ mult, const double *__restrict__ wtab,
                                                      const uint8_t *__restrict__ gflag, double *partials, Scal *s) {
+    pdl_enter();
     if (s->done) return;
     const double alpha = s->alpha;
     double acc = 0.0;
@@ -421,6 +507,7 @@ __global__ void __launch_bounds__(kBlock) k_update_r(int64_t N, double *__restri
 __global__ void __launch_bounds__(kBlock) k_update_xp(int64_t N, double *__restrict__ x, double *__restrict__ p,
                                                       const double *__restrict__ r, double *partials, Scal *s,
                                                       cudaGraphConditionalHandle h, int use_cond) {
+    pdl_enter();
     if (s->done) return;
     const double alpha = s->alpha, beta = s->beta;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
@@ -604,6 +691,7 @@ __global__ void __launch_bounds__(kBlock) k_update_r32(int64_t N, float *__restr
                                                        const float *__restrict__ wtab,
                                                        const uint8_t *__restrict__ gflag128, double *partials,
                                                        Scal *si, Scal *so) {
+    pdl_enter();
     if (si->done) return;
     const float alpha = si->alpha32;
     float acc = 0.f;
@@ -658,6 +746,7 @@ __global__ void __launch_bounds__(kBlock) k_update_r32(int64_t N, float *__restr
 __global__ void __launch_bounds__(kBlock) k_update_dp32(int64_t N, float *__restrict__ d, float *__restrict__ p,
                                                         const float *__restrict__ r, double *partials, Scal *si,
                                                         cudaGraphConditionalHandle h, int use_cond) {
+    pdl_enter();
     if (si->done) return;
     const float alpha = si->alpha32, beta = si->beta32;
     const int64_t stride = (int64_t)gridDim.x * kBlock;

@@ -36,6 +36,7 @@ EXPORTS = (
     "ssg_set_stream",
     "ssg_set_driver",
     "ssg_set_mixed",
+    "ssg_set_pdl",
     "ssg_destroy",
     "ssg_partition",
     "ssg_get_sizes",
@@ -116,6 +117,7 @@ def lib():
         L.ssg_set_stream.argtypes = [vp, vp]
         L.ssg_set_driver.argtypes = [vp, C.c_int]
         L.ssg_set_mixed.argtypes = [vp, C.c_double, C.c_int32]
+        L.ssg_set_pdl.argtypes = [vp, C.c_int]
         L.ssg_destroy.argtypes = [vp]
         L.ssg_partition.argtypes = [vp, i32, vp, vp, vp, vp, i32, C.POINTER(vp)]
         L.ssg_get_sizes.argtypes = [vp, C.POINTER(ssg_sizes)]
@@ -186,6 +188,10 @@ def ssg_set_driver(ctx, driver: int):
 
 def ssg_set_mixed(ctx, inner_rtol: float, max_outer: int):
     return _check(lib().ssg_set_mixed(ctx, inner_rtol, max_outer), "ssg_set_mixed")
+
+
+def ssg_set_pdl(ctx, enable: bool):
+    return _check(lib().ssg_set_pdl(ctx, int(bool(enable))), "ssg_set_pdl")
 
 
 def ssg_destroy(ctx):
@@ -339,6 +345,9 @@ class Context:
 
     def set_driver(self, driver: int):
         ssg_set_driver(self.h, driver)
+
+    def set_pdl(self, enable: bool):
+        ssg_set_pdl(self.h, enable)
 
     def set_mixed(self, inner_rtol: float = 1e-4, max_outer: int = 30):
         ssg_set_mixed(self.h, inner_rtol, max_outer)
