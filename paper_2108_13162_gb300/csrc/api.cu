@@ -253,14 +253,20 @@ WorkPlan make_plan(const HostMaps &M, int num_sms) {
     return W;
 }
 
+// Partials of the loop reductions: the SpMV writes the first half, the
+// residual update the second, each read by the next kernel.
+double *part_pq(ssg_system *S) { return S->d_partials; }
+double *part_rr(ssg_system *S) { return S->d_partials + S->n_partials / 2; }
+
 int launch_body(ssg_system *S, cudaStream_t st, int use_cond) {
     const int64_t N = S->maps.nloc;
-    SSG_CUDA_TRY(launch_k(false, k_spmv_asm<kEpiAlpha, double>, S->grid_spmv, kSpmvThreads, st, S->op, S->d_p, S->d_q,
-                          S->d_partials, S->d_scal, (double *)nullptr, S->cond, use_cond));
+    SSG_CUDA_TRY(launch_k(false, k_spmv_asm<kEpiPartials, double>, S->grid_spmv, kSpmvThreads, st, S->op, S->d_p,
+                          S->d_q, part_pq(S), S->d_scal, (double *)nullptr, S->cond, use_cond));
     SSG_CUDA_TRY(launch_k(S->pdl, k_update_r, S->grid_vec, kBlock, st, N, S->d_r, S->d_q, S->op.mult, S->op.wtab,
-                          S->op.gflag, S->d_partials, S->d_scal));
-    SSG_CUDA_TRY(launch_k(S->pdl, k_update_xp, S->grid_vec, kBlock, st, N, S->d_xl, S->d_p, S->d_r, S->d_partials,
-                          S->d_scal, S->cond, use_cond));
+                          S->op.gflag, (const double *)part_pq(S), S->grid_spmv, part_rr(S), S->d_scal, S->cond,
+                          use_cond));
+    SSG_CUDA_TRY(launch_k(S->pdl, k_update_xp, S->grid_vec, kBlock, st, N, S->d_xl, S->d_p, S->d_r,
+                          (const double *)part_rr(S), S->grid_vec, S->d_scal, S->cond, use_cond));
     return SSG_OK;
 }
 
@@ -356,12 +362,13 @@ int launch_inner_init(ssg_system *S, cudaStream_t st, int use_cond) {
 
 int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond) {
     const int64_t N = S->maps.nloc;
-    SSG_CUDA_TRY(launch_k(false, k_spmv_asm<kEpiAlpha, float>, S->grid_spmv32, kSpmvThreads, st, S->op32, S->d_p32,
-                          S->d_q32, S->d_partials, S->d_scal_in, (double *)nullptr, S->cond_in, use_cond));
+    SSG_CUDA_TRY(launch_k(false, k_spmv_asm<kEpiPartials, float>, S->grid_spmv32, kSpmvThreads, st, S->op32,
+                          S->d_p32, S->d_q32, part_pq(S), S->d_scal_in, (double *)nullptr, S->cond_in, use_cond));
     SSG_CUDA_TRY(launch_k(S->pdl, k_update_r32, S->grid_vec, kBlock, st, N, S->d_r32, S->d_q32, S->op.mult,
-                          S->op.wtab32, S->op.gflag128, S->d_partials, S->d_scal_in, S->d_scal));
+                          S->op.wtab32, S->op.gflag128, (const double *)part_pq(S), S->grid_spmv32, part_rr(S),
+                          S->d_scal_in, (const Scal *)S->d_scal, S->cond_in, use_cond));
     SSG_CUDA_TRY(launch_k(S->pdl, k_update_dp32, S->grid_vec, kBlock, st, N, S->d_d32, S->d_p32, S->d_r32,
-                          S->d_partials, S->d_scal_in, S->cond_in, use_cond));
+                          (const double *)part_rr(S), S->grid_vec, S->d_scal_in, S->d_scal, S->cond_in, use_cond));
     return SSG_OK;
 }
 
@@ -747,8 +754,8 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     if (C->driver == SSG_DRIVER_GRAPH) {
         if (mode == SSG_MIXED)  // init, per refinement: inner init + 3 tail kernels, 3 per inner iteration
             launches += 1 + 4 * static_cast<int64_t>(h.iter) + 3 * static_cast<int64_t>(h.total);
-        else
-            launches += 1 + 3 * static_cast<int64_t>(h.iter) + (h.status == SSG_E_BREAKDOWN ? 1 : 0);
+        else  // init, 3 per iteration (a breakdown ends after the SpMV and residual kernels of one more)
+            launches += 1 + 3 * static_cast<int64_t>(h.iter) + (h.status == SSG_E_BREAKDOWN ? 3 : 0);
     }
     if (st) {
         st->status = h.status;

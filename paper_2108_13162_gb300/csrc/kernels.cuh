@@ -70,6 +70,17 @@ struct Scal {
     int32_t max_outer;
     float alpha32;   // alpha and beta rounded to FP32 once (FP32 kernels read these:
     float beta32;    // a double-to-float conversion per thread costs FP64 pipe time)
+    // Hand-offs inside an iteration.  No kernel reads a field that another
+    // block of the same kernel writes: the residual update (block 0) copies
+    // rho, iter and total into the *_b fields the direction update reads, and
+    // the direction update (block 0) writes the new rho/iter/total and raises
+    // halt[(k+1) & 1], while every kernel of iteration k reads halt[k & 1].
+    double rho_b;
+    int32_t iter_b;
+    int32_t total_b;
+    int32_t halt[2];
+    int32_t brk;     // (S p, p) <= 0 seen: every later kernel returns at once
+    int32_t pad2;
 };
 
 enum { kTicketSpmv = 0, kTicketR = 1, kTicketXP = 2, kTicketMisc = 3 };
@@ -113,7 +124,9 @@ struct DevOp {
     const uint8_t *gflag128;  // [ceil(nloc / 128)] the same for groups of 128 entries
 };
 
-enum { kEpiStore = 0, kEpiAlpha = 1 };
+// kEpiStore: the (x, y)_w total is written to *out by the last block (ticket);
+// kEpiPartials: each block only writes its partial, the next kernel sums them.
+enum { kEpiStore = 0, kEpiPartials = 1 };
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -190,6 +203,19 @@ __device__ __forceinline__ double sum_partials(const double *partials, int G) {
 __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Every block sums the previous kernel's block partials in the same fixed
+// order (the partials are complete and visible at the kernel boundary), so
+// all blocks hold the bitwise same total without a ticket or a last block.
+__device__ __forceinline__ double all_sum_partials(const double *partials, int G) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < G; i += kBlock) v += __ldcg(partials + i);
+    const double t = block_sum(v);
+    __shared__ double bc;
+    if (threadIdx.x == 0) bc = t;
+    __syncthreads();
+    return bc;
 }
 
 __device__ __forceinline__ void stop_loop(Scal *s, cudaGraphConditionalHandle h, int use_cond) {
@@ -355,7 +381,7 @@ __global__ void __launch_bounds__(kSpmvThreads, SpmvTraits<T>::kBlocksPerSM)
     k_spmv_asm(DevOp A, const T *__restrict__ x, T *__restrict__ y, double *partials, Scal *s, double *out,
                cudaGraphConditionalHandle h, int use_cond) {
     pdl_enter();
-    if (EPI == kEpiAlpha && s->done) return;
+    if (EPI == kEpiPartials && (s->brk || s->halt[s->iter & 1])) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 range = A.warp_range[blockIdx.x * kSpmvWarps + warp];
     const T *__restrict__ sv = slice_vals<T>(A);
@@ -422,22 +448,15 @@ __global__ void __launch_bounds__(kSpmvThreads, SpmvTraits<T>::kBlocksPerSM)
 #pragma unroll
         for (int w = 1; w < kSpmvWarps; ++w) bs += wsum[w];
     }
+    if (EPI == kEpiPartials) {
+        if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+        return;
+    }
     if (publish_and_check_last(partials, bs, &s->ticket[kTicketSpmv])) {
         const double tot = sum_partials<kSpmvThreads>(partials, gridDim.x);
         if (threadIdx.x == 0) {
             s->ticket[kTicketSpmv] = 0;
-            if (EPI == kEpiStore) {
-                if (out) *out = tot;
-            } else {
-                s->pq = tot;
-                if (!(tot > 0.0) || !isfinite(tot)) {
-                    s->status = SSG_E_BREAKDOWN;
-                    stop_loop(s, h, use_cond);
-                } else {
-                    s->alpha = s->rho / tot;
-                    s->alpha32 = float(s->alpha);
-                }
-            }
+            if (out) *out = tot;
         }
     }
 }
@@ -446,14 +465,31 @@ __device__ __forceinline__ double wsq(double r, unsigned int m, const double *__
     return m == 1u ? fma(r, r, acc) : fma(__ldg(wtab + m) * r, r, acc);
 }
 
-// r <- r - alpha q and (r, r)_w; the last block forms beta (Algorithm 3 lines
-// 5 and 7, M = I) and the stopping decision, applied after the x/p update.
+// Algorithm 3 lines 3 and 5 (M = I): every block sums the SpMV's partials of
+// (p, S p)_w, forms alpha = rho / (p, S p)_w (or stops on a breakdown), then
+// r <- r - alpha q and its share of (r, r)_w.
 __global__ void __launch_bounds__(kBlock) k_update_r(int64_t N, double *__restrict__ r, const double *__restrict__ q,
                                                      const uint8_t *__restrict__ mult, const double *__restrict__ wtab,
-                                                     const uint8_t *__restrict__ gflag, double *partials, Scal *s) {
+                                                     const uint8_t *__restrict__ gflag, const double *part_pq,
+                                                     int G1, double *part_rr, Scal *s, cudaGraphConditionalHandle h,
+                                                     int use_cond) {
     pdl_enter();
-    if (s->done) return;
-    const double alpha = s->alpha;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s->rho_b = s->rho;
+        s->iter_b = s->iter;
+    }
+    if (s->brk || s->halt[s->iter & 1]) return;
+    const double pq = all_sum_partials(part_pq, G1);
+    if (!(pq > 0.0) || !isfinite(pq)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            s->pq = pq;
+            s->status = SSG_E_BREAKDOWN;
+            s->brk = 1;
+            stop_loop(s, h, use_cond);
+        }
+        return;
+    }
+    const double alpha = s->rho / pq;
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N2 = N >> 1;
@@ -484,32 +520,28 @@ __global__ void __launch_bounds__(kBlock) k_update_r(int64_t N, double *__restri
         acc = fma(__ldg(wtab + mult[N - 1]) * ri, ri, acc);
     }
     const double bs = block_sum(acc);
-    if (publish_and_check_last(partials, bs, &s->ticket[kTicketR])) {
-        const double tot = sum_partials(partials, gridDim.x);
-        if (threadIdx.x == 0) {
-            s->ticket[kTicketR] = 0;
-            s->beta = tot / s->rho;
-            s->rho = tot;
-            s->iter += 1;
-            s->relres = s->bnorm > 0.0 ? sqrt(tot) / s->bnorm : 0.0;
-            if (sqrt(tot) <= s->rtol * s->bnorm) {
-                s->status = SSG_OK;
-                s->stop_after_xp = 1;
-            } else if (s->iter >= s->max_iter) {
-                s->status = SSG_E_NOT_CONVERGED;
-                s->stop_after_xp = 1;
-            }
+    if (threadIdx.x == 0) {
+        part_rr[blockIdx.x] = bs;
+        if (blockIdx.x == 0) {
+            s->alpha = alpha;
+            s->alpha32 = float(alpha);
+            s->pq = pq;
         }
     }
 }
 
-// x <- x + alpha p; p <- r + beta p (Algorithm 3 lines 4 and 8).
+// Algorithm 3 lines 4, 7, 8 (M = I): every block sums the partials of
+// (r_{k+1}, r_{k+1})_w, forms beta, and x <- x + alpha p, p <- r + beta p;
+// block 0 records the iteration and the stopping decision (recursive
+// residual <= rtol ||b||, or max_iter reached), applied after this update.
 __global__ void __launch_bounds__(kBlock) k_update_xp(int64_t N, double *__restrict__ x, double *__restrict__ p,
-                                                      const double *__restrict__ r, double *partials, Scal *s,
-                                                      cudaGraphConditionalHandle h, int use_cond) {
+                                                      const double *__restrict__ r, const double *part_rr, int G2,
+                                                      Scal *s, cudaGraphConditionalHandle h, int use_cond) {
     pdl_enter();
-    if (s->done) return;
-    const double alpha = s->alpha, beta = s->beta;
+    const int k = s->iter_b;
+    if (s->brk || s->halt[k & 1]) return;
+    const double rr = all_sum_partials(part_rr, G2);
+    const double alpha = s->alpha, beta = rr / s->rho_b;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N2 = N >> 1;
     double2 *x2 = reinterpret_cast<double2 *>(x);
@@ -529,10 +561,18 @@ __global__ void __launch_bounds__(kBlock) k_update_xp(int64_t N, double *__restr
         x[N - 1] = fma(alpha, pi, x[N - 1]);
         p[N - 1] = fma(beta, pi, r[N - 1]);
     }
-    if (publish_and_check_last(partials, 0.0, &s->ticket[kTicketXP])) {
-        if (threadIdx.x == 0) {
-            s->ticket[kTicketXP] = 0;
-            if (s->stop_after_xp) stop_loop(s, h, use_cond);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s->rho = rr;
+        s->beta = beta;
+        s->iter = k + 1;
+        s->relres = s->bnorm > 0.0 ? sqrt(rr) / s->bnorm : 0.0;
+        int stop = 1;
+        if (sqrt(rr) <= s->rtol * s->bnorm) s->status = SSG_OK;
+        else if (k + 1 >= s->max_iter) s->status = SSG_E_NOT_CONVERGED;
+        else stop = 0;
+        if (stop) {
+            s->halt[(k + 1) & 1] = 1;
+            stop_loop(s, h, use_cond);
         }
     }
 }
@@ -571,6 +611,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t N, const double *__r
             s->total = 0;
             s->done = 0;
             s->stop_after_xp = 0;
+            s->brk = 0;
+            s->halt[1] = 0;
             s->alpha = 0.0;
             s->beta = 0.0;
             s->relres = s->bnorm > 0.0 ? sqrt(rr) / s->bnorm : 0.0;
@@ -583,6 +625,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t N, const double *__r
                 stop = 1;
             }
             s->done = stop;
+            s->halt[0] = stop;
             if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
         }
     }
@@ -677,23 +720,44 @@ __global__ void __launch_bounds__(kBlock) k_inner_init(int64_t N, const double *
             si->stop_after_xp = 0;
             const int stop = !(tot > 0.0) || so->total >= so->max_iter;
             si->done = stop;
+            si->brk = 0;
+            si->halt[0] = stop;
+            si->halt[1] = 0;
             if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
         }
     }
 }
 
-// r32 <- r32 - alpha q32 and (r32, r32)_w (products and block sums in
-// FP32, grid sum in FP64); the last block forms beta and the inner stopping
-// decision.  A warp covers the 128 entries of flag group i >> 5 (float4 per
-// lane); groups without interface copies skip the weights.
+// Inner Algorithm 3 lines 3 and 5 in FP32: every block sums the FP32 SpMV's
+// partials of (p, S p)_w (FP64), forms alpha (or stops on a breakdown), then
+// r32 <- r32 - alpha q32 and its share of (r32, r32)_w (products and block
+// sums in FP32).  A warp covers the 128 entries of flag group i >> 5 (float4
+// per lane); groups without interface copies skip the weights.
 __global__ void __launch_bounds__(kBlock) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
                                                        const uint8_t *__restrict__ mult,
                                                        const float *__restrict__ wtab,
-                                                       const uint8_t *__restrict__ gflag128, double *partials,
-                                                       Scal *si, Scal *so) {
+                                                       const uint8_t *__restrict__ gflag128, const double *part_pq,
+                                                       int G1, double *part_rr, Scal *si, const Scal *so,
+                                                       cudaGraphConditionalHandle h, int use_cond) {
     pdl_enter();
-    if (si->done) return;
-    const float alpha = si->alpha32;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        si->rho_b = si->rho;
+        si->iter_b = si->iter;
+        si->total_b = so->total;
+    }
+    if (si->brk || si->halt[si->iter & 1]) return;
+    const double pq = all_sum_partials(part_pq, G1);
+    if (!(pq > 0.0) || !isfinite(pq)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            si->pq = pq;
+            si->status = SSG_E_BREAKDOWN;
+            si->brk = 1;
+            stop_loop(si, h, use_cond);
+        }
+        return;
+    }
+    const double alpha_d = si->rho / pq;
+    const float alpha = float(alpha_d);
     float acc = 0.f;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N4 = N >> 2;
@@ -728,27 +792,32 @@ __global__ void __launch_bounds__(kBlock) k_update_r32(int64_t N, float *__restr
         acc = fmaf(__ldg(wtab + mult[i]) * ri, ri, acc);
     }
     const double bs = double(block_sumf(acc));
-    if (publish_and_check_last(partials, bs, &si->ticket[kTicketR])) {
-        const double tot = sum_partials(partials, gridDim.x);
-        if (threadIdx.x == 0) {
-            si->ticket[kTicketR] = 0;
-            si->beta = tot / si->rho;
-            si->beta32 = float(si->beta);
-            si->rho = tot;
-            si->iter += 1;
-            so->total += 1;
-            if (sqrt(tot) <= si->tau * sqrt(si->rho0) || so->total >= so->max_iter) si->stop_after_xp = 1;
+    if (threadIdx.x == 0) {
+        part_rr[blockIdx.x] = bs;
+        if (blockIdx.x == 0) {
+            si->alpha = alpha_d;
+            si->alpha32 = alpha;
+            si->pq = pq;
         }
     }
 }
 
-// d32 <- d32 + alpha p32; p32 <- r32 + beta p32.
+// Inner Algorithm 3 lines 4, 7, 8 in FP32: every block sums the partials of
+// (r32, r32)_w, forms beta, and d32 <- d32 + alpha p32, p32 <- r32 + beta p32;
+// block 0 records the iteration and the inner stopping decision
+// (sqrt(rho) <= tau sqrt(rho0), or the inner iterations summed over
+// refinements reach max_iter).
 __global__ void __launch_bounds__(kBlock) k_update_dp32(int64_t N, float *__restrict__ d, float *__restrict__ p,
-                                                        const float *__restrict__ r, double *partials, Scal *si,
-                                                        cudaGraphConditionalHandle h, int use_cond) {
+                                                        const float *__restrict__ r, const double *part_rr, int G2,
+                                                        Scal *si, Scal *so, cudaGraphConditionalHandle h,
+                                                        int use_cond) {
     pdl_enter();
-    if (si->done) return;
-    const float alpha = si->alpha32, beta = si->beta32;
+    const int k = si->iter_b;
+    if (si->brk || si->halt[k & 1]) return;
+    const double rr = all_sum_partials(part_rr, G2);
+    const double beta_d = rr / si->rho_b;
+    const float alpha = si->alpha32, beta = float(beta_d);
+    const int total1 = si->total_b + 1;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N4 = N >> 2;
     float4 *__restrict__ d4 = reinterpret_cast<float4 *>(d);
@@ -772,10 +841,15 @@ __global__ void __launch_bounds__(kBlock) k_update_dp32(int64_t N, float *__rest
         d[i] = fmaf(alpha, pi, d[i]);
         p[i] = fmaf(beta, pi, r[i]);
     }
-    if (publish_and_check_last(partials, 0.0, &si->ticket[kTicketXP])) {
-        if (threadIdx.x == 0) {
-            si->ticket[kTicketXP] = 0;
-            if (si->stop_after_xp) stop_loop(si, h, use_cond);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        si->rho = rr;
+        si->beta = beta_d;
+        si->beta32 = beta;
+        si->iter = k + 1;
+        so->total = total1;
+        if (sqrt(rr) <= si->tau * sqrt(si->rho0) || total1 >= so->max_iter) {
+            si->halt[(k + 1) & 1] = 1;
+            stop_loop(si, h, use_cond);
         }
     }
 }
