@@ -60,6 +60,8 @@ def parse_args(argv=None):
                          "Both stop on an FP64 relative residual of 1e-8; the other mode is timed too and reported")
     ap.add_argument("--pdl", choices=("on", "off"), default="off",
                     help="programmatic dependent launch for the per-iteration update kernels")
+    ap.add_argument("--profile-spmv", choices=("fp64", "fp32"), default=None,
+                    help="only build the workload and launch the SpMV --spmv-reps times (for ncu); no JSON line")
     ap.add_argument("--driver", choices=("graph", "host"), default="graph",
                     help="graph: one CUDA graph per solve (timed default); host: same kernels launched from a "
                          "host loop (for profilers that cannot see kernels inside conditional graphs)")
@@ -345,6 +347,12 @@ def run_ours(args, dist):
     stream = torch.cuda.current_stream(dev)
     prob = make_workload()
     ctx = Context(dev, stream)
+    if args.profile_spmv:
+        S = System(ctx, prob.A, prob.part, prob.P)
+        time_spmv(S, args.profile_spmv, stream, args.spmv_reps)
+        S.close()
+        ctx.close()
+        return 0
     if args.driver == "host":
         ctx.set_driver(ssg.SSG_DRIVER_HOST)
     ctx.set_pdl(args.pdl == "on")
