@@ -4,7 +4,7 @@
  * Cheik Ahamed & Magoules, "Parallel Sub-Structuring Methods for solving
  * Sparse Linear Systems on a cluster of GPU".  The problem statement the ABI
  * follows: a sparse symmetric positive-definite system S u = f in CSR form
- * (Section 2.2, Section 2.4 Eq. linear_systems) is split into sub-structures
+ * (Section 1.2, Section 2.4 Eq. linear_systems) is split into sub-structures
  * (Section 2.4: local matrices S_i whose interface blocks sum to S_33,
  * Eq. mat_subdomains / interface_summation) and solved with the Conjugate
  * Gradient (Algorithm 3) whose SpMV is the two-step local product plus

@@ -115,6 +115,12 @@ def _bind(L):
         L.or_sub_cg_mixed.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int32, C.c_double, C.c_int32,
                                       C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)]
         L.or_sub_cg_mixed.restype = C.c_int
+        L.or_pcg.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_double, C.c_int32,
+                             C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+        L.or_pcg.restype = C.c_int
+        L.or_sub_pcg.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int32, C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_double)]
+        L.or_sub_pcg.restype = C.c_int
         L.or_cholesky_solve.argtypes = [C.c_int32, _f64p, _f64p, _f64p]
         L.or_cholesky_solve.restype = C.c_int
     return L
@@ -125,7 +131,7 @@ def _c(a, dt):
 
 
 def spmv(A, x):
-    """Global CSR product y = A x (Section 2.2 storage, rows summed left to right)."""
+    """Global CSR product y = A x (Section 1.2 storage, rows summed left to right)."""
     x = _c(x, np.float64)
     y = np.empty(A.n, np.float64)
     lib().or_spmv(A.n, _c(A.rowptr, np.int32), _c(A.colidx, np.int32), _c(A.val, np.float64), x, y)
@@ -287,6 +293,38 @@ def _spmv32(self, xl):
 
 
 Partition.spmv32 = _spmv32
+
+
+@dataclass
+class PCGResult:
+    x: np.ndarray
+    status: int
+    iters: int
+    relres: float
+
+
+def pcg(A, b, rtol, max_iter, x0=None) -> PCGResult:
+    """Algorithm 3 with M = diag(A) on the global matrix (ssg_oracle.c: or_pcg)."""
+    b = _c(b, np.float64).ravel()
+    x = np.zeros(A.n) if x0 is None else _c(x0, np.float64).ravel().copy()
+    it = C.c_int32()
+    rr = C.c_double()
+    st = lib().or_pcg(A.n, _c(A.rowptr, np.int32), _c(A.colidx, np.int32), _c(A.val, np.float64), b, x, rtol,
+                      max_iter, C.byref(it), C.byref(rr))
+    return PCGResult(x, st, it.value, rr.value)
+
+
+def _sub_pcg(self, b, rtol, max_iter, x0=None) -> PCGResult:
+    """Sub-structured Algorithm 3 with M = diag(S) (ssg_oracle.c: or_sub_pcg)."""
+    b = _c(b, np.float64).ravel()
+    x = np.zeros(self.maps.n) if x0 is None else _c(x0, np.float64).ravel().copy()
+    it = C.c_int32()
+    rr = C.c_double()
+    st = self._L.or_sub_pcg(self.h, b, x, rtol, max_iter, C.byref(it), C.byref(rr))
+    return PCGResult(x, st, it.value, rr.value)
+
+
+Partition.pcg = _sub_pcg
 
 
 def cholesky_solve(Adense, b):

@@ -10,7 +10,7 @@
  *
  * What it computes, by paper section:
  *   or_spmv          global CSR product y = A x, rows in order, each row summed
- *                    left to right (CSR storage, Section 2.2).
+ *                    left to right (CSR storage, Section 1.2).
  *   or_cg            Algorithm 3 (Conjugate Gradient) with M = I on the global
  *                    CSR, x1 = x0, stopping on the recursive residual.
  *   or_partition     the sub-structure data of Section 2.4: local matrices S_i
@@ -40,7 +40,7 @@
 #define OR_NOT_CONVERGED 5
 
 /* ------------------------------------------------------------------ */
-/* Global CSR product (Section 2.2).                                   */
+/* Global CSR product (Section 1.2).                                   */
 /* ------------------------------------------------------------------ */
 void or_spmv(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, const double *x,
              double *y) {
@@ -617,5 +617,148 @@ int or_sub_cg_mixed(const or_part *h, const double *b, double *x, double rtol, i
     *outer_out = outer;
     *relres_out = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;
     free(bl); free(xl); free(r); free(q); free(val32); free(r32); free(p32); free(q32); free(d32);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 3 with the diagonal preconditioner M = diag(S).           */
+/* ------------------------------------------------------------------ */
+/*
+ * Algorithm 3 with the preconditioner the paper's experiments use, the
+ * diagonal of the matrix (Section 3.1): z = M^{-1} r = r / diag(S),
+ * alpha = (z, r) / (S p, p), beta = (r_{k+1}, z_{k+1}) / (r_k, z_k),
+ * p = z + beta p.  Reading: the stopping test stays on the recursive residual
+ * sqrt((r, r)) <= rtol ||b|| (the paper gives none), so both (r, z) and
+ * (r, r) are formed each iteration.  A missing or non-positive diagonal
+ * entry is invalid input.
+ */
+int or_pcg(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, const double *b, double *x,
+           double rtol, int32_t max_iter, int32_t *iters_out, double *relres_out) {
+    size_t N = (size_t)(n > 0 ? n : 1);
+    double *d = (double *)malloc(sizeof(double) * N), *r = (double *)malloc(sizeof(double) * N);
+    double *z = (double *)malloc(sizeof(double) * N), *p = (double *)malloc(sizeof(double) * N);
+    double *q = (double *)malloc(sizeof(double) * N);
+    if (!d || !r || !z || !p || !q) {
+        free(d); free(r); free(z); free(p); free(q);
+        return OR_OOM;
+    }
+    int status = OR_NOT_CONVERGED;
+    for (int32_t i = 0; i < n; ++i) {
+        d[i] = 0.0;
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            if (colidx[k] == i) d[i] = val[k];
+        if (!(d[i] > 0.0)) status = OR_INVALID;
+    }
+    if (status == OR_INVALID) {
+        free(d); free(r); free(z); free(p); free(q);
+        return OR_INVALID;
+    }
+    or_spmv(n, rowptr, colidx, val, x, q);
+    for (int32_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    for (int32_t i = 0; i < n; ++i) z[i] = r[i] / d[i];
+    for (int32_t i = 0; i < n; ++i) p[i] = z[i];
+    double rz = dot_plain(n, r, z), rr = dot_plain(n, r, r);
+    const double bnorm = sqrt(dot_plain(n, b, b));
+    int32_t k = 0;
+    if (sqrt(rr) <= rtol * bnorm) status = OR_OK;
+    while (status == OR_NOT_CONVERGED && k < max_iter) {
+        or_spmv(n, rowptr, colidx, val, p, q);
+        const double pq = dot_plain(n, q, p);
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            status = OR_BREAKDOWN;
+            break;
+        }
+        const double alpha = rz / pq;
+        for (int32_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+        for (int32_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
+        for (int32_t i = 0; i < n; ++i) z[i] = r[i] / d[i];
+        const double rz_new = dot_plain(n, r, z);
+        rr = dot_plain(n, r, r);
+        const double beta = rz_new / rz;
+        for (int32_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        rz = rz_new;
+        ++k;
+        if (sqrt(rr) <= rtol * bnorm) status = OR_OK;
+    }
+    *iters_out = k;
+    *relres_out = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+    free(d); free(r); free(z); free(p); free(q);
+    return status;
+}
+
+/* The assembled diagonal of S at every local entry: node i's diagonal entry
+ * lies in the local matrix of part(i), row own[i], local column own[i] - off. */
+static int local_diagonal(const or_part *h, double *dl) {
+    double *dg = (double *)malloc(sizeof(double) * (size_t)(h->n > 0 ? h->n : 1));
+    if (!dg) return OR_OOM;
+    for (int32_t i = 0; i < h->n; ++i) {
+        const int32_t k = h->own[i];
+        int32_t s = 0;
+        while (h->off[s + 1] <= k) ++s;
+        dg[i] = 0.0;
+        for (int32_t e = h->lrowptr[k]; e < h->lrowptr[k + 1]; ++e)
+            if (h->lcol[e] == k - h->off[s]) dg[i] = h->lval[e];
+        if (!(dg[i] > 0.0)) {
+            free(dg);
+            return OR_INVALID;
+        }
+    }
+    for (int64_t k = 0; k < h->nloc; ++k) dl[k] = dg[h->l2g[k]];
+    free(dg);
+    return OR_OK;
+}
+
+/* or_pcg on the sub-structured operator with weighted dots (Section 3.4). */
+int or_sub_pcg(const or_part *h, const double *b, double *x, double rtol, int32_t max_iter, int32_t *iters_out,
+               double *relres_out) {
+    size_t N = (size_t)(h->nloc > 0 ? h->nloc : 1);
+    const int64_t L = h->nloc;
+    double *dl = (double *)malloc(sizeof(double) * N), *bl = (double *)malloc(sizeof(double) * N);
+    double *xl = (double *)malloc(sizeof(double) * N), *r = (double *)malloc(sizeof(double) * N);
+    double *z = (double *)malloc(sizeof(double) * N), *p = (double *)malloc(sizeof(double) * N);
+    double *q = (double *)malloc(sizeof(double) * N);
+    if (!dl || !bl || !xl || !r || !z || !p || !q) {
+        free(dl); free(bl); free(xl); free(r); free(z); free(p); free(q);
+        return OR_OOM;
+    }
+    int status = local_diagonal(h, dl);
+    if (status != OR_OK) {
+        free(dl); free(bl); free(xl); free(r); free(z); free(p); free(q);
+        return status;
+    }
+    status = OR_NOT_CONVERGED;
+    or_scatter(h, b, bl);
+    or_scatter(h, x, xl);
+    or_sub_spmv(h, xl, q);
+    for (int64_t k = 0; k < L; ++k) r[k] = bl[k] - q[k];
+    for (int64_t k = 0; k < L; ++k) z[k] = r[k] / dl[k];
+    for (int64_t k = 0; k < L; ++k) p[k] = z[k];
+    double rz = or_wdot(h, r, z), rr = or_wdot(h, r, r);
+    const double bnorm = sqrt(or_wdot(h, bl, bl));
+    int32_t it = 0;
+    if (sqrt(rr) <= rtol * bnorm) status = OR_OK;
+    while (status == OR_NOT_CONVERGED && it < max_iter) {
+        or_sub_spmv(h, p, q);
+        const double pq = or_wdot(h, q, p);
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            status = OR_BREAKDOWN;
+            break;
+        }
+        const double alpha = rz / pq;
+        for (int64_t k = 0; k < L; ++k) xl[k] = xl[k] + alpha * p[k];
+        for (int64_t k = 0; k < L; ++k) r[k] = r[k] - alpha * q[k];
+        for (int64_t k = 0; k < L; ++k) z[k] = r[k] / dl[k];
+        const double rz_new = or_wdot(h, r, z);
+        rr = or_wdot(h, r, r);
+        const double beta = rz_new / rz;
+        for (int64_t k = 0; k < L; ++k) p[k] = z[k] + beta * p[k];
+        rz = rz_new;
+        ++it;
+        if (sqrt(rr) <= rtol * bnorm) status = OR_OK;
+    }
+    or_gather(h, xl, x);
+    *iters_out = it;
+    *relres_out = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+    free(dl); free(bl); free(xl); free(r); free(z); free(p); free(q);
     return status;
 }

@@ -4,7 +4,7 @@ Every generator is deterministic for a given ``numpy.random.Generator`` state
 (PCG64).  The matrices are the discretised model problem of Section 2.4
 (Eq. model_problem / linear_systems: an elliptic operator with homogeneous
 Dirichlet data gives a sparse symmetric positive-definite S), in CSR form as
-described in Section 2.2 (values, column indices, row pointers), but 0-based
+described in Section 1.2 (values, column indices, row pointers), but 0-based
 with int32 indices and float64 values.
 
 Symmetry is exact: every off-diagonal value is computed once per edge/face and

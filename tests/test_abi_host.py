@@ -109,7 +109,7 @@ def test_invalid_inputs():
         ssg.ssg_partition(None, A.n, A.rowptr, c, A.val, part, 1)
     with pytest.raises(ssg.SSGError):
         ssg.ssg_partition(None, A.n, A.rowptr, A.colidx, A.val, part, 0)
-    # the non-symmetric worked example of Section 2.2
+    # the non-symmetric worked example of Section 1.2
     ex = CSR(5, np.array([0, 2, 4, 6, 9, 11], np.int32), np.array([0, 1, 1, 2, 0, 2, 1, 3, 4, 2, 4], np.int32),
              np.array([-5, 14, 8, 1, 2, 10, 4, 2, 9, 15, 7], np.float64))
     with pytest.raises(ssg.SSGError):

@@ -15,7 +15,11 @@ P6  tiny SPD systems: CG to 1e-12 matches a dense Cholesky solve (oracle's own
 P7  finite termination: A = I in one step, d distinct eigenvalues in <= d
     steps, the 1D Laplacian of size n in <= n steps.
 P8  manufactured solution recovered within 2*kappa*rtol.
-P9  the worked 5x5 CSR example of Section 2.2.
+P9  the worked 5x5 CSR example of Section 1.2.
+P10 Algorithm 3 with the diagonal preconditioner M = diag(S): a diagonal S is
+    solved in one iteration; one subdomain equals the global PCG bit for bit;
+    k iterations equal k iterations of plain CG on D^-1/2 S D^-1/2 mapped
+    back by D^-1/2 (global and sub-structured); agreement with Cholesky.
 Planted mistakes: textual mutations of the oracle's C source must each break
 at least one pin.
 """
@@ -227,7 +231,7 @@ def pin_manufactured(A, part, P, xs, b, rtol):
 
 # ---------------------------------------------------------------- tests
 def test_csr_example_5x5():
-    """P9: the 5x5 example of Section 2.2, encoded and multiplied."""
+    """P9: the 5x5 example of Section 1.2, encoded and multiplied."""
     lines = [l.split() for l in open(os.path.join(GOLDEN, "csr_example_5x5.txt")) if l.strip() and l[0] != "#"]
     i = lines.index(["dense"])
     dense = np.array([[float(v) for v in lines[i + 1 + r]] for r in range(5)])
@@ -368,8 +372,8 @@ MUTATIONS = {
     # off-diagonal entries owned by the higher subdomain, interface entries counted twice
     "double_owner": ("return part[i] < part[j] ? part[i] : part[j];", "return part[i];"),
     # wrong sign in the residual update
-    "residual_sign": ("for (int64_t k = 0; k < L; ++k) r[k] = r[k] - alpha * q[k];",
-                      "for (int64_t k = 0; k < L; ++k) r[k] = r[k] + alpha * q[k];"),
+    "residual_sign": ("for (int64_t k = 0; k < L; ++k) r[k] = r[k] - alpha * q[k];\n        double rho_new",
+                      "for (int64_t k = 0; k < L; ++k) r[k] = r[k] + alpha * q[k];\n        double rho_new"),
     # row index used where the column index belongs in the local product
     "wrong_index": ("acc += h->lval[k] * xl[o + h->lcol[k]];", "acc += h->lval[k] * xl[o + li];"),
     # inverted ratio for the new direction
@@ -412,6 +416,170 @@ def test_planted_mistake_is_caught(name):
     finally:
         os.remove(path)
     assert failures, "planted mistake %s slipped through every pin" % name
+
+
+# ---------------------------------------------------------------- P10: diagonal preconditioner
+def _diag(A):
+    return np.array([A.val[A.rowptr[i]:A.rowptr[i + 1]][A.colidx[A.rowptr[i]:A.rowptr[i + 1]] == i][0]
+                     for i in range(A.n)])
+
+
+def _sym_scaled(A):
+    """D^-1/2 A D^-1/2 with D = diag(A), entry by entry."""
+    s = 1.0 / np.sqrt(_diag(A))
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    return CSR(A.n, A.rowptr, A.colidx, A.val * (s[rows] * s[A.colidx])), s
+
+
+def pin_pcg_diagonal():
+    """M = S for a diagonal S: z_1 = S^-1 b, so one iteration solves it."""
+    rng = np.random.default_rng(21)
+    n = 90
+    d = rng.uniform(0.5, 50.0, n)
+    Dg = CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), d)
+    b = rng.uniform(-1, 1, n)
+    part = rng.integers(0, 4, n).astype(np.int32)
+    for r in (oracle.pcg(Dg, b, 1e-12, 10), oracle.Partition(Dg, part, 4).pcg(b, 1e-12, 10)):
+        assert r.status == oracle.OK and r.iters == 1
+        assert np.all(np.abs(r.x - b / d) <= 4 * U * np.abs(b / d))
+
+
+def pin_pcg_p1_bitwise(A, b):
+    Pt = oracle.Partition(A, np.zeros(A.n, np.int32), 1)
+    r1 = Pt.pcg(b, 1e-10, 5 * A.n)
+    r0 = oracle.pcg(A, b, 1e-10, 5 * A.n)
+    assert r1.status == r0.status == oracle.OK and r1.iters == r0.iters
+    assert np.array_equal(r1.x, r0.x)
+
+
+def pin_pcg_scaled_equivalence(A, part, P, k=6, seed=8):
+    """Jacobi-preconditioned CG on S is plain CG on D^-1/2 S D^-1/2 in the
+    variable D^1/2 x: after k iterations both give the same x up to rounding."""
+    b = np.random.default_rng(seed).uniform(-1, 1, A.n)
+    Ah, s = _sym_scaled(A)
+    xh = oracle.cg(Ah, s * b, 0.0, k).x
+    x_ref = s * xh
+    scale = np.linalg.norm(x_ref)
+    xg = oracle.pcg(A, b, 0.0, k).x
+    assert np.linalg.norm(xg - x_ref) <= 1e-10 * scale
+    Pt = oracle.Partition(A, part, P)
+    xs = Pt.pcg(b, 0.0, k).x
+    assert np.linalg.norm(xs - x_ref) <= 1e-10 * scale
+    xsh = oracle.Partition(Ah, part, P).cg(s * b, 0.0, k).x
+    assert np.linalg.norm(xs - s * xsh) <= 1e-10 * scale
+
+
+def pin_pcg_cholesky(A, part, P, seed=5):
+    b = np.random.default_rng(seed).uniform(-1, 1, A.n)
+    x_chol = oracle.cholesky_solve(_dense(A), b)
+    r = oracle.Partition(A, part, P).pcg(b, 1e-12, 20 * A.n)
+    assert r.status == oracle.OK
+    assert np.linalg.norm(r.x - x_chol) <= 1e-10 * np.linalg.norm(x_chol)
+
+
+def _run_pcg_pins():
+    failures = []
+    checks = [
+        ("pcg_diagonal", pin_pcg_diagonal),
+        ("pcg_scaled", lambda: [pin_pcg_scaled_equivalence(*c[1:]) for c in SMALL[:4]]),
+        ("pcg_cholesky", lambda: [pin_pcg_cholesky(*c[1:]) for c in SMALL[:4]]),
+    ]
+    for name, fn in checks:
+        try:
+            fn()
+        except Exception as e:  # noqa: BLE001 - any failure counts as caught
+            failures.append((name, type(e).__name__))
+    return failures
+
+
+def test_pcg_diagonal_one_step():
+    pin_pcg_diagonal()
+
+
+def test_pcg_single_subdomain_is_global_pcg():
+    A = fv3d_7pt(6, 5, 7, np.exp(np.random.default_rng(4).standard_normal((7, 5, 6))))
+    pin_pcg_p1_bitwise(A, np.random.default_rng(2).uniform(-1, 1, A.n))
+
+
+@pytest.mark.parametrize("case", SMALL, ids=[c[0] for c in SMALL])
+def test_pcg_scaled_equivalence(case):
+    _, A, part, P = case
+    pin_pcg_scaled_equivalence(A, part, P)
+
+
+@pytest.mark.parametrize("case", SMALL, ids=[c[0] for c in SMALL])
+def test_pcg_matches_cholesky(case):
+    _, A, part, P = case
+    pin_pcg_cholesky(A, part, P)
+
+
+def test_pcg_manufactured_and_fewer_iterations():
+    """On the heterogeneous FV problem the diagonal preconditioner removes the
+    kappa scaling: it converges in fewer iterations, the true residual is
+    <= rtol (to rounding), and ||x - x*|| / ||x*|| <= cond(S) ||r|| / ||b||."""
+    p = config_problem(2, scale=24)
+    b = p.b[:, 0]
+    Pt = oracle.Partition(p.A, p.part, p.P)
+    r = Pt.pcg(b, 1e-8, 100000)
+    r0 = Pt.cg(b, 1e-8, 100000)
+    assert r.status == oracle.OK and r.iters < 0.7 * r0.iters
+    tr = np.linalg.norm(b - oracle.spmv(p.A, r.x)) / np.linalg.norm(b)
+    assert tr <= 1.01e-8
+    kap = oracle.cond_from_lanczos(r0.alpha, r0.beta)
+    assert np.linalg.norm(r.x - p.xstar[:, 0]) / np.linalg.norm(p.xstar[:, 0]) <= 1.1 * kap * tr
+
+
+def test_pcg_rejects_missing_diagonal():
+    n = 6
+    # a symmetric matrix whose row 2 stores no diagonal entry
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        if i != 2:
+            rows.append(i), cols.append(i), vals.append(4.0)
+        if i + 1 < n:
+            rows += [i, i + 1]
+            cols += [i + 1, i]
+            vals += [-1.0, -1.0]
+    import scipy.sparse as sp
+
+    M = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+    M.sort_indices()
+    A = CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64))
+    assert oracle.pcg(A, np.ones(n), 1e-10, 10).status == oracle.INVALID
+
+
+PCG_MUTATIONS = {
+    # z = M r instead of M^-1 r
+    "pcg_times_diag": ("        for (int64_t k = 0; k < L; ++k) z[k] = r[k] / dl[k];\n        const double rz_new",
+                       "        for (int64_t k = 0; k < L; ++k) z[k] = r[k] * dl[k];\n        const double rz_new"),
+    # the new direction built from r instead of z
+    "pcg_direction_from_r": ("for (int64_t k = 0; k < L; ++k) p[k] = z[k] + beta * p[k];",
+                             "for (int64_t k = 0; k < L; ++k) p[k] = r[k] + beta * p[k];"),
+    # beta from the unpreconditioned residual norms
+    "pcg_beta_from_rr": ("        const double rz_new = or_wdot(h, r, z);\n        rr = or_wdot(h, r, r);",
+                         "        rr = or_wdot(h, r, r);\n        const double rz_new = rr;"),
+    # the diagonal taken from the local copy, which lacks the other copies' share
+    "pcg_local_diagonal": ("for (int64_t k = 0; k < h->nloc; ++k) dl[k] = dg[h->l2g[k]];",
+                           "for (int64_t k = 0; k < h->nloc; ++k) dl[k] = h->lrowptr[k + 1] > h->lrowptr[k] ? dg[h->l2g[k]] * (h->own[h->l2g[k]] == k ? 1.0 : 0.5) : 1.0;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PCG_MUTATIONS))
+def test_pcg_planted_mistake_is_caught(name):
+    old, new = PCG_MUTATIONS[name]
+    src = oracle.source_text()
+    assert src.count(old) == 1, "mutation anchor not found: %s" % name
+    path = oracle.compile_variant(src.replace(old, new), name)
+    try:
+        with oracle.use_library(path):
+            failures = _run_pcg_pins()
+    finally:
+        os.remove(path)
+    assert failures, "planted mistake %s slipped through every pin" % name
+
+
+def test_pcg_pins_pass_on_oracle():
+    assert _run_pcg_pins() == []
 
 
 # ---------------------------------------------------------------- mixed precision (library mode SSG_MIXED)
