@@ -62,6 +62,8 @@ def parse_args(argv=None):
                     help="programmatic dependent launch for the per-iteration update kernels")
     ap.add_argument("--profile-spmv", choices=("fp64", "fp32"), default=None,
                     help="only build the workload and launch the SpMV --spmv-reps times (for ncu); no JSON line")
+    ap.add_argument("--no-multi-rhs", action="store_true",
+                    help="skip the 16-right-hand-side measurement (96^3 FV, reported beside the headline)")
     ap.add_argument("--driver", choices=("graph", "host"), default="graph",
                     help="graph: one CUDA graph per solve (timed default); host: same kernels launched from a "
                          "host loop (for profilers that cannot see kernels inside conditional graphs)")
@@ -229,6 +231,89 @@ def time_spmv(S, prec, stream, reps):
     k1.record(stream)
     torch.cuda.synchronize()
     return k0.elapsed_time(k1) / 1e3 / reps
+
+
+def spmm_algorithmic_bytes(sizes, k: int, vb: int = 8) -> int:
+    """The SpMV bytes with k vectors: the matrix and index arrays once, the x
+    and y blocks (k values per local entry) once each."""
+    return ((vb + 4) * sizes.nnz + 4 * (sizes.nloc + 1) + 2 * vb * k * sizes.nloc + 4 * sizes.ncopies
+            + 4 * (sizes.ngamma + 1))
+
+
+def time_spmm(S, prec, k, stream, reps):
+    """Average duration of one k-vector product launch (CUDA events on its stream)."""
+    import torch
+
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    xl = torch.rand((S.sizes.nloc, k), dtype=torch.float64, device="cuda").to(dt)
+    y = torch.empty_like(xl)
+    for _ in range(3):
+        S.spmm(xl, y)
+    torch.cuda.synchronize()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        S.spmm(xl, y)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    return k0.elapsed_time(k1) / 1e3 / reps
+
+
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (no FP64 figure is measured on this pool)
+
+
+def bench_multi_rhs(ctx, stream, reps, spmv_reps):
+    """The 16-right-hand-side workload (96^3 FV, 27 subdomains): time to 1e-8
+    for all 16 with the columns iterating together (K = 16) and one after
+    another, FP64 and mixed, plus the k-vector product's roofline."""
+    import torch
+
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+    from synth import config_problem
+
+    p = config_problem(5)
+    S = System(ctx, p.A, p.part, p.P)
+    B = torch.from_numpy(p.b.T.copy()).cuda()
+    X = torch.zeros_like(B)
+    out = {"workload": "fv3d_7pt_96^3_kappa=exp(N(0,1))_3x3x3_subdomains_16rhs", "n": p.A.n, "nnz": p.A.nnz,
+           "nloc": S.sizes.nloc, "rhs": B.shape[0], "rtol": RTOL}
+    for mode_name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED)):
+        for kb in (16, 1):
+            ctx.set_rhs_block(kb)
+            X.zero_()
+            ssg.ssg_solve(S.h, B.shape[0], B, X, False, RTOL, 0, mode)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                rc, st = ssg.ssg_solve(S.h, B.shape[0], B, X, False, RTOL, 0, mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rc != ssg.SSG_OK:
+                raise RuntimeError("16-RHS solve did not converge: %r" % st)
+            key = "%s_%s" % (mode_name, "together" if kb == 16 else "one_by_one")
+            out[key + "_s"] = e0.elapsed_time(e1) / 1e3 / reps
+            out[key + "_iters_max"] = max(s["iters"] for s in st)
+            out[key + "_true_relres_max"] = max(s["true_relres"] for s in st)
+            out[key + "_launches"] = sum(s["kernel_launches"] for s in st) if kb == 1 else st[0]["kernel_launches"]
+    ctx.set_rhs_block(16)
+    peak, peak_src = measured_peaks()
+    flops = 2.0 * p.A.nnz * 16
+    t64 = time_spmm(S, "fp64", 16, stream, spmv_reps)
+    t32 = time_spmm(S, "fp32", 16, stream, spmv_reps)
+    nb32 = spmm_algorithmic_bytes(S.sizes, 16, 4)
+    out["spmm_fp64_k16"] = {"bound": "alu", "achieved": flops / t64 / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                            "unit": "TFLOP/s", "frac": flops / t64 / 1e12 / FP64_NOMINAL_TFLOPS,
+                            "peak_source": "nominal FP64 rate", "launch_us": t64 * 1e6,
+                            "hbm_gbs": spmm_algorithmic_bytes(S.sizes, 16, 8) / t64 / 1e9}
+    out["spmm_fp32_k16"] = {"bound": "hbm", "achieved": nb32 / t32 / 1e9, "peak": peak, "unit": "GB/s",
+                            "frac": nb32 / t32 / 1e9 / peak, "peak_source": peak_src, "launch_us": t32 * 1e6,
+                            "algorithmic_bytes": nb32}
+    S.close()
+    return out
 
 
 def measured_peaks():
@@ -432,6 +517,9 @@ def run_ours(args, dist):
             "launch_us": spmv_s * 1e6,
         }
     dominant = "fp32" if args.mode == "mixed" else "fp64"
+    multi = None
+    if not args.no_multi_rhs:
+        multi = bench_multi_rhs(ctx, stream, max(1, min(args.steps, 3)), args.spmv_reps)
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
@@ -481,6 +569,7 @@ def run_ours(args, dist):
         "gpu_launches": int(dist.sum(launches)),
         "clocks": ck,
         "cpu_baseline": cpu,
+        "multi_rhs": multi,
     }
     if dist.rank == 0:
         print(json.dumps(line), flush=True)

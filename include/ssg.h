@@ -73,11 +73,12 @@ typedef struct {
     int32_t status;          /* SSG_OK, SSG_E_BREAKDOWN or SSG_E_NOT_CONVERGED for this right-hand side */
     int32_t iters;           /* CG iterations (mixed mode: inner iterations summed over refinements) */
     int32_t outer;           /* refinement steps (mixed mode); 1 in FP64 mode */
-    int32_t reserved;
+    int32_t block;           /* right-hand sides that iterated together with this one (1, 2, 4, 8 or 16) */
     double relres;           /* final recursive residual sqrt((r,r)_w) / sqrt((b,b)_w) */
     double true_relres;      /* ||b - S x|| / ||b|| recomputed in FP64 after the solve */
-    double solve_ms;         /* device time of this solve (CUDA events on the context stream) */
-    int64_t kernel_launches; /* kernels executed on the device for this solve */
+    double solve_ms;         /* device time of this solve (CUDA events on the context stream); for a
+                                block of right-hand sides, the time of the whole block */
+    int64_t kernel_launches; /* kernels executed on the device for this solve (or block) */
 } ssg_stats;
 
 /*
@@ -104,6 +105,17 @@ int ssg_set_pdl(ssg_ctx *ctx, int enable);
  * SSG_E_INVALID unless 0 < inner_rtol < 1 and max_outer >= 1.
  */
 int ssg_set_mixed(ssg_ctx *ctx, double inner_rtol, int32_t max_outer);
+/*
+ * How many right-hand sides of one ssg_solve call iterate together: kmax =
+ * 1, 2, 4, 8 or 16 (default 16).  A group of k > 1 right-hand sides runs K
+ * Algorithm 3 iterations side by side (K = the power of two >= k, the extra
+ * columns zero), each with its own alpha, beta and stopping test, and reads
+ * the local matrices once per iteration for all of them (the product of
+ * Section 3.4.1 with K vectors).  A right-hand side whose test has passed
+ * stops changing, so each one gets the iterates of its own solve up to the
+ * order of the floating-point sums.  kmax = 1 solves them one after another.
+ */
+int ssg_set_rhs_block(ssg_ctx *ctx, int32_t kmax);
 /* Free a context.  Refused with SSG_E_INVALID (nothing freed) while systems
  * created on it are still alive: destroy those first. */
 int ssg_destroy(ssg_ctx *ctx);
@@ -183,6 +195,20 @@ int ssg_spmv_assembled(ssg_system *sys, const double *x_loc, double *y_loc, doub
 int ssg_spmv_assembled_f32(ssg_system *sys, const float *x_loc, float *y_loc, double *xSx_dev);
 
 /*
+ * The sub-structured product of ssg_spmv_assembled with k vectors at once
+ * (k = 2, 4, 8 or 16): x_loc and y_loc are device blocks of nloc*k doubles,
+ * interleaved (entry i of vector j at i*k + j), aligned to 16 bytes.  The
+ * local matrices are read once for all k vectors; each column of y_loc is
+ * bit-identical to ssg_spmv_assembled of that column (same summation
+ * order).  SSG_E_INVALID for another k, null, aliased or misaligned blocks.
+ */
+int ssg_spmm_assembled(ssg_system *sys, int32_t k, const double *x_loc, double *y_loc);
+/* The same in FP32 (values rounded to FP32 once, FP32 arithmetic; columns
+ * bit-identical to ssg_spmv_assembled_f32); blocks aligned to
+ * min(16, 4k) bytes. */
+int ssg_spmm_assembled_f32(ssg_system *sys, int32_t k, const float *x_loc, float *y_loc);
+
+/*
  * Interface-weighted dot of Section 3.4.2: result = sum_k w_k u_k v_k over the
  * nloc local entries with w_k = 1/m of the entry's node (equals the global dot
  * for consistent vectors).  Device pointers; *result_dev is written on the
@@ -204,6 +230,7 @@ int ssg_wdot(ssg_system *sys, const double *u_loc, const double *v_loc, double *
  * products summed in FP64) on S d = r; max_iter then caps the inner
  * iterations summed over refinements (ssg_set_mixed sets the inner tolerance
  * and the refinement cap).
+ * Groups of up to ssg_set_rhs_block right-hand sides iterate together.
  * stats (host, may be NULL) receives k entries.  Blocks until done.
  * Returns SSG_OK when every right-hand side converged, else the first
  * non-OK per-RHS status (x still holds the last iterates).

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "block.cuh"
 #include "kernels.cuh"
 #include "ssg_internal.h"
 
@@ -35,6 +36,7 @@ struct ssg_ctx {
     int pdl = 0;               // programmatic dependent launch inside the loop bodies (measured: off is faster)
     double inner_rtol = 1e-4;  // SSG_MIXED: inner FP32 CG tolerance
     int32_t max_outer = 30;    // SSG_MIXED: refinement steps cap
+    int32_t rhs_block = 16;    // right-hand sides solved together (1, 2, 4, 8 or 16)
 };
 
 struct ssg_system {
@@ -69,6 +71,24 @@ struct ssg_system {
     cudaGraphExec_t exec_m = nullptr;
     cudaGraphConditionalHandle cond_out = 0, cond_in = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // several right-hand sides together (block.cuh)
+    DevOp opB64{}, opB32{};  // SpMM launches: warp ranges for grid_spmmB64 / grid_spmmB32 blocks
+    int grid_spmmB64 = 0, grid_spmmB32 = 0;
+    struct BlockGraph {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphConditionalHandle c_out = 0, c_in = 0;
+    };
+    struct BlockState {
+        void *mem = nullptr;  // one allocation for kcap columns
+        int kcap = 0;
+        double *bl = nullptr, *xl = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *part = nullptr;
+        float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
+        double *bg = nullptr, *xg = nullptr;  // global staging for ssg_solve_host (n x kcap)
+        ScalB *so = nullptr, *si = nullptr;
+        int gmax = 0;  // largest grid whose partials the loops exchange
+        BlockGraph g64[5], gmx[5];  // by log2 K
+    } blk;
 };
 
 #define SSG_CUDA_TRY(call)                                                                      \
@@ -118,7 +138,8 @@ struct WorkPlan {
     std::vector<int32_t> scol, sseg;
     std::vector<WorkItem> items;
     std::vector<int2> warp_range64, warp_range32;  // per warp of the FP64 / FP32 launch
-    int grid64 = 0, grid32 = 0;
+    std::vector<int2> warp_rangeB64, warp_rangeB32;  // the same for the K-vector products
+    int grid64 = 0, grid32 = 0, gridB64 = 0, gridB32 = 0;
 };
 
 // Cut the item list into one contiguous range of about equal cost per warp
@@ -250,6 +271,10 @@ WorkPlan make_plan(const HostMaps &M, int num_sms) {
     W.grid32 = std::max(1, std::min(per, num_sms * SpmvTraits<float>::kBlocksPerSM));
     W.warp_range64 = cut_ranges(W.items, W.grid64);
     W.warp_range32 = cut_ranges(W.items, W.grid32);
+    W.gridB64 = std::max(1, std::min(per, num_sms * SpmmTraits<double>::kBlocksPerSM));
+    W.gridB32 = std::max(1, std::min(per, num_sms * SpmmTraits<float>::kBlocksPerSM));
+    W.warp_rangeB64 = cut_ranges(W.items, W.gridB64);
+    W.warp_rangeB32 = cut_ranges(W.items, W.gridB32);
     return W;
 }
 
@@ -540,6 +565,8 @@ int upload(ssg_system *S) {
     size_t i_items = add(plan.items.data(), sizeof(WorkItem) * plan.items.size());
     size_t i_brange = add(plan.warp_range64.data(), sizeof(int2) * plan.warp_range64.size());
     size_t i_brange32 = add(plan.warp_range32.data(), sizeof(int2) * plan.warp_range32.size());
+    size_t i_brangeB64 = add(plan.warp_rangeB64.data(), sizeof(int2) * plan.warp_rangeB64.size());
+    size_t i_brangeB32 = add(plan.warp_rangeB32.data(), sizeof(int2) * plan.warp_rangeB32.size());
     size_t i_iptr = add(M.iptr.data(), sizeof(int32_t) * (M.ngamma + 1));
     size_t i_icopy = add(M.icopy.data(), sizeof(int32_t) * M.ncopies);
     size_t i_mult = add(mloc.data(), N);
@@ -621,6 +648,12 @@ int upload(ssg_system *S) {
     S->d_bg = static_cast<double *>(at(i_bg));
     S->op32 = S->op;
     S->op32.warp_range = static_cast<const int2 *>(at(i_brange32));
+    S->opB64 = S->op;
+    S->opB64.warp_range = static_cast<const int2 *>(at(i_brangeB64));
+    S->opB32 = S->op;
+    S->opB32.warp_range = static_cast<const int2 *>(at(i_brangeB32));
+    S->grid_spmmB64 = plan.gridB64;
+    S->grid_spmmB32 = plan.gridB32;
     SSG_CUDA_TRY(cudaMemsetAsync(S->d_scal, 0, sizeof(Scal), C->stream));
     SSG_CUDA_TRY(cudaMemsetAsync(S->d_scal_op, 0, sizeof(Scal), C->stream));
     SSG_CUDA_TRY(cudaEventCreate(&S->ev0));
@@ -761,13 +794,383 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
         st->status = h.status;
         st->iters = mode == SSG_MIXED ? h.total : h.iter;
         st->outer = mode == SSG_MIXED ? h.iter : 1;
-        st->reserved = 0;
+        st->block = 1;
         st->relres = h.relres;
         st->true_relres = h.bnorm > 0.0 ? std::sqrt(h.aux) / h.bnorm : std::sqrt(h.aux);
         st->solve_ms = ms;
         st->kernel_launches = launches;
     }
     return h.status;
+}
+
+// ---------------------------------------------------------------------------
+// Several right-hand sides together: K columns per launch (block.cuh).
+// ---------------------------------------------------------------------------
+
+int log2_of(int K) { return K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4; }
+
+int grid_vecB(const ssg_system *S, int K) {
+    const int64_t pairs = S->maps.nloc * K / 2;
+    return std::max(1, std::min<int>(static_cast<int>((pairs + kBlock - 1) / kBlock),
+                                     S->ctx->num_sms * kVecBlocksPerSM));
+}
+
+void destroy_block_graphs(ssg_system *S) {
+    for (int i = 0; i < 5; ++i)
+        for (ssg_system::BlockGraph *G : {&S->blk.g64[i], &S->blk.gmx[i]}) {
+            if (G->exec) cudaGraphExecDestroy(G->exec);
+            if (G->g) cudaGraphDestroy(G->g);
+            *G = ssg_system::BlockGraph{};
+        }
+}
+
+void free_block(ssg_system *S) {
+    destroy_block_graphs(S);
+    if (S->blk.mem) {
+        if (S->ctx && S->ctx->stream) cudaStreamSynchronize(S->ctx->stream);
+        cudaFree(S->blk.mem);
+    }
+    S->blk = ssg_system::BlockState{};
+}
+
+// Device vectors for K columns (kept for later solves with K' <= K).
+int ensure_block(ssg_system *S, int K) {
+    if (S->blk.kcap >= K) return SSG_OK;
+    free_block(S);
+    const int64_t N = S->maps.nloc, n = S->maps.n;
+    const int gmax = std::max(std::max(S->grid_spmmB64, S->grid_spmmB32), S->ctx->num_sms * kVecBlocksPerSM);
+    size_t total = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = total;
+        total = align_up(total + bytes, 256);
+        return o;
+    };
+    const size_t NK = static_cast<size_t>(N) * K;
+    const size_t o_bl = take(8 * NK), o_xl = take(8 * NK), o_r = take(8 * NK), o_p = take(8 * NK),
+                 o_q = take(8 * NK);
+    const size_t o_r32 = take(4 * NK), o_p32 = take(4 * NK), o_q32 = take(4 * NK), o_d32 = take(4 * NK);
+    const size_t o_part = take(sizeof(double) * 4 * static_cast<size_t>(gmax) * kMaxRhs);
+    const size_t o_bg = take(8 * static_cast<size_t>(n) * K), o_xg = take(8 * static_cast<size_t>(n) * K);
+    const size_t o_so = take(sizeof(ScalB)), o_si = take(sizeof(ScalB));
+    void *mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, total);
+    if (e != cudaSuccess) {
+        set_error(std::string("block vectors of ") + std::to_string(total) + " bytes: " + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? SSG_E_OOM : SSG_E_CUDA;
+    }
+    char *b = static_cast<char *>(mem);
+    ssg_system::BlockState &B = S->blk;
+    B.mem = mem;
+    B.kcap = K;
+    B.gmax = gmax;
+    B.bl = reinterpret_cast<double *>(b + o_bl);
+    B.xl = reinterpret_cast<double *>(b + o_xl);
+    B.r = reinterpret_cast<double *>(b + o_r);
+    B.p = reinterpret_cast<double *>(b + o_p);
+    B.q = reinterpret_cast<double *>(b + o_q);
+    B.r32 = reinterpret_cast<float *>(b + o_r32);
+    B.p32 = reinterpret_cast<float *>(b + o_p32);
+    B.q32 = reinterpret_cast<float *>(b + o_q32);
+    B.d32 = reinterpret_cast<float *>(b + o_d32);
+    B.part = reinterpret_cast<double *>(b + o_part);
+    B.bg = reinterpret_cast<double *>(b + o_bg);
+    B.xg = reinterpret_cast<double *>(b + o_xg);
+    B.so = reinterpret_cast<ScalB *>(b + o_so);
+    B.si = reinterpret_cast<ScalB *>(b + o_si);
+    SSG_CUDA_TRY(cudaMemsetAsync(mem, 0, total, S->ctx->stream));
+    return SSG_OK;
+}
+
+// Partials: the setup, residual and inner-setup kernels and the K-vector
+// products use the first half, the residual updates the second.
+double *blk_part_a(ssg_system *S) { return S->blk.part; }
+double *blk_part_b(ssg_system *S) { return S->blk.part + 2 * static_cast<size_t>(S->blk.gmax) * kMaxRhs; }
+
+template <int K>
+int launch_initB(ssg_system *S, cudaStream_t st, double *p, cudaGraphConditionalHandle h, int use_cond) {
+    ssg_system::BlockState &B = S->blk;
+    const int gv = grid_vecB(S, K);
+    // q holds S x_1 when a guess was given, else zeros (set before the loop)
+    k_residualB<K><<<gv, kBlock, 0, st>>>(S->maps.nloc, B.bl, B.q, B.r, p, S->op.mult, S->op.wtab, blk_part_a(S),
+                                          1, 1);
+    k_init_finB<K><<<1, kBlock, 0, st>>>(blk_part_a(S), gv, B.so, h, use_cond);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+template <int K>
+int launch_bodyB64(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
+    ssg_system::BlockState &B = S->blk;
+    const int64_t N = S->maps.nloc;
+    const int gv = grid_vecB(S, K);
+    k_spmm_asm<double, K, true><<<S->grid_spmmB64, kSpmvThreads, 0, st>>>(S->opB64, B.p, B.q, blk_part_a(S), B.so);
+    k_update_rB<K><<<gv, kBlock, 0, st>>>(N, B.r, B.q, S->op.mult, S->op.wtab, S->op.gflag, blk_part_a(S),
+                                          S->grid_spmmB64, blk_part_b(S), B.so);
+    k_update_xpB<K><<<gv, kBlock, 0, st>>>(N, B.xl, B.p, B.r, blk_part_b(S), gv, B.so, h, use_cond);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+template <int K>
+int launch_inner_initB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
+    ssg_system::BlockState &B = S->blk;
+    const int gv = grid_vecB(S, K);
+    k_inner_initB<K><<<gv, kBlock, 0, st>>>(S->maps.nloc, B.r, B.r32, B.p32, B.d32, S->op.mult, S->op.wtab32,
+                                            blk_part_a(S));
+    k_inner_finB<K><<<1, kBlock, 0, st>>>(blk_part_a(S), gv, B.si, B.so, h, use_cond);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+template <int K>
+int launch_inner_bodyB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
+    ssg_system::BlockState &B = S->blk;
+    const int64_t N = S->maps.nloc;
+    const int gv = grid_vecB(S, K);
+    k_spmm_asm<float, K, true><<<S->grid_spmmB32, kSpmvThreads, 0, st>>>(S->opB32, B.p32, B.q32, blk_part_a(S),
+                                                                          B.si);
+    k_update_r32B<K><<<gv, kBlock, 0, st>>>(N, B.r32, B.q32, S->op.mult, S->op.wtab32, S->op.gflag128,
+                                            blk_part_a(S), S->grid_spmmB32, blk_part_b(S), B.si);
+    k_update_dp32B<K><<<gv, kBlock, 0, st>>>(N, B.d32, B.p32, B.r32, blk_part_b(S), gv, B.si, B.so, h, use_cond);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+template <int K>
+int launch_outer_tailB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
+    ssg_system::BlockState &B = S->blk;
+    const int64_t N = S->maps.nloc;
+    const int gv = grid_vecB(S, K);
+    k_ir_correct<<<grid_for(N * K, S->ctx->num_sms), kBlock, 0, st>>>(N * K, B.xl, B.d32);
+    k_spmm_asm<double, K, false><<<S->grid_spmmB64, kSpmvThreads, 0, st>>>(S->opB64, B.xl, B.q, nullptr, nullptr);
+    k_residualB<K><<<gv, kBlock, 0, st>>>(N, B.bl, B.q, B.r, nullptr, S->op.mult, S->op.wtab, blk_part_a(S), 1, 0);
+    k_outer_finB<K><<<1, kBlock, 0, st>>>(blk_part_a(S), gv, B.so, B.si, 0, h, use_cond);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+// init -> WHILE(c_out) { body }
+template <typename FI, typename FB>
+int build_loop_graph(ssg_system::BlockGraph &G, FI init, FB body) {
+    SSG_CUDA_TRY(cudaGraphCreate(&G.g, 0));
+    SSG_CUDA_TRY(cudaGraphConditionalHandleCreate(&G.c_out, G.g, 0u, cudaGraphCondAssignDefault));
+    cudaStream_t cap;
+    SSG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int rc = SSG_OK;
+    cudaGraphNode_t n_init = nullptr, n_loop = nullptr;
+    cudaGraph_t g_body = nullptr;
+    cudaError_t e = capture_into(cap, G.g, nullptr, 0, [&](cudaStream_t c) { return init(c, G.c_out); }, &rc);
+    if (e == cudaSuccess && rc == SSG_OK) e = last_node(G.g, &n_init);
+    if (e == cudaSuccess && rc == SSG_OK) e = add_while(G.g, &n_init, G.c_out, &n_loop, &g_body);
+    if (e == cudaSuccess && rc == SSG_OK)
+        e = capture_into(cap, g_body, nullptr, 0, [&](cudaStream_t c) { return body(c, G.c_out); }, &rc);
+    if (e == cudaSuccess && rc == SSG_OK) e = cudaGraphInstantiate(&G.exec, G.g, 0);
+    cudaStreamDestroy(cap);
+    if (rc == SSG_OK && e != cudaSuccess) {
+        set_error(std::string("building the block CG graph: ") + cudaGetErrorString(e));
+        rc = SSG_E_CUDA;
+    }
+    if (rc != SSG_OK) {
+        if (G.g) cudaGraphDestroy(G.g);
+        G = ssg_system::BlockGraph{};
+    }
+    return rc;
+}
+
+// init -> WHILE(c_out) { inner init -> WHILE(c_in) { inner body } -> tail }
+template <typename FI, typename FII, typename FIB, typename FT>
+int build_nested_graph(ssg_system::BlockGraph &G, FI init, FII iinit, FIB ibody, FT tail) {
+    SSG_CUDA_TRY(cudaGraphCreate(&G.g, 0));
+    SSG_CUDA_TRY(cudaGraphConditionalHandleCreate(&G.c_out, G.g, 0u, cudaGraphCondAssignDefault));
+    cudaStream_t cap;
+    SSG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int rc = SSG_OK;
+    cudaGraphNode_t n_init = nullptr, n_outer = nullptr, n_iinit = nullptr, n_inner = nullptr;
+    cudaGraph_t body_out = nullptr, body_in = nullptr;
+    cudaError_t e = capture_into(cap, G.g, nullptr, 0, [&](cudaStream_t c) { return init(c, G.c_out); }, &rc);
+    if (e == cudaSuccess && rc == SSG_OK) e = last_node(G.g, &n_init);
+    if (e == cudaSuccess && rc == SSG_OK) e = add_while(G.g, &n_init, G.c_out, &n_outer, &body_out);
+    if (e == cudaSuccess && rc == SSG_OK)
+        e = cudaGraphConditionalHandleCreate(&G.c_in, body_out, 0u, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess && rc == SSG_OK)
+        e = capture_into(cap, body_out, nullptr, 0, [&](cudaStream_t c) { return iinit(c, G.c_in); }, &rc);
+    if (e == cudaSuccess && rc == SSG_OK) e = last_node(body_out, &n_iinit);
+    if (e == cudaSuccess && rc == SSG_OK) e = add_while(body_out, &n_iinit, G.c_in, &n_inner, &body_in);
+    if (e == cudaSuccess && rc == SSG_OK)
+        e = capture_into(cap, body_in, nullptr, 0, [&](cudaStream_t c) { return ibody(c, G.c_in); }, &rc);
+    if (e == cudaSuccess && rc == SSG_OK)
+        e = capture_into(cap, body_out, &n_inner, 1, [&](cudaStream_t c) { return tail(c, G.c_out); }, &rc);
+    if (e == cudaSuccess && rc == SSG_OK) e = cudaGraphInstantiate(&G.exec, G.g, 0);
+    cudaStreamDestroy(cap);
+    if (rc == SSG_OK && e != cudaSuccess) {
+        set_error(std::string("building the block mixed-precision graph: ") + cudaGetErrorString(e));
+        rc = SSG_E_CUDA;
+    }
+    if (rc != SSG_OK) {
+        if (G.g) cudaGraphDestroy(G.g);
+        G = ssg_system::BlockGraph{};
+    }
+    return rc;
+}
+
+int read_scalb(ssg_system *S, const ScalB *src, ScalB *dst) {
+    SSG_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(ScalB), cudaMemcpyDeviceToHost, S->ctx->stream));
+    SSG_CUDA_TRY(cudaStreamSynchronize(S->ctx->stream));
+    return SSG_OK;
+}
+
+template <int K>
+int run_blockB(ssg_system *S, int mode, int64_t *launches) {
+    ssg_ctx *C = S->ctx;
+    cudaStream_t s = C->stream;
+    ssg_system::BlockState &B = S->blk;
+    int rc = SSG_OK;
+    if (C->driver == SSG_DRIVER_GRAPH) {
+        ssg_system::BlockGraph &G = mode == SSG_MIXED ? B.gmx[log2_of(K)] : B.g64[log2_of(K)];
+        if (!G.exec) {
+            if (mode == SSG_MIXED)
+                rc = build_nested_graph(
+                    G, [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_initB<K>(S, c, nullptr, h, 1); },
+                    [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_inner_initB<K>(S, c, h, 1); },
+                    [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_inner_bodyB<K>(S, c, h, 1); },
+                    [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_outer_tailB<K>(S, c, h, 1); });
+            else
+                rc = build_loop_graph(
+                    G, [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_initB<K>(S, c, B.p, h, 1); },
+                    [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_bodyB64<K>(S, c, h, 1); });
+            if (rc != SSG_OK) return rc;
+        }
+        SSG_CUDA_TRY(cudaGraphLaunch(G.exec, s));
+        return SSG_OK;
+    }
+    ScalB ho{}, hi{};
+    if (mode != SSG_MIXED) {
+        rc = launch_initB<K>(S, s, B.p, 0, 0);
+        *launches += 2;
+        for (; rc == SSG_OK;) {
+            rc = read_scalb(S, B.so, &ho);
+            if (rc != SSG_OK || ho.done) break;
+            for (int i = 0; i < kHostChunk && rc == SSG_OK; ++i) rc = launch_bodyB64<K>(S, s, 0, 0);
+            *launches += 3 * kHostChunk;
+        }
+        return rc;
+    }
+    rc = launch_initB<K>(S, s, nullptr, 0, 0);
+    *launches += 2;
+    for (; rc == SSG_OK;) {
+        rc = read_scalb(S, B.so, &ho);
+        if (rc != SSG_OK || ho.done) break;
+        rc = launch_inner_initB<K>(S, s, 0, 0);
+        *launches += 2;
+        for (; rc == SSG_OK;) {
+            rc = read_scalb(S, B.si, &hi);
+            if (rc != SSG_OK || hi.done) break;
+            for (int i = 0; i < kHostChunk && rc == SSG_OK; ++i) rc = launch_inner_bodyB<K>(S, s, 0, 0);
+            *launches += 3 * kHostChunk;
+        }
+        if (rc == SSG_OK) rc = launch_outer_tailB<K>(S, s, 0, 0);
+        *launches += 4;
+    }
+    return rc;
+}
+
+// nr (<= K) right-hand sides at b_glob / x_glob (device, column j at j*n).
+template <int K>
+int solve_block(ssg_system *S, int nr, const double *b_glob, double *x_glob, int guess, double rtol,
+                int32_t max_iter, int mode, ssg_stats *st) {
+    int rc = ensure_block(S, K);
+    if (rc != SSG_OK) return rc;
+    ssg_ctx *C = S->ctx;
+    cudaStream_t s = C->stream;
+    ssg_system::BlockState &B = S->blk;
+    const int64_t N = S->maps.nloc, n = S->maps.n;
+    int64_t launches = 0;
+    SSG_CUDA_TRY(cudaEventRecord(S->ev0, s));
+    k_scatterB<K><<<grid_for(N * K, C->num_sms), kBlock, 0, s>>>(N, S->d_l2g, n, nr, b_glob, B.bl);
+    ++launches;
+    if (guess) {
+        k_scatterB<K><<<grid_for(N * K, C->num_sms), kBlock, 0, s>>>(N, S->d_l2g, n, nr, x_glob, B.xl);
+        k_spmm_asm<double, K, false><<<S->grid_spmmB64, kSpmvThreads, 0, s>>>(S->opB64, B.xl, B.q, nullptr, nullptr);
+        launches += 2;
+    } else {
+        SSG_CUDA_TRY(cudaMemsetAsync(B.xl, 0, sizeof(double) * N * K, s));
+        SSG_CUDA_TRY(cudaMemsetAsync(B.q, 0, sizeof(double) * N * K, s));
+    }
+    k_set_paramsB<<<1, 32, 0, s>>>(B.so, rtol, max_iter, guess, nr, C->inner_rtol, C->max_outer);
+    ++launches;
+    SSG_CUDA_TRY(cudaGetLastError());
+    rc = run_blockB<K>(S, mode, &launches);
+    if (rc != SSG_OK) return rc;
+    k_gatherB<K><<<grid_for(n * nr, C->num_sms), kBlock, 0, s>>>(n, S->d_own, nr, B.xl, x_glob);
+    // true residuals ||b_j - S x_j||_w in FP64
+    k_spmm_asm<double, K, false><<<S->grid_spmmB64, kSpmvThreads, 0, s>>>(S->opB64, B.xl, B.q, nullptr, nullptr);
+    const int gv = grid_vecB(S, K);
+    k_residualB<K><<<gv, kBlock, 0, s>>>(N, B.bl, B.q, nullptr, nullptr, S->op.mult, S->op.wtab, blk_part_a(S), 1,
+                                         0);
+    k_outer_finB<K><<<1, kBlock, 0, s>>>(blk_part_a(S), gv, B.so, B.si, 1, 0, 0);
+    launches += 4;
+    SSG_CUDA_TRY(cudaGetLastError());
+    SSG_CUDA_TRY(cudaEventRecord(S->ev1, s));
+    ScalB h{};
+    rc = read_scalb(S, B.so, &h);
+    if (rc != SSG_OK) return rc;
+    float ms = 0.f;
+    SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
+    if (C->driver == SSG_DRIVER_GRAPH) {
+        if (mode == SSG_MIXED)  // init 2; per refinement inner init 2 + tail 4; 3 per inner loop iteration
+            launches += 2 + 6 * static_cast<int64_t>(h.iter) + 3 * static_cast<int64_t>(h.loops);
+        else
+            launches += 2 + 3 * static_cast<int64_t>(h.iter);
+    }
+    int first_bad = SSG_OK;
+    for (int j = 0; j < nr; ++j) {
+        if (h.status[j] != SSG_OK && first_bad == SSG_OK) first_bad = h.status[j];
+        if (!st) continue;
+        st[j].status = h.status[j];
+        st[j].iters = h.iters[j];
+        st[j].outer = mode == SSG_MIXED ? h.outer[j] : 1;
+        st[j].block = K;
+        st[j].relres = h.relres[j];
+        st[j].true_relres = h.bnorm[j] > 0.0 ? std::sqrt(h.aux[j]) / h.bnorm[j] : std::sqrt(h.aux[j]);
+        st[j].solve_ms = ms;
+        st[j].kernel_launches = launches;
+    }
+    return first_bad;
+}
+
+int solve_block_k(ssg_system *S, int nr, const double *b, double *x, int guess, double rtol, int32_t max_iter,
+                  int mode, ssg_stats *st) {
+    if (nr <= 2) return solve_block<2>(S, nr, b, x, guess, rtol, max_iter, mode, st);
+    if (nr <= 4) return solve_block<4>(S, nr, b, x, guess, rtol, max_iter, mode, st);
+    if (nr <= 8) return solve_block<8>(S, nr, b, x, guess, rtol, max_iter, mode, st);
+    return solve_block<16>(S, nr, b, x, guess, rtol, max_iter, mode, st);
+}
+
+template <typename T>
+int spmm_checked(ssg_system *S, int32_t k, const T *x_loc, T *y_loc) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (!(k == 2 || k == 4 || k == 8 || k == 16)) {
+        set_error("k must be 2, 4, 8 or 16");
+        return SSG_E_INVALID;
+    }
+    const uintptr_t need = std::min<uintptr_t>(16, sizeof(T) * k);
+    if (!x_loc || !y_loc || x_loc == y_loc || reinterpret_cast<uintptr_t>(x_loc) % need ||
+        reinterpret_cast<uintptr_t>(y_loc) % need) {
+        set_error("x_loc and y_loc must be distinct device blocks aligned to min(16, k * element size) bytes");
+        return SSG_E_INVALID;
+    }
+    const DevOp &A = sizeof(T) == 8 ? S->opB64 : S->opB32;
+    const int grid = sizeof(T) == 8 ? S->grid_spmmB64 : S->grid_spmmB32;
+    cudaStream_t st = S->ctx->stream;
+    switch (k) {
+        case 2: k_spmm_asm<T, 2, false><<<grid, kSpmvThreads, 0, st>>>(A, x_loc, y_loc, nullptr, nullptr); break;
+        case 4: k_spmm_asm<T, 4, false><<<grid, kSpmvThreads, 0, st>>>(A, x_loc, y_loc, nullptr, nullptr); break;
+        case 8: k_spmm_asm<T, 8, false><<<grid, kSpmvThreads, 0, st>>>(A, x_loc, y_loc, nullptr, nullptr); break;
+        default: k_spmm_asm<T, 16, false><<<grid, kSpmvThreads, 0, st>>>(A, x_loc, y_loc, nullptr, nullptr); break;
+    }
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
 }
 
 }  // namespace
@@ -847,6 +1250,15 @@ int ssg_set_mixed(ssg_ctx *ctx, double inner_rtol, int32_t max_outer) {
     }
     ctx->inner_rtol = inner_rtol;
     ctx->max_outer = max_outer;
+    return SSG_OK;
+}
+
+int ssg_set_rhs_block(ssg_ctx *ctx, int32_t kmax) {
+    if (!ctx || !(kmax == 1 || kmax == 2 || kmax == 4 || kmax == 8 || kmax == 16)) {
+        set_error("ssg_set_rhs_block: kmax must be 1, 2, 4, 8 or 16");
+        return SSG_E_INVALID;
+    }
+    ctx->rhs_block = kmax;
     return SSG_OK;
 }
 
@@ -981,6 +1393,14 @@ int ssg_spmv_assembled_f32(ssg_system *S, const float *x_loc, float *y_loc, doub
     return SSG_OK;
 }
 
+int ssg_spmm_assembled(ssg_system *S, int32_t k, const double *x_loc, double *y_loc) {
+    return spmm_checked<double>(S, k, x_loc, y_loc);
+}
+
+int ssg_spmm_assembled_f32(ssg_system *S, int32_t k, const float *x_loc, float *y_loc) {
+    return spmm_checked<float>(S, k, x_loc, y_loc);
+}
+
 int ssg_wdot(ssg_system *S, const double *u, const double *v, double *result_dev) {
     int rc = check_dev(S);
     if (rc != SSG_OK) return rc;
@@ -1009,11 +1429,16 @@ int ssg_solve(ssg_system *S, int32_t k, const double *b, double *x, int32_t x_is
     if (max_iter <= 0) max_iter = S->maps.n;
     SSG_CUDA_TRY(cudaSetDevice(S->ctx->device));
     int first_bad = SSG_OK;
-    for (int32_t j = 0; j < k; ++j) {
+    const int kb = std::max(1, S->ctx->rhs_block);
+    for (int32_t j = 0; j < k;) {
+        const int nr = std::min<int>(k - j, kb);
         const size_t o = static_cast<size_t>(j) * S->maps.n;
-        rc = solve_one(S, b + o, x + o, x_is_guess, rtol, max_iter, mode, stats ? stats + j : nullptr);
+        ssg_stats *sj = stats ? stats + j : nullptr;
+        rc = nr == 1 ? solve_one(S, b + o, x + o, x_is_guess, rtol, max_iter, mode, sj)
+                     : solve_block_k(S, nr, b + o, x + o, x_is_guess, rtol, max_iter, mode, sj);
         if (rc == SSG_E_CUDA || rc == SSG_E_OOM || rc == SSG_E_INVALID) return rc;
         if (rc != SSG_OK && first_bad == SSG_OK) first_bad = rc;
+        j += nr;
     }
     if (first_bad != SSG_OK) set_error(ssg_error_string(first_bad));
     return first_bad;
@@ -1027,17 +1452,31 @@ int ssg_solve_host(ssg_system *S, int32_t k, const double *b_host, double *x_hos
         set_error("bad k or null b/x");
         return SSG_E_INVALID;
     }
+    if (!(rtol >= 0.0) || (mode != SSG_FP64 && mode != SSG_MIXED)) {
+        set_error("negative rtol or bad mode");
+        return SSG_E_INVALID;
+    }
     cudaStream_t s = S->ctx->stream;
-    const size_t nb = sizeof(double) * S->maps.n;
+    const int kb = std::max(1, S->ctx->rhs_block);
     int first_bad = SSG_OK;
-    for (int32_t j = 0; j < k; ++j) {
+    for (int32_t j = 0; j < k;) {
+        const int nr = std::min<int>(k - j, kb);
         const size_t o = static_cast<size_t>(j) * S->maps.n;
-        SSG_CUDA_TRY(cudaMemcpyAsync(S->d_bg, b_host + o, nb, cudaMemcpyHostToDevice, s));
-        if (x_is_guess) SSG_CUDA_TRY(cudaMemcpyAsync(S->d_xg, x_host + o, nb, cudaMemcpyHostToDevice, s));
-        rc = ssg_solve(S, 1, S->d_bg, S->d_xg, x_is_guess, rtol, max_iter, mode, stats ? stats + j : nullptr);
+        const size_t nb = sizeof(double) * S->maps.n * nr;
+        double *bg = S->d_bg, *xg = S->d_xg;
+        if (nr > 1) {
+            rc = ensure_block(S, nr <= 2 ? 2 : nr <= 4 ? 4 : nr <= 8 ? 8 : 16);
+            if (rc != SSG_OK) return rc;
+            bg = S->blk.bg;
+            xg = S->blk.xg;
+        }
+        SSG_CUDA_TRY(cudaMemcpyAsync(bg, b_host + o, nb, cudaMemcpyHostToDevice, s));
+        if (x_is_guess) SSG_CUDA_TRY(cudaMemcpyAsync(xg, x_host + o, nb, cudaMemcpyHostToDevice, s));
+        rc = ssg_solve(S, nr, bg, xg, x_is_guess, rtol, max_iter, mode, stats ? stats + j : nullptr);
         if (rc == SSG_E_CUDA || rc == SSG_E_OOM || rc == SSG_E_INVALID) return rc;
         if (rc != SSG_OK && first_bad == SSG_OK) first_bad = rc;
-        SSG_CUDA_TRY(cudaMemcpyAsync(x_host + o, S->d_xg, nb, cudaMemcpyDeviceToHost, s));
+        SSG_CUDA_TRY(cudaMemcpyAsync(x_host + o, xg, nb, cudaMemcpyDeviceToHost, s));
+        j += nr;
     }
     SSG_CUDA_TRY(cudaStreamSynchronize(s));
     return first_bad;
@@ -1052,6 +1491,7 @@ int ssg_system_destroy(ssg_system *S) {
     if (S->graph_m) cudaGraphDestroy(S->graph_m);
     if (S->ev0) cudaEventDestroy(S->ev0);
     if (S->ev1) cudaEventDestroy(S->ev1);
+    free_block(S);
     if (S->arena) {
         if (S->ctx && S->ctx->stream) cudaStreamSynchronize(S->ctx->stream);
         cudaFree(S->arena);

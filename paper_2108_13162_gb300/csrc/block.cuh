@@ -1,0 +1,827 @@
+// Several right-hand sides solved together (ssg_solve with k > 1).
+//
+// K right-hand sides (K = 2, 4, 8 or 16) run Algorithm 3 side by side, each
+// with its own alpha, beta and stopping test; the local matrices of the
+// sub-structures are streamed once per iteration for all K columns, so the
+// SpMV of Section 3.4.1 becomes a product with K vectors.  A column whose
+// test has passed (or that broke down) is frozen: its alpha and beta are
+// zero from then on, so x, r and the inner correction keep their bits.  Each
+// column therefore follows the same sequence of operations as a solve of its
+// right-hand side alone.
+//
+// Local vector blocks are interleaved: entry k of column j sits at k*K + j,
+// so one local entry's K values are contiguous (K*8 bytes in FP64).
+//
+// Reductions stay deterministic: a block writes one partial per column, and
+// every block of the next kernel sums the partials of each column in the
+// same fixed order.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace ssg {
+
+constexpr int kMaxRhs = 16;
+
+// State of K solves, resident on the device.  Bit j of `act` is set while
+// column j still iterates.
+struct ScalB {
+    double rho[kMaxRhs];     // (r, r)_w of the last completed iteration
+    double rho_b[kMaxRhs];   // rho as the residual update saw it
+    double alpha[kMaxRhs];
+    double pq[kMaxRhs];
+    double bnorm[kMaxRhs];
+    double relres[kMaxRhs];
+    double aux[kMaxRhs];     // true residual (b - S x, b - S x)_w at the end
+    double rho0[kMaxRhs];    // inner solves: (r, r)_w at the start of the inner solve
+    double tau[kMaxRhs];     // inner solves: relative tolerance of this inner solve
+    int32_t iters[kMaxRhs];  // FP64: iterations; SSG_MIXED outer state: inner iterations summed
+    int32_t outer[kMaxRhs];  // SSG_MIXED: refinements
+    int32_t status[kMaxRhs];
+    uint32_t act;
+    uint32_t act_b;          // act as the residual update left it (hand-off to the x/p update)
+    int32_t iter;            // completed loop iterations
+    int32_t iter_b;
+    int32_t max_iter;
+    int32_t nrhs;            // columns in use (the rest are padding)
+    double rtol;
+    double inner_rtol;
+    int32_t max_outer;
+    int32_t guess;
+    int32_t halt[2];
+    int32_t done;
+    int32_t loops;           // SSG_MIXED outer state: inner loop iterations summed (launch count)
+};
+
+template <typename T>
+struct SpmmTraits;
+template <>
+struct SpmmTraits<double> {
+    static constexpr int kBlocksPerSM = 2;  // K FP64 accumulators and two entries' rows in flight per lane
+};
+template <>
+struct SpmmTraits<float> {
+    static constexpr int kBlocksPerSM = 2;
+};
+
+// K contiguous values of one local entry.
+template <int K>
+__device__ __forceinline__ void load_row(const double *__restrict__ p, double (&v)[K]) {
+    const double2 *p2 = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int q = 0; q < K / 2; ++q) {
+        const double2 t = __ldg(p2 + q);
+        v[2 * q] = t.x;
+        v[2 * q + 1] = t.y;
+    }
+}
+template <int K>
+__device__ __forceinline__ void load_row(const float *__restrict__ p, float (&v)[K]) {
+    if constexpr (K >= 4) {
+        const float4 *p4 = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) {
+            const float4 t = __ldg(p4 + q);
+            v[4 * q] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+        }
+    } else {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = t.x;
+        v[1] = t.y;
+    }
+}
+template <int K>
+__device__ __forceinline__ void store_row(double *__restrict__ p, const double (&v)[K]) {
+    double2 *p2 = reinterpret_cast<double2 *>(p);
+#pragma unroll
+    for (int q = 0; q < K / 2; ++q) p2[q] = make_double2(v[2 * q], v[2 * q + 1]);
+}
+template <int K>
+__device__ __forceinline__ void store_row(float *__restrict__ p, const float (&v)[K]) {
+    if constexpr (K >= 4) {
+        float4 *p4 = reinterpret_cast<float4 *>(p);
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) p4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    }
+}
+
+// NC consecutive sliced-ELL entries of a lane's row for all K columns: value
+// and column loads first, then the NC rows of x, then the FMAs in CSR order.
+template <int NC, int K, typename T>
+__device__ __forceinline__ void slice_chunk_k(const T *__restrict__ sv, const int32_t *__restrict__ sc,
+                                              const T *__restrict__ X, int base, int k0, T (&acc)[K]) {
+    T v[NC];
+    int c[NC];
+#pragma unroll
+    for (int e = 0; e < NC; ++e) {
+        v[e] = __ldcs(sv + base + (k0 + e) * kSliceRows);
+        c[e] = __ldcs(sc + base + (k0 + e) * kSliceRows);
+    }
+    T xv[NC][K];
+#pragma unroll
+    for (int e = 0; e < NC; ++e) load_row<K>(X + (size_t)c[e] * K, xv[e]);
+#pragma unroll
+    for (int e = 0; e < NC; ++e)
+#pragma unroll
+        for (int j = 0; j < K; ++j) acc[j] = fma(v[e], xv[e][j], acc[j]);
+}
+
+// Sub-structured product with K vectors: Y = S X, then (with DOTS) each
+// block's partial of (x_j, y_j)_w at partials[block * K + j].  The work list
+// and the summation orders (CSR order inside a row, ascending subdomain at
+// an interface node) are those of the single-vector kernel.
+template <typename T, int K, bool DOTS>
+__global__ void __launch_bounds__(kSpmvThreads, SpmmTraits<T>::kBlocksPerSM)
+    k_spmm_asm(DevOp A, const T *__restrict__ X, T *__restrict__ Y, double *partials, const ScalB *s) {
+    if (s && s->halt[s->iter & 1]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int2 range = A.warp_range[blockIdx.x * kSpmvWarps + warp];
+    const T *__restrict__ sv = slice_vals<T>(A);
+    const T *__restrict__ val = row_vals<T>(A);
+    const T *__restrict__ ival = copy_vals<T>(A);
+    T dot[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) dot[j] = T(0);
+    for (int it = range.x; it < range.y; ++it) {
+        const WorkItem W = A.items[it];
+        if (W.kind == kItemSlice || W.kind == kItemIfaceSlice) {
+            T acc[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) acc[j] = T(0);
+            const int base = W.e0 + lane;
+            int k = 0;
+            for (; k + 2 <= W.e1; k += 2) slice_chunk_k<2, K, T>(sv, A.scol, X, base, k, acc);
+            if (k < W.e1) slice_chunk_k<1, K, T>(sv, A.scol, X, base, k, acc);
+            if (W.kind == kItemSlice) {
+                const int r = W.a + lane;
+                if (r < W.b) {
+                    store_row<K>(Y + (size_t)r * K, acc);
+                    if (DOTS) {
+                        T xr[K];
+                        load_row<K>(X + (size_t)r * K, xr);
+#pragma unroll
+                        for (int j = 0; j < K; ++j) dot[j] = fma(xr[j], acc[j], dot[j]);
+                    }
+                }
+            } else {
+                const int c = W.a + lane;
+                const bool valid = c < W.b;
+                const int seg = valid ? __ldg(A.sseg + c) : 0;
+                const int l0 = seg & 0xff, m = seg >> 8;
+                const int mmax = __reduce_max_sync(0xffffffffu, m);
+                T S[K];
+#pragma unroll
+                for (int j = 0; j < K; ++j) S[j] = T(0);
+                for (int t = 0; t < mmax; ++t) {
+                    const int src = (l0 + t) & 31;
+#pragma unroll
+                    for (int j = 0; j < K; ++j) {
+                        const T v = __shfl_sync(0xffffffffu, acc[j], src);
+                        if (t < m) S[j] += v;
+                    }
+                }
+                if (valid) {
+                    const int row = __ldg(A.icopy + c);
+                    store_row<K>(Y + (size_t)row * K, S);
+                    if (DOTS) {
+                        const T w = wtab_of<T>(A, m);
+                        T xr[K];
+                        load_row<K>(X + (size_t)row * K, xr);
+#pragma unroll
+                        for (int j = 0; j < K; ++j) dot[j] = fma(w * xr[j], S[j], dot[j]);
+                    }
+                }
+            }
+        } else if (W.kind == kItemLongRow) {
+            T acc[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) acc[j] = T(0);
+            for (int k = W.e0 + lane; k < W.e1; k += 32) {
+                const T v = val[k];
+                T xv[K];
+                load_row<K>(X + (size_t)A.col[k] * K, xv);
+#pragma unroll
+                for (int j = 0; j < K; ++j) acc[j] = fma(v, xv[j], acc[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < K; ++j) acc[j] = T(warp_sum(double(acc[j])));
+            if (lane == 0) {
+                store_row<K>(Y + (size_t)W.a * K, acc);
+                if (DOTS) {
+                    T xr[K];
+                    load_row<K>(X + (size_t)W.a * K, xr);
+#pragma unroll
+                    for (int j = 0; j < K; ++j) dot[j] = fma(xr[j], acc[j], dot[j]);
+                }
+            }
+        } else {
+            T S[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) S[j] = T(0);
+            for (int c = W.c0; c < W.c1; ++c) {
+                T acc[K];
+#pragma unroll
+                for (int j = 0; j < K; ++j) acc[j] = T(0);
+                for (int k = A.irp[c] + lane; k < A.irp[c + 1]; k += 32) {
+                    const T v = ival[k];
+                    T xv[K];
+                    load_row<K>(X + (size_t)A.icol[k] * K, xv);
+#pragma unroll
+                    for (int j = 0; j < K; ++j) acc[j] = fma(v, xv[j], acc[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < K; ++j) S[j] += T(warp_sum(double(acc[j])));  // valid in lane 0
+            }
+            if (lane == 0) {
+                const T w = wtab_of<T>(A, W.c1 - W.c0);
+                for (int c = W.c0; c < W.c1; ++c) {
+                    const int row = A.icopy[c];
+                    store_row<K>(Y + (size_t)row * K, S);
+                    if (DOTS) {
+                        T xr[K];
+                        load_row<K>(X + (size_t)row * K, xr);
+#pragma unroll
+                        for (int j = 0; j < K; ++j) dot[j] = fma(w * xr[j], S[j], dot[j]);
+                    }
+                }
+            }
+        }
+    }
+    if (DOTS) {
+        __shared__ double wsum[kSpmvWarps][K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const double wv = warp_sum(double(dot[j]));
+            if (lane == 0) wsum[warp][j] = wv;
+        }
+        __syncthreads();
+        if (threadIdx.x < K) {
+            double bs = wsum[0][threadIdx.x];
+#pragma unroll
+            for (int w = 1; w < kSpmvWarps; ++w) bs += wsum[w][threadIdx.x];
+            partials[(size_t)blockIdx.x * K + threadIdx.x] = bs;
+        }
+    }
+}
+
+// Every block sums each column's partials (G blocks of the previous kernel,
+// K per block) in the same fixed order: warp w takes the columns j = w mod 8,
+// lane-strided over the blocks, then a fixed shuffle tree.  Result in tot[K]
+// (shared), valid after the call in every thread.
+template <int K>
+__device__ __forceinline__ void all_sum_cols(const double *partials, int G, double *tot) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = warp; j < K; j += kBlock / 32) {
+        double v = 0.0;
+        for (int g = lane; g < G; g += 32) v += __ldcg(partials + (size_t)g * K + j);
+        v = warp_sum(v);
+        if (lane == 0) tot[j] = v;
+    }
+    __syncthreads();
+}
+
+// Per-column block sum of thread accumulators.  Thread t holds acc[u] for
+// the column (VW t + u) mod K (true when the element loop strides by a
+// multiple of K, as all loops below do); the block's sums go to out[0..K).
+template <int K, int VW, typename A>
+__device__ __forceinline__ void block_cols_sum(const A (&acc)[VW], double *out) {
+    __shared__ A red[kBlock * VW];
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < VW; ++u) red[threadIdx.x * VW + u] = acc[u];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kPer = kBlock * VW / K;  // entries per column
+    for (int j = warp; j < K; j += kBlock / 32) {
+        A v = A(0);
+        for (int i = lane; i < kPer; i += 32) v += red[i * K + j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) out[j] = double(v);
+    }
+}
+
+__device__ __forceinline__ void stop_loop_b(ScalB *s, int k1, cudaGraphConditionalHandle h, int use_cond) {
+    s->halt[k1 & 1] = 1;
+    s->done = 1;
+    if (use_cond) cudaGraphSetConditional(h, 0);
+}
+
+// Algorithm 3 lines 3 and 5 for K columns (FP64): alpha_j = rho_j / (p_j,
+// S p_j)_w for every active column (a column with (p, S p)_w <= 0 stops with
+// a breakdown), r_j <- r_j - alpha_j q_j and each block's partials of
+// (r_j, r_j)_w.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_update_rB(int64_t N, double *__restrict__ r, const double *__restrict__ q,
+                                                      const uint8_t *__restrict__ mult,
+                                                      const double *__restrict__ wtab,
+                                                      const uint8_t *__restrict__ gflag, const double *part_pq, int G1,
+                                                      double *part_rr, ScalB *s) {
+    __shared__ double tot[K];
+    __shared__ double alpha_s[K];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int j = 0; j < K; ++j) s->rho_b[j] = s->rho[j];
+        s->iter_b = s->iter;
+    }
+    if (s->halt[s->iter & 1]) return;
+    const uint32_t act = s->act;
+    all_sum_cols<K>(part_pq, G1, tot);
+    if (threadIdx.x < K) {
+        const int j = threadIdx.x;
+        const double pq = tot[j];
+        double a = 0.0;
+        if (((act >> j) & 1u) && pq > 0.0 && isfinite(pq)) a = s->rho[j] / pq;
+        alpha_s[j] = a;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        uint32_t ab = act;
+        for (int j = 0; j < K; ++j) {
+            if (!((act >> j) & 1u)) continue;
+            const double pq = tot[j];
+            s->pq[j] = pq;
+            s->alpha[j] = alpha_s[j];
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                s->status[j] = SSG_E_BREAKDOWN;
+                ab &= ~(1u << j);
+            }
+        }
+        s->act_b = ab;
+    }
+    const int j0 = (2 * threadIdx.x) % K;
+    const double a0 = alpha_s[j0], a1 = alpha_s[j0 + 1];
+    double acc[2] = {0.0, 0.0};
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    const int64_t NK2 = N * K / 2;
+    double2 *__restrict__ r2 = reinterpret_cast<double2 *>(r);
+    const double2 *__restrict__ q2 = reinterpret_cast<const double2 *>(q);
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < NK2; i += stride) {
+        double2 rv = r2[i];
+        const double2 qv = __ldcs(q2 + i);
+        rv.x = fma(-a0, qv.x, rv.x);
+        rv.y = fma(-a1, qv.y, rv.y);
+        r2[i] = rv;
+        const int64_t e = (2 * i) / K;  // local entry of both values
+        if (__ldg(gflag + (e >> 6)) == 0) {
+            acc[0] = fma(rv.x, rv.x, acc[0]);
+            acc[1] = fma(rv.y, rv.y, acc[1]);
+        } else {
+            const double w = __ldg(wtab + mult[e]);
+            acc[0] = fma(w * rv.x, rv.x, acc[0]);
+            acc[1] = fma(w * rv.y, rv.y, acc[1]);
+        }
+    }
+    block_cols_sum<K, 2>(acc, part_rr + (size_t)blockIdx.x * K);
+}
+
+// Algorithm 3 lines 4, 7, 8 for K columns (FP64): beta_j = (r_j, r_j)_w /
+// rho_j, x_j <- x_j + alpha_j p_j, p_j <- r_j + beta_j p_j (alpha = beta = 0
+// for frozen columns); block 0 records each column's iteration and stopping
+// decision and ends the loop when no column is left.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_update_xpB(int64_t N, double *__restrict__ x, double *__restrict__ p,
+                                                       const double *__restrict__ r, const double *part_rr, int G2,
+                                                       ScalB *s, cudaGraphConditionalHandle h, int use_cond) {
+    __shared__ double tot[K];
+    __shared__ double alpha_s[K], beta_s[K];
+    const int k = s->iter_b;
+    if (s->halt[k & 1]) return;
+    const uint32_t ab = s->act_b;
+    all_sum_cols<K>(part_rr, G2, tot);
+    if (threadIdx.x < K) {
+        const int j = threadIdx.x;
+        const bool on = (ab >> j) & 1u;
+        alpha_s[j] = on ? s->alpha[j] : 0.0;
+        beta_s[j] = on ? tot[j] / s->rho_b[j] : 0.0;
+    }
+    __syncthreads();
+    const int j0 = (2 * threadIdx.x) % K;
+    const double a0 = alpha_s[j0], a1 = alpha_s[j0 + 1];
+    const double b0 = beta_s[j0], b1 = beta_s[j0 + 1];
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    const int64_t NK2 = N * K / 2;
+    double2 *x2 = reinterpret_cast<double2 *>(x);
+    double2 *p2 = reinterpret_cast<double2 *>(p);
+    const double2 *r2 = reinterpret_cast<const double2 *>(r);
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < NK2; i += stride) {
+        const double2 pv = p2[i];
+        double2 xv = __ldcs(x2 + i);
+        const double2 rv = r2[i];
+        xv.x = fma(a0, pv.x, xv.x);
+        xv.y = fma(a1, pv.y, xv.y);
+        __stcs(x2 + i, xv);
+        p2[i] = make_double2(fma(b0, pv.x, rv.x), fma(b1, pv.y, rv.y));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        uint32_t na = ab;
+        for (int j = 0; j < K; ++j) {
+            if (!((ab >> j) & 1u)) continue;
+            const double rr = tot[j];
+            s->rho[j] = rr;
+            s->iters[j] = k + 1;
+            s->relres[j] = s->bnorm[j] > 0.0 ? sqrt(rr) / s->bnorm[j] : 0.0;
+            if (sqrt(rr) <= s->rtol * s->bnorm[j]) {
+                s->status[j] = SSG_OK;
+                na &= ~(1u << j);
+            }
+        }
+        s->iter = k + 1;
+        if (na && k + 1 >= s->max_iter) {
+            for (int j = 0; j < K; ++j)
+                if ((na >> j) & 1u) s->status[j] = SSG_E_NOT_CONVERGED;
+            na = 0;
+        }
+        s->act = na;
+        if (!na) stop_loop_b(s, k + 1, h, use_cond);
+    }
+}
+
+// Setup of Algorithm 3 line 1 for K columns: r = b - q (q = S x_1 with a
+// guess) or r = b, p = r when p is given, and each block's partials of
+// (r_j, r_j)_w (part[block*K + j]) and (b_j, b_j)_w (part[(G + block)*K + j]).
+// With p == nullptr this is the FP64 residual of the refinement loop.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_residualB(int64_t N, const double *__restrict__ b,
+                                                      const double *__restrict__ q, double *__restrict__ r,
+                                                      double *__restrict__ p, const uint8_t *__restrict__ mult,
+                                                      const double *__restrict__ wtab, double *part, int use_q,
+                                                      int with_b) {
+    double arr[2] = {0.0, 0.0}, abb[2] = {0.0, 0.0};
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    const int64_t NK2 = N * K / 2;
+    const double2 *b2 = reinterpret_cast<const double2 *>(b);
+    const double2 *q2 = reinterpret_cast<const double2 *>(q);
+    double2 *r2 = reinterpret_cast<double2 *>(r);
+    double2 *p2 = reinterpret_cast<double2 *>(p);
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < NK2; i += stride) {
+        const double2 bv = b2[i];
+        double2 rv = bv;
+        if (use_q) {
+            const double2 qv = q2[i];
+            rv.x = bv.x - qv.x;
+            rv.y = bv.y - qv.y;
+        }
+        if (r) r2[i] = rv;
+        if (p) p2[i] = rv;
+        const double w = __ldg(wtab + mult[(2 * i) / K]);
+        arr[0] = fma(w * rv.x, rv.x, arr[0]);
+        arr[1] = fma(w * rv.y, rv.y, arr[1]);
+        if (with_b) {
+            abb[0] = fma(w * bv.x, bv.x, abb[0]);
+            abb[1] = fma(w * bv.y, bv.y, abb[1]);
+        }
+    }
+    block_cols_sum<K, 2>(arr, part + (size_t)blockIdx.x * K);
+    if (with_b) block_cols_sum<K, 2>(abb, part + (size_t)(gridDim.x + blockIdx.x) * K);
+}
+
+__global__ void k_set_paramsB(ScalB *s, double rtol, int32_t max_iter, int32_t guess, int32_t nrhs,
+                              double inner_rtol, int32_t max_outer) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        s->rtol = rtol;
+        s->max_iter = max_iter;
+        s->guess = guess;
+        s->nrhs = nrhs;
+        s->inner_rtol = inner_rtol;
+        s->max_outer = max_outer;
+        s->done = 0;
+    }
+}
+
+// One block, after k_residualB (with_b) of the setup: rho_j, ||b_j||_w, the
+// test before the first iteration, and the loop condition.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_init_finB(const double *part, int G, ScalB *s,
+                                                      cudaGraphConditionalHandle h, int use_cond) {
+    __shared__ double rr[K], bb[K];
+    all_sum_cols<K>(part, G, rr);
+    all_sum_cols<K>(part + (size_t)G * K, G, bb);
+    if (threadIdx.x == 0) {
+        uint32_t act = 0;
+        for (int j = 0; j < K; ++j) {
+            s->rho[j] = rr[j];
+            s->rho_b[j] = rr[j];
+            s->bnorm[j] = sqrt(bb[j]);
+            s->relres[j] = s->bnorm[j] > 0.0 ? sqrt(rr[j]) / s->bnorm[j] : 0.0;
+            s->iters[j] = 0;
+            s->outer[j] = 0;
+            s->alpha[j] = 0.0;
+            s->pq[j] = 0.0;
+            s->aux[j] = 0.0;
+            if (j >= s->nrhs || sqrt(rr[j]) <= s->rtol * s->bnorm[j]) {
+                s->status[j] = SSG_OK;
+            } else {
+                s->status[j] = SSG_E_NOT_CONVERGED;
+                if (s->max_iter > 0) act |= 1u << j;
+            }
+        }
+        s->act = act;
+        s->act_b = act;
+        s->iter = 0;
+        s->iter_b = 0;
+        s->loops = 0;
+        s->done = act == 0;
+        s->halt[0] = act == 0;
+        s->halt[1] = 0;
+        if (use_cond) cudaGraphSetConditional(h, act ? 1u : 0u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SSG_MIXED for K columns: FP32 inner CG inside FP64 iterative refinement.
+// Outer state so (act = columns still refining, iters = inner iterations
+// summed, outer = refinements); inner state si (act = columns still in the
+// current inner solve).
+// ---------------------------------------------------------------------------
+
+// Inner setup: r32 = (float) r64, p32 = r32, d32 = 0 and each block's
+// partials of (r32, r32)_w (FP32 products and block sums).
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_inner_initB(int64_t N, const double *__restrict__ r64,
+                                                        float *__restrict__ r32, float *__restrict__ p32,
+                                                        float *__restrict__ d32, const uint8_t *__restrict__ mult,
+                                                        const float *__restrict__ wtab, double *part) {
+    float acc[2] = {0.f, 0.f};
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    const int64_t NK2 = N * K / 2;
+    const double2 *r2 = reinterpret_cast<const double2 *>(r64);
+    float2 *rr2 = reinterpret_cast<float2 *>(r32);
+    float2 *pp2 = reinterpret_cast<float2 *>(p32);
+    float2 *dd2 = reinterpret_cast<float2 *>(d32);
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < NK2; i += stride) {
+        const double2 rv = r2[i];
+        const float2 f = make_float2(float(rv.x), float(rv.y));
+        rr2[i] = f;
+        pp2[i] = f;
+        dd2[i] = make_float2(0.f, 0.f);
+        const float w = __ldg(wtab + mult[(2 * i) / K]);
+        acc[0] = fmaf(w * f.x, f.x, acc[0]);
+        acc[1] = fmaf(w * f.y, f.y, acc[1]);
+    }
+    block_cols_sum<K, 2>(acc, part + (size_t)blockIdx.x * K);
+}
+
+// One block: rho0_j of the inner solves, their tolerances
+// tau_j = max(inner_rtol, rtol ||b_j|| / ||r64_j||), the active set, and the
+// inner loop condition.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_inner_finB(const double *part, int G, ScalB *si, const ScalB *so,
+                                                       cudaGraphConditionalHandle h, int use_cond) {
+    __shared__ double rr[K];
+    all_sum_cols<K>(part, G, rr);
+    if (threadIdx.x == 0) {
+        uint32_t act = 0;
+        for (int j = 0; j < K; ++j) {
+            const double tot = rr[j];
+            si->rho[j] = tot;
+            si->rho_b[j] = tot;
+            si->rho0[j] = tot;
+            const double tau =
+                so->bnorm[j] > 0.0 && so->rho[j] > 0.0 ? so->rtol * so->bnorm[j] / sqrt(so->rho[j]) : 0.0;
+            si->tau[j] = tau > so->inner_rtol ? tau : so->inner_rtol;
+            si->alpha[j] = 0.0;
+            si->status[j] = SSG_OK;
+            if (((so->act >> j) & 1u) && tot > 0.0 && so->iters[j] < so->max_iter) act |= 1u << j;
+        }
+        si->act = act;
+        si->act_b = act;
+        si->iter = 0;
+        si->iter_b = 0;
+        si->done = act == 0;
+        si->halt[0] = act == 0;
+        si->halt[1] = 0;
+        if (use_cond) cudaGraphSetConditional(h, act ? 1u : 0u);
+    }
+}
+
+// Inner Algorithm 3 lines 3 and 5 in FP32 for K columns (alpha formed in
+// FP64 from the FP64 sums of the partials, then rounded to FP32 once).
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_update_r32B(int64_t N, float *__restrict__ r, const float *__restrict__ q,
+                                                        const uint8_t *__restrict__ mult,
+                                                        const float *__restrict__ wtab,
+                                                        const uint8_t *__restrict__ gflag128, const double *part_pq,
+                                                        int G1, double *part_rr, ScalB *si) {
+    constexpr int VW = K >= 4 ? 4 : 2;
+    __shared__ double tot[K];
+    __shared__ float alpha_s[K];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int j = 0; j < K; ++j) si->rho_b[j] = si->rho[j];
+        si->iter_b = si->iter;
+    }
+    if (si->halt[si->iter & 1]) return;
+    const uint32_t act = si->act;
+    all_sum_cols<K>(part_pq, G1, tot);
+    if (threadIdx.x < K) {
+        const int j = threadIdx.x;
+        const double pq = tot[j];
+        double a = 0.0;
+        if (((act >> j) & 1u) && pq > 0.0 && isfinite(pq)) a = si->rho[j] / pq;
+        alpha_s[j] = float(a);
+        if (blockIdx.x == 0 && ((act >> j) & 1u)) {
+            si->pq[j] = pq;
+            si->alpha[j] = a;
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        uint32_t ab = act;
+        for (int j = 0; j < K; ++j) {
+            if (!((act >> j) & 1u)) continue;
+            const double pq = tot[j];
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                si->status[j] = SSG_E_BREAKDOWN;
+                ab &= ~(1u << j);
+            }
+        }
+        si->act_b = ab;
+    }
+    const int j0 = (VW * threadIdx.x) % K;
+    float a[VW];
+#pragma unroll
+    for (int u = 0; u < VW; ++u) a[u] = alpha_s[j0 + u];
+    float acc[VW];
+#pragma unroll
+    for (int u = 0; u < VW; ++u) acc[u] = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    const int64_t NV = N * K / VW;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < NV; i += stride) {
+        float rv[VW], qv[VW];
+        if constexpr (VW == 4) {
+            const float4 t = reinterpret_cast<const float4 *>(r)[i];
+            const float4 u = __ldcs(reinterpret_cast<const float4 *>(q) + i);
+            rv[0] = t.x, rv[1] = t.y, rv[2] = t.z, rv[3] = t.w;
+            qv[0] = u.x, qv[1] = u.y, qv[2] = u.z, qv[3] = u.w;
+        } else {
+            const float2 t = reinterpret_cast<const float2 *>(r)[i];
+            const float2 u = __ldcs(reinterpret_cast<const float2 *>(q) + i);
+            rv[0] = t.x, rv[1] = t.y;
+            qv[0] = u.x, qv[1] = u.y;
+        }
+#pragma unroll
+        for (int u = 0; u < VW; ++u) rv[u] = fmaf(-a[u], qv[u], rv[u]);
+        if constexpr (VW == 4)
+            reinterpret_cast<float4 *>(r)[i] = make_float4(rv[0], rv[1], rv[2], rv[3]);
+        else
+            reinterpret_cast<float2 *>(r)[i] = make_float2(rv[0], rv[1]);
+        const int64_t e = (VW * i) / K;
+        if (__ldg(gflag128 + (e >> 7)) == 0) {
+#pragma unroll
+            for (int u = 0; u < VW; ++u) acc[u] = fmaf(rv[u], rv[u], acc[u]);
+        } else {
+            const float w = __ldg(wtab + mult[e]);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) acc[u] = fmaf(w * rv[u], rv[u], acc[u]);
+        }
+    }
+    block_cols_sum<K, VW>(acc, part_rr + (size_t)blockIdx.x * K);
+}
+
+// Inner Algorithm 3 lines 4, 7, 8 in FP32 for K columns: d_j <- d_j +
+// alpha_j p_j, p_j <- r_j + beta_j p_j; block 0 counts each active column's
+// inner iteration and applies its inner test (sqrt(rho_j) <= tau_j
+// sqrt(rho0_j), or its inner iterations summed reach max_iter).
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_update_dp32B(int64_t N, float *__restrict__ d, float *__restrict__ p,
+                                                         const float *__restrict__ r, const double *part_rr, int G2,
+                                                         ScalB *si, ScalB *so, cudaGraphConditionalHandle h,
+                                                         int use_cond) {
+    constexpr int VW = K >= 4 ? 4 : 2;
+    __shared__ double tot[K];
+    __shared__ float alpha_s[K], beta_s[K];
+    const int k = si->iter_b;
+    if (si->halt[k & 1]) return;
+    const uint32_t ab = si->act_b;
+    all_sum_cols<K>(part_rr, G2, tot);
+    if (threadIdx.x < K) {
+        const int j = threadIdx.x;
+        const bool on = (ab >> j) & 1u;
+        alpha_s[j] = on ? float(si->alpha[j]) : 0.f;
+        beta_s[j] = on ? float(tot[j] / si->rho_b[j]) : 0.f;
+    }
+    __syncthreads();
+    const int j0 = (VW * threadIdx.x) % K;
+    float a[VW], bt[VW];
+#pragma unroll
+    for (int u = 0; u < VW; ++u) {
+        a[u] = alpha_s[j0 + u];
+        bt[u] = beta_s[j0 + u];
+    }
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    const int64_t NV = N * K / VW;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < NV; i += stride) {
+        float pv[VW], dv[VW], rv[VW];
+        if constexpr (VW == 4) {
+            const float4 t = reinterpret_cast<const float4 *>(p)[i];
+            const float4 u = reinterpret_cast<const float4 *>(d)[i];
+            const float4 w = reinterpret_cast<const float4 *>(r)[i];
+            pv[0] = t.x, pv[1] = t.y, pv[2] = t.z, pv[3] = t.w;
+            dv[0] = u.x, dv[1] = u.y, dv[2] = u.z, dv[3] = u.w;
+            rv[0] = w.x, rv[1] = w.y, rv[2] = w.z, rv[3] = w.w;
+        } else {
+            const float2 t = reinterpret_cast<const float2 *>(p)[i];
+            const float2 u = reinterpret_cast<const float2 *>(d)[i];
+            const float2 w = reinterpret_cast<const float2 *>(r)[i];
+            pv[0] = t.x, pv[1] = t.y;
+            dv[0] = u.x, dv[1] = u.y;
+            rv[0] = w.x, rv[1] = w.y;
+        }
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+            dv[u] = fmaf(a[u], pv[u], dv[u]);
+            pv[u] = fmaf(bt[u], pv[u], rv[u]);
+        }
+        if constexpr (VW == 4) {
+            reinterpret_cast<float4 *>(d)[i] = make_float4(dv[0], dv[1], dv[2], dv[3]);
+            reinterpret_cast<float4 *>(p)[i] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        } else {
+            reinterpret_cast<float2 *>(d)[i] = make_float2(dv[0], dv[1]);
+            reinterpret_cast<float2 *>(p)[i] = make_float2(pv[0], pv[1]);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        uint32_t na = ab;
+        for (int j = 0; j < K; ++j) {
+            if (!((ab >> j) & 1u)) continue;
+            const double rr = tot[j];
+            si->rho[j] = rr;
+            const int t1 = so->iters[j] + 1;
+            so->iters[j] = t1;
+            if (sqrt(rr) <= si->tau[j] * sqrt(si->rho0[j]) || t1 >= so->max_iter) na &= ~(1u << j);
+        }
+        si->iter = k + 1;
+        so->loops += 1;
+        si->act = na;
+        if (!na) stop_loop_b(si, k + 1, h, use_cond);
+    }
+}
+
+// One block, after the refinement's residual (k_residualB without b): each
+// refining column's outer decision (converged, inner breakdown, refinement or
+// iteration cap) and the outer loop condition.  With final != 0 it only
+// stores the true residual of every column in aux.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_outer_finB(const double *part, int G, ScalB *so, const ScalB *si,
+                                                       int final_, cudaGraphConditionalHandle h, int use_cond) {
+    __shared__ double rr[K];
+    all_sum_cols<K>(part, G, rr);
+    if (threadIdx.x != 0) return;
+    if (final_) {
+        for (int j = 0; j < K; ++j) so->aux[j] = rr[j];
+        return;
+    }
+    uint32_t na = so->act;
+    for (int j = 0; j < K; ++j) {
+        if (!((na >> j) & 1u)) continue;
+        const double tot = rr[j];
+        so->rho[j] = tot;
+        so->outer[j] += 1;
+        so->relres[j] = so->bnorm[j] > 0.0 ? sqrt(tot) / so->bnorm[j] : 0.0;
+        int stop = 1;
+        if (sqrt(tot) <= so->rtol * so->bnorm[j]) {
+            so->status[j] = SSG_OK;
+        } else if (si->status[j] == SSG_E_BREAKDOWN) {
+            so->status[j] = SSG_E_BREAKDOWN;
+        } else if (so->outer[j] >= so->max_outer || so->iters[j] >= so->max_iter) {
+            so->status[j] = SSG_E_NOT_CONVERGED;
+        } else {
+            stop = 0;
+        }
+        if (stop) na &= ~(1u << j);
+    }
+    so->act = na;
+    so->iter += 1;
+    so->done = na == 0;
+    if (use_cond) cudaGraphSetConditional(h, na ? 1u : 0u);
+}
+
+// Global (n x k, right-hand side j at j*n) <-> interleaved local block
+// (nloc x K); columns k..K-1 of the block are zero.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_scatterB(int64_t N, const int32_t *__restrict__ l2g, int64_t n, int nr,
+                                                     const double *__restrict__ xg, double *__restrict__ xl) {
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < N * K; e += stride) {
+        const int64_t i = e / K;
+        const int j = (int)(e % K);
+        xl[e] = j < nr ? __ldg(xg + (int64_t)j * n + l2g[i]) : 0.0;
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_gatherB(int64_t n, const int32_t *__restrict__ own, int nr,
+                                                    const double *__restrict__ xl, double *__restrict__ xg) {
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < n * nr; e += stride) {
+        const int j = (int)(e / n);
+        const int64_t g = e % n;
+        xg[e] = __ldg(xl + (int64_t)own[g] * K + j);
+    }
+}
+
+}  // namespace ssg

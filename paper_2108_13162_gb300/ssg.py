@@ -36,6 +36,7 @@ EXPORTS = (
     "ssg_set_stream",
     "ssg_set_driver",
     "ssg_set_mixed",
+    "ssg_set_rhs_block",
     "ssg_set_pdl",
     "ssg_destroy",
     "ssg_partition",
@@ -45,6 +46,8 @@ EXPORTS = (
     "ssg_gather",
     "ssg_spmv_assembled",
     "ssg_spmv_assembled_f32",
+    "ssg_spmm_assembled",
+    "ssg_spmm_assembled_f32",
     "ssg_wdot",
     "ssg_solve",
     "ssg_solve_host",
@@ -72,7 +75,7 @@ class ssg_stats(C.Structure):
         ("status", C.c_int32),
         ("iters", C.c_int32),
         ("outer", C.c_int32),
-        ("reserved", C.c_int32),
+        ("block", C.c_int32),
         ("relres", C.c_double),
         ("true_relres", C.c_double),
         ("solve_ms", C.c_double),
@@ -80,7 +83,7 @@ class ssg_stats(C.Structure):
     ]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class SSGError(RuntimeError):
@@ -117,6 +120,7 @@ def lib():
         L.ssg_set_stream.argtypes = [vp, vp]
         L.ssg_set_driver.argtypes = [vp, C.c_int]
         L.ssg_set_mixed.argtypes = [vp, C.c_double, C.c_int32]
+        L.ssg_set_rhs_block.argtypes = [vp, C.c_int32]
         L.ssg_set_pdl.argtypes = [vp, C.c_int]
         L.ssg_destroy.argtypes = [vp]
         L.ssg_partition.argtypes = [vp, i32, vp, vp, vp, vp, i32, C.POINTER(vp)]
@@ -127,6 +131,8 @@ def lib():
         L.ssg_spmv_assembled.argtypes = [vp, vp, vp, vp]
         L.ssg_spmv_assembled_f32.argtypes = [vp, vp, vp, vp]
         L.ssg_wdot.argtypes = [vp, vp, vp, vp]
+        L.ssg_spmm_assembled.argtypes = [vp, i32, vp, vp]
+        L.ssg_spmm_assembled_f32.argtypes = [vp, i32, vp, vp]
         L.ssg_solve.argtypes = [vp, i32, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
         L.ssg_solve_host.argtypes = [vp, i32, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
         L.ssg_system_destroy.argtypes = [vp]
@@ -188,6 +194,10 @@ def ssg_set_driver(ctx, driver: int):
 
 def ssg_set_mixed(ctx, inner_rtol: float, max_outer: int):
     return _check(lib().ssg_set_mixed(ctx, inner_rtol, max_outer), "ssg_set_mixed")
+
+
+def ssg_set_rhs_block(ctx, kmax: int):
+    return _check(lib().ssg_set_rhs_block(ctx, kmax), "ssg_set_rhs_block")
 
 
 def ssg_set_pdl(ctx, enable: bool):
@@ -267,6 +277,14 @@ def ssg_spmv_assembled_f32(sys, x_loc, y_loc, xSx=None):
         lib().ssg_spmv_assembled_f32(sys, _dev_f32(x_loc), _dev_f32(y_loc), None if xSx is None else _dev_f64(xSx)),
         "ssg_spmv_assembled_f32",
     )
+
+
+def ssg_spmm_assembled(sys, k, x_loc, y_loc):
+    return _check(lib().ssg_spmm_assembled(sys, k, _dev_f64(x_loc), _dev_f64(y_loc)), "ssg_spmm_assembled")
+
+
+def ssg_spmm_assembled_f32(sys, k, x_loc, y_loc):
+    return _check(lib().ssg_spmm_assembled_f32(sys, k, _dev_f32(x_loc), _dev_f32(y_loc)), "ssg_spmm_assembled_f32")
 
 
 def ssg_wdot(sys, u_loc, v_loc, out):
@@ -352,6 +370,10 @@ class Context:
     def set_mixed(self, inner_rtol: float = 1e-4, max_outer: int = 30):
         ssg_set_mixed(self.h, inner_rtol, max_outer)
 
+    def set_rhs_block(self, kmax: int = 16):
+        """Right-hand sides of one solve call that iterate together (1, 2, 4, 8, 16)."""
+        ssg_set_rhs_block(self.h, kmax)
+
     def close(self):
         """Free the context once no System created on it is alive (the C
         library refuses earlier; a System keeps its Context referenced)."""
@@ -395,6 +417,19 @@ class System:
     def spmv(self, x_loc, out=None, xSx=None):
         out = self._empty_loc() if out is None else out
         ssg_spmv_assembled(self.h, x_loc, out, xSx)
+        return out
+
+    def spmm(self, x_loc, out=None):
+        """Product with k vectors: x_loc is an (nloc, k) CUDA tensor (row-major,
+        i.e. interleaved), float64 or float32; k = 2, 4, 8 or 16."""
+        import torch
+
+        k = x_loc.shape[1]
+        out = torch.empty_like(x_loc) if out is None else out
+        if x_loc.dtype == torch.float32:
+            ssg_spmm_assembled_f32(self.h, k, x_loc, out)
+        else:
+            ssg_spmm_assembled(self.h, k, x_loc, out)
         return out
 
     def spmv_prec(self, x_loc, out, prec="fp64", xSx=None):
