@@ -266,7 +266,9 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (no FP64 figure is measured on this poo
 def bench_multi_rhs(ctx, stream, reps, spmv_reps):
     """The 16-right-hand-side workload (96^3 FV, 27 subdomains): time to 1e-8
     for all 16 with the columns iterating together (K = 16) and one after
-    another, FP64 and mixed, plus the k-vector product's roofline."""
+    another, FP64 and mixed, the differentiable solve (forward + adjoint),
+    and the k-vector product's roofline."""
+    import numpy as np
     import torch
 
     from paper_2108_13162_gb300 import ssg
@@ -300,6 +302,32 @@ def bench_multi_rhs(ctx, stream, reps, spmv_reps):
             out[key + "_true_relres_max"] = max(s["true_relres"] for s in st)
             out[key + "_launches"] = sum(s["kernel_launches"] for s in st) if kb == 1 else st[0]["kernel_launches"]
     ctx.set_rhs_block(16)
+    # the differentiable solve: L = sum_j ||x_j - t_j||^2, gradients with
+    # respect to B and the per-cell log conductivities (forward + adjoint)
+    from paper_2108_13162_gb300 import autograd as ag
+
+    dims = tuple(p.meta["grid"])
+    logk0 = torch.from_numpy(p.meta["log_kappa"].ravel().copy()).cuda()
+    Tt = torch.from_numpy(np.random.default_rng(2108).uniform(-1, 1, tuple(B.shape))).cuda()
+    for mode_name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED)):
+        def step():
+            lk = logk0.clone().requires_grad_(True)
+            Bg = B.clone().requires_grad_(True)
+            Xs = ag.solve(S, ag.fv7_values(S, dims, lk), Bg, rtol=RTOL, mode=mode)
+            L = torch.sum((Xs - Tt) ** 2)
+            L.backward()
+            return lk.grad, Bg.grad
+        step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            gk, gb = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["grad_%s_s" % mode_name] = e0.elapsed_time(e1) / 1e3 / reps
+        out["grad_%s_norms" % mode_name] = [float(gk.norm()), float(gb.norm())]
     peak, peak_src = measured_peaks()
     flops = 2.0 * p.A.nnz * 16
     t64 = time_spmm(S, "fp64", 16, stream, spmv_reps)

@@ -243,6 +243,38 @@ int ssg_solve(ssg_system *sys, int32_t k, const double *b, double *x, int32_t x_
 int ssg_solve_host(ssg_system *sys, int32_t k, const double *b_host, double *x_host, int32_t x_is_guess,
                    double rtol, int32_t max_iter, int32_t mode, ssg_stats *stats);
 
+/*
+ * Differentiable solves (not in the paper; its method is the forward solve).
+ *
+ * ssg_set_values: new matrix values for the same pattern.  val (device, nnz
+ * doubles) is in the order of the CSR given to ssg_partition; every device
+ * copy of the local matrices (FP64 and the FP32 rounding of SSG_MIXED) is
+ * refreshed on the context stream.  The values must stay symmetric and the
+ * matrix positive definite (a solve reports SSG_E_BREAKDOWN otherwise); the
+ * host maps of ssg_copy_maps keep the values given at partition time.
+ *
+ * ssg_pattern_grad: g[e] = -sum_{j<k} lam[j*n + i] * x[j*n + c] for each
+ * stored entry e = (i, c) of that CSR (device, nnz doubles): the gradient of
+ * a loss L(x) with respect to the stored entries of S when S x_j = b_j and
+ * S lam_j = dL/dx_j (S symmetric).  lam and x: device, n*k, column j at j*n.
+ */
+int ssg_set_values(ssg_system *sys, const double *val);
+int ssg_pattern_grad(ssg_system *sys, int32_t k, const double *lam, const double *x, double *g);
+/*
+ * 7-point finite-volume diffusion on an nx x ny x nz cell grid (the synthetic
+ * workloads): cell (ix, iy, iz) = ix + nx (iy + ny iz), kappa = exp(logk),
+ * an interior face carries the harmonic mean 2 k_a k_b / (k_a + k_b), a
+ * boundary face 2 k; A_ij = -t of the shared face, A_ii = sum of the cell's
+ * six face coefficients.  ssg_fv7_values writes the nnz values (device, CSR
+ * order, columns ascending in each row); ssg_fv7_adjoint maps g = dL/dA
+ * (device, CSR order) to dL/dlogk (device, n).  The system's matrix must
+ * have this grid's 7-point pattern (checked on the host at the first call
+ * for a grid: SSG_E_INVALID otherwise).
+ */
+int ssg_fv7_values(ssg_system *sys, int32_t nx, int32_t ny, int32_t nz, const double *logk, double *val);
+int ssg_fv7_adjoint(ssg_system *sys, int32_t nx, int32_t ny, int32_t nz, const double *logk, const double *g,
+                    double *glogk);
+
 int ssg_system_destroy(ssg_system *sys);
 
 /*

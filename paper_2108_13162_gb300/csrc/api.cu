@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "block.cuh"
 #include "kernels.cuh"
 #include "ssg_internal.h"
@@ -71,6 +72,12 @@ struct ssg_system {
     cudaGraphExec_t exec_m = nullptr;
     cudaGraphConditionalHandle cond_out = 0, cond_in = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // new values for the same pattern (ssg_set_values): the input-CSR entry
+    // each device value copies (-1: padding)
+    int32_t *d_vmap = nullptr, *d_imap = nullptr, *d_smap = nullptr;
+    int64_t n_ival = 0, n_sval = 0;
+    int32_t *d_growptr = nullptr;  // 7-point grid row pointers (ssg_fv7_*), after the pattern check
+    int fv7_dims[3] = {0, 0, 0};
     // several right-hand sides together (block.cuh)
     DevOp opB64{}, opB32{};  // SpMM launches: warp ranges for grid_spmmB64 / grid_spmmB32 blocks
     int grid_spmmB64 = 0, grid_spmmB32 = 0;
@@ -134,6 +141,7 @@ cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), int grid, int block, cuda
 struct WorkPlan {
     std::vector<int32_t> irp, icol;  // interface copy rows in CSR form (long nodes)
     std::vector<double> ival;
+    std::vector<int32_t> isrc, ssrc;  // local entry each copy-row / sliced value copies (-1: padding)
     std::vector<double> sval;        // sliced-ELL values
     std::vector<int32_t> scol, sseg;
     std::vector<WorkItem> items;
@@ -182,6 +190,7 @@ WorkPlan make_plan(const HostMaps &M, int num_sms) {
         for (int32_t k = M.lrowptr[row]; k < M.lrowptr[row + 1]; ++k) {
             W.icol.push_back(o + M.lcol[k]);
             W.ival.push_back(M.lval[k]);
+            W.isrc.push_back(k);
         }
         W.irp[c + 1] = static_cast<int32_t>(W.icol.size());
     }
@@ -208,9 +217,11 @@ WorkPlan make_plan(const HostMaps &M, int num_sms) {
                         const int32_t e = M.lrowptr[row] + k;
                         W.sval.push_back(M.lval[e]);
                         W.scol.push_back(o + M.lcol[e]);
+                        W.ssrc.push_back(e);
                     } else {
                         W.sval.push_back(0.0);
                         W.scol.push_back(row < r1 ? row : r);
+                        W.ssrc.push_back(-1);
                     }
                 }
             rows.push_back({kItemSlice, r, r1, off, w, 0, 0, 0});
@@ -249,9 +260,11 @@ WorkPlan make_plan(const HostMaps &M, int num_sms) {
                 if (c < c1 && k < W.irp[c + 1] - W.irp[c]) {
                     W.sval.push_back(W.ival[W.irp[c] + k]);
                     W.scol.push_back(W.icol[W.irp[c] + k]);
+                    W.ssrc.push_back(W.isrc[W.irp[c] + k]);
                 } else {
                     W.sval.push_back(0.0);
                     W.scol.push_back(M.icopy[c < c1 ? c : c0]);
+                    W.ssrc.push_back(-1);
                 }
             }
         iface.push_back({kItemIfaceSlice, c0, c1, off, w, 0, 0, 0});
@@ -585,6 +598,12 @@ int upload(ssg_system *S) {
     size_t i_q32 = add(nullptr, sizeof(float) * N);
     size_t i_d32 = add(nullptr, sizeof(float) * N);
     size_t i_scal_in = add(nullptr, sizeof(Scal));
+    std::vector<int32_t> imap(plan.isrc.size()), smap(plan.ssrc.size());
+    for (size_t i = 0; i < imap.size(); ++i) imap[i] = M.lsrc[plan.isrc[i]];
+    for (size_t i = 0; i < smap.size(); ++i) smap[i] = plan.ssrc[i] >= 0 ? M.lsrc[plan.ssrc[i]] : -1;
+    size_t i_vmap = add(M.lsrc.data(), sizeof(int32_t) * M.nnz);
+    size_t i_imap = add(imap.data(), sizeof(int32_t) * imap.size());
+    size_t i_smap = add(smap.data(), sizeof(int32_t) * smap.size());
     size_t i_bl = add(nullptr, sizeof(double) * N);
     size_t i_xl = add(nullptr, sizeof(double) * N);
     size_t i_r = add(nullptr, sizeof(double) * N);
@@ -617,6 +636,11 @@ int upload(ssg_system *S) {
     S->d_q32 = static_cast<float *>(at(i_q32));
     S->d_d32 = static_cast<float *>(at(i_d32));
     S->d_scal_in = static_cast<Scal *>(at(i_scal_in));
+    S->d_vmap = static_cast<int32_t *>(at(i_vmap));
+    S->d_imap = static_cast<int32_t *>(at(i_imap));
+    S->d_smap = static_cast<int32_t *>(at(i_smap));
+    S->n_ival = static_cast<int64_t>(imap.size());
+    S->n_sval = static_cast<int64_t>(smap.size());
     S->op.irp = static_cast<const int32_t *>(at(i_irp));
     S->op.icol = static_cast<const int32_t *>(at(i_icol));
     S->op.ival = static_cast<const double *>(at(i_ival));
@@ -1173,6 +1197,62 @@ int spmm_checked(ssg_system *S, int32_t k, const T *x_loc, T *y_loc) {
     return SSG_OK;
 }
 
+// The system's input matrix must have the 7-point pattern of an nx x ny x nz
+// grid (rows in cell order, columns ascending) before the grid kernels may
+// index it: checked once on the host from the entry map, then the row
+// pointers go to the device.
+int check_fv7(ssg_system *S, int nx, int ny, int nz) {
+    if (S->d_growptr && S->fv7_dims[0] == nx && S->fv7_dims[1] == ny && S->fv7_dims[2] == nz) return SSG_OK;
+    const HostMaps &M = S->maps;
+    if (nx < 1 || ny < 1 || nz < 1 || static_cast<int64_t>(nx) * ny * nz != M.n) {
+        set_error("grid size does not match the system");
+        return SSG_E_INVALID;
+    }
+    const int64_t n = M.n;
+    std::vector<int32_t> rp(static_cast<size_t>(n) + 1, 0), cols;
+    cols.reserve(static_cast<size_t>(M.nnz));
+    const int64_t sxy = static_cast<int64_t>(nx) * ny;
+    for (int64_t i = 0; i < n; ++i) {
+        const int ix = static_cast<int>(i % nx), iy = static_cast<int>((i / nx) % ny), iz = static_cast<int>(i / sxy);
+        if (iz > 0) cols.push_back(static_cast<int32_t>(i - sxy));
+        if (iy > 0) cols.push_back(static_cast<int32_t>(i - nx));
+        if (ix > 0) cols.push_back(static_cast<int32_t>(i - 1));
+        cols.push_back(static_cast<int32_t>(i));
+        if (ix < nx - 1) cols.push_back(static_cast<int32_t>(i + 1));
+        if (iy < ny - 1) cols.push_back(static_cast<int32_t>(i + nx));
+        if (iz < nz - 1) cols.push_back(static_cast<int32_t>(i + sxy));
+        rp[i + 1] = static_cast<int32_t>(cols.size());
+    }
+    if (static_cast<int64_t>(cols.size()) != M.nnz) {
+        set_error("the system's matrix does not have the 7-point pattern of this grid");
+        return SSG_E_INVALID;
+    }
+    // every local entry (row l2g[r], column l2g[off + lcol]) must sit at the
+    // input position the pattern gives it
+    for (int32_t s = 0; s < M.P; ++s)
+        for (int64_t r = M.off[s]; r < M.off[s + 1]; ++r) {
+            const int64_t gi = M.l2g[r];
+            for (int32_t e = M.lrowptr[r]; e < M.lrowptr[r + 1]; ++e) {
+                const int32_t k = M.lsrc[e];
+                const int32_t gj = M.l2g[M.off[s] + M.lcol[e]];
+                if (k < rp[gi] || k >= rp[gi + 1] || cols[k] != gj) {
+                    set_error("the system's matrix does not have the 7-point pattern of this grid");
+                    return SSG_E_INVALID;
+                }
+            }
+        }
+    if (S->d_growptr) cudaFree(S->d_growptr);
+    S->d_growptr = nullptr;
+    SSG_CUDA_TRY(cudaMalloc(&S->d_growptr, sizeof(int32_t) * rp.size()));
+    SSG_CUDA_TRY(cudaMemcpyAsync(S->d_growptr, rp.data(), sizeof(int32_t) * rp.size(), cudaMemcpyHostToDevice,
+                                 S->ctx->stream));
+    SSG_CUDA_TRY(cudaStreamSynchronize(S->ctx->stream));
+    S->fv7_dims[0] = nx;
+    S->fv7_dims[1] = ny;
+    S->fv7_dims[2] = nz;
+    return SSG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1414,6 +1494,74 @@ int ssg_wdot(ssg_system *S, const double *u, const double *v, double *result_dev
     return SSG_OK;
 }
 
+int ssg_set_values(ssg_system *S, const double *val) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (!val) {
+        set_error("null values");
+        return SSG_E_INVALID;
+    }
+    cudaStream_t st = S->ctx->stream;
+    const int ns = S->ctx->num_sms;
+    k_gather_vals<<<grid_for(S->maps.nnz, ns), kBlock, 0, st>>>(S->maps.nnz, S->d_vmap, val,
+                                                                const_cast<double *>(S->op.val),
+                                                                const_cast<float *>(S->op.val32));
+    if (S->n_ival)
+        k_gather_vals<<<grid_for(S->n_ival, ns), kBlock, 0, st>>>(S->n_ival, S->d_imap, val,
+                                                                  const_cast<double *>(S->op.ival),
+                                                                  const_cast<float *>(S->op.ival32));
+    if (S->n_sval)
+        k_gather_vals<<<grid_for(S->n_sval, ns), kBlock, 0, st>>>(S->n_sval, S->d_smap, val,
+                                                                  const_cast<double *>(S->op.sval),
+                                                                  const_cast<float *>(S->op.sval32));
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int ssg_pattern_grad(ssg_system *S, int32_t k, const double *lam, const double *x, double *g) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (k < 1 || !lam || !x || !g) {
+        set_error("bad k or null vector");
+        return SSG_E_INVALID;
+    }
+    k_pattern_grad<<<grid_for(S->maps.nloc, S->ctx->num_sms), kBlock, 0, S->ctx->stream>>>(
+        S->maps.nloc, S->maps.n, k, S->op.rowptr, S->op.col, S->d_l2g, S->d_vmap, lam, x, g);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int ssg_fv7_values(ssg_system *S, int32_t nx, int32_t ny, int32_t nz, const double *logk, double *val) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (!logk || !val) {
+        set_error("null vector");
+        return SSG_E_INVALID;
+    }
+    rc = check_fv7(S, nx, ny, nz);
+    if (rc != SSG_OK) return rc;
+    k_fv7_values<<<grid_for(S->maps.n, S->ctx->num_sms), kBlock, 0, S->ctx->stream>>>(Fv7Grid{nx, ny, nz}, logk,
+                                                                                       S->d_growptr, val);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int ssg_fv7_adjoint(ssg_system *S, int32_t nx, int32_t ny, int32_t nz, const double *logk, const double *gval,
+                    double *glogk) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (!logk || !gval || !glogk) {
+        set_error("null vector");
+        return SSG_E_INVALID;
+    }
+    rc = check_fv7(S, nx, ny, nz);
+    if (rc != SSG_OK) return rc;
+    k_fv7_adjoint<<<grid_for(S->maps.n, S->ctx->num_sms), kBlock, 0, S->ctx->stream>>>(Fv7Grid{nx, ny, nz}, logk,
+                                                                                        S->d_growptr, gval, glogk);
+    SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
 int ssg_solve(ssg_system *S, int32_t k, const double *b, double *x, int32_t x_is_guess, double rtol,
               int32_t max_iter, int32_t mode, ssg_stats *stats) {
     int rc = check_dev(S);
@@ -1492,6 +1640,7 @@ int ssg_system_destroy(ssg_system *S) {
     if (S->ev0) cudaEventDestroy(S->ev0);
     if (S->ev1) cudaEventDestroy(S->ev1);
     free_block(S);
+    if (S->d_growptr) cudaFree(S->d_growptr);
     if (S->arena) {
         if (S->ctx && S->ctx->stream) cudaStreamSynchronize(S->ctx->stream);
         cudaFree(S->arena);

@@ -135,7 +135,8 @@ int build_host_maps(int32_t n, const int32_t *rowptr, const int32_t *colidx, con
         M.lrowptr.assign(static_cast<size_t>(M.nloc) + 1, 0);
         M.lcol.resize(static_cast<size_t>(M.nnz));
         M.lval.resize(static_cast<size_t>(M.nnz));
-        std::vector<std::pair<int32_t, double>> row;
+        M.lsrc.resize(static_cast<size_t>(M.nnz));
+        std::vector<std::pair<int32_t, int32_t>> row;  // (local column, entry of the input CSR)
         int64_t w = 0;
         for (int32_t s = 0; s < P; ++s) {
             const int32_t ns = M.off[s + 1] - M.off[s];
@@ -151,15 +152,16 @@ int build_host_maps(int32_t n, const int32_t *rowptr, const int32_t *colidx, con
                     const int32_t *mb = mem.data() + mptr[j], *me = mem.data() + mptr[j + 1];
                     const int32_t *f = std::lower_bound(mb, me, s);
                     if (f == me || *f != s) { *err = "internal: column node missing from subdomain"; return SSG_E_INVALID; }
-                    row.emplace_back(loc[f - mem.data()], val[k]);
+                    row.emplace_back(loc[f - mem.data()], k);
                 }
                 std::sort(row.begin(), row.end(),
-                          [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
+                          [](const std::pair<int32_t, int32_t> &a, const std::pair<int32_t, int32_t> &b) {
                               return a.first < b.first;
                           });
                 for (auto &e : row) {
                     M.lcol[w] = e.first;
-                    M.lval[w] = e.second;
+                    M.lval[w] = val[e.second];
+                    M.lsrc[w] = e.second;
                     ++w;
                 }
                 M.lrowptr[static_cast<size_t>(M.off[s]) + li + 1] = static_cast<int32_t>(w);

@@ -18,6 +18,7 @@ struct HostMaps {
     int64_t ncopies = 0;
     std::vector<int32_t> off, nint, l2g, mult, lrowptr, lcol, gamma, iptr, icopy, own;
     std::vector<double> lval;
+    std::vector<int32_t> lsrc;  // entry of the input CSR each local entry copies (ownership is one-to-one)
 };
 
 // Returns SSG_OK or SSG_E_INVALID / SSG_E_OOM with a message in *err.

@@ -51,6 +51,10 @@ EXPORTS = (
     "ssg_wdot",
     "ssg_solve",
     "ssg_solve_host",
+    "ssg_set_values",
+    "ssg_pattern_grad",
+    "ssg_fv7_values",
+    "ssg_fv7_adjoint",
     "ssg_system_destroy",
     "ssg_error_string",
     "ssg_last_error",
@@ -132,6 +136,10 @@ def lib():
         L.ssg_spmv_assembled_f32.argtypes = [vp, vp, vp, vp]
         L.ssg_wdot.argtypes = [vp, vp, vp, vp]
         L.ssg_spmm_assembled.argtypes = [vp, i32, vp, vp]
+        L.ssg_set_values.argtypes = [vp, vp]
+        L.ssg_pattern_grad.argtypes = [vp, i32, vp, vp, vp]
+        L.ssg_fv7_values.argtypes = [vp, i32, i32, i32, vp, vp]
+        L.ssg_fv7_adjoint.argtypes = [vp, i32, i32, i32, vp, vp, vp]
         L.ssg_spmm_assembled_f32.argtypes = [vp, i32, vp, vp]
         L.ssg_solve.argtypes = [vp, i32, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
         L.ssg_solve_host.argtypes = [vp, i32, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
@@ -285,6 +293,23 @@ def ssg_spmm_assembled(sys, k, x_loc, y_loc):
 
 def ssg_spmm_assembled_f32(sys, k, x_loc, y_loc):
     return _check(lib().ssg_spmm_assembled_f32(sys, k, _dev_f32(x_loc), _dev_f32(y_loc)), "ssg_spmm_assembled_f32")
+
+
+def ssg_set_values(sys, val):
+    return _check(lib().ssg_set_values(sys, _dev_f64(val)), "ssg_set_values")
+
+
+def ssg_pattern_grad(sys, k, lam, x, g):
+    return _check(lib().ssg_pattern_grad(sys, k, _dev_f64(lam), _dev_f64(x), _dev_f64(g)), "ssg_pattern_grad")
+
+
+def ssg_fv7_values(sys, nx, ny, nz, logk, val):
+    return _check(lib().ssg_fv7_values(sys, nx, ny, nz, _dev_f64(logk), _dev_f64(val)), "ssg_fv7_values")
+
+
+def ssg_fv7_adjoint(sys, nx, ny, nz, logk, g, glogk):
+    return _check(lib().ssg_fv7_adjoint(sys, nx, ny, nz, _dev_f64(logk), _dev_f64(g), _dev_f64(glogk)),
+                  "ssg_fv7_adjoint")
 
 
 def ssg_wdot(sys, u_loc, v_loc, out):
