@@ -472,7 +472,7 @@ def run_ours(args, dist):
     S = System(ctx, prob.A, prob.part, prob.P)
     b = torch.from_numpy(prob.b[:, 0].copy()).to("cuda:%d" % dev)
     x = torch.zeros_like(b)
-    modes = {"fp64": ssg.SSG_FP64, "mixed": ssg.SSG_MIXED}
+    modes = {"fp64": ssg.SSG_FP64, "mixed": ssg.SSG_MIXED, "jacobi": ssg.SSG_FP64_JACOBI}
 
     def solve(mode):
         x.zero_()
@@ -512,6 +512,12 @@ def run_ours(args, dist):
     for _ in range(max(args.warmup, 0)):
         solve(other)
     ms_other, sts_other, _ = timed(other, args.steps)
+
+    # Algorithm 3 with the paper's diagonal preconditioner, same protocol (reported)
+    for _ in range(max(args.warmup, 0)):
+        x.zero_()
+        ssg.ssg_solve(S.h, 1, b, x, False, RTOL, 0, ssg.SSG_FP64_JACOBI)
+    ms_jac, sts_jac, _ = timed("jacobi", args.steps)
 
     # end to end through the host-buffer C ABI call (pinned host memory)
     bh = torch.from_numpy(prob.b[:, 0].copy()).pin_memory().numpy()
@@ -586,6 +592,9 @@ def run_ours(args, dist):
             other + "_iters": sts_other[-1]["iters"],
             other + "_true_relres": sts_other[-1]["true_relres"],
             "fp64_us_per_iter": (ms_step if args.mode == "fp64" else ms_other) * 1e3 / statistics.median(fp64_iters),
+            "jacobi_s": ms_jac / 1e3,
+            "jacobi_iters": sts_jac[-1]["iters"],
+            "jacobi_true_relres": sts_jac[-1]["true_relres"],
             "l2": "inputs larger than L2 (175 MB matrix + 5 x 18 MB vectors > 129 MB)",
             "parallelism": "replicas" if dist.world > 1 else "single",
             "driver": args.driver,

@@ -51,6 +51,9 @@ extern "C" {
 /* solve modes */
 #define SSG_FP64 0  /* Algorithm 3 in FP64 throughout */
 #define SSG_MIXED 1 /* FP32 inner CG inside FP64 iterative refinement */
+#define SSG_FP64_JACOBI 2 /* Algorithm 3 with the diagonal preconditioner M = diag(S) of the   \
+                             paper's experiments (Section 3.1), FP64; right-hand sides solved \
+                             one after another */
 
 /* driver modes (ssg_set_driver) */
 #define SSG_DRIVER_GRAPH 0 /* one CUDA-graph launch per solve, device-side while loop */
@@ -123,8 +126,7 @@ int ssg_destroy(ssg_ctx *ctx);
 /*
  * Sub-structuring of Section 2.4 (Eq. 2.4:eqn0, mat_subdomains,
  * interface_summation) for an assembled matrix, plus the interface lists of
- * Section 3.4.2 ("the list of nodes along the interface and the number of
- * neighboring sub-domains").
+ * Section 3.4.2 (for every interface node, the subdomains that hold it).
  *
  * Inputs (host, copied): S in 0-based CSR (rowptr[n+1], colidx[nnz],
  * val[nnz]); columns sorted and unique in each row; the pattern and the values
@@ -223,7 +225,11 @@ int ssg_wdot(ssg_system *sys, const double *u_loc, const double *v_loc, double *
  * initial guess x_1, else the iteration starts from 0.  Readings where the
  * paper is silent: stop after the first iteration with
  * sqrt((r,r)_w) <= rtol * sqrt((b,b)_w) (recursive residual) or after
- * max_iter iterations (max_iter <= 0 means n).  mode = SSG_FP64 or SSG_MIXED.
+ * max_iter iterations (max_iter <= 0 means n).  mode = SSG_FP64, SSG_MIXED or
+ * SSG_FP64_JACOBI.  SSG_FP64_JACOBI: z = M^-1 r with M = diag(S) (stored as
+ * the reciprocal 1 / S_ii per local entry), alpha = (r, z)_w / (S p, p)_w,
+ * beta = (r, z)_w(k+1) / (r, z)_w(k), p = z + beta p; the stopping test stays
+ * on (r, r)_w; SSG_E_INVALID if a diagonal entry is missing or not positive.
  * SSG_MIXED: iterative refinement in FP64 (r = b - S x with the FP64
  * sub-structured SpMV, x += d, the stopping test on that true residual)
  * around an inner Algorithm 3 in FP32 (values, vectors and SpMV in FP32, dot

@@ -58,6 +58,11 @@ struct ssg_system {
     double *d_partials = nullptr;
     int32_t n_partials = 0;
     Scal *d_scal = nullptr;     // CG state
+    int32_t *d_dmap = nullptr;  // local entry holding the diagonal of each local entry's node
+    double *d_dinv = nullptr;   // 1 / diag(S) per local entry (SSG_FP64_JACOBI)
+    float *d_dinv32 = nullptr;
+    int *d_diag_bad = nullptr;  // set by k_dinv on a missing or non-positive diagonal
+    int diag_state = -1;        // host copy of *d_diag_bad: -1 not read since the values changed
     Scal *d_scal_op = nullptr;  // state for the stand-alone SpMV / dot calls
     double *d_xg = nullptr, *d_bg = nullptr;  // global staging for ssg_solve_host
     bool pdl = false;  // loop-body kernels use programmatic dependent launch
@@ -68,6 +73,9 @@ struct ssg_system {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle cond = 0;
+    cudaGraph_t graph_pc = nullptr;  // SSG_FP64_JACOBI
+    cudaGraphExec_t exec_pc = nullptr;
+    cudaGraphConditionalHandle cond_pc = 0;
     cudaGraph_t graph_m = nullptr;  // SSG_MIXED: nested refinement / inner loops
     cudaGraphExec_t exec_m = nullptr;
     cudaGraphConditionalHandle cond_out = 0, cond_in = 0;
@@ -291,101 +299,43 @@ WorkPlan make_plan(const HostMaps &M, int num_sms) {
     return W;
 }
 
-// Partials of the loop reductions: the SpMV writes the first half, the
-// residual update the second, each read by the next kernel.
+// Partials of the loop reductions, three slots of n_partials / 3: the SpMV
+// writes (p, S p)_w, the residual update (r, r)_w and, with the diagonal
+// preconditioner, (r, z)_w; each is read by the next kernel.
 double *part_pq(ssg_system *S) { return S->d_partials; }
-double *part_rr(ssg_system *S) { return S->d_partials + S->n_partials / 2; }
+double *part_rr(ssg_system *S) { return S->d_partials + S->n_partials / 3; }
+double *part_rz(ssg_system *S) { return S->d_partials + 2 * (S->n_partials / 3); }
 
-int launch_body(ssg_system *S, cudaStream_t st, int use_cond) {
+int launch_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const int64_t N = S->maps.nloc;
+    const cudaGraphConditionalHandle h = pc ? S->cond_pc : S->cond;
     SSG_CUDA_TRY(launch_k(false, k_spmv_asm<kEpiPartials, double>, S->grid_spmv, kSpmvThreads, st, S->op, S->d_p,
-                          S->d_q, part_pq(S), S->d_scal, (double *)nullptr, S->cond, use_cond));
-    SSG_CUDA_TRY(launch_k(S->pdl, k_update_r, S->grid_vec, kBlock, st, N, S->d_r, S->d_q, S->op.mult, S->op.wtab,
-                          S->op.gflag, (const double *)part_pq(S), S->grid_spmv, part_rr(S), S->d_scal, S->cond,
-                          use_cond));
-    SSG_CUDA_TRY(launch_k(S->pdl, k_update_xp, S->grid_vec, kBlock, st, N, S->d_xl, S->d_p, S->d_r,
-                          (const double *)part_rr(S), S->grid_vec, S->d_scal, S->cond, use_cond));
+                          S->d_q, part_pq(S), S->d_scal, (double *)nullptr, h, use_cond));
+    SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_r<true> : k_update_r<false>, S->grid_vec, kBlock, st, N, S->d_r,
+                          S->d_q, S->op.mult, S->op.wtab, S->op.gflag, (const double *)part_pq(S), S->grid_spmv,
+                          part_rr(S), S->d_scal, h, use_cond, (const double *)S->d_dinv, part_rz(S)));
+    SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_xp<true> : k_update_xp<false>, S->grid_vec, kBlock, st, N, S->d_xl,
+                          S->d_p, S->d_r, (const double *)part_rr(S), S->grid_vec, S->d_scal, h, use_cond,
+                          (const double *)S->d_dinv, (const double *)part_rz(S)));
     return SSG_OK;
 }
 
-int launch_init(ssg_system *S, cudaStream_t st, int use_cond) {
-    k_cg_init<<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_bl, S->d_q, S->d_r, S->d_p, S->op.mult,
-                                              S->op.wtab, S->d_partials, S->d_scal, S->cond, use_cond);
+int launch_init(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
+    const cudaGraphConditionalHandle h = pc ? S->cond_pc : S->cond;
+    if (pc)
+        k_cg_init<true><<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_bl, S->d_q, S->d_r, S->d_p, S->op.mult,
+                                                        S->op.wtab, S->d_partials, S->d_scal, h, use_cond, S->d_dinv);
+    else
+        k_cg_init<false><<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_bl, S->d_q, S->d_r, S->d_p, S->op.mult,
+                                                         S->op.wtab, S->d_partials, S->d_scal, h, use_cond, nullptr);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
 
-int build_graph_once(ssg_system *S);
-
-// Build the FP64 graph; if the driver refuses programmatic edges inside the
-// conditional body, rebuild it with plain launches.
-int build_graph(ssg_system *S) {
-    if (S->exec) return SSG_OK;
-    int rc = build_graph_once(S);
-    if (rc != SSG_OK && S->pdl) {
-        S->pdl = false;
-        rc = build_graph_once(S);
-    }
-    return rc;
-}
-
-int build_graph_once(ssg_system *S) {
-    SSG_CUDA_TRY(cudaGraphCreate(&S->graph, 0));
-    SSG_CUDA_TRY(cudaGraphConditionalHandleCreate(&S->cond, S->graph, 0u, cudaGraphCondAssignDefault));
-    cudaStream_t cap;
-    SSG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    int rc = SSG_OK;
-    // setup kernel
-    cudaError_t e = cudaStreamBeginCaptureToGraph(cap, S->graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-    if (e == cudaSuccess) {
-        rc = launch_init(S, cap, 1);
-        cudaGraph_t g2 = nullptr;
-        cudaError_t e2 = cudaStreamEndCapture(cap, &g2);
-        if (rc == SSG_OK && e2 != cudaSuccess) e = e2;
-    }
-    cudaGraphNode_t init_node = nullptr;
-    if (e == cudaSuccess && rc == SSG_OK) {
-        size_t nn = 0;
-        e = cudaGraphGetNodes(S->graph, nullptr, &nn);
-        if (e == cudaSuccess && nn == 1) e = cudaGraphGetNodes(S->graph, &init_node, &nn);
-    }
-    cudaGraph_t body = nullptr;
-    if (e == cudaSuccess && rc == SSG_OK) {
-        cudaGraphNodeParams cp = {};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = S->cond;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        cudaGraphNode_t cnode;
-        e = cudaGraphAddNode(&cnode, S->graph, &init_node, nullptr, 1, &cp);
-        if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
-    }
-    if (e == cudaSuccess && rc == SSG_OK) {
-        e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-        if (e == cudaSuccess) {
-            rc = launch_body(S, cap, 1);
-            cudaGraph_t g3 = nullptr;
-            cudaError_t e3 = cudaStreamEndCapture(cap, &g3);
-            if (rc == SSG_OK && e3 != cudaSuccess) e = e3;
-        }
-    }
-    if (e == cudaSuccess && rc == SSG_OK) e = cudaGraphInstantiate(&S->exec, S->graph, 0);
-    cudaStreamDestroy(cap);
-    if (rc != SSG_OK) return rc;
-    if (e != cudaSuccess) {
-        set_error(std::string("building the CG graph: ") + cudaGetErrorString(e));
-        if (S->graph) cudaGraphDestroy(S->graph);
-        S->graph = nullptr;
-        S->exec = nullptr;
-        return SSG_E_CUDA;
-    }
-    return SSG_OK;
-}
-
-
 int launch_mixed_init(ssg_system *S, cudaStream_t st, int use_cond) {
-    k_cg_init<<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_bl, S->d_q, S->d_r, nullptr, S->op.mult, S->op.wtab,
-                                              S->d_partials, S->d_scal, S->cond_out, use_cond);
+    k_cg_init<false><<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_bl, S->d_q, S->d_r, nullptr, S->op.mult,
+                                                     S->op.wtab, S->d_partials, S->d_scal, S->cond_out, use_cond,
+                                                     nullptr);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
@@ -464,6 +414,51 @@ cudaError_t add_while(cudaGraph_t g, const cudaGraphNode_t *dep, cudaGraphCondit
     return e;
 }
 
+int build_graph_once(ssg_system *S, bool pc);
+
+// Build the FP64 graph (with or without the diagonal preconditioner); if the
+// driver refuses programmatic edges inside the conditional body, rebuild it
+// with plain launches.
+int build_graph(ssg_system *S, bool pc) {
+    if (pc ? S->exec_pc : S->exec) return SSG_OK;
+    int rc = build_graph_once(S, pc);
+    if (rc != SSG_OK && S->pdl) {
+        S->pdl = false;
+        rc = build_graph_once(S, pc);
+    }
+    return rc;
+}
+
+int build_graph_once(ssg_system *S, bool pc) {
+    cudaGraph_t &graph = pc ? S->graph_pc : S->graph;
+    cudaGraphExec_t &exec = pc ? S->exec_pc : S->exec;
+    cudaGraphConditionalHandle &cond = pc ? S->cond_pc : S->cond;
+    SSG_CUDA_TRY(cudaGraphCreate(&graph, 0));
+    SSG_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, graph, 0u, cudaGraphCondAssignDefault));
+    cudaStream_t cap;
+    SSG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int rc = SSG_OK;
+    cudaGraphNode_t init_node = nullptr, loop_node = nullptr;
+    cudaGraph_t body = nullptr;
+    cudaError_t e = capture_into(cap, graph, nullptr, 0, [&](cudaStream_t c) { return launch_init(S, c, 1, pc); }, &rc);
+    if (e == cudaSuccess && rc == SSG_OK) e = last_node(graph, &init_node);
+    if (e == cudaSuccess && rc == SSG_OK) e = add_while(graph, &init_node, cond, &loop_node, &body);
+    if (e == cudaSuccess && rc == SSG_OK)
+        e = capture_into(cap, body, nullptr, 0, [&](cudaStream_t c) { return launch_body(S, c, 1, pc); }, &rc);
+    if (e == cudaSuccess && rc == SSG_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaStreamDestroy(cap);
+    if (rc != SSG_OK) return rc;
+    if (e != cudaSuccess) {
+        set_error(std::string("building the CG graph: ") + cudaGetErrorString(e));
+        if (graph) cudaGraphDestroy(graph);
+        graph = nullptr;
+        exec = nullptr;
+        return SSG_E_CUDA;
+    }
+    return SSG_OK;
+}
+
+
 // SSG_MIXED graph: init -> WHILE(outer) { inner_init -> WHILE(inner) { FP32
 // SpMV, r update, d/p update } -> x += d -> FP64 SpMV -> residual + test }.
 int build_graph_mixed_once(ssg_system *S);
@@ -513,6 +508,10 @@ int build_graph_mixed_once(ssg_system *S) {
     return SSG_OK;
 }
 
+int grid_for(int64_t n, int num_sms) {
+    return std::max(1, std::min<int>(static_cast<int>((n + kBlock - 1) / kBlock), num_sms * 8));
+}
+
 int upload(ssg_system *S) {
     const HostMaps &M = S->maps;
     ssg_ctx *C = S->ctx;
@@ -543,7 +542,7 @@ int upload(ssg_system *S) {
     S->grid_spmv = plan.grid64;
     S->grid_spmv32 = plan.grid32;
     S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N / 2 + kBlock - 1) / kBlock), C->num_sms * kVecBlocksPerSM));
-    S->n_partials = 2 * std::max(std::max(S->grid_spmv, S->grid_spmv32), S->grid_vec);
+    S->n_partials = 3 * std::max(std::max(S->grid_spmv, S->grid_spmv32), S->grid_vec);
 
     struct Piece {
         const void *src;
@@ -601,6 +600,18 @@ int upload(ssg_system *S) {
     std::vector<int32_t> imap(plan.isrc.size()), smap(plan.ssrc.size());
     for (size_t i = 0; i < imap.size(); ++i) imap[i] = M.lsrc[plan.isrc[i]];
     for (size_t i = 0; i < smap.size(); ++i) smap[i] = plan.ssrc[i] >= 0 ? M.lsrc[plan.ssrc[i]] : -1;
+    // local entry holding the diagonal of each local entry's node (in the
+    // owner's local matrix), -1 if the matrix stores none
+    std::vector<int32_t> diag_of_row(static_cast<size_t>(N), -1), dmap(static_cast<size_t>(N), -1);
+    for (int32_t sd = 0; sd < M.P; ++sd)
+        for (int64_t r = M.off[sd]; r < M.off[sd + 1]; ++r)
+            for (int32_t e = M.lrowptr[r]; e < M.lrowptr[r + 1]; ++e)
+                if (M.off[sd] + M.lcol[e] == r) diag_of_row[r] = e;
+    for (int64_t k = 0; k < N; ++k) dmap[k] = diag_of_row[M.own[M.l2g[k]]];
+    size_t i_dmap = add(dmap.data(), sizeof(int32_t) * N);
+    size_t i_dinv = add(nullptr, sizeof(double) * N);
+    size_t i_dinv32 = add(nullptr, sizeof(float) * N);
+    size_t i_diag_bad = add(nullptr, sizeof(int));
     size_t i_vmap = add(M.lsrc.data(), sizeof(int32_t) * M.nnz);
     size_t i_imap = add(imap.data(), sizeof(int32_t) * imap.size());
     size_t i_smap = add(smap.data(), sizeof(int32_t) * smap.size());
@@ -636,6 +647,10 @@ int upload(ssg_system *S) {
     S->d_q32 = static_cast<float *>(at(i_q32));
     S->d_d32 = static_cast<float *>(at(i_d32));
     S->d_scal_in = static_cast<Scal *>(at(i_scal_in));
+    S->d_dmap = static_cast<int32_t *>(at(i_dmap));
+    S->d_dinv = static_cast<double *>(at(i_dinv));
+    S->d_dinv32 = static_cast<float *>(at(i_dinv32));
+    S->d_diag_bad = static_cast<int *>(at(i_diag_bad));
     S->d_vmap = static_cast<int32_t *>(at(i_vmap));
     S->d_imap = static_cast<int32_t *>(at(i_imap));
     S->d_smap = static_cast<int32_t *>(at(i_smap));
@@ -680,6 +695,9 @@ int upload(ssg_system *S) {
     S->grid_spmmB32 = plan.gridB32;
     SSG_CUDA_TRY(cudaMemsetAsync(S->d_scal, 0, sizeof(Scal), C->stream));
     SSG_CUDA_TRY(cudaMemsetAsync(S->d_scal_op, 0, sizeof(Scal), C->stream));
+    k_dinv<<<grid_for(N, C->num_sms), kBlock, 0, C->stream>>>(N, S->d_dmap, S->op.val, S->d_dinv, S->d_dinv32,
+                                                               S->d_diag_bad);
+    SSG_CUDA_TRY(cudaGetLastError());
     SSG_CUDA_TRY(cudaEventCreate(&S->ev0));
     SSG_CUDA_TRY(cudaEventCreate(&S->ev1));
     // the host vectors above are freed when this function returns
@@ -700,10 +718,6 @@ int check_dev(const ssg_system *S) {
     return SSG_OK;
 }
 
-int grid_for(int64_t n, int num_sms) {
-    return std::max(1, std::min<int>(static_cast<int>((n + kBlock - 1) / kBlock), num_sms * 8));
-}
-
 // One right-hand side: b_glob/x_glob are device pointers (length n).
 int read_scal(ssg_system *S, const Scal *src, Scal *dst) {
     SSG_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(Scal), cudaMemcpyDeviceToHost, S->ctx->stream));
@@ -713,9 +727,9 @@ int read_scal(ssg_system *S, const Scal *src, Scal *dst) {
 
 // Host-loop drivers (SSG_DRIVER_HOST): the same kernels, launched directly,
 // the done flags read back every kHostChunk iterations.
-int run_host_fp64(ssg_system *S, int64_t *launches) {
+int run_host_fp64(ssg_system *S, int64_t *launches, bool pc) {
     cudaStream_t s = S->ctx->stream;
-    int rc = launch_init(S, s, 0);
+    int rc = launch_init(S, s, 0, pc);
     if (rc != SSG_OK) return rc;
     *launches += 1;
     Scal h{};
@@ -724,7 +738,7 @@ int run_host_fp64(ssg_system *S, int64_t *launches) {
         if (rc != SSG_OK) return rc;
         if (h.done) return SSG_OK;
         for (int i = 0; i < kHostChunk; ++i) {
-            rc = launch_body(S, s, 0);
+            rc = launch_body(S, s, 0, pc);
             if (rc != SSG_OK) return rc;
         }
         *launches += 3 * kHostChunk;
@@ -760,9 +774,30 @@ int run_host_mixed(ssg_system *S, int64_t *launches) {
     }
 }
 
+// The diagonal preconditioner needs every diagonal entry present and
+// positive; k_dinv flags the first violation, read here once per set of values.
+int check_diag(ssg_system *S) {
+    if (S->diag_state < 0) {
+        int bad = 0;
+        SSG_CUDA_TRY(cudaMemcpyAsync(&bad, S->d_diag_bad, sizeof(int), cudaMemcpyDeviceToHost, S->ctx->stream));
+        SSG_CUDA_TRY(cudaStreamSynchronize(S->ctx->stream));
+        S->diag_state = bad ? 1 : 0;
+    }
+    if (S->diag_state) {
+        set_error("SSG_FP64_JACOBI needs every diagonal entry present and positive");
+        return SSG_E_INVALID;
+    }
+    return SSG_OK;
+}
+
 // One right-hand side: b_glob/x_glob are device pointers (length n).
 int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, double rtol, int32_t max_iter,
               int mode, ssg_stats *st) {
+    const bool pc = mode == SSG_FP64_JACOBI;
+    if (pc) {
+        int rc0 = check_diag(S);
+        if (rc0 != SSG_OK) return rc0;
+    }
     ssg_ctx *C = S->ctx;
     cudaStream_t s = C->stream;
     const int64_t N = S->maps.nloc;
@@ -787,11 +822,11 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     SSG_CUDA_TRY(cudaGetLastError());
     int rc = SSG_OK;
     if (C->driver == SSG_DRIVER_GRAPH) {
-        rc = mode == SSG_MIXED ? build_graph_mixed(S) : build_graph(S);
+        rc = mode == SSG_MIXED ? build_graph_mixed(S) : build_graph(S, pc);
         if (rc != SSG_OK) return rc;
-        SSG_CUDA_TRY(cudaGraphLaunch(mode == SSG_MIXED ? S->exec_m : S->exec, s));
+        SSG_CUDA_TRY(cudaGraphLaunch(mode == SSG_MIXED ? S->exec_m : pc ? S->exec_pc : S->exec, s));
     } else {
-        rc = mode == SSG_MIXED ? run_host_mixed(S, &launches) : run_host_fp64(S, &launches);
+        rc = mode == SSG_MIXED ? run_host_mixed(S, &launches) : run_host_fp64(S, &launches, pc);
         if (rc != SSG_OK) return rc;
     }
     k_gather<<<grid_for(S->maps.n, C->num_sms), kBlock, 0, s>>>(S->maps.n, S->d_own, S->d_xl, x_glob);
@@ -1514,6 +1549,10 @@ int ssg_set_values(ssg_system *S, const double *val) {
         k_gather_vals<<<grid_for(S->n_sval, ns), kBlock, 0, st>>>(S->n_sval, S->d_smap, val,
                                                                   const_cast<double *>(S->op.sval),
                                                                   const_cast<float *>(S->op.sval32));
+    SSG_CUDA_TRY(cudaMemsetAsync(S->d_diag_bad, 0, sizeof(int), st));
+    k_dinv<<<grid_for(S->maps.nloc, ns), kBlock, 0, st>>>(S->maps.nloc, S->d_dmap, S->op.val, S->d_dinv, S->d_dinv32,
+                                                           S->d_diag_bad);
+    S->diag_state = -1;
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
@@ -1570,14 +1609,15 @@ int ssg_solve(ssg_system *S, int32_t k, const double *b, double *x, int32_t x_is
         set_error("bad k, null b/x, or negative rtol");
         return SSG_E_INVALID;
     }
-    if (mode != SSG_FP64 && mode != SSG_MIXED) {
-        set_error("mode must be SSG_FP64 or SSG_MIXED");
+    if (mode != SSG_FP64 && mode != SSG_MIXED && mode != SSG_FP64_JACOBI) {
+        set_error("mode must be SSG_FP64, SSG_MIXED or SSG_FP64_JACOBI");
         return SSG_E_INVALID;
     }
     if (max_iter <= 0) max_iter = S->maps.n;
     SSG_CUDA_TRY(cudaSetDevice(S->ctx->device));
     int first_bad = SSG_OK;
-    const int kb = std::max(1, S->ctx->rhs_block);
+    // the diagonal preconditioner runs one right-hand side at a time
+    const int kb = mode == SSG_FP64_JACOBI ? 1 : std::max(1, S->ctx->rhs_block);
     for (int32_t j = 0; j < k;) {
         const int nr = std::min<int>(k - j, kb);
         const size_t o = static_cast<size_t>(j) * S->maps.n;
@@ -1600,12 +1640,12 @@ int ssg_solve_host(ssg_system *S, int32_t k, const double *b_host, double *x_hos
         set_error("bad k or null b/x");
         return SSG_E_INVALID;
     }
-    if (!(rtol >= 0.0) || (mode != SSG_FP64 && mode != SSG_MIXED)) {
+    if (!(rtol >= 0.0) || (mode != SSG_FP64 && mode != SSG_MIXED && mode != SSG_FP64_JACOBI)) {
         set_error("negative rtol or bad mode");
         return SSG_E_INVALID;
     }
     cudaStream_t s = S->ctx->stream;
-    const int kb = std::max(1, S->ctx->rhs_block);
+    const int kb = mode == SSG_FP64_JACOBI ? 1 : std::max(1, S->ctx->rhs_block);
     int first_bad = SSG_OK;
     for (int32_t j = 0; j < k;) {
         const int nr = std::min<int>(k - j, kb);
@@ -1635,6 +1675,8 @@ int ssg_system_destroy(ssg_system *S) {
     if (S->ctx) cudaSetDevice(S->ctx->device);
     if (S->exec) cudaGraphExecDestroy(S->exec);
     if (S->graph) cudaGraphDestroy(S->graph);
+    if (S->exec_pc) cudaGraphExecDestroy(S->exec_pc);
+    if (S->graph_pc) cudaGraphDestroy(S->graph_pc);
     if (S->exec_m) cudaGraphExecDestroy(S->exec_m);
     if (S->graph_m) cudaGraphDestroy(S->graph_m);
     if (S->ev0) cudaEventDestroy(S->ev0);

@@ -45,7 +45,8 @@ constexpr int kHostChunk = 32;    // iterations per host-loop chunk (SSG_DRIVER_
 
 // Scalar state of one CG solve, resident on the device.
 struct Scal {
-    double rho;      // (r_k, r_k)_w
+    double rho;      // (r_k, z_k)_w (z = M^-1 r; z = r without a preconditioner)
+    double rr;       // (r_k, r_k)_w: the stopping test
     double alpha;    // alpha_k
     double beta;     // beta_k
     double pq;       // (S p_k, p_k)_w
@@ -465,14 +466,18 @@ __device__ __forceinline__ double wsq(double r, unsigned int m, const double *__
     return m == 1u ? fma(r, r, acc) : fma(__ldg(wtab + m) * r, r, acc);
 }
 
-// Algorithm 3 lines 3 and 5 (M = I): every block sums the SpMV's partials of
+// Algorithm 3 lines 3 and 5: every block sums the SpMV's partials of
 // (p, S p)_w, forms alpha = rho / (p, S p)_w (or stops on a breakdown), then
-// r <- r - alpha q and its share of (r, r)_w.
+// r <- r - alpha q and its share of (r, r)_w.  With the diagonal
+// preconditioner (PC, dinv = 1 / diag(S) per local entry) the block also
+// forms its share of (r, z)_w, z = dinv r, into part_rz.
+template <bool PC>
 __global__ void __launch_bounds__(kBlock) k_update_r(int64_t N, double *__restrict__ r, const double *__restrict__ q,
                                                      const uint8_t *__restrict__ mult, const double *__restrict__ wtab,
                                                      const uint8_t *__restrict__ gflag, const double *part_pq,
                                                      int G1, double *part_rr, Scal *s, cudaGraphConditionalHandle h,
-                                                     int use_cond) {
+                                                     int use_cond, const double *__restrict__ dinv,
+                                                     double *part_rz) {
     pdl_enter();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         s->rho_b = s->rho;
@@ -490,12 +495,13 @@ __global__ void __launch_bounds__(kBlock) k_update_r(int64_t N, double *__restri
         return;
     }
     const double alpha = s->rho / pq;
-    double acc = 0.0;
+    double acc = 0.0, acz = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N2 = N >> 1;
     double2 *__restrict__ r2 = reinterpret_cast<double2 *>(r);
     const double2 *__restrict__ q2 = reinterpret_cast<const double2 *>(q);
     const uchar2 *__restrict__ m2 = reinterpret_cast<const uchar2 *>(mult);
+    const double2 *__restrict__ d2 = reinterpret_cast<const double2 *>(dinv);
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N2; i += stride) {
         double2 rv = r2[i];
         const double2 qv = __ldcs(q2 + i);
@@ -508,20 +514,35 @@ __global__ void __launch_bounds__(kBlock) k_update_r(int64_t N, double *__restri
         if (__ldg(gflag + (i >> 5)) == 0) {
             acc = fma(rv.x, rv.x, acc);
             acc = fma(rv.y, rv.y, acc);
+            if (PC) {
+                const double2 dv = __ldg(d2 + i);
+                acz = fma(rv.x, rv.x * dv.x, acz);
+                acz = fma(rv.y, rv.y * dv.y, acz);
+            }
         } else {
             const uchar2 mv = m2[i];
-            acc = fma(__ldg(wtab + mv.x) * rv.x, rv.x, acc);
-            acc = fma(__ldg(wtab + mv.y) * rv.y, rv.y, acc);
+            const double wx = __ldg(wtab + mv.x) * rv.x, wy = __ldg(wtab + mv.y) * rv.y;
+            acc = fma(wx, rv.x, acc);
+            acc = fma(wy, rv.y, acc);
+            if (PC) {
+                const double2 dv = __ldg(d2 + i);
+                acz = fma(wx, rv.x * dv.x, acz);
+                acz = fma(wy, rv.y * dv.y, acz);
+            }
         }
     }
     if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         const double ri = fma(-alpha, q[N - 1], r[N - 1]);
         r[N - 1] = ri;
-        acc = fma(__ldg(wtab + mult[N - 1]) * ri, ri, acc);
+        const double wi = __ldg(wtab + mult[N - 1]) * ri;
+        acc = fma(wi, ri, acc);
+        if (PC) acz = fma(wi, ri * dinv[N - 1], acz);
     }
     const double bs = block_sum(acc);
+    const double bz = PC ? block_sum(acz) : 0.0;
     if (threadIdx.x == 0) {
         part_rr[blockIdx.x] = bs;
+        if (PC) part_rz[blockIdx.x] = bz;
         if (blockIdx.x == 0) {
             s->alpha = alpha;
             s->alpha32 = float(alpha);
@@ -530,39 +551,51 @@ __global__ void __launch_bounds__(kBlock) k_update_r(int64_t N, double *__restri
     }
 }
 
-// Algorithm 3 lines 4, 7, 8 (M = I): every block sums the partials of
-// (r_{k+1}, r_{k+1})_w, forms beta, and x <- x + alpha p, p <- r + beta p;
-// block 0 records the iteration and the stopping decision (recursive
-// residual <= rtol ||b||, or max_iter reached), applied after this update.
+// Algorithm 3 lines 4, 7, 8: every block sums the partials of (r_{k+1},
+// r_{k+1})_w (and of (r_{k+1}, z_{k+1})_w with the diagonal preconditioner),
+// forms beta = (r, z)_{k+1} / (r, z)_k, and x <- x + alpha p, p <- z + beta p
+// (z = r without a preconditioner, z = dinv r with it); block 0 records the
+// iteration and the stopping decision (recursive residual sqrt((r, r)_w) <=
+// rtol ||b||, or max_iter reached), applied after this update.
+template <bool PC>
 __global__ void __launch_bounds__(kBlock) k_update_xp(int64_t N, double *__restrict__ x, double *__restrict__ p,
                                                       const double *__restrict__ r, const double *part_rr, int G2,
-                                                      Scal *s, cudaGraphConditionalHandle h, int use_cond) {
+                                                      Scal *s, cudaGraphConditionalHandle h, int use_cond,
+                                                      const double *__restrict__ dinv, const double *part_rz) {
     pdl_enter();
     const int k = s->iter_b;
     if (s->brk || s->halt[k & 1]) return;
     const double rr = all_sum_partials(part_rr, G2);
-    const double alpha = s->alpha, beta = rr / s->rho_b;
+    const double rz = PC ? all_sum_partials(part_rz, G2) : rr;
+    const double alpha = s->alpha, beta = rz / s->rho_b;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N2 = N >> 1;
     double2 *x2 = reinterpret_cast<double2 *>(x);
     double2 *p2 = reinterpret_cast<double2 *>(p);
     const double2 *r2 = reinterpret_cast<const double2 *>(r);
+    const double2 *__restrict__ d2 = reinterpret_cast<const double2 *>(dinv);
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N2; i += stride) {
         const double2 pv = p2[i];
         double2 xv = __ldcs(x2 + i);
-        const double2 rv = r2[i];
+        double2 zv = r2[i];
+        if (PC) {
+            const double2 dv = __ldg(d2 + i);
+            zv.x *= dv.x;
+            zv.y *= dv.y;
+        }
         xv.x = fma(alpha, pv.x, xv.x);
         xv.y = fma(alpha, pv.y, xv.y);
         __stcs(x2 + i, xv);
-        p2[i] = make_double2(fma(beta, pv.x, rv.x), fma(beta, pv.y, rv.y));
+        p2[i] = make_double2(fma(beta, pv.x, zv.x), fma(beta, pv.y, zv.y));
     }
     if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         const double pi = p[N - 1];
         x[N - 1] = fma(alpha, pi, x[N - 1]);
-        p[N - 1] = fma(beta, pi, r[N - 1]);
+        p[N - 1] = fma(beta, pi, PC ? r[N - 1] * dinv[N - 1] : r[N - 1]);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        s->rho = rr;
+        s->rho = rz;
+        s->rr = rr;
         s->beta = beta;
         s->iter = k + 1;
         s->relres = s->bnorm > 0.0 ? sqrt(rr) / s->bnorm : 0.0;
@@ -577,35 +610,47 @@ __global__ void __launch_bounds__(kBlock) k_update_xp(int64_t N, double *__restr
     }
 }
 
-// Setup of Algorithm 3 line 1 with M = I: r = b - q (q = S x_1 when a guess
-// is given, else r = b), p = r, rho = (r, r)_w, bnorm = sqrt((b, b)_w), and
-// the stopping test before the first iteration.
+// Setup of Algorithm 3 line 1: r = b - q (q = S x_1 when a guess is given,
+// else r = b), z = r (z = dinv r with the diagonal preconditioner, PC),
+// p = z, rho = (r, z)_w, (r, r)_w, bnorm = sqrt((b, b)_w), and the stopping
+// test before the first iteration.  Partials: (r, r)_w at [0, G), (b, b)_w
+// at [G, 2G), (r, z)_w at [2G, 3G).
+template <bool PC>
 __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t N, const double *__restrict__ b,
                                                     const double *__restrict__ q, double *__restrict__ r,
                                                     double *__restrict__ p, const uint8_t *__restrict__ mult,
                                                     const double *__restrict__ wtab, double *partials, Scal *s,
-                                                    cudaGraphConditionalHandle h, int use_cond) {
+                                                    cudaGraphConditionalHandle h, int use_cond,
+                                                    const double *__restrict__ dinv) {
     const int guess = s->guess;
-    double arr = 0.0, abb = 0.0;
+    double arr = 0.0, abb = 0.0, arz = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N; i += stride) {
         const double bi = b[i];
         const double ri = guess ? bi - q[i] : bi;
+        const double zi = PC ? ri * dinv[i] : ri;
         r[i] = ri;
-        if (p) p[i] = ri;
+        if (p) p[i] = zi;
         const unsigned int m = mult[i];
         arr = wsq(ri, m, wtab, arr);
         abb = wsq(bi, m, wtab, abb);
+        if (PC) arz = fma(__ldg(wtab + m) * ri, zi, arz);
     }
     const double srr = block_sum(arr);
     const double sbb = block_sum(abb);
-    if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = sbb;
+    const double srz = PC ? block_sum(arz) : 0.0;
+    if (threadIdx.x == 0) {
+        partials[gridDim.x + blockIdx.x] = sbb;
+        if (PC) partials[2 * gridDim.x + blockIdx.x] = srz;
+    }
     if (publish_and_check_last(partials, srr, &s->ticket[kTicketMisc])) {
         const double rr = sum_partials(partials, gridDim.x);
         const double bb = sum_partials(partials + gridDim.x, gridDim.x);
+        const double rz = PC ? sum_partials(partials + 2 * gridDim.x, gridDim.x) : rr;
         if (threadIdx.x == 0) {
             s->ticket[kTicketMisc] = 0;
-            s->rho = rr;
+            s->rho = rz;
+            s->rr = rr;
             s->bnorm = sqrt(bb);
             s->iter = 0;
             s->total = 0;
@@ -628,6 +673,24 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t N, const double *__r
             s->halt[0] = stop;
             if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
         }
+    }
+}
+
+// dinv[k] = 1 / S_ii for the node i of local entry k (its diagonal entry sits
+// at local entry dmap[k] of the concatenated local matrices); a missing or
+// non-positive diagonal sets *bad and leaves dinv[k] = 0.
+__global__ void __launch_bounds__(kBlock) k_dinv(int64_t N, const int32_t *__restrict__ dmap,
+                                                 const double *__restrict__ val, double *__restrict__ dinv,
+                                                 float *__restrict__ dinv32, int *bad) {
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N; i += stride) {
+        const int32_t e = dmap[i];
+        const double d = e >= 0 ? val[e] : 0.0;
+        double v = 0.0;
+        if (d > 0.0 && isfinite(d)) v = 1.0 / d;
+        else *bad = 1;
+        dinv[i] = v;
+        dinv32[i] = float(v);
     }
 }
 

@@ -27,6 +27,7 @@ SSG_E_NOT_CONVERGED = 5
 SSG_E_TIMEOUT = 6
 SSG_FP64 = 0
 SSG_MIXED = 1
+SSG_FP64_JACOBI = 2
 SSG_DRIVER_GRAPH = 0
 SSG_DRIVER_HOST = 1
 
