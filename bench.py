@@ -60,10 +60,19 @@ def parse_args(argv=None):
                          "Both stop on an FP64 relative residual of 1e-8; the other mode is timed too and reported")
     ap.add_argument("--pdl", choices=("on", "off"), default="off",
                     help="programmatic dependent launch for the per-iteration update kernels")
+    ap.add_argument("--profile-spmm", choices=("fp64", "fp32"), default=None,
+                    help="only build the 96^3 16-right-hand-side workload and launch the 16-vector product "
+                         "--spmv-reps times (for ncu); no JSON line")
+    ap.add_argument("--profile-block", choices=("fp64", "mixed"), default=None,
+                    help="only build the 96^3 16-right-hand-side workload and run one solve of all 16 together "
+                         "with the host-loop driver (for an ncu launch list); no JSON line")
     ap.add_argument("--profile-spmv", choices=("fp64", "fp32"), default=None,
                     help="only build the workload and launch the SpMV --spmv-reps times (for ncu); no JSON line")
     ap.add_argument("--no-multi-rhs", action="store_true",
                     help="skip the 16-right-hand-side measurement (96^3 FV, reported beside the headline)")
+    ap.add_argument("--batch", choices=("off", "small", "full"), default="small",
+                    help="many independent systems in one launch, reported beside the headline: small = 512 "
+                         "systems of side 32..128, full = 512 of side 32..512 (several minutes of host setup)")
     ap.add_argument("--driver", choices=("graph", "host"), default="graph",
                     help="graph: one CUDA graph per solve (timed default); host: same kernels launched from a "
                          "host loop (for profilers that cannot see kernels inside conditional graphs)")
@@ -344,6 +353,66 @@ def bench_multi_rhs(ctx, stream, reps, spmv_reps):
     return out
 
 
+def bench_batch(ctx, stream, reps, size):
+    """Workload 4: independent 2D finite-volume systems (4-16 box subdomains,
+    1-8 right-hand sides each) solved together in one graph launch, FP64 and
+    mixed, against the same systems solved one after another.  size "full":
+    512 systems with sides 32..512; "small": 512 systems with sides 32..128."""
+    import numpy as np
+    import torch
+
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import Batch, System
+    from synth import batch_problem
+
+    hi = 512 if size == "full" else 128
+    bp = batch_problem(512, 32, hi)
+    t0 = time.perf_counter()
+    B = Batch(ctx, [(A, pt, P, b.shape[0]) for A, pt, P, b in zip(bp.A, bp.part, bp.P, bp.b)])
+    setup_s = time.perf_counter() - t0
+    bb = torch.from_numpy(np.concatenate([b.ravel() for b in bp.b])).cuda()
+    out = {"workload": "fv2d_5pt_batch512_side32-%d_sigma0.5_4-16subdomains_1-8rhs" % hi,
+           "systems": len(bp.A), "unknowns": int(sum(A.n for A in bp.A)), "nnz": int(sum(A.nnz for A in bp.A)),
+           "rhs": int(sum(b.shape[0] for b in bp.b)), "subdomains": int(sum(bp.P)), "rtol": RTOL,
+           "setup_s": setup_s}
+    for mode_name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED)):
+        x, rc, st = B.solve(bb, rtol=RTOL, mode=mode)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            x, rc, st = B.solve(bb, rtol=RTOL, mode=mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rc != ssg.SSG_OK:
+            raise RuntimeError("batch solve did not converge")
+        out[mode_name + "_together_s"] = e0.elapsed_time(e1) / 1e3 / reps
+        out[mode_name + "_iters_max"] = max(t["iters"] for t in st)
+        out[mode_name + "_true_relres_max"] = max(t["true_relres"] for t in st)
+        out[mode_name + "_launches"] = st[0]["kernel_launches"]
+    B.close()
+    # the same systems one after another (each with its right-hand sides together)
+    if size != "full":
+        for mode_name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED)):
+            tot = 0.0
+            for A, pt, P, b in zip(bp.A, bp.part, bp.P, bp.b):
+                S = System(ctx, A, pt, P)
+                bt = torch.from_numpy(b.copy()).cuda()
+                S.solve(bt, rtol=RTOL, mode=mode)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                S.solve(bt, rtol=RTOL, mode=mode)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1) / 1e3
+                S.close()
+            out[mode_name + "_one_by_one_s"] = tot
+    return out
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -458,8 +527,33 @@ def run_ours(args, dist):
     dev = dist.local_rank
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    prob = make_workload()
     ctx = Context(dev, stream)
+    if args.profile_block:
+        from synth import config_problem
+
+        p5 = config_problem(5)
+        S = System(ctx, p5.A, p5.part, p5.P)
+        ctx.set_driver(ssg.SSG_DRIVER_HOST)
+        B = torch.from_numpy(p5.b.T.copy()).cuda()
+        X = torch.zeros_like(B)
+        mode = ssg.SSG_MIXED if args.profile_block == "mixed" else ssg.SSG_FP64
+        rc, st = ssg.ssg_solve(S.h, B.shape[0], B, X, False, RTOL, 0, mode)
+        torch.cuda.synchronize()
+        print("block solve: status %d, iterations %d, launches %d" % (rc, max(t["iters"] for t in st),
+                                                                      st[0]["kernel_launches"]))
+        S.close()
+        ctx.close()
+        return 0
+    if args.profile_spmm:
+        from synth import config_problem
+
+        p5 = config_problem(5)
+        S = System(ctx, p5.A, p5.part, p5.P)
+        time_spmm(S, args.profile_spmm, 16, stream, args.spmv_reps)
+        S.close()
+        ctx.close()
+        return 0
+    prob = make_workload()
     if args.profile_spmv:
         S = System(ctx, prob.A, prob.part, prob.P)
         time_spmv(S, args.profile_spmv, stream, args.spmv_reps)
@@ -554,6 +648,9 @@ def run_ours(args, dist):
     multi = None
     if not args.no_multi_rhs:
         multi = bench_multi_rhs(ctx, stream, max(1, min(args.steps, 3)), args.spmv_reps)
+    batch = None
+    if args.batch != "off":
+        batch = bench_batch(ctx, stream, max(1, min(args.steps, 3)), args.batch)
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
@@ -607,6 +704,7 @@ def run_ours(args, dist):
         "clocks": ck,
         "cpu_baseline": cpu,
         "multi_rhs": multi,
+        "batch": batch,
     }
     if dist.rank == 0:
         print(json.dumps(line), flush=True)

@@ -148,6 +148,37 @@ int ssg_destroy(ssg_ctx *ctx);
 int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
                   const int32_t *part, int32_t P, ssg_system **sys);
 
+/*
+ * A batch of independent systems solved together (not in the paper; its
+ * method is one system).  The caller passes the union of the systems as one
+ * block-diagonal CSR (the input conventions of ssg_partition): system s owns
+ * the nodes [sys_node_off[s], sys_node_off[s+1]) and the subdomain ids
+ * [sys_sub_off[s], sys_sub_off[s+1]) (every one of its nodes' part values
+ * lies there; no stored entry couples two systems), and has sys_nrhs[s]
+ * right-hand sides (1..16).  nsys + 1 offsets, both starting at 0, strictly
+ * increasing.  The sub-structures are built as by ssg_partition for the
+ * union; the product's work is cut per system so that every block of every
+ * kernel works inside one system.  SSG_E_INVALID for bad tables, a node whose
+ * subdomain lies outside its system's range or an entry coupling two systems.
+ */
+int ssg_partition_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off, const int32_t *sys_sub_off,
+                        const int32_t *sys_nrhs, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                        const int32_t *part, ssg_system **sys);
+/*
+ * Solve every system of a batch for its right-hand sides in one graph
+ * launch: each (system, right-hand side) runs its own Algorithm 3 (SSG_FP64)
+ * or its own refinement (SSG_MIXED) with the readings of ssg_solve; the
+ * columns of all systems iterate together (K = the power of two >= the
+ * largest sys_nrhs), a finished system's blocks return at once.  b and x
+ * (device, rhs_off[nsys] doubles each, caller-allocated: the library cannot
+ * check their length) hold system s's right-hand side j at rhs_off[s] + j * n_s, with
+ * rhs_off[s] = sum over s' < s of sys_nrhs[s'] * n_s' (n_s = its node count);
+ * stats (host, may be NULL) receives one entry per (system, right-hand side)
+ * in that order.  max_iter <= 0 means the largest n_s.  Returns SSG_OK when
+ * every right-hand side converged, else the first non-OK status.
+ */
+int ssg_solve_batch(ssg_system *sys, const double *b, double *x, int32_t x_is_guess, double rtol, int32_t max_iter,
+                    int32_t mode, ssg_stats *stats);
 int ssg_get_sizes(const ssg_system *sys, ssg_sizes *out);
 
 /*

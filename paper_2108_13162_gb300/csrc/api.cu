@@ -86,9 +86,15 @@ struct ssg_system {
     int64_t n_ival = 0, n_sval = 0;
     int32_t *d_growptr = nullptr;  // 7-point grid row pointers (ssg_fv7_*), after the pattern check
     int fv7_dims[3] = {0, 0, 0};
-    // several right-hand sides together (block.cuh)
-    DevOp opB64{}, opB32{};  // SpMM launches: warp ranges for grid_spmmB64 / grid_spmmB32 blocks
-    int grid_spmmB64 = 0, grid_spmmB32 = 0;
+    // several right-hand sides and independent systems together (block.cuh):
+    // segments = independent systems (one for a system from ssg_partition)
+    DevOp opB64{}, opB32{};  // K-vector product launches (warp ranges cut inside each segment)
+    int grid_spmmB = 0;
+    int32_t nseg = 1, nchunks = 0;
+    std::vector<int32_t> seg_sub, seg_node, seg_nrhs;  // [nseg+1], [nseg+1], [nseg]
+    std::vector<int64_t> seg_rhs_off;                  // [nseg]
+    int32_t batch_k = 0;       // largest right-hand-side count of a batch (0: not a batch)
+    SegTab tab{};              // device copies of the segment tables
     struct BlockGraph {
         cudaGraph_t g = nullptr;
         cudaGraphExec_t exec = nullptr;
@@ -97,11 +103,11 @@ struct ssg_system {
     struct BlockState {
         void *mem = nullptr;  // one allocation for kcap columns
         int kcap = 0;
-        double *bl = nullptr, *xl = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *part = nullptr;
+        double *bl = nullptr, *xl = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+        double *part_a = nullptr, *part_b = nullptr;
         float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
         double *bg = nullptr, *xg = nullptr;  // global staging for ssg_solve_host (n x kcap)
-        ScalB *so = nullptr, *si = nullptr;
-        int gmax = 0;  // largest grid whose partials the loops exchange
+        ScalB *so = nullptr, *si = nullptr;  // [nseg + 1]: one state per segment, then the loop counters
         BlockGraph g64[5], gmx[5];  // by log2 K
     } blk;
 };
@@ -154,37 +160,46 @@ struct WorkPlan {
     std::vector<int32_t> scol, sseg;
     std::vector<WorkItem> items;
     std::vector<int2> warp_range64, warp_range32;  // per warp of the FP64 / FP32 launch
-    std::vector<int2> warp_rangeB64, warp_rangeB32;  // the same for the K-vector products
-    int grid64 = 0, grid32 = 0, gridB64 = 0, gridB32 = 0;
+    std::vector<int2> warp_rangeB;   // per warp of the K-vector product: cut inside each segment
+    std::vector<int32_t> blk_seg, seg_blk;  // segment of each K-vector product block; blocks per segment
+    std::vector<int4> chunk;                // vector-kernel chunks (segment, first entry, end entry, 0)
+    std::vector<int32_t> seg_chunk;         // chunks per segment
+    int grid64 = 0, grid32 = 0, gridB = 0;
 };
 
-// Cut the item list into one contiguous range of about equal cost per warp
-// of a launch of `blocks` blocks.
-std::vector<int2> cut_ranges(const std::vector<WorkItem> &items, int blocks) {
-    const int n = static_cast<int>(items.size());
+double item_cost(const WorkItem &w) {
+    double cost = 64.0;
+    if (w.kind == kItemSlice || w.kind == kItemIfaceSlice) cost += 32.0 * w.e1;
+    else cost += 4.0 * (w.e1 - w.e0);
+    return cost;
+}
+
+// Cut items [lo0, hi0) into one contiguous range of about equal cost per warp
+// of `blocks` blocks; the ranges are appended to R (absolute item indices).
+void cut_ranges(const std::vector<WorkItem> &items, int lo0, int hi0, int blocks, std::vector<int2> &R) {
+    const int n = hi0 - lo0;
     const int G = blocks * kSpmvWarps;
     std::vector<double> prefix(static_cast<size_t>(n) + 1, 0.0);
-    for (int i = 0; i < n; ++i) {
-        const WorkItem &w = items[i];
-        double cost = 64.0;
-        if (w.kind == kItemSlice || w.kind == kItemIfaceSlice) cost += 32.0 * w.e1;
-        else cost += 4.0 * (w.e1 - w.e0);
-        prefix[i + 1] = prefix[i] + cost;
-    }
-    std::vector<int2> R(G);
+    for (int i = 0; i < n; ++i) prefix[i + 1] = prefix[i] + item_cost(items[lo0 + i]);
     int lo = 0;
     for (int b = 0; b < G; ++b) {
         const double target = prefix[n] * (b + 1) / G;
         int hi = lo;
         while (hi < n && (prefix[hi + 1] <= target || hi == lo)) ++hi;
         if (b == G - 1) hi = n;
-        R[b] = make_int2(lo, hi);
+        R.push_back(make_int2(lo0 + lo, lo0 + hi));
         lo = hi;
     }
+}
+
+std::vector<int2> cut_ranges(const std::vector<WorkItem> &items, int blocks) {
+    std::vector<int2> R;
+    cut_ranges(items, 0, static_cast<int>(items.size()), blocks, R);
     return R;
 }
 
-WorkPlan make_plan(const HostMaps &M, int num_sms) {
+// seg_sub: subdomains of each segment (independent systems), [nseg + 1].
+WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &seg_sub) {
     WorkPlan W;
     std::vector<int32_t> sub_of(static_cast<size_t>(M.nloc));
     for (int32_t s = 0; s < M.P; ++s)
@@ -236,7 +251,13 @@ WorkPlan make_plan(const HostMaps &M, int num_sms) {
             r = r1;
         }
     }
-    // interface slices (whole nodes)
+    // segments (independent systems): every item stays inside one
+    const int nseg = static_cast<int>(seg_sub.size()) - 1;
+    std::vector<int32_t> seg_of_sub(static_cast<size_t>(M.P), 0);
+    for (int sg = 0; sg < nseg; ++sg)
+        for (int32_t sd = seg_sub[sg]; sd < seg_sub[sg + 1]; ++sd) seg_of_sub[sd] = sg;
+    auto node_seg = [&](int32_t gg) { return seg_of_sub[sub_of[M.icopy[M.iptr[gg]]]]; };
+    // interface slices (whole nodes, one segment)
     int32_t g = 0;
     while (g < M.ngamma) {
         auto long_node = [&](int32_t gg) {
@@ -253,7 +274,7 @@ WorkPlan make_plan(const HostMaps &M, int num_sms) {
         }
         const int32_t c0 = M.iptr[g];
         int32_t g1 = g, w = 0;
-        while (g1 < M.ngamma && !long_node(g1) && M.iptr[g1 + 1] - c0 <= kSliceRows) {
+        while (g1 < M.ngamma && !long_node(g1) && M.iptr[g1 + 1] - c0 <= kSliceRows && node_seg(g1) == node_seg(g)) {
             for (int32_t c = M.iptr[g1]; c < M.iptr[g1 + 1]; ++c) w = std::max(w, W.irp[c + 1] - W.irp[c]);
             ++g1;
         }
@@ -278,24 +299,67 @@ WorkPlan make_plan(const HostMaps &M, int num_sms) {
         iface.push_back({kItemIfaceSlice, c0, c1, off, w, 0, 0, 0});
         g = g1;
     }
-    // interleave: interface item j goes after interior item floor((j+1) * nrows / (niface+1))
-    const size_t nr = rows.size(), ni = iface.size();
-    size_t j = 0;
-    for (size_t i = 0; i <= nr; ++i) {
-        while (j < ni && (j + 1) * nr <= i * (ni + 1)) W.items.push_back(iface[j++]);
-        if (i < nr) W.items.push_back(rows[i]);
+    // per segment, interface item j goes after interior item floor((j+1) *
+    // nrows / (niface+1)) of the segment
+    auto item_seg = [&](const WorkItem &w) {
+        if (w.kind == kItemSlice || w.kind == kItemLongRow) return seg_of_sub[sub_of[w.a]];
+        const int32_t c = w.kind == kItemIfaceSlice ? w.a : w.c0;
+        return seg_of_sub[sub_of[M.icopy[c]]];
+    };
+    std::vector<int32_t> seg_item(static_cast<size_t>(nseg) + 1, 0);
+    {
+        size_t ir = 0, ii = 0;
+        for (int sg = 0; sg < nseg; ++sg) {
+            size_t r0 = ir, i0 = ii;
+            while (ir < rows.size() && item_seg(rows[ir]) == sg) ++ir;
+            while (ii < iface.size() && item_seg(iface[ii]) == sg) ++ii;
+            const size_t nr = ir - r0, ni = ii - i0;
+            size_t j = 0;
+            for (size_t i = 0; i <= nr; ++i) {
+                while (j < ni && (j + 1) * nr <= i * (ni + 1)) W.items.push_back(iface[i0 + j++]);
+                if (i < nr) W.items.push_back(rows[r0 + i]);
+            }
+            while (j < ni) W.items.push_back(iface[i0 + j++]);
+            seg_item[sg + 1] = static_cast<int32_t>(W.items.size());
+        }
     }
-    while (j < ni) W.items.push_back(iface[j++]);
     const int n = static_cast<int>(W.items.size());
     const int per = (n + kSpmvWarps - 1) / kSpmvWarps;
     W.grid64 = std::max(1, std::min(per, num_sms * SpmvTraits<double>::kBlocksPerSM));
     W.grid32 = std::max(1, std::min(per, num_sms * SpmvTraits<float>::kBlocksPerSM));
     W.warp_range64 = cut_ranges(W.items, W.grid64);
     W.warp_range32 = cut_ranges(W.items, W.grid32);
-    W.gridB64 = std::max(1, std::min(per, num_sms * SpmmTraits<double>::kBlocksPerSM));
-    W.gridB32 = std::max(1, std::min(per, num_sms * SpmmTraits<float>::kBlocksPerSM));
-    W.warp_rangeB64 = cut_ranges(W.items, W.gridB64);
-    W.warp_rangeB32 = cut_ranges(W.items, W.gridB32);
+    // K-vector product: blocks shared out among the segments by cost, at
+    // least one each, every block inside one segment
+    std::vector<double> seg_cost(static_cast<size_t>(nseg), 0.0);
+    double total = 0.0;
+    for (int sg = 0; sg < nseg; ++sg) {
+        for (int i = seg_item[sg]; i < seg_item[sg + 1]; ++i) seg_cost[sg] += item_cost(W.items[i]);
+        total += seg_cost[sg];
+    }
+    const int target = std::max(1, std::min(per, num_sms * SpmmTraits<double>::kBlocksPerSM * (nseg > 1 ? 4 : 1)));
+    W.seg_blk.assign(static_cast<size_t>(nseg) + 1, 0);
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int nit = seg_item[sg + 1] - seg_item[sg];
+        int gs = nseg == 1 ? target
+                           : static_cast<int>(std::floor(target * (total > 0 ? seg_cost[sg] / total : 0.0) + 0.5));
+        gs = std::max(1, std::min(gs, std::max(1, (nit + kSpmvWarps - 1) / kSpmvWarps)));
+        cut_ranges(W.items, seg_item[sg], seg_item[sg + 1], gs, W.warp_rangeB);
+        for (int b = 0; b < gs; ++b) W.blk_seg.push_back(sg);
+        W.seg_blk[sg + 1] = W.seg_blk[sg] + gs;
+    }
+    W.gridB = W.seg_blk[nseg];
+    // vector-kernel chunks: about num_sms * kVecBlocksPerSM in all, a multiple
+    // of 64 entries, at least one per segment
+    const int64_t ch = std::max<int64_t>(64, (M.nloc / (num_sms * kVecBlocksPerSM) + 63) / 64 * 64);
+    W.seg_chunk.assign(static_cast<size_t>(nseg) + 1, 0);
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int64_t e0 = M.off[seg_sub[sg]], e1 = M.off[seg_sub[sg + 1]];
+        for (int64_t e = e0; e < e1; e += ch)
+            W.chunk.push_back(make_int4(sg, static_cast<int>(e), static_cast<int>(std::min(e + ch, e1)), 0));
+        if (e1 == e0) W.chunk.push_back(make_int4(sg, static_cast<int>(e0), static_cast<int>(e0), 0));
+        W.seg_chunk[sg + 1] = static_cast<int32_t>(W.chunk.size());
+    }
     return W;
 }
 
@@ -516,7 +580,14 @@ int upload(ssg_system *S) {
     const HostMaps &M = S->maps;
     ssg_ctx *C = S->ctx;
     SSG_CUDA_TRY(cudaSetDevice(C->device));
-    WorkPlan plan = make_plan(M, C->num_sms);
+    if (S->seg_sub.empty()) {
+        S->seg_sub = {0, M.P};
+        S->seg_node = {0, M.n};
+        S->seg_nrhs = {1};
+        S->seg_rhs_off = {0};
+    }
+    S->nseg = static_cast<int32_t>(S->seg_sub.size()) - 1;
+    WorkPlan plan = make_plan(M, C->num_sms, S->seg_sub);
     const int64_t N = M.nloc;
     // concatenated column ids
     std::vector<int32_t> gcol(static_cast<size_t>(M.nnz));
@@ -577,8 +648,14 @@ int upload(ssg_system *S) {
     size_t i_items = add(plan.items.data(), sizeof(WorkItem) * plan.items.size());
     size_t i_brange = add(plan.warp_range64.data(), sizeof(int2) * plan.warp_range64.size());
     size_t i_brange32 = add(plan.warp_range32.data(), sizeof(int2) * plan.warp_range32.size());
-    size_t i_brangeB64 = add(plan.warp_rangeB64.data(), sizeof(int2) * plan.warp_rangeB64.size());
-    size_t i_brangeB32 = add(plan.warp_rangeB32.data(), sizeof(int2) * plan.warp_rangeB32.size());
+    size_t i_brangeB = add(plan.warp_rangeB.data(), sizeof(int2) * plan.warp_rangeB.size());
+    size_t i_blk_seg = add(plan.blk_seg.data(), sizeof(int32_t) * plan.blk_seg.size());
+    size_t i_seg_blk = add(plan.seg_blk.data(), sizeof(int32_t) * plan.seg_blk.size());
+    size_t i_chunk = add(plan.chunk.data(), sizeof(int4) * plan.chunk.size());
+    size_t i_seg_chunk = add(plan.seg_chunk.data(), sizeof(int32_t) * plan.seg_chunk.size());
+    size_t i_node_off = add(S->seg_node.data(), sizeof(int32_t) * S->seg_node.size());
+    size_t i_rhs_off = add(S->seg_rhs_off.data(), sizeof(int64_t) * S->seg_rhs_off.size());
+    size_t i_nrhs = add(S->seg_nrhs.data(), sizeof(int32_t) * S->seg_nrhs.size());
     size_t i_iptr = add(M.iptr.data(), sizeof(int32_t) * (M.ngamma + 1));
     size_t i_icopy = add(M.icopy.data(), sizeof(int32_t) * M.ncopies);
     size_t i_mult = add(mloc.data(), N);
@@ -688,11 +765,19 @@ int upload(ssg_system *S) {
     S->op32 = S->op;
     S->op32.warp_range = static_cast<const int2 *>(at(i_brange32));
     S->opB64 = S->op;
-    S->opB64.warp_range = static_cast<const int2 *>(at(i_brangeB64));
+    S->opB64.warp_range = static_cast<const int2 *>(at(i_brangeB));
     S->opB32 = S->op;
-    S->opB32.warp_range = static_cast<const int2 *>(at(i_brangeB32));
-    S->grid_spmmB64 = plan.gridB64;
-    S->grid_spmmB32 = plan.gridB32;
+    S->opB32.warp_range = static_cast<const int2 *>(at(i_brangeB));
+    S->grid_spmmB = plan.gridB;
+    S->nchunks = static_cast<int32_t>(plan.chunk.size());
+    S->tab.blk_seg = static_cast<const int32_t *>(at(i_blk_seg));
+    S->tab.seg_blk = static_cast<const int32_t *>(at(i_seg_blk));
+    S->tab.chunk = static_cast<const int4 *>(at(i_chunk));
+    S->tab.seg_chunk = static_cast<const int32_t *>(at(i_seg_chunk));
+    S->tab.node_off = static_cast<const int32_t *>(at(i_node_off));
+    S->tab.rhs_off = static_cast<const int64_t *>(at(i_rhs_off));
+    S->tab.nrhs = static_cast<const int32_t *>(at(i_nrhs));
+    S->tab.nseg = S->nseg;
     SSG_CUDA_TRY(cudaMemsetAsync(S->d_scal, 0, sizeof(Scal), C->stream));
     SSG_CUDA_TRY(cudaMemsetAsync(S->d_scal_op, 0, sizeof(Scal), C->stream));
     k_dinv<<<grid_for(N, C->num_sms), kBlock, 0, C->stream>>>(N, S->d_dmap, S->op.val, S->d_dinv, S->d_dinv32,
@@ -863,16 +948,11 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
 }
 
 // ---------------------------------------------------------------------------
-// Several right-hand sides together: K columns per launch (block.cuh).
+// Several right-hand sides, and several independent systems, together:
+// K columns per launch, one state per segment (block.cuh).
 // ---------------------------------------------------------------------------
 
 int log2_of(int K) { return K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4; }
-
-int grid_vecB(const ssg_system *S, int K) {
-    const int64_t pairs = S->maps.nloc * K / 2;
-    return std::max(1, std::min<int>(static_cast<int>((pairs + kBlock - 1) / kBlock),
-                                     S->ctx->num_sms * kVecBlocksPerSM));
-}
 
 void destroy_block_graphs(ssg_system *S) {
     for (int i = 0; i < 5; ++i)
@@ -892,12 +972,13 @@ void free_block(ssg_system *S) {
     S->blk = ssg_system::BlockState{};
 }
 
-// Device vectors for K columns (kept for later solves with K' <= K).
+// Device vectors for K columns (kept for later solves with K' <= K), the
+// partials and one state per segment (+1 for the loop counters).
 int ensure_block(ssg_system *S, int K) {
     if (S->blk.kcap >= K) return SSG_OK;
     free_block(S);
     const int64_t N = S->maps.nloc, n = S->maps.n;
-    const int gmax = std::max(std::max(S->grid_spmmB64, S->grid_spmmB32), S->ctx->num_sms * kVecBlocksPerSM);
+    const int64_t gmax = std::max<int64_t>(S->grid_spmmB, 2 * static_cast<int64_t>(S->nchunks));
     size_t total = 0;
     auto take = [&](size_t bytes) {
         const size_t o = total;
@@ -908,9 +989,10 @@ int ensure_block(ssg_system *S, int K) {
     const size_t o_bl = take(8 * NK), o_xl = take(8 * NK), o_r = take(8 * NK), o_p = take(8 * NK),
                  o_q = take(8 * NK);
     const size_t o_r32 = take(4 * NK), o_p32 = take(4 * NK), o_q32 = take(4 * NK), o_d32 = take(4 * NK);
-    const size_t o_part = take(sizeof(double) * 4 * static_cast<size_t>(gmax) * kMaxRhs);
+    const size_t o_pa = take(sizeof(double) * static_cast<size_t>(gmax) * kMaxRhs);
+    const size_t o_pb = take(sizeof(double) * static_cast<size_t>(S->nchunks) * kMaxRhs);
     const size_t o_bg = take(8 * static_cast<size_t>(n) * K), o_xg = take(8 * static_cast<size_t>(n) * K);
-    const size_t o_so = take(sizeof(ScalB)), o_si = take(sizeof(ScalB));
+    const size_t o_so = take(sizeof(ScalB) * (S->nseg + 1)), o_si = take(sizeof(ScalB) * (S->nseg + 1));
     void *mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, total);
     if (e != cudaSuccess) {
@@ -921,7 +1003,6 @@ int ensure_block(ssg_system *S, int K) {
     ssg_system::BlockState &B = S->blk;
     B.mem = mem;
     B.kcap = K;
-    B.gmax = gmax;
     B.bl = reinterpret_cast<double *>(b + o_bl);
     B.xl = reinterpret_cast<double *>(b + o_xl);
     B.r = reinterpret_cast<double *>(b + o_r);
@@ -931,7 +1012,8 @@ int ensure_block(ssg_system *S, int K) {
     B.p32 = reinterpret_cast<float *>(b + o_p32);
     B.q32 = reinterpret_cast<float *>(b + o_q32);
     B.d32 = reinterpret_cast<float *>(b + o_d32);
-    B.part = reinterpret_cast<double *>(b + o_part);
+    B.part_a = reinterpret_cast<double *>(b + o_pa);
+    B.part_b = reinterpret_cast<double *>(b + o_pb);
     B.bg = reinterpret_cast<double *>(b + o_bg);
     B.xg = reinterpret_cast<double *>(b + o_xg);
     B.so = reinterpret_cast<ScalB *>(b + o_so);
@@ -940,19 +1022,15 @@ int ensure_block(ssg_system *S, int K) {
     return SSG_OK;
 }
 
-// Partials: the setup, residual and inner-setup kernels and the K-vector
-// products use the first half, the residual updates the second.
-double *blk_part_a(ssg_system *S) { return S->blk.part; }
-double *blk_part_b(ssg_system *S) { return S->blk.part + 2 * static_cast<size_t>(S->blk.gmax) * kMaxRhs; }
-
+// Partials: the K-vector product and the setup / residual / inner-setup
+// kernels write part_a, the residual updates part_b.
 template <int K>
 int launch_initB(ssg_system *S, cudaStream_t st, double *p, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
-    const int gv = grid_vecB(S, K);
     // q holds S x_1 when a guess was given, else zeros (set before the loop)
-    k_residualB<K><<<gv, kBlock, 0, st>>>(S->maps.nloc, B.bl, B.q, B.r, p, S->op.mult, S->op.wtab, blk_part_a(S),
-                                          1, 1);
-    k_init_finB<K><<<1, kBlock, 0, st>>>(blk_part_a(S), gv, B.so, h, use_cond);
+    k_residualB<K><<<S->nchunks, kBlock, 0, st>>>(B.bl, B.q, B.r, p, S->op.mult, S->op.wtab, B.part_a, S->tab, 1, 1);
+    k_init_finB<K><<<S->nseg, kBlock, 0, st>>>(B.part_a, S->nchunks, S->tab, B.so);
+    k_seg_cond<<<1, kBlock, 0, st>>>(B.so, S->nseg, B.so + S->nseg, nullptr, 1, h, use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
@@ -960,12 +1038,11 @@ int launch_initB(ssg_system *S, cudaStream_t st, double *p, cudaGraphConditional
 template <int K>
 int launch_bodyB64(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
-    const int64_t N = S->maps.nloc;
-    const int gv = grid_vecB(S, K);
-    k_spmm_asm<double, K, true><<<S->grid_spmmB64, kSpmvThreads, 0, st>>>(S->opB64, B.p, B.q, blk_part_a(S), B.so);
-    k_update_rB<K><<<gv, kBlock, 0, st>>>(N, B.r, B.q, S->op.mult, S->op.wtab, S->op.gflag, blk_part_a(S),
-                                          S->grid_spmmB64, blk_part_b(S), B.so);
-    k_update_xpB<K><<<gv, kBlock, 0, st>>>(N, B.xl, B.p, B.r, blk_part_b(S), gv, B.so, h, use_cond);
+    k_spmm_seg<double, K, true><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(S->opB64, B.p, B.q, B.part_a, S->tab, B.so);
+    k_update_rB<K><<<S->nchunks, kBlock, 0, st>>>(B.q, B.r, S->op.mult, S->op.wtab, S->op.gflag, B.part_a, B.part_b,
+                                                  S->tab, B.so);
+    k_update_xpB<K><<<S->nchunks, kBlock, 0, st>>>(B.xl, B.p, B.r, B.part_b, S->tab, B.so);
+    k_seg_cond<<<1, kBlock, 0, st>>>(B.so, S->nseg, B.so + S->nseg, nullptr, 0, h, use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
@@ -973,10 +1050,10 @@ int launch_bodyB64(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h,
 template <int K>
 int launch_inner_initB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
-    const int gv = grid_vecB(S, K);
-    k_inner_initB<K><<<gv, kBlock, 0, st>>>(S->maps.nloc, B.r, B.r32, B.p32, B.d32, S->op.mult, S->op.wtab32,
-                                            blk_part_a(S));
-    k_inner_finB<K><<<1, kBlock, 0, st>>>(blk_part_a(S), gv, B.si, B.so, h, use_cond);
+    k_inner_initB<K><<<S->nchunks, kBlock, 0, st>>>(B.r, B.r32, B.p32, B.d32, S->op.mult, S->op.wtab32, B.part_a,
+                                                    S->tab);
+    k_inner_finB<K><<<S->nseg, kBlock, 0, st>>>(B.part_a, S->tab, B.si, B.so);
+    k_seg_cond<<<1, kBlock, 0, st>>>(B.si, S->nseg, B.si + S->nseg, nullptr, 1, h, use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
@@ -984,13 +1061,12 @@ int launch_inner_initB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandl
 template <int K>
 int launch_inner_bodyB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
-    const int64_t N = S->maps.nloc;
-    const int gv = grid_vecB(S, K);
-    k_spmm_asm<float, K, true><<<S->grid_spmmB32, kSpmvThreads, 0, st>>>(S->opB32, B.p32, B.q32, blk_part_a(S),
-                                                                          B.si);
-    k_update_r32B<K><<<gv, kBlock, 0, st>>>(N, B.r32, B.q32, S->op.mult, S->op.wtab32, S->op.gflag128,
-                                            blk_part_a(S), S->grid_spmmB32, blk_part_b(S), B.si);
-    k_update_dp32B<K><<<gv, kBlock, 0, st>>>(N, B.d32, B.p32, B.r32, blk_part_b(S), gv, B.si, B.so, h, use_cond);
+    k_spmm_seg<float, K, true><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(S->opB32, B.p32, B.q32, B.part_a, S->tab,
+                                                                        B.si);
+    k_update_r32B<K><<<S->nchunks, kBlock, 0, st>>>(B.q32, B.r32, S->op.mult, S->op.wtab32, S->op.gflag128,
+                                                    B.part_a, B.part_b, S->tab, B.si);
+    k_update_dp32B<K><<<S->nchunks, kBlock, 0, st>>>(B.d32, B.p32, B.r32, B.part_b, S->tab, B.si, B.so);
+    k_seg_cond<<<1, kBlock, 0, st>>>(B.si, S->nseg, B.si + S->nseg, B.so + S->nseg, 0, h, use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
@@ -999,11 +1075,12 @@ template <int K>
 int launch_outer_tailB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
     const int64_t N = S->maps.nloc;
-    const int gv = grid_vecB(S, K);
     k_ir_correct<<<grid_for(N * K, S->ctx->num_sms), kBlock, 0, st>>>(N * K, B.xl, B.d32);
-    k_spmm_asm<double, K, false><<<S->grid_spmmB64, kSpmvThreads, 0, st>>>(S->opB64, B.xl, B.q, nullptr, nullptr);
-    k_residualB<K><<<gv, kBlock, 0, st>>>(N, B.bl, B.q, B.r, nullptr, S->op.mult, S->op.wtab, blk_part_a(S), 1, 0);
-    k_outer_finB<K><<<1, kBlock, 0, st>>>(blk_part_a(S), gv, B.so, B.si, 0, h, use_cond);
+    k_spmm_seg<double, K, false><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(S->opB64, B.xl, B.q, nullptr, S->tab, B.so);
+    k_residualB<K><<<S->nchunks, kBlock, 0, st>>>(B.bl, B.q, B.r, nullptr, S->op.mult, S->op.wtab, B.part_a, S->tab,
+                                                  1, 0);
+    k_outer_finB<K><<<S->nseg, kBlock, 0, st>>>(B.part_a, S->tab, B.so, B.si, 0);
+    k_seg_cond<<<1, kBlock, 0, st>>>(B.so, S->nseg, B.so + S->nseg, nullptr, 0, h, use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
@@ -1072,7 +1149,7 @@ int build_nested_graph(ssg_system::BlockGraph &G, FI init, FII iinit, FIB ibody,
     return rc;
 }
 
-int read_scalb(ssg_system *S, const ScalB *src, ScalB *dst) {
+int read_glob(ssg_system *S, const ScalB *src, ScalB *dst) {
     SSG_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(ScalB), cudaMemcpyDeviceToHost, S->ctx->stream));
     SSG_CUDA_TRY(cudaStreamSynchronize(S->ctx->stream));
     return SSG_OK;
@@ -1103,106 +1180,131 @@ int run_blockB(ssg_system *S, int mode, int64_t *launches) {
         return SSG_OK;
     }
     ScalB ho{}, hi{};
+    const ScalB *go = B.so + S->nseg, *gi = B.si + S->nseg;
     if (mode != SSG_MIXED) {
         rc = launch_initB<K>(S, s, B.p, 0, 0);
-        *launches += 2;
+        *launches += 3;
         for (; rc == SSG_OK;) {
-            rc = read_scalb(S, B.so, &ho);
+            rc = read_glob(S, go, &ho);
             if (rc != SSG_OK || ho.done) break;
             for (int i = 0; i < kHostChunk && rc == SSG_OK; ++i) rc = launch_bodyB64<K>(S, s, 0, 0);
-            *launches += 3 * kHostChunk;
+            *launches += 4 * kHostChunk;
         }
         return rc;
     }
     rc = launch_initB<K>(S, s, nullptr, 0, 0);
-    *launches += 2;
+    *launches += 3;
     for (; rc == SSG_OK;) {
-        rc = read_scalb(S, B.so, &ho);
+        rc = read_glob(S, go, &ho);
         if (rc != SSG_OK || ho.done) break;
         rc = launch_inner_initB<K>(S, s, 0, 0);
-        *launches += 2;
+        *launches += 3;
         for (; rc == SSG_OK;) {
-            rc = read_scalb(S, B.si, &hi);
+            rc = read_glob(S, gi, &hi);
             if (rc != SSG_OK || hi.done) break;
             for (int i = 0; i < kHostChunk && rc == SSG_OK; ++i) rc = launch_inner_bodyB<K>(S, s, 0, 0);
-            *launches += 3 * kHostChunk;
+            *launches += 4 * kHostChunk;
         }
         if (rc == SSG_OK) rc = launch_outer_tailB<K>(S, s, 0, 0);
-        *launches += 4;
+        *launches += 5;
     }
     return rc;
 }
 
-// nr (<= K) right-hand sides at b_glob / x_glob (device, column j at j*n).
+// All segments' right-hand sides at b_glob / x_glob (device; segment sg's
+// right-hand side j at seg_rhs_off[sg] + j * n_sg); nr_single > 0 for a
+// one-segment solve of nr_single right-hand sides; st receives one entry per
+// (segment, right-hand side) in that order.
 template <int K>
-int solve_block(ssg_system *S, int nr, const double *b_glob, double *x_glob, int guess, double rtol,
+int solve_block(ssg_system *S, int nr_single, const double *b_glob, double *x_glob, int guess, double rtol,
                 int32_t max_iter, int mode, ssg_stats *st) {
     int rc = ensure_block(S, K);
     if (rc != SSG_OK) return rc;
     ssg_ctx *C = S->ctx;
     cudaStream_t s = C->stream;
     ssg_system::BlockState &B = S->blk;
-    const int64_t N = S->maps.nloc, n = S->maps.n;
+    const int64_t N = S->maps.nloc;
     int64_t launches = 0;
     SSG_CUDA_TRY(cudaEventRecord(S->ev0, s));
-    k_scatterB<K><<<grid_for(N * K, C->num_sms), kBlock, 0, s>>>(N, S->d_l2g, n, nr, b_glob, B.bl);
-    ++launches;
+    k_set_paramsB<<<1, kBlock, 0, s>>>(B.so, S->nseg, rtol, max_iter, guess, C->inner_rtol, C->max_outer,
+                                       const_cast<int32_t *>(S->tab.nrhs), nr_single);
+    k_scatterB<K><<<S->nchunks, kBlock, 0, s>>>(S->d_l2g, b_glob, B.bl, S->tab);
+    launches += 2;
     if (guess) {
-        k_scatterB<K><<<grid_for(N * K, C->num_sms), kBlock, 0, s>>>(N, S->d_l2g, n, nr, x_glob, B.xl);
-        k_spmm_asm<double, K, false><<<S->grid_spmmB64, kSpmvThreads, 0, s>>>(S->opB64, B.xl, B.q, nullptr, nullptr);
+        k_scatterB<K><<<S->nchunks, kBlock, 0, s>>>(S->d_l2g, x_glob, B.xl, S->tab);
+        k_spmm_seg<double, K, false><<<S->grid_spmmB, kSpmvThreads, 0, s>>>(S->opB64, B.xl, B.q, nullptr, S->tab,
+                                                                             nullptr);
         launches += 2;
     } else {
         SSG_CUDA_TRY(cudaMemsetAsync(B.xl, 0, sizeof(double) * N * K, s));
         SSG_CUDA_TRY(cudaMemsetAsync(B.q, 0, sizeof(double) * N * K, s));
     }
-    k_set_paramsB<<<1, 32, 0, s>>>(B.so, rtol, max_iter, guess, nr, C->inner_rtol, C->max_outer);
-    ++launches;
     SSG_CUDA_TRY(cudaGetLastError());
     rc = run_blockB<K>(S, mode, &launches);
     if (rc != SSG_OK) return rc;
-    k_gatherB<K><<<grid_for(n * nr, C->num_sms), kBlock, 0, s>>>(n, S->d_own, nr, B.xl, x_glob);
+    k_gatherB<K><<<S->nchunks, kBlock, 0, s>>>(S->d_l2g, S->d_own, B.xl, x_glob, S->tab);
     // true residuals ||b_j - S x_j||_w in FP64
-    k_spmm_asm<double, K, false><<<S->grid_spmmB64, kSpmvThreads, 0, s>>>(S->opB64, B.xl, B.q, nullptr, nullptr);
-    const int gv = grid_vecB(S, K);
-    k_residualB<K><<<gv, kBlock, 0, s>>>(N, B.bl, B.q, nullptr, nullptr, S->op.mult, S->op.wtab, blk_part_a(S), 1,
-                                         0);
-    k_outer_finB<K><<<1, kBlock, 0, s>>>(blk_part_a(S), gv, B.so, B.si, 1, 0, 0);
+    k_spmm_seg<double, K, false><<<S->grid_spmmB, kSpmvThreads, 0, s>>>(S->opB64, B.xl, B.q, nullptr, S->tab,
+                                                                         nullptr);
+    k_residualB<K><<<S->nchunks, kBlock, 0, s>>>(B.bl, B.q, nullptr, nullptr, S->op.mult, S->op.wtab, B.part_a,
+                                                 S->tab, 1, 0);
+    k_outer_finB<K><<<S->nseg, kBlock, 0, s>>>(B.part_a, S->tab, B.so, B.si, 1);
     launches += 4;
     SSG_CUDA_TRY(cudaGetLastError());
     SSG_CUDA_TRY(cudaEventRecord(S->ev1, s));
-    ScalB h{};
-    rc = read_scalb(S, B.so, &h);
-    if (rc != SSG_OK) return rc;
+    std::vector<ScalB> h(static_cast<size_t>(S->nseg) + 1);
+    SSG_CUDA_TRY(cudaMemcpyAsync(h.data(), B.so, sizeof(ScalB) * h.size(), cudaMemcpyDeviceToHost, s));
+    SSG_CUDA_TRY(cudaStreamSynchronize(s));
     float ms = 0.f;
     SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
+    const ScalB &g = h[S->nseg];
     if (C->driver == SSG_DRIVER_GRAPH) {
-        if (mode == SSG_MIXED)  // init 2; per refinement inner init 2 + tail 4; 3 per inner loop iteration
-            launches += 2 + 6 * static_cast<int64_t>(h.iter) + 3 * static_cast<int64_t>(h.loops);
+        if (mode == SSG_MIXED)  // init 3; per refinement inner init 3 + tail 5; 4 per inner loop iteration
+            launches += 3 + 8 * static_cast<int64_t>(g.iter) + 4 * static_cast<int64_t>(g.loops);
         else
-            launches += 2 + 3 * static_cast<int64_t>(h.iter);
+            launches += 3 + 4 * static_cast<int64_t>(g.iter);
     }
     int first_bad = SSG_OK;
-    for (int j = 0; j < nr; ++j) {
-        if (h.status[j] != SSG_OK && first_bad == SSG_OK) first_bad = h.status[j];
-        if (!st) continue;
-        st[j].status = h.status[j];
-        st[j].iters = h.iters[j];
-        st[j].outer = mode == SSG_MIXED ? h.outer[j] : 1;
-        st[j].block = K;
-        st[j].relres = h.relres[j];
-        st[j].true_relres = h.bnorm[j] > 0.0 ? std::sqrt(h.aux[j]) / h.bnorm[j] : std::sqrt(h.aux[j]);
-        st[j].solve_ms = ms;
-        st[j].kernel_launches = launches;
+    size_t o = 0;
+    for (int sg = 0; sg < S->nseg; ++sg) {
+        const ScalB &hs = h[sg];
+        const int nr = nr_single > 0 ? nr_single : S->seg_nrhs[sg];
+        for (int j = 0; j < nr; ++j, ++o) {
+            if (hs.status[j] != SSG_OK && first_bad == SSG_OK) first_bad = hs.status[j];
+            if (!st) continue;
+            ssg_stats &t = st[o];
+            t.status = hs.status[j];
+            t.iters = hs.iters[j];
+            t.outer = mode == SSG_MIXED ? hs.outer[j] : 1;
+            t.block = K;
+            t.relres = hs.relres[j];
+            t.true_relres = hs.bnorm[j] > 0.0 ? std::sqrt(hs.aux[j]) / hs.bnorm[j] : std::sqrt(hs.aux[j]);
+            t.solve_ms = ms;
+            t.kernel_launches = launches;
+        }
     }
     return first_bad;
 }
 
 int solve_block_k(ssg_system *S, int nr, const double *b, double *x, int guess, double rtol, int32_t max_iter,
                   int mode, ssg_stats *st) {
+    if (S->nseg != 1) {
+        set_error("a batch of systems is solved with ssg_solve_batch");
+        return SSG_E_INVALID;
+    }
     if (nr <= 2) return solve_block<2>(S, nr, b, x, guess, rtol, max_iter, mode, st);
     if (nr <= 4) return solve_block<4>(S, nr, b, x, guess, rtol, max_iter, mode, st);
     if (nr <= 8) return solve_block<8>(S, nr, b, x, guess, rtol, max_iter, mode, st);
     return solve_block<16>(S, nr, b, x, guess, rtol, max_iter, mode, st);
+}
+
+int solve_batch_k(ssg_system *S, const double *b, double *x, int guess, double rtol, int32_t max_iter, int mode,
+                  ssg_stats *st) {
+    const int k = S->batch_k;
+    if (k <= 2) return solve_block<2>(S, 0, b, x, guess, rtol, max_iter, mode, st);
+    if (k <= 4) return solve_block<4>(S, 0, b, x, guess, rtol, max_iter, mode, st);
+    if (k <= 8) return solve_block<8>(S, 0, b, x, guess, rtol, max_iter, mode, st);
+    return solve_block<16>(S, 0, b, x, guess, rtol, max_iter, mode, st);
 }
 
 template <typename T>
@@ -1220,13 +1322,13 @@ int spmm_checked(ssg_system *S, int32_t k, const T *x_loc, T *y_loc) {
         return SSG_E_INVALID;
     }
     const DevOp &A = sizeof(T) == 8 ? S->opB64 : S->opB32;
-    const int grid = sizeof(T) == 8 ? S->grid_spmmB64 : S->grid_spmmB32;
+    const int grid = S->grid_spmmB;
     cudaStream_t st = S->ctx->stream;
     switch (k) {
-        case 2: k_spmm_asm<T, 2, false><<<grid, kSpmvThreads, 0, st>>>(A, x_loc, y_loc, nullptr, nullptr); break;
-        case 4: k_spmm_asm<T, 4, false><<<grid, kSpmvThreads, 0, st>>>(A, x_loc, y_loc, nullptr, nullptr); break;
-        case 8: k_spmm_asm<T, 8, false><<<grid, kSpmvThreads, 0, st>>>(A, x_loc, y_loc, nullptr, nullptr); break;
-        default: k_spmm_asm<T, 16, false><<<grid, kSpmvThreads, 0, st>>>(A, x_loc, y_loc, nullptr, nullptr); break;
+        case 2: k_spmm_asm<T, 2><<<grid, kSpmvThreads, 0, st>>>(A, x_loc, y_loc); break;
+        case 4: k_spmm_asm<T, 4><<<grid, kSpmvThreads, 0, st>>>(A, x_loc, y_loc); break;
+        case 8: k_spmm_asm<T, 8><<<grid, kSpmvThreads, 0, st>>>(A, x_loc, y_loc); break;
+        default: k_spmm_asm<T, 16><<<grid, kSpmvThreads, 0, st>>>(A, x_loc, y_loc); break;
     }
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
@@ -1415,6 +1517,93 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
     }
     *sys = S;
     return SSG_OK;
+}
+
+int ssg_partition_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off, const int32_t *sys_sub_off,
+                        const int32_t *sys_nrhs, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                        const int32_t *part, ssg_system **sys) {
+    if (!sys) {
+        set_error("sys is null");
+        return SSG_E_INVALID;
+    }
+    *sys = nullptr;
+    if (!ctx || nsys < 1 || !sys_node_off || !sys_sub_off || !sys_nrhs) {
+        set_error("batch: need a context, nsys >= 1 and the per-system tables");
+        return SSG_E_INVALID;
+    }
+    if (sys_node_off[0] != 0 || sys_sub_off[0] != 0) {
+        set_error("batch: node and subdomain offsets must start at 0");
+        return SSG_E_INVALID;
+    }
+    for (int32_t s = 0; s < nsys; ++s)
+        if (sys_node_off[s + 1] <= sys_node_off[s] || sys_sub_off[s + 1] <= sys_sub_off[s] || sys_nrhs[s] < 1 ||
+            sys_nrhs[s] > kMaxRhs) {
+            set_error("batch: every system needs >= 1 node, >= 1 subdomain and 1..16 right-hand sides");
+            return SSG_E_INVALID;
+        }
+    const int32_t n = sys_node_off[nsys], P = sys_sub_off[nsys];
+    ssg_system *S = new (std::nothrow) ssg_system();
+    if (!S) return SSG_E_OOM;
+    std::string err;
+    int rc = build_host_maps(n, rowptr, colidx, val, part, P, S->maps, &err);
+    if (rc != SSG_OK) {
+        set_error(err);
+        delete S;
+        return rc;
+    }
+    // the union must be block diagonal and every system's subdomains its own
+    for (int32_t s = 0; s < nsys && rc == SSG_OK; ++s)
+        for (int32_t i = sys_node_off[s]; i < sys_node_off[s + 1] && rc == SSG_OK; ++i) {
+            if (part[i] < sys_sub_off[s] || part[i] >= sys_sub_off[s + 1]) rc = SSG_E_INVALID;
+            for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+                if (colidx[k] < sys_node_off[s] || colidx[k] >= sys_node_off[s + 1]) rc = SSG_E_INVALID;
+        }
+    if (rc != SSG_OK) {
+        set_error("batch: a node's subdomain lies outside its system's range, or an entry couples two systems");
+        delete S;
+        return rc;
+    }
+    S->seg_sub.assign(sys_sub_off, sys_sub_off + nsys + 1);
+    S->seg_node.assign(sys_node_off, sys_node_off + nsys + 1);
+    S->seg_nrhs.assign(sys_nrhs, sys_nrhs + nsys);
+    S->seg_rhs_off.assign(static_cast<size_t>(nsys), 0);
+    int64_t o = 0;
+    for (int32_t s = 0; s < nsys; ++s) {
+        S->seg_rhs_off[s] = o;
+        o += static_cast<int64_t>(sys_nrhs[s]) * (sys_node_off[s + 1] - sys_node_off[s]);
+        S->batch_k = std::max(S->batch_k, sys_nrhs[s]);
+    }
+    S->ctx = ctx;
+    ctx->live_systems++;
+    S->pdl = ctx->pdl != 0;
+    rc = upload(S);
+    if (rc != SSG_OK) {
+        ssg_system_destroy(S);
+        return rc;
+    }
+    *sys = S;
+    return SSG_OK;
+}
+
+int ssg_solve_batch(ssg_system *S, const double *b, double *x, int32_t x_is_guess, double rtol, int32_t max_iter,
+                    int32_t mode, ssg_stats *stats) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (S->batch_k < 1) {
+        set_error("not a batch of systems (use ssg_partition_batch)");
+        return SSG_E_INVALID;
+    }
+    if (!b || !x || !(rtol >= 0.0) || (mode != SSG_FP64 && mode != SSG_MIXED)) {
+        set_error("null b/x, negative rtol, or mode not SSG_FP64 / SSG_MIXED");
+        return SSG_E_INVALID;
+    }
+    int32_t nmax = 0;
+    for (int32_t s = 0; s < S->nseg; ++s) nmax = std::max(nmax, S->seg_node[s + 1] - S->seg_node[s]);
+    if (max_iter <= 0) max_iter = nmax;
+    SSG_CUDA_TRY(cudaSetDevice(S->ctx->device));
+    rc = solve_batch_k(S, b, x, x_is_guess, rtol, max_iter, mode, stats);
+    if (rc != SSG_OK && rc != SSG_E_CUDA && rc != SSG_E_OOM && rc != SSG_E_INVALID) set_error(ssg_error_string(rc));
+    return rc;
 }
 
 int ssg_get_sizes(const ssg_system *S, ssg_sizes *o) {

@@ -1,4 +1,4 @@
-// Several right-hand sides solved together (ssg_solve with k > 1).
+// Several right-hand sides, and several independent systems, solved together.
 //
 // K right-hand sides (K = 2, 4, 8 or 16) run Algorithm 3 side by side, each
 // with its own alpha, beta and stopping test; the local matrices of the
@@ -9,12 +9,20 @@
 // column therefore follows the same sequence of operations as a solve of its
 // right-hand side alone.
 //
+// Independent systems ("segments") are solved as one operator: the union of
+// their sub-structures, block diagonal, with the subdomains of each system
+// contiguous.  Every block of every kernel works inside one segment (the
+// product's work list is cut per segment, the vector kernels run one block
+// per chunk of one segment's local entries), each segment has its own state
+// (ScalB) for its K columns, and a segment whose columns are all frozen
+// skips its blocks.  One system with K columns is the case of one segment.
+//
 // Local vector blocks are interleaved: entry k of column j sits at k*K + j,
 // so one local entry's K values are contiguous (K*8 bytes in FP64).
 //
 // Reductions stay deterministic: a block writes one partial per column, and
-// every block of the next kernel sums the partials of each column in the
-// same fixed order.
+// every block of the next kernel sums its segment's partials of each column
+// in the same fixed order.
 #pragma once
 
 #include "kernels.cuh"
@@ -131,14 +139,25 @@ __device__ __forceinline__ void slice_chunk_k(const T *__restrict__ sv, const in
         for (int j = 0; j < K; ++j) acc[j] = fma(v[e], xv[e][j], acc[j]);
 }
 
+// Segment tables (host-built, see api.cu).
+struct SegTab {
+    const int32_t *blk_seg;    // [product grid] segment of each block of the K-vector product
+    const int32_t *seg_blk;    // [nseg + 1] product blocks of each segment
+    const int4 *chunk;         // [nchunks] (segment, first local entry, end local entry, 0)
+    const int32_t *seg_chunk;  // [nseg + 1] chunks of each segment
+    const int32_t *node_off;   // [nseg + 1] first global node of each segment
+    const int64_t *rhs_off;    // [nseg] first value of the segment's right-hand sides in b / x
+    const int32_t *nrhs;       // [nseg] right-hand sides of the segment (columns >= nrhs are padding)
+    int32_t nseg;
+};
+
 // Sub-structured product with K vectors: Y = S X, then (with DOTS) each
 // block's partial of (x_j, y_j)_w at partials[block * K + j].  The work list
 // and the summation orders (CSR order inside a row, ascending subdomain at
 // an interface node) are those of the single-vector kernel.
 template <typename T, int K, bool DOTS>
-__global__ void __launch_bounds__(kSpmvThreads, SpmmTraits<T>::kBlocksPerSM)
-    k_spmm_asm(DevOp A, const T *__restrict__ X, T *__restrict__ Y, double *partials, const ScalB *s) {
-    if (s && s->halt[s->iter & 1]) return;
+__device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ X, T *__restrict__ Y,
+                                          double *partials) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 range = A.warp_range[blockIdx.x * kSpmvWarps + warp];
     const T *__restrict__ sv = slice_vals<T>(A);
@@ -269,16 +288,33 @@ __global__ void __launch_bounds__(kSpmvThreads, SpmmTraits<T>::kBlocksPerSM)
     }
 }
 
-// Every block sums each column's partials (G blocks of the previous kernel,
-// K per block) in the same fixed order: warp w takes the columns j = w mod 8,
-// lane-strided over the blocks, then a fixed shuffle tree.  Result in tot[K]
-// (shared), valid after the call in every thread.
+// The K-vector product of ssg_spmm_assembled (no state, no partials).
+template <typename T, int K>
+__global__ void __launch_bounds__(kSpmvThreads, SpmmTraits<T>::kBlocksPerSM)
+    k_spmm_asm(DevOp A, const T *__restrict__ X, T *__restrict__ Y) {
+    spmm_body<T, K, false>(A, X, Y, nullptr);
+}
+
+// The K-vector product inside the solves: blocks of a segment whose columns
+// are all frozen (segs given) return at once.
+template <typename T, int K, bool DOTS>
+__global__ void __launch_bounds__(kSpmvThreads, SpmmTraits<T>::kBlocksPerSM)
+    k_spmm_seg(DevOp A, const T *__restrict__ X, T *__restrict__ Y, double *partials, SegTab tab,
+               const ScalB *segs) {
+    if (segs && segs[tab.blk_seg[blockIdx.x]].act == 0) return;
+    spmm_body<T, K, DOTS>(A, X, Y, partials);
+}
+
+// Sums of each column's partials over blocks [b0, b1) of the previous kernel
+// (K per block), the same fixed order in every block: warp w takes the
+// columns j = w mod 8, lane-strided over the blocks, then a fixed shuffle
+// tree.  Result in tot[K] (shared), valid after the call in every thread.
 template <int K>
-__device__ __forceinline__ void all_sum_cols(const double *partials, int G, double *tot) {
+__device__ __forceinline__ void seg_sum_cols(const double *partials, int b0, int b1, double *tot) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int j = warp; j < K; j += kBlock / 32) {
         double v = 0.0;
-        for (int g = lane; g < G; g += 32) v += __ldcg(partials + (size_t)g * K + j);
+        for (int g = b0 + lane; g < b1; g += 32) v += __ldcg(partials + (size_t)g * K + j);
         v = warp_sum(v);
         if (lane == 0) tot[j] = v;
     }
@@ -286,8 +322,9 @@ __device__ __forceinline__ void all_sum_cols(const double *partials, int G, doub
 }
 
 // Per-column block sum of thread accumulators.  Thread t holds acc[u] for
-// the column (VW t + u) mod K (true when the element loop strides by a
-// multiple of K, as all loops below do); the block's sums go to out[0..K).
+// the column (VW t + u) mod K (true when the element loop starts at a
+// multiple of K and strides by a multiple of K, as all loops below do); the
+// block's sums go to out[0..K).
 template <int K, int VW, typename A>
 __device__ __forceinline__ void block_cols_sum(const A (&acc)[VW], double *out) {
     __shared__ A red[kBlock * VW];
@@ -306,31 +343,47 @@ __device__ __forceinline__ void block_cols_sum(const A (&acc)[VW], double *out) 
     }
 }
 
-__device__ __forceinline__ void stop_loop_b(ScalB *s, int k1, cudaGraphConditionalHandle h, int use_cond) {
-    s->halt[k1 & 1] = 1;
-    s->done = 1;
-    if (use_cond) cudaGraphSetConditional(h, 0);
+// One block: the loop condition of a segmented loop (any segment with an
+// active column continues), the loop count in glob->iter (reset: set to 0
+// instead of counted), and the running count of inner iterations in
+// count->loops when count is given.
+__global__ void __launch_bounds__(kBlock) k_seg_cond(const ScalB *segs, int nseg, ScalB *glob, ScalB *count,
+                                                     int reset, cudaGraphConditionalHandle h, int use_cond) {
+    int any = 0;
+    for (int sg = threadIdx.x; sg < nseg; sg += kBlock) any |= segs[sg].act != 0;
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        glob->iter = reset ? 0 : glob->iter + 1;
+        if (reset) glob->loops = 0;
+        if (count && !reset) count->loops += 1;
+        glob->done = !any;
+        if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
+    }
 }
 
-// Algorithm 3 lines 3 and 5 for K columns (FP64): alpha_j = rho_j / (p_j,
-// S p_j)_w for every active column (a column with (p, S p)_w <= 0 stops with
-// a breakdown), r_j <- r_j - alpha_j q_j and each block's partials of
-// (r_j, r_j)_w.
+// Algorithm 3 lines 3 and 5 for K columns (FP64), one block per chunk:
+// alpha_j = rho_j / (p_j, S p_j)_w for every active column of the chunk's
+// segment (a column with (p, S p)_w <= 0 stops with a breakdown),
+// r_j <- r_j - alpha_j q_j over the chunk and its partials of (r_j, r_j)_w.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_update_rB(int64_t N, double *__restrict__ r, const double *__restrict__ q,
+__global__ void __launch_bounds__(kBlock) k_update_rB(const double *__restrict__ q, double *__restrict__ r,
                                                       const uint8_t *__restrict__ mult,
                                                       const double *__restrict__ wtab,
-                                                      const uint8_t *__restrict__ gflag, const double *part_pq, int G1,
-                                                      double *part_rr, ScalB *s) {
+                                                      const uint8_t *__restrict__ gflag, const double *part_pq,
+                                                      double *part_rr, SegTab tab, ScalB *segs) {
     __shared__ double tot[K];
     __shared__ double alpha_s[K];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int4 ch = tab.chunk[blockIdx.x];
+    ScalB *s = segs + ch.x;
+    const bool first = (int)blockIdx.x == tab.seg_chunk[ch.x];
+    const uint32_t act = s->act;
+    if (first && threadIdx.x == 0) {
         for (int j = 0; j < K; ++j) s->rho_b[j] = s->rho[j];
         s->iter_b = s->iter;
+        if (!act) s->act_b = 0;
     }
-    if (s->halt[s->iter & 1]) return;
-    const uint32_t act = s->act;
-    all_sum_cols<K>(part_pq, G1, tot);
+    if (!act) return;
+    seg_sum_cols<K>(part_pq, tab.seg_blk[ch.x], tab.seg_blk[ch.x + 1], tot);
     if (threadIdx.x < K) {
         const int j = threadIdx.x;
         const double pq = tot[j];
@@ -339,7 +392,7 @@ __global__ void __launch_bounds__(kBlock) k_update_rB(int64_t N, double *__restr
         alpha_s[j] = a;
     }
     __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (first && threadIdx.x == 0) {
         uint32_t ab = act;
         for (int j = 0; j < K; ++j) {
             if (!((act >> j) & 1u)) continue;
@@ -356,11 +409,10 @@ __global__ void __launch_bounds__(kBlock) k_update_rB(int64_t N, double *__restr
     const int j0 = (2 * threadIdx.x) % K;
     const double a0 = alpha_s[j0], a1 = alpha_s[j0 + 1];
     double acc[2] = {0.0, 0.0};
-    const int64_t stride = (int64_t)gridDim.x * kBlock;
-    const int64_t NK2 = N * K / 2;
     double2 *__restrict__ r2 = reinterpret_cast<double2 *>(r);
     const double2 *__restrict__ q2 = reinterpret_cast<const double2 *>(q);
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < NK2; i += stride) {
+    const int64_t i1 = (int64_t)ch.z * K / 2;
+    for (int64_t i = (int64_t)ch.y * K / 2 + threadIdx.x; i < i1; i += kBlock) {
         double2 rv = r2[i];
         const double2 qv = __ldcs(q2 + i);
         rv.x = fma(-a0, qv.x, rv.x);
@@ -379,20 +431,26 @@ __global__ void __launch_bounds__(kBlock) k_update_rB(int64_t N, double *__restr
     block_cols_sum<K, 2>(acc, part_rr + (size_t)blockIdx.x * K);
 }
 
-// Algorithm 3 lines 4, 7, 8 for K columns (FP64): beta_j = (r_j, r_j)_w /
-// rho_j, x_j <- x_j + alpha_j p_j, p_j <- r_j + beta_j p_j (alpha = beta = 0
-// for frozen columns); block 0 records each column's iteration and stopping
-// decision and ends the loop when no column is left.
+// Algorithm 3 lines 4, 7, 8 for K columns (FP64), one block per chunk:
+// beta_j = (r_j, r_j)_w / rho_j, x_j <- x_j + alpha_j p_j, p_j <- r_j +
+// beta_j p_j (alpha = beta = 0 for frozen columns); the segment's first chunk
+// records each column's iteration and stopping decision.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_update_xpB(int64_t N, double *__restrict__ x, double *__restrict__ p,
-                                                       const double *__restrict__ r, const double *part_rr, int G2,
-                                                       ScalB *s, cudaGraphConditionalHandle h, int use_cond) {
+__global__ void __launch_bounds__(kBlock) k_update_xpB(double *__restrict__ x, double *__restrict__ p,
+                                                       const double *__restrict__ r, const double *part_rr,
+                                                       SegTab tab, ScalB *segs) {
     __shared__ double tot[K];
     __shared__ double alpha_s[K], beta_s[K];
-    const int k = s->iter_b;
-    if (s->halt[k & 1]) return;
+    const int4 ch = tab.chunk[blockIdx.x];
+    ScalB *s = segs + ch.x;
+    const bool first = (int)blockIdx.x == tab.seg_chunk[ch.x];
     const uint32_t ab = s->act_b;
-    all_sum_cols<K>(part_rr, G2, tot);
+    if (!ab) {
+        if (first && threadIdx.x == 0) s->act = 0;
+        return;
+    }
+    const int k = s->iter_b;
+    seg_sum_cols<K>(part_rr, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], tot);
     if (threadIdx.x < K) {
         const int j = threadIdx.x;
         const bool on = (ab >> j) & 1u;
@@ -403,12 +461,11 @@ __global__ void __launch_bounds__(kBlock) k_update_xpB(int64_t N, double *__rest
     const int j0 = (2 * threadIdx.x) % K;
     const double a0 = alpha_s[j0], a1 = alpha_s[j0 + 1];
     const double b0 = beta_s[j0], b1 = beta_s[j0 + 1];
-    const int64_t stride = (int64_t)gridDim.x * kBlock;
-    const int64_t NK2 = N * K / 2;
     double2 *x2 = reinterpret_cast<double2 *>(x);
     double2 *p2 = reinterpret_cast<double2 *>(p);
     const double2 *r2 = reinterpret_cast<const double2 *>(r);
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < NK2; i += stride) {
+    const int64_t i1 = (int64_t)ch.z * K / 2;
+    for (int64_t i = (int64_t)ch.y * K / 2 + threadIdx.x; i < i1; i += kBlock) {
         const double2 pv = p2[i];
         double2 xv = __ldcs(x2 + i);
         const double2 rv = r2[i];
@@ -417,7 +474,7 @@ __global__ void __launch_bounds__(kBlock) k_update_xpB(int64_t N, double *__rest
         __stcs(x2 + i, xv);
         p2[i] = make_double2(fma(b0, pv.x, rv.x), fma(b1, pv.y, rv.y));
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (first && threadIdx.x == 0) {
         uint32_t na = ab;
         for (int j = 0; j < K; ++j) {
             if (!((ab >> j) & 1u)) continue;
@@ -437,28 +494,29 @@ __global__ void __launch_bounds__(kBlock) k_update_xpB(int64_t N, double *__rest
             na = 0;
         }
         s->act = na;
-        if (!na) stop_loop_b(s, k + 1, h, use_cond);
     }
 }
 
-// Setup of Algorithm 3 line 1 for K columns: r = b - q (q = S x_1 with a
-// guess) or r = b, p = r when p is given, and each block's partials of
-// (r_j, r_j)_w (part[block*K + j]) and (b_j, b_j)_w (part[(G + block)*K + j]).
-// With p == nullptr this is the FP64 residual of the refinement loop.
+// Setup of Algorithm 3 line 1 for K columns, one block per chunk: r = b - q
+// (use_q; q = S x_1 with a guess, else zeros) or r = b, p = r when p is
+// given, and the chunk's partials of (r_j, r_j)_w (part[chunk*K + j]) and,
+// with with_b, (b_j, b_j)_w (part[(nchunks + chunk)*K + j]).  With p ==
+// nullptr this is the FP64 residual of the refinement; with r == nullptr
+// only the norms are formed (the true residual at the end of a solve).
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_residualB(int64_t N, const double *__restrict__ b,
-                                                      const double *__restrict__ q, double *__restrict__ r,
-                                                      double *__restrict__ p, const uint8_t *__restrict__ mult,
-                                                      const double *__restrict__ wtab, double *part, int use_q,
-                                                      int with_b) {
+__global__ void __launch_bounds__(kBlock) k_residualB(const double *__restrict__ b, const double *__restrict__ q,
+                                                      double *__restrict__ r, double *__restrict__ p,
+                                                      const uint8_t *__restrict__ mult,
+                                                      const double *__restrict__ wtab, double *part, SegTab tab,
+                                                      int use_q, int with_b) {
+    const int4 ch = tab.chunk[blockIdx.x];
     double arr[2] = {0.0, 0.0}, abb[2] = {0.0, 0.0};
-    const int64_t stride = (int64_t)gridDim.x * kBlock;
-    const int64_t NK2 = N * K / 2;
     const double2 *b2 = reinterpret_cast<const double2 *>(b);
     const double2 *q2 = reinterpret_cast<const double2 *>(q);
     double2 *r2 = reinterpret_cast<double2 *>(r);
     double2 *p2 = reinterpret_cast<double2 *>(p);
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < NK2; i += stride) {
+    const int64_t i1 = (int64_t)ch.z * K / 2;
+    for (int64_t i = (int64_t)ch.y * K / 2 + threadIdx.x; i < i1; i += kBlock) {
         const double2 bv = b2[i];
         double2 rv = bv;
         if (use_q) {
@@ -480,28 +538,33 @@ __global__ void __launch_bounds__(kBlock) k_residualB(int64_t N, const double *_
     if (with_b) block_cols_sum<K, 2>(abb, part + (size_t)(gridDim.x + blockIdx.x) * K);
 }
 
-__global__ void k_set_paramsB(ScalB *s, double rtol, int32_t max_iter, int32_t guess, int32_t nrhs,
-                              double inner_rtol, int32_t max_outer) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
+// Parameters of every segment's solve (one thread per segment); nr_single > 0
+// sets the right-hand-side count of a one-segment solve.
+__global__ void k_set_paramsB(ScalB *segs, int nseg, double rtol, int32_t max_iter, int32_t guess,
+                              double inner_rtol, int32_t max_outer, int32_t *nrhs, int nr_single) {
+    if (nr_single > 0 && blockIdx.x == 0 && threadIdx.x == 0) nrhs[0] = nr_single;
+    for (int sg = blockIdx.x * blockDim.x + threadIdx.x; sg < nseg; sg += gridDim.x * blockDim.x) {
+        ScalB *s = segs + sg;
         s->rtol = rtol;
         s->max_iter = max_iter;
         s->guess = guess;
-        s->nrhs = nrhs;
         s->inner_rtol = inner_rtol;
         s->max_outer = max_outer;
         s->done = 0;
     }
 }
 
-// One block, after k_residualB (with_b) of the setup: rho_j, ||b_j||_w, the
-// test before the first iteration, and the loop condition.
+// One block per segment, after k_residualB (with_b) of the setup: rho_j,
+// ||b_j||_w and the test before the first iteration.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_init_finB(const double *part, int G, ScalB *s,
-                                                      cudaGraphConditionalHandle h, int use_cond) {
+__global__ void __launch_bounds__(kBlock) k_init_finB(const double *part, int nchunks, SegTab tab, ScalB *segs) {
     __shared__ double rr[K], bb[K];
-    all_sum_cols<K>(part, G, rr);
-    all_sum_cols<K>(part + (size_t)G * K, G, bb);
+    const int sg = blockIdx.x;
+    ScalB *s = segs + sg;
+    seg_sum_cols<K>(part, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rr);
+    seg_sum_cols<K>(part + (size_t)nchunks * K, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], bb);
     if (threadIdx.x == 0) {
+        const int nr = tab.nrhs[sg];
         uint32_t act = 0;
         for (int j = 0; j < K; ++j) {
             s->rho[j] = rr[j];
@@ -513,47 +576,45 @@ __global__ void __launch_bounds__(kBlock) k_init_finB(const double *part, int G,
             s->alpha[j] = 0.0;
             s->pq[j] = 0.0;
             s->aux[j] = 0.0;
-            if (j >= s->nrhs || sqrt(rr[j]) <= s->rtol * s->bnorm[j]) {
+            if (j >= nr || sqrt(rr[j]) <= s->rtol * s->bnorm[j]) {
                 s->status[j] = SSG_OK;
             } else {
                 s->status[j] = SSG_E_NOT_CONVERGED;
                 if (s->max_iter > 0) act |= 1u << j;
             }
         }
+        s->nrhs = nr;
         s->act = act;
         s->act_b = act;
         s->iter = 0;
         s->iter_b = 0;
         s->loops = 0;
         s->done = act == 0;
-        s->halt[0] = act == 0;
-        s->halt[1] = 0;
-        if (use_cond) cudaGraphSetConditional(h, act ? 1u : 0u);
     }
 }
 
 // ---------------------------------------------------------------------------
 // SSG_MIXED for K columns: FP32 inner CG inside FP64 iterative refinement.
-// Outer state so (act = columns still refining, iters = inner iterations
-// summed, outer = refinements); inner state si (act = columns still in the
-// current inner solve).
+// Outer state so[seg] (act = columns still refining, iters = inner
+// iterations summed, outer = refinements); inner state si[seg] (act = columns
+// still in the current inner solve).
 // ---------------------------------------------------------------------------
 
-// Inner setup: r32 = (float) r64, p32 = r32, d32 = 0 and each block's
-// partials of (r32, r32)_w (FP32 products and block sums).
+// Inner setup, one block per chunk: r32 = (float) r64, p32 = r32, d32 = 0 and
+// the chunk's partials of (r32, r32)_w (FP32 products and block sums).
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_inner_initB(int64_t N, const double *__restrict__ r64,
-                                                        float *__restrict__ r32, float *__restrict__ p32,
-                                                        float *__restrict__ d32, const uint8_t *__restrict__ mult,
-                                                        const float *__restrict__ wtab, double *part) {
+__global__ void __launch_bounds__(kBlock) k_inner_initB(const double *__restrict__ r64, float *__restrict__ r32,
+                                                        float *__restrict__ p32, float *__restrict__ d32,
+                                                        const uint8_t *__restrict__ mult,
+                                                        const float *__restrict__ wtab, double *part, SegTab tab) {
+    const int4 ch = tab.chunk[blockIdx.x];
     float acc[2] = {0.f, 0.f};
-    const int64_t stride = (int64_t)gridDim.x * kBlock;
-    const int64_t NK2 = N * K / 2;
     const double2 *r2 = reinterpret_cast<const double2 *>(r64);
     float2 *rr2 = reinterpret_cast<float2 *>(r32);
     float2 *pp2 = reinterpret_cast<float2 *>(p32);
     float2 *dd2 = reinterpret_cast<float2 *>(d32);
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < NK2; i += stride) {
+    const int64_t i1 = (int64_t)ch.z * K / 2;
+    for (int64_t i = (int64_t)ch.y * K / 2 + threadIdx.x; i < i1; i += kBlock) {
         const double2 rv = r2[i];
         const float2 f = make_float2(float(rv.x), float(rv.y));
         rr2[i] = f;
@@ -566,80 +627,82 @@ __global__ void __launch_bounds__(kBlock) k_inner_initB(int64_t N, const double 
     block_cols_sum<K, 2>(acc, part + (size_t)blockIdx.x * K);
 }
 
-// One block: rho0_j of the inner solves, their tolerances
-// tau_j = max(inner_rtol, rtol ||b_j|| / ||r64_j||), the active set, and the
-// inner loop condition.
+// One block per segment: rho0_j of the inner solves, their tolerances
+// tau_j = max(inner_rtol, rtol ||b_j|| / ||r64_j||) and the active set.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_inner_finB(const double *part, int G, ScalB *si, const ScalB *so,
-                                                       cudaGraphConditionalHandle h, int use_cond) {
+__global__ void __launch_bounds__(kBlock) k_inner_finB(const double *part, SegTab tab, ScalB *si, const ScalB *so) {
     __shared__ double rr[K];
-    all_sum_cols<K>(part, G, rr);
+    const int sg = blockIdx.x;
+    seg_sum_cols<K>(part, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rr);
     if (threadIdx.x == 0) {
+        ScalB *i = si + sg;
+        const ScalB *o = so + sg;
         uint32_t act = 0;
         for (int j = 0; j < K; ++j) {
             const double tot = rr[j];
-            si->rho[j] = tot;
-            si->rho_b[j] = tot;
-            si->rho0[j] = tot;
-            const double tau =
-                so->bnorm[j] > 0.0 && so->rho[j] > 0.0 ? so->rtol * so->bnorm[j] / sqrt(so->rho[j]) : 0.0;
-            si->tau[j] = tau > so->inner_rtol ? tau : so->inner_rtol;
-            si->alpha[j] = 0.0;
-            si->status[j] = SSG_OK;
-            if (((so->act >> j) & 1u) && tot > 0.0 && so->iters[j] < so->max_iter) act |= 1u << j;
+            i->rho[j] = tot;
+            i->rho_b[j] = tot;
+            i->rho0[j] = tot;
+            const double tau = o->bnorm[j] > 0.0 && o->rho[j] > 0.0 ? o->rtol * o->bnorm[j] / sqrt(o->rho[j]) : 0.0;
+            i->tau[j] = tau > o->inner_rtol ? tau : o->inner_rtol;
+            i->alpha[j] = 0.0;
+            i->status[j] = SSG_OK;
+            if (((o->act >> j) & 1u) && tot > 0.0 && o->iters[j] < o->max_iter) act |= 1u << j;
         }
-        si->act = act;
-        si->act_b = act;
-        si->iter = 0;
-        si->iter_b = 0;
-        si->done = act == 0;
-        si->halt[0] = act == 0;
-        si->halt[1] = 0;
-        if (use_cond) cudaGraphSetConditional(h, act ? 1u : 0u);
+        i->act = act;
+        i->act_b = act;
+        i->iter = 0;
+        i->iter_b = 0;
+        i->done = act == 0;
     }
 }
 
-// Inner Algorithm 3 lines 3 and 5 in FP32 for K columns (alpha formed in
-// FP64 from the FP64 sums of the partials, then rounded to FP32 once).
+// Inner Algorithm 3 lines 3 and 5 in FP32 for K columns, one block per chunk
+// (alpha formed in FP64 from the FP64 sums of the partials, then rounded to
+// FP32 once).
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_update_r32B(int64_t N, float *__restrict__ r, const float *__restrict__ q,
+__global__ void __launch_bounds__(kBlock) k_update_r32B(const float *__restrict__ q, float *__restrict__ r,
                                                         const uint8_t *__restrict__ mult,
                                                         const float *__restrict__ wtab,
                                                         const uint8_t *__restrict__ gflag128, const double *part_pq,
-                                                        int G1, double *part_rr, ScalB *si) {
+                                                        double *part_rr, SegTab tab, ScalB *si) {
     constexpr int VW = K >= 4 ? 4 : 2;
     __shared__ double tot[K];
     __shared__ float alpha_s[K];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        for (int j = 0; j < K; ++j) si->rho_b[j] = si->rho[j];
-        si->iter_b = si->iter;
+    const int4 ch = tab.chunk[blockIdx.x];
+    ScalB *s = si + ch.x;
+    const bool first = (int)blockIdx.x == tab.seg_chunk[ch.x];
+    const uint32_t act = s->act;
+    if (first && threadIdx.x == 0) {
+        for (int j = 0; j < K; ++j) s->rho_b[j] = s->rho[j];
+        s->iter_b = s->iter;
+        if (!act) s->act_b = 0;
     }
-    if (si->halt[si->iter & 1]) return;
-    const uint32_t act = si->act;
-    all_sum_cols<K>(part_pq, G1, tot);
+    if (!act) return;
+    seg_sum_cols<K>(part_pq, tab.seg_blk[ch.x], tab.seg_blk[ch.x + 1], tot);
     if (threadIdx.x < K) {
         const int j = threadIdx.x;
         const double pq = tot[j];
         double a = 0.0;
-        if (((act >> j) & 1u) && pq > 0.0 && isfinite(pq)) a = si->rho[j] / pq;
+        if (((act >> j) & 1u) && pq > 0.0 && isfinite(pq)) a = s->rho[j] / pq;
         alpha_s[j] = float(a);
-        if (blockIdx.x == 0 && ((act >> j) & 1u)) {
-            si->pq[j] = pq;
-            si->alpha[j] = a;
+        if (first && ((act >> j) & 1u)) {
+            s->pq[j] = pq;
+            s->alpha[j] = a;
         }
     }
     __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (first && threadIdx.x == 0) {
         uint32_t ab = act;
         for (int j = 0; j < K; ++j) {
             if (!((act >> j) & 1u)) continue;
             const double pq = tot[j];
             if (!(pq > 0.0) || !isfinite(pq)) {
-                si->status[j] = SSG_E_BREAKDOWN;
+                s->status[j] = SSG_E_BREAKDOWN;
                 ab &= ~(1u << j);
             }
         }
-        si->act_b = ab;
+        s->act_b = ab;
     }
     const int j0 = (VW * threadIdx.x) % K;
     float a[VW];
@@ -648,9 +711,8 @@ __global__ void __launch_bounds__(kBlock) k_update_r32B(int64_t N, float *__rest
     float acc[VW];
 #pragma unroll
     for (int u = 0; u < VW; ++u) acc[u] = 0.f;
-    const int64_t stride = (int64_t)gridDim.x * kBlock;
-    const int64_t NV = N * K / VW;
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < NV; i += stride) {
+    const int64_t i1 = (int64_t)ch.z * K / VW;
+    for (int64_t i = (int64_t)ch.y * K / VW + threadIdx.x; i < i1; i += kBlock) {
         float rv[VW], qv[VW];
         if constexpr (VW == 4) {
             const float4 t = reinterpret_cast<const float4 *>(r)[i];
@@ -682,27 +744,33 @@ __global__ void __launch_bounds__(kBlock) k_update_r32B(int64_t N, float *__rest
     block_cols_sum<K, VW>(acc, part_rr + (size_t)blockIdx.x * K);
 }
 
-// Inner Algorithm 3 lines 4, 7, 8 in FP32 for K columns: d_j <- d_j +
-// alpha_j p_j, p_j <- r_j + beta_j p_j; block 0 counts each active column's
-// inner iteration and applies its inner test (sqrt(rho_j) <= tau_j
-// sqrt(rho0_j), or its inner iterations summed reach max_iter).
+// Inner Algorithm 3 lines 4, 7, 8 in FP32 for K columns, one block per chunk:
+// d_j <- d_j + alpha_j p_j, p_j <- r_j + beta_j p_j; the segment's first chunk
+// counts each active column's inner iteration and applies its inner test
+// (sqrt(rho_j) <= tau_j sqrt(rho0_j), or its inner iterations summed reach
+// max_iter).
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_update_dp32B(int64_t N, float *__restrict__ d, float *__restrict__ p,
-                                                         const float *__restrict__ r, const double *part_rr, int G2,
-                                                         ScalB *si, ScalB *so, cudaGraphConditionalHandle h,
-                                                         int use_cond) {
+__global__ void __launch_bounds__(kBlock) k_update_dp32B(float *__restrict__ d, float *__restrict__ p,
+                                                         const float *__restrict__ r, const double *part_rr,
+                                                         SegTab tab, ScalB *si, ScalB *so) {
     constexpr int VW = K >= 4 ? 4 : 2;
     __shared__ double tot[K];
     __shared__ float alpha_s[K], beta_s[K];
-    const int k = si->iter_b;
-    if (si->halt[k & 1]) return;
-    const uint32_t ab = si->act_b;
-    all_sum_cols<K>(part_rr, G2, tot);
+    const int4 ch = tab.chunk[blockIdx.x];
+    ScalB *s = si + ch.x;
+    const bool first = (int)blockIdx.x == tab.seg_chunk[ch.x];
+    const uint32_t ab = s->act_b;
+    if (!ab) {
+        if (first && threadIdx.x == 0) s->act = 0;
+        return;
+    }
+    const int k = s->iter_b;
+    seg_sum_cols<K>(part_rr, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], tot);
     if (threadIdx.x < K) {
         const int j = threadIdx.x;
         const bool on = (ab >> j) & 1u;
-        alpha_s[j] = on ? float(si->alpha[j]) : 0.f;
-        beta_s[j] = on ? float(tot[j] / si->rho_b[j]) : 0.f;
+        alpha_s[j] = on ? float(s->alpha[j]) : 0.f;
+        beta_s[j] = on ? float(tot[j] / s->rho_b[j]) : 0.f;
     }
     __syncthreads();
     const int j0 = (VW * threadIdx.x) % K;
@@ -712,9 +780,8 @@ __global__ void __launch_bounds__(kBlock) k_update_dp32B(int64_t N, float *__res
         a[u] = alpha_s[j0 + u];
         bt[u] = beta_s[j0 + u];
     }
-    const int64_t stride = (int64_t)gridDim.x * kBlock;
-    const int64_t NV = N * K / VW;
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < NV; i += stride) {
+    const int64_t i1 = (int64_t)ch.z * K / VW;
+    for (int64_t i = (int64_t)ch.y * K / VW + threadIdx.x; i < i1; i += kBlock) {
         float pv[VW], dv[VW], rv[VW];
         if constexpr (VW == 4) {
             const float4 t = reinterpret_cast<const float4 *>(p)[i];
@@ -744,83 +811,96 @@ __global__ void __launch_bounds__(kBlock) k_update_dp32B(int64_t N, float *__res
             reinterpret_cast<float2 *>(p)[i] = make_float2(pv[0], pv[1]);
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (first && threadIdx.x == 0) {
+        ScalB *o = so + ch.x;
         uint32_t na = ab;
         for (int j = 0; j < K; ++j) {
             if (!((ab >> j) & 1u)) continue;
             const double rr = tot[j];
-            si->rho[j] = rr;
-            const int t1 = so->iters[j] + 1;
-            so->iters[j] = t1;
-            if (sqrt(rr) <= si->tau[j] * sqrt(si->rho0[j]) || t1 >= so->max_iter) na &= ~(1u << j);
+            s->rho[j] = rr;
+            const int t1 = o->iters[j] + 1;
+            o->iters[j] = t1;
+            if (sqrt(rr) <= s->tau[j] * sqrt(s->rho0[j]) || t1 >= o->max_iter) na &= ~(1u << j);
         }
-        si->iter = k + 1;
-        so->loops += 1;
-        si->act = na;
-        if (!na) stop_loop_b(si, k + 1, h, use_cond);
+        s->iter = k + 1;
+        s->act = na;
     }
 }
 
-// One block, after the refinement's residual (k_residualB without b): each
-// refining column's outer decision (converged, inner breakdown, refinement or
-// iteration cap) and the outer loop condition.  With final != 0 it only
-// stores the true residual of every column in aux.
+// One block per segment, after the refinement's residual (k_residualB
+// without b): each refining column's outer decision (converged, inner
+// breakdown, refinement or iteration cap).  With final_ != 0 it only stores
+// the true residual of every column in aux.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_outer_finB(const double *part, int G, ScalB *so, const ScalB *si,
-                                                       int final_, cudaGraphConditionalHandle h, int use_cond) {
+__global__ void __launch_bounds__(kBlock) k_outer_finB(const double *part, SegTab tab, ScalB *so, const ScalB *si,
+                                                       int final_) {
     __shared__ double rr[K];
-    all_sum_cols<K>(part, G, rr);
+    const int sg = blockIdx.x;
+    seg_sum_cols<K>(part, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rr);
     if (threadIdx.x != 0) return;
+    ScalB *o = so + sg;
     if (final_) {
-        for (int j = 0; j < K; ++j) so->aux[j] = rr[j];
+        for (int j = 0; j < K; ++j) o->aux[j] = rr[j];
         return;
     }
-    uint32_t na = so->act;
+    const ScalB *i = si + sg;
+    uint32_t na = o->act;
     for (int j = 0; j < K; ++j) {
         if (!((na >> j) & 1u)) continue;
         const double tot = rr[j];
-        so->rho[j] = tot;
-        so->outer[j] += 1;
-        so->relres[j] = so->bnorm[j] > 0.0 ? sqrt(tot) / so->bnorm[j] : 0.0;
+        o->rho[j] = tot;
+        o->outer[j] += 1;
+        o->relres[j] = o->bnorm[j] > 0.0 ? sqrt(tot) / o->bnorm[j] : 0.0;
         int stop = 1;
-        if (sqrt(tot) <= so->rtol * so->bnorm[j]) {
-            so->status[j] = SSG_OK;
-        } else if (si->status[j] == SSG_E_BREAKDOWN) {
-            so->status[j] = SSG_E_BREAKDOWN;
-        } else if (so->outer[j] >= so->max_outer || so->iters[j] >= so->max_iter) {
-            so->status[j] = SSG_E_NOT_CONVERGED;
+        if (sqrt(tot) <= o->rtol * o->bnorm[j]) {
+            o->status[j] = SSG_OK;
+        } else if (i->status[j] == SSG_E_BREAKDOWN) {
+            o->status[j] = SSG_E_BREAKDOWN;
+        } else if (o->outer[j] >= o->max_outer || o->iters[j] >= o->max_iter) {
+            o->status[j] = SSG_E_NOT_CONVERGED;
         } else {
             stop = 0;
         }
         if (stop) na &= ~(1u << j);
     }
-    so->act = na;
-    so->iter += 1;
-    so->done = na == 0;
-    if (use_cond) cudaGraphSetConditional(h, na ? 1u : 0u);
+    o->act = na;
+    o->iter += 1;
 }
 
-// Global (n x k, right-hand side j at j*n) <-> interleaved local block
-// (nloc x K); columns k..K-1 of the block are zero.
+// Global right-hand sides <-> interleaved local blocks (nloc x K), one block
+// per chunk.  Segment sg's right-hand side j (< nrhs[sg]) starts at
+// rhs_off[sg] + j * n_sg, node g of the segment at offset g - node_off[sg];
+// columns nrhs..K-1 of the block are zero.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_scatterB(int64_t N, const int32_t *__restrict__ l2g, int64_t n, int nr,
-                                                     const double *__restrict__ xg, double *__restrict__ xl) {
-    const int64_t stride = (int64_t)gridDim.x * kBlock;
-    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < N * K; e += stride) {
+__global__ void __launch_bounds__(kBlock) k_scatterB(const int32_t *__restrict__ l2g, const double *__restrict__ xg,
+                                                     double *__restrict__ xl, SegTab tab) {
+    const int4 ch = tab.chunk[blockIdx.x];
+    const int sg = ch.x;
+    const int nr = tab.nrhs[sg];
+    const int64_t n0 = tab.node_off[sg], ns = tab.node_off[sg + 1] - n0, ro = tab.rhs_off[sg];
+    for (int64_t e = (int64_t)ch.y * K + threadIdx.x; e < (int64_t)ch.z * K; e += kBlock) {
         const int64_t i = e / K;
         const int j = (int)(e % K);
-        xl[e] = j < nr ? __ldg(xg + (int64_t)j * n + l2g[i]) : 0.0;
+        xl[e] = j < nr ? __ldg(xg + ro + j * ns + (l2g[i] - n0)) : 0.0;
     }
 }
 
+// Owner copies of the local blocks -> global right-hand-side layout.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_gatherB(int64_t n, const int32_t *__restrict__ own, int nr,
-                                                    const double *__restrict__ xl, double *__restrict__ xg) {
-    const int64_t stride = (int64_t)gridDim.x * kBlock;
-    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < n * nr; e += stride) {
-        const int j = (int)(e / n);
-        const int64_t g = e % n;
-        xg[e] = __ldg(xl + (int64_t)own[g] * K + j);
+__global__ void __launch_bounds__(kBlock) k_gatherB(const int32_t *__restrict__ l2g, const int32_t *__restrict__ own,
+                                                    const double *__restrict__ xl, double *__restrict__ xg,
+                                                    SegTab tab) {
+    const int4 ch = tab.chunk[blockIdx.x];
+    const int sg = ch.x;
+    const int nr = tab.nrhs[sg];
+    const int64_t n0 = tab.node_off[sg], ns = tab.node_off[sg + 1] - n0, ro = tab.rhs_off[sg];
+    for (int64_t e = (int64_t)ch.y * K + threadIdx.x; e < (int64_t)ch.z * K; e += kBlock) {
+        const int64_t i = e / K;
+        const int j = (int)(e % K);
+        if (j >= nr) continue;
+        const int32_t g = l2g[i];
+        if (own[g] != i) continue;
+        xg[ro + j * ns + (g - n0)] = xl[e];
     }
 }
 

@@ -41,6 +41,8 @@ EXPORTS = (
     "ssg_set_pdl",
     "ssg_destroy",
     "ssg_partition",
+    "ssg_partition_batch",
+    "ssg_solve_batch",
     "ssg_get_sizes",
     "ssg_copy_maps",
     "ssg_scatter",
@@ -129,6 +131,8 @@ def lib():
         L.ssg_set_pdl.argtypes = [vp, C.c_int]
         L.ssg_destroy.argtypes = [vp]
         L.ssg_partition.argtypes = [vp, i32, vp, vp, vp, vp, i32, C.POINTER(vp)]
+        L.ssg_partition_batch.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]
+        L.ssg_solve_batch.argtypes = [vp, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
         L.ssg_get_sizes.argtypes = [vp, C.POINTER(ssg_sizes)]
         L.ssg_copy_maps.argtypes = [vp] * 12
         L.ssg_scatter.argtypes = [vp, vp, vp]
@@ -230,6 +234,33 @@ def ssg_partition(ctx, n, rowptr, colidx, val, part, P):
         "ssg_partition",
     )
     return h
+
+
+def ssg_partition_batch(ctx, sys_node_off, sys_sub_off, sys_nrhs, rowptr, colidx, val, part):
+    node_off = np.ascontiguousarray(sys_node_off, np.int32)
+    sub_off = np.ascontiguousarray(sys_sub_off, np.int32)
+    nrhs = np.ascontiguousarray(sys_nrhs, np.int32)
+    rowptr = np.ascontiguousarray(rowptr, np.int32)
+    colidx = np.ascontiguousarray(colidx, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    part = np.ascontiguousarray(part, np.int32)
+    nsys = nrhs.size
+    n = int(node_off[-1])
+    if node_off.size != nsys + 1 or sub_off.size != nsys + 1 or rowptr.size != n + 1 or part.size != n \
+            or colidx.size != val.size or colidx.size < rowptr[-1]:
+        raise ValueError("batch tables / CSR arrays have inconsistent sizes")
+    h = C.c_void_p()
+    _check(lib().ssg_partition_batch(ctx, nsys, _ptr(node_off), _ptr(sub_off), _ptr(nrhs), _ptr(rowptr),
+                                     _ptr(colidx), _ptr(val), _ptr(part), C.byref(h)), "ssg_partition_batch")
+    return h
+
+
+def ssg_solve_batch(sys, nstats, b, x, x_is_guess=False, rtol=1e-8, max_iter=0, mode=SSG_FP64):
+    """Batch solve (device buffers); returns (status, stats per (system, right-hand side))."""
+    st = (ssg_stats * nstats)()
+    rc = lib().ssg_solve_batch(sys, _dev_f64(b), _dev_f64(x), int(bool(x_is_guess)), rtol, max_iter, mode, st)
+    _check(rc, "ssg_solve_batch", ok=(SSG_OK, SSG_E_BREAKDOWN, SSG_E_NOT_CONVERGED))
+    return rc, [st[i].as_dict() for i in range(nstats)]
 
 
 def ssg_get_sizes(sys):
@@ -406,6 +437,50 @@ class Context:
         if getattr(self, "h", None):
             if ssg_destroy(self.h) == SSG_OK:
                 self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Batch:
+    """Independent systems solved together (ssg_partition_batch / ssg_solve_batch).
+
+    systems: list of (A, part, P, nrhs) with part in 0..P-1 per system."""
+
+    def __init__(self, ctx: Context, systems):
+        import scipy.sparse as sp
+
+        self.ctx = ctx
+        ns = [A.n for A, _, _, _ in systems]
+        Ps = [P for _, _, P, _ in systems]
+        self.nrhs = [int(k) for _, _, _, k in systems]
+        self.node_off = np.concatenate([[0], np.cumsum(ns)]).astype(np.int32)
+        self.sub_off = np.concatenate([[0], np.cumsum(Ps)]).astype(np.int32)
+        U = sp.block_diag([A.to_scipy() for A, _, _, _ in systems], format="csr")
+        U.sort_indices()
+        part = np.concatenate([np.asarray(pt, np.int32) + self.sub_off[s]
+                               for s, (_, pt, _, _) in enumerate(systems)])
+        self.h = ssg_partition_batch(ctx.h, self.node_off, self.sub_off, self.nrhs, U.indptr, U.indices, U.data, part)
+        self.rhs_off = np.concatenate([[0], np.cumsum([k * n for k, n in zip(self.nrhs, ns)])]).astype(np.int64)
+        s = ssg_get_sizes(self.h)
+        self.sizes = Sizes(s.n, s.P, s.nnz, s.nloc, s.ngamma, s.max_mult, s.ncopies)
+
+    def solve(self, b, x=None, rtol=1e-8, max_iter=0, mode=SSG_FP64):
+        """b: float64 CUDA tensor of rhs_off[-1] values (system s's right-hand
+        side j at rhs_off[s] + j * n_s); returns (x, status, stats)."""
+        import torch
+
+        if b.numel() != int(self.rhs_off[-1]) or (x is not None and x.numel() != b.numel()):
+            raise ValueError("b (and x) must hold %d values" % int(self.rhs_off[-1]))
+        guess = x is not None
+        xx = torch.zeros_like(b) if x is None else x.clone()
+        rc, st = ssg_solve_batch(self.h, int(sum(self.nrhs)), b.contiguous(), xx, guess, rtol, max_iter, mode)
+        return xx, rc, st
+
+    def close(self):
+        if getattr(self, "h", None):
+            ssg_system_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         self.close()

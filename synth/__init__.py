@@ -15,6 +15,9 @@ from .problems import (  # noqa: F401
     poisson2d_5pt,
     laplace1d,
     fv3d_7pt,
+    fv2d_5pt,
+    BatchProblem,
+    batch_problem,
     fe2d_p1_jittered,
     random_spd,
     box_partition_2d,

@@ -154,6 +154,74 @@ def fv3d_7pt(nx: int, ny: int, nz: int, kappa: np.ndarray) -> CSR:
     return _csr_from_stencil(cols, vals, mask)
 
 
+def fv2d_5pt(nx: int, ny: int, kappa: np.ndarray) -> CSR:
+    """Cell-centred finite volumes on an nx x ny grid, the 2D counterpart of
+    ``fv3d_7pt``: cell (ix, iy) has id ix + nx*iy, ``kappa`` is indexed
+    [iy, ix], interior faces carry 2 k_a k_b / (k_a + k_b), boundary faces
+    2 k, A_ii sums the four face coefficients in the order y-, x-, x+, y+."""
+    k = np.asarray(kappa, dtype=np.float64).reshape(ny, nx)
+
+    def harm(a, b):
+        return 2.0 * a * b / (a + b)
+
+    bnd = 2.0 * k
+    txm, txp, tym, typ = bnd.copy(), bnd.copy(), bnd.copy(), bnd.copy()
+    fx = harm(k[:, :-1], k[:, 1:])
+    txp[:, :-1] = fx
+    txm[:, 1:] = fx
+    fy = harm(k[:-1, :], k[1:, :])
+    typ[:-1, :] = fy
+    tym[1:, :] = fy
+    diag = tym + txm
+    diag = diag + txp
+    diag = diag + typ
+    iy, ix = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    ix = ix.ravel()
+    iy = iy.ravel()
+    gid = ix + nx * iy
+    cols = np.stack([gid - nx, gid - 1, gid, gid + 1, gid + nx], axis=1)
+    vals = np.stack([-tym.ravel(), -txm.ravel(), diag.ravel(), -txp.ravel(), -typ.ravel()], axis=1)
+    mask = np.stack([iy > 0, ix > 0, np.ones_like(ix, bool), ix < nx - 1, iy < ny - 1], axis=1)
+    return _csr_from_stencil(cols, vals, mask)
+
+
+@dataclass
+class BatchProblem:
+    """Independent systems solved together: system s is (A[s], part[s], P[s])
+    with right-hand sides b[s] (k_s x n_s)."""
+
+    name: str
+    A: list
+    part: list
+    P: list
+    b: list
+    meta: dict
+
+
+def batch_problem(nsys: int = 512, side_lo: int = 32, side_hi: int = 512, seed: int = CONFIG_SEED_BASE + 4,
+                  sigma: float = 0.5) -> BatchProblem:
+    """Workload 4: nsys 2D variable-coefficient finite-volume Poisson systems,
+    side uniform in [side_lo, side_hi], log kappa ~ N(0, sigma^2) per cell,
+    px x py boxes with px, py uniform in {2, 3, 4} (4 to 16 subdomains), 1 to 8
+    right-hand sides uniform in [-1, 1].  Stream order per system: side, kappa,
+    boxes, right-hand-side count, right-hand sides."""
+    rng = np.random.default_rng(seed)
+    As, parts, Ps, bs, sides = [], [], [], [], []
+    for _ in range(nsys):
+        n = int(rng.integers(side_lo, side_hi + 1))
+        kap = np.exp(sigma * rng.standard_normal((n, n)))
+        px, py = (int(v) for v in rng.integers(2, 5, size=2))
+        k = int(rng.integers(1, 9))
+        b = rng.uniform(-1.0, 1.0, size=(k, n * n))
+        As.append(fv2d_5pt(n, n, kap))
+        parts.append(box_partition_2d(n, n, px, py))
+        Ps.append(px * py)
+        bs.append(b)
+        sides.append(n)
+    return BatchProblem("fv2d_5pt_batch%d_side%d-%d" % (nsys, side_lo, side_hi), As, parts, Ps, bs,
+                        {"sides": sides, "sigma": sigma})
+
+
 def fe2d_p1_jittered(N: int, rng: np.random.Generator, jitter: float = 0.3):
     """P1 finite-element Laplacian on a jittered N x N free-node mesh.
 

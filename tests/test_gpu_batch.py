@@ -1,0 +1,166 @@
+"""GPU batch of independent systems (ssg_partition_batch / ssg_solve_batch)
+against the oracle's independent solves of each system, through the C ABI.
+
+Workload 4's recipe at test size: 12 2D finite-volume systems with sides
+8..40, 4 to 16 box subdomains and 1 to 8 right-hand sides each, all solved in
+one graph launch.  Per (system, right-hand side) the readings of the
+single-system parity tests hold: early iterates (k <= 6) within 1e-10,
+solutions converged to 1e-12 within 1e-10, iteration counts at 1e-8 within
+max(2, 3 %); mixed mode: refinements within +-1, inner iterations within
+max(3 per refinement, 5 %), true residual <= rtol.  The graph and host-loop drivers give the
+same bits; bad batch tables are refused.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import batch_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    from paper_2108_13162_gb300 import build as ssg_build
+    from paper_2108_13162_gb300.ssg import Context
+
+    ssg_build.build()
+    c = Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def bp():
+    return batch_problem(12, 8, 40)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _make(ctx, bp):
+    from paper_2108_13162_gb300.ssg import Batch
+
+    return Batch(ctx, [(A, pt, P, b.shape[0]) for A, pt, P, b in zip(bp.A, bp.part, bp.P, bp.b)])
+
+
+def _b_all(bp):
+    import torch
+
+    return torch.from_numpy(np.concatenate([b.ravel() for b in bp.b])).cuda()
+
+
+def _split(B, bp, x):
+    x = x.cpu().numpy()
+    out = []
+    for s, b in enumerate(bp.b):
+        o = int(B.rhs_off[s])
+        out.append(x[o:o + b.size].reshape(b.shape))
+    return out
+
+
+def _each(bp):
+    for s, (A, pt, P, b) in enumerate(zip(bp.A, bp.part, bp.P, bp.b)):
+        ref = oracle.Partition(A, pt, P)
+        for j in range(b.shape[0]):
+            yield s, j, ref, b[j]
+
+
+def test_batch_early_iterates_and_converged(ctx, bp):
+    from paper_2108_13162_gb300 import ssg
+
+    B = _make(ctx, bp)
+    x, rc, st = B.solve(_b_all(bp), rtol=0.0, max_iter=6)
+    assert rc == ssg.SSG_E_NOT_CONVERGED
+    xs = _split(B, bp, x)
+    t = 0
+    for s, j, ref, b in _each(bp):
+        assert st[t]["iters"] == 6 and st[t]["block"] == 8
+        assert _rel(xs[s][j], ref.cg(b, 0.0, 6).x) <= 1e-10
+        t += 1
+    x, rc, st = B.solve(_b_all(bp), rtol=1e-12, max_iter=100000)
+    assert rc == ssg.SSG_OK
+    xs = _split(B, bp, x)
+    for s, j, ref, b in _each(bp):
+        assert _rel(xs[s][j], ref.cg(b, 1e-12, 100000).x) <= 1e-10
+
+
+def test_batch_counts_at_1e8(ctx, bp):
+    from paper_2108_13162_gb300 import ssg
+
+    B = _make(ctx, bp)
+    x, rc, st = B.solve(_b_all(bp), rtol=1e-8, max_iter=100000)
+    assert rc == ssg.SSG_OK
+    t = 0
+    iters = []
+    for s, j, ref, b in _each(bp):
+        r = ref.cg(b, 1e-8, 100000)
+        assert abs(st[t]["iters"] - r.iters) <= max(2, 0.03 * r.iters)
+        assert st[t]["true_relres"] <= 1.01e-8
+        iters.append(r.iters)
+        t += 1
+    assert max(iters) > 2 * min(iters)  # uneven systems: early finishers are frozen, others go on
+
+
+def test_batch_mixed(ctx, bp):
+    from paper_2108_13162_gb300 import ssg
+
+    B = _make(ctx, bp)
+    x, rc, st = B.solve(_b_all(bp), rtol=1e-8, max_iter=100000, mode=ssg.SSG_MIXED)
+    assert rc == ssg.SSG_OK
+    xs = _split(B, bp, x)
+    t = 0
+    for s, j, ref, b in _each(bp):
+        rm = ref.cg_mixed(b, 1e-8, 100000, 1e-4, 30)
+        tr = np.linalg.norm(b - oracle.spmv(bp.A[s], xs[s][j])) / np.linalg.norm(b)
+        assert tr <= 1.0001e-8
+        assert abs(st[t]["outer"] - rm.outer) <= 1
+        assert abs(st[t]["iters"] - rm.iters) <= max(3 * rm.outer, 0.05 * rm.iters)
+        t += 1
+
+
+def test_batch_drivers_agree(ctx, bp):
+    from paper_2108_13162_gb300 import ssg
+
+    B = _make(ctx, bp)
+    for mode in (ssg.SSG_FP64, ssg.SSG_MIXED):
+        x1, rc1, s1 = B.solve(_b_all(bp), rtol=1e-8, mode=mode)
+        ctx.set_driver(ssg.SSG_DRIVER_HOST)
+        try:
+            x2, rc2, s2 = B.solve(_b_all(bp), rtol=1e-8, mode=mode)
+        finally:
+            ctx.set_driver(ssg.SSG_DRIVER_GRAPH)
+        assert rc1 == rc2 == ssg.SSG_OK
+        assert np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
+        assert [(a["iters"], a["outer"]) for a in s1] == [(a["iters"], a["outer"]) for a in s2]
+
+
+def test_batch_rejects_bad_tables(ctx, bp):
+    import scipy.sparse as sp
+
+    from paper_2108_13162_gb300 import ssg
+
+    A0, A1 = bp.A[0], bp.A[1]
+    U = sp.block_diag([A0.to_scipy(), A1.to_scipy()], format="lil")
+    U[0, A0.n] = -0.1  # couples the two systems
+    U[A0.n, 0] = -0.1
+    U = U.tocsr()
+    U.sort_indices()
+    part = np.concatenate([bp.part[0], bp.part[1] + bp.P[0]]).astype(np.int32)
+    node_off = [0, A0.n, A0.n + A1.n]
+    sub_off = [0, bp.P[0], bp.P[0] + bp.P[1]]
+    with pytest.raises(ssg.SSGError):
+        ssg.ssg_partition_batch(ctx.h, node_off, sub_off, [1, 1], U.indptr, U.indices, U.data, part)
+    V = sp.block_diag([A0.to_scipy(), A1.to_scipy()], format="csr")
+    V.sort_indices()
+    bad = part.copy()
+    bad[0] = bp.P[0]  # a node of system 0 in a subdomain of system 1
+    with pytest.raises(ssg.SSGError):
+        ssg.ssg_partition_batch(ctx.h, node_off, sub_off, [1, 1], V.indptr, V.indices, V.data, bad)
+    with pytest.raises(ssg.SSGError):
+        ssg.ssg_partition_batch(ctx.h, node_off, sub_off, [1, 17], V.indptr, V.indices, V.data, part)
