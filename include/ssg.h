@@ -149,6 +149,27 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
                   const int32_t *part, int32_t P, ssg_system **sys);
 
 /*
+ * Sub-structures from finite elements, as Section 2.4 builds them: subdomain
+ * s owns the elements e with epart[e] = s; V_s is the set of free nodes of its
+ * elements; its local matrix is the sum of its own element matrices in local
+ * numbering (S_s = sum over e in s of K_e, each entry summed in ascending
+ * element order), so the interface blocks of the local matrices add up to the
+ * global one (Eq. interface_summation) and every S_s is a Neumann matrix.
+ * Inputs (host, copied): ne elements of nv nodes, elem[e*nv + a] in [0, n)
+ * or -1 for an eliminated (Dirichlet) node whose row and column are dropped;
+ * kel[(e*nv + a)*nv + b] the symmetric element matrices; epart[e] in [0, P).
+ * Numbering, multiplicities, interface lists and weights follow
+ * ssg_partition; the owner copy of a node is its copy in the lowest
+ * subdomain; SSG_FP64_JACOBI uses the assembled diagonal (the copies'
+ * diagonal entries summed in ascending s).  Such a system has no input-CSR
+ * values: ssg_set_values, ssg_pattern_grad and ssg_fv7_* refuse it.
+ * SSG_E_INVALID for part ids or node ids out of range, a non-symmetric
+ * element matrix, or a node that belongs to no element.
+ */
+int ssg_partition_fe(ssg_ctx *ctx, int32_t n, int32_t ne, int32_t nv, const int32_t *elem, const double *kel,
+                     const int32_t *epart, int32_t P, ssg_system **sys);
+
+/*
  * A batch of independent systems solved together (not in the paper; its
  * method is one system).  The caller passes the union of the systems as one
  * block-diagonal CSR (the input conventions of ssg_partition): system s owns

@@ -99,6 +99,9 @@ def _bind(L):
         L.or_cg.restype = C.c_int
         L.or_partition.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _i32p, C.c_int32, C.POINTER(C.c_int)]
         L.or_partition.restype = C.c_void_p
+        L.or_partition_fe.argtypes = [C.c_int32, C.c_int32, C.c_int32, _i32p, _f64p, _i32p, C.c_int32,
+                                      C.POINTER(C.c_int)]
+        L.or_partition_fe.restype = C.c_void_p
         L.or_part_free.argtypes = [C.c_void_p]
         L.or_part_sizes.argtypes = [C.c_void_p, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")]
         L.or_part_copy.argtypes = [C.c_void_p] + [_i32p] * 6 + [_f64p] + [_i32p] * 4 + [_f64p]
@@ -194,18 +197,23 @@ class Maps:
 
 
 class Partition:
-    """Handle on the oracle's sub-structure data (or_partition)."""
+    """Handle on the oracle's sub-structure data (or_partition, or
+    or_partition_fe through ``from_elements``)."""
 
-    def __init__(self, A, part, P):
+    def __init__(self, A, part, P, _handle=None):
         self.A = A
         st = C.c_int()
         self._L = lib()
-        self._rp = _c(A.rowptr, np.int32)
-        self._ci = _c(A.colidx, np.int32)
-        self._va = _c(A.val, np.float64)
-        self._pa = _c(part, np.int32)
-        h = self._L.or_partition(A.n, self._rp, self._ci, self._va, self._pa, int(P), C.byref(st))
-        self.status = st.value
+        if _handle is None:
+            self._rp = _c(A.rowptr, np.int32)
+            self._ci = _c(A.colidx, np.int32)
+            self._va = _c(A.val, np.float64)
+            self._pa = _c(part, np.int32)
+            h = self._L.or_partition(A.n, self._rp, self._ci, self._va, self._pa, int(P), C.byref(st))
+            self.status = st.value
+        else:
+            h = _handle
+            self.status = OK
         self.h = h
         if not h:
             raise ValueError("oracle partition rejected the input (status %d)" % st.value)
@@ -222,6 +230,20 @@ class Partition:
         self._L.or_part_copy(h, m.off, m.nint, m.l2g, m.mult, m.lrowptr, m.lcol, m.lval, m.gamma, m.iptr,
                            m.icopy, m.own, m.w)
         self.maps = m
+
+    @classmethod
+    def from_elements(cls, n, elem, kel, epart, P):
+        """Sub-structures from finite elements (or_partition_fe): elem (ne, nv)
+        node ids (-1: eliminated), kel (ne, nv, nv) element matrices, epart (ne)
+        subdomain of every element."""
+        elem = _c(elem, np.int32)
+        ne, nv = elem.shape
+        st = C.c_int()
+        h = lib().or_partition_fe(int(n), int(ne), int(nv), elem.ravel(), _c(kel, np.float64).ravel(),
+                                  _c(epart, np.int32), int(P), C.byref(st))
+        if not h:
+            raise ValueError("oracle element partition rejected the input (status %d)" % st.value)
+        return cls(None, None, P, _handle=h)
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -686,23 +686,23 @@ int or_pcg(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double
     return status;
 }
 
-/* The assembled diagonal of S at every local entry: node i's diagonal entry
- * lies in the local matrix of part(i), row own[i], local column own[i] - off. */
+/* The assembled diagonal of S at every local entry: d_i = sum over the copies
+ * of node i (ascending s) of the diagonal entry of its local row, where one is
+ * stored.  With entry ownership only the copy in part(i) stores one, so d_i
+ * is the global S_ii; with element sub-structures every copy holds a partial
+ * sum (Eq. interface_summation). */
 static int local_diagonal(const or_part *h, double *dl) {
-    double *dg = (double *)malloc(sizeof(double) * (size_t)(h->n > 0 ? h->n : 1));
+    double *dg = (double *)calloc((size_t)(h->n > 0 ? h->n : 1), sizeof(double));
     if (!dg) return OR_OOM;
-    for (int32_t i = 0; i < h->n; ++i) {
-        const int32_t k = h->own[i];
-        int32_t s = 0;
-        while (h->off[s + 1] <= k) ++s;
-        dg[i] = 0.0;
-        for (int32_t e = h->lrowptr[k]; e < h->lrowptr[k + 1]; ++e)
-            if (h->lcol[e] == k - h->off[s]) dg[i] = h->lval[e];
+    for (int32_t s = 0; s < h->P; ++s)
+        for (int32_t k = h->off[s]; k < h->off[s + 1]; ++k)
+            for (int32_t e = h->lrowptr[k]; e < h->lrowptr[k + 1]; ++e)
+                if (h->lcol[e] == k - h->off[s]) dg[h->l2g[k]] = dg[h->l2g[k]] + h->lval[e];
+    for (int32_t i = 0; i < h->n; ++i)
         if (!(dg[i] > 0.0)) {
             free(dg);
             return OR_INVALID;
         }
-    }
     for (int64_t k = 0; k < h->nloc; ++k) dl[k] = dg[h->l2g[k]];
     free(dg);
     return OR_OK;
@@ -761,4 +761,184 @@ int or_sub_pcg(const or_part *h, const double *b, double *x, double rtol, int32_
     *relres_out = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
     free(dl); free(bl); free(xl); free(r); free(z); free(p); free(q);
     return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sub-structures by elements (Section 2.4, finite elements).          */
+/* ------------------------------------------------------------------ */
+typedef struct { int32_t s, r, c, e; double v; } fe_entry;
+static int cmp_fe_entry(const void *x, const void *y) {
+    const fe_entry *p = (const fe_entry *)x, *q = (const fe_entry *)y;
+    if (p->s != q->s) return (p->s > q->s) - (p->s < q->s);
+    if (p->r != q->r) return (p->r > q->r) - (p->r < q->r);
+    if (p->c != q->c) return (p->c > q->c) - (p->c < q->c);
+    return (p->e > q->e) - (p->e < q->e);
+}
+typedef struct { int32_t node, s; } fe_pair;
+static int cmp_fe_pair(const void *x, const void *y) {
+    const fe_pair *p = (const fe_pair *)x, *q = (const fe_pair *)y;
+    if (p->node != q->node) return (p->node > q->node) - (p->node < q->node);
+    return (p->s > q->s) - (p->s < q->s);
+}
+
+/*
+ * Sub-structures from finite elements, as Section 2.4 builds them: subdomain s
+ * owns the elements e with epart[e] = s, V_s is the set of free nodes of its
+ * elements, and its local matrix is the sum of its own element matrices in
+ * local numbering (S_s = sum over e in s of K_e), so the interface blocks of
+ * the local matrices add up to the global interface block (Eq.
+ * interface_summation) and every S_s is a Neumann matrix (positive
+ * semi-definite).  Element e has nv nodes elem[e*nv + a] (-1: an eliminated
+ * Dirichlet node) and the symmetric matrix kel[e*nv*nv + a*nv + b]; rows and
+ * columns of eliminated nodes are dropped.  A local entry is the sum of its
+ * element contributions in ascending element order.  Numbering, multiplicity,
+ * interface lists and weights are those of or_partition; the owner copy of a
+ * node is its copy in the lowest subdomain holding it.  Invalid: epart out of
+ * range, a node index out of range, a free node in no element, a
+ * non-symmetric element matrix.
+ */
+or_part *or_partition_fe(int32_t n, int32_t ne, int32_t nv, const int32_t *elem, const double *kel,
+                         const int32_t *epart, int32_t P, int *status) {
+    *status = OR_INVALID;
+    if (n <= 0 || ne <= 0 || nv <= 0 || P <= 0) return NULL;
+    for (int32_t e = 0; e < ne; ++e) {
+        if (epart[e] < 0 || epart[e] >= P) return NULL;
+        for (int32_t a = 0; a < nv; ++a) {
+            if (elem[(int64_t)e * nv + a] < -1 || elem[(int64_t)e * nv + a] >= n) return NULL;
+            for (int32_t b = 0; b < nv; ++b)
+                if (kel[((int64_t)e * nv + a) * nv + b] != kel[((int64_t)e * nv + b) * nv + a]) return NULL;
+        }
+    }
+    *status = OR_OOM;
+    or_part *h = (or_part *)calloc(1, sizeof(or_part));
+    const int64_t npair = (int64_t)ne * nv;
+    fe_pair *pairs = (fe_pair *)malloc(sizeof(fe_pair) * (size_t)npair);
+    int32_t *mem_ptr = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)npair);
+    int32_t *memloc = (int32_t *)malloc(sizeof(int32_t) * (size_t)npair);
+    fe_entry *ent = (fe_entry *)malloc(sizeof(fe_entry) * (size_t)(npair * nv));
+    int32_t *cnt = (int32_t *)calloc((size_t)P, sizeof(int32_t));
+    if (!h || !pairs || !mem_ptr || !mem || !memloc || !ent || !cnt) goto fail;
+    h->n = n;
+    h->P = P;
+    /* membership: sorted unique (node, subdomain) pairs */
+    int64_t np = 0;
+    for (int32_t e = 0; e < ne; ++e)
+        for (int32_t a = 0; a < nv; ++a) {
+            const int32_t i = elem[(int64_t)e * nv + a];
+            if (i >= 0) { pairs[np].node = i; pairs[np].s = epart[e]; ++np; }
+        }
+    qsort(pairs, (size_t)np, sizeof(fe_pair), cmp_fe_pair);
+    {
+        int64_t w = 0;
+        for (int64_t t = 0; t < np; ++t) {
+            if (t > 0 && pairs[t].node == pairs[t - 1].node && pairs[t].s == pairs[t - 1].s) continue;
+            mem[w] = pairs[t].s;
+            mem_ptr[pairs[t].node + 1]++;
+            ++w;
+        }
+        for (int32_t j = 0; j < n; ++j) mem_ptr[j + 1] += mem_ptr[j];
+    }
+    for (int32_t j = 0; j < n; ++j)
+        if (mem_ptr[j + 1] == mem_ptr[j]) { *status = OR_INVALID; goto fail; }
+    h->mult = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    h->off = (int32_t *)calloc((size_t)P + 1, sizeof(int32_t));
+    h->nint = (int32_t *)calloc((size_t)P, sizeof(int32_t));
+    if (!h->mult || !h->off || !h->nint) goto fail;
+    for (int32_t j = 0; j < n; ++j) h->mult[j] = mem_ptr[j + 1] - mem_ptr[j];
+    for (int32_t j = 0; j < n; ++j)
+        for (int32_t t = mem_ptr[j]; t < mem_ptr[j + 1]; ++t) {
+            cnt[mem[t]]++;
+            if (h->mult[j] == 1) h->nint[mem[t]]++;
+        }
+    for (int32_t s = 0; s < P; ++s) h->off[s + 1] = h->off[s] + cnt[s];
+    h->nloc = h->off[P];
+    h->l2g = (int32_t *)malloc(sizeof(int32_t) * (size_t)h->nloc);
+    if (!h->l2g) goto fail;
+    for (int32_t s = 0; s < P; ++s) cnt[s] = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int32_t j = 0; j < n; ++j) {
+            if ((h->mult[j] >= 2) != pass) continue;
+            for (int32_t t = mem_ptr[j]; t < mem_ptr[j + 1]; ++t) {
+                const int32_t s = mem[t];
+                memloc[t] = cnt[s]++;
+                h->l2g[h->off[s] + memloc[t]] = j;
+            }
+        }
+    h->own = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!h->own) goto fail;
+    for (int32_t j = 0; j < n; ++j) h->own[j] = h->off[mem[mem_ptr[j]]] + memloc[mem_ptr[j]];
+    /* local matrices: element contributions keyed by (s, local row, local column, e) */
+    int64_t nent = 0;
+    for (int32_t e = 0; e < ne; ++e) {
+        const int32_t s = epart[e];
+        for (int32_t a = 0; a < nv; ++a) {
+            const int32_t i = elem[(int64_t)e * nv + a];
+            if (i < 0) continue;
+            int32_t li = -1;
+            for (int32_t t = mem_ptr[i]; t < mem_ptr[i + 1]; ++t)
+                if (mem[t] == s) li = memloc[t];
+            for (int32_t b = 0; b < nv; ++b) {
+                const int32_t j = elem[(int64_t)e * nv + b];
+                if (j < 0) continue;
+                int32_t lj = -1;
+                for (int32_t t = mem_ptr[j]; t < mem_ptr[j + 1]; ++t)
+                    if (mem[t] == s) lj = memloc[t];
+                ent[nent].s = s;
+                ent[nent].r = li;
+                ent[nent].c = lj;
+                ent[nent].e = e;
+                ent[nent].v = kel[((int64_t)e * nv + a) * nv + b];
+                ++nent;
+            }
+        }
+    }
+    qsort(ent, (size_t)nent, sizeof(fe_entry), cmp_fe_entry);
+    h->lrowptr = (int32_t *)calloc((size_t)h->nloc + 1, sizeof(int32_t));
+    h->lcol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nent > 0 ? nent : 1));
+    h->lval = (double *)malloc(sizeof(double) * (size_t)(nent > 0 ? nent : 1));
+    if (!h->lrowptr || !h->lcol || !h->lval) goto fail;
+    {
+        int64_t w = 0;
+        for (int64_t t = 0; t < nent;) {
+            int64_t u = t;
+            double v = 0.0;
+            while (u < nent && ent[u].s == ent[t].s && ent[u].r == ent[t].r && ent[u].c == ent[t].c) v = v + ent[u++].v;
+            h->lcol[w] = ent[t].c;
+            h->lval[w] = v;
+            h->lrowptr[h->off[ent[t].s] + ent[t].r + 1]++;
+            ++w;
+            t = u;
+        }
+        for (int64_t k = 0; k < h->nloc; ++k) h->lrowptr[k + 1] += h->lrowptr[k];
+        h->nnz = w;
+    }
+    /* interface lists and weights, as or_partition */
+    h->ngamma = 0;
+    h->ncopies = 0;
+    for (int32_t j = 0; j < n; ++j)
+        if (h->mult[j] >= 2) { h->ngamma++; h->ncopies += h->mult[j]; }
+    h->gamma = (int32_t *)malloc(sizeof(int32_t) * (size_t)(h->ngamma > 0 ? h->ngamma : 1));
+    h->iptr = (int32_t *)calloc((size_t)h->ngamma + 1, sizeof(int32_t));
+    h->icopy = (int32_t *)malloc(sizeof(int32_t) * (size_t)(h->ncopies > 0 ? h->ncopies : 1));
+    h->w = (double *)malloc(sizeof(double) * (size_t)h->nloc);
+    if (!h->gamma || !h->iptr || !h->icopy || !h->w) goto fail;
+    {
+        int32_t g = 0;
+        int64_t c = 0;
+        for (int32_t j = 0; j < n; ++j) {
+            if (h->mult[j] < 2) continue;
+            h->gamma[g] = j;
+            for (int32_t t = mem_ptr[j]; t < mem_ptr[j + 1]; ++t) h->icopy[c++] = h->off[mem[t]] + memloc[t];
+            h->iptr[++g] = (int32_t)c;
+        }
+    }
+    for (int64_t k = 0; k < h->nloc; ++k) h->w[k] = 1.0 / (double)h->mult[h->l2g[k]];
+    free(pairs); free(mem_ptr); free(mem); free(memloc); free(ent); free(cnt);
+    *status = OR_OK;
+    return h;
+fail:
+    free(pairs); free(mem_ptr); free(mem); free(memloc); free(ent); free(cnt);
+    or_part_free(h);
+    return NULL;
 }

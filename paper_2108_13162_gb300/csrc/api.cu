@@ -337,7 +337,10 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
         for (int i = seg_item[sg]; i < seg_item[sg + 1]; ++i) seg_cost[sg] += item_cost(W.items[i]);
         total += seg_cost[sg];
     }
-    const int target = std::max(1, std::min(per, num_sms * SpmmTraits<double>::kBlocksPerSM * (nseg > 1 ? 4 : 1)));
+    constexpr int kSpmmBlocks = SpmmTraits<double>::kBlocksPerSM > SpmmTraits<float>::kBlocksPerSM
+                                    ? SpmmTraits<double>::kBlocksPerSM
+                                    : SpmmTraits<float>::kBlocksPerSM;
+    const int target = std::max(1, std::min(per, num_sms * kSpmmBlocks * (nseg > 1 ? 4 : 1)));
     W.seg_blk.assign(static_cast<size_t>(nseg) + 1, 0);
     for (int sg = 0; sg < nseg; ++sg) {
         const int nit = seg_item[sg + 1] - seg_item[sg];
@@ -674,9 +677,12 @@ int upload(ssg_system *S) {
     size_t i_q32 = add(nullptr, sizeof(float) * N);
     size_t i_d32 = add(nullptr, sizeof(float) * N);
     size_t i_scal_in = add(nullptr, sizeof(Scal));
+    // element sub-structures have no input-CSR entry per local entry (-1 maps)
+    const bool from_csr = !M.lsrc.empty();
+    std::vector<int32_t> vmap = from_csr ? M.lsrc : std::vector<int32_t>(static_cast<size_t>(M.nnz), -1);
     std::vector<int32_t> imap(plan.isrc.size()), smap(plan.ssrc.size());
-    for (size_t i = 0; i < imap.size(); ++i) imap[i] = M.lsrc[plan.isrc[i]];
-    for (size_t i = 0; i < smap.size(); ++i) smap[i] = plan.ssrc[i] >= 0 ? M.lsrc[plan.ssrc[i]] : -1;
+    for (size_t i = 0; i < imap.size(); ++i) imap[i] = vmap[plan.isrc[i]];
+    for (size_t i = 0; i < smap.size(); ++i) smap[i] = plan.ssrc[i] >= 0 ? vmap[plan.ssrc[i]] : -1;
     // local entry holding the diagonal of each local entry's node (in the
     // owner's local matrix), -1 if the matrix stores none
     std::vector<int32_t> diag_of_row(static_cast<size_t>(N), -1), dmap(static_cast<size_t>(N), -1);
@@ -685,11 +691,29 @@ int upload(ssg_system *S) {
             for (int32_t e = M.lrowptr[r]; e < M.lrowptr[r + 1]; ++e)
                 if (M.off[sd] + M.lcol[e] == r) diag_of_row[r] = e;
     for (int64_t k = 0; k < N; ++k) dmap[k] = diag_of_row[M.own[M.l2g[k]]];
+    // element sub-structures: every copy holds a partial diagonal, so 1 / S_ii
+    // comes from the assembled diagonal of the host maps
+    std::vector<double> hdinv;
+    std::vector<float> hdinv32;
+    int hbad = 0;
+    if (!from_csr) {
+        hdinv.resize(static_cast<size_t>(N));
+        hdinv32.resize(static_cast<size_t>(N));
+        for (int64_t k = 0; k < N; ++k) {
+            const double d = M.diag[M.l2g[k]];
+            double v = 0.0;
+            if (d > 0.0 && std::isfinite(d)) v = 1.0 / d;
+            else hbad = 1;
+            hdinv[k] = v;
+            hdinv32[k] = static_cast<float>(v);
+        }
+        std::fill(dmap.begin(), dmap.end(), -1);
+    }
     size_t i_dmap = add(dmap.data(), sizeof(int32_t) * N);
-    size_t i_dinv = add(nullptr, sizeof(double) * N);
-    size_t i_dinv32 = add(nullptr, sizeof(float) * N);
-    size_t i_diag_bad = add(nullptr, sizeof(int));
-    size_t i_vmap = add(M.lsrc.data(), sizeof(int32_t) * M.nnz);
+    size_t i_dinv = add(from_csr ? nullptr : hdinv.data(), sizeof(double) * N);
+    size_t i_dinv32 = add(from_csr ? nullptr : hdinv32.data(), sizeof(float) * N);
+    size_t i_diag_bad = add(from_csr ? nullptr : &hbad, sizeof(int));
+    size_t i_vmap = add(vmap.data(), sizeof(int32_t) * M.nnz);
     size_t i_imap = add(imap.data(), sizeof(int32_t) * imap.size());
     size_t i_smap = add(smap.data(), sizeof(int32_t) * smap.size());
     size_t i_bl = add(nullptr, sizeof(double) * N);
@@ -780,8 +804,9 @@ int upload(ssg_system *S) {
     S->tab.nseg = S->nseg;
     SSG_CUDA_TRY(cudaMemsetAsync(S->d_scal, 0, sizeof(Scal), C->stream));
     SSG_CUDA_TRY(cudaMemsetAsync(S->d_scal_op, 0, sizeof(Scal), C->stream));
-    k_dinv<<<grid_for(N, C->num_sms), kBlock, 0, C->stream>>>(N, S->d_dmap, S->op.val, S->d_dinv, S->d_dinv32,
-                                                               S->d_diag_bad);
+    if (from_csr)
+        k_dinv<<<grid_for(N, C->num_sms), kBlock, 0, C->stream>>>(N, S->d_dmap, S->op.val, S->d_dinv, S->d_dinv32,
+                                                                   S->d_diag_bad);
     SSG_CUDA_TRY(cudaGetLastError());
     SSG_CUDA_TRY(cudaEventCreate(&S->ev0));
     SSG_CUDA_TRY(cudaEventCreate(&S->ev1));
@@ -1341,7 +1366,7 @@ int spmm_checked(ssg_system *S, int32_t k, const T *x_loc, T *y_loc) {
 int check_fv7(ssg_system *S, int nx, int ny, int nz) {
     if (S->d_growptr && S->fv7_dims[0] == nx && S->fv7_dims[1] == ny && S->fv7_dims[2] == nz) return SSG_OK;
     const HostMaps &M = S->maps;
-    if (nx < 1 || ny < 1 || nz < 1 || static_cast<int64_t>(nx) * ny * nz != M.n) {
+    if (M.lsrc.empty() || nx < 1 || ny < 1 || nz < 1 || static_cast<int64_t>(nx) * ny * nz != M.n) {
         set_error("grid size does not match the system");
         return SSG_E_INVALID;
     }
@@ -1500,6 +1525,36 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
     if (!S) return SSG_E_OOM;
     std::string err;
     int rc = build_host_maps(n, rowptr, colidx, val, part, P, S->maps, &err);
+    if (rc != SSG_OK) {
+        set_error(err);
+        delete S;
+        return rc;
+    }
+    S->ctx = ctx;
+    if (ctx) {
+        ctx->live_systems++;
+        S->pdl = ctx->pdl != 0;
+        rc = upload(S);
+        if (rc != SSG_OK) {
+            ssg_system_destroy(S);
+            return rc;
+        }
+    }
+    *sys = S;
+    return SSG_OK;
+}
+
+int ssg_partition_fe(ssg_ctx *ctx, int32_t n, int32_t ne, int32_t nv, const int32_t *elem, const double *kel,
+                     const int32_t *epart, int32_t P, ssg_system **sys) {
+    if (!sys) {
+        set_error("sys is null");
+        return SSG_E_INVALID;
+    }
+    *sys = nullptr;
+    ssg_system *S = new (std::nothrow) ssg_system();
+    if (!S) return SSG_E_OOM;
+    std::string err;
+    int rc = build_host_maps_fe(n, ne, nv, elem, kel, epart, P, S->maps, &err);
     if (rc != SSG_OK) {
         set_error(err);
         delete S;
@@ -1725,6 +1780,10 @@ int ssg_set_values(ssg_system *S, const double *val) {
         set_error("null values");
         return SSG_E_INVALID;
     }
+    if (S->maps.lsrc.empty()) {
+        set_error("a system built from elements has no input-CSR values to replace");
+        return SSG_E_INVALID;
+    }
     cudaStream_t st = S->ctx->stream;
     const int ns = S->ctx->num_sms;
     k_gather_vals<<<grid_for(S->maps.nnz, ns), kBlock, 0, st>>>(S->maps.nnz, S->d_vmap, val,
@@ -1751,6 +1810,10 @@ int ssg_pattern_grad(ssg_system *S, int32_t k, const double *lam, const double *
     if (rc != SSG_OK) return rc;
     if (k < 1 || !lam || !x || !g) {
         set_error("bad k or null vector");
+        return SSG_E_INVALID;
+    }
+    if (S->maps.lsrc.empty()) {
+        set_error("a system built from elements has no input-CSR entries");
         return SSG_E_INVALID;
     }
     k_pattern_grad<<<grid_for(S->maps.nloc, S->ctx->num_sms), kBlock, 0, S->ctx->stream>>>(

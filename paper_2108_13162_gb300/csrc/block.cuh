@@ -69,7 +69,7 @@ struct SpmmTraits<double> {
 };
 template <>
 struct SpmmTraits<float> {
-    static constexpr int kBlocksPerSM = 2;
+    static constexpr int kBlocksPerSM = 4;
 };
 
 // K contiguous values of one local entry.
@@ -118,27 +118,6 @@ __device__ __forceinline__ void store_row(float *__restrict__ p, const float (&v
     }
 }
 
-// NC consecutive sliced-ELL entries of a lane's row for all K columns: value
-// and column loads first, then the NC rows of x, then the FMAs in CSR order.
-template <int NC, int K, typename T>
-__device__ __forceinline__ void slice_chunk_k(const T *__restrict__ sv, const int32_t *__restrict__ sc,
-                                              const T *__restrict__ X, int base, int k0, T (&acc)[K]) {
-    T v[NC];
-    int c[NC];
-#pragma unroll
-    for (int e = 0; e < NC; ++e) {
-        v[e] = __ldcs(sv + base + (k0 + e) * kSliceRows);
-        c[e] = __ldcs(sc + base + (k0 + e) * kSliceRows);
-    }
-    T xv[NC][K];
-#pragma unroll
-    for (int e = 0; e < NC; ++e) load_row<K>(X + (size_t)c[e] * K, xv[e]);
-#pragma unroll
-    for (int e = 0; e < NC; ++e)
-#pragma unroll
-        for (int j = 0; j < K; ++j) acc[j] = fma(v[e], xv[e][j], acc[j]);
-}
-
 // Segment tables (host-built, see api.cu).
 struct SegTab {
     const int32_t *blk_seg;    // [product grid] segment of each block of the K-vector product
@@ -151,132 +130,249 @@ struct SegTab {
     int32_t nseg;
 };
 
+// Lane layout of the K-vector product: each lane holds VW consecutive
+// columns of one row (one 16-byte vector when K values take 16 bytes or
+// more), LPR lanes cover a row, a warp covers RPP rows of a 32-row slice per
+// pass and LPR passes cover the slice.  The x and y rows of one pass are
+// then contiguous 16-byte pieces (a coalesced request per row) and the
+// slice's value and column loads are broadcasts.
+template <typename T, int K>
+struct SpmmShape {
+    static constexpr int VW = (K * (int)sizeof(T) >= 16) ? 16 / (int)sizeof(T) : K;
+    static constexpr int LPR = K / VW;
+    static constexpr int RPP = 32 / LPR;
+};
+
+template <int VW>
+__device__ __forceinline__ void load_vec(const double *__restrict__ p, double (&v)[VW]) {
+    const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+}
+template <int VW>
+__device__ __forceinline__ void load_vec(const float *__restrict__ p, float (&v)[VW]) {
+    if constexpr (VW == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    } else {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = t.x, v[1] = t.y;
+    }
+}
+template <int VW>
+__device__ __forceinline__ void store_vec(double *__restrict__ p, const double (&v)[VW]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+template <int VW>
+__device__ __forceinline__ void store_vec(float *__restrict__ p, const float (&v)[VW]) {
+    if constexpr (VW == 4)
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+
+// NC consecutive sliced-ELL entries for the lane's LPR rows of a slice (row
+// p * RPP + rl in pass p) and its VW columns: value and column loads
+// (broadcast within a row's lanes), then the NC * LPR x pieces, then the FMAs
+// in CSR order.
+template <int NC, int LPR, int RPP, int VW, int K, typename T>
+__device__ __forceinline__ void slice_chunk_v(const T *__restrict__ sv, const int32_t *__restrict__ sc,
+                                              const T *__restrict__ X, int base, int k0, int col0,
+                                              T (&acc)[LPR][VW]) {
+    T v[NC][LPR];
+    int c[NC][LPR];
+#pragma unroll
+    for (int e = 0; e < NC; ++e)
+#pragma unroll
+        for (int p = 0; p < LPR; ++p) {
+            v[e][p] = __ldcs(sv + base + p * RPP + (k0 + e) * kSliceRows);
+            c[e][p] = __ldcs(sc + base + p * RPP + (k0 + e) * kSliceRows);
+        }
+    T xv[NC][LPR][VW];
+#pragma unroll
+    for (int e = 0; e < NC; ++e)
+#pragma unroll
+        for (int p = 0; p < LPR; ++p) load_vec<VW>(X + (size_t)c[e][p] * K + col0, xv[e][p]);
+#pragma unroll
+    for (int e = 0; e < NC; ++e)
+#pragma unroll
+        for (int p = 0; p < LPR; ++p)
+#pragma unroll
+            for (int u = 0; u < VW; ++u) acc[p][u] = fma(v[e][p], xv[e][p][u], acc[p][u]);
+}
+
 // Sub-structured product with K vectors: Y = S X, then (with DOTS) each
 // block's partial of (x_j, y_j)_w at partials[block * K + j].  The work list
 // and the summation orders (CSR order inside a row, ascending subdomain at
-// an interface node) are those of the single-vector kernel.
+// an interface node) are those of the single-vector kernel, so every column
+// is bit-identical to it.
 template <typename T, int K, bool DOTS>
 __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ X, T *__restrict__ Y,
                                           double *partials) {
+    using Sh = SpmmShape<T, K>;
+    constexpr int VW = Sh::VW, LPR = Sh::LPR, RPP = Sh::RPP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sub = lane % LPR, rl = lane / LPR, col0 = sub * VW;
     const int2 range = A.warp_range[blockIdx.x * kSpmvWarps + warp];
     const T *__restrict__ sv = slice_vals<T>(A);
     const T *__restrict__ val = row_vals<T>(A);
     const T *__restrict__ ival = copy_vals<T>(A);
-    T dot[K];
+    __shared__ T stage[kSpmvWarps][kSliceRows][K];  // copy-row products of an interface slice
+    T dot[VW];
 #pragma unroll
-    for (int j = 0; j < K; ++j) dot[j] = T(0);
+    for (int u = 0; u < VW; ++u) dot[u] = T(0);
     for (int it = range.x; it < range.y; ++it) {
         const WorkItem W = A.items[it];
         if (W.kind == kItemSlice || W.kind == kItemIfaceSlice) {
-            T acc[K];
+            const bool iface = W.kind == kItemIfaceSlice;
+            constexpr int NC = (sizeof(T) == 8 && K >= 8) ? 1 : 2;
+            T acc[LPR][VW];
 #pragma unroll
-            for (int j = 0; j < K; ++j) acc[j] = T(0);
-            const int base = W.e0 + lane;
+            for (int p = 0; p < LPR; ++p)
+#pragma unroll
+                for (int u = 0; u < VW; ++u) acc[p][u] = T(0);
+            const int base = W.e0 + rl;
             int k = 0;
-            for (; k + 2 <= W.e1; k += 2) slice_chunk_k<2, K, T>(sv, A.scol, X, base, k, acc);
-            if (k < W.e1) slice_chunk_k<1, K, T>(sv, A.scol, X, base, k, acc);
-            if (W.kind == kItemSlice) {
-                const int r = W.a + lane;
-                if (r < W.b) {
-                    store_row<K>(Y + (size_t)r * K, acc);
-                    if (DOTS) {
-                        T xr[K];
-                        load_row<K>(X + (size_t)r * K, xr);
+            for (; k + NC <= W.e1; k += NC)
+                slice_chunk_v<NC, LPR, RPP, VW, K, T>(sv, A.scol, X, base, k, col0, acc);
+            for (; k < W.e1; ++k) slice_chunk_v<1, LPR, RPP, VW, K, T>(sv, A.scol, X, base, k, col0, acc);
 #pragma unroll
-                        for (int j = 0; j < K; ++j) dot[j] = fma(xr[j], acc[j], dot[j]);
+            for (int pass = 0; pass < LPR; ++pass) {
+                const int sr = pass * RPP + rl;
+                if (!iface) {
+                    const int r = W.a + sr;
+                    if (r < W.b) {
+                        store_vec<VW>(Y + (size_t)r * K + col0, acc[pass]);
+                        if (DOTS) {
+                            T xr[VW];
+                            load_vec<VW>(X + (size_t)r * K + col0, xr);
+#pragma unroll
+                            for (int u = 0; u < VW; ++u) dot[u] = fma(xr[u], acc[pass][u], dot[u]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) stage[warp][sr][col0 + u] = acc[pass][u];
+                }
+            }
+            if (iface) {
+                __syncwarp();
+#pragma unroll
+                for (int pass = 0; pass < LPR; ++pass) {
+                    const int sr = pass * RPP + rl;
+                    const int c = W.a + sr;
+                    if (c < W.b) {
+                        const int seg = __ldg(A.sseg + c);
+                        const int l0 = seg & 0xff, m = seg >> 8;
+                        T S[VW];
+#pragma unroll
+                        for (int u = 0; u < VW; ++u) S[u] = T(0);
+                        for (int t = 0; t < m; ++t)
+#pragma unroll
+                            for (int u = 0; u < VW; ++u) S[u] += stage[warp][l0 + t][col0 + u];
+                        const int row = __ldg(A.icopy + c);
+                        store_vec<VW>(Y + (size_t)row * K + col0, S);
+                        if (DOTS) {
+                            const T w = wtab_of<T>(A, m);
+                            T xr[VW];
+                            load_vec<VW>(X + (size_t)row * K + col0, xr);
+#pragma unroll
+                            for (int u = 0; u < VW; ++u) dot[u] = fma(w * xr[u], S[u], dot[u]);
+                        }
                     }
                 }
-            } else {
-                const int c = W.a + lane;
-                const bool valid = c < W.b;
-                const int seg = valid ? __ldg(A.sseg + c) : 0;
-                const int l0 = seg & 0xff, m = seg >> 8;
-                const int mmax = __reduce_max_sync(0xffffffffu, m);
-                T S[K];
-#pragma unroll
-                for (int j = 0; j < K; ++j) S[j] = T(0);
-                for (int t = 0; t < mmax; ++t) {
-                    const int src = (l0 + t) & 31;
-#pragma unroll
-                    for (int j = 0; j < K; ++j) {
-                        const T v = __shfl_sync(0xffffffffu, acc[j], src);
-                        if (t < m) S[j] += v;
-                    }
-                }
-                if (valid) {
-                    const int row = __ldg(A.icopy + c);
-                    store_row<K>(Y + (size_t)row * K, S);
-                    if (DOTS) {
-                        const T w = wtab_of<T>(A, m);
-                        T xr[K];
-                        load_row<K>(X + (size_t)row * K, xr);
-#pragma unroll
-                        for (int j = 0; j < K; ++j) dot[j] = fma(w * xr[j], S[j], dot[j]);
-                    }
-                }
+                __syncwarp();
             }
         } else if (W.kind == kItemLongRow) {
-            T acc[K];
+            // one long row, VW columns at a time: lane-strided partial sums and
+            // the fixed warp tree of the single-vector kernel for every column
+            for (int g0 = 0; g0 < K; g0 += VW) {
+                T acc[VW];
 #pragma unroll
-            for (int j = 0; j < K; ++j) acc[j] = T(0);
-            for (int k = W.e0 + lane; k < W.e1; k += 32) {
-                const T v = val[k];
-                T xv[K];
-                load_row<K>(X + (size_t)A.col[k] * K, xv);
+                for (int u = 0; u < VW; ++u) acc[u] = T(0);
+                for (int k = W.e0 + lane; k < W.e1; k += 32) {
+                    const T v = val[k];
+                    T xv[VW];
+                    load_vec<VW>(X + (size_t)A.col[k] * K + g0, xv);
 #pragma unroll
-                for (int j = 0; j < K; ++j) acc[j] = fma(v, xv[j], acc[j]);
-            }
+                    for (int u = 0; u < VW; ++u) acc[u] = fma(v, xv[u], acc[u]);
+                }
 #pragma unroll
-            for (int j = 0; j < K; ++j) acc[j] = T(warp_sum(double(acc[j])));
-            if (lane == 0) {
-                store_row<K>(Y + (size_t)W.a * K, acc);
-                if (DOTS) {
-                    T xr[K];
-                    load_row<K>(X + (size_t)W.a * K, xr);
+                for (int u = 0; u < VW; ++u) acc[u] = T(warp_sum(double(acc[u])));  // valid in lane 0
+                if (lane == 0) {
+                    store_vec<VW>(Y + (size_t)W.a * K + g0, acc);
 #pragma unroll
-                    for (int j = 0; j < K; ++j) dot[j] = fma(xr[j], acc[j], dot[j]);
+                    for (int u = 0; u < VW; ++u) stage[warp][0][g0 + u] = acc[u];
                 }
             }
+            __syncwarp();
+            if (DOTS && rl == 0) {
+                T xr[VW];
+                load_vec<VW>(X + (size_t)W.a * K + col0, xr);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) dot[u] = fma(xr[u], stage[warp][0][col0 + u], dot[u]);
+            }
+            __syncwarp();
         } else {
-            T S[K];
+            // one interface node with long copy rows, VW columns at a time: each
+            // copy row reduced by the warp (fixed tree), copies summed in
+            // ascending s
+            for (int g0 = 0; g0 < K; g0 += VW) {
+                T S[VW];
 #pragma unroll
-            for (int j = 0; j < K; ++j) S[j] = T(0);
-            for (int c = W.c0; c < W.c1; ++c) {
-                T acc[K];
+                for (int u = 0; u < VW; ++u) S[u] = T(0);
+                for (int c = W.c0; c < W.c1; ++c) {
+                    T acc[VW];
 #pragma unroll
-                for (int j = 0; j < K; ++j) acc[j] = T(0);
-                for (int k = A.irp[c] + lane; k < A.irp[c + 1]; k += 32) {
-                    const T v = ival[k];
-                    T xv[K];
-                    load_row<K>(X + (size_t)A.icol[k] * K, xv);
+                    for (int u = 0; u < VW; ++u) acc[u] = T(0);
+                    for (int k = A.irp[c] + lane; k < A.irp[c + 1]; k += 32) {
+                        const T v = ival[k];
+                        T xv[VW];
+                        load_vec<VW>(X + (size_t)A.icol[k] * K + g0, xv);
 #pragma unroll
-                    for (int j = 0; j < K; ++j) acc[j] = fma(v, xv[j], acc[j]);
+                        for (int u = 0; u < VW; ++u) acc[u] = fma(v, xv[u], acc[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) S[u] += T(warp_sum(double(acc[u])));  // valid in lane 0
                 }
+                if (lane == 0) {
 #pragma unroll
-                for (int j = 0; j < K; ++j) S[j] += T(warp_sum(double(acc[j])));  // valid in lane 0
+                    for (int u = 0; u < VW; ++u) stage[warp][0][g0 + u] = S[u];
+                }
             }
-            if (lane == 0) {
-                const T w = wtab_of<T>(A, W.c1 - W.c0);
+            __syncwarp();
+            const T w = wtab_of<T>(A, W.c1 - W.c0);
+            if (rl == 0) {
+                T Sv[VW];
+#pragma unroll
+                for (int u = 0; u < VW; ++u) Sv[u] = stage[warp][0][col0 + u];
                 for (int c = W.c0; c < W.c1; ++c) {
                     const int row = A.icopy[c];
-                    store_row<K>(Y + (size_t)row * K, S);
+                    store_vec<VW>(Y + (size_t)row * K + col0, Sv);
                     if (DOTS) {
-                        T xr[K];
-                        load_row<K>(X + (size_t)row * K, xr);
+                        T xr[VW];
+                        load_vec<VW>(X + (size_t)row * K + col0, xr);
 #pragma unroll
-                        for (int j = 0; j < K; ++j) dot[j] = fma(w * xr[j], S[j], dot[j]);
+                        for (int u = 0; u < VW; ++u) dot[u] = fma(w * xr[u], Sv[u], dot[u]);
                     }
                 }
             }
+            __syncwarp();
         }
     }
     if (DOTS) {
         __shared__ double wsum[kSpmvWarps][K];
+        // lanes holding the same columns (equal lane mod LPR) are summed by a fixed xor tree
+        double dv[VW];
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const double wv = warp_sum(double(dot[j]));
-            if (lane == 0) wsum[warp][j] = wv;
+        for (int u = 0; u < VW; ++u) {
+            dv[u] = double(dot[u]);
+#pragma unroll
+            for (int o = 16; o >= LPR; o >>= 1) dv[u] += __shfl_xor_sync(0xffffffffu, dv[u], o);
+        }
+        if (rl == 0) {
+#pragma unroll
+            for (int u = 0; u < VW; ++u) wsum[warp][col0 + u] = dv[u];
         }
         __syncthreads();
         if (threadIdx.x < K) {
@@ -307,14 +403,27 @@ __global__ void __launch_bounds__(kSpmvThreads, SpmmTraits<T>::kBlocksPerSM)
 
 // Sums of each column's partials over blocks [b0, b1) of the previous kernel
 // (K per block), the same fixed order in every block: warp w takes the
-// columns j = w mod 8, lane-strided over the blocks, then a fixed shuffle
-// tree.  Result in tot[K] (shared), valid after the call in every thread.
+// columns j = w mod 8; lane l adds the blocks b0 + l + 32 i into accumulator
+// i mod 8 (eight loads in flight instead of a chain of dependent ones), the
+// accumulators are combined as a fixed tree, then the lanes by a fixed
+// shuffle tree.  Result in tot[K] (shared), valid after the call in every
+// thread.
 template <int K>
 __device__ __forceinline__ void seg_sum_cols(const double *partials, int b0, int b1, double *tot) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int j = warp; j < K; j += kBlock / 32) {
-        double v = 0.0;
-        for (int g = b0 + lane; g < b1; g += 32) v += __ldcg(partials + (size_t)g * K + j);
+        double a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = 0.0;
+        int g = b0 + lane;
+        for (; g + 7 * 32 < b1; g += 8 * 32) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] += __ldcg(partials + (size_t)(g + 32 * u) * K + j);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (g + 32 * u < b1) a[u] += __ldcg(partials + (size_t)(g + 32 * u) * K + j);
+        double v = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
         v = warp_sum(v);
         if (lane == 0) tot[j] = v;
     }

@@ -18,12 +18,17 @@ struct HostMaps {
     int64_t ncopies = 0;
     std::vector<int32_t> off, nint, l2g, mult, lrowptr, lcol, gamma, iptr, icopy, own;
     std::vector<double> lval;
-    std::vector<int32_t> lsrc;  // entry of the input CSR each local entry copies (ownership is one-to-one)
+    std::vector<int32_t> lsrc;  // entry of the input CSR each local entry copies (ownership is one-to-one);
+                                // empty for element sub-structures (local entries are sums)
+    std::vector<double> diag;   // element sub-structures: assembled diagonal per node
 };
 
 // Returns SSG_OK or SSG_E_INVALID / SSG_E_OOM with a message in *err.
 int build_host_maps(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
                     const int32_t *part, int32_t P, HostMaps &out, std::string *err);
+
+int build_host_maps_fe(int32_t n, int32_t ne, int32_t nv, const int32_t *elem, const double *kel,
+                       const int32_t *epart, int32_t P, HostMaps &out, std::string *err);
 
 void set_error(const std::string &msg);
 

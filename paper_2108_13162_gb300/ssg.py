@@ -41,6 +41,7 @@ EXPORTS = (
     "ssg_set_pdl",
     "ssg_destroy",
     "ssg_partition",
+    "ssg_partition_fe",
     "ssg_partition_batch",
     "ssg_solve_batch",
     "ssg_get_sizes",
@@ -132,6 +133,7 @@ def lib():
         L.ssg_destroy.argtypes = [vp]
         L.ssg_partition.argtypes = [vp, i32, vp, vp, vp, vp, i32, C.POINTER(vp)]
         L.ssg_partition_batch.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]
+        L.ssg_partition_fe.argtypes = [vp, i32, i32, i32, vp, vp, vp, i32, C.POINTER(vp)]
         L.ssg_solve_batch.argtypes = [vp, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
         L.ssg_get_sizes.argtypes = [vp, C.POINTER(ssg_sizes)]
         L.ssg_copy_maps.argtypes = [vp] * 12
@@ -233,6 +235,19 @@ def ssg_partition(ctx, n, rowptr, colidx, val, part, P):
         lib().ssg_partition(ctx, n, _ptr(rowptr), _ptr(colidx), _ptr(val), _ptr(part), P, C.byref(h)),
         "ssg_partition",
     )
+    return h
+
+
+def ssg_partition_fe(ctx, n, elem, kel, epart, P):
+    elem = np.ascontiguousarray(elem, np.int32)
+    kel = np.ascontiguousarray(kel, np.float64)
+    epart = np.ascontiguousarray(epart, np.int32)
+    ne, nv = elem.shape
+    if kel.shape != (ne, nv, nv) or epart.size != ne:
+        raise ValueError("element arrays have inconsistent sizes")
+    h = C.c_void_p()
+    _check(lib().ssg_partition_fe(ctx, n, ne, nv, _ptr(elem), _ptr(kel), _ptr(epart), P, C.byref(h)),
+           "ssg_partition_fe")
     return h
 
 
@@ -487,13 +502,21 @@ class Batch:
 
 
 class System:
-    """A partitioned system (ssg_partition) with device-side operators."""
+    """A partitioned system (ssg_partition, or ssg_partition_fe through
+    ``from_elements``) with device-side operators."""
 
-    def __init__(self, ctx: Context | None, A, part, P):
+    def __init__(self, ctx: Context | None, A, part, P, _handle=None):
         self.ctx = ctx
-        self.h = ssg_partition(None if ctx is None else ctx.h, A.n, A.rowptr, A.colidx, A.val, part, P)
+        self.h = _handle if _handle is not None else ssg_partition(None if ctx is None else ctx.h, A.n, A.rowptr,
+                                                                    A.colidx, A.val, part, P)
         s = ssg_get_sizes(self.h)
         self.sizes = Sizes(s.n, s.P, s.nnz, s.nloc, s.ngamma, s.max_mult, s.ncopies)
+
+    @classmethod
+    def from_elements(cls, ctx: Context | None, n, elem, kel, epart, P):
+        """Sub-structures from finite elements: elem (ne, nv) node ids (-1 for
+        an eliminated node), kel (ne, nv, nv) element matrices, epart (ne)."""
+        return cls(ctx, None, None, P, _handle=ssg_partition_fe(None if ctx is None else ctx.h, n, elem, kel, epart, P))
 
     def maps(self):
         return ssg_copy_maps(self.h)

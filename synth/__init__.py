@@ -19,6 +19,9 @@ from .problems import (  # noqa: F401
     BatchProblem,
     batch_problem,
     fe2d_p1_jittered,
+    fe2d_p1_elements,
+    fe_assemble,
+    fe_element_problem,
     random_spd,
     box_partition_2d,
     box_partition_3d,

@@ -223,7 +223,32 @@ def batch_problem(nsys: int = 512, side_lo: int = 32, side_hi: int = 512, seed: 
 
 
 def fe2d_p1_jittered(N: int, rng: np.random.Generator, jitter: float = 0.3):
-    """P1 finite-element Laplacian on a jittered N x N free-node mesh.
+    """Assembled P1 finite-element Laplacian of ``fe2d_p1_elements`` (same
+    random stream): returns (CSR, coords [n,2], n_inverted_triangles)."""
+    ids, Ke, coords, n_inv = fe2d_p1_elements(N, rng, jitter)
+    return fe_assemble(N * N, ids, Ke), coords, n_inv
+
+
+def fe_assemble(n: int, ids: np.ndarray, Ke: np.ndarray) -> CSR:
+    """Global matrix sum_e K_e over the free nodes (ids -1 dropped), made
+    exactly symmetric from its upper triangle."""
+    import scipy.sparse as sp
+
+    nv = ids.shape[1]
+    I = np.repeat(ids, nv, axis=1).reshape(-1, nv, nv)
+    J = np.tile(ids, (1, nv)).reshape(-1, nv, nv)
+    keep = (I >= 0) & (J >= 0)
+    A = sp.coo_matrix((Ke[keep], (I[keep], J[keep])), shape=(n, n)).tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    U = sp.triu(A, 0, format="csr")
+    S = (U + sp.triu(U, 1, format="csr").T).tocsr()
+    S.sort_indices()
+    return CSR(n, S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(np.float64))
+
+
+def fe2d_p1_elements(N: int, rng: np.random.Generator, jitter: float = 0.3):
+    """P1 finite-element Laplacian on a jittered N x N free-node mesh, by elements.
 
     The N x N free nodes sit inside a ring of fixed (unjittered) Dirichlet
     nodes, (N+2)^2 nodes in all, spacing h = 1/(N+1).  Every free node is moved
@@ -234,7 +259,9 @@ def fe2d_p1_jittered(N: int, rng: np.random.Generator, jitter: float = 0.3):
     semi-definite contribution.  Free node (ix, iy), 1 <= ix, iy <= N, has id
     (ix-1) + N*(iy-1).
 
-    Returns (CSR, coords [n,2], n_inverted_triangles).
+    Returns (ids [ne, 3] free node of each vertex or -1 for a Dirichlet
+    node, Ke [ne, 3, 3] element matrices, coords [n, 2] of the free nodes,
+    n_inverted_triangles).
     """
     h = 1.0 / (N + 1)
     M = N + 2
@@ -276,21 +303,8 @@ def fe2d_p1_jittered(N: int, rng: np.random.Generator, jitter: float = 0.3):
     n_inv = int(np.count_nonzero(det <= 0.0))
     scale = 1.0 / (2.0 * np.abs(det))
     Ke = (bvec[:, :, None] * bvec[:, None, :] + cvec[:, :, None] * cvec[:, None, :]) * scale[:, None, None]
-    I = np.repeat(ids, 3, axis=1).reshape(-1, 3, 3)
-    J = np.tile(ids, (1, 3)).reshape(-1, 3, 3)
-    keep = (I >= 0) & (J >= 0)
-    import scipy.sparse as sp
-
-    n = N * N
-    A = sp.coo_matrix((Ke[keep], (I[keep], J[keep])), shape=(n, n)).tocsr()
-    A.sum_duplicates()
-    A.sort_indices()
-    U = sp.triu(A, 0, format="csr")
-    S = (U + sp.triu(U, 1, format="csr").T).tocsr()
-    S.sort_indices()
     coords = np.stack([X[1:-1, 1:-1].ravel(), Y[1:-1, 1:-1].ravel()], axis=1)
-    csr = CSR(n, S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(np.float64))
-    return csr, coords, n_inv
+    return ids.astype(np.int32), Ke, coords, n_inv
 
 
 def random_spd(n: int, avg_deg: float, rng: np.random.Generator, shift: float = 0.5) -> CSR:
@@ -337,6 +351,27 @@ def box_partition_3d(nx: int, ny: int, nz: int, px: int, py: int, pz: int) -> np
     by = (iy * py) // ny
     bz = (iz * pz) // nz
     return (bx + px * (by + py * bz)).ravel().astype(np.int32)
+
+
+def fe_element_problem(N: int, levels: int, seed: int = CONFIG_SEED_BASE + 3):
+    """Workload 3's mesh by elements: the jittered P1 mesh of side N, its
+    element matrices, and an element partition by recursive coordinate
+    bisection of the element centroids (free vertices only; an element with
+    no free vertex goes to subdomain 0).  Stream order: jitter, diagonals,
+    x*, RCB ratios.  Returns (ids, Ke, epart, P, A, xstar, b)."""
+    rng = np.random.default_rng(seed)
+    ids, Ke, coords, _ = fe2d_p1_elements(N, rng)
+    n = N * N
+    A = fe_assemble(n, ids, Ke)
+    xs = rng.uniform(-1.0, 1.0, size=n)
+    b = A.to_scipy() @ xs
+    free = ids >= 0
+    cnt = np.maximum(free.sum(axis=1), 1)
+    cx = np.where(free, coords[np.maximum(ids, 0), 0], 0.0).sum(axis=1) / cnt
+    cy = np.where(free, coords[np.maximum(ids, 0), 1], 0.0).sum(axis=1) / cnt
+    epart = rcb_partition(np.stack([cx, cy], axis=1), levels, rng)
+    epart[free.sum(axis=1) == 0] = 0
+    return ids, Ke, epart, 2**levels, A, xs, b
 
 
 def rcb_partition(coords: np.ndarray, levels: int, rng: np.random.Generator, lo=0.3, hi=0.7) -> np.ndarray:

@@ -133,3 +133,42 @@ def test_error_strings():
     for code in range(7):
         assert ssg.ssg_error_string(code)
     assert "breakdown" in ssg.ssg_error_string(ssg.SSG_E_BREAKDOWN).lower()
+
+
+@pytest.mark.parametrize("N,levels", [(14, 3), (33, 4), (8, 0)])
+def test_element_maps_bit_exact_vs_oracle(N, levels):
+    """Sub-structures from finite elements (ssg_partition_fe vs
+    or_partition_fe): every map and every summed local value identical."""
+    from synth import fe_element_problem
+
+    ids, Ke, epart, P, A, xs, b = fe_element_problem(N, levels)
+    sys_ = ssg.ssg_partition_fe(None, A.n, ids, Ke, epart, P)
+    try:
+        got = ssg.ssg_copy_maps(sys_)
+        sz = ssg.ssg_get_sizes(sys_)
+    finally:
+        ssg.ssg_system_destroy(sys_)
+    ref = oracle.Partition.from_elements(A.n, ids, Ke, epart, P).maps
+    assert (sz.n, sz.P, sz.nnz, sz.nloc, sz.ngamma, sz.ncopies) == (
+        ref.n, ref.P, ref.nnz, ref.nloc, ref.ngamma, ref.ncopies)
+    for k in ("off", "nint", "l2g", "mult", "lrowptr", "lcol", "gamma", "iptr", "icopy", "own"):
+        assert np.array_equal(got[k], getattr(ref, k)), k
+    assert np.array_equal(got["lval"].view(np.int64), ref.lval.view(np.int64))
+
+
+def test_element_input_rejected():
+    from synth import fe_element_problem
+
+    ids, Ke, epart, P, A, xs, b = fe_element_problem(6, 1)
+    bad = epart.copy()
+    bad[1] = -1
+    with pytest.raises(ssg.SSGError):
+        ssg.ssg_partition_fe(None, A.n, ids, Ke, bad, P)
+    K2 = Ke.copy()
+    K2[0, 1, 2] += 1.0
+    with pytest.raises(ssg.SSGError):
+        ssg.ssg_partition_fe(None, A.n, ids, K2, epart, P)
+    ids2 = ids.copy()
+    ids2[ids2 == 3] = 4
+    with pytest.raises(ssg.SSGError):
+        ssg.ssg_partition_fe(None, A.n, ids2, Ke, epart, P)

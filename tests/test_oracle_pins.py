@@ -368,7 +368,8 @@ MUTATIONS = {
     "no_assembly_sum": ("double S = 0.0;\n        for (int32_t c = h->iptr[g]; c < h->iptr[g + 1]; ++c) S += yl[h->icopy[c]];",
                         "double S = 0.0;\n        for (int32_t c = h->iptr[g]; c < h->iptr[g + 1]; ++c) S = yl[h->icopy[c]];"),
     # unweighted dot (w = 1 on every copy)
-    "unit_weights": ("h->w[k] = 1.0 / (double)h->mult[h->l2g[k]];", "h->w[k] = 1.0;"),
+    "unit_weights": ("    if (!h->w) { free(memloc); goto oom; }\n    for (int64_t k = 0; k < h->nloc; ++k) h->w[k] = 1.0 / (double)h->mult[h->l2g[k]];",
+                     "    if (!h->w) { free(memloc); goto oom; }\n    for (int64_t k = 0; k < h->nloc; ++k) h->w[k] = 1.0;"),
     # off-diagonal entries owned by the higher subdomain, interface entries counted twice
     "double_owner": ("return part[i] < part[j] ? part[i] : part[j];", "return part[i];"),
     # wrong sign in the residual update
