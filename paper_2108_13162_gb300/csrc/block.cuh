@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_cond(const ScalB *segs, int nseg
 // segment (a column with (p, S p)_w <= 0 stops with a breakdown),
 // r_j <- r_j - alpha_j q_j over the chunk and its partials of (r_j, r_j)_w.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_update_rB(const double *__restrict__ q, double *__restrict__ r,
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_rB(const double *__restrict__ q, double *__restrict__ r,
                                                       const uint8_t *__restrict__ mult,
                                                       const double *__restrict__ wtab,
                                                       const uint8_t *__restrict__ gflag, const double *part_pq,
@@ -520,23 +520,33 @@ __global__ void __launch_bounds__(kBlock) k_update_rB(const double *__restrict__
     double acc[2] = {0.0, 0.0};
     double2 *__restrict__ r2 = reinterpret_cast<double2 *>(r);
     const double2 *__restrict__ q2 = reinterpret_cast<const double2 *>(q);
-    const int64_t i1 = (int64_t)ch.z * K / 2;
-    for (int64_t i = (int64_t)ch.y * K / 2 + threadIdx.x; i < i1; i += kBlock) {
-        double2 rv = r2[i];
-        const double2 qv = __ldcs(q2 + i);
-        rv.x = fma(-a0, qv.x, rv.x);
-        rv.y = fma(-a1, qv.y, rv.y);
-        r2[i] = rv;
-        const int64_t e = (2 * i) / K;  // local entry of both values
-        if (__ldg(gflag + (e >> 6)) == 0) {
-            acc[0] = fma(rv.x, rv.x, acc[0]);
-            acc[1] = fma(rv.y, rv.y, acc[1]);
-        } else {
-            const double w = __ldg(wtab + mult[e]);
-            acc[0] = fma(w * rv.x, rv.x, acc[0]);
-            acc[1] = fma(w * rv.y, rv.y, acc[1]);
-        }
-    }
+    struct Ld {
+        double2 r, q;
+        uint8_t g;
+    };
+    stream_loop<4>(
+        (int64_t)ch.y * K / 2 + threadIdx.x, (int64_t)ch.z * K / 2, kBlock,
+        [&](int64_t i) {
+            Ld l;
+            l.r = r2[i];
+            l.q = __ldcs(q2 + i);
+            l.g = __ldg(gflag + (((2 * i) / K) >> 6));
+            return l;
+        },
+        [&](int64_t i, Ld l) {
+            double2 rv = l.r;
+            rv.x = fma(-a0, l.q.x, rv.x);
+            rv.y = fma(-a1, l.q.y, rv.y);
+            r2[i] = rv;
+            if (l.g == 0) {
+                acc[0] = fma(rv.x, rv.x, acc[0]);
+                acc[1] = fma(rv.y, rv.y, acc[1]);
+            } else {
+                const double w = __ldg(wtab + mult[(2 * i) / K]);  // local entry of both values
+                acc[0] = fma(w * rv.x, rv.x, acc[0]);
+                acc[1] = fma(w * rv.y, rv.y, acc[1]);
+            }
+        });
     block_cols_sum<K, 2>(acc, part_rr + (size_t)blockIdx.x * K);
 }
 
@@ -545,7 +555,7 @@ __global__ void __launch_bounds__(kBlock) k_update_rB(const double *__restrict__
 // beta_j p_j (alpha = beta = 0 for frozen columns); the segment's first chunk
 // records each column's iteration and stopping decision.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_update_xpB(double *__restrict__ x, double *__restrict__ p,
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_xpB(double *__restrict__ x, double *__restrict__ p,
                                                        const double *__restrict__ r, const double *part_rr,
                                                        SegTab tab, ScalB *segs) {
     __shared__ double tot[K];
@@ -573,16 +583,25 @@ __global__ void __launch_bounds__(kBlock) k_update_xpB(double *__restrict__ x, d
     double2 *x2 = reinterpret_cast<double2 *>(x);
     double2 *p2 = reinterpret_cast<double2 *>(p);
     const double2 *r2 = reinterpret_cast<const double2 *>(r);
-    const int64_t i1 = (int64_t)ch.z * K / 2;
-    for (int64_t i = (int64_t)ch.y * K / 2 + threadIdx.x; i < i1; i += kBlock) {
-        const double2 pv = p2[i];
-        double2 xv = __ldcs(x2 + i);
-        const double2 rv = r2[i];
-        xv.x = fma(a0, pv.x, xv.x);
-        xv.y = fma(a1, pv.y, xv.y);
-        __stcs(x2 + i, xv);
-        p2[i] = make_double2(fma(b0, pv.x, rv.x), fma(b1, pv.y, rv.y));
-    }
+    struct Ld {
+        double2 p, x, r;
+    };
+    stream_loop<4>(
+        (int64_t)ch.y * K / 2 + threadIdx.x, (int64_t)ch.z * K / 2, kBlock,
+        [&](int64_t i) {
+            Ld l;
+            l.p = p2[i];
+            l.x = __ldcs(x2 + i);
+            l.r = r2[i];
+            return l;
+        },
+        [&](int64_t i, Ld l) {
+            double2 xv = l.x;
+            xv.x = fma(a0, l.p.x, xv.x);
+            xv.y = fma(a1, l.p.y, xv.y);
+            __stcs(x2 + i, xv);
+            p2[i] = make_double2(fma(b0, l.p.x, l.r.x), fma(b1, l.p.y, l.r.y));
+        });
     if (first && threadIdx.x == 0) {
         uint32_t na = ab;
         for (int j = 0; j < K; ++j) {
@@ -770,7 +789,7 @@ __global__ void __launch_bounds__(kBlock) k_inner_finB(const double *part, SegTa
 // (alpha formed in FP64 from the FP64 sums of the partials, then rounded to
 // FP32 once).
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_update_r32B(const float *__restrict__ q, float *__restrict__ r,
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32B(const float *__restrict__ q, float *__restrict__ r,
                                                         const uint8_t *__restrict__ mult,
                                                         const float *__restrict__ wtab,
                                                         const uint8_t *__restrict__ gflag128, const double *part_pq,
@@ -820,36 +839,45 @@ __global__ void __launch_bounds__(kBlock) k_update_r32B(const float *__restrict_
     float acc[VW];
 #pragma unroll
     for (int u = 0; u < VW; ++u) acc[u] = 0.f;
-    const int64_t i1 = (int64_t)ch.z * K / VW;
-    for (int64_t i = (int64_t)ch.y * K / VW + threadIdx.x; i < i1; i += kBlock) {
-        float rv[VW], qv[VW];
-        if constexpr (VW == 4) {
-            const float4 t = reinterpret_cast<const float4 *>(r)[i];
-            const float4 u = __ldcs(reinterpret_cast<const float4 *>(q) + i);
-            rv[0] = t.x, rv[1] = t.y, rv[2] = t.z, rv[3] = t.w;
-            qv[0] = u.x, qv[1] = u.y, qv[2] = u.z, qv[3] = u.w;
-        } else {
-            const float2 t = reinterpret_cast<const float2 *>(r)[i];
-            const float2 u = __ldcs(reinterpret_cast<const float2 *>(q) + i);
-            rv[0] = t.x, rv[1] = t.y;
-            qv[0] = u.x, qv[1] = u.y;
-        }
+    struct Ld {
+        float r[VW], q[VW];
+        uint8_t g;
+    };
+    stream_loop<4>(
+        (int64_t)ch.y * K / VW + threadIdx.x, (int64_t)ch.z * K / VW, kBlock,
+        [&](int64_t i) {
+            Ld l;
+            if constexpr (VW == 4) {
+                const float4 t = reinterpret_cast<const float4 *>(r)[i];
+                const float4 u = __ldcs(reinterpret_cast<const float4 *>(q) + i);
+                l.r[0] = t.x, l.r[1] = t.y, l.r[2] = t.z, l.r[3] = t.w;
+                l.q[0] = u.x, l.q[1] = u.y, l.q[2] = u.z, l.q[3] = u.w;
+            } else {
+                const float2 t = reinterpret_cast<const float2 *>(r)[i];
+                const float2 u = __ldcs(reinterpret_cast<const float2 *>(q) + i);
+                l.r[0] = t.x, l.r[1] = t.y;
+                l.q[0] = u.x, l.q[1] = u.y;
+            }
+            l.g = __ldg(gflag128 + (((VW * i) / K) >> 7));
+            return l;
+        },
+        [&](int64_t i, Ld l) {
+            float rv[VW];
 #pragma unroll
-        for (int u = 0; u < VW; ++u) rv[u] = fmaf(-a[u], qv[u], rv[u]);
-        if constexpr (VW == 4)
-            reinterpret_cast<float4 *>(r)[i] = make_float4(rv[0], rv[1], rv[2], rv[3]);
-        else
-            reinterpret_cast<float2 *>(r)[i] = make_float2(rv[0], rv[1]);
-        const int64_t e = (VW * i) / K;
-        if (__ldg(gflag128 + (e >> 7)) == 0) {
+            for (int u = 0; u < VW; ++u) rv[u] = fmaf(-a[u], l.q[u], l.r[u]);
+            if constexpr (VW == 4)
+                reinterpret_cast<float4 *>(r)[i] = make_float4(rv[0], rv[1], rv[2], rv[3]);
+            else
+                reinterpret_cast<float2 *>(r)[i] = make_float2(rv[0], rv[1]);
+            if (l.g == 0) {
 #pragma unroll
-            for (int u = 0; u < VW; ++u) acc[u] = fmaf(rv[u], rv[u], acc[u]);
-        } else {
-            const float w = __ldg(wtab + mult[e]);
+                for (int u = 0; u < VW; ++u) acc[u] = fmaf(rv[u], rv[u], acc[u]);
+            } else {
+                const float w = __ldg(wtab + mult[(VW * i) / K]);
 #pragma unroll
-            for (int u = 0; u < VW; ++u) acc[u] = fmaf(w * rv[u], rv[u], acc[u]);
-        }
-    }
+                for (int u = 0; u < VW; ++u) acc[u] = fmaf(w * rv[u], rv[u], acc[u]);
+            }
+        });
     block_cols_sum<K, VW>(acc, part_rr + (size_t)blockIdx.x * K);
 }
 
@@ -859,7 +887,7 @@ __global__ void __launch_bounds__(kBlock) k_update_r32B(const float *__restrict_
 // (sqrt(rho_j) <= tau_j sqrt(rho0_j), or its inner iterations summed reach
 // max_iter).
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_update_dp32B(float *__restrict__ d, float *__restrict__ p,
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32B(float *__restrict__ d, float *__restrict__ p,
                                                          const float *__restrict__ r, const double *part_rr,
                                                          SegTab tab, ScalB *si, ScalB *so) {
     constexpr int VW = K >= 4 ? 4 : 2;
@@ -889,37 +917,45 @@ __global__ void __launch_bounds__(kBlock) k_update_dp32B(float *__restrict__ d, 
         a[u] = alpha_s[j0 + u];
         bt[u] = beta_s[j0 + u];
     }
-    const int64_t i1 = (int64_t)ch.z * K / VW;
-    for (int64_t i = (int64_t)ch.y * K / VW + threadIdx.x; i < i1; i += kBlock) {
-        float pv[VW], dv[VW], rv[VW];
-        if constexpr (VW == 4) {
-            const float4 t = reinterpret_cast<const float4 *>(p)[i];
-            const float4 u = reinterpret_cast<const float4 *>(d)[i];
-            const float4 w = reinterpret_cast<const float4 *>(r)[i];
-            pv[0] = t.x, pv[1] = t.y, pv[2] = t.z, pv[3] = t.w;
-            dv[0] = u.x, dv[1] = u.y, dv[2] = u.z, dv[3] = u.w;
-            rv[0] = w.x, rv[1] = w.y, rv[2] = w.z, rv[3] = w.w;
-        } else {
-            const float2 t = reinterpret_cast<const float2 *>(p)[i];
-            const float2 u = reinterpret_cast<const float2 *>(d)[i];
-            const float2 w = reinterpret_cast<const float2 *>(r)[i];
-            pv[0] = t.x, pv[1] = t.y;
-            dv[0] = u.x, dv[1] = u.y;
-            rv[0] = w.x, rv[1] = w.y;
-        }
+    struct Ld {
+        float p[VW], d[VW], r[VW];
+    };
+    stream_loop<2>(
+        (int64_t)ch.y * K / VW + threadIdx.x, (int64_t)ch.z * K / VW, kBlock,
+        [&](int64_t i) {
+            Ld l;
+            if constexpr (VW == 4) {
+                const float4 t = reinterpret_cast<const float4 *>(p)[i];
+                const float4 u = reinterpret_cast<const float4 *>(d)[i];
+                const float4 w = reinterpret_cast<const float4 *>(r)[i];
+                l.p[0] = t.x, l.p[1] = t.y, l.p[2] = t.z, l.p[3] = t.w;
+                l.d[0] = u.x, l.d[1] = u.y, l.d[2] = u.z, l.d[3] = u.w;
+                l.r[0] = w.x, l.r[1] = w.y, l.r[2] = w.z, l.r[3] = w.w;
+            } else {
+                const float2 t = reinterpret_cast<const float2 *>(p)[i];
+                const float2 u = reinterpret_cast<const float2 *>(d)[i];
+                const float2 w = reinterpret_cast<const float2 *>(r)[i];
+                l.p[0] = t.x, l.p[1] = t.y;
+                l.d[0] = u.x, l.d[1] = u.y;
+                l.r[0] = w.x, l.r[1] = w.y;
+            }
+            return l;
+        },
+        [&](int64_t i, Ld l) {
+            float pv[VW], dv[VW];
 #pragma unroll
-        for (int u = 0; u < VW; ++u) {
-            dv[u] = fmaf(a[u], pv[u], dv[u]);
-            pv[u] = fmaf(bt[u], pv[u], rv[u]);
-        }
-        if constexpr (VW == 4) {
-            reinterpret_cast<float4 *>(d)[i] = make_float4(dv[0], dv[1], dv[2], dv[3]);
-            reinterpret_cast<float4 *>(p)[i] = make_float4(pv[0], pv[1], pv[2], pv[3]);
-        } else {
-            reinterpret_cast<float2 *>(d)[i] = make_float2(dv[0], dv[1]);
-            reinterpret_cast<float2 *>(p)[i] = make_float2(pv[0], pv[1]);
-        }
-    }
+            for (int u = 0; u < VW; ++u) {
+                dv[u] = fmaf(a[u], l.p[u], l.d[u]);
+                pv[u] = fmaf(bt[u], l.p[u], l.r[u]);
+            }
+            if constexpr (VW == 4) {
+                reinterpret_cast<float4 *>(d)[i] = make_float4(dv[0], dv[1], dv[2], dv[3]);
+                reinterpret_cast<float4 *>(p)[i] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+            } else {
+                reinterpret_cast<float2 *>(d)[i] = make_float2(dv[0], dv[1]);
+                reinterpret_cast<float2 *>(p)[i] = make_float2(pv[0], pv[1]);
+            }
+        });
     if (first && threadIdx.x == 0) {
         ScalB *o = so + ch.x;
         uint32_t na = ab;

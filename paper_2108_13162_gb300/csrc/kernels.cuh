@@ -37,8 +37,8 @@ struct SpmvTraits<double> {
 };
 template <>
 struct SpmvTraits<float> {
-    static constexpr int kBlocksPerSM = 4;
-    static constexpr bool kPrefetch = true;
+    static constexpr int kBlocksPerSM = 5;  // measured: 32.0 us vs 32.8 (4 blocks, with or without prefetch)
+    static constexpr bool kPrefetch = false;
 };
 constexpr int kVecBlocksPerSM = 4;
 constexpr int kHostChunk = 32;    // iterations per host-loop chunk (SSG_DRIVER_HOST)
@@ -217,6 +217,24 @@ __device__ __forceinline__ double all_sum_partials(const double *partials, int G
     if (threadIdx.x == 0) bc = t;
     __syncthreads();
     return bc;
+}
+
+// Streams i = i0, i0 + step, ... < i1 through load(i) and apply(i, loaded),
+// U indices at a time: the U loads are issued before the first apply, so a
+// thread keeps U requests in flight instead of one, and the applies still run
+// in ascending i (per-thread sums keep their order and bits).
+template <int U, typename L, typename A>
+__device__ __forceinline__ void stream_loop(int64_t i0, int64_t i1, int64_t step, L load, A apply) {
+    using R = decltype(load(i0));
+    int64_t i = i0;
+    for (; i + (U - 1) * step < i1; i += U * step) {
+        R v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = load(i + u * step);
+#pragma unroll
+        for (int u = 0; u < U; ++u) apply(i + u * step, v[u]);
+    }
+    for (; i < i1; i += step) apply(i, load(i));
 }
 
 __device__ __forceinline__ void stop_loop(Scal *s, cudaGraphConditionalHandle h, int use_cond) {
@@ -472,7 +490,7 @@ __device__ __forceinline__ double wsq(double r, unsigned int m, const double *__
 // preconditioner (PC, dinv = 1 / diag(S) per local entry) the block also
 // forms its share of (r, z)_w, z = dinv r, into part_rz.
 template <bool PC>
-__global__ void __launch_bounds__(kBlock) k_update_r(int64_t N, double *__restrict__ r, const double *__restrict__ q,
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r(int64_t N, double *__restrict__ r, const double *__restrict__ q,
                                                      const uint8_t *__restrict__ mult, const double *__restrict__ wtab,
                                                      const uint8_t *__restrict__ gflag, const double *part_pq,
                                                      int G1, double *part_rr, Scal *s, cudaGraphConditionalHandle h,
@@ -502,35 +520,46 @@ __global__ void __launch_bounds__(kBlock) k_update_r(int64_t N, double *__restri
     const double2 *__restrict__ q2 = reinterpret_cast<const double2 *>(q);
     const uchar2 *__restrict__ m2 = reinterpret_cast<const uchar2 *>(mult);
     const double2 *__restrict__ d2 = reinterpret_cast<const double2 *>(dinv);
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N2; i += stride) {
-        double2 rv = r2[i];
-        const double2 qv = __ldcs(q2 + i);
-        rv.x = fma(-alpha, qv.x, rv.x);
-        rv.y = fma(-alpha, qv.y, rv.y);
-        r2[i] = rv;
-        // a warp covers the 64 entries of group i >> 5; groups without an
-        // interface copy have weight 1 everywhere and skip the weight lookup
-        // (1.0 * r == r, so both forms give the same bits)
-        if (__ldg(gflag + (i >> 5)) == 0) {
-            acc = fma(rv.x, rv.x, acc);
-            acc = fma(rv.y, rv.y, acc);
-            if (PC) {
-                const double2 dv = __ldg(d2 + i);
-                acz = fma(rv.x, rv.x * dv.x, acz);
-                acz = fma(rv.y, rv.y * dv.y, acz);
+    struct Ld {
+        double2 r, q, d;
+        uint8_t g;
+    };
+    stream_loop<PC ? 2 : 4>(
+        (int64_t)blockIdx.x * kBlock + threadIdx.x, N2, stride,
+        [&](int64_t i) {
+            Ld l;
+            l.r = r2[i];
+            l.q = __ldcs(q2 + i);
+            l.g = __ldg(gflag + (i >> 5));
+            if (PC) l.d = __ldg(d2 + i);
+            return l;
+        },
+        [&](int64_t i, Ld l) {
+            double2 rv = l.r;
+            rv.x = fma(-alpha, l.q.x, rv.x);
+            rv.y = fma(-alpha, l.q.y, rv.y);
+            r2[i] = rv;
+            // a warp covers the 64 entries of group i >> 5; groups without an
+            // interface copy have weight 1 everywhere and skip the weight lookup
+            // (1.0 * r == r, so both forms give the same bits)
+            if (l.g == 0) {
+                acc = fma(rv.x, rv.x, acc);
+                acc = fma(rv.y, rv.y, acc);
+                if (PC) {
+                    acz = fma(rv.x, rv.x * l.d.x, acz);
+                    acz = fma(rv.y, rv.y * l.d.y, acz);
+                }
+            } else {
+                const uchar2 mv = m2[i];
+                const double wx = __ldg(wtab + mv.x) * rv.x, wy = __ldg(wtab + mv.y) * rv.y;
+                acc = fma(wx, rv.x, acc);
+                acc = fma(wy, rv.y, acc);
+                if (PC) {
+                    acz = fma(wx, rv.x * l.d.x, acz);
+                    acz = fma(wy, rv.y * l.d.y, acz);
+                }
             }
-        } else {
-            const uchar2 mv = m2[i];
-            const double wx = __ldg(wtab + mv.x) * rv.x, wy = __ldg(wtab + mv.y) * rv.y;
-            acc = fma(wx, rv.x, acc);
-            acc = fma(wy, rv.y, acc);
-            if (PC) {
-                const double2 dv = __ldg(d2 + i);
-                acz = fma(wx, rv.x * dv.x, acz);
-                acz = fma(wy, rv.y * dv.y, acz);
-            }
-        }
-    }
+        });
     if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         const double ri = fma(-alpha, q[N - 1], r[N - 1]);
         r[N - 1] = ri;
@@ -558,7 +587,7 @@ __global__ void __launch_bounds__(kBlock) k_update_r(int64_t N, double *__restri
 // iteration and the stopping decision (recursive residual sqrt((r, r)_w) <=
 // rtol ||b||, or max_iter reached), applied after this update.
 template <bool PC>
-__global__ void __launch_bounds__(kBlock) k_update_xp(int64_t N, double *__restrict__ x, double *__restrict__ p,
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_xp(int64_t N, double *__restrict__ x, double *__restrict__ p,
                                                       const double *__restrict__ r, const double *part_rr, int G2,
                                                       Scal *s, cudaGraphConditionalHandle h, int use_cond,
                                                       const double *__restrict__ dinv, const double *part_rz) {
@@ -574,20 +603,30 @@ __global__ void __launch_bounds__(kBlock) k_update_xp(int64_t N, double *__restr
     double2 *p2 = reinterpret_cast<double2 *>(p);
     const double2 *r2 = reinterpret_cast<const double2 *>(r);
     const double2 *__restrict__ d2 = reinterpret_cast<const double2 *>(dinv);
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N2; i += stride) {
-        const double2 pv = p2[i];
-        double2 xv = __ldcs(x2 + i);
-        double2 zv = r2[i];
-        if (PC) {
-            const double2 dv = __ldg(d2 + i);
-            zv.x *= dv.x;
-            zv.y *= dv.y;
-        }
-        xv.x = fma(alpha, pv.x, xv.x);
-        xv.y = fma(alpha, pv.y, xv.y);
-        __stcs(x2 + i, xv);
-        p2[i] = make_double2(fma(beta, pv.x, zv.x), fma(beta, pv.y, zv.y));
-    }
+    struct Ld {
+        double2 p, x, z;
+    };
+    stream_loop<PC ? 2 : 4>(
+        (int64_t)blockIdx.x * kBlock + threadIdx.x, N2, stride,
+        [&](int64_t i) {
+            Ld l;
+            l.p = p2[i];
+            l.x = __ldcs(x2 + i);
+            l.z = r2[i];
+            if (PC) {
+                const double2 dv = __ldg(d2 + i);
+                l.z.x *= dv.x;
+                l.z.y *= dv.y;
+            }
+            return l;
+        },
+        [&](int64_t i, Ld l) {
+            double2 xv = l.x;
+            xv.x = fma(alpha, l.p.x, xv.x);
+            xv.y = fma(alpha, l.p.y, xv.y);
+            __stcs(x2 + i, xv);
+            p2[i] = make_double2(fma(beta, l.p.x, l.z.x), fma(beta, l.p.y, l.z.y));
+        });
     if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         const double pi = p[N - 1];
         x[N - 1] = fma(alpha, pi, x[N - 1]);
@@ -796,7 +835,7 @@ __global__ void __launch_bounds__(kBlock) k_inner_init(int64_t N, const double *
 // r32 <- r32 - alpha q32 and its share of (r32, r32)_w (products and block
 // sums in FP32).  A warp covers the 128 entries of flag group i >> 5 (float4
 // per lane); groups without interface copies skip the weights.
-__global__ void __launch_bounds__(kBlock) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
                                                        const uint8_t *__restrict__ mult,
                                                        const float *__restrict__ wtab,
                                                        const uint8_t *__restrict__ gflag128, const double *part_pq,
@@ -827,27 +866,39 @@ __global__ void __launch_bounds__(kBlock) k_update_r32(int64_t N, float *__restr
     float4 *__restrict__ r4 = reinterpret_cast<float4 *>(r);
     const float4 *__restrict__ q4 = reinterpret_cast<const float4 *>(q);
     const uchar4 *__restrict__ m4 = reinterpret_cast<const uchar4 *>(mult);
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N4; i += stride) {
-        float4 rv = r4[i];
-        const float4 qv = __ldcs(q4 + i);
-        rv.x = fmaf(-alpha, qv.x, rv.x);
-        rv.y = fmaf(-alpha, qv.y, rv.y);
-        rv.z = fmaf(-alpha, qv.z, rv.z);
-        rv.w = fmaf(-alpha, qv.w, rv.w);
-        r4[i] = rv;
-        if (__ldg(gflag128 + (i >> 5)) == 0) {
-            acc = fmaf(rv.x, rv.x, acc);
-            acc = fmaf(rv.y, rv.y, acc);
-            acc = fmaf(rv.z, rv.z, acc);
-            acc = fmaf(rv.w, rv.w, acc);
-        } else {
-            const uchar4 mv = m4[i];
-            acc = fmaf(__ldg(wtab + mv.x) * rv.x, rv.x, acc);
-            acc = fmaf(__ldg(wtab + mv.y) * rv.y, rv.y, acc);
-            acc = fmaf(__ldg(wtab + mv.z) * rv.z, rv.z, acc);
-            acc = fmaf(__ldg(wtab + mv.w) * rv.w, rv.w, acc);
-        }
-    }
+    struct Ld {
+        float4 r, q;
+        uint8_t g;
+    };
+    stream_loop<4>(
+        (int64_t)blockIdx.x * kBlock + threadIdx.x, N4, stride,
+        [&](int64_t i) {
+            Ld l;
+            l.r = r4[i];
+            l.q = __ldcs(q4 + i);
+            l.g = __ldg(gflag128 + (i >> 5));
+            return l;
+        },
+        [&](int64_t i, Ld l) {
+            float4 rv = l.r;
+            rv.x = fmaf(-alpha, l.q.x, rv.x);
+            rv.y = fmaf(-alpha, l.q.y, rv.y);
+            rv.z = fmaf(-alpha, l.q.z, rv.z);
+            rv.w = fmaf(-alpha, l.q.w, rv.w);
+            r4[i] = rv;
+            if (l.g == 0) {
+                acc = fmaf(rv.x, rv.x, acc);
+                acc = fmaf(rv.y, rv.y, acc);
+                acc = fmaf(rv.z, rv.z, acc);
+                acc = fmaf(rv.w, rv.w, acc);
+            } else {
+                const uchar4 mv = m4[i];
+                acc = fmaf(__ldg(wtab + mv.x) * rv.x, rv.x, acc);
+                acc = fmaf(__ldg(wtab + mv.y) * rv.y, rv.y, acc);
+                acc = fmaf(__ldg(wtab + mv.z) * rv.z, rv.z, acc);
+                acc = fmaf(__ldg(wtab + mv.w) * rv.w, rv.w, acc);
+            }
+        });
     if (blockIdx.x == 0 && threadIdx.x < (N & 3)) {
         const int64_t i = (N & ~int64_t(3)) + threadIdx.x;
         const float ri = fmaf(-alpha, q[i], r[i]);
@@ -870,7 +921,7 @@ __global__ void __launch_bounds__(kBlock) k_update_r32(int64_t N, float *__restr
 // block 0 records the iteration and the inner stopping decision
 // (sqrt(rho) <= tau sqrt(rho0), or the inner iterations summed over
 // refinements reach max_iter).
-__global__ void __launch_bounds__(kBlock) k_update_dp32(int64_t N, float *__restrict__ d, float *__restrict__ p,
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t N, float *__restrict__ d, float *__restrict__ p,
                                                         const float *__restrict__ r, const double *part_rr, int G2,
                                                         Scal *si, Scal *so, cudaGraphConditionalHandle h,
                                                         int use_cond) {
@@ -886,18 +937,29 @@ __global__ void __launch_bounds__(kBlock) k_update_dp32(int64_t N, float *__rest
     float4 *__restrict__ d4 = reinterpret_cast<float4 *>(d);
     float4 *__restrict__ p4 = reinterpret_cast<float4 *>(p);
     const float4 *__restrict__ r4 = reinterpret_cast<const float4 *>(r);
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N4; i += stride) {
-        const float4 pv = p4[i];
-        float4 dv = d4[i];
-        const float4 rv = r4[i];
-        dv.x = fmaf(alpha, pv.x, dv.x);
-        dv.y = fmaf(alpha, pv.y, dv.y);
-        dv.z = fmaf(alpha, pv.z, dv.z);
-        dv.w = fmaf(alpha, pv.w, dv.w);
-        d4[i] = dv;
-        p4[i] = make_float4(fmaf(beta, pv.x, rv.x), fmaf(beta, pv.y, rv.y), fmaf(beta, pv.z, rv.z),
-                            fmaf(beta, pv.w, rv.w));
-    }
+    struct Ld {
+        float4 p, d, r;
+    };
+    stream_loop<2>(
+        (int64_t)blockIdx.x * kBlock + threadIdx.x, N4, stride,
+        [&](int64_t i) {
+            Ld l;
+            l.p = p4[i];
+            l.d = d4[i];
+            l.r = r4[i];
+            return l;
+        },
+        [&](int64_t i, Ld l) {
+            float4 dv = l.d;
+            const float4 pv = l.p, rv = l.r;
+            dv.x = fmaf(alpha, pv.x, dv.x);
+            dv.y = fmaf(alpha, pv.y, dv.y);
+            dv.z = fmaf(alpha, pv.z, dv.z);
+            dv.w = fmaf(alpha, pv.w, dv.w);
+            d4[i] = dv;
+            p4[i] = make_float4(fmaf(beta, pv.x, rv.x), fmaf(beta, pv.y, rv.y), fmaf(beta, pv.z, rv.z),
+                                fmaf(beta, pv.w, rv.w));
+        });
     if (blockIdx.x == 0 && threadIdx.x < (N & 3)) {
         const int64_t i = (N & ~int64_t(3)) + threadIdx.x;
         const float pi = p[i];
