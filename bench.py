@@ -566,7 +566,8 @@ def run_ours(args, dist):
     S = System(ctx, prob.A, prob.part, prob.P)
     b = torch.from_numpy(prob.b[:, 0].copy()).to("cuda:%d" % dev)
     x = torch.zeros_like(b)
-    modes = {"fp64": ssg.SSG_FP64, "mixed": ssg.SSG_MIXED, "jacobi": ssg.SSG_FP64_JACOBI}
+    modes = {"fp64": ssg.SSG_FP64, "mixed": ssg.SSG_MIXED, "jacobi": ssg.SSG_FP64_JACOBI,
+             "mixed_jacobi": ssg.SSG_MIXED_JACOBI}
 
     def solve(mode):
         x.zero_()
@@ -612,6 +613,10 @@ def run_ours(args, dist):
         x.zero_()
         ssg.ssg_solve(S.h, 1, b, x, False, RTOL, 0, ssg.SSG_FP64_JACOBI)
     ms_jac, sts_jac, _ = timed("jacobi", args.steps)
+    for _ in range(max(args.warmup, 0)):
+        x.zero_()
+        ssg.ssg_solve(S.h, 1, b, x, False, RTOL, 0, ssg.SSG_MIXED_JACOBI)
+    ms_mjac, sts_mjac, _ = timed("mixed_jacobi", args.steps)
 
     # end to end through the host-buffer C ABI call (pinned host memory)
     bh = torch.from_numpy(prob.b[:, 0].copy()).pin_memory().numpy()
@@ -692,6 +697,10 @@ def run_ours(args, dist):
             "jacobi_s": ms_jac / 1e3,
             "jacobi_iters": sts_jac[-1]["iters"],
             "jacobi_true_relres": sts_jac[-1]["true_relres"],
+            "mixed_jacobi_s": ms_mjac / 1e3,
+            "mixed_jacobi_iters": sts_mjac[-1]["iters"],
+            "mixed_jacobi_outer": sts_mjac[-1]["outer"],
+            "mixed_jacobi_true_relres": sts_mjac[-1]["true_relres"],
             "l2": "inputs larger than L2 (175 MB matrix + 5 x 18 MB vectors > 129 MB)",
             "parallelism": "replicas" if dist.world > 1 else "single",
             "driver": args.driver,

@@ -54,6 +54,8 @@ extern "C" {
 #define SSG_FP64_JACOBI 2 /* Algorithm 3 with the diagonal preconditioner M = diag(S) of the   \
                              paper's experiments (Section 3.1), FP64; right-hand sides solved \
                              one after another */
+#define SSG_MIXED_JACOBI 3 /* SSG_MIXED with the diagonal preconditioner in the FP32 inner solves;  \
+                              right-hand sides solved one after another */
 
 /* driver modes (ssg_set_driver) */
 #define SSG_DRIVER_GRAPH 0 /* one CUDA-graph launch per solve, device-side while loop */
@@ -248,6 +250,27 @@ int ssg_spmv_assembled(ssg_system *sys, const double *x_loc, double *y_loc, doub
  */
 int ssg_spmv_assembled_f32(ssg_system *sys, const float *x_loc, float *y_loc, double *xSx_dev);
 
+/* Result of ssg_autotune: per precision, the launch shape (blocks per SM)
+ * and L2 prefetch distance of every candidate, its mean launch time, and the
+ * index chosen. */
+typedef struct {
+    int32_t fp64_choice, fp32_choice;
+    int32_t fp64_blocks_per_sm[4], fp64_l2_ahead[4];
+    int32_t fp32_blocks_per_sm[4], fp32_l2_ahead[4];
+    double fp64_us[4], fp32_us[4];
+} ssg_tune;
+/*
+ * Time the single-vector SpMV instances (launch shapes of 3 to 5 blocks per
+ * SM, L2 prefetch of the next slices on or off; four per precision) on this
+ * system, reps launches each (reps <= 0: 20), and use the fastest for the
+ * following solves and products.  The choice changes only the order of the
+ * block partial sums (results within the same rounding bounds; bit-for-bit
+ * repeatable once chosen).  Without a call the defaults are entry 0, the
+ * measured best on the 128^3 finite-volume system.  Blocks until done;
+ * graphs built earlier are rebuilt on the next solve.
+ */
+int ssg_autotune(ssg_system *sys, int32_t reps, ssg_tune *out);
+
 /*
  * The sub-structured product of ssg_spmv_assembled with k vectors at once
  * (k = 2, 4, 8 or 16): x_loc and y_loc are device blocks of nloc*k doubles,
@@ -282,6 +305,9 @@ int ssg_wdot(ssg_system *sys, const double *u_loc, const double *v_loc, double *
  * the reciprocal 1 / S_ii per local entry), alpha = (r, z)_w / (S p, p)_w,
  * beta = (r, z)_w(k+1) / (r, z)_w(k), p = z + beta p; the stopping test stays
  * on (r, r)_w; SSG_E_INVALID if a diagonal entry is missing or not positive.
+ * SSG_MIXED_JACOBI: the refinement of SSG_MIXED whose inner FP32 solves use
+ * the same preconditioner (z = r * 1/S_ii rounded to FP32, the inner test on
+ * (r, r)_w).
  * SSG_MIXED: iterative refinement in FP64 (r = b - S x with the FP64
  * sub-structured SpMV, x += d, the stopping test on that true residual)
  * around an inner Algorithm 3 in FP32 (values, vectors and SpMV in FP32, dot

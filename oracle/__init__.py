@@ -124,6 +124,9 @@ def _bind(L):
         L.or_sub_pcg.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int32, C.POINTER(C.c_int32),
                                  C.POINTER(C.c_double)]
         L.or_sub_pcg.restype = C.c_int
+        L.or_sub_pcg_mixed.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int32, C.c_double, C.c_int32,
+                                       C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+        L.or_sub_pcg_mixed.restype = C.c_int
         L.or_cholesky_solve.argtypes = [C.c_int32, _f64p, _f64p, _f64p]
         L.or_cholesky_solve.restype = C.c_int
     return L
@@ -347,6 +350,22 @@ def _sub_pcg(self, b, rtol, max_iter, x0=None) -> PCGResult:
 
 
 Partition.pcg = _sub_pcg
+
+
+def _sub_pcg_mixed(self, b, rtol, max_iter, inner_rtol=1e-4, max_outer=30, x0=None) -> "MixedResult":
+    """Mixed refinement with diagonal-preconditioned FP32 inner solves
+    (ssg_oracle.c: or_sub_pcg_mixed)."""
+    b = _c(b, np.float64).ravel()
+    x = np.zeros(self.maps.n) if x0 is None else _c(x0, np.float64).ravel().copy()
+    it = C.c_int32()
+    ou = C.c_int32()
+    rr = C.c_double()
+    st = self._L.or_sub_pcg_mixed(self.h, b, x, rtol, max_iter, inner_rtol, max_outer, C.byref(it), C.byref(ou),
+                                  C.byref(rr))
+    return MixedResult(x, st, it.value, ou.value, rr.value)
+
+
+Partition.pcg_mixed = _sub_pcg_mixed
 
 
 def cholesky_solve(Adense, b):

@@ -942,3 +942,90 @@ fail:
     or_part_free(h);
     return NULL;
 }
+
+/* ------------------------------------------------------------------ */
+/* Mixed precision with the diagonal preconditioner.                   */
+/* ------------------------------------------------------------------ */
+/*
+ * or_sub_cg_mixed with Algorithm 3's diagonal preconditioner in the inner
+ * FP32 solves: z32 = r32 / (float) diag(S) (the assembled diagonal of
+ * local_diagonal, rounded to FP32), alpha = (r32, z32)_w / (p32, S p32)_w,
+ * beta = (r32, z32)_w(k+1) / (r32, z32)_w(k), p32 = z32 + beta p32; the inner
+ * test stays on (r32, r32)_w: sqrt((r32, r32)_w) <= tau sqrt((r32, r32)_w at
+ * the inner start).  The outer FP64 refinement is that of or_sub_cg_mixed.
+ */
+int or_sub_pcg_mixed(const or_part *h, const double *b, double *x, double rtol, int32_t max_iter,
+                     double inner_rtol, int32_t max_outer, int32_t *iters_out, int32_t *outer_out,
+                     double *relres_out) {
+    size_t N = (size_t)(h->nloc > 0 ? h->nloc : 1);
+    const int64_t L = h->nloc;
+    double *bl = (double *)malloc(sizeof(double) * N), *xl = (double *)malloc(sizeof(double) * N);
+    double *r = (double *)malloc(sizeof(double) * N), *q = (double *)malloc(sizeof(double) * N);
+    double *dl = (double *)malloc(sizeof(double) * N);
+    float *val32 = (float *)malloc(sizeof(float) * (size_t)(h->nnz > 0 ? h->nnz : 1));
+    float *r32 = (float *)malloc(sizeof(float) * N), *z32 = (float *)malloc(sizeof(float) * N);
+    float *p32 = (float *)malloc(sizeof(float) * N), *q32 = (float *)malloc(sizeof(float) * N);
+    float *d32 = (float *)malloc(sizeof(float) * N), *g32 = (float *)malloc(sizeof(float) * N);
+    int status = OR_OOM;
+    if (!bl || !xl || !r || !q || !dl || !val32 || !r32 || !z32 || !p32 || !q32 || !d32 || !g32) goto done;
+    status = local_diagonal(h, dl);
+    if (status != OR_OK) goto done;
+    for (int64_t k = 0; k < L; ++k) g32[k] = (float)dl[k];
+    for (int64_t k = 0; k < h->nnz; ++k) val32[k] = (float)h->lval[k];
+    or_scatter(h, b, bl);
+    or_scatter(h, x, xl);
+    or_sub_spmv(h, xl, q);
+    for (int64_t k = 0; k < L; ++k) r[k] = bl[k] - q[k];
+    double rho = or_wdot(h, r, r);
+    const double bnorm = sqrt(or_wdot(h, bl, bl));
+    int32_t outer = 0, total = 0;
+    status = OR_NOT_CONVERGED;
+    if (sqrt(rho) <= rtol * bnorm) status = OR_OK;
+    while (status == OR_NOT_CONVERGED && outer < max_outer && total < max_iter) {
+        double tau = rtol * bnorm / sqrt(rho);
+        if (tau < inner_rtol) tau = inner_rtol;
+        for (int64_t k = 0; k < L; ++k) {
+            r32[k] = (float)r[k];
+            z32[k] = r32[k] / g32[k];
+            p32[k] = z32[k];
+            d32[k] = 0.0f;
+        }
+        double rz = wdot32(h, r32, z32);
+        double rr = wdot32(h, r32, r32);
+        const double rr0 = rr;
+        int broke = 0;
+        while (sqrt(rr) > tau * sqrt(rr0) && total < max_iter) {
+            sub_spmv32(h, val32, p32, q32);
+            const double pq = wdot32(h, p32, q32);
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                broke = 1;
+                break;
+            }
+            const float alpha = (float)(rz / pq);
+            for (int64_t k = 0; k < L; ++k) d32[k] = d32[k] + alpha * p32[k];
+            for (int64_t k = 0; k < L; ++k) r32[k] = r32[k] - alpha * q32[k];
+            for (int64_t k = 0; k < L; ++k) z32[k] = r32[k] / g32[k];
+            const double rz_new = wdot32(h, r32, z32);
+            rr = wdot32(h, r32, r32);
+            const float beta = (float)(rz_new / rz);
+            for (int64_t k = 0; k < L; ++k) p32[k] = z32[k] + beta * p32[k];
+            rz = rz_new;
+            ++total;
+        }
+        for (int64_t k = 0; k < L; ++k) xl[k] = xl[k] + (double)d32[k];
+        or_sub_spmv(h, xl, q);
+        for (int64_t k = 0; k < L; ++k) r[k] = bl[k] - q[k];
+        rho = or_wdot(h, r, r);
+        ++outer;
+        if (sqrt(rho) <= rtol * bnorm) status = OR_OK;
+        else if (broke) status = OR_BREAKDOWN;
+    }
+    or_gather(h, xl, x);
+    *iters_out = total;
+    *outer_out = outer;
+    *relres_out = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;
+done:
+    free(bl); free(xl); free(r); free(q); free(dl); free(val32); free(r32); free(z32); free(p32); free(q32);
+    free(d32); free(g32);
+    return status;
+}

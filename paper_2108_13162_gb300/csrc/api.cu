@@ -68,6 +68,9 @@ struct ssg_system {
     bool pdl = false;  // loop-body kernels use programmatic dependent launch
     int grid_spmv = 0;
     int grid_spmv32 = 0;
+    int grid_bps[6] = {0, 0, 0, 0, 0, 0};           // single-vector grids for 3, 4, 5 blocks per SM
+    const int2 *range_bps[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int var64 = 0, var32 = 0;                       // chosen SpMV instances (ssg_autotune)
     int grid_vec = 0;
     // graph
     cudaGraph_t graph = nullptr;
@@ -76,9 +79,9 @@ struct ssg_system {
     cudaGraph_t graph_pc = nullptr;  // SSG_FP64_JACOBI
     cudaGraphExec_t exec_pc = nullptr;
     cudaGraphConditionalHandle cond_pc = 0;
-    cudaGraph_t graph_m = nullptr;  // SSG_MIXED: nested refinement / inner loops
-    cudaGraphExec_t exec_m = nullptr;
-    cudaGraphConditionalHandle cond_out = 0, cond_in = 0;
+    cudaGraph_t graph_m[2] = {nullptr, nullptr};  // SSG_MIXED, SSG_MIXED_JACOBI: nested loops
+    cudaGraphExec_t exec_m[2] = {nullptr, nullptr};
+    cudaGraphConditionalHandle cond_out[2] = {0, 0}, cond_in[2] = {0, 0};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // new values for the same pattern (ssg_set_values): the input-CSR entry
     // each device value copies (-1: padding)
@@ -142,6 +145,29 @@ cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), int grid, int block, cuda
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// Single-vector SpMV instances ssg_autotune chooses from (launch shape x L2
+// prefetch distance); entry 0 is the default, the measured best on the 128^3
+// system.
+template <typename T>
+struct SpmvVariant {
+    int bps, ahead;
+    void (*part)(DevOp, const T *, T *, double *, Scal *, double *, cudaGraphConditionalHandle, int);
+    void (*store)(DevOp, const T *, T *, double *, Scal *, double *, cudaGraphConditionalHandle, int);
+};
+constexpr int kSpmvVariants = 4;
+const SpmvVariant<double> kSpmv64Variants[kSpmvVariants] = {
+    {4, 0, k_spmv_asm<kEpiPartials, double, 4, 0>, k_spmv_asm<kEpiStore, double, 4, 0>},
+    {4, 1, k_spmv_asm<kEpiPartials, double, 4, 1>, k_spmv_asm<kEpiStore, double, 4, 1>},
+    {3, 0, k_spmv_asm<kEpiPartials, double, 3, 0>, k_spmv_asm<kEpiStore, double, 3, 0>},
+    {3, 1, k_spmv_asm<kEpiPartials, double, 3, 1>, k_spmv_asm<kEpiStore, double, 3, 1>},
+};
+const SpmvVariant<float> kSpmv32Variants[kSpmvVariants] = {
+    {5, 1, k_spmv_asm<kEpiPartials, float, 5, 1>, k_spmv_asm<kEpiStore, float, 5, 1>},
+    {5, 0, k_spmv_asm<kEpiPartials, float, 5, 0>, k_spmv_asm<kEpiStore, float, 5, 0>},
+    {4, 1, k_spmv_asm<kEpiPartials, float, 4, 1>, k_spmv_asm<kEpiStore, float, 4, 1>},
+    {4, 2, k_spmv_asm<kEpiPartials, float, 4, 2>, k_spmv_asm<kEpiStore, float, 4, 2>},
+};
+
 // SpMV work list (see WorkItem in kernels.cuh) and the sliced-ELL copy of
 // the local matrices it streams.  Interior slices: up to 32 consecutive
 // interior rows of one subdomain, width = their longest row; a row longer
@@ -159,12 +185,13 @@ struct WorkPlan {
     std::vector<double> sval;        // sliced-ELL values
     std::vector<int32_t> scol, sseg;
     std::vector<WorkItem> items;
-    std::vector<int2> warp_range64, warp_range32;  // per warp of the FP64 / FP32 launch
+    std::vector<int2> range_bps[6];  // per warp of a single-vector launch sized for 3, 4 or 5 blocks per SM
     std::vector<int2> warp_rangeB;   // per warp of the K-vector product: cut inside each segment
     std::vector<int32_t> blk_seg, seg_blk;  // segment of each K-vector product block; blocks per segment
     std::vector<int4> chunk;                // vector-kernel chunks (segment, first entry, end entry, 0)
     std::vector<int32_t> seg_chunk;         // chunks per segment
-    int grid64 = 0, grid32 = 0, gridB = 0;
+    int grid_bps[6] = {0, 0, 0, 0, 0, 0};
+    int gridB = 0;
 };
 
 double item_cost(const WorkItem &w) {
@@ -325,10 +352,10 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
     }
     const int n = static_cast<int>(W.items.size());
     const int per = (n + kSpmvWarps - 1) / kSpmvWarps;
-    W.grid64 = std::max(1, std::min(per, num_sms * SpmvTraits<double>::kBlocksPerSM));
-    W.grid32 = std::max(1, std::min(per, num_sms * SpmvTraits<float>::kBlocksPerSM));
-    W.warp_range64 = cut_ranges(W.items, W.grid64);
-    W.warp_range32 = cut_ranges(W.items, W.grid32);
+    for (int bps = 3; bps <= 5; ++bps) {
+        W.grid_bps[bps] = std::max(1, std::min(per, num_sms * bps));
+        W.range_bps[bps] = cut_ranges(W.items, W.grid_bps[bps]);
+    }
     // K-vector product: blocks shared out among the segments by cost, at
     // least one each, every block inside one segment
     std::vector<double> seg_cost(static_cast<size_t>(nseg), 0.0);
@@ -376,7 +403,7 @@ double *part_rz(ssg_system *S) { return S->d_partials + 2 * (S->n_partials / 3);
 int launch_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const int64_t N = S->maps.nloc;
     const cudaGraphConditionalHandle h = pc ? S->cond_pc : S->cond;
-    SSG_CUDA_TRY(launch_k(false, k_spmv_asm<kEpiPartials, double>, S->grid_spmv, kSpmvThreads, st, S->op, S->d_p,
+    SSG_CUDA_TRY(launch_k(false, kSpmv64Variants[S->var64].part, S->grid_spmv, kSpmvThreads, st, S->op, S->d_p,
                           S->d_q, part_pq(S), S->d_scal, (double *)nullptr, h, use_cond));
     SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_r<true> : k_update_r<false>, S->grid_vec, kBlock, st, N, S->d_r,
                           S->d_q, S->op.mult, S->op.wtab, S->op.gflag, (const double *)part_pq(S), S->grid_spmv,
@@ -399,41 +426,45 @@ int launch_init(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     return SSG_OK;
 }
 
-int launch_mixed_init(ssg_system *S, cudaStream_t st, int use_cond) {
+int launch_mixed_init(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     k_cg_init<false><<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_bl, S->d_q, S->d_r, nullptr, S->op.mult,
-                                                     S->op.wtab, S->d_partials, S->d_scal, S->cond_out, use_cond,
+                                                     S->op.wtab, S->d_partials, S->d_scal, S->cond_out[pc], use_cond,
                                                      nullptr);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
 
-int launch_inner_init(ssg_system *S, cudaStream_t st, int use_cond) {
-    k_inner_init<<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_r, S->d_r32, S->d_p32, S->d_d32, S->op.mult,
-                                                 S->op.wtab32, S->d_partials, S->d_scal_in, S->d_scal, S->cond_in,
-                                                 use_cond);
+int launch_inner_init(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
+    auto kern = pc ? k_inner_init<true> : k_inner_init<false>;
+    kern<<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_r, S->d_r32, S->d_p32, S->d_d32, S->op.mult, S->op.wtab32,
+                                         S->d_partials, S->d_scal_in, S->d_scal, S->cond_in[pc], use_cond,
+                                         S->d_dinv32);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
 
-int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond) {
+int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const int64_t N = S->maps.nloc;
-    SSG_CUDA_TRY(launch_k(false, k_spmv_asm<kEpiPartials, float>, S->grid_spmv32, kSpmvThreads, st, S->op32,
-                          S->d_p32, S->d_q32, part_pq(S), S->d_scal_in, (double *)nullptr, S->cond_in, use_cond));
-    SSG_CUDA_TRY(launch_k(S->pdl, k_update_r32, S->grid_vec, kBlock, st, N, S->d_r32, S->d_q32, S->op.mult,
-                          S->op.wtab32, S->op.gflag128, (const double *)part_pq(S), S->grid_spmv32, part_rr(S),
-                          S->d_scal_in, (const Scal *)S->d_scal, S->cond_in, use_cond));
-    SSG_CUDA_TRY(launch_k(S->pdl, k_update_dp32, S->grid_vec, kBlock, st, N, S->d_d32, S->d_p32, S->d_r32,
-                          (const double *)part_rr(S), S->grid_vec, S->d_scal_in, S->d_scal, S->cond_in, use_cond));
+    const cudaGraphConditionalHandle h = S->cond_in[pc];
+    SSG_CUDA_TRY(launch_k(false, kSpmv32Variants[S->var32].part, S->grid_spmv32, kSpmvThreads, st, S->op32,
+                          S->d_p32, S->d_q32, part_pq(S), S->d_scal_in, (double *)nullptr, h, use_cond));
+    SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_r32<true> : k_update_r32<false>, S->grid_vec, kBlock, st, N,
+                          S->d_r32, S->d_q32, S->op.mult, S->op.wtab32, S->op.gflag128, (const double *)part_pq(S),
+                          S->grid_spmv32, part_rr(S), S->d_scal_in, (const Scal *)S->d_scal, h, use_cond,
+                          (const float *)S->d_dinv32, part_rz(S)));
+    SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_dp32<true> : k_update_dp32<false>, S->grid_vec, kBlock, st, N,
+                          S->d_d32, S->d_p32, S->d_r32, (const double *)part_rr(S), S->grid_vec, S->d_scal_in,
+                          S->d_scal, h, use_cond, (const float *)S->d_dinv32, (const double *)part_rz(S)));
     return SSG_OK;
 }
 
-int launch_outer_tail(ssg_system *S, cudaStream_t st, int use_cond) {
+int launch_outer_tail(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const int64_t N = S->maps.nloc;
     k_ir_correct<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_xl, S->d_d32);
-    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, 0, st>>>(
+    kSpmv64Variants[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, st>>>(
         S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
     k_ir_residual<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_bl, S->d_q, S->d_r, S->op.mult, S->op.wtab, S->d_partials,
-                                                  S->d_scal, S->d_scal_in, S->cond_out, use_cond);
+                                                  S->d_scal, S->d_scal_in, S->cond_out[pc], use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
@@ -528,48 +559,53 @@ int build_graph_once(ssg_system *S, bool pc) {
 
 // SSG_MIXED graph: init -> WHILE(outer) { inner_init -> WHILE(inner) { FP32
 // SpMV, r update, d/p update } -> x += d -> FP64 SpMV -> residual + test }.
-int build_graph_mixed_once(ssg_system *S);
+int build_graph_mixed_once(ssg_system *S, bool pc);
 
-int build_graph_mixed(ssg_system *S) {
-    if (S->exec_m) return SSG_OK;
-    int rc = build_graph_mixed_once(S);
+int build_graph_mixed(ssg_system *S, bool pc) {
+    if (S->exec_m[pc]) return SSG_OK;
+    int rc = build_graph_mixed_once(S, pc);
     if (rc != SSG_OK && S->pdl) {
         S->pdl = false;
-        rc = build_graph_mixed_once(S);
+        rc = build_graph_mixed_once(S, pc);
     }
     return rc;
 }
 
-int build_graph_mixed_once(ssg_system *S) {
-    SSG_CUDA_TRY(cudaGraphCreate(&S->graph_m, 0));
-    SSG_CUDA_TRY(cudaGraphConditionalHandleCreate(&S->cond_out, S->graph_m, 0u, cudaGraphCondAssignDefault));
+int build_graph_mixed_once(ssg_system *S, bool pc) {
+    cudaGraph_t &gm = S->graph_m[pc];
+    SSG_CUDA_TRY(cudaGraphCreate(&gm, 0));
+    SSG_CUDA_TRY(cudaGraphConditionalHandleCreate(&S->cond_out[pc], gm, 0u, cudaGraphCondAssignDefault));
     cudaStream_t cap;
     SSG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     int rc = SSG_OK;
-    cudaError_t e = capture_into(cap, S->graph_m, nullptr, 0, [&](cudaStream_t c) { return launch_mixed_init(S, c, 1); }, &rc);
+    cudaError_t e =
+        capture_into(cap, gm, nullptr, 0, [&](cudaStream_t c) { return launch_mixed_init(S, c, 1, pc); }, &rc);
     cudaGraphNode_t n_init = nullptr, n_outer = nullptr, n_iinit = nullptr, n_inner = nullptr;
     cudaGraph_t body_out = nullptr, body_in = nullptr;
-    if (e == cudaSuccess && rc == SSG_OK) e = last_node(S->graph_m, &n_init);
-    if (e == cudaSuccess && rc == SSG_OK) e = add_while(S->graph_m, &n_init, S->cond_out, &n_outer, &body_out);
+    if (e == cudaSuccess && rc == SSG_OK) e = last_node(gm, &n_init);
+    if (e == cudaSuccess && rc == SSG_OK) e = add_while(gm, &n_init, S->cond_out[pc], &n_outer, &body_out);
     // the inner handle must exist before the kernels that set it are captured
     if (e == cudaSuccess && rc == SSG_OK)
-        e = cudaGraphConditionalHandleCreate(&S->cond_in, body_out, 0u, cudaGraphCondAssignDefault);
+        e = cudaGraphConditionalHandleCreate(&S->cond_in[pc], body_out, 0u, cudaGraphCondAssignDefault);
     if (e == cudaSuccess && rc == SSG_OK)
-        e = capture_into(cap, body_out, nullptr, 0, [&](cudaStream_t c) { return launch_inner_init(S, c, 1); }, &rc);
+        e = capture_into(cap, body_out, nullptr, 0, [&](cudaStream_t c) { return launch_inner_init(S, c, 1, pc); },
+                         &rc);
     if (e == cudaSuccess && rc == SSG_OK) e = last_node(body_out, &n_iinit);
-    if (e == cudaSuccess && rc == SSG_OK) e = add_while(body_out, &n_iinit, S->cond_in, &n_inner, &body_in);
+    if (e == cudaSuccess && rc == SSG_OK) e = add_while(body_out, &n_iinit, S->cond_in[pc], &n_inner, &body_in);
     if (e == cudaSuccess && rc == SSG_OK)
-        e = capture_into(cap, body_in, nullptr, 0, [&](cudaStream_t c) { return launch_inner_body(S, c, 1); }, &rc);
+        e = capture_into(cap, body_in, nullptr, 0, [&](cudaStream_t c) { return launch_inner_body(S, c, 1, pc); },
+                         &rc);
     if (e == cudaSuccess && rc == SSG_OK)
-        e = capture_into(cap, body_out, &n_inner, 1, [&](cudaStream_t c) { return launch_outer_tail(S, c, 1); }, &rc);
-    if (e == cudaSuccess && rc == SSG_OK) e = cudaGraphInstantiate(&S->exec_m, S->graph_m, 0);
+        e = capture_into(cap, body_out, &n_inner, 1,
+                         [&](cudaStream_t c) { return launch_outer_tail(S, c, 1, pc); }, &rc);
+    if (e == cudaSuccess && rc == SSG_OK) e = cudaGraphInstantiate(&S->exec_m[pc], gm, 0);
     cudaStreamDestroy(cap);
     if (rc != SSG_OK) return rc;
     if (e != cudaSuccess) {
         set_error(std::string("building the mixed-precision graph: ") + cudaGetErrorString(e));
-        if (S->graph_m) cudaGraphDestroy(S->graph_m);
-        S->graph_m = nullptr;
-        S->exec_m = nullptr;
+        if (gm) cudaGraphDestroy(gm);
+        gm = nullptr;
+        S->exec_m[pc] = nullptr;
         return SSG_E_CUDA;
     }
     return SSG_OK;
@@ -613,10 +649,11 @@ int upload(ssg_system *S) {
         wtab32[m] = static_cast<float>(wtab[m]);
     }
 
-    S->grid_spmv = plan.grid64;
-    S->grid_spmv32 = plan.grid32;
+    for (int bps = 3; bps <= 5; ++bps) S->grid_bps[bps] = plan.grid_bps[bps];
+    S->grid_spmv = plan.grid_bps[kSpmv64Variants[0].bps];
+    S->grid_spmv32 = plan.grid_bps[kSpmv32Variants[0].bps];
     S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N / 2 + kBlock - 1) / kBlock), C->num_sms * kVecBlocksPerSM));
-    S->n_partials = 3 * std::max(std::max(S->grid_spmv, S->grid_spmv32), S->grid_vec);
+    S->n_partials = 3 * std::max(std::max(plan.grid_bps[3], std::max(plan.grid_bps[4], plan.grid_bps[5])), S->grid_vec);
 
     struct Piece {
         const void *src;
@@ -649,8 +686,9 @@ int upload(ssg_system *S) {
     size_t i_scol = add(plan.scol.data(), sizeof(int32_t) * plan.scol.size());
     size_t i_sseg = add(plan.sseg.data(), sizeof(int32_t) * plan.sseg.size());
     size_t i_items = add(plan.items.data(), sizeof(WorkItem) * plan.items.size());
-    size_t i_brange = add(plan.warp_range64.data(), sizeof(int2) * plan.warp_range64.size());
-    size_t i_brange32 = add(plan.warp_range32.data(), sizeof(int2) * plan.warp_range32.size());
+    size_t i_range_bps[6] = {0, 0, 0, 0, 0, 0};
+    for (int bps = 3; bps <= 5; ++bps)
+        i_range_bps[bps] = add(plan.range_bps[bps].data(), sizeof(int2) * plan.range_bps[bps].size());
     size_t i_brangeB = add(plan.warp_rangeB.data(), sizeof(int2) * plan.warp_rangeB.size());
     size_t i_blk_seg = add(plan.blk_seg.data(), sizeof(int32_t) * plan.blk_seg.size());
     size_t i_seg_blk = add(plan.seg_blk.data(), sizeof(int32_t) * plan.seg_blk.size());
@@ -765,7 +803,8 @@ int upload(ssg_system *S) {
     S->op.scol = static_cast<const int32_t *>(at(i_scol));
     S->op.sseg = static_cast<const int32_t *>(at(i_sseg));
     S->op.items = static_cast<const WorkItem *>(at(i_items));
-    S->op.warp_range = static_cast<const int2 *>(at(i_brange));
+    for (int bps = 3; bps <= 5; ++bps) S->range_bps[bps] = static_cast<const int2 *>(at(i_range_bps[bps]));
+    S->op.warp_range = S->range_bps[kSpmv64Variants[0].bps];
     S->op32 = S->op;  // filled below once the op is complete
     S->op.iptr = static_cast<const int32_t *>(at(i_iptr));
     S->op.icopy = static_cast<const int32_t *>(at(i_icopy));
@@ -787,7 +826,7 @@ int upload(ssg_system *S) {
     S->d_xg = static_cast<double *>(at(i_xg));
     S->d_bg = static_cast<double *>(at(i_bg));
     S->op32 = S->op;
-    S->op32.warp_range = static_cast<const int2 *>(at(i_brange32));
+    S->op32.warp_range = S->range_bps[kSpmv32Variants[0].bps];
     S->opB64 = S->op;
     S->opB64.warp_range = static_cast<const int2 *>(at(i_brangeB));
     S->opB32 = S->op;
@@ -855,9 +894,9 @@ int run_host_fp64(ssg_system *S, int64_t *launches, bool pc) {
     }
 }
 
-int run_host_mixed(ssg_system *S, int64_t *launches) {
+int run_host_mixed(ssg_system *S, int64_t *launches, bool pc) {
     cudaStream_t s = S->ctx->stream;
-    int rc = launch_mixed_init(S, s, 0);
+    int rc = launch_mixed_init(S, s, 0, pc);
     if (rc != SSG_OK) return rc;
     *launches += 1;
     Scal ho{}, hi{};
@@ -865,7 +904,7 @@ int run_host_mixed(ssg_system *S, int64_t *launches) {
         rc = read_scal(S, S->d_scal, &ho);
         if (rc != SSG_OK) return rc;
         if (ho.done) return SSG_OK;
-        rc = launch_inner_init(S, s, 0);
+        rc = launch_inner_init(S, s, 0, pc);
         if (rc != SSG_OK) return rc;
         *launches += 1;
         for (;;) {
@@ -873,12 +912,12 @@ int run_host_mixed(ssg_system *S, int64_t *launches) {
             if (rc != SSG_OK) return rc;
             if (hi.done) break;
             for (int i = 0; i < kHostChunk; ++i) {
-                rc = launch_inner_body(S, s, 0);
+                rc = launch_inner_body(S, s, 0, pc);
                 if (rc != SSG_OK) return rc;
             }
             *launches += 3 * kHostChunk;
         }
-        rc = launch_outer_tail(S, s, 0);
+        rc = launch_outer_tail(S, s, 0, pc);
         if (rc != SSG_OK) return rc;
         *launches += 3;
     }
@@ -903,7 +942,8 @@ int check_diag(ssg_system *S) {
 // One right-hand side: b_glob/x_glob are device pointers (length n).
 int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, double rtol, int32_t max_iter,
               int mode, ssg_stats *st) {
-    const bool pc = mode == SSG_FP64_JACOBI;
+    const bool mixed = mode == SSG_MIXED || mode == SSG_MIXED_JACOBI;
+    const bool pc = mode == SSG_FP64_JACOBI || mode == SSG_MIXED_JACOBI;
     if (pc) {
         int rc0 = check_diag(S);
         if (rc0 != SSG_OK) return rc0;
@@ -917,7 +957,7 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     ++launches;
     if (guess) {
         k_scatter<<<grid_for(N, C->num_sms), kBlock, 0, s>>>(N, S->d_l2g, x_glob, S->d_xl);
-        k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, 0, s>>>(
+        kSpmv64Variants[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, s>>>(
             S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
         launches += 2;
     } else {
@@ -925,23 +965,23 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     }
     k_set_params<<<1, 32, 0, s>>>(S->d_scal, rtol, max_iter, guess);
     ++launches;
-    if (mode == SSG_MIXED) {
+    if (mixed) {
         k_set_mixed<<<1, 32, 0, s>>>(S->d_scal, C->inner_rtol, C->max_outer);
         ++launches;
     }
     SSG_CUDA_TRY(cudaGetLastError());
     int rc = SSG_OK;
     if (C->driver == SSG_DRIVER_GRAPH) {
-        rc = mode == SSG_MIXED ? build_graph_mixed(S) : build_graph(S, pc);
+        rc = mixed ? build_graph_mixed(S, pc) : build_graph(S, pc);
         if (rc != SSG_OK) return rc;
-        SSG_CUDA_TRY(cudaGraphLaunch(mode == SSG_MIXED ? S->exec_m : pc ? S->exec_pc : S->exec, s));
+        SSG_CUDA_TRY(cudaGraphLaunch(mixed ? S->exec_m[pc] : pc ? S->exec_pc : S->exec, s));
     } else {
-        rc = mode == SSG_MIXED ? run_host_mixed(S, &launches) : run_host_fp64(S, &launches, pc);
+        rc = mixed ? run_host_mixed(S, &launches, pc) : run_host_fp64(S, &launches, pc);
         if (rc != SSG_OK) return rc;
     }
     k_gather<<<grid_for(S->maps.n, C->num_sms), kBlock, 0, s>>>(S->maps.n, S->d_own, S->d_xl, x_glob);
     // true residual ||b - S x||_w in FP64
-    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, 0, s>>>(
+    kSpmv64Variants[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, s>>>(
         S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
     k_wdot<true><<<S->grid_vec, kBlock, 0, s>>>(N, S->d_bl, S->d_q, S->op.mult, S->op.wtab, S->d_partials,
                                                 S->d_scal_op, &S->d_scal->aux);
@@ -954,15 +994,15 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     float ms = 0.f;
     SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
     if (C->driver == SSG_DRIVER_GRAPH) {
-        if (mode == SSG_MIXED)  // init, per refinement: inner init + 3 tail kernels, 3 per inner iteration
+        if (mixed)  // init, per refinement: inner init + 3 tail kernels, 3 per inner iteration
             launches += 1 + 4 * static_cast<int64_t>(h.iter) + 3 * static_cast<int64_t>(h.total);
         else  // init, 3 per iteration (a breakdown ends after the SpMV and residual kernels of one more)
             launches += 1 + 3 * static_cast<int64_t>(h.iter) + (h.status == SSG_E_BREAKDOWN ? 3 : 0);
     }
     if (st) {
         st->status = h.status;
-        st->iters = mode == SSG_MIXED ? h.total : h.iter;
-        st->outer = mode == SSG_MIXED ? h.iter : 1;
+        st->iters = mixed ? h.total : h.iter;
+        st->outer = mixed ? h.iter : 1;
         st->block = 1;
         st->relres = h.relres;
         st->true_relres = h.bnorm > 0.0 ? std::sqrt(h.aux) / h.bnorm : std::sqrt(h.aux);
@@ -1733,7 +1773,7 @@ int ssg_spmv_assembled(ssg_system *S, const double *x_loc, double *y_loc, double
         set_error("x_loc and y_loc must be distinct non-null device vectors");
         return SSG_E_INVALID;
     }
-    k_spmv_asm<kEpiStore, double><<<S->grid_spmv, kSpmvThreads, 0, S->ctx->stream>>>(
+    kSpmv64Variants[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, S->ctx->stream>>>(
         S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
@@ -1746,9 +1786,90 @@ int ssg_spmv_assembled_f32(ssg_system *S, const float *x_loc, float *y_loc, doub
         set_error("x_loc and y_loc must be distinct non-null device vectors");
         return SSG_E_INVALID;
     }
-    k_spmv_asm<kEpiStore, float><<<S->grid_spmv32, kSpmvThreads, 0, S->ctx->stream>>>(
+    kSpmv32Variants[S->var32].store<<<S->grid_spmv32, kSpmvThreads, 0, S->ctx->stream>>>(
         S->op32, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
     SSG_CUDA_TRY(cudaGetLastError());
+    return SSG_OK;
+}
+
+int ssg_autotune(ssg_system *S, int32_t reps, ssg_tune *out) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (reps <= 0) reps = 20;
+    cudaStream_t st = S->ctx->stream;
+    ssg_tune t{};
+    // FP64 instances on the solver's work vectors (zero-initialised, finite)
+    double best = 1e30;
+    for (int v = 0; v < kSpmvVariants; ++v) {
+        const SpmvVariant<double> &V = kSpmv64Variants[v];
+        DevOp A = S->op;
+        A.warp_range = S->range_bps[V.bps];
+        const int grid = S->grid_bps[V.bps];
+        for (int i = 0; i < 3; ++i)
+            V.store<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
+        SSG_CUDA_TRY(cudaEventRecord(S->ev0, st));
+        for (int i = 0; i < reps; ++i)
+            V.store<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
+        SSG_CUDA_TRY(cudaEventRecord(S->ev1, st));
+        SSG_CUDA_TRY(cudaGetLastError());
+        SSG_CUDA_TRY(cudaEventSynchronize(S->ev1));
+        float ms = 0.f;
+        SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
+        t.fp64_blocks_per_sm[v] = V.bps;
+        t.fp64_l2_ahead[v] = V.ahead;
+        t.fp64_us[v] = 1e3 * ms / reps;
+        if (t.fp64_us[v] < best) {
+            best = t.fp64_us[v];
+            t.fp64_choice = v;
+        }
+    }
+    best = 1e30;
+    for (int v = 0; v < kSpmvVariants; ++v) {
+        const SpmvVariant<float> &V = kSpmv32Variants[v];
+        DevOp A = S->op32;
+        A.warp_range = S->range_bps[V.bps];
+        const int grid = S->grid_bps[V.bps];
+        for (int i = 0; i < 3; ++i)
+            V.store<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p32, S->d_q32, S->d_partials, S->d_scal_op, nullptr, 0, 0);
+        SSG_CUDA_TRY(cudaEventRecord(S->ev0, st));
+        for (int i = 0; i < reps; ++i)
+            V.store<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p32, S->d_q32, S->d_partials, S->d_scal_op, nullptr, 0, 0);
+        SSG_CUDA_TRY(cudaEventRecord(S->ev1, st));
+        SSG_CUDA_TRY(cudaGetLastError());
+        SSG_CUDA_TRY(cudaEventSynchronize(S->ev1));
+        float ms = 0.f;
+        SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
+        t.fp32_blocks_per_sm[v] = V.bps;
+        t.fp32_l2_ahead[v] = V.ahead;
+        t.fp32_us[v] = 1e3 * ms / reps;
+        if (t.fp32_us[v] < best) {
+            best = t.fp32_us[v];
+            t.fp32_choice = v;
+        }
+    }
+    // adopt the choices; graphs holding the previous instances are rebuilt on demand
+    SSG_CUDA_TRY(cudaStreamSynchronize(st));
+    S->var64 = t.fp64_choice;
+    S->var32 = t.fp32_choice;
+    S->op.warp_range = S->range_bps[kSpmv64Variants[S->var64].bps];
+    S->grid_spmv = S->grid_bps[kSpmv64Variants[S->var64].bps];
+    S->op32.warp_range = S->range_bps[kSpmv32Variants[S->var32].bps];
+    S->grid_spmv32 = S->grid_bps[kSpmv32Variants[S->var32].bps];
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    if (S->exec_pc) cudaGraphExecDestroy(S->exec_pc);
+    if (S->graph_pc) cudaGraphDestroy(S->graph_pc);
+    S->exec = nullptr;
+    S->graph = nullptr;
+    S->exec_pc = nullptr;
+    S->graph_pc = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        if (S->exec_m[i]) cudaGraphExecDestroy(S->exec_m[i]);
+        if (S->graph_m[i]) cudaGraphDestroy(S->graph_m[i]);
+        S->exec_m[i] = nullptr;
+        S->graph_m[i] = nullptr;
+    }
+    if (out) *out = t;
     return SSG_OK;
 }
 
@@ -1861,15 +1982,15 @@ int ssg_solve(ssg_system *S, int32_t k, const double *b, double *x, int32_t x_is
         set_error("bad k, null b/x, or negative rtol");
         return SSG_E_INVALID;
     }
-    if (mode != SSG_FP64 && mode != SSG_MIXED && mode != SSG_FP64_JACOBI) {
-        set_error("mode must be SSG_FP64, SSG_MIXED or SSG_FP64_JACOBI");
+    if (mode != SSG_FP64 && mode != SSG_MIXED && mode != SSG_FP64_JACOBI && mode != SSG_MIXED_JACOBI) {
+        set_error("mode must be SSG_FP64, SSG_MIXED, SSG_FP64_JACOBI or SSG_MIXED_JACOBI");
         return SSG_E_INVALID;
     }
     if (max_iter <= 0) max_iter = S->maps.n;
     SSG_CUDA_TRY(cudaSetDevice(S->ctx->device));
     int first_bad = SSG_OK;
     // the diagonal preconditioner runs one right-hand side at a time
-    const int kb = mode == SSG_FP64_JACOBI ? 1 : std::max(1, S->ctx->rhs_block);
+    const int kb = mode == SSG_FP64_JACOBI || mode == SSG_MIXED_JACOBI ? 1 : std::max(1, S->ctx->rhs_block);
     for (int32_t j = 0; j < k;) {
         const int nr = std::min<int>(k - j, kb);
         const size_t o = static_cast<size_t>(j) * S->maps.n;
@@ -1892,12 +2013,13 @@ int ssg_solve_host(ssg_system *S, int32_t k, const double *b_host, double *x_hos
         set_error("bad k or null b/x");
         return SSG_E_INVALID;
     }
-    if (!(rtol >= 0.0) || (mode != SSG_FP64 && mode != SSG_MIXED && mode != SSG_FP64_JACOBI)) {
+    if (!(rtol >= 0.0) || (mode != SSG_FP64 && mode != SSG_MIXED && mode != SSG_FP64_JACOBI &&
+                           mode != SSG_MIXED_JACOBI)) {
         set_error("negative rtol or bad mode");
         return SSG_E_INVALID;
     }
     cudaStream_t s = S->ctx->stream;
-    const int kb = mode == SSG_FP64_JACOBI ? 1 : std::max(1, S->ctx->rhs_block);
+    const int kb = mode == SSG_FP64_JACOBI || mode == SSG_MIXED_JACOBI ? 1 : std::max(1, S->ctx->rhs_block);
     int first_bad = SSG_OK;
     for (int32_t j = 0; j < k;) {
         const int nr = std::min<int>(k - j, kb);
@@ -1929,8 +2051,10 @@ int ssg_system_destroy(ssg_system *S) {
     if (S->graph) cudaGraphDestroy(S->graph);
     if (S->exec_pc) cudaGraphExecDestroy(S->exec_pc);
     if (S->graph_pc) cudaGraphDestroy(S->graph_pc);
-    if (S->exec_m) cudaGraphExecDestroy(S->exec_m);
-    if (S->graph_m) cudaGraphDestroy(S->graph_m);
+    for (int i = 0; i < 2; ++i) {
+        if (S->exec_m[i]) cudaGraphExecDestroy(S->exec_m[i]);
+        if (S->graph_m[i]) cudaGraphDestroy(S->graph_m[i]);
+    }
     if (S->ev0) cudaEventDestroy(S->ev0);
     if (S->ev1) cudaEventDestroy(S->ev1);
     free_block(S);

@@ -66,10 +66,12 @@ struct SpmmTraits;
 template <>
 struct SpmmTraits<double> {
     static constexpr int kBlocksPerSM = 2;  // K FP64 accumulators and two entries' rows in flight per lane
+    static constexpr int kL2Ahead = 0;      // slices ahead whose value and column lines go to L2 (0: none)
 };
 template <>
 struct SpmmTraits<float> {
     static constexpr int kBlocksPerSM = 4;
+    static constexpr int kL2Ahead = 0;
 };
 
 // K contiguous values of one local entry.
@@ -223,6 +225,13 @@ __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ 
     for (int u = 0; u < VW; ++u) dot[u] = T(0);
     for (int it = range.x; it < range.y; ++it) {
         const WorkItem W = A.items[it];
+        if (SpmmTraits<T>::kL2Ahead > 0 && it + SpmmTraits<T>::kL2Ahead < range.y) {
+            const WorkItem Wp = A.items[it + SpmmTraits<T>::kL2Ahead];
+            if ((Wp.kind == kItemSlice || Wp.kind == kItemIfaceSlice) && lane < Wp.e1) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(sv + Wp.e0 + lane * kSliceRows));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
+            }
+        }
         if (W.kind == kItemSlice || W.kind == kItemIfaceSlice) {
             const bool iface = W.kind == kItemIfaceSlice;
             constexpr int NC = (sizeof(T) == 8 && K >= 8) ? 1 : 2;

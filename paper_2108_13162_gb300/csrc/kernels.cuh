@@ -34,11 +34,14 @@ template <>
 struct SpmvTraits<double> {
     static constexpr int kBlocksPerSM = 4;  // measured: 4 blocks without prefetch beat 3 with it
     static constexpr bool kPrefetch = false;
+    static constexpr int kL2Ahead = 0;      // slices ahead whose lines are prefetched into L2 (0: none);
+                                            // measured: 1 ahead 45.1 us, none 43.9 (the FP64 pipe is busy)
 };
 template <>
 struct SpmvTraits<float> {
     static constexpr int kBlocksPerSM = 5;  // measured: 32.0 us vs 32.8 (4 blocks, with or without prefetch)
     static constexpr bool kPrefetch = false;
+    static constexpr int kL2Ahead = 1;      // measured on the 128^3 system: 28.9 us (0: 31.8, 2: 29.9, 4: 31.7)
 };
 constexpr int kVecBlocksPerSM = 4;
 constexpr int kHostChunk = 32;    // iterations per host-loop chunk (SSG_DRIVER_HOST)
@@ -395,8 +398,12 @@ __device__ __forceinline__ void finish_slice(const DevOp &A, const WorkItem &W, 
     }
 }
 
-template <int EPI, typename T>
-__global__ void __launch_bounds__(kSpmvThreads, SpmvTraits<T>::kBlocksPerSM)
+// BPS: resident blocks per SM the launch is built for (the grid and the
+// register budget); AHEAD: slices ahead whose value and column lines are
+// prefetched into L2 (0: none).  The defaults are the measured best on the
+// 128^3 system; ssg_autotune times the other instances on a given system.
+template <int EPI, typename T, int BPS = SpmvTraits<T>::kBlocksPerSM, int AHEAD = SpmvTraits<T>::kL2Ahead>
+__global__ void __launch_bounds__(kSpmvThreads, BPS)
     k_spmv_asm(DevOp A, const T *__restrict__ x, T *__restrict__ y, double *partials, Scal *s, double *out,
                cudaGraphConditionalHandle h, int use_cond) {
     pdl_enter();
@@ -415,6 +422,14 @@ __global__ void __launch_bounds__(kSpmvThreads, SpmvTraits<T>::kBlocksPerSM)
     for (int it = range.x; it < range.y; ++it) {
         const bool has_next = it + 1 < range.y;
         const WorkItem Wn = has_next ? A.items[it + 1] : WorkItem{};
+        if (AHEAD > 0 && it + AHEAD < range.y) {
+            // the value and column lines of a slice further ahead, one line per lane
+            const WorkItem Wp = A.items[it + AHEAD];
+            if ((Wp.kind == kItemSlice || Wp.kind == kItemIfaceSlice) && lane < Wp.e1) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(sv + Wp.e0 + lane * kSliceRows));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
+            }
+        }
         if (kPF && short_slice(W)) {
             if (has_next && short_slice(Wn)) load_cols(nxt, A.scol, Wn, lane);
             const T acc = cols_row<T>(cur, sv, W, lane, x);
@@ -789,27 +804,36 @@ __global__ void __launch_bounds__(kBlock) k_gather(int64_t n, const int32_t *__r
 // Inner setup: r32 = (float) r64, p32 = r32, d32 = 0, rho0 = (r32, r32)_w and
 // the inner tolerance tau = max(inner_rtol, rtol ||b|| / ||r64||), so the last
 // refinement is not solved further than the outer test needs.
+template <bool PC>
 __global__ void __launch_bounds__(kBlock) k_inner_init(int64_t N, const double *__restrict__ r64,
                                                        float *__restrict__ r32, float *__restrict__ p32,
                                                        float *__restrict__ d32, const uint8_t *__restrict__ mult,
                                                        const float *__restrict__ wtab, double *partials, Scal *si,
-                                                       const Scal *so, cudaGraphConditionalHandle h, int use_cond) {
-    float acc = 0.f;
+                                                       const Scal *so, cudaGraphConditionalHandle h, int use_cond,
+                                                       const float *__restrict__ dinv32) {
+    float acc = 0.f, acz = 0.f;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < N; i += stride) {
         const float ri = float(r64[i]);
+        const float zi = PC ? ri * __ldg(dinv32 + i) : ri;
         r32[i] = ri;
-        p32[i] = ri;
+        p32[i] = zi;
         d32[i] = 0.f;
         const unsigned int m = mult[i];
-        acc = fmaf(__ldg(wtab + m) * ri, ri, acc);
+        const float wr = __ldg(wtab + m) * ri;
+        acc = fmaf(wr, ri, acc);
+        if (PC) acz = fmaf(wr, zi, acz);
     }
     const double bs = double(block_sumf(acc));
+    const double bz = PC ? double(block_sumf(acz)) : 0.0;
+    if (PC && threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = bz;
     if (publish_and_check_last(partials, bs, &si->ticket[kTicketMisc])) {
         const double tot = sum_partials(partials, gridDim.x);
+        const double trz = PC ? sum_partials(partials + gridDim.x, gridDim.x) : tot;
         if (threadIdx.x == 0) {
             si->ticket[kTicketMisc] = 0;
-            si->rho = tot;
+            si->rho = trz;
+            si->rr = tot;
             si->rho0 = tot;
             double tau = so->bnorm > 0.0 && so->rho > 0.0 ? so->rtol * so->bnorm / sqrt(so->rho) : 0.0;
             si->tau = tau > so->inner_rtol ? tau : so->inner_rtol;
@@ -835,12 +859,14 @@ __global__ void __launch_bounds__(kBlock) k_inner_init(int64_t N, const double *
 // r32 <- r32 - alpha q32 and its share of (r32, r32)_w (products and block
 // sums in FP32).  A warp covers the 128 entries of flag group i >> 5 (float4
 // per lane); groups without interface copies skip the weights.
+template <bool PC>
 __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
                                                        const uint8_t *__restrict__ mult,
                                                        const float *__restrict__ wtab,
                                                        const uint8_t *__restrict__ gflag128, const double *part_pq,
                                                        int G1, double *part_rr, Scal *si, const Scal *so,
-                                                       cudaGraphConditionalHandle h, int use_cond) {
+                                                       cudaGraphConditionalHandle h, int use_cond,
+                                                       const float *__restrict__ dinv32, double *part_rz) {
     pdl_enter();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         si->rho_b = si->rho;
@@ -860,23 +886,25 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
     }
     const double alpha_d = si->rho / pq;
     const float alpha = float(alpha_d);
-    float acc = 0.f;
+    float acc = 0.f, acz = 0.f;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N4 = N >> 2;
     float4 *__restrict__ r4 = reinterpret_cast<float4 *>(r);
     const float4 *__restrict__ q4 = reinterpret_cast<const float4 *>(q);
     const uchar4 *__restrict__ m4 = reinterpret_cast<const uchar4 *>(mult);
+    const float4 *__restrict__ z4 = reinterpret_cast<const float4 *>(dinv32);
     struct Ld {
-        float4 r, q;
+        float4 r, q, d;
         uint8_t g;
     };
-    stream_loop<4>(
+    stream_loop<PC ? 2 : 4>(
         (int64_t)blockIdx.x * kBlock + threadIdx.x, N4, stride,
         [&](int64_t i) {
             Ld l;
             l.r = r4[i];
             l.q = __ldcs(q4 + i);
             l.g = __ldg(gflag128 + (i >> 5));
+            if (PC) l.d = __ldg(z4 + i);
             return l;
         },
         [&](int64_t i, Ld l) {
@@ -886,28 +914,42 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
             rv.z = fmaf(-alpha, l.q.z, rv.z);
             rv.w = fmaf(-alpha, l.q.w, rv.w);
             r4[i] = rv;
+            float4 w = make_float4(1.f, 1.f, 1.f, 1.f);
+            if (l.g != 0) {
+                const uchar4 mv = m4[i];
+                w = make_float4(__ldg(wtab + mv.x), __ldg(wtab + mv.y), __ldg(wtab + mv.z), __ldg(wtab + mv.w));
+            }
             if (l.g == 0) {
                 acc = fmaf(rv.x, rv.x, acc);
                 acc = fmaf(rv.y, rv.y, acc);
                 acc = fmaf(rv.z, rv.z, acc);
                 acc = fmaf(rv.w, rv.w, acc);
             } else {
-                const uchar4 mv = m4[i];
-                acc = fmaf(__ldg(wtab + mv.x) * rv.x, rv.x, acc);
-                acc = fmaf(__ldg(wtab + mv.y) * rv.y, rv.y, acc);
-                acc = fmaf(__ldg(wtab + mv.z) * rv.z, rv.z, acc);
-                acc = fmaf(__ldg(wtab + mv.w) * rv.w, rv.w, acc);
+                acc = fmaf(w.x * rv.x, rv.x, acc);
+                acc = fmaf(w.y * rv.y, rv.y, acc);
+                acc = fmaf(w.z * rv.z, rv.z, acc);
+                acc = fmaf(w.w * rv.w, rv.w, acc);
+            }
+            if (PC) {
+                acz = fmaf(w.x * rv.x, rv.x * l.d.x, acz);
+                acz = fmaf(w.y * rv.y, rv.y * l.d.y, acz);
+                acz = fmaf(w.z * rv.z, rv.z * l.d.z, acz);
+                acz = fmaf(w.w * rv.w, rv.w * l.d.w, acz);
             }
         });
     if (blockIdx.x == 0 && threadIdx.x < (N & 3)) {
         const int64_t i = (N & ~int64_t(3)) + threadIdx.x;
         const float ri = fmaf(-alpha, q[i], r[i]);
         r[i] = ri;
-        acc = fmaf(__ldg(wtab + mult[i]) * ri, ri, acc);
+        const float wi = __ldg(wtab + mult[i]) * ri;
+        acc = fmaf(wi, ri, acc);
+        if (PC) acz = fmaf(wi, ri * dinv32[i], acz);
     }
     const double bs = double(block_sumf(acc));
+    const double bz = PC ? double(block_sumf(acz)) : 0.0;
     if (threadIdx.x == 0) {
         part_rr[blockIdx.x] = bs;
+        if (PC) part_rz[blockIdx.x] = bz;
         if (blockIdx.x == 0) {
             si->alpha = alpha_d;
             si->alpha32 = alpha;
@@ -921,15 +963,18 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
 // block 0 records the iteration and the inner stopping decision
 // (sqrt(rho) <= tau sqrt(rho0), or the inner iterations summed over
 // refinements reach max_iter).
+template <bool PC>
 __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t N, float *__restrict__ d, float *__restrict__ p,
                                                         const float *__restrict__ r, const double *part_rr, int G2,
                                                         Scal *si, Scal *so, cudaGraphConditionalHandle h,
-                                                        int use_cond) {
+                                                        int use_cond, const float *__restrict__ dinv32,
+                                                        const double *part_rz) {
     pdl_enter();
     const int k = si->iter_b;
     if (si->brk || si->halt[k & 1]) return;
     const double rr = all_sum_partials(part_rr, G2);
-    const double beta_d = rr / si->rho_b;
+    const double rz = PC ? all_sum_partials(part_rz, G2) : rr;
+    const double beta_d = rz / si->rho_b;
     const float alpha = si->alpha32, beta = float(beta_d);
     const int total1 = si->total_b + 1;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
@@ -937,8 +982,9 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t
     float4 *__restrict__ d4 = reinterpret_cast<float4 *>(d);
     float4 *__restrict__ p4 = reinterpret_cast<float4 *>(p);
     const float4 *__restrict__ r4 = reinterpret_cast<const float4 *>(r);
+    const float4 *__restrict__ z4 = reinterpret_cast<const float4 *>(dinv32);
     struct Ld {
-        float4 p, d, r;
+        float4 p, d, z;
     };
     stream_loop<2>(
         (int64_t)blockIdx.x * kBlock + threadIdx.x, N4, stride,
@@ -946,28 +992,36 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t
             Ld l;
             l.p = p4[i];
             l.d = d4[i];
-            l.r = r4[i];
+            l.z = r4[i];
+            if (PC) {
+                const float4 dv = __ldg(z4 + i);
+                l.z.x *= dv.x;
+                l.z.y *= dv.y;
+                l.z.z *= dv.z;
+                l.z.w *= dv.w;
+            }
             return l;
         },
         [&](int64_t i, Ld l) {
             float4 dv = l.d;
-            const float4 pv = l.p, rv = l.r;
+            const float4 pv = l.p, zv = l.z;
             dv.x = fmaf(alpha, pv.x, dv.x);
             dv.y = fmaf(alpha, pv.y, dv.y);
             dv.z = fmaf(alpha, pv.z, dv.z);
             dv.w = fmaf(alpha, pv.w, dv.w);
             d4[i] = dv;
-            p4[i] = make_float4(fmaf(beta, pv.x, rv.x), fmaf(beta, pv.y, rv.y), fmaf(beta, pv.z, rv.z),
-                                fmaf(beta, pv.w, rv.w));
+            p4[i] = make_float4(fmaf(beta, pv.x, zv.x), fmaf(beta, pv.y, zv.y), fmaf(beta, pv.z, zv.z),
+                                fmaf(beta, pv.w, zv.w));
         });
     if (blockIdx.x == 0 && threadIdx.x < (N & 3)) {
         const int64_t i = (N & ~int64_t(3)) + threadIdx.x;
         const float pi = p[i];
         d[i] = fmaf(alpha, pi, d[i]);
-        p[i] = fmaf(beta, pi, r[i]);
+        p[i] = fmaf(beta, pi, PC ? r[i] * dinv32[i] : r[i]);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        si->rho = rr;
+        si->rho = rz;
+        si->rr = rr;
         si->beta = beta_d;
         si->beta32 = beta;
         si->iter = k + 1;

@@ -28,6 +28,7 @@ SSG_E_TIMEOUT = 6
 SSG_FP64 = 0
 SSG_MIXED = 1
 SSG_FP64_JACOBI = 2
+SSG_MIXED_JACOBI = 3
 SSG_DRIVER_GRAPH = 0
 SSG_DRIVER_HOST = 1
 
@@ -50,6 +51,7 @@ EXPORTS = (
     "ssg_gather",
     "ssg_spmv_assembled",
     "ssg_spmv_assembled_f32",
+    "ssg_autotune",
     "ssg_spmm_assembled",
     "ssg_spmm_assembled_f32",
     "ssg_wdot",
@@ -92,6 +94,23 @@ class ssg_stats(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ssg_tune(C.Structure):
+    _fields_ = [
+        ("fp64_choice", C.c_int32),
+        ("fp32_choice", C.c_int32),
+        ("fp64_blocks_per_sm", C.c_int32 * 4),
+        ("fp64_l2_ahead", C.c_int32 * 4),
+        ("fp32_blocks_per_sm", C.c_int32 * 4),
+        ("fp32_l2_ahead", C.c_int32 * 4),
+        ("fp64_us", C.c_double * 4),
+        ("fp32_us", C.c_double * 4),
+    ]
+
+    def as_dict(self):
+        return {f: (list(getattr(self, f)) if not isinstance(getattr(self, f), int) else getattr(self, f))
+                for f, _ in self._fields_}
 
 
 class SSGError(RuntimeError):
@@ -143,6 +162,7 @@ def lib():
         L.ssg_spmv_assembled_f32.argtypes = [vp, vp, vp, vp]
         L.ssg_wdot.argtypes = [vp, vp, vp, vp]
         L.ssg_spmm_assembled.argtypes = [vp, i32, vp, vp]
+        L.ssg_autotune.argtypes = [vp, i32, C.POINTER(ssg_tune)]
         L.ssg_set_values.argtypes = [vp, vp]
         L.ssg_pattern_grad.argtypes = [vp, i32, vp, vp, vp]
         L.ssg_fv7_values.argtypes = [vp, i32, i32, i32, vp, vp]
@@ -332,6 +352,12 @@ def ssg_spmv_assembled_f32(sys, x_loc, y_loc, xSx=None):
         lib().ssg_spmv_assembled_f32(sys, _dev_f32(x_loc), _dev_f32(y_loc), None if xSx is None else _dev_f64(xSx)),
         "ssg_spmv_assembled_f32",
     )
+
+
+def ssg_autotune(sys, reps=20):
+    t = ssg_tune()
+    _check(lib().ssg_autotune(sys, reps, C.byref(t)), "ssg_autotune")
+    return t.as_dict()
 
 
 def ssg_spmm_assembled(sys, k, x_loc, y_loc):
@@ -542,6 +568,10 @@ class System:
         out = self._empty_loc() if out is None else out
         ssg_spmv_assembled(self.h, x_loc, out, xSx)
         return out
+
+    def autotune(self, reps=20):
+        """Pick the fastest single-vector SpMV instances for this system."""
+        return ssg_autotune(self.h, reps)
 
     def spmm(self, x_loc, out=None):
         """Product with k vectors: x_loc is an (nloc, k) CUDA tensor (row-major,

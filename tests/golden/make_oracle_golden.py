@@ -3,8 +3,9 @@
 The full 128^3 finite-volume workload (4x4x4 boxes, kappa = exp(g),
 g ~ N(0,1), x* ~ U[-1,1], b = A x*) solved by the oracle's sub-structured CG
 (Algorithm 3, M = I) to a recursive relative residual of 1e-8 and of 1e-12, the
-mixed-precision refinement (FP32 inner CG, FP64 residuals) to 1e-8, and
-Algorithm 3 with the diagonal preconditioner to 1e-8.  Stored per solve: the
+mixed-precision refinement (FP32 inner CG, FP64 residuals) to 1e-8,
+Algorithm 3 with the diagonal preconditioner to 1e-8, and the refinement with
+diagonal-preconditioned inner solves to 1e-8.  Stored per solve: the
 iteration count, final residuals, the Lanczos condition estimate (M = I) and
 the solution at 4096 seeded sample indices.  Calls only oracle/ and synth/;
 takes about three minutes of one CPU core.
@@ -29,14 +30,17 @@ from synth import config_problem  # noqa: E402
 OUT = os.path.join(HERE, "oracle_fv3d_128_4x4x4.json")
 
 
-def main(parts=("cg", "mixed", "jacobi")):
+ALL = ("cg", "mixed", "jacobi", "mixed_jacobi")
+
+
+def main(parts=ALL):
     p = config_problem(2)
     part = oracle.Partition(p.A, p.part, p.P)
     b = p.b[:, 0]
     idx = np.sort(np.random.default_rng(2108).choice(p.A.n, 4096, replace=False))
     rec = {"workload": p.name, "n": p.A.n, "nnz": p.A.nnz, "sample_seed": 2108, "sample_idx": idx.tolist(),
            "solves": []}
-    if set(parts) != {"cg", "mixed", "jacobi"} and os.path.exists(OUT):
+    if set(parts) != set(ALL) and os.path.exists(OUT):
         with open(OUT) as f:
             old = json.load(f)
         assert old["sample_idx"] == rec["sample_idx"]
@@ -77,6 +81,22 @@ def main(parts=("cg", "mixed", "jacobi")):
             "oracle_seconds_one_core": dt,
         }
         print("jacobi: %d iterations, %.1f s" % (r.iters, dt))
+    if "mixed_jacobi" in parts:
+        t0 = time.time()
+        r = part.pcg_mixed(b, 1e-8, 100000, 1e-4, 30)
+        dt = time.time() - t0
+        assert r.status == oracle.OK
+        rec["mixed_jacobi"] = {
+            "rtol": 1e-8,
+            "inner_rtol": 1e-4,
+            "iters": r.iters,
+            "outer": r.outer,
+            "relres": r.relres,
+            "err_vs_xstar": float(np.linalg.norm(r.x - p.xstar[:, 0]) / np.linalg.norm(p.xstar[:, 0])),
+            "sample_x": [float(v) for v in r.x[idx]],
+            "oracle_seconds_one_core": dt,
+        }
+        print("mixed jacobi: %d inner iterations, %d refinements, %.1f s" % (r.iters, r.outer, dt))
     with open(OUT, "w") as f:
         json.dump(rec, f)
     print("wrote %s" % OUT)
@@ -102,4 +122,4 @@ def mixed(p, part, b, idx, rec):
 
 
 if __name__ == "__main__":
-    main(tuple(sys.argv[1:]) or ("cg", "mixed", "jacobi"))
+    main(tuple(sys.argv[1:]) or ALL)

@@ -159,3 +159,43 @@ def test_jacobi_full_size_128cube(ctx):
     idx = np.array(g["sample_idx"])
     assert _rel(xg[idx], np.array(gj["sample_x"])) <= 2 * kap * 1e-8
     assert st[0]["true_relres"] <= 1.01e-8
+
+
+@pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
+def test_mixed_jacobi_matches_oracle(ctx, name, case):
+    """SSG_MIXED_JACOBI against or_sub_pcg_mixed: refinements within +-1, inner
+    iterations within max(3 per refinement, 5 %), FP64 true residual <= rtol."""
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    A, part, P, b = _unpack(case)
+    S = System(ctx, A, part, P)
+    ref = oracle.Partition(A, part, P)
+    rm = ref.pcg_mixed(b, 1e-8, 100000, 1e-4, 30)
+    x, rc, st = S.solve(_t(b), rtol=1e-8, max_iter=100000, mode=ssg.SSG_MIXED_JACOBI)
+    assert rc == ssg.SSG_OK and rm.status == oracle.OK
+    tr = np.linalg.norm(b - oracle.spmv(A, x.cpu().numpy())) / np.linalg.norm(b)
+    assert tr <= 1.0001e-8
+    assert abs(st[0]["outer"] - rm.outer) <= 1
+    assert abs(st[0]["iters"] - rm.iters) <= max(3 * rm.outer, 0.05 * rm.iters)
+
+
+def test_mixed_jacobi_full_size_128cube(ctx):
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_fv3d_128_4x4x4.json")) as f:
+        g = json.load(f)
+    gm = g["mixed_jacobi"]
+    kap = [s for s in g["solves"] if s["rtol"] == 1e-8][0]["kappa_lanczos"]
+    p = config_problem(2)
+    S = System(ctx, p.A, p.part, p.P)
+    x, rc, st = S.solve(_t(p.b[:, 0]), rtol=1e-8, max_iter=100000, mode=ssg.SSG_MIXED_JACOBI)
+    assert rc == ssg.SSG_OK
+    print("mixed jacobi 128^3: %d inner (oracle %d), %d refinements (oracle %d)" % (
+        st[0]["iters"], gm["iters"], st[0]["outer"], gm["outer"]))
+    assert abs(st[0]["outer"] - gm["outer"]) <= 1
+    assert abs(st[0]["iters"] - gm["iters"]) <= max(3 * gm["outer"], 0.05 * gm["iters"])
+    idx = np.array(g["sample_idx"])
+    assert _rel(x.cpu().numpy()[idx], np.array(gm["sample_x"])) <= 2 * kap * 1e-8
+    assert st[0]["true_relres"] <= 1.0001e-8

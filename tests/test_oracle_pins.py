@@ -615,10 +615,11 @@ def test_mixed_true_residual_and_manufactured(scale):
 
 MIXED_MUTATIONS = {
     # the outer residual is not recomputed after the correction
-    "stale_outer_residual": ("        or_sub_spmv(h, xl, q);\n        for (int64_t k = 0; k < L; ++k) r[k] = bl[k] - q[k];\n        rho = or_wdot(h, r, r);\n        ++outer;",
-                             "        ++outer;"),
+    "stale_outer_residual": ("(double)d32[k];\n        or_sub_spmv(h, xl, q);\n        for (int64_t k = 0; k < L; ++k) r[k] = bl[k] - q[k];\n        rho = or_wdot(h, r, r);\n        ++outer;\n        if (sqrt(rho) <= rtol * bnorm) status = OR_OK;\n        else if (broke) status = OR_BREAKDOWN;\n    }\n    or_gather(h, xl, x);\n    *iters_out = total;\n    *outer_out = outer;\n    *relres_out = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;\n    free(bl); free(xl); free(r); free(q); free(val32);",
+                             "(double)d32[k];\n        ++outer;\n        if (sqrt(rho) <= rtol * bnorm) status = OR_OK;\n        else if (broke) status = OR_BREAKDOWN;\n    }\n    or_gather(h, xl, x);\n    *iters_out = total;\n    *outer_out = outer;\n    *relres_out = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;\n    free(bl); free(xl); free(r); free(q); free(val32);"),
     # the correction is dropped
-    "no_correction": ("for (int64_t k = 0; k < L; ++k) xl[k] = xl[k] + (double)d32[k];", ""),
+    "no_correction": ("            rho32 = rho_new;\n            ++total;\n        }\n        for (int64_t k = 0; k < L; ++k) xl[k] = xl[k] + (double)d32[k];",
+                      "            rho32 = rho_new;\n            ++total;\n        }\n"),
 }
 
 
@@ -633,6 +634,64 @@ def test_mixed_planted_mistake_is_caught(name):
         with oracle.use_library(path):
             try:
                 test_mixed_true_residual_and_manufactured(16)
+            except AssertionError:
+                caught = True
+    finally:
+        os.remove(path)
+    assert caught, "planted mistake %s slipped through" % name
+
+
+# ---------------------------------------------------------------- mixed precision with the diagonal preconditioner
+def pin_pcg_mixed():
+    """Diagonal S with b exactly in FP32: every inner solve ends after one
+    iteration; on the heterogeneous FV problem the refinement reaches the FP64
+    true residual <= rtol, recovers x* within 2 kappa rtol, and its inner
+    solves need fewer iterations than the unpreconditioned ones."""
+    rng = np.random.default_rng(8)
+    n = 80
+    d = rng.uniform(0.5, 20.0, n)
+    Dg = CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), d)
+    b = np.float32(rng.uniform(-1, 1, n)).astype(np.float64)
+    r = oracle.Partition(Dg, (np.arange(n) % 4).astype(np.int32), 4).pcg_mixed(b, 1e-12, 100, 1e-4, 10)
+    assert r.status == oracle.OK and r.outer <= 3 and r.iters == r.outer
+    p = config_problem(2, scale=20)
+    b = p.b[:, 0]
+    Pt = oracle.Partition(p.A, p.part, p.P)
+    rm = Pt.pcg_mixed(b, 1e-8, 100000, 1e-4, 30)
+    assert rm.status == oracle.OK
+    tr = np.linalg.norm(b - oracle.spmv(p.A, rm.x)) / np.linalg.norm(b)
+    assert tr <= 1.0001e-8
+    r64 = Pt.cg(b, 1e-8, 100000)
+    kap = oracle.cond_from_lanczos(r64.alpha, r64.beta)
+    assert np.linalg.norm(rm.x - p.xstar[:, 0]) / np.linalg.norm(p.xstar[:, 0]) <= 2 * kap * 1e-8
+    assert rm.iters < 0.7 * Pt.cg_mixed(b, 1e-8, 100000, 1e-4, 30).iters
+
+
+def test_pcg_mixed_pins():
+    pin_pcg_mixed()
+
+
+PCG_MIXED_MUTATIONS = {
+    # z = M r instead of M^-1 r in the inner solves
+    "inner_times_diag": ("            for (int64_t k = 0; k < L; ++k) z32[k] = r32[k] / g32[k];\n            const double rz_new",
+                         "            for (int64_t k = 0; k < L; ++k) z32[k] = r32[k] * g32[k];\n            const double rz_new"),
+    # the inner direction built from r instead of z
+    "inner_direction_from_r": ("for (int64_t k = 0; k < L; ++k) p32[k] = z32[k] + beta * p32[k];",
+                               "for (int64_t k = 0; k < L; ++k) p32[k] = r32[k] + beta * p32[k];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PCG_MIXED_MUTATIONS))
+def test_pcg_mixed_planted_mistake_is_caught(name):
+    old, new = PCG_MIXED_MUTATIONS[name]
+    src = oracle.source_text()
+    assert src.count(old) == 1, name
+    path = oracle.compile_variant(src.replace(old, new), name)
+    caught = False
+    try:
+        with oracle.use_library(path):
+            try:
+                pin_pcg_mixed()
             except AssertionError:
                 caught = True
     finally:
