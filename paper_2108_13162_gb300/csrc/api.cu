@@ -379,9 +379,9 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
         W.seg_blk[sg + 1] = W.seg_blk[sg] + gs;
     }
     W.gridB = W.seg_blk[nseg];
-    // vector-kernel chunks: about num_sms * kVecBlocksPerSM in all, a multiple
-    // of 64 entries, at least one per segment
-    const int64_t ch = std::max<int64_t>(64, (M.nloc / (num_sms * kVecBlocksPerSM) + 63) / 64 * 64);
+    // vector-kernel chunks: about one per SM in all, a multiple of 64
+    // entries, at least one per segment
+    const int64_t ch = std::max<int64_t>(64, (M.nloc / num_sms + 63) / 64 * 64);
     W.seg_chunk.assign(static_cast<size_t>(nseg) + 1, 0);
     for (int sg = 0; sg < nseg; ++sg) {
         const int64_t e0 = M.off[seg_sub[sg]], e1 = M.off[seg_sub[sg + 1]];
@@ -1093,7 +1093,7 @@ template <int K>
 int launch_initB(ssg_system *S, cudaStream_t st, double *p, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
     // q holds S x_1 when a guess was given, else zeros (set before the loop)
-    k_residualB<K><<<S->nchunks, kBlock, 0, st>>>(B.bl, B.q, B.r, p, S->op.mult, S->op.wtab, B.part_a, S->tab, 1, 1);
+    k_residualB<K><<<S->nchunks, kBlockV, 0, st>>>(B.bl, B.q, B.r, p, S->op.mult, S->op.wtab, B.part_a, S->tab, 1, 1);
     k_init_finB<K><<<S->nseg, kBlock, 0, st>>>(B.part_a, S->nchunks, S->tab, B.so);
     k_seg_cond<<<1, kBlock, 0, st>>>(B.so, S->nseg, B.so + S->nseg, nullptr, 1, h, use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
@@ -1104,9 +1104,9 @@ template <int K>
 int launch_bodyB64(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
     k_spmm_seg<double, K, true><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(S->opB64, B.p, B.q, B.part_a, S->tab, B.so);
-    k_update_rB<K><<<S->nchunks, kBlock, 0, st>>>(B.q, B.r, S->op.mult, S->op.wtab, S->op.gflag, B.part_a, B.part_b,
+    k_update_rB<K><<<S->nchunks, kBlockV, 0, st>>>(B.q, B.r, S->op.mult, S->op.wtab, S->op.gflag, B.part_a, B.part_b,
                                                   S->tab, B.so);
-    k_update_xpB<K><<<S->nchunks, kBlock, 0, st>>>(B.xl, B.p, B.r, B.part_b, S->tab, B.so);
+    k_update_xpB<K><<<S->nchunks, kBlockV, 0, st>>>(B.xl, B.p, B.r, B.part_b, S->tab, B.so);
     k_seg_cond<<<1, kBlock, 0, st>>>(B.so, S->nseg, B.so + S->nseg, nullptr, 0, h, use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
@@ -1115,7 +1115,7 @@ int launch_bodyB64(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h,
 template <int K>
 int launch_inner_initB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
-    k_inner_initB<K><<<S->nchunks, kBlock, 0, st>>>(B.r, B.r32, B.p32, B.d32, S->op.mult, S->op.wtab32, B.part_a,
+    k_inner_initB<K><<<S->nchunks, kBlockV, 0, st>>>(B.r, B.r32, B.p32, B.d32, S->op.mult, S->op.wtab32, B.part_a,
                                                     S->tab);
     k_inner_finB<K><<<S->nseg, kBlock, 0, st>>>(B.part_a, S->tab, B.si, B.so);
     k_seg_cond<<<1, kBlock, 0, st>>>(B.si, S->nseg, B.si + S->nseg, nullptr, 1, h, use_cond);
@@ -1128,9 +1128,9 @@ int launch_inner_bodyB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandl
     ssg_system::BlockState &B = S->blk;
     k_spmm_seg<float, K, true><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(S->opB32, B.p32, B.q32, B.part_a, S->tab,
                                                                         B.si);
-    k_update_r32B<K><<<S->nchunks, kBlock, 0, st>>>(B.q32, B.r32, S->op.mult, S->op.wtab32, S->op.gflag128,
+    k_update_r32B<K><<<S->nchunks, kBlockV, 0, st>>>(B.q32, B.r32, S->op.mult, S->op.wtab32, S->op.gflag128,
                                                     B.part_a, B.part_b, S->tab, B.si);
-    k_update_dp32B<K><<<S->nchunks, kBlock, 0, st>>>(B.d32, B.p32, B.r32, B.part_b, S->tab, B.si, B.so);
+    k_update_dp32B<K><<<S->nchunks, kBlockV, 0, st>>>(B.d32, B.p32, B.r32, B.part_b, S->tab, B.si, B.so);
     k_seg_cond<<<1, kBlock, 0, st>>>(B.si, S->nseg, B.si + S->nseg, B.so + S->nseg, 0, h, use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
@@ -1142,7 +1142,7 @@ int launch_outer_tailB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandl
     const int64_t N = S->maps.nloc;
     k_ir_correct<<<grid_for(N * K, S->ctx->num_sms), kBlock, 0, st>>>(N * K, B.xl, B.d32);
     k_spmm_seg<double, K, false><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(S->opB64, B.xl, B.q, nullptr, S->tab, B.so);
-    k_residualB<K><<<S->nchunks, kBlock, 0, st>>>(B.bl, B.q, B.r, nullptr, S->op.mult, S->op.wtab, B.part_a, S->tab,
+    k_residualB<K><<<S->nchunks, kBlockV, 0, st>>>(B.bl, B.q, B.r, nullptr, S->op.mult, S->op.wtab, B.part_a, S->tab,
                                                   1, 0);
     k_outer_finB<K><<<S->nseg, kBlock, 0, st>>>(B.part_a, S->tab, B.so, B.si, 0);
     k_seg_cond<<<1, kBlock, 0, st>>>(B.so, S->nseg, B.so + S->nseg, nullptr, 0, h, use_cond);
@@ -1293,10 +1293,10 @@ int solve_block(ssg_system *S, int nr_single, const double *b_glob, double *x_gl
     SSG_CUDA_TRY(cudaEventRecord(S->ev0, s));
     k_set_paramsB<<<1, kBlock, 0, s>>>(B.so, S->nseg, rtol, max_iter, guess, C->inner_rtol, C->max_outer,
                                        const_cast<int32_t *>(S->tab.nrhs), nr_single);
-    k_scatterB<K><<<S->nchunks, kBlock, 0, s>>>(S->d_l2g, b_glob, B.bl, S->tab);
+    k_scatterB<K><<<S->nchunks, kBlockV, 0, s>>>(S->d_l2g, b_glob, B.bl, S->tab);
     launches += 2;
     if (guess) {
-        k_scatterB<K><<<S->nchunks, kBlock, 0, s>>>(S->d_l2g, x_glob, B.xl, S->tab);
+        k_scatterB<K><<<S->nchunks, kBlockV, 0, s>>>(S->d_l2g, x_glob, B.xl, S->tab);
         k_spmm_seg<double, K, false><<<S->grid_spmmB, kSpmvThreads, 0, s>>>(S->opB64, B.xl, B.q, nullptr, S->tab,
                                                                              nullptr);
         launches += 2;
@@ -1307,11 +1307,11 @@ int solve_block(ssg_system *S, int nr_single, const double *b_glob, double *x_gl
     SSG_CUDA_TRY(cudaGetLastError());
     rc = run_blockB<K>(S, mode, &launches);
     if (rc != SSG_OK) return rc;
-    k_gatherB<K><<<S->nchunks, kBlock, 0, s>>>(S->d_l2g, S->d_own, B.xl, x_glob, S->tab);
+    k_gatherB<K><<<S->nchunks, kBlockV, 0, s>>>(S->d_l2g, S->d_own, B.xl, x_glob, S->tab);
     // true residuals ||b_j - S x_j||_w in FP64
     k_spmm_seg<double, K, false><<<S->grid_spmmB, kSpmvThreads, 0, s>>>(S->opB64, B.xl, B.q, nullptr, S->tab,
                                                                          nullptr);
-    k_residualB<K><<<S->nchunks, kBlock, 0, s>>>(B.bl, B.q, nullptr, nullptr, S->op.mult, S->op.wtab, B.part_a,
+    k_residualB<K><<<S->nchunks, kBlockV, 0, s>>>(B.bl, B.q, nullptr, nullptr, S->op.mult, S->op.wtab, B.part_a,
                                                  S->tab, 1, 0);
     k_outer_finB<K><<<S->nseg, kBlock, 0, s>>>(B.part_a, S->tab, B.so, B.si, 1);
     launches += 4;

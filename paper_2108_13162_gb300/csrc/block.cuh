@@ -30,6 +30,11 @@
 namespace ssg {
 
 constexpr int kMaxRhs = 16;
+// Threads per block of the chunk kernels (one chunk of local entries per
+// block, about one block per SM): every block sums its segment's partials of
+// the previous kernel in FP64 (2 DFMA/clk/SM on this part), so fewer, larger
+// chunks keep that sum small next to the chunk's own streaming.
+constexpr int kBlockV = 1024;
 
 // State of K solves, resident on the device.  Bit j of `act` is set while
 // column j still iterates.
@@ -417,10 +422,10 @@ __global__ void __launch_bounds__(kSpmvThreads, SpmmTraits<T>::kBlocksPerSM)
 // accumulators are combined as a fixed tree, then the lanes by a fixed
 // shuffle tree.  Result in tot[K] (shared), valid after the call in every
 // thread.
-template <int K>
+template <int K, int NT = kBlockV>
 __device__ __forceinline__ void seg_sum_cols(const double *partials, int b0, int b1, double *tot) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int j = warp; j < K; j += kBlock / 32) {
+    for (int j = warp; j < K; j += NT / 32) {
         double a[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) a[u] = 0.0;
@@ -445,14 +450,14 @@ __device__ __forceinline__ void seg_sum_cols(const double *partials, int b0, int
 // block's sums go to out[0..K).
 template <int K, int VW, typename A>
 __device__ __forceinline__ void block_cols_sum(const A (&acc)[VW], double *out) {
-    __shared__ A red[kBlock * VW];
+    __shared__ A red[kBlockV * VW];
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < VW; ++u) red[threadIdx.x * VW + u] = acc[u];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int kPer = kBlock * VW / K;  // entries per column
-    for (int j = warp; j < K; j += kBlock / 32) {
+    constexpr int kPer = kBlockV * VW / K;  // entries per column
+    for (int j = warp; j < K; j += kBlockV / 32) {
         A v = A(0);
         for (int i = lane; i < kPer; i += 32) v += red[i * K + j];
 #pragma unroll
@@ -484,7 +489,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_cond(const ScalB *segs, int nseg
 // segment (a column with (p, S p)_w <= 0 stops with a breakdown),
 // r_j <- r_j - alpha_j q_j over the chunk and its partials of (r_j, r_j)_w.
 template <int K>
-__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_rB(const double *__restrict__ q, double *__restrict__ r,
+__global__ void __launch_bounds__(kBlockV, 1) k_update_rB(const double *__restrict__ q, double *__restrict__ r,
                                                       const uint8_t *__restrict__ mult,
                                                       const double *__restrict__ wtab,
                                                       const uint8_t *__restrict__ gflag, const double *part_pq,
@@ -534,7 +539,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_rB(const dou
         uint8_t g;
     };
     stream_loop<4>(
-        (int64_t)ch.y * K / 2 + threadIdx.x, (int64_t)ch.z * K / 2, kBlock,
+        (int64_t)ch.y * K / 2 + threadIdx.x, (int64_t)ch.z * K / 2, kBlockV,
         [&](int64_t i) {
             Ld l;
             l.r = r2[i];
@@ -564,7 +569,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_rB(const dou
 // beta_j p_j (alpha = beta = 0 for frozen columns); the segment's first chunk
 // records each column's iteration and stopping decision.
 template <int K>
-__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_xpB(double *__restrict__ x, double *__restrict__ p,
+__global__ void __launch_bounds__(kBlockV, 1) k_update_xpB(double *__restrict__ x, double *__restrict__ p,
                                                        const double *__restrict__ r, const double *part_rr,
                                                        SegTab tab, ScalB *segs) {
     __shared__ double tot[K];
@@ -596,7 +601,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_xpB(double *
         double2 p, x, r;
     };
     stream_loop<4>(
-        (int64_t)ch.y * K / 2 + threadIdx.x, (int64_t)ch.z * K / 2, kBlock,
+        (int64_t)ch.y * K / 2 + threadIdx.x, (int64_t)ch.z * K / 2, kBlockV,
         [&](int64_t i) {
             Ld l;
             l.p = p2[i];
@@ -641,7 +646,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_xpB(double *
 // nullptr this is the FP64 residual of the refinement; with r == nullptr
 // only the norms are formed (the true residual at the end of a solve).
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_residualB(const double *__restrict__ b, const double *__restrict__ q,
+__global__ void __launch_bounds__(kBlockV, 1) k_residualB(const double *__restrict__ b, const double *__restrict__ q,
                                                       double *__restrict__ r, double *__restrict__ p,
                                                       const uint8_t *__restrict__ mult,
                                                       const double *__restrict__ wtab, double *part, SegTab tab,
@@ -653,7 +658,7 @@ __global__ void __launch_bounds__(kBlock) k_residualB(const double *__restrict__
     double2 *r2 = reinterpret_cast<double2 *>(r);
     double2 *p2 = reinterpret_cast<double2 *>(p);
     const int64_t i1 = (int64_t)ch.z * K / 2;
-    for (int64_t i = (int64_t)ch.y * K / 2 + threadIdx.x; i < i1; i += kBlock) {
+    for (int64_t i = (int64_t)ch.y * K / 2 + threadIdx.x; i < i1; i += kBlockV) {
         const double2 bv = b2[i];
         double2 rv = bv;
         if (use_q) {
@@ -698,8 +703,8 @@ __global__ void __launch_bounds__(kBlock) k_init_finB(const double *part, int nc
     __shared__ double rr[K], bb[K];
     const int sg = blockIdx.x;
     ScalB *s = segs + sg;
-    seg_sum_cols<K>(part, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rr);
-    seg_sum_cols<K>(part + (size_t)nchunks * K, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], bb);
+    seg_sum_cols<K, kBlock>(part, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rr);
+    seg_sum_cols<K, kBlock>(part + (size_t)nchunks * K, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], bb);
     if (threadIdx.x == 0) {
         const int nr = tab.nrhs[sg];
         uint32_t act = 0;
@@ -740,7 +745,7 @@ __global__ void __launch_bounds__(kBlock) k_init_finB(const double *part, int nc
 // Inner setup, one block per chunk: r32 = (float) r64, p32 = r32, d32 = 0 and
 // the chunk's partials of (r32, r32)_w (FP32 products and block sums).
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_inner_initB(const double *__restrict__ r64, float *__restrict__ r32,
+__global__ void __launch_bounds__(kBlockV, 1) k_inner_initB(const double *__restrict__ r64, float *__restrict__ r32,
                                                         float *__restrict__ p32, float *__restrict__ d32,
                                                         const uint8_t *__restrict__ mult,
                                                         const float *__restrict__ wtab, double *part, SegTab tab) {
@@ -751,7 +756,7 @@ __global__ void __launch_bounds__(kBlock) k_inner_initB(const double *__restrict
     float2 *pp2 = reinterpret_cast<float2 *>(p32);
     float2 *dd2 = reinterpret_cast<float2 *>(d32);
     const int64_t i1 = (int64_t)ch.z * K / 2;
-    for (int64_t i = (int64_t)ch.y * K / 2 + threadIdx.x; i < i1; i += kBlock) {
+    for (int64_t i = (int64_t)ch.y * K / 2 + threadIdx.x; i < i1; i += kBlockV) {
         const double2 rv = r2[i];
         const float2 f = make_float2(float(rv.x), float(rv.y));
         rr2[i] = f;
@@ -770,7 +775,7 @@ template <int K>
 __global__ void __launch_bounds__(kBlock) k_inner_finB(const double *part, SegTab tab, ScalB *si, const ScalB *so) {
     __shared__ double rr[K];
     const int sg = blockIdx.x;
-    seg_sum_cols<K>(part, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rr);
+    seg_sum_cols<K, kBlock>(part, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rr);
     if (threadIdx.x == 0) {
         ScalB *i = si + sg;
         const ScalB *o = so + sg;
@@ -798,7 +803,7 @@ __global__ void __launch_bounds__(kBlock) k_inner_finB(const double *part, SegTa
 // (alpha formed in FP64 from the FP64 sums of the partials, then rounded to
 // FP32 once).
 template <int K>
-__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32B(const float *__restrict__ q, float *__restrict__ r,
+__global__ void __launch_bounds__(kBlockV, 1) k_update_r32B(const float *__restrict__ q, float *__restrict__ r,
                                                         const uint8_t *__restrict__ mult,
                                                         const float *__restrict__ wtab,
                                                         const uint8_t *__restrict__ gflag128, const double *part_pq,
@@ -853,7 +858,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32B(const f
         uint8_t g;
     };
     stream_loop<4>(
-        (int64_t)ch.y * K / VW + threadIdx.x, (int64_t)ch.z * K / VW, kBlock,
+        (int64_t)ch.y * K / VW + threadIdx.x, (int64_t)ch.z * K / VW, kBlockV,
         [&](int64_t i) {
             Ld l;
             if constexpr (VW == 4) {
@@ -896,7 +901,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32B(const f
 // (sqrt(rho_j) <= tau_j sqrt(rho0_j), or its inner iterations summed reach
 // max_iter).
 template <int K>
-__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32B(float *__restrict__ d, float *__restrict__ p,
+__global__ void __launch_bounds__(kBlockV, 1) k_update_dp32B(float *__restrict__ d, float *__restrict__ p,
                                                          const float *__restrict__ r, const double *part_rr,
                                                          SegTab tab, ScalB *si, ScalB *so) {
     constexpr int VW = K >= 4 ? 4 : 2;
@@ -930,7 +935,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32B(float 
         float p[VW], d[VW], r[VW];
     };
     stream_loop<2>(
-        (int64_t)ch.y * K / VW + threadIdx.x, (int64_t)ch.z * K / VW, kBlock,
+        (int64_t)ch.y * K / VW + threadIdx.x, (int64_t)ch.z * K / VW, kBlockV,
         [&](int64_t i) {
             Ld l;
             if constexpr (VW == 4) {
@@ -990,7 +995,7 @@ __global__ void __launch_bounds__(kBlock) k_outer_finB(const double *part, SegTa
                                                        int final_) {
     __shared__ double rr[K];
     const int sg = blockIdx.x;
-    seg_sum_cols<K>(part, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rr);
+    seg_sum_cols<K, kBlock>(part, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rr);
     if (threadIdx.x != 0) return;
     ScalB *o = so + sg;
     if (final_) {
@@ -1026,13 +1031,13 @@ __global__ void __launch_bounds__(kBlock) k_outer_finB(const double *part, SegTa
 // rhs_off[sg] + j * n_sg, node g of the segment at offset g - node_off[sg];
 // columns nrhs..K-1 of the block are zero.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_scatterB(const int32_t *__restrict__ l2g, const double *__restrict__ xg,
+__global__ void __launch_bounds__(kBlockV, 1) k_scatterB(const int32_t *__restrict__ l2g, const double *__restrict__ xg,
                                                      double *__restrict__ xl, SegTab tab) {
     const int4 ch = tab.chunk[blockIdx.x];
     const int sg = ch.x;
     const int nr = tab.nrhs[sg];
     const int64_t n0 = tab.node_off[sg], ns = tab.node_off[sg + 1] - n0, ro = tab.rhs_off[sg];
-    for (int64_t e = (int64_t)ch.y * K + threadIdx.x; e < (int64_t)ch.z * K; e += kBlock) {
+    for (int64_t e = (int64_t)ch.y * K + threadIdx.x; e < (int64_t)ch.z * K; e += kBlockV) {
         const int64_t i = e / K;
         const int j = (int)(e % K);
         xl[e] = j < nr ? __ldg(xg + ro + j * ns + (l2g[i] - n0)) : 0.0;
@@ -1041,14 +1046,14 @@ __global__ void __launch_bounds__(kBlock) k_scatterB(const int32_t *__restrict__
 
 // Owner copies of the local blocks -> global right-hand-side layout.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_gatherB(const int32_t *__restrict__ l2g, const int32_t *__restrict__ own,
+__global__ void __launch_bounds__(kBlockV, 1) k_gatherB(const int32_t *__restrict__ l2g, const int32_t *__restrict__ own,
                                                     const double *__restrict__ xl, double *__restrict__ xg,
                                                     SegTab tab) {
     const int4 ch = tab.chunk[blockIdx.x];
     const int sg = ch.x;
     const int nr = tab.nrhs[sg];
     const int64_t n0 = tab.node_off[sg], ns = tab.node_off[sg + 1] - n0, ro = tab.rhs_off[sg];
-    for (int64_t e = (int64_t)ch.y * K + threadIdx.x; e < (int64_t)ch.z * K; e += kBlock) {
+    for (int64_t e = (int64_t)ch.y * K + threadIdx.x; e < (int64_t)ch.z * K; e += kBlockV) {
         const int64_t i = e / K;
         const int j = (int)(e % K);
         if (j >= nr) continue;
