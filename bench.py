@@ -70,6 +70,8 @@ def parse_args(argv=None):
                     help="only build the workload and launch the SpMV --spmv-reps times (for ncu); no JSON line")
     ap.add_argument("--no-multi-rhs", action="store_true",
                     help="skip the 16-right-hand-side measurement (96^3 FV, reported beside the headline)")
+    ap.add_argument("--no-fe", action="store_true",
+                    help="skip the 1024^2 P1 finite-element workload (256 RCB subdomains, autotuned SpMV)")
     ap.add_argument("--batch", choices=("off", "small", "full"), default="small",
                     help="many independent systems in one launch, reported beside the headline: small = 512 "
                          "systems of side 32..128, full = 512 of side 32..512 (several minutes of host setup)")
@@ -413,6 +415,41 @@ def bench_batch(ctx, stream, reps, size):
     return out
 
 
+def bench_fe(ctx, stream, reps):
+    """Workload 3: P1 finite elements on the jittered 1024^2 mesh, 256 uneven
+    RCB subdomains: the SpMV instances chosen by ssg_autotune for this
+    irregular system, then time to 1e-8 in FP64, mixed and mixed + Jacobi."""
+    import torch
+
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+    from synth import config_problem
+
+    p = config_problem(3)
+    S = System(ctx, p.A, p.part, p.P)
+    tune = S.autotune(reps=20)
+    b = torch.from_numpy(p.b[:, 0].copy()).cuda()
+    out = {"workload": "fe2d_p1_jittered_1024^2_rcb256", "n": p.A.n, "nnz": p.A.nnz, "subdomains": p.P,
+           "nloc": S.sizes.nloc, "rtol": RTOL, "autotune": tune}
+    for name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED), ("mixed_jacobi", ssg.SSG_MIXED_JACOBI)):
+        x, rc, st = S.solve(b, rtol=RTOL, mode=mode)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            x, rc, st = S.solve(b, rtol=RTOL, mode=mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rc != ssg.SSG_OK:
+            raise RuntimeError("FE solve did not converge")
+        out[name + "_s"] = e0.elapsed_time(e1) / 1e3 / reps
+        out[name + "_iters"] = st[0]["iters"]
+        out[name + "_true_relres"] = st[0]["true_relres"]
+    S.close()
+    return out
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -423,12 +460,28 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def spmv_source_sha256():
+    """sha256 of the SpMV kernel's own source: the regions of kernels.cuh
+    between the [spmv-source-begin] / [spmv-source-end] markers, joined."""
+    text = open(KERNEL_SOURCE).read()
+    parts = []
+    pos = 0
+    while True:
+        a = text.find("[spmv-source-begin]", pos)
+        if a < 0:
+            break
+        b = text.index("[spmv-source-end]", a)
+        parts.append(text[a:b])
+        pos = b
+    return hashlib.sha256("".join(parts).encode()).hexdigest()
+
+
 def profiled_traffic(prec="fp64"):
     """Per-launch DRAM bytes from the committed ncu summary, only if the
     kernel source is unchanged since the counters were taken."""
     try:
         text = open(PROFILE_RECORDS[prec]).read()
-        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+        src = spmv_source_sha256()
     except OSError:
         return None
     rec = {}
@@ -653,6 +706,9 @@ def run_ours(args, dist):
     multi = None
     if not args.no_multi_rhs:
         multi = bench_multi_rhs(ctx, stream, max(1, min(args.steps, 3)), args.spmv_reps)
+    fe = None
+    if not args.no_fe:
+        fe = bench_fe(ctx, stream, max(1, min(args.steps, 3)))
     batch = None
     if args.batch != "off":
         batch = bench_batch(ctx, stream, max(1, min(args.steps, 3)), args.batch)
@@ -714,6 +770,7 @@ def run_ours(args, dist):
         "cpu_baseline": cpu,
         "multi_rhs": multi,
         "batch": batch,
+        "fe2d": fe,
     }
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
