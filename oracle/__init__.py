@@ -129,6 +129,14 @@ def _bind(L):
         L.or_sub_pcg_mixed.restype = C.c_int
         L.or_cholesky_solve.argtypes = [C.c_int32, _f64p, _f64p, _f64p]
         L.or_cholesky_solve.restype = C.c_int
+        i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+        vp = C.c_void_p
+        for f in (L.or_band_row, L.or_band_col):
+            f.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_int32, C.c_int32, i64p, vp, vp, vp]
+            f.restype = C.c_int
+        for f in (L.or_band_row_spmv, L.or_band_col_spmv):
+            f.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_int32, _f64p, _f64p]
+            f.restype = C.c_int
     return L
 
 
@@ -366,6 +374,50 @@ def _sub_pcg_mixed(self, b, rtol, max_iter, inner_rtol=1e-4, max_outer=30, x0=No
 
 
 Partition.pcg_mixed = _sub_pcg_mixed
+
+
+@dataclass
+class Band:
+    """Band p of a band-row (Algorithm 1) or band-column (Algorithm 2)
+    splitting: an np x n (row) or n x np (column) CSR matrix starting at
+    row / column ``displ`` of A."""
+
+    kind: str
+    p: int
+    np: int
+    displ: int
+    rowptr: np.ndarray
+    colidx: np.ndarray
+    val: np.ndarray
+
+
+def band(A, kind, nb, p) -> Band:
+    """Band p of nb (0-based) of the band-row (kind "row", or_band_row) or
+    band-column (kind "col", or_band_col) splitting of A."""
+    f = lib().or_band_row if kind == "row" else lib().or_band_col
+    args = (A.n, _c(A.rowptr, np.int32), _c(A.colidx, np.int32), _c(A.val, np.float64), int(nb), int(p))
+    sz = np.zeros(3, np.int64)
+    if f(*args, sz, None, None, None) != OK:
+        raise ValueError("oracle band splitting rejected the input")
+    npr, displ, nz = (int(v) for v in sz)
+    rows = npr if kind == "row" else A.n
+    br = np.zeros(rows + 1, np.int32)
+    bc = np.zeros(max(nz, 1), np.int32)
+    bv = np.zeros(max(nz, 1), np.float64)
+    f(*args, sz, br.ctypes.data, bc.ctypes.data, bv.ctypes.data)
+    return Band(kind, int(p), npr, displ, br, bc[:nz].copy(), bv[:nz].copy())
+
+
+def band_spmv(A, kind, nb, x):
+    """y = A x through the band-row or band-column splitting with nb bands
+    (or_band_row_spmv / or_band_col_spmv)."""
+    f = lib().or_band_row_spmv if kind == "row" else lib().or_band_col_spmv
+    y = np.zeros(A.n, np.float64)
+    st = f(A.n, _c(A.rowptr, np.int32), _c(A.colidx, np.int32), _c(A.val, np.float64), int(nb),
+           _c(x, np.float64), y)
+    if st != OK:
+        raise ValueError("oracle band product rejected the input (status %d)" % st)
+    return y
 
 
 def cholesky_solve(Adense, b):

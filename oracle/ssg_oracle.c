@@ -24,6 +24,10 @@
  *   or_wdot          the interface-weighted dot of Section 3.4.2, w = 1/m.
  *   or_sub_cg        Algorithm 3 with the sub-structured SpMV and weighted dots.
  *   or_cholesky_solve  textbook dense Cholesky (second opinion on tiny systems).
+ *   or_band_row, or_band_col  the band-row and band-column splittings of
+ *                    Sections 2.1 and 2.2 (Algorithms 1 and 2), one band at a time.
+ *   or_band_row_spmv, or_band_col_spmv  y = A x through either splitting: each
+ *                    band's block of y, or the sum of the bands' partial products.
  *
  * Readings where the paper is silent (no tolerance, no initial guess, no
  * weights, no rule for splitting an assembled S_33) are stated at each function.
@@ -1028,4 +1032,139 @@ done:
     free(bl); free(xl); free(r); free(q); free(dl); free(val32); free(r32); free(z32); free(p32); free(q32);
     free(d32); free(g32);
     return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Band splittings (Section 2.1 Algorithm 1, Section 2.2 Algorithm 2). */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Extent of band p of nb: q = floor(n / nb) rows (Algorithm 1) or columns
+ * (Algorithm 2) per band, the last band taking the rest, n - (nb-1) q.
+ * Reading: bands are numbered 0..nb-1 (the listing mixes 1- and 0-based
+ * numbering); 0 < nb <= n.  Returns OR_INVALID otherwise.
+ */
+static int band_extent(int32_t n, int32_t nb, int32_t p, int32_t *np, int32_t *displ) {
+    if (n <= 0 || nb <= 0 || nb > n || p < 0 || p >= nb) return OR_INVALID;
+    const int32_t q = n / nb;
+    *displ = p * q;
+    *np = (p == nb - 1) ? n - p * q : q;
+    return OR_OK;
+}
+
+/*
+ * Algorithm 1, band-row splitting: band p holds rows [displ, displ + N_p) of
+ * A as an N_p x n CSR matrix.  Its row pointers are A's, shifted so that the
+ * band starts at 0; its column ids (global, 0..n-1) and values are A's
+ * entries of those rows, copied in order.  sizes[0..2] = N_p, displ,
+ * nnz_count.  brow (N_p + 1), bcol and bval (nnz_count) may be NULL to query
+ * the sizes only.
+ */
+int or_band_row(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, int32_t nb,
+                int32_t p, int64_t *sizes, int32_t *brow, int32_t *bcol, double *bval) {
+    int32_t np, displ;
+    if (band_extent(n, nb, p, &np, &displ) != OR_OK) return OR_INVALID;
+    const int32_t nnz_displ = rowptr[displ];
+    const int32_t nnz_count = rowptr[displ + np] - nnz_displ;
+    sizes[0] = np;
+    sizes[1] = displ;
+    sizes[2] = nnz_count;
+    if (brow) {
+        for (int32_t i = 0; i <= np; ++i) brow[i] = rowptr[displ + i] - nnz_displ;
+        for (int32_t k = 0; k < nnz_count; ++k) {
+            bcol[k] = colidx[nnz_displ + k];
+            bval[k] = val[nnz_displ + k];
+        }
+    }
+    return OR_OK;
+}
+
+/*
+ * Algorithm 2, band-column splitting: band p holds columns [displ, displ +
+ * N_p) of A as an n x N_p CSR matrix: every row of A, keeping (in order) the
+ * entries whose column lies in the band, with the column id shifted by displ
+ * (reading: the listing's column offset is the band's first column, and its
+ * inner loop runs over row i of A).  sizes as for or_band_row; brow has n + 1
+ * entries.
+ */
+int or_band_col(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, int32_t nb,
+                int32_t p, int64_t *sizes, int32_t *brow, int32_t *bcol, double *bval) {
+    int32_t np, displ;
+    if (band_extent(n, nb, p, &np, &displ) != OR_OK) return OR_INVALID;
+    int64_t c = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        if (brow) brow[i] = (int32_t)c;
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            if (displ <= colidx[k] && colidx[k] < displ + np) {
+                if (brow) {
+                    bcol[c] = colidx[k] - displ;
+                    bval[c] = val[k];
+                }
+                ++c;
+            }
+        }
+    }
+    if (brow) brow[n] = (int32_t)c;
+    sizes[0] = np;
+    sizes[1] = displ;
+    sizes[2] = c;
+    return OR_OK;
+}
+
+/*
+ * y = A x through the band-row splitting: every band multiplies its rows by
+ * the whole of x (rows in order, each summed left to right) and writes its
+ * block y[displ .. displ + N_p).
+ */
+int or_band_row_spmv(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, int32_t nb,
+                     const double *x, double *y) {
+    for (int32_t p = 0; p < nb; ++p) {
+        int64_t sz[3];
+        if (or_band_row(n, rowptr, colidx, val, nb, p, sz, NULL, NULL, NULL) != OR_OK) return OR_INVALID;
+        int32_t *br = (int32_t *)malloc(sizeof(int32_t) * (size_t)(sz[0] + 1));
+        int32_t *bc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(sz[2] > 0 ? sz[2] : 1));
+        double *bv = (double *)malloc(sizeof(double) * (size_t)(sz[2] > 0 ? sz[2] : 1));
+        if (!br || !bc || !bv) {
+            free(br); free(bc); free(bv);
+            return OR_OOM;
+        }
+        or_band_row(n, rowptr, colidx, val, nb, p, sz, br, bc, bv);
+        or_spmv((int32_t)sz[0], br, bc, bv, x, y + sz[1]);
+        free(br); free(bc); free(bv);
+    }
+    return OR_OK;
+}
+
+/*
+ * y = A x through the band-column splitting: band p forms the partial
+ * product y_p = A_p x[displ .. displ + N_p) (n entries, each row summed left
+ * to right), and y is the sum of the partials taken in ascending p, starting
+ * from zero (reading: the paper does not give the order in which the bands'
+ * contributions are summed; one fixed order makes the result reproducible).
+ */
+int or_band_col_spmv(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val, int32_t nb,
+                     const double *x, double *y) {
+    double *yp = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!yp) return OR_OOM;
+    for (int32_t i = 0; i < n; ++i) y[i] = 0.0;
+    for (int32_t p = 0; p < nb; ++p) {
+        int64_t sz[3];
+        if (or_band_col(n, rowptr, colidx, val, nb, p, sz, NULL, NULL, NULL) != OR_OK) {
+            free(yp);
+            return OR_INVALID;
+        }
+        int32_t *br = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+        int32_t *bc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(sz[2] > 0 ? sz[2] : 1));
+        double *bv = (double *)malloc(sizeof(double) * (size_t)(sz[2] > 0 ? sz[2] : 1));
+        if (!br || !bc || !bv) {
+            free(br); free(bc); free(bv); free(yp);
+            return OR_OOM;
+        }
+        or_band_col(n, rowptr, colidx, val, nb, p, sz, br, bc, bv);
+        or_spmv(n, br, bc, bv, x + sz[1], yp);
+        for (int32_t i = 0; i < n; ++i) y[i] += yp[i];
+        free(br); free(bc); free(bv);
+    }
+    free(yp);
+    return OR_OK;
 }
