@@ -70,6 +70,10 @@ def parse_args(argv=None):
                     help="only build the workload and launch the SpMV --spmv-reps times (for ncu); no JSON line")
     ap.add_argument("--no-multi-rhs", action="store_true",
                     help="skip the 16-right-hand-side measurement (96^3 FV, reported beside the headline)")
+    ap.add_argument("--no-bands", action="store_true",
+                    help="skip the band-row / band-column comparison operators and global CG")
+    ap.add_argument("--profile-band", choices=("row", "col"), default=None,
+                    help="only run the band product of the 128^3 matrix (64 bands) spmv-reps times (for ncu)")
     ap.add_argument("--no-fe", action="store_true",
                     help="skip the 1024^2 P1 finite-element workload (256 RCB subdomains, autotuned SpMV)")
     ap.add_argument("--batch", choices=("off", "small", "full"), default="small",
@@ -450,6 +454,72 @@ def bench_fe(ctx, stream, reps):
     return out
 
 
+def band_algorithmic_bytes(n, nnz, nb=0):
+    """y = A x on global CSR: values and column ids once (12 B per entry), row
+    pointers, x and y once each (band-column: plus its band boundaries)."""
+    return 12 * nnz + 4 * (n + 1) + 8 * n + 8 * n
+
+
+def time_band(B, x, y, stream, reps):
+    import torch
+
+    from paper_2108_13162_gb300 import ssg
+
+    ssg.ssg_band_spmv(B.h, x, y)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ssg.ssg_band_spmv(B.h, x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def bench_bands(ctx, stream, prob, reps, spmv_reps):
+    """The paper's other splittings as comparison operators on the 128^3
+    matrix, 64 bands (as many as subdomains): band-row and band-column
+    products (autotuned kernel, CUDA events, matrix larger than L2), and
+    plain global CG (one subdomain) to 1e-8 in FP64 and mixed precision."""
+    import numpy as np
+    import torch
+
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import Band, System
+
+    A = prob.A
+    peak, _ = measured_peaks()
+    x = torch.from_numpy(np.random.default_rng(5).uniform(-1, 1, A.n)).cuda()
+    y = torch.empty_like(x)
+    nbytes = band_algorithmic_bytes(A.n, A.nnz)
+    out = {"bands": 64, "algorithmic_bytes": nbytes}
+    for name, kind in (("row", ssg.SSG_BAND_ROW), ("col", ssg.SSG_BAND_COL)):
+        B = Band(ctx, A, kind, 64)
+        tune = B.autotune(reps=10)
+        t = time_band(B, x, y, stream, spmv_reps)
+        out[name] = {"variant": tune["variant"], "rule_variant": tune["rule_variant"], "variants_us": tune["us"],
+                     "launch_us": t * 1e6, "achieved_gbs": nbytes / t / 1e9, "frac": nbytes / t / 1e9 / peak}
+        B.close()
+    S1 = System(ctx, A, np.zeros(A.n, np.int32), 1)
+    b = torch.from_numpy(prob.b[:, 0].copy()).cuda()
+    for name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED)):
+        xg, rc, st = S1.solve(b, rtol=RTOL, mode=mode)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            xg, rc, st = S1.solve(b, rtol=RTOL, mode=mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["global_cg_%s_s" % name] = e0.elapsed_time(e1) / 1e3 / reps
+        out["global_cg_%s_iters" % name] = st[0]["iters"]
+    out["global_cg_spmv_us"] = time_spmv(S1, "fp64", stream, spmv_reps) * 1e6
+    S1.close()
+    return out
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -607,6 +677,16 @@ def run_ours(args, dist):
         ctx.close()
         return 0
     prob = make_workload()
+    if args.profile_band:
+        from paper_2108_13162_gb300.ssg import Band
+
+        B = Band(ctx, prob.A, ssg.SSG_BAND_ROW if args.profile_band == "row" else ssg.SSG_BAND_COL, 64)
+        xb = torch.from_numpy(prob.b[:, 0].copy()).cuda()
+        t = time_band(B, xb, torch.empty_like(xb), stream, args.spmv_reps)
+        print("band-%s product: %.1f us (rule variant)" % (args.profile_band, t * 1e6))
+        B.close()
+        ctx.close()
+        return 0
     if args.profile_spmv:
         S = System(ctx, prob.A, prob.part, prob.P)
         time_spmv(S, args.profile_spmv, stream, args.spmv_reps)
@@ -709,6 +789,9 @@ def run_ours(args, dist):
     fe = None
     if not args.no_fe:
         fe = bench_fe(ctx, stream, max(1, min(args.steps, 3)))
+    bands = None
+    if not args.no_bands:
+        bands = bench_bands(ctx, stream, prob, max(1, min(args.steps, 3)), args.spmv_reps)
     batch = None
     if args.batch != "off":
         batch = bench_batch(ctx, stream, max(1, min(args.steps, 3)), args.batch)
@@ -771,6 +854,7 @@ def run_ours(args, dist):
         "multi_rhs": multi,
         "batch": batch,
         "fe2d": fe,
+        "splittings": bands,
     }
     if dist.rank == 0:
         print(json.dumps(line), flush=True)

@@ -51,11 +51,9 @@ extern "C" {
 /* solve modes */
 #define SSG_FP64 0  /* Algorithm 3 in FP64 throughout */
 #define SSG_MIXED 1 /* FP32 inner CG inside FP64 iterative refinement */
-#define SSG_FP64_JACOBI 2 /* Algorithm 3 with the diagonal preconditioner M = diag(S) of the   \
-                             paper's experiments (Section 3.1), FP64; right-hand sides solved \
-                             one after another */
-#define SSG_MIXED_JACOBI 3 /* SSG_MIXED with the diagonal preconditioner in the FP32 inner solves;  \
-                              right-hand sides solved one after another */
+#define SSG_FP64_JACOBI 2  /* Algorithm 3 with the diagonal preconditioner M = diag(S) of the \
+                              paper's experiments (Section 3.1), FP64 */
+#define SSG_MIXED_JACOBI 3 /* SSG_MIXED with the diagonal preconditioner in the FP32 inner solves */
 
 /* driver modes (ssg_set_driver) */
 #define SSG_DRIVER_GRAPH 0 /* one CUDA-graph launch per solve, device-side while loop */
@@ -189,8 +187,9 @@ int ssg_partition_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off,
                         const int32_t *part, ssg_system **sys);
 /*
  * Solve every system of a batch for its right-hand sides in one graph
- * launch: each (system, right-hand side) runs its own Algorithm 3 (SSG_FP64)
- * or its own refinement (SSG_MIXED) with the readings of ssg_solve; the
+ * launch: each (system, right-hand side) runs its own Algorithm 3 (SSG_FP64,
+ * SSG_FP64_JACOBI) or its own refinement (SSG_MIXED, SSG_MIXED_JACOBI) with
+ * the readings of ssg_solve; the
  * columns of all systems iterate together (K = the power of two >= the
  * largest sys_nrhs), a finished system's blocks return at once.  b and x
  * (device, rhs_off[nsys] doubles each, caller-allocated: the library cannot
@@ -385,6 +384,68 @@ int ssg_system_destroy(ssg_system *sys);
  */
 int ssg_wdot_noalloc(const double *u_loc, const double *v_loc, const uint8_t *mult_loc, int64_t nloc,
                      double *result_dev, void *stream);
+
+/*
+ * Band splittings (Sections 2.1 and 2.2, Algorithms 1 and 2): the paper's
+ * two other ways of sharing a matrix among processors, kept here as
+ * comparison operators for the sub-structured product.  Band p of nb
+ * (0-based) covers q = floor(n / nb) rows (SSG_BAND_ROW) or columns
+ * (SSG_BAND_COL) starting at displ = p q; the last band takes the rest.
+ *   SSG_BAND_ROW: band p is the N_p x n CSR matrix of rows [displ, displ +
+ *     N_p): A's row pointers shifted to start at 0, A's global column ids and
+ *     values copied in order (Algorithm 1).  y = A x: each band writes its
+ *     block of y from the whole of x.
+ *   SSG_BAND_COL: band p is the n x N_p CSR matrix of the entries of every
+ *     row whose column lies in [displ, displ + N_p), column ids shifted by
+ *     displ (Algorithm 2; reading: the listing's column offset is the band's
+ *     first column).  y = A x is the sum of the bands' partial products
+ *     A_p x[displ .. displ + N_p), taken in ascending p (reading: the paper
+ *     gives no order for that sum; a fixed one keeps y reproducible).
+ * On one GPU every band lives in the same memory, so the device keeps A once
+ * (the bands of either splitting are row or column ranges of it) and one
+ * kernel computes all bands' products; each row's entries are summed left to
+ * right with fused multiply-adds, per band for SSG_BAND_COL.
+ *
+ * ssg_band_split: inputs (host, copied): A in 0-based CSR with columns sorted
+ *   and unique in each row (no symmetry needed; empty rows allowed), 1 <= nb
+ *   <= n.  SSG_E_INVALID otherwise.  Uploads A and the kernel's tile table.
+ * ssg_band_get: band p's sizes (sizes[0] = N_p, sizes[1] = displ, sizes[2] =
+ *   nnz of the band) and, when the pointers are not NULL, its CSR arrays into
+ *   caller host buffers (rowptr: N_p + 1 or n + 1 entries; colidx, val: nnz).
+ * ssg_band_spmv: y = A x through the band's splitting; x and y are device
+ *   vectors of n doubles (not overlapping), ordered on the context stream.
+ * ssg_band_set_variant: which kernel computes the product:
+ *   SSG_BAND_AUTO (the row-length rule: the staged kernel while the mean row
+ *   length is at most 8, the entries a staged tile holds per thread; else
+ *   lanes per row = the power of two >= half the mean row length, from 2 to
+ *   32; band-column: the staged kernel), SSG_BAND_STAGED (tiles of whole rows staged in shared
+ *   memory by bulk asynchronous copies, one thread per row: the left-to-right
+ *   order), 1 (one thread per row from global memory, left to right), or
+ *   2, 4, 8, 16, 32 lanes per row (strided partial sums, then a fixed
+ *   shuffle tree: same products, another summation order; SSG_BAND_ROW only).
+ * ssg_band_autotune: times every variant valid for the splitting (reps
+ *   launches each, CUDA events on the context stream), keeps the fastest and
+ *   reports each variant's mean time in microseconds (us[i] for variant
+ *   code[i], 0 where not valid).
+ */
+#define SSG_BAND_ROW 0
+#define SSG_BAND_COL 1
+#define SSG_BAND_AUTO 0
+#define SSG_BAND_STAGED (-1)
+typedef struct ssg_band ssg_band;
+typedef struct {
+    int32_t variant;      /* the variant now in use */
+    int32_t rule_variant; /* what SSG_BAND_AUTO picks for this matrix */
+    int32_t code[7];      /* SSG_BAND_STAGED, 1, 2, 4, 8, 16, 32 */
+    float us[7];
+} ssg_band_tune;
+int ssg_band_split(ssg_ctx *ctx, int32_t kind, int32_t n, const int32_t *rowptr, const int32_t *colidx,
+                   const double *val, int32_t nb, ssg_band **out);
+int ssg_band_get(const ssg_band *band, int32_t p, int64_t *sizes, int32_t *rowptr, int32_t *colidx, double *val);
+int ssg_band_spmv(ssg_band *band, const double *x, double *y);
+int ssg_band_set_variant(ssg_band *band, int32_t variant);
+int ssg_band_autotune(ssg_band *band, int32_t reps, ssg_band_tune *out);
+int ssg_band_destroy(ssg_band *band);
 
 const char *ssg_error_string(int status);
 const char *ssg_last_error(void);

@@ -17,6 +17,7 @@
 #include "adjoint.cuh"
 #include "block.cuh"
 #include "kernels.cuh"
+#include "ssg_ctx.h"
 #include "ssg_internal.h"
 
 namespace ssg {
@@ -27,18 +28,6 @@ void set_error(const std::string &msg) { g_last_error = msg; }
 }  // namespace ssg
 
 using namespace ssg;
-
-struct ssg_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int driver = SSG_DRIVER_GRAPH;
-    int num_sms = 0;
-    int live_systems = 0;  // systems created on this context and not yet destroyed
-    int pdl = 0;               // programmatic dependent launch inside the loop bodies (measured: off is faster)
-    double inner_rtol = 1e-4;  // SSG_MIXED: inner FP32 CG tolerance
-    int32_t max_outer = 30;    // SSG_MIXED: refinement steps cap
-    int32_t rhs_block = 16;    // right-hand sides solved together (1, 2, 4, 8 or 16)
-};
 
 struct ssg_system {
     ssg_ctx *ctx = nullptr;
@@ -111,7 +100,7 @@ struct ssg_system {
         float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
         double *bg = nullptr, *xg = nullptr;  // global staging for ssg_solve_host (n x kcap)
         ScalB *so = nullptr, *si = nullptr;  // [nseg + 1]: one state per segment, then the loop counters
-        BlockGraph g64[5], gmx[5];  // by log2 K
+        BlockGraph graph[4][5];  // by mode (SSG_FP64 .. SSG_MIXED_JACOBI) and log2 K
     } blk;
 };
 
@@ -1020,11 +1009,11 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
 int log2_of(int K) { return K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4; }
 
 void destroy_block_graphs(ssg_system *S) {
-    for (int i = 0; i < 5; ++i)
-        for (ssg_system::BlockGraph *G : {&S->blk.g64[i], &S->blk.gmx[i]}) {
-            if (G->exec) cudaGraphExecDestroy(G->exec);
-            if (G->g) cudaGraphDestroy(G->g);
-            *G = ssg_system::BlockGraph{};
+    for (auto &by_k : S->blk.graph)
+        for (ssg_system::BlockGraph &G : by_k) {
+            if (G.exec) cudaGraphExecDestroy(G.exec);
+            if (G.g) cudaGraphDestroy(G.g);
+            G = ssg_system::BlockGraph{};
         }
 }
 
@@ -1043,7 +1032,9 @@ int ensure_block(ssg_system *S, int K) {
     if (S->blk.kcap >= K) return SSG_OK;
     free_block(S);
     const int64_t N = S->maps.nloc, n = S->maps.n;
-    const int64_t gmax = std::max<int64_t>(S->grid_spmmB, 2 * static_cast<int64_t>(S->nchunks));
+    // part_a: the product's block partials, or up to three partial sets of the
+    // setup kernels; part_b: (r, r)_w and, with the preconditioner, (r, z)_w
+    const int64_t gmax = std::max<int64_t>(S->grid_spmmB, 3 * static_cast<int64_t>(S->nchunks));
     size_t total = 0;
     auto take = [&](size_t bytes) {
         const size_t o = total;
@@ -1055,7 +1046,7 @@ int ensure_block(ssg_system *S, int K) {
                  o_q = take(8 * NK);
     const size_t o_r32 = take(4 * NK), o_p32 = take(4 * NK), o_q32 = take(4 * NK), o_d32 = take(4 * NK);
     const size_t o_pa = take(sizeof(double) * static_cast<size_t>(gmax) * kMaxRhs);
-    const size_t o_pb = take(sizeof(double) * static_cast<size_t>(S->nchunks) * kMaxRhs);
+    const size_t o_pb = take(sizeof(double) * 2 * static_cast<size_t>(S->nchunks) * kMaxRhs);
     const size_t o_bg = take(8 * static_cast<size_t>(n) * K), o_xg = take(8 * static_cast<size_t>(n) * K);
     const size_t o_so = take(sizeof(ScalB) * (S->nseg + 1)), o_si = take(sizeof(ScalB) * (S->nseg + 1));
     void *mem = nullptr;
@@ -1089,48 +1080,50 @@ int ensure_block(ssg_system *S, int K) {
 
 // Partials: the K-vector product and the setup / residual / inner-setup
 // kernels write part_a, the residual updates part_b.
-template <int K>
+template <int K, bool PC>
 int launch_initB(ssg_system *S, cudaStream_t st, double *p, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
     // q holds S x_1 when a guess was given, else zeros (set before the loop)
-    k_residualB<K><<<S->nchunks, kBlockV, 0, st>>>(B.bl, B.q, B.r, p, S->op.mult, S->op.wtab, B.part_a, S->tab, 1, 1);
-    k_init_finB<K><<<S->nseg, kBlock, 0, st>>>(B.part_a, S->nchunks, S->tab, B.so);
+    k_residualB<K, PC><<<S->nchunks, kBlockV, 0, st>>>(B.bl, B.q, B.r, p, S->op.mult, S->op.wtab, B.part_a, S->tab, 1,
+                                                      1, S->d_dinv);
+    k_init_finB<K, PC><<<S->nseg, kBlock, 0, st>>>(B.part_a, S->nchunks, S->tab, B.so);
     k_seg_cond<<<1, kBlock, 0, st>>>(B.so, S->nseg, B.so + S->nseg, nullptr, 1, h, use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
 
-template <int K>
+template <int K, bool PC>
 int launch_bodyB64(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
     k_spmm_seg<double, K, true><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(S->opB64, B.p, B.q, B.part_a, S->tab, B.so);
-    k_update_rB<K><<<S->nchunks, kBlockV, 0, st>>>(B.q, B.r, S->op.mult, S->op.wtab, S->op.gflag, B.part_a, B.part_b,
-                                                  S->tab, B.so);
-    k_update_xpB<K><<<S->nchunks, kBlockV, 0, st>>>(B.xl, B.p, B.r, B.part_b, S->tab, B.so);
+    k_update_rB<K, PC><<<S->nchunks, kBlockV, 0, st>>>(B.q, B.r, S->op.mult, S->op.wtab, S->op.gflag, B.part_a,
+                                                      B.part_b, S->tab, B.so, S->d_dinv);
+    k_update_xpB<K, PC><<<S->nchunks, kBlockV, 0, st>>>(B.xl, B.p, B.r, B.part_b, S->tab, B.so, S->d_dinv);
     k_seg_cond<<<1, kBlock, 0, st>>>(B.so, S->nseg, B.so + S->nseg, nullptr, 0, h, use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
 
-template <int K>
+template <int K, bool PC>
 int launch_inner_initB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
-    k_inner_initB<K><<<S->nchunks, kBlockV, 0, st>>>(B.r, B.r32, B.p32, B.d32, S->op.mult, S->op.wtab32, B.part_a,
-                                                    S->tab);
-    k_inner_finB<K><<<S->nseg, kBlock, 0, st>>>(B.part_a, S->tab, B.si, B.so);
+    k_inner_initB<K, PC><<<S->nchunks, kBlockV, 0, st>>>(B.r, B.r32, B.p32, B.d32, S->op.mult, S->op.wtab32, B.part_a,
+                                                        S->tab, S->d_dinv32);
+    k_inner_finB<K, PC><<<S->nseg, kBlock, 0, st>>>(B.part_a, S->nchunks, S->tab, B.si, B.so);
     k_seg_cond<<<1, kBlock, 0, st>>>(B.si, S->nseg, B.si + S->nseg, nullptr, 1, h, use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
 
-template <int K>
+template <int K, bool PC>
 int launch_inner_bodyB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
     k_spmm_seg<float, K, true><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(S->opB32, B.p32, B.q32, B.part_a, S->tab,
                                                                         B.si);
-    k_update_r32B<K><<<S->nchunks, kBlockV, 0, st>>>(B.q32, B.r32, S->op.mult, S->op.wtab32, S->op.gflag128,
-                                                    B.part_a, B.part_b, S->tab, B.si);
-    k_update_dp32B<K><<<S->nchunks, kBlockV, 0, st>>>(B.d32, B.p32, B.r32, B.part_b, S->tab, B.si, B.so);
+    k_update_r32B<K, PC><<<S->nchunks, kBlockV, 0, st>>>(B.q32, B.r32, S->op.mult, S->op.wtab32, S->op.gflag128,
+                                                        B.part_a, B.part_b, S->tab, B.si, S->d_dinv32);
+    k_update_dp32B<K, PC><<<S->nchunks, kBlockV, 0, st>>>(B.d32, B.p32, B.r32, B.part_b, S->tab, B.si, B.so,
+                                                         S->d_dinv32);
     k_seg_cond<<<1, kBlock, 0, st>>>(B.si, S->nseg, B.si + S->nseg, B.so + S->nseg, 0, h, use_cond);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
@@ -1220,25 +1213,29 @@ int read_glob(ssg_system *S, const ScalB *src, ScalB *dst) {
     return SSG_OK;
 }
 
-template <int K>
-int run_blockB(ssg_system *S, int mode, int64_t *launches) {
+template <int K, bool PC>
+int run_blockB_pc(ssg_system *S, int mode, int64_t *launches) {
     ssg_ctx *C = S->ctx;
     cudaStream_t s = C->stream;
     ssg_system::BlockState &B = S->blk;
+    const bool mixed = mode == SSG_MIXED || mode == SSG_MIXED_JACOBI;
     int rc = SSG_OK;
     if (C->driver == SSG_DRIVER_GRAPH) {
-        ssg_system::BlockGraph &G = mode == SSG_MIXED ? B.gmx[log2_of(K)] : B.g64[log2_of(K)];
+        ssg_system::BlockGraph &G = B.graph[mode][log2_of(K)];
         if (!G.exec) {
-            if (mode == SSG_MIXED)
+            if (mixed)
                 rc = build_nested_graph(
-                    G, [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_initB<K>(S, c, nullptr, h, 1); },
-                    [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_inner_initB<K>(S, c, h, 1); },
-                    [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_inner_bodyB<K>(S, c, h, 1); },
+                    G,
+                    [&](cudaStream_t c, cudaGraphConditionalHandle h) {
+                        return launch_initB<K, false>(S, c, nullptr, h, 1);
+                    },
+                    [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_inner_initB<K, PC>(S, c, h, 1); },
+                    [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_inner_bodyB<K, PC>(S, c, h, 1); },
                     [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_outer_tailB<K>(S, c, h, 1); });
             else
                 rc = build_loop_graph(
-                    G, [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_initB<K>(S, c, B.p, h, 1); },
-                    [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_bodyB64<K>(S, c, h, 1); });
+                    G, [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_initB<K, PC>(S, c, B.p, h, 1); },
+                    [&](cudaStream_t c, cudaGraphConditionalHandle h) { return launch_bodyB64<K, PC>(S, c, h, 1); });
             if (rc != SSG_OK) return rc;
         }
         SSG_CUDA_TRY(cudaGraphLaunch(G.exec, s));
@@ -1246,34 +1243,40 @@ int run_blockB(ssg_system *S, int mode, int64_t *launches) {
     }
     ScalB ho{}, hi{};
     const ScalB *go = B.so + S->nseg, *gi = B.si + S->nseg;
-    if (mode != SSG_MIXED) {
-        rc = launch_initB<K>(S, s, B.p, 0, 0);
+    if (!mixed) {
+        rc = launch_initB<K, PC>(S, s, B.p, 0, 0);
         *launches += 3;
         for (; rc == SSG_OK;) {
             rc = read_glob(S, go, &ho);
             if (rc != SSG_OK || ho.done) break;
-            for (int i = 0; i < kHostChunk && rc == SSG_OK; ++i) rc = launch_bodyB64<K>(S, s, 0, 0);
+            for (int i = 0; i < kHostChunk && rc == SSG_OK; ++i) rc = launch_bodyB64<K, PC>(S, s, 0, 0);
             *launches += 4 * kHostChunk;
         }
         return rc;
     }
-    rc = launch_initB<K>(S, s, nullptr, 0, 0);
+    rc = launch_initB<K, false>(S, s, nullptr, 0, 0);
     *launches += 3;
     for (; rc == SSG_OK;) {
         rc = read_glob(S, go, &ho);
         if (rc != SSG_OK || ho.done) break;
-        rc = launch_inner_initB<K>(S, s, 0, 0);
+        rc = launch_inner_initB<K, PC>(S, s, 0, 0);
         *launches += 3;
         for (; rc == SSG_OK;) {
             rc = read_glob(S, gi, &hi);
             if (rc != SSG_OK || hi.done) break;
-            for (int i = 0; i < kHostChunk && rc == SSG_OK; ++i) rc = launch_inner_bodyB<K>(S, s, 0, 0);
+            for (int i = 0; i < kHostChunk && rc == SSG_OK; ++i) rc = launch_inner_bodyB<K, PC>(S, s, 0, 0);
             *launches += 4 * kHostChunk;
         }
         if (rc == SSG_OK) rc = launch_outer_tailB<K>(S, s, 0, 0);
         *launches += 5;
     }
     return rc;
+}
+
+template <int K>
+int run_blockB(ssg_system *S, int mode, int64_t *launches) {
+    return mode == SSG_FP64_JACOBI || mode == SSG_MIXED_JACOBI ? run_blockB_pc<K, true>(S, mode, launches)
+                                                               : run_blockB_pc<K, false>(S, mode, launches);
 }
 
 // All segments' right-hand sides at b_glob / x_glob (device; segment sg's
@@ -1283,7 +1286,13 @@ int run_blockB(ssg_system *S, int mode, int64_t *launches) {
 template <int K>
 int solve_block(ssg_system *S, int nr_single, const double *b_glob, double *x_glob, int guess, double rtol,
                 int32_t max_iter, int mode, ssg_stats *st) {
-    int rc = ensure_block(S, K);
+    const bool mixed = mode == SSG_MIXED || mode == SSG_MIXED_JACOBI;
+    int rc = SSG_OK;
+    if (mode == SSG_FP64_JACOBI || mode == SSG_MIXED_JACOBI) {
+        rc = check_diag(S);
+        if (rc != SSG_OK) return rc;
+    }
+    rc = ensure_block(S, K);
     if (rc != SSG_OK) return rc;
     ssg_ctx *C = S->ctx;
     cudaStream_t s = C->stream;
@@ -1324,7 +1333,7 @@ int solve_block(ssg_system *S, int nr_single, const double *b_glob, double *x_gl
     SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
     const ScalB &g = h[S->nseg];
     if (C->driver == SSG_DRIVER_GRAPH) {
-        if (mode == SSG_MIXED)  // init 3; per refinement inner init 3 + tail 5; 4 per inner loop iteration
+        if (mixed)  // init 3; per refinement inner init 3 + tail 5; 4 per inner loop iteration
             launches += 3 + 8 * static_cast<int64_t>(g.iter) + 4 * static_cast<int64_t>(g.loops);
         else
             launches += 3 + 4 * static_cast<int64_t>(g.iter);
@@ -1340,7 +1349,7 @@ int solve_block(ssg_system *S, int nr_single, const double *b_glob, double *x_gl
             ssg_stats &t = st[o];
             t.status = hs.status[j];
             t.iters = hs.iters[j];
-            t.outer = mode == SSG_MIXED ? hs.outer[j] : 1;
+            t.outer = mixed ? hs.outer[j] : 1;
             t.block = K;
             t.relres = hs.relres[j];
             t.true_relres = hs.bnorm[j] > 0.0 ? std::sqrt(hs.aux[j]) / hs.bnorm[j] : std::sqrt(hs.aux[j]);
@@ -1688,8 +1697,9 @@ int ssg_solve_batch(ssg_system *S, const double *b, double *x, int32_t x_is_gues
         set_error("not a batch of systems (use ssg_partition_batch)");
         return SSG_E_INVALID;
     }
-    if (!b || !x || !(rtol >= 0.0) || (mode != SSG_FP64 && mode != SSG_MIXED)) {
-        set_error("null b/x, negative rtol, or mode not SSG_FP64 / SSG_MIXED");
+    if (!b || !x || !(rtol >= 0.0) ||
+        (mode != SSG_FP64 && mode != SSG_MIXED && mode != SSG_FP64_JACOBI && mode != SSG_MIXED_JACOBI)) {
+        set_error("null b/x, negative rtol, or mode not SSG_FP64 / SSG_MIXED / SSG_FP64_JACOBI / SSG_MIXED_JACOBI");
         return SSG_E_INVALID;
     }
     int32_t nmax = 0;
@@ -1989,8 +1999,7 @@ int ssg_solve(ssg_system *S, int32_t k, const double *b, double *x, int32_t x_is
     if (max_iter <= 0) max_iter = S->maps.n;
     SSG_CUDA_TRY(cudaSetDevice(S->ctx->device));
     int first_bad = SSG_OK;
-    // the diagonal preconditioner runs one right-hand side at a time
-    const int kb = mode == SSG_FP64_JACOBI || mode == SSG_MIXED_JACOBI ? 1 : std::max(1, S->ctx->rhs_block);
+    const int kb = std::max(1, S->ctx->rhs_block);
     for (int32_t j = 0; j < k;) {
         const int nr = std::min<int>(k - j, kb);
         const size_t o = static_cast<size_t>(j) * S->maps.n;
@@ -2019,7 +2028,7 @@ int ssg_solve_host(ssg_system *S, int32_t k, const double *b_host, double *x_hos
         return SSG_E_INVALID;
     }
     cudaStream_t s = S->ctx->stream;
-    const int kb = mode == SSG_FP64_JACOBI || mode == SSG_MIXED_JACOBI ? 1 : std::max(1, S->ctx->rhs_block);
+    const int kb = std::max(1, S->ctx->rhs_block);
     int first_bad = SSG_OK;
     for (int32_t j = 0; j < k;) {
         const int nr = std::min<int>(k - j, kb);

@@ -39,7 +39,8 @@ constexpr int kBlockV = 1024;
 // State of K solves, resident on the device.  Bit j of `act` is set while
 // column j still iterates.
 struct ScalB {
-    double rho[kMaxRhs];     // (r, r)_w of the last completed iteration
+    double rho[kMaxRhs];     // (r, z)_w of the last completed iteration (z = r without a preconditioner)
+    double rrt[kMaxRhs];     // (r, r)_w of the last completed iteration: the stopping test
     double rho_b[kMaxRhs];   // rho as the residual update saw it
     double alpha[kMaxRhs];
     double pq[kMaxRhs];
@@ -487,13 +488,17 @@ __global__ void __launch_bounds__(kBlock) k_seg_cond(const ScalB *segs, int nseg
 // Algorithm 3 lines 3 and 5 for K columns (FP64), one block per chunk:
 // alpha_j = rho_j / (p_j, S p_j)_w for every active column of the chunk's
 // segment (a column with (p, S p)_w <= 0 stops with a breakdown),
-// r_j <- r_j - alpha_j q_j over the chunk and its partials of (r_j, r_j)_w.
-template <int K>
+// r_j <- r_j - alpha_j q_j over the chunk and its partials of (r_j, r_j)_w
+// at part_rr[chunk*K + j].  With the diagonal preconditioner (PC, dinv =
+// 1 / diag(S) per local entry, shared by the K columns) also the partials of
+// (r_j, z_j)_w, z = dinv r, at part_rr[(nchunks + chunk)*K + j].
+template <int K, bool PC = false>
 __global__ void __launch_bounds__(kBlockV, 1) k_update_rB(const double *__restrict__ q, double *__restrict__ r,
                                                       const uint8_t *__restrict__ mult,
                                                       const double *__restrict__ wtab,
                                                       const uint8_t *__restrict__ gflag, const double *part_pq,
-                                                      double *part_rr, SegTab tab, ScalB *segs) {
+                                                      double *part_rr, SegTab tab, ScalB *segs,
+                                                      const double *__restrict__ dinv = nullptr) {
     __shared__ double tot[K];
     __shared__ double alpha_s[K];
     const int4 ch = tab.chunk[blockIdx.x];
@@ -531,20 +536,22 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_rB(const double *__restri
     }
     const int j0 = (2 * threadIdx.x) % K;
     const double a0 = alpha_s[j0], a1 = alpha_s[j0 + 1];
-    double acc[2] = {0.0, 0.0};
+    double acc[2] = {0.0, 0.0}, acz[2] = {0.0, 0.0};
     double2 *__restrict__ r2 = reinterpret_cast<double2 *>(r);
     const double2 *__restrict__ q2 = reinterpret_cast<const double2 *>(q);
     struct Ld {
         double2 r, q;
+        double d;
         uint8_t g;
     };
-    stream_loop<4>(
+    stream_loop<PC ? 2 : 4>(
         (int64_t)ch.y * K / 2 + threadIdx.x, (int64_t)ch.z * K / 2, kBlockV,
         [&](int64_t i) {
             Ld l;
             l.r = r2[i];
             l.q = __ldcs(q2 + i);
             l.g = __ldg(gflag + (((2 * i) / K) >> 6));
+            if (PC) l.d = __ldg(dinv + (2 * i) / K);  // local entry of both values
             return l;
         },
         [&](int64_t i, Ld l) {
@@ -552,27 +559,34 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_rB(const double *__restri
             rv.x = fma(-a0, l.q.x, rv.x);
             rv.y = fma(-a1, l.q.y, rv.y);
             r2[i] = rv;
-            if (l.g == 0) {
-                acc[0] = fma(rv.x, rv.x, acc[0]);
-                acc[1] = fma(rv.y, rv.y, acc[1]);
-            } else {
+            // weight 1 (no lookup) in 64-entry groups without interface copies
+            double wx = rv.x, wy = rv.y;
+            if (l.g != 0) {
                 const double w = __ldg(wtab + mult[(2 * i) / K]);  // local entry of both values
-                acc[0] = fma(w * rv.x, rv.x, acc[0]);
-                acc[1] = fma(w * rv.y, rv.y, acc[1]);
+                wx = w * rv.x;
+                wy = w * rv.y;
+            }
+            acc[0] = fma(wx, rv.x, acc[0]);
+            acc[1] = fma(wy, rv.y, acc[1]);
+            if (PC) {
+                acz[0] = fma(wx, rv.x * l.d, acz[0]);
+                acz[1] = fma(wy, rv.y * l.d, acz[1]);
             }
         });
     block_cols_sum<K, 2>(acc, part_rr + (size_t)blockIdx.x * K);
+    if (PC) block_cols_sum<K, 2>(acz, part_rr + (size_t)(gridDim.x + blockIdx.x) * K);
 }
 
 // Algorithm 3 lines 4, 7, 8 for K columns (FP64), one block per chunk:
 // beta_j = (r_j, r_j)_w / rho_j, x_j <- x_j + alpha_j p_j, p_j <- r_j +
 // beta_j p_j (alpha = beta = 0 for frozen columns); the segment's first chunk
 // records each column's iteration and stopping decision.
-template <int K>
+template <int K, bool PC = false>
 __global__ void __launch_bounds__(kBlockV, 1) k_update_xpB(double *__restrict__ x, double *__restrict__ p,
                                                        const double *__restrict__ r, const double *part_rr,
-                                                       SegTab tab, ScalB *segs) {
-    __shared__ double tot[K];
+                                                       SegTab tab, ScalB *segs,
+                                                       const double *__restrict__ dinv = nullptr) {
+    __shared__ double tot[K], totz[K];
     __shared__ double alpha_s[K], beta_s[K];
     const int4 ch = tab.chunk[blockIdx.x];
     ScalB *s = segs + ch.x;
@@ -584,11 +598,12 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_xpB(double *__restrict__ 
     }
     const int k = s->iter_b;
     seg_sum_cols<K>(part_rr, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], tot);
+    if (PC) seg_sum_cols<K>(part_rr + (size_t)gridDim.x * K, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], totz);
     if (threadIdx.x < K) {
         const int j = threadIdx.x;
         const bool on = (ab >> j) & 1u;
         alpha_s[j] = on ? s->alpha[j] : 0.0;
-        beta_s[j] = on ? tot[j] / s->rho_b[j] : 0.0;
+        beta_s[j] = on ? (PC ? totz[j] : tot[j]) / s->rho_b[j] : 0.0;
     }
     __syncthreads();
     const int j0 = (2 * threadIdx.x) % K;
@@ -598,15 +613,20 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_xpB(double *__restrict__ 
     double2 *p2 = reinterpret_cast<double2 *>(p);
     const double2 *r2 = reinterpret_cast<const double2 *>(r);
     struct Ld {
-        double2 p, x, r;
+        double2 p, x, r;  // r: z = dinv r with PC
     };
-    stream_loop<4>(
+    stream_loop<PC ? 2 : 4>(
         (int64_t)ch.y * K / 2 + threadIdx.x, (int64_t)ch.z * K / 2, kBlockV,
         [&](int64_t i) {
             Ld l;
             l.p = p2[i];
             l.x = __ldcs(x2 + i);
             l.r = r2[i];
+            if (PC) {
+                const double dv = __ldg(dinv + (2 * i) / K);
+                l.r.x *= dv;
+                l.r.y *= dv;
+            }
             return l;
         },
         [&](int64_t i, Ld l) {
@@ -621,7 +641,8 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_xpB(double *__restrict__ 
         for (int j = 0; j < K; ++j) {
             if (!((ab >> j) & 1u)) continue;
             const double rr = tot[j];
-            s->rho[j] = rr;
+            s->rho[j] = PC ? totz[j] : rr;
+            s->rrt[j] = rr;
             s->iters[j] = k + 1;
             s->relres[j] = s->bnorm[j] > 0.0 ? sqrt(rr) / s->bnorm[j] : 0.0;
             if (sqrt(rr) <= s->rtol * s->bnorm[j]) {
@@ -640,19 +661,21 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_xpB(double *__restrict__ 
 }
 
 // Setup of Algorithm 3 line 1 for K columns, one block per chunk: r = b - q
-// (use_q; q = S x_1 with a guess, else zeros) or r = b, p = r when p is
-// given, and the chunk's partials of (r_j, r_j)_w (part[chunk*K + j]) and,
-// with with_b, (b_j, b_j)_w (part[(nchunks + chunk)*K + j]).  With p ==
-// nullptr this is the FP64 residual of the refinement; with r == nullptr
-// only the norms are formed (the true residual at the end of a solve).
-template <int K>
+// (use_q; q = S x_1 with a guess, else zeros) or r = b, p = z when p is
+// given (z = r, or z = dinv r with the diagonal preconditioner, PC), and the
+// chunk's partials of (r_j, r_j)_w (part[chunk*K + j]), with with_b of
+// (b_j, b_j)_w (part[(nchunks + chunk)*K + j]) and with PC of (r_j, z_j)_w
+// (part[(2 nchunks + chunk)*K + j]).  With p == nullptr this is the FP64
+// residual of the refinement; with r == nullptr only the norms are formed
+// (the true residual at the end of a solve).
+template <int K, bool PC = false>
 __global__ void __launch_bounds__(kBlockV, 1) k_residualB(const double *__restrict__ b, const double *__restrict__ q,
                                                       double *__restrict__ r, double *__restrict__ p,
                                                       const uint8_t *__restrict__ mult,
                                                       const double *__restrict__ wtab, double *part, SegTab tab,
-                                                      int use_q, int with_b) {
+                                                      int use_q, int with_b, const double *__restrict__ dinv = nullptr) {
     const int4 ch = tab.chunk[blockIdx.x];
-    double arr[2] = {0.0, 0.0}, abb[2] = {0.0, 0.0};
+    double arr[2] = {0.0, 0.0}, abb[2] = {0.0, 0.0}, arz[2] = {0.0, 0.0};
     const double2 *b2 = reinterpret_cast<const double2 *>(b);
     const double2 *q2 = reinterpret_cast<const double2 *>(q);
     double2 *r2 = reinterpret_cast<double2 *>(r);
@@ -666,8 +689,14 @@ __global__ void __launch_bounds__(kBlockV, 1) k_residualB(const double *__restri
             rv.x = bv.x - qv.x;
             rv.y = bv.y - qv.y;
         }
+        double2 zv = rv;
+        if (PC) {
+            const double dv = __ldg(dinv + (2 * i) / K);
+            zv.x *= dv;
+            zv.y *= dv;
+        }
         if (r) r2[i] = rv;
-        if (p) p2[i] = rv;
+        if (p) p2[i] = zv;
         const double w = __ldg(wtab + mult[(2 * i) / K]);
         arr[0] = fma(w * rv.x, rv.x, arr[0]);
         arr[1] = fma(w * rv.y, rv.y, arr[1]);
@@ -675,9 +704,14 @@ __global__ void __launch_bounds__(kBlockV, 1) k_residualB(const double *__restri
             abb[0] = fma(w * bv.x, bv.x, abb[0]);
             abb[1] = fma(w * bv.y, bv.y, abb[1]);
         }
+        if (PC) {
+            arz[0] = fma(w * rv.x, zv.x, arz[0]);
+            arz[1] = fma(w * rv.y, zv.y, arz[1]);
+        }
     }
     block_cols_sum<K, 2>(arr, part + (size_t)blockIdx.x * K);
     if (with_b) block_cols_sum<K, 2>(abb, part + (size_t)(gridDim.x + blockIdx.x) * K);
+    if (PC) block_cols_sum<K, 2>(arz, part + (size_t)(2 * gridDim.x + blockIdx.x) * K);
 }
 
 // Parameters of every segment's solve (one thread per segment); nr_single > 0
@@ -698,19 +732,21 @@ __global__ void k_set_paramsB(ScalB *segs, int nseg, double rtol, int32_t max_it
 
 // One block per segment, after k_residualB (with_b) of the setup: rho_j,
 // ||b_j||_w and the test before the first iteration.
-template <int K>
+template <int K, bool PC = false>
 __global__ void __launch_bounds__(kBlock) k_init_finB(const double *part, int nchunks, SegTab tab, ScalB *segs) {
-    __shared__ double rr[K], bb[K];
+    __shared__ double rr[K], bb[K], rz[K];
     const int sg = blockIdx.x;
     ScalB *s = segs + sg;
     seg_sum_cols<K, kBlock>(part, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rr);
     seg_sum_cols<K, kBlock>(part + (size_t)nchunks * K, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], bb);
+    if (PC) seg_sum_cols<K, kBlock>(part + (size_t)2 * nchunks * K, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rz);
     if (threadIdx.x == 0) {
         const int nr = tab.nrhs[sg];
         uint32_t act = 0;
         for (int j = 0; j < K; ++j) {
-            s->rho[j] = rr[j];
-            s->rho_b[j] = rr[j];
+            s->rho[j] = PC ? rz[j] : rr[j];
+            s->rho_b[j] = s->rho[j];
+            s->rrt[j] = rr[j];
             s->bnorm[j] = sqrt(bb[j]);
             s->relres[j] = s->bnorm[j] > 0.0 ? sqrt(rr[j]) / s->bnorm[j] : 0.0;
             s->iters[j] = 0;
@@ -742,15 +778,19 @@ __global__ void __launch_bounds__(kBlock) k_init_finB(const double *part, int nc
 // still in the current inner solve).
 // ---------------------------------------------------------------------------
 
-// Inner setup, one block per chunk: r32 = (float) r64, p32 = r32, d32 = 0 and
-// the chunk's partials of (r32, r32)_w (FP32 products and block sums).
-template <int K>
+// Inner setup, one block per chunk: r32 = (float) r64, p32 = z32 (z32 = r32,
+// or r32 * (1 / S_ii rounded to FP32) with the diagonal preconditioner, PC),
+// d32 = 0 and the chunk's partials of (r32, r32)_w at part[chunk*K + j] and
+// with PC of (r32, z32)_w at part[(nchunks + chunk)*K + j] (FP32 products and
+// block sums).
+template <int K, bool PC = false>
 __global__ void __launch_bounds__(kBlockV, 1) k_inner_initB(const double *__restrict__ r64, float *__restrict__ r32,
                                                         float *__restrict__ p32, float *__restrict__ d32,
                                                         const uint8_t *__restrict__ mult,
-                                                        const float *__restrict__ wtab, double *part, SegTab tab) {
+                                                        const float *__restrict__ wtab, double *part, SegTab tab,
+                                                        const float *__restrict__ dinv32 = nullptr) {
     const int4 ch = tab.chunk[blockIdx.x];
-    float acc[2] = {0.f, 0.f};
+    float acc[2] = {0.f, 0.f}, acz[2] = {0.f, 0.f};
     const double2 *r2 = reinterpret_cast<const double2 *>(r64);
     float2 *rr2 = reinterpret_cast<float2 *>(r32);
     float2 *pp2 = reinterpret_cast<float2 *>(p32);
@@ -759,31 +799,45 @@ __global__ void __launch_bounds__(kBlockV, 1) k_inner_initB(const double *__rest
     for (int64_t i = (int64_t)ch.y * K / 2 + threadIdx.x; i < i1; i += kBlockV) {
         const double2 rv = r2[i];
         const float2 f = make_float2(float(rv.x), float(rv.y));
+        float2 z = f;
+        if (PC) {
+            const float dv = __ldg(dinv32 + (2 * i) / K);
+            z.x *= dv;
+            z.y *= dv;
+        }
         rr2[i] = f;
-        pp2[i] = f;
+        pp2[i] = z;
         dd2[i] = make_float2(0.f, 0.f);
         const float w = __ldg(wtab + mult[(2 * i) / K]);
         acc[0] = fmaf(w * f.x, f.x, acc[0]);
         acc[1] = fmaf(w * f.y, f.y, acc[1]);
+        if (PC) {
+            acz[0] = fmaf(w * f.x, z.x, acz[0]);
+            acz[1] = fmaf(w * f.y, z.y, acz[1]);
+        }
     }
     block_cols_sum<K, 2>(acc, part + (size_t)blockIdx.x * K);
+    if (PC) block_cols_sum<K, 2>(acz, part + (size_t)(gridDim.x + blockIdx.x) * K);
 }
 
 // One block per segment: rho0_j of the inner solves, their tolerances
 // tau_j = max(inner_rtol, rtol ||b_j|| / ||r64_j||) and the active set.
-template <int K>
-__global__ void __launch_bounds__(kBlock) k_inner_finB(const double *part, SegTab tab, ScalB *si, const ScalB *so) {
-    __shared__ double rr[K];
+template <int K, bool PC = false>
+__global__ void __launch_bounds__(kBlock) k_inner_finB(const double *part, int nchunks, SegTab tab, ScalB *si,
+                                                       const ScalB *so) {
+    __shared__ double rr[K], rz[K];
     const int sg = blockIdx.x;
     seg_sum_cols<K, kBlock>(part, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rr);
+    if (PC) seg_sum_cols<K, kBlock>(part + (size_t)nchunks * K, tab.seg_chunk[sg], tab.seg_chunk[sg + 1], rz);
     if (threadIdx.x == 0) {
         ScalB *i = si + sg;
         const ScalB *o = so + sg;
         uint32_t act = 0;
         for (int j = 0; j < K; ++j) {
             const double tot = rr[j];
-            i->rho[j] = tot;
-            i->rho_b[j] = tot;
+            i->rho[j] = PC ? rz[j] : tot;
+            i->rho_b[j] = i->rho[j];
+            i->rrt[j] = tot;
             i->rho0[j] = tot;
             const double tau = o->bnorm[j] > 0.0 && o->rho[j] > 0.0 ? o->rtol * o->bnorm[j] / sqrt(o->rho[j]) : 0.0;
             i->tau[j] = tau > o->inner_rtol ? tau : o->inner_rtol;
@@ -802,12 +856,13 @@ __global__ void __launch_bounds__(kBlock) k_inner_finB(const double *part, SegTa
 // Inner Algorithm 3 lines 3 and 5 in FP32 for K columns, one block per chunk
 // (alpha formed in FP64 from the FP64 sums of the partials, then rounded to
 // FP32 once).
-template <int K>
+template <int K, bool PC = false>
 __global__ void __launch_bounds__(kBlockV, 1) k_update_r32B(const float *__restrict__ q, float *__restrict__ r,
                                                         const uint8_t *__restrict__ mult,
                                                         const float *__restrict__ wtab,
                                                         const uint8_t *__restrict__ gflag128, const double *part_pq,
-                                                        double *part_rr, SegTab tab, ScalB *si) {
+                                                        double *part_rr, SegTab tab, ScalB *si,
+                                                        const float *__restrict__ dinv32 = nullptr) {
     constexpr int VW = K >= 4 ? 4 : 2;
     __shared__ double tot[K];
     __shared__ float alpha_s[K];
@@ -850,14 +905,15 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_r32B(const float *__restr
     float a[VW];
 #pragma unroll
     for (int u = 0; u < VW; ++u) a[u] = alpha_s[j0 + u];
-    float acc[VW];
+    float acc[VW], acz[VW];
 #pragma unroll
-    for (int u = 0; u < VW; ++u) acc[u] = 0.f;
+    for (int u = 0; u < VW; ++u) acc[u] = acz[u] = 0.f;
     struct Ld {
         float r[VW], q[VW];
+        float d;
         uint8_t g;
     };
-    stream_loop<4>(
+    stream_loop<PC ? 2 : 4>(
         (int64_t)ch.y * K / VW + threadIdx.x, (int64_t)ch.z * K / VW, kBlockV,
         [&](int64_t i) {
             Ld l;
@@ -873,6 +929,7 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_r32B(const float *__restr
                 l.q[0] = u.x, l.q[1] = u.y;
             }
             l.g = __ldg(gflag128 + (((VW * i) / K) >> 7));
+            if (PC) l.d = __ldg(dinv32 + (VW * i) / K);  // local entry of the VW values
             return l;
         },
         [&](int64_t i, Ld l) {
@@ -883,16 +940,23 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_r32B(const float *__restr
                 reinterpret_cast<float4 *>(r)[i] = make_float4(rv[0], rv[1], rv[2], rv[3]);
             else
                 reinterpret_cast<float2 *>(r)[i] = make_float2(rv[0], rv[1]);
-            if (l.g == 0) {
+            float wr[VW];
 #pragma unroll
-                for (int u = 0; u < VW; ++u) acc[u] = fmaf(rv[u], rv[u], acc[u]);
-            } else {
+            for (int u = 0; u < VW; ++u) wr[u] = rv[u];
+            if (l.g != 0) {
                 const float w = __ldg(wtab + mult[(VW * i) / K]);
 #pragma unroll
-                for (int u = 0; u < VW; ++u) acc[u] = fmaf(w * rv[u], rv[u], acc[u]);
+                for (int u = 0; u < VW; ++u) wr[u] = w * rv[u];
+            }
+#pragma unroll
+            for (int u = 0; u < VW; ++u) acc[u] = fmaf(wr[u], rv[u], acc[u]);
+            if (PC) {
+#pragma unroll
+                for (int u = 0; u < VW; ++u) acz[u] = fmaf(wr[u], rv[u] * l.d, acz[u]);
             }
         });
     block_cols_sum<K, VW>(acc, part_rr + (size_t)blockIdx.x * K);
+    if (PC) block_cols_sum<K, VW>(acz, part_rr + (size_t)(gridDim.x + blockIdx.x) * K);
 }
 
 // Inner Algorithm 3 lines 4, 7, 8 in FP32 for K columns, one block per chunk:
@@ -900,12 +964,13 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_r32B(const float *__restr
 // counts each active column's inner iteration and applies its inner test
 // (sqrt(rho_j) <= tau_j sqrt(rho0_j), or its inner iterations summed reach
 // max_iter).
-template <int K>
+template <int K, bool PC = false>
 __global__ void __launch_bounds__(kBlockV, 1) k_update_dp32B(float *__restrict__ d, float *__restrict__ p,
                                                          const float *__restrict__ r, const double *part_rr,
-                                                         SegTab tab, ScalB *si, ScalB *so) {
+                                                         SegTab tab, ScalB *si, ScalB *so,
+                                                         const float *__restrict__ dinv32 = nullptr) {
     constexpr int VW = K >= 4 ? 4 : 2;
-    __shared__ double tot[K];
+    __shared__ double tot[K], totz[K];
     __shared__ float alpha_s[K], beta_s[K];
     const int4 ch = tab.chunk[blockIdx.x];
     ScalB *s = si + ch.x;
@@ -917,11 +982,12 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_dp32B(float *__restrict__
     }
     const int k = s->iter_b;
     seg_sum_cols<K>(part_rr, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], tot);
+    if (PC) seg_sum_cols<K>(part_rr + (size_t)gridDim.x * K, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], totz);
     if (threadIdx.x < K) {
         const int j = threadIdx.x;
         const bool on = (ab >> j) & 1u;
         alpha_s[j] = on ? float(s->alpha[j]) : 0.f;
-        beta_s[j] = on ? float(tot[j] / s->rho_b[j]) : 0.f;
+        beta_s[j] = on ? float((PC ? totz[j] : tot[j]) / s->rho_b[j]) : 0.f;
     }
     __syncthreads();
     const int j0 = (VW * threadIdx.x) % K;
@@ -953,6 +1019,11 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_dp32B(float *__restrict__
                 l.d[0] = u.x, l.d[1] = u.y;
                 l.r[0] = w.x, l.r[1] = w.y;
             }
+            if (PC) {  // l.r becomes z = r * (1 / S_ii)
+                const float dv = __ldg(dinv32 + (VW * i) / K);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) l.r[u] *= dv;
+            }
             return l;
         },
         [&](int64_t i, Ld l) {
@@ -976,7 +1047,8 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_dp32B(float *__restrict__
         for (int j = 0; j < K; ++j) {
             if (!((ab >> j) & 1u)) continue;
             const double rr = tot[j];
-            s->rho[j] = rr;
+            s->rho[j] = PC ? totz[j] : rr;
+            s->rrt[j] = rr;
             const int t1 = o->iters[j] + 1;
             o->iters[j] = t1;
             if (sqrt(rr) <= s->tau[j] * sqrt(s->rho0[j]) || t1 >= o->max_iter) na &= ~(1u << j);

@@ -31,6 +31,10 @@ SSG_FP64_JACOBI = 2
 SSG_MIXED_JACOBI = 3
 SSG_DRIVER_GRAPH = 0
 SSG_DRIVER_HOST = 1
+SSG_BAND_ROW = 0
+SSG_BAND_COL = 1
+SSG_BAND_AUTO = 0
+SSG_BAND_STAGED = -1
 
 # every entry point declared in include/ssg.h
 EXPORTS = (
@@ -65,6 +69,12 @@ EXPORTS = (
     "ssg_error_string",
     "ssg_last_error",
     "ssg_wdot_noalloc",
+    "ssg_band_split",
+    "ssg_band_get",
+    "ssg_band_spmv",
+    "ssg_band_set_variant",
+    "ssg_band_autotune",
+    "ssg_band_destroy",
 )
 
 
@@ -111,6 +121,19 @@ class ssg_tune(C.Structure):
     def as_dict(self):
         return {f: (list(getattr(self, f)) if not isinstance(getattr(self, f), int) else getattr(self, f))
                 for f, _ in self._fields_}
+
+
+class ssg_band_tune(C.Structure):
+    _fields_ = [
+        ("variant", C.c_int32),
+        ("rule_variant", C.c_int32),
+        ("code", C.c_int32 * 7),
+        ("us", C.c_float * 7),
+    ]
+
+    def as_dict(self):
+        return {"variant": self.variant, "rule_variant": self.rule_variant,
+                "us": {int(c): float(u) for c, u in zip(self.code, self.us) if u > 0}}
 
 
 class SSGError(RuntimeError):
@@ -172,6 +195,12 @@ def lib():
         L.ssg_solve_host.argtypes = [vp, i32, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
         L.ssg_system_destroy.argtypes = [vp]
         L.ssg_wdot_noalloc.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
+        L.ssg_band_split.argtypes = [vp, i32, i32, vp, vp, vp, i32, C.POINTER(vp)]
+        L.ssg_band_get.argtypes = [vp, i32, vp, vp, vp, vp]
+        L.ssg_band_spmv.argtypes = [vp, vp, vp]
+        L.ssg_band_set_variant.argtypes = [vp, i32]
+        L.ssg_band_autotune.argtypes = [vp, i32, C.POINTER(ssg_band_tune)]
+        L.ssg_band_destroy.argtypes = [vp]
         L.ssg_error_string.argtypes = [C.c_int]
         L.ssg_error_string.restype = C.c_char_p
         L.ssg_last_error.argtypes = []
@@ -360,6 +389,51 @@ def ssg_autotune(sys, reps=20):
     return t.as_dict()
 
 
+def ssg_band_split(ctx, kind, n, rowptr, colidx, val, nb):
+    rowptr = np.ascontiguousarray(rowptr, np.int32)
+    colidx = np.ascontiguousarray(colidx, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    if rowptr.size != n + 1 or colidx.size != val.size or colidx.size < rowptr[-1]:
+        raise ValueError("CSR arrays have inconsistent sizes")
+    h = C.c_void_p()
+    _check(lib().ssg_band_split(ctx, kind, n, _ptr(rowptr), _ptr(colidx), _ptr(val), nb, C.byref(h)),
+           "ssg_band_split")
+    return h
+
+
+def ssg_band_get(band, p, n_rows_total):
+    """Band p's CSR arrays (host): returns (N_p, displ, rowptr, colidx, val).
+    n_rows_total: the band's row count, N_p (band-row) or n (band-column),
+    is found from a first call with NULL arrays."""
+    sz = np.zeros(3, np.int64)
+    _check(lib().ssg_band_get(band, p, _ptr(sz), None, None, None), "ssg_band_get")
+    rows = int(sz[0]) if n_rows_total is None else n_rows_total
+    rp = np.zeros(rows + 1, np.int32)
+    ci = np.zeros(max(int(sz[2]), 1), np.int32)
+    va = np.zeros(max(int(sz[2]), 1), np.float64)
+    _check(lib().ssg_band_get(band, p, _ptr(sz), _ptr(rp), _ptr(ci), _ptr(va)), "ssg_band_get")
+    nz = int(sz[2])
+    return int(sz[0]), int(sz[1]), rp, ci[:nz].copy(), va[:nz].copy()
+
+
+def ssg_band_spmv(band, x, y):
+    return _check(lib().ssg_band_spmv(band, _dev_f64(x), _dev_f64(y)), "ssg_band_spmv")
+
+
+def ssg_band_set_variant(band, variant):
+    return _check(lib().ssg_band_set_variant(band, variant), "ssg_band_set_variant")
+
+
+def ssg_band_autotune(band, reps=20):
+    t = ssg_band_tune()
+    _check(lib().ssg_band_autotune(band, reps, C.byref(t)), "ssg_band_autotune")
+    return t.as_dict()
+
+
+def ssg_band_destroy(band):
+    return _check(lib().ssg_band_destroy(band), "ssg_band_destroy")
+
+
 def ssg_spmm_assembled(sys, k, x_loc, y_loc):
     return _check(lib().ssg_spmm_assembled(sys, k, _dev_f64(x_loc), _dev_f64(y_loc)), "ssg_spmm_assembled")
 
@@ -521,6 +595,43 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             ssg_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Band:
+    """Band-row (kind SSG_BAND_ROW) or band-column (SSG_BAND_COL) splitting of
+    A into nb bands (ssg_band_split), with its product y = A x."""
+
+    def __init__(self, ctx: Context, A, kind, nb):
+        self.ctx = ctx
+        self.n = A.n
+        self.kind = kind
+        self.nb = nb
+        self.h = ssg_band_split(ctx.h, kind, A.n, A.rowptr, A.colidx, A.val, nb)
+
+    def band(self, p):
+        """(N_p, displ, rowptr, colidx, val) of band p (host arrays)."""
+        return ssg_band_get(self.h, p, None if self.kind == SSG_BAND_ROW else self.n)
+
+    def spmv(self, x, out=None):
+        import torch
+
+        out = torch.empty(self.n, dtype=torch.float64, device=x.device) if out is None else out
+        ssg_band_spmv(self.h, x, out)
+        return out
+
+    def set_variant(self, variant):
+        ssg_band_set_variant(self.h, variant)
+
+    def autotune(self, reps=20):
+        return ssg_band_autotune(self.h, reps)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ssg_band_destroy(self.h)
             self.h = None
 
     def __del__(self):

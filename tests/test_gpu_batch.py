@@ -201,3 +201,41 @@ def test_batch_mixed_shapes_and_guess(ctx):
                 assert _rel(xs[o + j * A.n:o + (j + 1) * A.n], r.x) <= 1e-10
                 assert st[t]["block"] == 2
                 t += 1
+
+
+def test_batch_jacobi(ctx, bp):
+    """The batch with the diagonal preconditioner: SSG_FP64_JACOBI per (system,
+    right-hand side) against or_sub_pcg (early iterates within 1e-10, counts
+    at 1e-8 within max(2, 3 %)), SSG_MIXED_JACOBI against or_sub_pcg_mixed
+    (refinements within +-1, inner iterations within max(3 per refinement,
+    5 %), FP64 true residual <= rtol)."""
+    from paper_2108_13162_gb300 import ssg
+
+    B = _make(ctx, bp)
+    x, rc, st = B.solve(_b_all(bp), rtol=0.0, max_iter=6, mode=ssg.SSG_FP64_JACOBI)
+    assert rc == ssg.SSG_E_NOT_CONVERGED
+    xs = _split(B, bp, x)
+    t = 0
+    for s, j, ref, b in _each(bp):
+        assert st[t]["iters"] == 6
+        assert _rel(xs[s][j], ref.pcg(b, 0.0, 6).x) <= 1e-10
+        t += 1
+    x, rc, st = B.solve(_b_all(bp), rtol=1e-8, max_iter=100000, mode=ssg.SSG_FP64_JACOBI)
+    assert rc == ssg.SSG_OK
+    t = 0
+    for s, j, ref, b in _each(bp):
+        r = ref.pcg(b, 1e-8, 100000)
+        assert abs(st[t]["iters"] - r.iters) <= max(2, 0.03 * r.iters)
+        assert st[t]["true_relres"] <= 1.01e-8
+        t += 1
+    x, rc, st = B.solve(_b_all(bp), rtol=1e-8, max_iter=100000, mode=ssg.SSG_MIXED_JACOBI)
+    assert rc == ssg.SSG_OK
+    xs = _split(B, bp, x)
+    t = 0
+    for s, j, ref, b in _each(bp):
+        rm = ref.pcg_mixed(b, 1e-8, 100000, 1e-4, 30)
+        tr = np.linalg.norm(b - oracle.spmv(bp.A[s], xs[s][j])) / np.linalg.norm(b)
+        assert tr <= 1.0001e-8
+        assert abs(st[t]["outer"] - rm.outer) <= 1
+        assert abs(st[t]["iters"] - rm.iters) <= max(3 * rm.outer, 0.05 * rm.iters)
+        t += 1

@@ -1,5 +1,7 @@
 """GPU solves with the diagonal preconditioner (SSG_FP64_JACOBI, Algorithm 3
-with M = diag(S)) against the oracle's or_sub_pcg, through the C ABI.
+with M = diag(S), and SSG_MIXED_JACOBI) against the oracle's or_sub_pcg and
+or_sub_pcg_mixed, through the C ABI, one right-hand side at a time and
+several together (the K-column kernels).
 
 The readings are those of the unpreconditioned parity tests: early iterates
 (k <= 6) within 1e-10, solutions converged to 1e-12 within 1e-10, iteration
@@ -99,11 +101,59 @@ def test_jacobi_fewer_iterations_and_drivers_agree(ctx):
         ctx.set_driver(ssg.SSG_DRIVER_GRAPH)
     assert s2[0]["iters"] == s1[0]["iters"]
     assert np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
-    # several right-hand sides: solved one after another, each as alone
+    # several right-hand sides iterate together (K = 2), each column against the oracle
     B = np.stack([p.b[:, 0], 2.0 * p.b[:, 0]])
     X, rc, st = S.solve(_t(B), rtol=1e-8, mode=ssg.SSG_FP64_JACOBI)
-    assert rc == ssg.SSG_OK and [s["block"] for s in st] == [1, 1]
-    assert np.array_equal(X.cpu().numpy()[0], x1.cpu().numpy())
+    assert rc == ssg.SSG_OK and [s["block"] for s in st] == [2, 2]
+    ref = oracle.Partition(p.A, p.part, p.P)
+    for j in range(2):
+        r = ref.pcg(B[j], 1e-8, 100000)
+        assert abs(st[j]["iters"] - r.iters) <= max(2, 0.03 * r.iters)
+        assert st[j]["true_relres"] <= 1.01e-8
+    ctx.set_driver(ssg.SSG_DRIVER_HOST)
+    try:
+        X2, rc2, st2 = S.solve(_t(B), rtol=1e-8, mode=ssg.SSG_FP64_JACOBI)
+    finally:
+        ctx.set_driver(ssg.SSG_DRIVER_GRAPH)
+    assert rc2 == ssg.SSG_OK and [a["iters"] for a in st2] == [a["iters"] for a in st]
+    assert np.array_equal(X2.cpu().numpy(), X.cpu().numpy())
+
+
+@pytest.mark.parametrize("name,case", CASES[1:], ids=[c[0] for c in CASES[1:]])
+@pytest.mark.parametrize("k", [3, 16])
+def test_jacobi_block_matches_oracle(ctx, name, case, k):
+    """k right-hand sides through the K-column kernels (K = 4, 16) with the
+    diagonal preconditioner: per column the single-solve readings (early
+    iterates within 1e-10, converged to 1e-12 within 1e-10; mixed: refinements
+    within +-1, inner iterations within max(3 per refinement, 5 %), FP64 true
+    residual <= rtol)."""
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    A, part, P, b = _unpack(case)
+    rng = np.random.default_rng(k)
+    B = np.stack([b] + [rng.uniform(-1, 1, A.n) for _ in range(k - 1)])
+    S = System(ctx, A, part, P)
+    ref = oracle.Partition(A, part, P)
+    X, rc, st = S.solve(_t(B), rtol=0.0, max_iter=6, mode=ssg.SSG_FP64_JACOBI)
+    assert rc == ssg.SSG_E_NOT_CONVERGED and all(t["iters"] == 6 and t["block"] == (4 if k == 3 else 16) for t in st)
+    X = X.cpu().numpy()
+    for j in range(k):
+        assert _rel(X[j], ref.pcg(B[j], 0.0, 6).x) <= 1e-10
+    X, rc, st = S.solve(_t(B), rtol=1e-12, max_iter=100000, mode=ssg.SSG_FP64_JACOBI)
+    assert rc == ssg.SSG_OK
+    X = X.cpu().numpy()
+    for j in range(k):
+        assert _rel(X[j], ref.pcg(B[j], 1e-12, 100000).x) <= 1e-10
+    X, rc, st = S.solve(_t(B), rtol=1e-8, max_iter=100000, mode=ssg.SSG_MIXED_JACOBI)
+    assert rc == ssg.SSG_OK
+    X = X.cpu().numpy()
+    for j in range(k):
+        rm = ref.pcg_mixed(B[j], 1e-8, 100000, 1e-4, 30)
+        tr = np.linalg.norm(B[j] - oracle.spmv(A, X[j])) / np.linalg.norm(B[j])
+        assert tr <= 1.0001e-8
+        assert abs(st[j]["outer"] - rm.outer) <= 1
+        assert abs(st[j]["iters"] - rm.iters) <= max(3 * rm.outer, 0.05 * rm.iters)
 
 
 def test_jacobi_rejects_bad_diagonal(ctx):
