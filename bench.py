@@ -281,8 +281,9 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (no FP64 figure is measured on this poo
 def bench_multi_rhs(ctx, stream, reps, spmv_reps):
     """The 16-right-hand-side workload (96^3 FV, 27 subdomains): time to 1e-8
     for all 16 with the columns iterating together (K = 16) and one after
-    another, FP64 and mixed, the differentiable solve (forward + adjoint),
-    and the k-vector product's roofline."""
+    another, FP64, mixed and both with the diagonal preconditioner, the
+    differentiable solve (forward + adjoint), and the k-vector product's
+    roofline."""
     import numpy as np
     import torch
 
@@ -296,7 +297,8 @@ def bench_multi_rhs(ctx, stream, reps, spmv_reps):
     X = torch.zeros_like(B)
     out = {"workload": "fv3d_7pt_96^3_kappa=exp(N(0,1))_3x3x3_subdomains_16rhs", "n": p.A.n, "nnz": p.A.nnz,
            "nloc": S.sizes.nloc, "rhs": B.shape[0], "rtol": RTOL}
-    for mode_name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED)):
+    for mode_name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED), ("jacobi", ssg.SSG_FP64_JACOBI),
+                            ("mixed_jacobi", ssg.SSG_MIXED_JACOBI)):
         for kb in (16, 1):
             ctx.set_rhs_block(kb)
             X.zero_()
@@ -361,8 +363,9 @@ def bench_multi_rhs(ctx, stream, reps, spmv_reps):
 
 def bench_batch(ctx, stream, reps, size):
     """Workload 4: independent 2D finite-volume systems (4-16 box subdomains,
-    1-8 right-hand sides each) solved together in one graph launch, FP64 and
-    mixed, against the same systems solved one after another.  size "full":
+    1-8 right-hand sides each) solved together in one graph launch, FP64,
+    mixed and mixed with the diagonal preconditioner, against the same systems
+    solved one after another (FP64, mixed).  size "full":
     512 systems with sides 32..512; "small": 512 systems with sides 32..128."""
     import numpy as np
     import torch
@@ -381,7 +384,7 @@ def bench_batch(ctx, stream, reps, size):
            "systems": len(bp.A), "unknowns": int(sum(A.n for A in bp.A)), "nnz": int(sum(A.nnz for A in bp.A)),
            "rhs": int(sum(b.shape[0] for b in bp.b)), "subdomains": int(sum(bp.P)), "rtol": RTOL,
            "setup_s": setup_s}
-    for mode_name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED)):
+    for mode_name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED), ("mixed_jacobi", ssg.SSG_MIXED_JACOBI)):
         x, rc, st = B.solve(bb, rtol=RTOL, mode=mode)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)

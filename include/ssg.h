@@ -415,10 +415,10 @@ int ssg_wdot_noalloc(const double *u_loc, const double *v_loc, const uint8_t *mu
  * ssg_band_spmv: y = A x through the band's splitting; x and y are device
  *   vectors of n doubles (not overlapping), ordered on the context stream.
  * ssg_band_set_variant: which kernel computes the product:
- *   SSG_BAND_AUTO (the row-length rule: the staged kernel while the mean row
- *   length is at most 8, the entries a staged tile holds per thread; else
- *   lanes per row = the power of two >= half the mean row length, from 2 to
- *   32; band-column: the staged kernel), SSG_BAND_STAGED (tiles of whole rows staged in shared
+ *   SSG_BAND_AUTO (the row-length rule: one thread per row while the mean
+ *   row length is at most 8, else lanes per row = the power of two >= half
+ *   the mean row length, from 2 to 32; band-column: one thread per row),
+ *   SSG_BAND_STAGED (tiles of whole rows staged in shared
  *   memory by bulk asynchronous copies, one thread per row: the left-to-right
  *   order), 1 (one thread per row from global memory, left to right), or
  *   2, 4, 8, 16, 32 lanes per row (strided partial sums, then a fixed

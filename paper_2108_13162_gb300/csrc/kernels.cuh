@@ -224,6 +224,24 @@ __device__ __forceinline__ double all_sum_partials(const double *partials, int G
     return bc;
 }
 
+// num / den formed once by thread 0 and handed to the block: an FP64 division
+// is a sequence of FP64 instructions, and every thread of every block
+// dividing on its own kept the FP64 pipe (2 operations per clock per SM)
+// busy for microseconds before the stream could start.  With to_f32 the
+// quotient is also rounded to FP32 once (*q32).
+__device__ __forceinline__ double block_quotient(double num, double den, float *q32 = nullptr) {
+    __shared__ double q;
+    __shared__ float qf;
+    __syncthreads();  // a previous call's readers are done
+    if (threadIdx.x == 0) {
+        q = num / den;
+        qf = float(q);
+    }
+    __syncthreads();
+    if (q32) *q32 = qf;
+    return q;
+}
+
 // Streams i = i0, i0 + step, ... < i1 through load(i) and apply(i, loaded),
 // U indices at a time: the U loads are issued before the first apply, so a
 // thread keeps U requests in flight instead of one, and the applies still run
@@ -474,9 +492,15 @@ __global__ void __launch_bounds__(kSpmvThreads, BPS)
         }
         W = Wn;
     }
-    // fixed-order reduction: lanes of each warp, then the block's warps in order
+    // fixed-order reduction: lanes of each warp, then the block's warps in
+    // order; the FP32 product sums its lanes in FP32 (five FP64 shuffle-adds
+    // per warp at the end of every block queue on the FP64 pipe)
     __shared__ double wsum[kSpmvWarps];
-    const double wv = warp_sum(double(dot));
+    double wv;
+    if constexpr (sizeof(T) == 4)
+        wv = double(warp_sumf(dot));
+    else
+        wv = warp_sum(dot);
     if (lane == 0) wsum[warp] = wv;
     __syncthreads();
     double bs = 0.0;
@@ -532,7 +556,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r(int64_t N,
         }
         return;
     }
-    const double alpha = s->rho / pq;
+    const double alpha = block_quotient(s->rho, pq);
     double acc = 0.0, acz = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N2 = N >> 1;
@@ -613,7 +637,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_xp(int64_t N
     if (s->brk || s->halt[k & 1]) return;
     const double rr = all_sum_partials(part_rr, G2);
     const double rz = PC ? all_sum_partials(part_rz, G2) : rr;
-    const double alpha = s->alpha, beta = rz / s->rho_b;
+    const double alpha = s->alpha, beta = block_quotient(rz, s->rho_b);
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N2 = N >> 1;
     double2 *x2 = reinterpret_cast<double2 *>(x);
@@ -886,8 +910,8 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
         }
         return;
     }
-    const double alpha_d = si->rho / pq;
-    const float alpha = float(alpha_d);
+    float alpha;
+    const double alpha_d = block_quotient(si->rho, pq, &alpha);
     float acc = 0.f, acz = 0.f;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N4 = N >> 2;
@@ -976,8 +1000,9 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t
     if (si->brk || si->halt[k & 1]) return;
     const double rr = all_sum_partials(part_rr, G2);
     const double rz = PC ? all_sum_partials(part_rz, G2) : rr;
-    const double beta_d = rz / si->rho_b;
-    const float alpha = si->alpha32, beta = float(beta_d);
+    float beta;
+    const double beta_d = block_quotient(rz, si->rho_b, &beta);
+    const float alpha = si->alpha32;
     const int total1 = si->total_b + 1;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N4 = N >> 2;

@@ -130,12 +130,12 @@ def test_band_autotune_and_rule(ctx):
     from paper_2108_13162_gb300.ssg import Band
 
     def rule(A, code):
-        # the staged kernel while the mean row fits its tiles (2048 entries for
-        # 256 rows), else lanes = the power of two >= mean / 2 in [2, 32];
-        # band-column products always take the staged kernel
+        # one thread per row while the mean row length is at most 8, else
+        # lanes = the power of two >= mean / 2 in [2, 32]; band-column
+        # products always one thread per row
         mean = A.nnz / A.n
         if code == ssg.SSG_BAND_COL or mean <= 8:
-            return ssg.SSG_BAND_STAGED
+            return 1
         v = 2
         while v < 32 and v < mean / 2:
             v *= 2
@@ -147,7 +147,7 @@ def test_band_autotune_and_rule(ctx):
             B = Band(ctx, A, code, 7)
             assert B.autotune(reps=1)["rule_variant"] == rule(A, code)
             B.close()
-    assert rule(CASES[0][1], ssg.SSG_BAND_ROW) == ssg.SSG_BAND_STAGED and rule(CASES[1][1], ssg.SSG_BAND_ROW) > 1
+    assert rule(CASES[0][1], ssg.SSG_BAND_ROW) == 1 and rule(CASES[1][1], ssg.SSG_BAND_ROW) > 1
     A = CASES[1][1]
     for code, valid in ((ssg.SSG_BAND_ROW, ROW_VARIANTS), (ssg.SSG_BAND_COL, COL_VARIANTS)):
         B = Band(ctx, A, code, 7)
