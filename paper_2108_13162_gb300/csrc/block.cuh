@@ -511,31 +511,8 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_rB(const double *__restri
         if (!act) s->act_b = 0;
     }
     if (!act) return;
-    seg_sum_cols<K>(part_pq, tab.seg_blk[ch.x], tab.seg_blk[ch.x + 1], tot);
-    if (threadIdx.x < K) {
-        const int j = threadIdx.x;
-        const double pq = tot[j];
-        double a = 0.0;
-        if (((act >> j) & 1u) && pq > 0.0 && isfinite(pq)) a = s->rho[j] / pq;
-        alpha_s[j] = a;
-    }
-    __syncthreads();
-    if (first && threadIdx.x == 0) {
-        uint32_t ab = act;
-        for (int j = 0; j < K; ++j) {
-            if (!((act >> j) & 1u)) continue;
-            const double pq = tot[j];
-            s->pq[j] = pq;
-            s->alpha[j] = alpha_s[j];
-            if (!(pq > 0.0) || !isfinite(pq)) {
-                s->status[j] = SSG_E_BREAKDOWN;
-                ab &= ~(1u << j);
-            }
-        }
-        s->act_b = ab;
-    }
     const int j0 = (2 * threadIdx.x) % K;
-    const double a0 = alpha_s[j0], a1 = alpha_s[j0 + 1];
+    double a0 = 0.0, a1 = 0.0;
     double acc[2] = {0.0, 0.0}, acz[2] = {0.0, 0.0};
     double2 *__restrict__ r2 = reinterpret_cast<double2 *>(r);
     const double2 *__restrict__ q2 = reinterpret_cast<const double2 *>(q);
@@ -544,7 +521,7 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_rB(const double *__restri
         double d;
         uint8_t g;
     };
-    stream_loop<PC ? 2 : 4>(
+    stream_loop_after<PC ? 2 : 4>(
         (int64_t)ch.y * K / 2 + threadIdx.x, (int64_t)ch.z * K / 2, kBlockV,
         [&](int64_t i) {
             Ld l;
@@ -553,6 +530,34 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_rB(const double *__restri
             l.g = __ldg(gflag + (((2 * i) / K) >> 6));
             if (PC) l.d = __ldg(dinv + (2 * i) / K);  // local entry of both values
             return l;
+        },
+        [&]() {
+            seg_sum_cols<K>(part_pq, tab.seg_blk[ch.x], tab.seg_blk[ch.x + 1], tot);
+            if (threadIdx.x < K) {
+                const int j = threadIdx.x;
+                const double pq = tot[j];
+                double a = 0.0;
+                if (((act >> j) & 1u) && pq > 0.0 && isfinite(pq)) a = s->rho[j] / pq;
+                alpha_s[j] = a;
+            }
+            __syncthreads();
+            if (first && threadIdx.x == 0) {
+                uint32_t ab = act;
+                for (int j = 0; j < K; ++j) {
+                    if (!((act >> j) & 1u)) continue;
+                    const double pq = tot[j];
+                    s->pq[j] = pq;
+                    s->alpha[j] = alpha_s[j];
+                    if (!(pq > 0.0) || !isfinite(pq)) {
+                        s->status[j] = SSG_E_BREAKDOWN;
+                        ab &= ~(1u << j);
+                    }
+                }
+                s->act_b = ab;
+            }
+            a0 = alpha_s[j0];
+            a1 = alpha_s[j0 + 1];
+            return true;
         },
         [&](int64_t i, Ld l) {
             double2 rv = l.r;
@@ -597,25 +602,15 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_xpB(double *__restrict__ 
         return;
     }
     const int k = s->iter_b;
-    seg_sum_cols<K>(part_rr, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], tot);
-    if (PC) seg_sum_cols<K>(part_rr + (size_t)gridDim.x * K, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], totz);
-    if (threadIdx.x < K) {
-        const int j = threadIdx.x;
-        const bool on = (ab >> j) & 1u;
-        alpha_s[j] = on ? s->alpha[j] : 0.0;
-        beta_s[j] = on ? (PC ? totz[j] : tot[j]) / s->rho_b[j] : 0.0;
-    }
-    __syncthreads();
     const int j0 = (2 * threadIdx.x) % K;
-    const double a0 = alpha_s[j0], a1 = alpha_s[j0 + 1];
-    const double b0 = beta_s[j0], b1 = beta_s[j0 + 1];
+    double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
     double2 *x2 = reinterpret_cast<double2 *>(x);
     double2 *p2 = reinterpret_cast<double2 *>(p);
     const double2 *r2 = reinterpret_cast<const double2 *>(r);
     struct Ld {
         double2 p, x, r;  // r: z = dinv r with PC
     };
-    stream_loop<PC ? 2 : 4>(
+    stream_loop_after<PC ? 2 : 4>(
         (int64_t)ch.y * K / 2 + threadIdx.x, (int64_t)ch.z * K / 2, kBlockV,
         [&](int64_t i) {
             Ld l;
@@ -628,6 +623,22 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_xpB(double *__restrict__ 
                 l.r.y *= dv;
             }
             return l;
+        },
+        [&]() {
+            seg_sum_cols<K>(part_rr, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], tot);
+            if (PC) seg_sum_cols<K>(part_rr + (size_t)gridDim.x * K, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], totz);
+            if (threadIdx.x < K) {
+                const int j = threadIdx.x;
+                const bool on = (ab >> j) & 1u;
+                alpha_s[j] = on ? s->alpha[j] : 0.0;
+                beta_s[j] = on ? (PC ? totz[j] : tot[j]) / s->rho_b[j] : 0.0;
+            }
+            __syncthreads();
+            a0 = alpha_s[j0];
+            a1 = alpha_s[j0 + 1];
+            b0 = beta_s[j0];
+            b1 = beta_s[j0 + 1];
+            return true;
         },
         [&](int64_t i, Ld l) {
             double2 xv = l.x;
@@ -876,44 +887,17 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_r32B(const float *__restr
         if (!act) s->act_b = 0;
     }
     if (!act) return;
-    seg_sum_cols<K>(part_pq, tab.seg_blk[ch.x], tab.seg_blk[ch.x + 1], tot);
-    if (threadIdx.x < K) {
-        const int j = threadIdx.x;
-        const double pq = tot[j];
-        double a = 0.0;
-        if (((act >> j) & 1u) && pq > 0.0 && isfinite(pq)) a = s->rho[j] / pq;
-        alpha_s[j] = float(a);
-        if (first && ((act >> j) & 1u)) {
-            s->pq[j] = pq;
-            s->alpha[j] = a;
-        }
-    }
-    __syncthreads();
-    if (first && threadIdx.x == 0) {
-        uint32_t ab = act;
-        for (int j = 0; j < K; ++j) {
-            if (!((act >> j) & 1u)) continue;
-            const double pq = tot[j];
-            if (!(pq > 0.0) || !isfinite(pq)) {
-                s->status[j] = SSG_E_BREAKDOWN;
-                ab &= ~(1u << j);
-            }
-        }
-        s->act_b = ab;
-    }
     const int j0 = (VW * threadIdx.x) % K;
     float a[VW];
-#pragma unroll
-    for (int u = 0; u < VW; ++u) a[u] = alpha_s[j0 + u];
     float acc[VW], acz[VW];
 #pragma unroll
-    for (int u = 0; u < VW; ++u) acc[u] = acz[u] = 0.f;
+    for (int u = 0; u < VW; ++u) a[u] = acc[u] = acz[u] = 0.f;
     struct Ld {
         float r[VW], q[VW];
         float d;
         uint8_t g;
     };
-    stream_loop<PC ? 2 : 4>(
+    stream_loop_after<PC ? 2 : 4>(
         (int64_t)ch.y * K / VW + threadIdx.x, (int64_t)ch.z * K / VW, kBlockV,
         [&](int64_t i) {
             Ld l;
@@ -931,6 +915,36 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_r32B(const float *__restr
             l.g = __ldg(gflag128 + (((VW * i) / K) >> 7));
             if (PC) l.d = __ldg(dinv32 + (VW * i) / K);  // local entry of the VW values
             return l;
+        },
+        [&]() {
+            seg_sum_cols<K>(part_pq, tab.seg_blk[ch.x], tab.seg_blk[ch.x + 1], tot);
+            if (threadIdx.x < K) {
+                const int j = threadIdx.x;
+                const double pq = tot[j];
+                double a = 0.0;
+                if (((act >> j) & 1u) && pq > 0.0 && isfinite(pq)) a = s->rho[j] / pq;
+                alpha_s[j] = float(a);
+                if (first && ((act >> j) & 1u)) {
+                    s->pq[j] = pq;
+                    s->alpha[j] = a;
+                }
+            }
+            __syncthreads();
+            if (first && threadIdx.x == 0) {
+                uint32_t ab = act;
+                for (int j = 0; j < K; ++j) {
+                    if (!((act >> j) & 1u)) continue;
+                    const double pq = tot[j];
+                    if (!(pq > 0.0) || !isfinite(pq)) {
+                        s->status[j] = SSG_E_BREAKDOWN;
+                        ab &= ~(1u << j);
+                    }
+                }
+                s->act_b = ab;
+            }
+#pragma unroll
+            for (int u = 0; u < VW; ++u) a[u] = alpha_s[j0 + u];
+            return true;
         },
         [&](int64_t i, Ld l) {
             float rv[VW];
@@ -981,26 +995,12 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_dp32B(float *__restrict__
         return;
     }
     const int k = s->iter_b;
-    seg_sum_cols<K>(part_rr, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], tot);
-    if (PC) seg_sum_cols<K>(part_rr + (size_t)gridDim.x * K, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], totz);
-    if (threadIdx.x < K) {
-        const int j = threadIdx.x;
-        const bool on = (ab >> j) & 1u;
-        alpha_s[j] = on ? float(s->alpha[j]) : 0.f;
-        beta_s[j] = on ? float((PC ? totz[j] : tot[j]) / s->rho_b[j]) : 0.f;
-    }
-    __syncthreads();
     const int j0 = (VW * threadIdx.x) % K;
     float a[VW], bt[VW];
-#pragma unroll
-    for (int u = 0; u < VW; ++u) {
-        a[u] = alpha_s[j0 + u];
-        bt[u] = beta_s[j0 + u];
-    }
     struct Ld {
         float p[VW], d[VW], r[VW];
     };
-    stream_loop<2>(
+    stream_loop_after<2>(
         (int64_t)ch.y * K / VW + threadIdx.x, (int64_t)ch.z * K / VW, kBlockV,
         [&](int64_t i) {
             Ld l;
@@ -1025,6 +1025,23 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_dp32B(float *__restrict__
                 for (int u = 0; u < VW; ++u) l.r[u] *= dv;
             }
             return l;
+        },
+        [&]() {
+            seg_sum_cols<K>(part_rr, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], tot);
+            if (PC) seg_sum_cols<K>(part_rr + (size_t)gridDim.x * K, tab.seg_chunk[ch.x], tab.seg_chunk[ch.x + 1], totz);
+            if (threadIdx.x < K) {
+                const int j = threadIdx.x;
+                const bool on = (ab >> j) & 1u;
+                alpha_s[j] = on ? float(s->alpha[j]) : 0.f;
+                beta_s[j] = on ? float((PC ? totz[j] : tot[j]) / s->rho_b[j]) : 0.f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < VW; ++u) {
+                a[u] = alpha_s[j0 + u];
+                bt[u] = beta_s[j0 + u];
+            }
+            return true;
         },
         [&](int64_t i, Ld l) {
             float pv[VW], dv[VW];

@@ -260,6 +260,28 @@ __device__ __forceinline__ void stream_loop(int64_t i0, int64_t i1, int64_t step
     for (; i < i1; i += step) apply(i, load(i));
 }
 
+// stream_loop whose first loads (two indices) are issued before prologue()
+// runs: the prologue (summing the previous kernel's block partials, forming
+// alpha or beta) then overlaps those loads instead of stalling the stream.
+// The applies run in the same ascending order as stream_loop's.  prologue()
+// is called by every thread (it may hold barriers); when it returns false
+// nothing is applied and false is returned.
+template <int U, typename L, typename P, typename A>
+__device__ __forceinline__ bool stream_loop_after(int64_t i0, int64_t i1, int64_t step, L load, P prologue, A apply) {
+    constexpr int kPre = U < 2 ? U : 2;  // more held across the prologue spills registers
+    using R = decltype(load(i0));
+    R v[kPre];
+#pragma unroll
+    for (int u = 0; u < kPre; ++u)
+        if (i0 + u * step < i1) v[u] = load(i0 + u * step);
+    if (!prologue()) return false;
+#pragma unroll
+    for (int u = 0; u < kPre; ++u)
+        if (i0 + u * step < i1) apply(i0 + u * step, v[u]);
+    stream_loop<U>(i0 + kPre * step, i1, step, load, apply);
+    return true;
+}
+
 __device__ __forceinline__ void stop_loop(Scal *s, cudaGraphConditionalHandle h, int use_cond) {
     s->done = 1;
     if (use_cond) cudaGraphSetConditional(h, 0);
@@ -546,17 +568,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r(int64_t N,
         s->iter_b = s->iter;
     }
     if (s->brk || s->halt[s->iter & 1]) return;
-    const double pq = all_sum_partials(part_pq, G1);
-    if (!(pq > 0.0) || !isfinite(pq)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            s->pq = pq;
-            s->status = SSG_E_BREAKDOWN;
-            s->brk = 1;
-            stop_loop(s, h, use_cond);
-        }
-        return;
-    }
-    const double alpha = block_quotient(s->rho, pq);
+    double pq = 0.0, alpha = 0.0;
     double acc = 0.0, acz = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N2 = N >> 1;
@@ -568,7 +580,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r(int64_t N,
         double2 r, q, d;
         uint8_t g;
     };
-    stream_loop<PC ? 2 : 4>(
+    const bool go = stream_loop_after<PC ? 2 : 4>(
         (int64_t)blockIdx.x * kBlock + threadIdx.x, N2, stride,
         [&](int64_t i) {
             Ld l;
@@ -577,6 +589,20 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r(int64_t N,
             l.g = __ldg(gflag + (i >> 5));
             if (PC) l.d = __ldg(d2 + i);
             return l;
+        },
+        [&]() {
+            pq = all_sum_partials(part_pq, G1);
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    s->pq = pq;
+                    s->status = SSG_E_BREAKDOWN;
+                    s->brk = 1;
+                    stop_loop(s, h, use_cond);
+                }
+                return false;
+            }
+            alpha = block_quotient(s->rho, pq);
+            return true;
         },
         [&](int64_t i, Ld l) {
             double2 rv = l.r;
@@ -601,6 +627,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r(int64_t N,
                 acz = fma(wy, rv.y * l.d.y, acz);
             }
         });
+    if (!go) return;
     if ((N & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         const double ri = fma(-alpha, q[N - 1], r[N - 1]);
         r[N - 1] = ri;
@@ -635,9 +662,8 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_xp(int64_t N
     pdl_enter();
     const int k = s->iter_b;
     if (s->brk || s->halt[k & 1]) return;
-    const double rr = all_sum_partials(part_rr, G2);
-    const double rz = PC ? all_sum_partials(part_rz, G2) : rr;
-    const double alpha = s->alpha, beta = block_quotient(rz, s->rho_b);
+    double rr = 0.0, rz = 0.0, beta = 0.0;
+    const double alpha = s->alpha;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N2 = N >> 1;
     double2 *x2 = reinterpret_cast<double2 *>(x);
@@ -647,7 +673,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_xp(int64_t N
     struct Ld {
         double2 p, x, z;
     };
-    stream_loop<PC ? 2 : 4>(
+    stream_loop_after<PC ? 2 : 4>(
         (int64_t)blockIdx.x * kBlock + threadIdx.x, N2, stride,
         [&](int64_t i) {
             Ld l;
@@ -660,6 +686,12 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_xp(int64_t N
                 l.z.y *= dv.y;
             }
             return l;
+        },
+        [&]() {
+            rr = all_sum_partials(part_rr, G2);
+            rz = PC ? all_sum_partials(part_rz, G2) : rr;
+            beta = block_quotient(rz, s->rho_b);
+            return true;
         },
         [&](int64_t i, Ld l) {
             double2 xv = l.x;
@@ -900,18 +932,8 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
         si->total_b = so->total;
     }
     if (si->brk || si->halt[si->iter & 1]) return;
-    const double pq = all_sum_partials(part_pq, G1);
-    if (!(pq > 0.0) || !isfinite(pq)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            si->pq = pq;
-            si->status = SSG_E_BREAKDOWN;
-            si->brk = 1;
-            stop_loop(si, h, use_cond);
-        }
-        return;
-    }
-    float alpha;
-    const double alpha_d = block_quotient(si->rho, pq, &alpha);
+    double pq = 0.0, alpha_d = 0.0;
+    float alpha = 0.f;
     float acc = 0.f, acz = 0.f;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N4 = N >> 2;
@@ -923,7 +945,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
         float4 r, q, d;
         uint8_t g;
     };
-    stream_loop<PC ? 2 : 4>(
+    const bool go = stream_loop_after<PC ? 2 : 4>(
         (int64_t)blockIdx.x * kBlock + threadIdx.x, N4, stride,
         [&](int64_t i) {
             Ld l;
@@ -932,6 +954,20 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
             l.g = __ldg(gflag128 + (i >> 5));
             if (PC) l.d = __ldg(z4 + i);
             return l;
+        },
+        [&]() {
+            pq = all_sum_partials(part_pq, G1);
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    si->pq = pq;
+                    si->status = SSG_E_BREAKDOWN;
+                    si->brk = 1;
+                    stop_loop(si, h, use_cond);
+                }
+                return false;
+            }
+            alpha_d = block_quotient(si->rho, pq, &alpha);
+            return true;
         },
         [&](int64_t i, Ld l) {
             float4 rv = l.r;
@@ -963,6 +999,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
                 acz = fmaf(w.w * rv.w, rv.w * l.d.w, acz);
             }
         });
+    if (!go) return;
     if (blockIdx.x == 0 && threadIdx.x < (N & 3)) {
         const int64_t i = (N & ~int64_t(3)) + threadIdx.x;
         const float ri = fmaf(-alpha, q[i], r[i]);
@@ -998,10 +1035,8 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t
     pdl_enter();
     const int k = si->iter_b;
     if (si->brk || si->halt[k & 1]) return;
-    const double rr = all_sum_partials(part_rr, G2);
-    const double rz = PC ? all_sum_partials(part_rz, G2) : rr;
-    float beta;
-    const double beta_d = block_quotient(rz, si->rho_b, &beta);
+    double rr = 0.0, rz = 0.0, beta_d = 0.0;
+    float beta = 0.f;
     const float alpha = si->alpha32;
     const int total1 = si->total_b + 1;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
@@ -1013,7 +1048,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t
     struct Ld {
         float4 p, d, z;
     };
-    stream_loop<2>(
+    stream_loop_after<2>(
         (int64_t)blockIdx.x * kBlock + threadIdx.x, N4, stride,
         [&](int64_t i) {
             Ld l;
@@ -1028,6 +1063,12 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t
                 l.z.w *= dv.w;
             }
             return l;
+        },
+        [&]() {
+            rr = all_sum_partials(part_rr, G2);
+            rz = PC ? all_sum_partials(part_rz, G2) : rr;
+            beta_d = block_quotient(rz, si->rho_b, &beta);
+            return true;
         },
         [&](int64_t i, Ld l) {
             float4 dv = l.d;
