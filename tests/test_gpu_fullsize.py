@@ -1,0 +1,158 @@
+"""Full-size parity of the workloads the benchmark times besides the 128^3
+system (which test_gpu_solve / test_gpu_mixed / test_gpu_jacobi cover):
+
+  * P1 finite elements on the jittered 1024^2 mesh, 256 RCB subdomains;
+  * the batch of 512 independent 2D systems (sides 32..128, the benchmark's
+    default batch), 4-16 subdomains and 1-8 right-hand sides each;
+  * the 96^3 system with 16 right-hand sides iterating together.
+
+Element by element where the oracle finishes in seconds: the assembled
+SpMV over every local entry (within 4 (L_i + m_i) u (|A||x|)_i), the first six
+CG iterates (k <= 6) within 1e-10 for every entry (all right-hand sides).
+Where it does not (full solves to 1e-8 of a million unknowns), properties
+that hold at any size, computed with the oracle's FP64 products, not the
+GPU's: the true residual ||b - A x|| / ||b|| <= rtol (1.01 rtol for the
+recursive FP64 test, rtol for the mixed modes' FP64 test) for every right-hand
+side, and on seeded samples the oracle's iteration counts (FP64: within
+max(2, 3 %); mixed: refinements within +-1, inner iterations within max(3 per
+refinement, 5 %)).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import batch_problem, config_problem
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0**-53
+RTOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    from paper_2108_13162_gb300 import build as ssg_build
+    from paper_2108_13162_gb300.ssg import Context
+
+    ssg_build.build()
+    c = Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def _t(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _true_res(A, x, b):
+    return float(np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b))
+
+
+def test_fe_full_size_1024(ctx):
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    p = config_problem(3)
+    A, b = p.A, p.b[:, 0]
+    S = System(ctx, A, p.part, p.P)
+    ref = oracle.Partition(A, p.part, p.P)
+    m = ref.maps
+    # the assembled product on every local entry
+    x = np.random.default_rng(3).uniform(-1, 1, A.n)
+    xl = ref.scatter(x)
+    y = S.spmv(_t(xl)).cpu().numpy()
+    absAx = abs(A.to_scipy()) @ np.abs(x)
+    L = np.zeros(A.n)
+    np.maximum.at(L, m.l2g, np.diff(m.lrowptr))
+    assert np.all(np.abs(y - ref.spmv(xl)) <= 4.0 * (L[m.l2g] + m.mult[m.l2g]) * U * absAx[m.l2g] * 2)
+    # the first six iterates, every entry, plain and preconditioned
+    xg, rc, st = S.solve(_t(b), rtol=0.0, max_iter=6)
+    assert _rel(xg.cpu().numpy(), ref.cg(b, 0.0, 6).x) <= 1e-10
+    xg, rc, st = S.solve(_t(b), rtol=0.0, max_iter=6, mode=ssg.SSG_FP64_JACOBI)
+    assert _rel(xg.cpu().numpy(), ref.pcg(b, 0.0, 6).x) <= 1e-10
+    # the benchmark's solves to 1e-8: the true residual by the oracle's product
+    for mode, tol in ((ssg.SSG_FP64, 1.01 * RTOL), (ssg.SSG_MIXED, RTOL), (ssg.SSG_MIXED_JACOBI, RTOL)):
+        xg, rc, st = S.solve(_t(b), rtol=RTOL, mode=mode)
+        assert rc == ssg.SSG_OK
+        tr = _true_res(A, xg.cpu().numpy(), b)
+        print("fe2d 1024^2 mode %d: %d iterations, true residual %.3e" % (mode, st[0]["iters"], tr))
+        assert tr <= tol * 1.0001
+    S.close()
+
+
+def test_batch_full_size_512(ctx):
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import Batch
+
+    bp = batch_problem(512, 32, 128)
+    B = Batch(ctx, [(A, pt, P, b.shape[0]) for A, pt, P, b in zip(bp.A, bp.part, bp.P, bp.b)])
+    bb = _t(np.concatenate([b.ravel() for b in bp.b]))
+
+    def split(x):
+        x = x.cpu().numpy()
+        return [x[int(B.rhs_off[s]):int(B.rhs_off[s]) + b.size].reshape(b.shape) for s, b in enumerate(bp.b)]
+
+    pairs = [(s, j) for s, b in enumerate(bp.b) for j in range(b.shape[0])]
+    rng = np.random.default_rng(512)
+    sample = [pairs[i] for i in rng.choice(len(pairs), 12, replace=False)]
+    t_of = {pr: t for t, pr in enumerate(pairs)}
+    refs = {s: oracle.Partition(bp.A[s], bp.part[s], bp.P[s]) for s, _ in sample}
+    # the first six iterates of the sampled (system, right-hand side) pairs
+    x, rc, st = B.solve(bb, rtol=0.0, max_iter=6)
+    xs = split(x)
+    for s, j in sample:
+        assert _rel(xs[s][j], refs[s].cg(bp.b[s][j], 0.0, 6).x) <= 1e-10
+    # to 1e-8: every pair's true residual, the sampled pairs' counts
+    for mode in (ssg.SSG_FP64, ssg.SSG_MIXED):
+        x, rc, st = B.solve(bb, rtol=RTOL, mode=mode)
+        assert rc == ssg.SSG_OK
+        xs = split(x)
+        worst = max(_true_res(bp.A[s], xs[s][j], bp.b[s][j]) for s, j in pairs)
+        print("batch mode %d: worst true residual %.3e over %d pairs" % (mode, worst, len(pairs)))
+        assert worst <= (1.01 if mode == ssg.SSG_FP64 else 1.0001) * RTOL
+        for s, j in sample:
+            t = st[t_of[(s, j)]]
+            if mode == ssg.SSG_FP64:
+                r = refs[s].cg(bp.b[s][j], RTOL, 100000)
+                assert abs(t["iters"] - r.iters) <= max(2, 0.03 * r.iters)
+            else:
+                rm = refs[s].cg_mixed(bp.b[s][j], RTOL, 100000, 1e-4, 30)
+                assert abs(t["outer"] - rm.outer) <= 1
+                assert abs(t["iters"] - rm.iters) <= max(3 * rm.outer, 0.05 * rm.iters)
+    B.close()
+
+
+def test_sixteen_rhs_full_size_96(ctx):
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    p = config_problem(5)
+    A, Bm = p.A, p.b.T.copy()  # (16, n)
+    S = System(ctx, A, p.part, p.P)
+    ref = oracle.Partition(A, p.part, p.P)
+    X, rc, st = S.solve(_t(Bm), rtol=0.0, max_iter=6)
+    assert all(t["block"] == 16 for t in st)
+    X = X.cpu().numpy()
+    for j in range(16):
+        assert _rel(X[j], ref.cg(Bm[j], 0.0, 6).x) <= 1e-10
+    for mode in (ssg.SSG_FP64, ssg.SSG_MIXED, ssg.SSG_MIXED_JACOBI):
+        X, rc, st = S.solve(_t(Bm), rtol=RTOL, mode=mode)
+        assert rc == ssg.SSG_OK
+        X = X.cpu().numpy()
+        worst = max(_true_res(A, X[j], Bm[j]) for j in range(16))
+        print("96^3 x 16 mode %d: worst true residual %.3e" % (mode, worst))
+        assert worst <= (1.01 if mode == ssg.SSG_FP64 else 1.0001) * RTOL
+        if mode == ssg.SSG_FP64:
+            r = ref.cg(Bm[5], RTOL, 100000)  # one sampled column against the oracle's full run
+            assert abs(st[5]["iters"] - r.iters) <= max(2, 0.03 * r.iters)
+    S.close()
