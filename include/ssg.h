@@ -445,6 +445,15 @@ int ssg_band_get(const ssg_band *band, int32_t p, int64_t *sizes, int32_t *rowpt
 int ssg_band_spmv(ssg_band *band, const double *x, double *y);
 int ssg_band_set_variant(ssg_band *band, int32_t variant);
 int ssg_band_autotune(ssg_band *band, int32_t reps, ssg_band_tune *out);
+/*
+ * ssg_band_check_timeout: runs the staged kernel's bounded wait once on an
+ * mbarrier phase that nothing completes (no copy issued, nothing in flight):
+ * the wait gives up after one second, raises the operator's error flag, and
+ * the call returns SSG_E_TIMEOUT (then clears the flag; the context and the
+ * operator stay usable).  Any other status means the failure path did not
+ * work.  A test of failure detection without a GPU fault.
+ */
+int ssg_band_check_timeout(ssg_band *band);
 int ssg_band_destroy(ssg_band *band);
 
 const char *ssg_error_string(int status);

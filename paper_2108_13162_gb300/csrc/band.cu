@@ -40,7 +40,8 @@ constexpr int kStageBytes = kValBuf + kColBuf;
 constexpr int kStagedSmem = 2 * kStageBytes;  // two stages
 constexpr int kStagedBlocksPerSM = 4;
 constexpr int kVecBlocksPerSM = 8;
-constexpr uint32_t kWaitLimit = 1u << 22;     // bounded mbarrier wait (try_wait iterations)
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded mbarrier wait: one second of global time
+constexpr uint32_t kWaitMaxTries = 1u << 26;      // and a cap on the tries should the timer not advance
 static_assert(kValBuf % 16 == 0 && kColBuf % 16 == 0, "stage buffers keep 16-byte alignment");
 
 struct BandDev {
@@ -129,10 +130,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for the phase with the given parity; false when the limit ran out.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase with the given parity; false when the limit (one second,
+// or kWaitMaxTries tries) ran out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < kWaitMaxTries; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u && global_ns() - t0 > kWaitLimitNs) return false;
+    }
     return false;
 }
 
@@ -217,6 +227,21 @@ __global__ void __launch_bounds__(kBandBlock, kStagedBlocksPerSM)
         t = tn;
         b ^= 1;
     }
+}
+
+// The bounded wait's failure path, on its own: an mbarrier phase that
+// nothing completes (no arrival, no copy issued), waited for by one warp with
+// the staged kernel's bound; the timeout raises the error flag.  Nothing is
+// in flight, so the context stays usable.
+__global__ void k_band_wait_probe(int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicExch(err, 1);
 }
 
 // ---------------------------------------------------------------- lanes --
@@ -497,8 +522,8 @@ int ssg_band_get(const ssg_band *band, int32_t p, int64_t *sizes, int32_t *rowpt
         sizes[2] = A_rp[displ + np] - base;
         if (rowptr)
             for (int32_t i = 0; i <= np; ++i) rowptr[i] = A_rp[displ + i] - base;
-        if (colidx) std::memcpy(colidx, A_ci + base, sizeof(int32_t) * sizes[2]);
-        if (val) std::memcpy(val, A_v + base, sizeof(double) * sizes[2]);
+        if (colidx && sizes[2] > 0) std::memcpy(colidx, A_ci + base, sizeof(int32_t) * sizes[2]);
+        if (val && sizes[2] > 0) std::memcpy(val, A_v + base, sizeof(double) * sizes[2]);
         return SSG_OK;
     }
     int64_t c = 0;
@@ -593,6 +618,20 @@ int ssg_band_autotune(ssg_band *band, int32_t reps, ssg_band_tune *out) {
     out->variant = best_v;
     out->rule_variant = band->rule_variant;
     return SSG_OK;
+}
+
+int ssg_band_check_timeout(ssg_band *band) {
+    int rc = check_band(band);
+    if (rc != SSG_OK) return rc;
+    BAND_CUDA_TRY(cudaStreamSynchronize(band->ctx->stream));
+    rc = check_err_flag(band);
+    if (rc != SSG_OK) return rc;
+    k_band_wait_probe<<<1, 32, 0, band->ctx->stream>>>(band->dev.err);
+    BAND_CUDA_TRY(cudaGetLastError());
+    BAND_CUDA_TRY(cudaStreamSynchronize(band->ctx->stream));
+    rc = check_err_flag(band);
+    *band->h_err = 0;  // the probe's flag is its result, not a fault of the operator
+    return rc;
 }
 
 int ssg_band_destroy(ssg_band *band) {

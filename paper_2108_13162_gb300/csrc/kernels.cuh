@@ -260,15 +260,15 @@ __device__ __forceinline__ void stream_loop(int64_t i0, int64_t i1, int64_t step
     for (; i < i1; i += step) apply(i, load(i));
 }
 
-// stream_loop whose first loads (two indices) are issued before prologue()
-// runs: the prologue (summing the previous kernel's block partials, forming
-// alpha or beta) then overlaps those loads instead of stalling the stream.
-// The applies run in the same ascending order as stream_loop's.  prologue()
-// is called by every thread (it may hold barriers); when it returns false
+// stream_loop whose first PRE loads are issued before prologue() runs: the
+// prologue (summing the previous kernel's block partials, forming alpha or
+// beta) then overlaps those loads instead of stalling the stream.  The
+// applies run in the same ascending order as stream_loop's.  prologue() is
+// called by every thread (it may hold barriers); when it returns false
 // nothing is applied and false is returned.
-template <int U, typename L, typename P, typename A>
+template <int U, int PRE = (U < 2 ? U : 2), typename L, typename P, typename A>
 __device__ __forceinline__ bool stream_loop_after(int64_t i0, int64_t i1, int64_t step, L load, P prologue, A apply) {
-    constexpr int kPre = U < 2 ? U : 2;  // more held across the prologue spills registers
+    constexpr int kPre = PRE;
     using R = decltype(load(i0));
     R v[kPre];
 #pragma unroll
@@ -945,7 +945,9 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
         float4 r, q, d;
         uint8_t g;
     };
-    const bool go = stream_loop_after<PC ? 2 : 4>(
+    // a thread streams about four items on the 128^3 system: all of them
+    // are in flight before the prologue
+    const bool go = stream_loop_after<PC ? 2 : 4, PC ? 2 : 4>(
         (int64_t)blockIdx.x * kBlock + threadIdx.x, N4, stride,
         [&](int64_t i) {
             Ld l;

@@ -74,6 +74,7 @@ EXPORTS = (
     "ssg_band_spmv",
     "ssg_band_set_variant",
     "ssg_band_autotune",
+    "ssg_band_check_timeout",
     "ssg_band_destroy",
 )
 
@@ -200,6 +201,7 @@ def lib():
         L.ssg_band_spmv.argtypes = [vp, vp, vp]
         L.ssg_band_set_variant.argtypes = [vp, i32]
         L.ssg_band_autotune.argtypes = [vp, i32, C.POINTER(ssg_band_tune)]
+        L.ssg_band_check_timeout.argtypes = [vp]
         L.ssg_band_destroy.argtypes = [vp]
         L.ssg_error_string.argtypes = [C.c_int]
         L.ssg_error_string.restype = C.c_char_p
@@ -428,6 +430,11 @@ def ssg_band_autotune(band, reps=20):
     t = ssg_band_tune()
     _check(lib().ssg_band_autotune(band, reps, C.byref(t)), "ssg_band_autotune")
     return t.as_dict()
+
+
+def ssg_band_check_timeout(band):
+    """Status of the bounded-wait failure path (SSG_E_TIMEOUT when it works)."""
+    return lib().ssg_band_check_timeout(band)
 
 
 def ssg_band_destroy(band):

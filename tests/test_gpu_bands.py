@@ -209,3 +209,49 @@ def test_band_full_size_128cube(ctx, kind):
     ref = oracle.band(A, kind, 64, 63)
     assert np.array_equal(rp, ref.rowptr) and np.array_equal(ci, ref.colidx) and np.array_equal(va, ref.val)
     B.close()
+
+
+@pytest.mark.parametrize("kind", ["row", "col"])
+def test_band_degenerate_matrices(ctx, kind):
+    """One row (n = 1, one band) and a matrix without stored entries (every
+    row empty): y = A x exactly for every kernel variant."""
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import Band
+
+    code = ssg.SSG_BAND_ROW if kind == "row" else ssg.SSG_BAND_COL
+    one = CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([2.5]))
+    empty = CSR(5, np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    for A, nb in ((one, 1), (empty, 1), (empty, 5)):
+        B = Band(ctx, A, code, nb)
+        x = np.arange(1.0, A.n + 1.0)
+        y_ref = oracle.band_spmv(A, kind, nb, x)
+        for v in (ROW_VARIANTS if kind == "row" else COL_VARIANTS):
+            B.set_variant(v)
+            assert np.array_equal(B.spmv(_t(x)).cpu().numpy(), y_ref), (A.n, nb, v)
+        npr, displ, rp, ci, va = B.band(nb - 1)
+        ref = oracle.band(A, kind, nb, nb - 1)
+        assert np.array_equal(rp, ref.rowptr) and ci.size == ref.colidx.size
+        B.close()
+
+
+def test_band_bounded_wait_times_out(ctx):
+    """The staged kernel's mbarrier wait is bounded: on a phase that nothing
+    completes it gives up after about a second and reports SSG_E_TIMEOUT; the
+    operator (and the context) keep working afterwards."""
+    import time
+
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import Band
+
+    A = poisson2d_5pt(20, 20)
+    B = Band(ctx, A, ssg.SSG_BAND_ROW, 4)
+    t0 = time.perf_counter()
+    rc = ssg.ssg_band_check_timeout(B.h)
+    dt = time.perf_counter() - t0
+    assert rc == ssg.SSG_E_TIMEOUT, rc
+    assert 0.5 <= dt <= 30.0, dt
+    x = np.random.default_rng(2).uniform(-1, 1, A.n)
+    B.set_variant(ssg.SSG_BAND_STAGED)
+    y = B.spmv(_t(x)).cpu().numpy()
+    assert np.all(np.abs(y - oracle.band_spmv(A, "row", 4, x)) <= _bound(A, x, 4))
+    B.close()
