@@ -235,7 +235,9 @@ int ssg_gather(ssg_system *sys, const double *x_loc, double *x_glob);
  * every copy of an interface node receives the sum of its copies' local
  * values, summed in ascending subdomain order.  x_loc must be consistent for
  * y_loc to be the global product.  Device pointers, nloc long, must not
- * overlap.  If xSx_dev is not NULL it receives (x, S x)_w on the device.
+ * overlap.  If xSx_dev is not NULL it receives (x, S x)_w on the device (the
+ * launch then ends with a last-block sum of the block partials); with NULL
+ * the launch is the solver loop's own instance (block partials only).
  */
 int ssg_spmv_assembled(ssg_system *sys, const double *x_loc, double *y_loc, double *xSx_dev);
 
@@ -261,7 +263,8 @@ typedef struct {
 /*
  * Time the single-vector SpMV instances (launch shapes of 3 to 5 blocks per
  * SM, L2 prefetch of the next slices on or off; four per precision) on this
- * system, reps launches each (reps <= 0: 20), and use the fastest for the
+ * system as the solver loop launches them (block partials, no last-block
+ * sum), reps launches each (reps <= 0: 20), and use the fastest for the
  * following solves and products.  The choice changes only the order of the
  * block partial sums (results within the same rounding bounds; bit-for-bit
  * repeatable once chosen).  Without a call the defaults are entry 0, the

@@ -1783,8 +1783,14 @@ int ssg_spmv_assembled(ssg_system *S, const double *x_loc, double *y_loc, double
         set_error("x_loc and y_loc must be distinct non-null device vectors");
         return SSG_E_INVALID;
     }
-    kSpmv64Variants[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, S->ctx->stream>>>(
-        S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
+    // without xSx the loop's instance (block partials only); with it the one
+    // whose last block sums the partials (a ticket, a few microseconds more)
+    if (xSx_dev)
+        kSpmv64Variants[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, S->ctx->stream>>>(
+            S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
+    else
+        kSpmv64Variants[S->var64].part<<<S->grid_spmv, kSpmvThreads, 0, S->ctx->stream>>>(
+            S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, nullptr, 0, 0);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
@@ -1796,8 +1802,12 @@ int ssg_spmv_assembled_f32(ssg_system *S, const float *x_loc, float *y_loc, doub
         set_error("x_loc and y_loc must be distinct non-null device vectors");
         return SSG_E_INVALID;
     }
-    kSpmv32Variants[S->var32].store<<<S->grid_spmv32, kSpmvThreads, 0, S->ctx->stream>>>(
-        S->op32, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
+    if (xSx_dev)
+        kSpmv32Variants[S->var32].store<<<S->grid_spmv32, kSpmvThreads, 0, S->ctx->stream>>>(
+            S->op32, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
+    else
+        kSpmv32Variants[S->var32].part<<<S->grid_spmv32, kSpmvThreads, 0, S->ctx->stream>>>(
+            S->op32, x_loc, y_loc, S->d_partials, S->d_scal_op, nullptr, 0, 0);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
@@ -1808,7 +1818,8 @@ int ssg_autotune(ssg_system *S, int32_t reps, ssg_tune *out) {
     if (reps <= 0) reps = 20;
     cudaStream_t st = S->ctx->stream;
     ssg_tune t{};
-    // FP64 instances on the solver's work vectors (zero-initialised, finite)
+    // FP64 instances on the solver's work vectors (zero-initialised, finite),
+    // as the loop launches them (block partials, no last-block sum)
     double best = 1e30;
     for (int v = 0; v < kSpmvVariants; ++v) {
         const SpmvVariant<double> &V = kSpmv64Variants[v];
@@ -1816,10 +1827,10 @@ int ssg_autotune(ssg_system *S, int32_t reps, ssg_tune *out) {
         A.warp_range = S->range_bps[V.bps];
         const int grid = S->grid_bps[V.bps];
         for (int i = 0; i < 3; ++i)
-            V.store<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
+            V.part<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
         SSG_CUDA_TRY(cudaEventRecord(S->ev0, st));
         for (int i = 0; i < reps; ++i)
-            V.store<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
+            V.part<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
         SSG_CUDA_TRY(cudaEventRecord(S->ev1, st));
         SSG_CUDA_TRY(cudaGetLastError());
         SSG_CUDA_TRY(cudaEventSynchronize(S->ev1));
@@ -1840,10 +1851,10 @@ int ssg_autotune(ssg_system *S, int32_t reps, ssg_tune *out) {
         A.warp_range = S->range_bps[V.bps];
         const int grid = S->grid_bps[V.bps];
         for (int i = 0; i < 3; ++i)
-            V.store<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p32, S->d_q32, S->d_partials, S->d_scal_op, nullptr, 0, 0);
+            V.part<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p32, S->d_q32, S->d_partials, S->d_scal_op, nullptr, 0, 0);
         SSG_CUDA_TRY(cudaEventRecord(S->ev0, st));
         for (int i = 0; i < reps; ++i)
-            V.store<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p32, S->d_q32, S->d_partials, S->d_scal_op, nullptr, 0, 0);
+            V.part<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p32, S->d_q32, S->d_partials, S->d_scal_op, nullptr, 0, 0);
         SSG_CUDA_TRY(cudaEventRecord(S->ev1, st));
         SSG_CUDA_TRY(cudaGetLastError());
         SSG_CUDA_TRY(cudaEventSynchronize(S->ev1));

@@ -30,18 +30,16 @@ constexpr int kSliceRows = 32;              // rows (or interface copy rows) per
 constexpr int kSliceMaxWidth = 64;          // longer rows are handled one per warp from the CSR arrays
 // [spmv-source-begin] traits of the single-vector SpMV
 template <typename T>
-struct SpmvTraits;  // resident blocks per SM; whether column indices are loaded a slice ahead
+struct SpmvTraits;  // resident blocks per SM; slices ahead prefetched into L2
 template <>
 struct SpmvTraits<double> {
     static constexpr int kBlocksPerSM = 4;  // measured: 4 blocks without prefetch beat 3 with it
-    static constexpr bool kPrefetch = false;
     static constexpr int kL2Ahead = 0;      // slices ahead whose lines are prefetched into L2 (0: none);
                                             // measured: 1 ahead 45.1 us, none 43.9 (the FP64 pipe is busy)
 };
 template <>
 struct SpmvTraits<float> {
     static constexpr int kBlocksPerSM = 5;  // measured: 32.0 us vs 32.8 (4 blocks, with or without prefetch)
-    static constexpr bool kPrefetch = false;
     static constexpr int kL2Ahead = 1;      // measured on the 128^3 system: 28.9 us (0: 31.8, 2: 29.9, 4: 31.7)
 };
 // [spmv-source-end]
@@ -358,59 +356,6 @@ __device__ __forceinline__ T slice_row(const T *__restrict__ sv, const int32_t *
     }
 }
 
-// Column indices of one lane's row in a slice of width <= 8, loaded one
-// slice ahead: the current slice's value loads (DRAM) then go out together
-// with its x gathers (which only need the columns), so the two latencies
-// overlap instead of adding up.
-struct SliceCols {
-    int32_t c[8];
-};
-
-__device__ __forceinline__ bool short_slice(const WorkItem &W) {
-    return (W.kind == kItemSlice || W.kind == kItemIfaceSlice) && W.e1 <= 8;
-}
-
-__device__ __forceinline__ void load_cols(SliceCols &R, const int32_t *__restrict__ sc, const WorkItem &W, int lane) {
-    const int base = W.e0 + lane;
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-        if (j < W.e1) R.c[j] = __ldcs(sc + base + j * kSliceRows);
-}
-
-template <int N, typename T>
-__device__ __forceinline__ T fma_regs(const T *v, const T *xv) {
-    T acc = T(0);
-#pragma unroll
-    for (int j = 0; j < N; ++j) acc = fma(v[j], xv[j], acc);
-    return acc;
-}
-
-// Row product with the columns already in registers: value loads and x
-// gathers issued together, then exactly w FMAs in CSR order.
-template <typename T>
-__device__ __forceinline__ T cols_row(const SliceCols &R, const T *__restrict__ sv, const WorkItem &W, int lane,
-                                      const T *__restrict__ x) {
-    const int base = W.e0 + lane, w = W.e1;
-    T v[8], xv[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-        if (j < w) {
-            v[j] = __ldcs(sv + base + j * kSliceRows);
-            xv[j] = __ldg(x + R.c[j]);
-        }
-    switch (w) {
-        case 1: return fma_regs<1>(v, xv);
-        case 2: return fma_regs<2>(v, xv);
-        case 3: return fma_regs<3>(v, xv);
-        case 4: return fma_regs<4>(v, xv);
-        case 5: return fma_regs<5>(v, xv);
-        case 6: return fma_regs<6>(v, xv);
-        case 7: return fma_regs<7>(v, xv);
-        case 8: return fma_regs<8>(v, xv);
-        default: return T(0);
-    }
-}
-
 // Writes of one slice's results: interior rows, or interface copy rows whose
 // node sums are formed by shuffles in ascending subdomain order.
 template <typename T>
@@ -458,13 +403,8 @@ __global__ void __launch_bounds__(kSpmvThreads, BPS)
     const T *__restrict__ ival = copy_vals<T>(A);
     T dot = T(0);
 
-    constexpr bool kPF = SpmvTraits<T>::kPrefetch;
-    SliceCols cur, nxt;
-    WorkItem W = range.x < range.y ? A.items[range.x] : WorkItem{};
-    if (kPF && range.x < range.y && short_slice(W)) load_cols(cur, A.scol, W, lane);
     for (int it = range.x; it < range.y; ++it) {
-        const bool has_next = it + 1 < range.y;
-        const WorkItem Wn = has_next ? A.items[it + 1] : WorkItem{};
+        const WorkItem W = A.items[it];
         if (AHEAD > 0 && it + AHEAD < range.y) {
             // the value and column lines of a slice further ahead, one line per lane
             const WorkItem Wp = A.items[it + AHEAD];
@@ -473,46 +413,37 @@ __global__ void __launch_bounds__(kSpmvThreads, BPS)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
             }
         }
-        if (kPF && short_slice(W)) {
-            if (has_next && short_slice(Wn)) load_cols(nxt, A.scol, Wn, lane);
-            const T acc = cols_row<T>(cur, sv, W, lane, x);
+        if (W.kind == kItemSlice || W.kind == kItemIfaceSlice) {
+            const T acc = slice_row<T>(sv, A.scol, x, W.e0, W.e1, lane);
             finish_slice(A, W, acc, x, y, lane, dot);
-            cur = nxt;
+        } else if (W.kind == kItemLongRow) {
+            // one long row: lane-strided partial sums, fixed warp tree
+            T acc = T(0);
+            for (int k = W.e0 + lane; k < W.e1; k += 32) acc = fma(val[k], __ldg(x + A.col[k]), acc);
+            const T racc = T(warp_sum(double(acc)));
+            if (lane == 0) {
+                y[W.a] = racc;
+                dot = fma(__ldg(x + W.a), racc, dot);
+            }
         } else {
-            if (W.kind == kItemSlice || W.kind == kItemIfaceSlice) {
-                const T acc = slice_row<T>(sv, A.scol, x, W.e0, W.e1, lane);
-                finish_slice(A, W, acc, x, y, lane, dot);
-            } else if (W.kind == kItemLongRow) {
-                // one long row: lane-strided partial sums, fixed warp tree
+            // one interface node with long copy rows: each copy row reduced by
+            // the warp (fixed tree), copies summed in ascending s
+            T S = T(0);
+            for (int c = W.c0; c < W.c1; ++c) {
                 T acc = T(0);
-                for (int k = W.e0 + lane; k < W.e1; k += 32) acc = fma(val[k], __ldg(x + A.col[k]), acc);
-                const T racc = T(warp_sum(double(acc)));
-                if (lane == 0) {
-                    y[W.a] = racc;
-                    dot = fma(__ldg(x + W.a), racc, dot);
-                }
-            } else {
-                // one interface node with long copy rows: each copy row reduced by
-                // the warp (fixed tree), copies summed in ascending s
-                T S = T(0);
+                for (int k = A.irp[c] + lane; k < A.irp[c + 1]; k += 32)
+                    acc = fma(ival[k], __ldg(x + A.icol[k]), acc);
+                S += T(warp_sum(double(acc)));  // valid in lane 0
+            }
+            if (lane == 0) {
+                const T w = wtab_of<T>(A, W.c1 - W.c0);
                 for (int c = W.c0; c < W.c1; ++c) {
-                    T acc = T(0);
-                    for (int k = A.irp[c] + lane; k < A.irp[c + 1]; k += 32)
-                        acc = fma(ival[k], __ldg(x + A.icol[k]), acc);
-                    S += T(warp_sum(double(acc)));  // valid in lane 0
-                }
-                if (lane == 0) {
-                    const T w = wtab_of<T>(A, W.c1 - W.c0);
-                    for (int c = W.c0; c < W.c1; ++c) {
-                        const int row = A.icopy[c];
-                        y[row] = S;
-                        dot = fma(w * __ldg(x + row), S, dot);
-                    }
+                    const int row = A.icopy[c];
+                    y[row] = S;
+                    dot = fma(w * __ldg(x + row), S, dot);
                 }
             }
-            if (kPF && has_next && short_slice(Wn)) load_cols(cur, A.scol, Wn, lane);
         }
-        W = Wn;
     }
     // fixed-order reduction: lanes of each warp, then the block's warps in
     // order; the FP32 product sums its lanes in FP32 (five FP64 shuffle-adds
