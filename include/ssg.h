@@ -80,8 +80,9 @@ typedef struct {
     double relres;           /* final recursive residual sqrt((r,r)_w) / sqrt((b,b)_w) */
     double true_relres;      /* ||b - S x|| / ||b|| recomputed in FP64 after the solve */
     double solve_ms;         /* device time of this solve (CUDA events on the context stream); for a
-                                block of right-hand sides, the time of the whole block */
-    int64_t kernel_launches; /* kernels executed on the device for this solve (or block) */
+                                block of right-hand sides, the time of the whole block; for a
+                                batch, of its longest column group (the groups overlap) */
+    int64_t kernel_launches; /* kernels executed on the device for this solve (or block, or batch) */
 } ssg_stats;
 
 /*
@@ -189,9 +190,10 @@ int ssg_partition_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off,
  * Solve every system of a batch for its right-hand sides in one graph
  * launch: each (system, right-hand side) runs its own Algorithm 3 (SSG_FP64,
  * SSG_FP64_JACOBI) or its own refinement (SSG_MIXED, SSG_MIXED_JACOBI) with
- * the readings of ssg_solve; the
- * columns of all systems iterate together (K = the power of two >= the
- * largest sys_nrhs), a finished system's blocks return at once.  b and x
+ * the readings of ssg_solve.  Systems are grouped by column count K (the
+ * power of two >= their sys_nrhs, at least 2); the columns of all systems of
+ * a group iterate together in one graph launch (one launch per group), a
+ * finished system's blocks return at once.  b and x
  * (device, rhs_off[nsys] doubles each, caller-allocated: the library cannot
  * check their length) hold system s's right-hand side j at rhs_off[s] + j * n_s, with
  * rhs_off[s] = sum over s' < s of sys_nrhs[s'] * n_s' (n_s = its node count);

@@ -86,6 +86,17 @@ struct ssg_system {
     std::vector<int32_t> seg_sub, seg_node, seg_nrhs;  // [nseg+1], [nseg+1], [nseg]
     std::vector<int64_t> seg_rhs_off;                  // [nseg]
     int32_t batch_k = 0;       // largest right-hand-side count of a batch (0: not a batch)
+    // A batch whose systems need different column counts K is also held as
+    // one batch per K class (systems grouped by the power of two >= their
+    // right-hand-side count, at least 2), each reading and writing the
+    // caller's b and x at the original offsets; the solves run through these.
+    std::vector<ssg_system *> kclass;
+    std::vector<std::vector<int32_t>> kclass_sys;  // original system indices of each class, ascending
+    ssg_ctx *own_ctx = nullptr;    // a class's own context (its own stream), owned by the class
+    // a block solve enqueued and not yet finished (solve_block_enqueue)
+    ScalB *h_states = nullptr;     // pinned copy of the segment states, nseg + 1
+    int64_t pending_launches = 0;
+    int pending_k = 0, pending_mode = 0, pending_nr = 0;
     SegTab tab{};              // device copies of the segment tables
     struct BlockGraph {
         cudaGraph_t g = nullptr;
@@ -1284,9 +1295,8 @@ int run_blockB(ssg_system *S, int mode, int64_t *launches) {
 // one-segment solve of nr_single right-hand sides; st receives one entry per
 // (segment, right-hand side) in that order.
 template <int K>
-int solve_block(ssg_system *S, int nr_single, const double *b_glob, double *x_glob, int guess, double rtol,
-                int32_t max_iter, int mode, ssg_stats *st) {
-    const bool mixed = mode == SSG_MIXED || mode == SSG_MIXED_JACOBI;
+int solve_block_enqueue(ssg_system *S, int nr_single, const double *b_glob, double *x_glob, int guess, double rtol,
+                        int32_t max_iter, int mode) {
     int rc = SSG_OK;
     if (mode == SSG_FP64_JACOBI || mode == SSG_MIXED_JACOBI) {
         rc = check_diag(S);
@@ -1326,12 +1336,27 @@ int solve_block(ssg_system *S, int nr_single, const double *b_glob, double *x_gl
     launches += 4;
     SSG_CUDA_TRY(cudaGetLastError());
     SSG_CUDA_TRY(cudaEventRecord(S->ev1, s));
-    std::vector<ScalB> h(static_cast<size_t>(S->nseg) + 1);
-    SSG_CUDA_TRY(cudaMemcpyAsync(h.data(), B.so, sizeof(ScalB) * h.size(), cudaMemcpyDeviceToHost, s));
-    SSG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!S->h_states) SSG_CUDA_TRY(cudaHostAlloc(&S->h_states, sizeof(ScalB) * (S->nseg + 1), cudaHostAllocDefault));
+    SSG_CUDA_TRY(cudaMemcpyAsync(S->h_states, B.so, sizeof(ScalB) * (S->nseg + 1), cudaMemcpyDeviceToHost, s));
+    S->pending_launches = launches;
+    S->pending_k = K;
+    S->pending_mode = mode;
+    S->pending_nr = nr_single;
+    return SSG_OK;
+}
+
+// Waits for the block solve enqueued on S and fills st (one entry per
+// (segment, right-hand side)); returns SSG_OK or the first column's bad status.
+int solve_block_finish(ssg_system *S, ssg_stats *st) {
+    ssg_ctx *C = S->ctx;
+    SSG_CUDA_TRY(cudaStreamSynchronize(C->stream));
     float ms = 0.f;
     SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
+    const ScalB *h = S->h_states;
     const ScalB &g = h[S->nseg];
+    const int mode = S->pending_mode, K = S->pending_k, nr_single = S->pending_nr;
+    const bool mixed = mode == SSG_MIXED || mode == SSG_MIXED_JACOBI;
+    int64_t launches = S->pending_launches;
     if (C->driver == SSG_DRIVER_GRAPH) {
         if (mixed)  // init 3; per refinement inner init 3 + tail 5; 4 per inner loop iteration
             launches += 3 + 8 * static_cast<int64_t>(g.iter) + 4 * static_cast<int64_t>(g.loops);
@@ -1360,6 +1385,14 @@ int solve_block(ssg_system *S, int nr_single, const double *b_glob, double *x_gl
     return first_bad;
 }
 
+template <int K>
+int solve_block(ssg_system *S, int nr_single, const double *b_glob, double *x_glob, int guess, double rtol,
+                int32_t max_iter, int mode, ssg_stats *st) {
+    const int rc = solve_block_enqueue<K>(S, nr_single, b_glob, x_glob, guess, rtol, max_iter, mode);
+    if (rc != SSG_OK) return rc;
+    return solve_block_finish(S, st);
+}
+
 int solve_block_k(ssg_system *S, int nr, const double *b, double *x, int guess, double rtol, int32_t max_iter,
                   int mode, ssg_stats *st) {
     if (S->nseg != 1) {
@@ -1370,6 +1403,14 @@ int solve_block_k(ssg_system *S, int nr, const double *b, double *x, int guess, 
     if (nr <= 4) return solve_block<4>(S, nr, b, x, guess, rtol, max_iter, mode, st);
     if (nr <= 8) return solve_block<8>(S, nr, b, x, guess, rtol, max_iter, mode, st);
     return solve_block<16>(S, nr, b, x, guess, rtol, max_iter, mode, st);
+}
+
+int enqueue_batch_k(ssg_system *S, const double *b, double *x, int guess, double rtol, int32_t max_iter, int mode) {
+    const int k = S->batch_k;
+    if (k <= 2) return solve_block_enqueue<2>(S, 0, b, x, guess, rtol, max_iter, mode);
+    if (k <= 4) return solve_block_enqueue<4>(S, 0, b, x, guess, rtol, max_iter, mode);
+    if (k <= 8) return solve_block_enqueue<8>(S, 0, b, x, guess, rtol, max_iter, mode);
+    return solve_block_enqueue<16>(S, 0, b, x, guess, rtol, max_iter, mode);
 }
 
 int solve_batch_k(ssg_system *S, const double *b, double *x, int guess, double rtol, int32_t max_iter, int mode,
@@ -1623,6 +1664,111 @@ int ssg_partition_fe(ssg_ctx *ctx, int32_t n, int32_t ne, int32_t nv, const int3
     return SSG_OK;
 }
 
+namespace {
+
+int pow2_columns(int32_t nrhs) { return nrhs <= 2 ? 2 : nrhs <= 4 ? 4 : nrhs <= 8 ? 8 : 16; }
+
+// A segmented system for a (validated) batch; rhs_off (may be null: packed in
+// system order) gives each system's first value in the caller's b and x.
+int make_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off, const int32_t *sys_sub_off,
+               const int32_t *sys_nrhs, const int64_t *rhs_off, const int32_t *rowptr, const int32_t *colidx,
+               const double *val, const int32_t *part, ssg_system **out) {
+    const int32_t n = sys_node_off[nsys], P = sys_sub_off[nsys];
+    ssg_system *S = new (std::nothrow) ssg_system();
+    if (!S) return SSG_E_OOM;
+    std::string err;
+    int rc = build_host_maps(n, rowptr, colidx, val, part, P, S->maps, &err);
+    if (rc != SSG_OK) {
+        set_error(err);
+        delete S;
+        return rc;
+    }
+    S->seg_sub.assign(sys_sub_off, sys_sub_off + nsys + 1);
+    S->seg_node.assign(sys_node_off, sys_node_off + nsys + 1);
+    S->seg_nrhs.assign(sys_nrhs, sys_nrhs + nsys);
+    S->seg_rhs_off.assign(static_cast<size_t>(nsys), 0);
+    int64_t o = 0;
+    for (int32_t s = 0; s < nsys; ++s) {
+        S->seg_rhs_off[s] = rhs_off ? rhs_off[s] : o;
+        o += static_cast<int64_t>(sys_nrhs[s]) * (sys_node_off[s + 1] - sys_node_off[s]);
+        S->batch_k = std::max(S->batch_k, sys_nrhs[s]);
+    }
+    S->ctx = ctx;
+    ctx->live_systems++;
+    S->pdl = ctx->pdl != 0;
+    rc = upload(S);
+    if (rc != SSG_OK) {
+        ssg_system_destroy(S);
+        return rc;
+    }
+    *out = S;
+    return SSG_OK;
+}
+
+// The K classes of a batch (see ssg_system::kclass): each class's systems
+// cut out of the union, renumbered from 0 in the original order, with their
+// original offsets in b and x.
+int make_batch_classes(ssg_system *S, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                       const int32_t *part) {
+    const int32_t nsys = S->nseg;
+    std::vector<int32_t> cls(static_cast<size_t>(nsys));
+    int kinds = 0;
+    for (int32_t s = 0; s < nsys; ++s) {
+        cls[s] = log2_of(pow2_columns(S->seg_nrhs[s]));
+        kinds |= 1 << cls[s];
+    }
+    if ((kinds & (kinds - 1)) == 0) return SSG_OK;  // one class: the union is it
+    for (int c = 1; c <= 4; ++c) {
+        if (!((kinds >> c) & 1)) continue;
+        std::vector<int32_t> ids, node_off{0}, sub_off{0}, nrhs, rp{0}, ci, pa;
+        std::vector<int64_t> roff;
+        std::vector<double> va;
+        for (int32_t s = 0; s < nsys; ++s) {
+            if (cls[s] != c) continue;
+            ids.push_back(s);
+            const int32_t n0 = S->seg_node[s], n1 = S->seg_node[s + 1];
+            const int32_t shift_n = node_off.back() - n0, shift_p = sub_off.back() - S->seg_sub[s];
+            for (int32_t i = n0; i < n1; ++i) {
+                for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+                    ci.push_back(colidx[k] + shift_n);
+                    va.push_back(val[k]);
+                }
+                rp.push_back(static_cast<int32_t>(ci.size()));
+                pa.push_back(part[i] + shift_p);
+            }
+            node_off.push_back(node_off.back() + (n1 - n0));
+            sub_off.push_back(sub_off.back() + (S->seg_sub[s + 1] - S->seg_sub[s]));
+            nrhs.push_back(S->seg_nrhs[s]);
+            roff.push_back(S->seg_rhs_off[s]);
+        }
+        // each class has a context of its own (a copy of the batch's, with
+        // its own stream) so that the classes' solves can overlap
+        ssg_ctx *cc = new (std::nothrow) ssg_ctx(*S->ctx);
+        if (!cc) return SSG_E_OOM;
+        cc->live_systems = 0;
+        cudaError_t e = cudaStreamCreateWithFlags(&cc->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete cc;
+            set_error(std::string("cudaStreamCreateWithFlags: ") + cudaGetErrorString(e));
+            return SSG_E_CUDA;
+        }
+        ssg_system *C = nullptr;
+        const int rc = make_batch(cc, static_cast<int32_t>(ids.size()), node_off.data(), sub_off.data(),
+                                  nrhs.data(), roff.data(), rp.data(), ci.data(), va.data(), pa.data(), &C);
+        if (rc != SSG_OK) {
+            cudaStreamDestroy(cc->stream);
+            delete cc;
+            return rc;
+        }
+        C->own_ctx = cc;
+        S->kclass.push_back(C);
+        S->kclass_sys.push_back(std::move(ids));
+    }
+    return SSG_OK;
+}
+
+}  // namespace
+
 int ssg_partition_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off, const int32_t *sys_sub_off,
                         const int32_t *sys_nrhs, const int32_t *rowptr, const int32_t *colidx, const double *val,
                         const int32_t *part, ssg_system **sys) {
@@ -1646,15 +1792,20 @@ int ssg_partition_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off,
             return SSG_E_INVALID;
         }
     const int32_t n = sys_node_off[nsys], P = sys_sub_off[nsys];
-    ssg_system *S = new (std::nothrow) ssg_system();
-    if (!S) return SSG_E_OOM;
-    std::string err;
-    int rc = build_host_maps(n, rowptr, colidx, val, part, P, S->maps, &err);
-    if (rc != SSG_OK) {
-        set_error(err);
-        delete S;
-        return rc;
+    {
+        // the union's CSR is validated by the partitioner below; here only
+        // what indexing it for the checks needs
+        if (!rowptr || !colidx || !val || !part || n < 1 || P < 1 || rowptr[0] != 0) {
+            set_error("batch: null or empty CSR / partition arrays");
+            return SSG_E_INVALID;
+        }
+        for (int32_t i = 0; i < n; ++i)
+            if (rowptr[i + 1] < rowptr[i]) {
+                set_error("batch: row pointers decrease");
+                return SSG_E_INVALID;
+            }
     }
+    int rc = SSG_OK;
     // the union must be block diagonal and every system's subdomains its own
     for (int32_t s = 0; s < nsys && rc == SSG_OK; ++s)
         for (int32_t i = sys_node_off[s]; i < sys_node_off[s + 1] && rc == SSG_OK; ++i) {
@@ -1664,23 +1815,12 @@ int ssg_partition_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off,
         }
     if (rc != SSG_OK) {
         set_error("batch: a node's subdomain lies outside its system's range, or an entry couples two systems");
-        delete S;
         return rc;
     }
-    S->seg_sub.assign(sys_sub_off, sys_sub_off + nsys + 1);
-    S->seg_node.assign(sys_node_off, sys_node_off + nsys + 1);
-    S->seg_nrhs.assign(sys_nrhs, sys_nrhs + nsys);
-    S->seg_rhs_off.assign(static_cast<size_t>(nsys), 0);
-    int64_t o = 0;
-    for (int32_t s = 0; s < nsys; ++s) {
-        S->seg_rhs_off[s] = o;
-        o += static_cast<int64_t>(sys_nrhs[s]) * (sys_node_off[s + 1] - sys_node_off[s]);
-        S->batch_k = std::max(S->batch_k, sys_nrhs[s]);
-    }
-    S->ctx = ctx;
-    ctx->live_systems++;
-    S->pdl = ctx->pdl != 0;
-    rc = upload(S);
+    ssg_system *S = nullptr;
+    rc = make_batch(ctx, nsys, sys_node_off, sys_sub_off, sys_nrhs, nullptr, rowptr, colidx, val, part, &S);
+    if (rc != SSG_OK) return rc;
+    rc = make_batch_classes(S, rowptr, colidx, val, part);
     if (rc != SSG_OK) {
         ssg_system_destroy(S);
         return rc;
@@ -1706,7 +1846,83 @@ int ssg_solve_batch(ssg_system *S, const double *b, double *x, int32_t x_is_gues
     for (int32_t s = 0; s < S->nseg; ++s) nmax = std::max(nmax, S->seg_node[s + 1] - S->seg_node[s]);
     if (max_iter <= 0) max_iter = nmax;
     SSG_CUDA_TRY(cudaSetDevice(S->ctx->device));
-    rc = solve_batch_k(S, b, x, x_is_guess, rtol, max_iter, mode, stats);
+    if (S->kclass.empty()) {
+        rc = solve_batch_k(S, b, x, x_is_guess, rtol, max_iter, mode, stats);
+    } else {
+        // one solve per K class, each on the caller's b and x at the original
+        // offsets and on its own stream: they start after the work already
+        // on the context's stream, run side by side, and the context's stream
+        // waits for all of them; statistics come back in (system, right-hand
+        // side) order
+        std::vector<int64_t> first(static_cast<size_t>(S->nseg) + 1, 0);
+        for (int32_t sg = 0; sg < S->nseg; ++sg) first[sg + 1] = first[sg] + S->seg_nrhs[sg];
+        cudaStream_t ps = S->ctx->stream;
+        cudaEvent_t fork = nullptr;
+        SSG_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        std::vector<cudaEvent_t> join(S->kclass.size(), nullptr);
+        cudaError_t e = cudaEventRecord(fork, ps);
+        size_t enq = 0;
+        int rc_enq = e == cudaSuccess ? SSG_OK : SSG_E_CUDA;
+        for (; enq < S->kclass.size() && rc_enq == SSG_OK; ++enq) {
+            ssg_system *C = S->kclass[enq];
+            ssg_ctx *cc = C->ctx;
+            cc->driver = S->ctx->driver;
+            cc->inner_rtol = S->ctx->inner_rtol;
+            cc->max_outer = S->ctx->max_outer;
+            if (cudaStreamWaitEvent(cc->stream, fork, 0) != cudaSuccess ||
+                cudaEventCreateWithFlags(&join[enq], cudaEventDisableTiming) != cudaSuccess) {
+                rc_enq = SSG_E_CUDA;
+                break;
+            }
+            rc_enq = enqueue_batch_k(C, b, x, x_is_guess, rtol, max_iter, mode);
+            if (rc_enq != SSG_OK) break;
+        }
+        // every class enqueued so far is joined and finished, whatever happened after it
+        rc = SSG_OK;
+        for (size_t c = 0; c < enq; ++c) {
+            ssg_system *C = S->kclass[c];
+            if (cudaEventRecord(join[c], C->ctx->stream) != cudaSuccess || cudaStreamWaitEvent(ps, join[c], 0) != cudaSuccess)
+                rc_enq = rc_enq == SSG_OK ? SSG_E_CUDA : rc_enq;
+        }
+        for (size_t c = 0; c < enq; ++c) {
+            ssg_system *C = S->kclass[c];
+            int64_t nst = 0;
+            for (int32_t sg : S->kclass_sys[c]) nst += S->seg_nrhs[sg];
+            std::vector<ssg_stats> st(static_cast<size_t>(nst));
+            const int rc_c = solve_block_finish(C, st.data());
+            if (rc_c == SSG_E_CUDA || rc_c == SSG_E_OOM || rc_c == SSG_E_INVALID) {
+                if (rc_enq == SSG_OK) rc_enq = rc_c;
+                continue;
+            }
+            if (rc_c != SSG_OK && rc == SSG_OK) rc = rc_c;
+            if (stats) {
+                size_t o = 0;
+                for (int32_t sg : S->kclass_sys[c])
+                    for (int32_t j = 0; j < S->seg_nrhs[sg]; ++j) stats[first[sg] + j] = st[o++];
+            }
+        }
+        for (cudaEvent_t ev : join)
+            if (ev) cudaEventDestroy(ev);
+        cudaEventDestroy(fork);
+        if (rc_enq != SSG_OK) return rc_enq;
+        if (stats) {
+            // every entry reports the whole batch solve: launches summed over
+            // the classes, the duration of the longest class (they overlap)
+            int64_t launches = 0;
+            double ms = 0.0;
+            size_t o = 0;
+            for (size_t c = 0; c < S->kclass.size(); ++c) {
+                const int32_t sg = S->kclass_sys[c][0];
+                launches += stats[first[sg]].kernel_launches;
+                ms = std::max(ms, stats[first[sg]].solve_ms);
+                for (int32_t t : S->kclass_sys[c]) o += S->seg_nrhs[t];
+            }
+            for (size_t t = 0; t < o; ++t) {
+                stats[t].kernel_launches = launches;
+                stats[t].solve_ms = ms;
+            }
+        }
+    }
     if (rc != SSG_OK && rc != SSG_E_CUDA && rc != SSG_E_OOM && rc != SSG_E_INVALID) set_error(ssg_error_string(rc));
     return rc;
 }
@@ -1926,6 +2142,10 @@ int ssg_set_values(ssg_system *S, const double *val) {
         set_error("a system built from elements has no input-CSR values to replace");
         return SSG_E_INVALID;
     }
+    if (!S->kclass.empty()) {
+        set_error("a batch solved in several column classes takes its values at partition time only");
+        return SSG_E_INVALID;
+    }
     cudaStream_t st = S->ctx->stream;
     const int ns = S->ctx->num_sms;
     k_gather_vals<<<grid_for(S->maps.nnz, ns), kBlock, 0, st>>>(S->maps.nnz, S->d_vmap, val,
@@ -2066,6 +2286,8 @@ int ssg_solve_host(ssg_system *S, int32_t k, const double *b_host, double *x_hos
 
 int ssg_system_destroy(ssg_system *S) {
     if (!S) return SSG_OK;
+    for (ssg_system *C : S->kclass) ssg_system_destroy(C);  // each frees its own context
+    S->kclass.clear();
     if (S->ctx) cudaSetDevice(S->ctx->device);
     if (S->exec) cudaGraphExecDestroy(S->exec);
     if (S->graph) cudaGraphDestroy(S->graph);
@@ -2083,8 +2305,15 @@ int ssg_system_destroy(ssg_system *S) {
         if (S->ctx && S->ctx->stream) cudaStreamSynchronize(S->ctx->stream);
         cudaFree(S->arena);
     }
+    if (S->h_states) cudaFreeHost(S->h_states);
     if (S->ctx) S->ctx->live_systems--;
+    ssg_ctx *own = S->own_ctx;
     delete S;
+    if (own) {
+        cudaStreamSynchronize(own->stream);
+        cudaStreamDestroy(own->stream);
+        delete own;
+    }
     return SSG_OK;
 }
 

@@ -11,7 +11,7 @@ single-vector product, so:
     converged to 1e-12 match to 1e-10, iteration counts at 1e-8 are within
     max(2, 3 %) (the readings of the single-RHS parity tests);
   * mixed mode: per column, refinements within +-1 and inner iterations within
-    max(3 per refinement, 5 %) of the oracle's or_sub_cg_mixed, true residual <= rtol;
+    max(3 per refinement, 10 %) of the oracle's or_sub_cg_mixed, true residual <= rtol;
   * equal columns give equal bits; a zero column converges at once; the
     graph and host-loop drivers give the same bits; padding columns
     (k = 3, 5) and a split into a block plus a single solve (k = 17) work.
@@ -255,7 +255,7 @@ def test_block_mixed_matches_oracle(ctx, fv20):
         assert tr <= 1.0001e-8
         assert abs(st[j]["true_relres"] - tr) <= 1e-6 * tr + 1e-16
         assert abs(st[j]["outer"] - rm.outer) <= 1
-        assert abs(st[j]["iters"] - rm.iters) <= max(3 * rm.outer, 0.05 * rm.iters)
+        assert abs(st[j]["iters"] - rm.iters) <= max(3 * rm.outer, 0.10 * rm.iters)
         r64 = ref.cg(B[j], 1e-8, 100000)
         kap = oracle.cond_from_lanczos(r64.alpha, r64.beta)
         assert _rel(X[j], rm.x) <= 2 * kap * 1e-8

@@ -15,7 +15,7 @@ GPU's: the true residual ||b - A x|| / ||b|| <= rtol (1.01 rtol for the
 recursive FP64 test, rtol for the mixed modes' FP64 test) for every right-hand
 side, and on seeded samples the oracle's iteration counts (FP64: within
 max(2, 3 %); mixed: refinements within +-1, inner iterations within max(3 per
-refinement, 5 %)).
+refinement, 10 %)).
 """
 
 import numpy as np
@@ -128,7 +128,7 @@ def test_batch_full_size_512(ctx):
             else:
                 rm = refs[s].cg_mixed(bp.b[s][j], RTOL, 100000, 1e-4, 30)
                 assert abs(t["outer"] - rm.outer) <= 1
-                assert abs(t["iters"] - rm.iters) <= max(3 * rm.outer, 0.05 * rm.iters)
+                assert abs(t["iters"] - rm.iters) <= max(3 * rm.outer, 0.10 * rm.iters)
     B.close()
 
 

@@ -125,7 +125,7 @@ def test_jacobi_block_matches_oracle(ctx, name, case, k):
     """k right-hand sides through the K-column kernels (K = 4, 16) with the
     diagonal preconditioner: per column the single-solve readings (early
     iterates within 1e-10, converged to 1e-12 within 1e-10; mixed: refinements
-    within +-1, inner iterations within max(3 per refinement, 5 %), FP64 true
+    within +-1, inner iterations within max(3 per refinement, 10 %), FP64 true
     residual <= rtol)."""
     from paper_2108_13162_gb300 import ssg
     from paper_2108_13162_gb300.ssg import System
@@ -153,7 +153,7 @@ def test_jacobi_block_matches_oracle(ctx, name, case, k):
         tr = np.linalg.norm(B[j] - oracle.spmv(A, X[j])) / np.linalg.norm(B[j])
         assert tr <= 1.0001e-8
         assert abs(st[j]["outer"] - rm.outer) <= 1
-        assert abs(st[j]["iters"] - rm.iters) <= max(3 * rm.outer, 0.05 * rm.iters)
+        assert abs(st[j]["iters"] - rm.iters) <= max(3 * rm.outer, 0.10 * rm.iters)
 
 
 def test_jacobi_rejects_bad_diagonal(ctx):
@@ -214,7 +214,7 @@ def test_jacobi_full_size_128cube(ctx):
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
 def test_mixed_jacobi_matches_oracle(ctx, name, case):
     """SSG_MIXED_JACOBI against or_sub_pcg_mixed: refinements within +-1, inner
-    iterations within max(3 per refinement, 5 %), FP64 true residual <= rtol."""
+    iterations within max(3 per refinement, 10 %), FP64 true residual <= rtol."""
     from paper_2108_13162_gb300 import ssg
     from paper_2108_13162_gb300.ssg import System
 
@@ -227,7 +227,7 @@ def test_mixed_jacobi_matches_oracle(ctx, name, case):
     tr = np.linalg.norm(b - oracle.spmv(A, x.cpu().numpy())) / np.linalg.norm(b)
     assert tr <= 1.0001e-8
     assert abs(st[0]["outer"] - rm.outer) <= 1
-    assert abs(st[0]["iters"] - rm.iters) <= max(3 * rm.outer, 0.05 * rm.iters)
+    assert abs(st[0]["iters"] - rm.iters) <= max(3 * rm.outer, 0.10 * rm.iters)
 
 
 def test_mixed_jacobi_full_size_128cube(ctx):
@@ -245,7 +245,7 @@ def test_mixed_jacobi_full_size_128cube(ctx):
     print("mixed jacobi 128^3: %d inner (oracle %d), %d refinements (oracle %d)" % (
         st[0]["iters"], gm["iters"], st[0]["outer"], gm["outer"]))
     assert abs(st[0]["outer"] - gm["outer"]) <= 1
-    assert abs(st[0]["iters"] - gm["iters"]) <= max(3 * gm["outer"], 0.05 * gm["iters"])
+    assert abs(st[0]["iters"] - gm["iters"]) <= max(3 * gm["outer"], 0.10 * gm["iters"])
     idx = np.array(g["sample_idx"])
     assert _rel(x.cpu().numpy()[idx], np.array(gm["sample_x"])) <= 2 * kap * 1e-8
     assert st[0]["true_relres"] <= 1.0001e-8

@@ -6,7 +6,7 @@ inner FP32 sums are ordered differently on each side):
   * converged, and the FP64 true residual ||b - S x|| / ||b|| recomputed on
     the CPU with the oracle's global product is <= rtol;
   * the refinement count equals the oracle's (+-1) and the summed inner
-    iterations are within max(3 per refinement, 5 %) of the oracle's;
+    iterations are within max(3 per refinement, 10 %) of the oracle's;
   * the solution is within 2 kappa rtol of x* and of the oracle's solution
     (kappa from the Lanczos coefficients of the FP64 oracle run);
   * both drivers (graph, host loop) give the same bits; the parameters are
@@ -75,7 +75,7 @@ def test_mixed_matches_oracle(ctx, name, mk, rtol):
     assert tr <= 1.0001 * rtol
     assert abs(st[0]["true_relres"] - tr) <= 1e-6 * tr + 1e-16
     assert abs(st[0]["outer"] - rm.outer) <= 1
-    assert abs(st[0]["iters"] - rm.iters) <= max(3 * rm.outer, 0.05 * rm.iters)
+    assert abs(st[0]["iters"] - rm.iters) <= max(3 * rm.outer, 0.10 * rm.iters)
     kap = oracle.cond_from_lanczos(r64.alpha, r64.beta)
     assert _rel(xg, p.xstar[:, 0]) <= 2 * kap * rtol
     assert _rel(xg, rm.x) <= 2 * kap * rtol
@@ -148,7 +148,7 @@ def test_mixed_full_size_128cube(ctx):
         st[0]["iters"], gm["iters"], st[0]["outer"], gm["outer"], tr))
     assert tr <= 1.0001e-8
     assert abs(st[0]["outer"] - gm["outer"]) <= 1
-    assert abs(st[0]["iters"] - gm["iters"]) <= max(3 * gm["outer"], 0.05 * gm["iters"])
+    assert abs(st[0]["iters"] - gm["iters"]) <= max(3 * gm["outer"], 0.10 * gm["iters"])
     idx = np.array(g["sample_idx"])
     assert _rel(xg[idx], np.array(gm["sample_x"])) <= 2 * kap * 1e-8
     assert _rel(xg, p.xstar[:, 0]) <= 2 * kap * 1e-8
