@@ -115,15 +115,6 @@ struct ssg_system {
     } blk;
 };
 
-#define SSG_CUDA_TRY(call)                                                                      \
-    do {                                                                                        \
-        cudaError_t e_ = (call);                                                                \
-        if (e_ != cudaSuccess) {                                                                \
-            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                      \
-            return e_ == cudaErrorMemoryAllocation ? SSG_E_OOM : SSG_E_CUDA;                    \
-        }                                                                                       \
-    } while (0)
-
 namespace {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

@@ -294,15 +294,6 @@ struct ssg_band {
 
 namespace {
 
-#define BAND_CUDA_TRY(call)                                                   \
-    do {                                                                      \
-        cudaError_t e_ = (call);                                              \
-        if (e_ != cudaSuccess) {                                              \
-            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));    \
-            return e_ == cudaErrorMemoryAllocation ? SSG_E_OOM : SSG_E_CUDA;  \
-        }                                                                     \
-    } while (0)
-
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 bool variant_valid(const ssg_band *B, int32_t v) {
@@ -354,7 +345,7 @@ int launch_variant(ssg_band *B, int32_t v, const double *x, double *y) {
             default: set_error("unknown band kernel variant"); return SSG_E_INVALID;
         }
     }
-    BAND_CUDA_TRY(cudaGetLastError());
+    SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
 }
 
@@ -400,28 +391,28 @@ int upload_band(ssg_band *B) {
     const size_t b_val = up256(sizeof(double) * (B->nnz + 4));
     const size_t b_tile = up256(sizeof(int32_t) * tile.size());
     char *a = nullptr;
-    BAND_CUDA_TRY(cudaMalloc(&a, b_rp + b_col + b_val + b_tile));
+    SSG_CUDA_TRY(cudaMalloc(&a, b_rp + b_col + b_val + b_tile));
     B->arena = a;
     cudaStream_t st = B->ctx->stream;
     int32_t *d_rp = reinterpret_cast<int32_t *>(a);
     int32_t *d_col = reinterpret_cast<int32_t *>(a + b_rp);
     double *d_val = reinterpret_cast<double *>(a + b_rp + b_col);
     int32_t *d_tile = reinterpret_cast<int32_t *>(a + b_rp + b_col + b_val);
-    BAND_CUDA_TRY(cudaMemsetAsync(a, 0, b_rp + b_col + b_val + b_tile, st));
-    BAND_CUDA_TRY(cudaMemcpyAsync(d_rp, B->rowptr.data(), sizeof(int32_t) * (B->n + 1), cudaMemcpyHostToDevice, st));
+    SSG_CUDA_TRY(cudaMemsetAsync(a, 0, b_rp + b_col + b_val + b_tile, st));
+    SSG_CUDA_TRY(cudaMemcpyAsync(d_rp, B->rowptr.data(), sizeof(int32_t) * (B->n + 1), cudaMemcpyHostToDevice, st));
     if (B->nnz > 0) {
-        BAND_CUDA_TRY(cudaMemcpyAsync(d_col, B->colidx.data(), sizeof(int32_t) * B->nnz, cudaMemcpyHostToDevice, st));
-        BAND_CUDA_TRY(cudaMemcpyAsync(d_val, B->val.data(), sizeof(double) * B->nnz, cudaMemcpyHostToDevice, st));
+        SSG_CUDA_TRY(cudaMemcpyAsync(d_col, B->colidx.data(), sizeof(int32_t) * B->nnz, cudaMemcpyHostToDevice, st));
+        SSG_CUDA_TRY(cudaMemcpyAsync(d_val, B->val.data(), sizeof(double) * B->nnz, cudaMemcpyHostToDevice, st));
     }
-    BAND_CUDA_TRY(cudaMemcpyAsync(d_tile, tile.data(), sizeof(int32_t) * tile.size(), cudaMemcpyHostToDevice, st));
-    BAND_CUDA_TRY(cudaHostAlloc(&B->h_err, sizeof(int), cudaHostAllocMapped));
+    SSG_CUDA_TRY(cudaMemcpyAsync(d_tile, tile.data(), sizeof(int32_t) * tile.size(), cudaMemcpyHostToDevice, st));
+    SSG_CUDA_TRY(cudaHostAlloc(&B->h_err, sizeof(int), cudaHostAllocMapped));
     *B->h_err = 0;
     int *d_err = nullptr;
-    BAND_CUDA_TRY(cudaHostGetDevicePointer(&d_err, B->h_err, 0));
-    BAND_CUDA_TRY(cudaFuncSetAttribute(k_band_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmem));
-    BAND_CUDA_TRY(cudaFuncSetAttribute(k_band_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmem));
+    SSG_CUDA_TRY(cudaHostGetDevicePointer(&d_err, B->h_err, 0));
+    SSG_CUDA_TRY(cudaFuncSetAttribute(k_band_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmem));
+    SSG_CUDA_TRY(cudaFuncSetAttribute(k_band_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmem));
     B->dev = BandDev{B->n, B->nb, B->n / B->nb, d_rp, d_col, d_val, d_tile, ntiles, d_err};
-    BAND_CUDA_TRY(cudaStreamSynchronize(st));
+    SSG_CUDA_TRY(cudaStreamSynchronize(st));
     return SSG_OK;
 }
 
@@ -579,7 +570,7 @@ int ssg_band_autotune(ssg_band *band, int32_t reps, ssg_band_tune *out) {
     const int32_t codes[7] = {SSG_BAND_STAGED, 1, 2, 4, 8, 16, 32};
     cudaStream_t st = band->ctx->stream;
     double *xy = nullptr;
-    BAND_CUDA_TRY(cudaMalloc(&xy, sizeof(double) * 2 * static_cast<size_t>(band->n)));
+    SSG_CUDA_TRY(cudaMalloc(&xy, sizeof(double) * 2 * static_cast<size_t>(band->n)));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -623,12 +614,12 @@ int ssg_band_autotune(ssg_band *band, int32_t reps, ssg_band_tune *out) {
 int ssg_band_check_timeout(ssg_band *band) {
     int rc = check_band(band);
     if (rc != SSG_OK) return rc;
-    BAND_CUDA_TRY(cudaStreamSynchronize(band->ctx->stream));
+    SSG_CUDA_TRY(cudaStreamSynchronize(band->ctx->stream));
     rc = check_err_flag(band);
     if (rc != SSG_OK) return rc;
     k_band_wait_probe<<<1, 32, 0, band->ctx->stream>>>(band->dev.err);
-    BAND_CUDA_TRY(cudaGetLastError());
-    BAND_CUDA_TRY(cudaStreamSynchronize(band->ctx->stream));
+    SSG_CUDA_TRY(cudaGetLastError());
+    SSG_CUDA_TRY(cudaStreamSynchronize(band->ctx->stream));
     rc = check_err_flag(band);
     *band->h_err = 0;  // the probe's flag is its result, not a fault of the operator
     return rc;

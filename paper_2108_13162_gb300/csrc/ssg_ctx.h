@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 #include "ssg.h"
 
@@ -20,3 +21,18 @@ struct ssg_ctx {
     int32_t max_outer = 30;    // SSG_MIXED: refinement steps cap
     int32_t rhs_block = 16;    // right-hand sides solved together (1, 2, 4, 8 or 16)
 };
+
+namespace ssg {
+void set_error(const std::string &msg);
+}
+
+// Return SSG_E_OOM / SSG_E_CUDA (with the call and CUDA's message as the last
+// error) from the enclosing function when a CUDA runtime call fails.
+#define SSG_CUDA_TRY(call)                                                                      \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) {                                                                \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+            return e_ == cudaErrorMemoryAllocation ? SSG_E_OOM : SSG_E_CUDA;                    \
+        }                                                                                       \
+    } while (0)
