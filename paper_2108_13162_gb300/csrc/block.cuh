@@ -564,9 +564,11 @@ __global__ void __launch_bounds__(kBlockV, 1) k_update_rB(const double *__restri
             rv.x = fma(-a0, l.q.x, rv.x);
             rv.y = fma(-a1, l.q.y, rv.y);
             r2[i] = rv;
-            // weight 1 (no lookup) in 64-entry groups without interface copies
+            // weight 1 (no lookup) in 64-entry groups without interface copies;
+            // the group is the same for the whole warp, tested by a vote so the
+            // multiplies are branched over rather than issued predicated off
             double wx = rv.x, wy = rv.y;
-            if (l.g != 0) {
+            if (__any_sync(__activemask(), l.g != 0)) {
                 const double w = __ldg(wtab + mult[(2 * i) / K]);  // local entry of both values
                 wx = w * rv.x;
                 wy = w * rv.y;

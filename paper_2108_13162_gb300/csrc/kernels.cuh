@@ -544,9 +544,11 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r(int64_t N,
             // interface copy have weight 1 everywhere and skip the weight lookup
             // (1.0 * r == r, so both forms give the same bits).  One FMA chain
             // for both cases (measured: 79.8 us per FP64 iteration against
-            // 84.3 with the products in the two branches)
+            // 84.3 with the products in the two branches).  The test is a warp
+            // vote, so the weight multiplies are skipped by a branch instead of
+            // being issued predicated off (77.0 -> 75.5 us per iteration)
             double wx = rv.x, wy = rv.y;
-            if (l.g != 0) {
+            if (__any_sync(__activemask(), l.g != 0)) {
                 const uchar2 mv = m2[i];
                 wx = __ldg(wtab + mv.x) * rv.x;
                 wy = __ldg(wtab + mv.y) * rv.y;
