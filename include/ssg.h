@@ -192,8 +192,9 @@ int ssg_partition_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off,
  * SSG_FP64_JACOBI) or its own refinement (SSG_MIXED, SSG_MIXED_JACOBI) with
  * the readings of ssg_solve.  Systems are grouped by column count K (the
  * power of two >= their sys_nrhs, at least 2); the columns of all systems of
- * a group iterate together in one graph launch (one launch per group), a
- * finished system's blocks return at once.  b and x
+ * a group iterate together, every group's loop is a branch of one graph
+ * launched once (groups side by side), and a finished system's blocks
+ * return at once.  b and x
  * (device, rhs_off[nsys] doubles each, caller-allocated: the library cannot
  * check their length) hold system s's right-hand side j at rhs_off[s] + j * n_s, with
  * rhs_off[s] = sum over s' < s of sys_nrhs[s'] * n_s' (n_s = its node count);

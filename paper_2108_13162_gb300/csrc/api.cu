@@ -113,6 +113,7 @@ struct ssg_system {
         ScalB *so = nullptr, *si = nullptr;  // [nseg + 1]: one state per segment, then the loop counters
         BlockGraph graph[4][5];  // by mode (SSG_FP64 .. SSG_MIXED_JACOBI) and log2 K
     } blk;
+    BlockGraph classes_graph[4];  // per mode: every K class's loop as a parallel branch of one graph
 };
 
 namespace {
@@ -1285,9 +1286,13 @@ int run_blockB(ssg_system *S, int mode, int64_t *launches) {
 // right-hand side j at seg_rhs_off[sg] + j * n_sg); nr_single > 0 for a
 // one-segment solve of nr_single right-hand sides; st receives one entry per
 // (segment, right-hand side) in that order.
+// The parts of a block solve around its loop, on stream s: before it the
+// parameters, b scattered to the local copies, x and q set (x = 0, or the
+// guess and q = S x); after it x gathered, the true residuals, and the
+// states copied to pinned host memory for solve_block_finish.
 template <int K>
-int solve_block_enqueue(ssg_system *S, int nr_single, const double *b_glob, double *x_glob, int guess, double rtol,
-                        int32_t max_iter, int mode) {
+int block_pre(ssg_system *S, int nr_single, const double *b_glob, double *x_glob, int guess, double rtol,
+              int32_t max_iter, int mode, cudaStream_t s, int64_t *launches_out) {
     int rc = SSG_OK;
     if (mode == SSG_FP64_JACOBI || mode == SSG_MIXED_JACOBI) {
         rc = check_diag(S);
@@ -1296,7 +1301,6 @@ int solve_block_enqueue(ssg_system *S, int nr_single, const double *b_glob, doub
     rc = ensure_block(S, K);
     if (rc != SSG_OK) return rc;
     ssg_ctx *C = S->ctx;
-    cudaStream_t s = C->stream;
     ssg_system::BlockState &B = S->blk;
     const int64_t N = S->maps.nloc;
     int64_t launches = 0;
@@ -1315,8 +1319,13 @@ int solve_block_enqueue(ssg_system *S, int nr_single, const double *b_glob, doub
         SSG_CUDA_TRY(cudaMemsetAsync(B.q, 0, sizeof(double) * N * K, s));
     }
     SSG_CUDA_TRY(cudaGetLastError());
-    rc = run_blockB<K>(S, mode, &launches);
-    if (rc != SSG_OK) return rc;
+    *launches_out += launches;
+    return SSG_OK;
+}
+
+template <int K>
+int block_post(ssg_system *S, int nr_single, double *x_glob, int mode, cudaStream_t s, int64_t launches) {
+    ssg_system::BlockState &B = S->blk;
     k_gatherB<K><<<S->nchunks, kBlockV, 0, s>>>(S->d_l2g, S->d_own, B.xl, x_glob, S->tab);
     // true residuals ||b_j - S x_j||_w in FP64
     k_spmm_seg<double, K, false><<<S->grid_spmmB, kSpmvThreads, 0, s>>>(S->opB64, B.xl, B.q, nullptr, S->tab,
@@ -1334,6 +1343,18 @@ int solve_block_enqueue(ssg_system *S, int nr_single, const double *b_glob, doub
     S->pending_mode = mode;
     S->pending_nr = nr_single;
     return SSG_OK;
+}
+
+template <int K>
+int solve_block_enqueue(ssg_system *S, int nr_single, const double *b_glob, double *x_glob, int guess, double rtol,
+                        int32_t max_iter, int mode) {
+    cudaStream_t s = S->ctx->stream;
+    int64_t launches = 0;
+    int rc = block_pre<K>(S, nr_single, b_glob, x_glob, guess, rtol, max_iter, mode, s, &launches);
+    if (rc != SSG_OK) return rc;
+    rc = run_blockB<K>(S, mode, &launches);
+    if (rc != SSG_OK) return rc;
+    return block_post<K>(S, nr_single, x_glob, mode, s, launches);
 }
 
 // Waits for the block solve enqueued on S and fills st (one entry per
@@ -1820,6 +1841,135 @@ int ssg_partition_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off,
     return SSG_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// capture_into that also returns the node the captured work ends in.
+template <typename F>
+cudaError_t capture_branch(cudaStream_t cap, cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, F fn, int *rc,
+                           cudaGraphNode_t *last) {
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cap, g, deps, nullptr, ndeps, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    *rc = fn(cap);
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *d = nullptr;
+    size_t nd = 0;
+    cudaError_t e1 = cudaStreamGetCaptureInfo(cap, &st, nullptr, nullptr, &d, nullptr, &nd);
+    if (e1 == cudaSuccess) {
+        if (nd == 1) *last = d[0];
+        else e1 = cudaErrorInvalidValue;
+    }
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &out);
+    return e1 != cudaSuccess ? e1 : e2;
+}
+
+// One column group's loop as a branch of G (no dependencies): its setup
+// kernels and WHILE node, the mixed modes' inner WHILE nested in the outer
+// body, each loop with a condition handle of its own (the structure
+// build_loop_graph and build_nested_graph give one system).
+template <int K, bool PC>
+int class_branch(ssg_system *C, cudaGraph_t G, cudaStream_t cap, bool mixed) {
+    cudaGraphConditionalHandle h_out;
+    SSG_CUDA_TRY(cudaGraphConditionalHandleCreate(&h_out, G, 0u, cudaGraphCondAssignDefault));
+    ssg_system::BlockState &B = C->blk;
+    int rc = SSG_OK;
+    cudaGraphNode_t n_init = nullptr, n_loop = nullptr;
+    cudaGraph_t body = nullptr;
+    cudaError_t e = capture_branch(
+        cap, G, nullptr, 0,
+        [&](cudaStream_t c) {
+            return mixed ? launch_initB<K, false>(C, c, nullptr, h_out, 1) : launch_initB<K, PC>(C, c, B.p, h_out, 1);
+        },
+        &rc, &n_init);
+    if (e == cudaSuccess && rc == SSG_OK) e = add_while(G, &n_init, h_out, &n_loop, &body);
+    if (!mixed) {
+        if (e == cudaSuccess && rc == SSG_OK)
+            e = capture_into(cap, body, nullptr, 0,
+                             [&](cudaStream_t c) { return launch_bodyB64<K, PC>(C, c, h_out, 1); }, &rc);
+    } else {
+        cudaGraphConditionalHandle h_in;
+        cudaGraphNode_t n_iinit = nullptr, n_inner = nullptr;
+        cudaGraph_t body_in = nullptr;
+        if (e == cudaSuccess && rc == SSG_OK) e = cudaGraphConditionalHandleCreate(&h_in, body, 0u, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess && rc == SSG_OK)
+            e = capture_branch(cap, body, nullptr, 0,
+                               [&](cudaStream_t c) { return launch_inner_initB<K, PC>(C, c, h_in, 1); }, &rc, &n_iinit);
+        if (e == cudaSuccess && rc == SSG_OK) e = add_while(body, &n_iinit, h_in, &n_inner, &body_in);
+        if (e == cudaSuccess && rc == SSG_OK)
+            e = capture_into(cap, body_in, nullptr, 0,
+                             [&](cudaStream_t c) { return launch_inner_bodyB<K, PC>(C, c, h_in, 1); }, &rc);
+        if (e == cudaSuccess && rc == SSG_OK)
+            e = capture_into(cap, body, &n_inner, 1, [&](cudaStream_t c) { return launch_outer_tailB<K>(C, c, h_out, 1); },
+                             &rc);
+    }
+    if (rc == SSG_OK && e != cudaSuccess) {
+        set_error(std::string("building a column group's loop: ") + cudaGetErrorString(e));
+        rc = SSG_E_CUDA;
+    }
+    return rc;
+}
+
+int class_branch_k(ssg_system *C, cudaGraph_t G, cudaStream_t cap, int mode) {
+    const bool mixed = mode == SSG_MIXED || mode == SSG_MIXED_JACOBI;
+    const bool pc = mode == SSG_FP64_JACOBI || mode == SSG_MIXED_JACOBI;
+    switch (pow2_columns(C->batch_k)) {
+        case 2: return pc ? class_branch<2, true>(C, G, cap, mixed) : class_branch<2, false>(C, G, cap, mixed);
+        case 4: return pc ? class_branch<4, true>(C, G, cap, mixed) : class_branch<4, false>(C, G, cap, mixed);
+        case 8: return pc ? class_branch<8, true>(C, G, cap, mixed) : class_branch<8, false>(C, G, cap, mixed);
+        default: return pc ? class_branch<16, true>(C, G, cap, mixed) : class_branch<16, false>(C, G, cap, mixed);
+    }
+}
+
+int block_pre_k(ssg_system *C, const double *b, double *x, int guess, double rtol, int32_t max_iter, int mode,
+                cudaStream_t s, int64_t *launches) {
+    switch (pow2_columns(C->batch_k)) {
+        case 2: return block_pre<2>(C, 0, b, x, guess, rtol, max_iter, mode, s, launches);
+        case 4: return block_pre<4>(C, 0, b, x, guess, rtol, max_iter, mode, s, launches);
+        case 8: return block_pre<8>(C, 0, b, x, guess, rtol, max_iter, mode, s, launches);
+        default: return block_pre<16>(C, 0, b, x, guess, rtol, max_iter, mode, s, launches);
+    }
+}
+
+int block_post_k(ssg_system *C, double *x, int mode, cudaStream_t s, int64_t launches) {
+    switch (pow2_columns(C->batch_k)) {
+        case 2: return block_post<2>(C, 0, x, mode, s, launches);
+        case 4: return block_post<4>(C, 0, x, mode, s, launches);
+        case 8: return block_post<8>(C, 0, x, mode, s, launches);
+        default: return block_post<16>(C, 0, x, mode, s, launches);
+    }
+}
+
+// The graph of all column groups' loops for one mode (built at its first use,
+// after the groups' vectors exist).
+int classes_graph(ssg_system *S, int mode) {
+    ssg_system::BlockGraph &G = S->classes_graph[mode];
+    if (G.exec) return SSG_OK;
+    SSG_CUDA_TRY(cudaGraphCreate(&G.g, 0));
+    cudaStream_t cap;
+    SSG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int rc = SSG_OK;
+    for (size_t c = 0; c < S->kclass.size() && rc == SSG_OK; ++c) rc = class_branch_k(S->kclass[c], G.g, cap, mode);
+    cudaStreamDestroy(cap);
+    if (rc == SSG_OK) {
+        cudaError_t e = cudaGraphInstantiate(&G.exec, G.g, 0);
+        if (e != cudaSuccess) {
+            set_error(std::string("instantiating the column groups' graph: ") + cudaGetErrorString(e));
+            rc = SSG_E_CUDA;
+        }
+    }
+    if (rc != SSG_OK) {
+        if (G.g) cudaGraphDestroy(G.g);
+        G = ssg_system::BlockGraph{};
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
 int ssg_solve_batch(ssg_system *S, const double *b, double *x, int32_t x_is_guess, double rtol, int32_t max_iter,
                     int32_t mode, ssg_stats *stats) {
     int rc = check_dev(S);
@@ -1839,12 +1989,66 @@ int ssg_solve_batch(ssg_system *S, const double *b, double *x, int32_t x_is_gues
     SSG_CUDA_TRY(cudaSetDevice(S->ctx->device));
     if (S->kclass.empty()) {
         rc = solve_batch_k(S, b, x, x_is_guess, rtol, max_iter, mode, stats);
-    } else {
-        // one solve per K class, each on the caller's b and x at the original
-        // offsets and on its own stream: they start after the work already
-        // on the context's stream, run side by side, and the context's stream
-        // waits for all of them; statistics come back in (system, right-hand
+    } else if (S->ctx->driver == SSG_DRIVER_GRAPH) {
+        // every column group's loop is a branch of one graph, launched once
+        // on the context's stream; each group's setup before it and its end
+        // after it on the same stream; statistics in (system, right-hand
         // side) order
+        std::vector<int64_t> first(static_cast<size_t>(S->nseg) + 1, 0);
+        for (int32_t sg = 0; sg < S->nseg; ++sg) first[sg + 1] = first[sg] + S->seg_nrhs[sg];
+        cudaStream_t ps = S->ctx->stream;
+        std::vector<int64_t> launches(S->kclass.size(), 0);
+        for (size_t c = 0; c < S->kclass.size(); ++c) {
+            ssg_system *C = S->kclass[c];
+            C->ctx->driver = S->ctx->driver;
+            C->ctx->inner_rtol = S->ctx->inner_rtol;
+            C->ctx->max_outer = S->ctx->max_outer;
+            // the group's vectors are allocated (and zeroed on its own
+            // stream) before any of its work goes to the context's stream
+            rc = ensure_block(C, pow2_columns(C->batch_k));
+            if (rc != SSG_OK) return rc;
+            SSG_CUDA_TRY(cudaStreamSynchronize(C->ctx->stream));
+            rc = block_pre_k(C, b, x, x_is_guess, rtol, max_iter, mode, ps, &launches[c]);
+            if (rc != SSG_OK) return rc;
+        }
+        rc = classes_graph(S, mode);
+        if (rc != SSG_OK) return rc;
+        SSG_CUDA_TRY(cudaGraphLaunch(S->classes_graph[mode].exec, ps));
+        for (size_t c = 0; c < S->kclass.size(); ++c) {
+            rc = block_post_k(S->kclass[c], x, mode, ps, launches[c]);
+            if (rc != SSG_OK) return rc;
+        }
+        SSG_CUDA_TRY(cudaStreamSynchronize(ps));
+        rc = SSG_OK;
+        int64_t all_launches = 0;
+        double ms = 0.0;
+        for (size_t c = 0; c < S->kclass.size(); ++c) {
+            ssg_system *C = S->kclass[c];
+            int64_t nst = 0;
+            for (int32_t sg : S->kclass_sys[c]) nst += S->seg_nrhs[sg];
+            std::vector<ssg_stats> st(static_cast<size_t>(nst));
+            const int rc_c = solve_block_finish(C, st.data());
+            if (rc_c == SSG_E_CUDA || rc_c == SSG_E_OOM || rc_c == SSG_E_INVALID) return rc_c;
+            if (rc_c != SSG_OK && rc == SSG_OK) rc = rc_c;
+            if (!st.empty()) {
+                all_launches += st[0].kernel_launches;
+                ms = std::max(ms, st[0].solve_ms);
+            }
+            if (stats) {
+                size_t o = 0;
+                for (int32_t sg : S->kclass_sys[c])
+                    for (int32_t j = 0; j < S->seg_nrhs[sg]; ++j) stats[first[sg] + j] = st[o++];
+            }
+        }
+        if (stats)
+            for (int64_t t = 0; t < first[S->nseg]; ++t) {
+                stats[t].kernel_launches = all_launches;
+                stats[t].solve_ms = ms;
+            }
+    } else {
+        // host-loop driver: one solve per column group, each on its own
+        // stream (its loop polls on the host), side by side after the work
+        // already on the context's stream, which then waits for all of them
         std::vector<int64_t> first(static_cast<size_t>(S->nseg) + 1, 0);
         for (int32_t sg = 0; sg < S->nseg; ++sg) first[sg + 1] = first[sg] + S->seg_nrhs[sg];
         cudaStream_t ps = S->ctx->stream;
@@ -2277,6 +2481,10 @@ int ssg_solve_host(ssg_system *S, int32_t k, const double *b_host, double *x_hos
 
 int ssg_system_destroy(ssg_system *S) {
     if (!S) return SSG_OK;
+    for (ssg_system::BlockGraph &G : S->classes_graph) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        if (G.g) cudaGraphDestroy(G.g);
+    }
     for (ssg_system *C : S->kclass) ssg_system_destroy(C);  // each frees its own context
     S->kclass.clear();
     if (S->ctx) cudaSetDevice(S->ctx->device);
