@@ -114,6 +114,7 @@ struct ssg_system {
         BlockGraph graph[4][5];  // by mode (SSG_FP64 .. SSG_MIXED_JACOBI) and log2 K
     } blk;
     BlockGraph classes_graph[4];  // per mode: every K class's loop as a parallel branch of one graph
+    bool classes_graph_refused[4] = {false, false, false, false};  // building it failed: streams instead
 };
 
 namespace {
@@ -1966,6 +1967,26 @@ int classes_graph(ssg_system *S, int mode) {
     return rc;
 }
 
+// Settings copied to the groups' contexts, their vectors allocated (and
+// zeroed on their own streams, waited for), and the one-graph form built for
+// this mode.  A failure to build the graph marks the mode: its solves then
+// run the groups on their own streams.
+int batch_classes_ready(ssg_system *S, int mode) {
+    for (ssg_system *C : S->kclass) {
+        C->ctx->driver = S->ctx->driver;
+        C->ctx->inner_rtol = S->ctx->inner_rtol;
+        C->ctx->max_outer = S->ctx->max_outer;
+        int rc = ensure_block(C, pow2_columns(C->batch_k));
+        if (rc != SSG_OK) return rc;
+        SSG_CUDA_TRY(cudaStreamSynchronize(C->ctx->stream));
+    }
+    if (classes_graph(S, mode) != SSG_OK) {
+        S->classes_graph_refused[mode] = true;
+        return SSG_E_CUDA;
+    }
+    return SSG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1989,7 +2010,8 @@ int ssg_solve_batch(ssg_system *S, const double *b, double *x, int32_t x_is_gues
     SSG_CUDA_TRY(cudaSetDevice(S->ctx->device));
     if (S->kclass.empty()) {
         rc = solve_batch_k(S, b, x, x_is_guess, rtol, max_iter, mode, stats);
-    } else if (S->ctx->driver == SSG_DRIVER_GRAPH) {
+    } else if (S->ctx->driver == SSG_DRIVER_GRAPH && !S->classes_graph_refused[mode] &&
+               batch_classes_ready(S, mode) == SSG_OK) {
         // every column group's loop is a branch of one graph, launched once
         // on the context's stream; each group's setup before it and its end
         // after it on the same stream; statistics in (system, right-hand
@@ -1999,20 +2021,9 @@ int ssg_solve_batch(ssg_system *S, const double *b, double *x, int32_t x_is_gues
         cudaStream_t ps = S->ctx->stream;
         std::vector<int64_t> launches(S->kclass.size(), 0);
         for (size_t c = 0; c < S->kclass.size(); ++c) {
-            ssg_system *C = S->kclass[c];
-            C->ctx->driver = S->ctx->driver;
-            C->ctx->inner_rtol = S->ctx->inner_rtol;
-            C->ctx->max_outer = S->ctx->max_outer;
-            // the group's vectors are allocated (and zeroed on its own
-            // stream) before any of its work goes to the context's stream
-            rc = ensure_block(C, pow2_columns(C->batch_k));
-            if (rc != SSG_OK) return rc;
-            SSG_CUDA_TRY(cudaStreamSynchronize(C->ctx->stream));
-            rc = block_pre_k(C, b, x, x_is_guess, rtol, max_iter, mode, ps, &launches[c]);
+            rc = block_pre_k(S->kclass[c], b, x, x_is_guess, rtol, max_iter, mode, ps, &launches[c]);
             if (rc != SSG_OK) return rc;
         }
-        rc = classes_graph(S, mode);
-        if (rc != SSG_OK) return rc;
         SSG_CUDA_TRY(cudaGraphLaunch(S->classes_graph[mode].exec, ps));
         for (size_t c = 0; c < S->kclass.size(); ++c) {
             rc = block_post_k(S->kclass[c], x, mode, ps, launches[c]);
@@ -2046,9 +2057,10 @@ int ssg_solve_batch(ssg_system *S, const double *b, double *x, int32_t x_is_gues
                 stats[t].solve_ms = ms;
             }
     } else {
-        // host-loop driver: one solve per column group, each on its own
-        // stream (its loop polls on the host), side by side after the work
-        // already on the context's stream, which then waits for all of them
+        // host-loop driver (or a graph driver whose one-graph form could not
+        // be built): one solve per column group, each on its own stream, side
+        // by side after the work already on the context's stream, which then
+        // waits for all of them
         std::vector<int64_t> first(static_cast<size_t>(S->nseg) + 1, 0);
         for (int32_t sg = 0; sg < S->nseg; ++sg) first[sg + 1] = first[sg] + S->seg_nrhs[sg];
         cudaStream_t ps = S->ctx->stream;
