@@ -60,6 +60,8 @@ def parse_args(argv=None):
                          "Both stop on an FP64 relative residual of 1e-8; the other mode is timed too and reported")
     ap.add_argument("--pdl", choices=("on", "off"), default="off",
                     help="programmatic dependent launch for the per-iteration update kernels")
+    ap.add_argument("--fuse", choices=("on", "off"), default="off",
+                    help="FP32 inner residual and direction updates as one cooperative kernel (grid barrier)")
     ap.add_argument("--profile-spmm", choices=("fp64", "fp32"), default=None,
                     help="only build the 96^3 16-right-hand-side workload and launch the 16-vector product "
                          "--spmv-reps times (for ncu); no JSON line")
@@ -699,6 +701,7 @@ def run_ours(args, dist):
     if args.driver == "host":
         ctx.set_driver(ssg.SSG_DRIVER_HOST)
     ctx.set_pdl(args.pdl == "on")
+    ctx.set_fused(args.fuse == "on")
     S = System(ctx, prob.A, prob.part, prob.P)
     b = torch.from_numpy(prob.b[:, 0].copy()).to("cuda:%d" % dev)
     x = torch.zeros_like(b)
@@ -847,6 +850,7 @@ def run_ours(args, dist):
             "parallelism": "replicas" if dist.world > 1 else "single",
             "driver": args.driver,
             "pdl": args.pdl,
+            "fuse": args.fuse,
         },
         "roofline": roof[dominant],
         "roofline_other": roof["fp64" if dominant == "fp32" else "fp32"],

@@ -101,6 +101,25 @@ int ssg_set_driver(ssg_ctx *ctx, int driver);
  * GB300: no gain in SSG_MIXED, 13 us per iteration lost in SSG_FP64).
  * Applies to systems partitioned on this context afterwards. */
 int ssg_set_pdl(ssg_ctx *ctx, int enable);
+/* Run the FP32 residual update and the direction update of each inner
+ * iteration of SSG_MIXED / SSG_MIXED_JACOBI (Algorithm 3 lines 3-8 inside
+ * iterative refinement) as one cooperative kernel with a grid barrier
+ * between them, instead of two kernels.  Same operations in the same order:
+ * results are bit-identical either way.  enable != 0: on; default off
+ * (measured on GB300, 128^3 system: 44.5 us per inner iteration fused against
+ * 41.2 us with two kernels; the barrier costs more than the kernel boundary
+ * it replaces).
+ * Applies to systems partitioned on this context afterwards; a device or
+ * driver that cannot co-schedule the grid, or capture a cooperative kernel
+ * inside the loop graph, gets the two kernels.  A grid barrier that does not
+ * complete within about a second ends the solve with SSG_E_TIMEOUT. */
+int ssg_set_fused(ssg_ctx *ctx, int enable);
+/* Runs the fused update's grid barrier once in a two-block cooperative
+ * launch in which one block never arrives: the other's wait gives up after
+ * about a second and the call returns SSG_E_TIMEOUT (SSG_OK would mean the
+ * barrier completed, i.e. the failure path did not work).  The context stays
+ * usable.  A test of failure detection without a GPU fault. */
+int ssg_check_barrier_timeout(ssg_ctx *ctx);
 /*
  * Parameters of SSG_MIXED solves on this context (not a method of the paper;
  * its experiments are FP64 only): the inner FP32 CG stops when its residual

@@ -55,6 +55,8 @@ struct ssg_system {
     Scal *d_scal_op = nullptr;  // state for the stand-alone SpMV / dot calls
     double *d_xg = nullptr, *d_bg = nullptr;  // global staging for ssg_solve_host
     bool pdl = false;  // loop-body kernels use programmatic dependent launch
+    bool fuse = false;  // FP32 inner updates as one cooperative launch (k_update_rdp32)
+    unsigned long long *d_gbar = nullptr;  // its grid barrier's arrival counter, zeroed before each solve
     int grid_spmv = 0;
     int grid_spmv32 = 0;
     int grid_bps[6] = {0, 0, 0, 0, 0, 0};           // single-vector grids for 3, 4, 5 blocks per SM
@@ -135,6 +137,23 @@ cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), int grid, int block, cuda
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = pdl ? attr : nullptr;
     cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Cooperative launch: every block of the grid is resident at once (the
+// kernel holds a grid barrier).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_coop(void (*kern)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
@@ -420,6 +439,7 @@ int launch_init(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
 }
 
 int launch_mixed_init(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
+    SSG_CUDA_TRY(cudaMemsetAsync(S->d_gbar, 0, sizeof(unsigned long long) * kGridBarWords, st));
     k_cg_init<false><<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_bl, S->d_q, S->d_r, nullptr, S->op.mult,
                                                      S->op.wtab, S->d_partials, S->d_scal, S->cond_out[pc], use_cond,
                                                      nullptr);
@@ -441,6 +461,14 @@ int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const cudaGraphConditionalHandle h = S->cond_in[pc];
     SSG_CUDA_TRY(launch_k(false, kSpmv32Variants[S->var32].part, S->grid_spmv32, kSpmvThreads, st, S->op32,
                           S->d_p32, S->d_q32, part_pq(S), S->d_scal_in, (double *)nullptr, h, use_cond));
+    if (S->fuse) {
+        SSG_CUDA_TRY(launch_coop(pc ? k_update_rdp32<true> : k_update_rdp32<false>, S->grid_vec, kBlock, st, N,
+                                 S->d_r32, (const float *)S->d_q32, S->d_d32, S->d_p32, S->op.mult, S->op.wtab32,
+                                 S->op.gflag128, (const double *)part_pq(S), S->grid_spmv32, part_rr(S),
+                                 S->d_scal_in, S->d_scal, h, use_cond, (const float *)S->d_dinv32, part_rz(S),
+                                 S->d_gbar));
+        return SSG_OK;
+    }
     SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_r32<true> : k_update_r32<false>, S->grid_vec, kBlock, st, N,
                           S->d_r32, S->d_q32, S->op.mult, S->op.wtab32, S->op.gflag128, (const double *)part_pq(S),
                           S->grid_spmv32, part_rr(S), S->d_scal_in, (const Scal *)S->d_scal, h, use_cond,
@@ -557,6 +585,10 @@ int build_graph_mixed_once(ssg_system *S, bool pc);
 int build_graph_mixed(ssg_system *S, bool pc) {
     if (S->exec_m[pc]) return SSG_OK;
     int rc = build_graph_mixed_once(S, pc);
+    if (rc != SSG_OK && S->fuse) {  // no cooperative kernel inside the loop body: two launches
+        S->fuse = false;
+        rc = build_graph_mixed_once(S, pc);
+    }
     if (rc != SSG_OK && S->pdl) {
         S->pdl = false;
         rc = build_graph_mixed_once(S, pc);
@@ -647,6 +679,14 @@ int upload(ssg_system *S) {
     S->grid_spmv32 = plan.grid_bps[kSpmv32Variants[0].bps];
     S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N / 2 + kBlock - 1) / kBlock), C->num_sms * kVecBlocksPerSM));
     S->n_partials = 3 * std::max(std::max(plan.grid_bps[3], std::max(plan.grid_bps[4], plan.grid_bps[5])), S->grid_vec);
+    if (S->fuse) {
+        // the fused FP32 update needs its whole grid resident at once
+        int coop = 0, nb0 = 0, nb1 = 0;
+        SSG_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, C->device));
+        SSG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, k_update_rdp32<false>, kBlock, 0));
+        SSG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_update_rdp32<true>, kBlock, 0));
+        S->fuse = coop != 0 && static_cast<int64_t>(std::min(nb0, nb1)) * C->num_sms >= S->grid_vec;
+    }
 
     struct Piece {
         const void *src;
@@ -755,6 +795,7 @@ int upload(ssg_system *S) {
     size_t i_part = add(nullptr, sizeof(double) * S->n_partials);
     size_t i_scal = add(nullptr, sizeof(Scal));
     size_t i_scal2 = add(nullptr, sizeof(Scal));
+    size_t i_gbar = add(nullptr, sizeof(unsigned long long) * kGridBarWords);
     size_t i_xg = add(nullptr, sizeof(double) * M.n);
     size_t i_bg = add(nullptr, sizeof(double) * M.n);
 
@@ -779,6 +820,7 @@ int upload(ssg_system *S) {
     S->d_q32 = static_cast<float *>(at(i_q32));
     S->d_d32 = static_cast<float *>(at(i_d32));
     S->d_scal_in = static_cast<Scal *>(at(i_scal_in));
+    S->d_gbar = static_cast<unsigned long long *>(at(i_gbar));
     S->d_dmap = static_cast<int32_t *>(at(i_dmap));
     S->d_dinv = static_cast<double *>(at(i_dinv));
     S->d_dinv32 = static_cast<float *>(at(i_dinv32));
@@ -908,7 +950,7 @@ int run_host_mixed(ssg_system *S, int64_t *launches, bool pc) {
                 rc = launch_inner_body(S, s, 0, pc);
                 if (rc != SSG_OK) return rc;
             }
-            *launches += 3 * kHostChunk;
+            *launches += (S->fuse ? 2 : 3) * kHostChunk;
         }
         rc = launch_outer_tail(S, s, 0, pc);
         if (rc != SSG_OK) return rc;
@@ -987,8 +1029,8 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     float ms = 0.f;
     SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
     if (C->driver == SSG_DRIVER_GRAPH) {
-        if (mixed)  // init, per refinement: inner init + 3 tail kernels, 3 per inner iteration
-            launches += 1 + 4 * static_cast<int64_t>(h.iter) + 3 * static_cast<int64_t>(h.total);
+        if (mixed)  // init, per refinement: inner init + 3 tail kernels, 3 (fused: 2) per inner iteration
+            launches += 1 + 4 * static_cast<int64_t>(h.iter) + (S->fuse ? 2 : 3) * static_cast<int64_t>(h.total);
         else  // init, 3 per iteration (a breakdown ends after the SpMV and residual kernels of one more)
             launches += 1 + 3 * static_cast<int64_t>(h.iter) + (h.status == SSG_E_BREAKDOWN ? 3 : 0);
     }
@@ -1588,6 +1630,40 @@ int ssg_set_pdl(ssg_ctx *ctx, int enable) {
     return SSG_OK;
 }
 
+int ssg_set_fused(ssg_ctx *ctx, int enable) {
+    if (!ctx) {
+        set_error("null context");
+        return SSG_E_INVALID;
+    }
+    ctx->fuse = enable ? 1 : 0;
+    return SSG_OK;
+}
+
+int ssg_check_barrier_timeout(ssg_ctx *ctx) {
+    if (!ctx) {
+        set_error("null context");
+        return SSG_E_INVALID;
+    }
+    SSG_CUDA_TRY(cudaSetDevice(ctx->device));
+    SSG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    unsigned long long *buf = nullptr;  // barrier words, result
+    const size_t words = kGridBarWords + 1;
+    SSG_CUDA_TRY(cudaMalloc(&buf, words * sizeof(unsigned long long)));
+    unsigned long long res = 0;
+    cudaError_t e = cudaMemsetAsync(buf, 0, words * sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = launch_coop(k_grid_barrier_probe, 2, kBlock, ctx->stream, buf, buf + kGridBarWords);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&res, buf + kGridBarWords, sizeof(res), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        set_error(std::string("grid barrier probe: ") + cudaGetErrorString(e));
+        return SSG_E_CUDA;
+    }
+    if (res == 1) return SSG_E_TIMEOUT;
+    set_error("grid barrier probe: the wait did not run out");
+    return SSG_OK;
+}
+
 int ssg_set_mixed(ssg_ctx *ctx, double inner_rtol, int32_t max_outer) {
     if (!ctx || !(inner_rtol > 0.0 && inner_rtol < 1.0) || max_outer < 1) {
         set_error("ssg_set_mixed: need 0 < inner_rtol < 1 and max_outer >= 1");
@@ -1637,6 +1713,7 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
     if (ctx) {
         ctx->live_systems++;
         S->pdl = ctx->pdl != 0;
+        S->fuse = ctx->fuse != 0;
         rc = upload(S);
         if (rc != SSG_OK) {
             ssg_system_destroy(S);
@@ -1667,6 +1744,7 @@ int ssg_partition_fe(ssg_ctx *ctx, int32_t n, int32_t ne, int32_t nv, const int3
     if (ctx) {
         ctx->live_systems++;
         S->pdl = ctx->pdl != 0;
+        S->fuse = ctx->fuse != 0;
         rc = upload(S);
         if (rc != SSG_OK) {
             ssg_system_destroy(S);
@@ -1709,6 +1787,7 @@ int make_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off, const in
     S->ctx = ctx;
     ctx->live_systems++;
     S->pdl = ctx->pdl != 0;
+    S->fuse = ctx->fuse != 0;
     rc = upload(S);
     if (rc != SSG_OK) {
         ssg_system_destroy(S);

@@ -850,21 +850,21 @@ __global__ void __launch_bounds__(kBlock) k_inner_init(int64_t N, const double *
 // r32 <- r32 - alpha q32 and its share of (r32, r32)_w (products and block
 // sums in FP32).  A warp covers the 128 entries of flag group i >> 5 (float4
 // per lane); groups without interface copies skip the weights.
+// The block's part of it; false when the loop has stopped (every block
+// returns at the same point: all read the same state and partials).
 template <bool PC>
-__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
-                                                       const uint8_t *__restrict__ mult,
-                                                       const float *__restrict__ wtab,
-                                                       const uint8_t *__restrict__ gflag128, const double *part_pq,
-                                                       int G1, double *part_rr, Scal *si, const Scal *so,
-                                                       cudaGraphConditionalHandle h, int use_cond,
-                                                       const float *__restrict__ dinv32, double *part_rz) {
-    pdl_enter();
+__device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r, const float *__restrict__ q,
+                                                const uint8_t *__restrict__ mult, const float *__restrict__ wtab,
+                                                const uint8_t *__restrict__ gflag128, const double *part_pq, int G1,
+                                                double *part_rr, Scal *si, const Scal *so,
+                                                cudaGraphConditionalHandle h, int use_cond,
+                                                const float *__restrict__ dinv32, double *part_rz) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         si->rho_b = si->rho;
         si->iter_b = si->iter;
         si->total_b = so->total;
     }
-    if (si->brk || si->halt[si->iter & 1]) return;
+    if (si->brk || si->halt[si->iter & 1]) return false;
     double pq = 0.0, alpha_d = 0.0;
     float alpha = 0.f;
     float acc = 0.f, acz = 0.f;
@@ -934,7 +934,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
                 acz = fmaf(w.w * rv.w, rv.w * l.d.w, acz);
             }
         });
-    if (!go) return;
+    if (!go) return false;
     if (blockIdx.x == 0 && threadIdx.x < (N & 3)) {
         const int64_t i = (N & ~int64_t(3)) + threadIdx.x;
         const float ri = fmaf(-alpha, q[i], r[i]);
@@ -954,6 +954,18 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
             si->pq = pq;
         }
     }
+    return true;
+}
+
+template <bool PC>
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
+                                                       const uint8_t *__restrict__ mult, const float *__restrict__ wtab,
+                                                       const uint8_t *__restrict__ gflag128, const double *part_pq, int G1,
+                                                       double *part_rr, Scal *si, const Scal *so,
+                                                       cudaGraphConditionalHandle h, int use_cond,
+                                                       const float *__restrict__ dinv32, double *part_rz) {
+    pdl_enter();
+    update_r32_step<PC>(N, r, q, mult, wtab, gflag128, part_pq, G1, part_rr, si, so, h, use_cond, dinv32, part_rz);
 }
 
 // Inner Algorithm 3 lines 4, 7, 8 in FP32: every block sums the partials of
@@ -961,19 +973,16 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
 // block 0 records the iteration and the inner stopping decision
 // (sqrt(rho) <= tau sqrt(rho0), or the inner iterations summed over
 // refinements reach max_iter).
+// The block's part of it for iteration k, with alpha (FP32), the summed
+// inner iteration count and rho_k handed in by the caller.
 template <bool PC>
-__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t N, float *__restrict__ d, float *__restrict__ p,
-                                                        const float *__restrict__ r, const double *part_rr, int G2,
-                                                        Scal *si, Scal *so, cudaGraphConditionalHandle h,
-                                                        int use_cond, const float *__restrict__ dinv32,
-                                                        const double *part_rz) {
-    pdl_enter();
-    const int k = si->iter_b;
-    if (si->brk || si->halt[k & 1]) return;
+__device__ __forceinline__ void update_dp32_step(int64_t N, float *__restrict__ d, float *__restrict__ p,
+                                                 const float *__restrict__ r, const double *part_rr, int G2,
+                                                 Scal *si, Scal *so, cudaGraphConditionalHandle h, int use_cond,
+                                                 const float *__restrict__ dinv32, const double *part_rz, int k, float alpha, int total1,
+                                                 double rho_b) {
     double rr = 0.0, rz = 0.0, beta_d = 0.0;
     float beta = 0.f;
-    const float alpha = si->alpha32;
-    const int total1 = si->total_b + 1;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N4 = N >> 2;
     float4 *__restrict__ d4 = reinterpret_cast<float4 *>(d);
@@ -1002,7 +1011,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t
         [&]() {
             rr = all_sum_partials(part_rr, G2);
             rz = PC ? all_sum_partials(part_rz, G2) : rr;
-            beta_d = block_quotient(rz, si->rho_b, &beta);
+            beta_d = block_quotient(rz, rho_b, &beta);
             return true;
         },
         [&](int64_t i, Ld l) {
@@ -1036,6 +1045,129 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t
     }
 }
 
+template <bool PC>
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t N, float *__restrict__ d, float *__restrict__ p,
+                                                        const float *__restrict__ r, const double *part_rr, int G2,
+                                                        Scal *si, Scal *so, cudaGraphConditionalHandle h, int use_cond,
+                                                        const float *__restrict__ dinv32, const double *part_rz) {
+    pdl_enter();
+    const int k = si->iter_b;
+    if (si->brk || si->halt[k & 1]) return;
+    update_dp32_step<PC>(N, d, p, r, part_rr, G2, si, so, h, use_cond, dinv32, part_rz, k, si->alpha32,
+                         si->total_b + 1, si->rho_b);
+}
+
+// Bounds of the grid barrier's wait: about one second of %globaltimer, or
+// this many polls, whichever ends first.
+constexpr uint64_t kGridWaitNs = 1000000000ull;
+constexpr uint32_t kGridWaitPolls = 1u << 26;
+
+__device__ __forceinline__ uint64_t timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *a) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+    return v;
+}
+
+// Barrier over every block of a cooperative launch (all blocks resident at
+// once).  bar[0] counts arrivals (zeroed before a solve, advanced by exactly
+// gridDim.x per barrier); bar[16], a cache line away, holds the number of
+// the last completed round.  Thread 0 of each block publishes the block's
+// earlier writes and arrives; the last arrival of a round publishes the
+// round number, the others poll for it (reads only, off the line the
+// arrivals update).  False when the wait ran out (no block may then rely on
+// the others' writes); every thread of the block gets the same answer.
+constexpr int kGridBarWords = 32;  // two 128-byte lines of 64-bit words
+__device__ __forceinline__ bool grid_barrier(unsigned long long *bar) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long G = gridDim.x;
+        unsigned long long *round_done = bar + 16;
+        __threadfence();
+        const unsigned long long old = atomicAdd(bar, 1ull);
+        const unsigned long long round = old / G + 1;
+        int good = 0;
+        if (old % G == G - 1) {
+            __threadfence();
+            atomicMax(round_done, round);
+            good = 1;
+        } else {
+            const uint64_t t0 = timer_ns();
+            for (uint32_t it = 0; it < kGridWaitPolls; ++it) {
+                if (ld_acquire(round_done) >= round) {
+                    good = 1;
+                    break;
+                }
+                if ((it & 63u) == 63u && timer_ns() - t0 > kGridWaitNs) break;
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Failure-path probe of grid_barrier: block 1 returns without arriving, so
+// block 0's wait runs out after about a second; *result = 1 then (2 if the
+// barrier had completed).
+__global__ void k_grid_barrier_probe(unsigned long long *count, unsigned long long *result) {
+    if (blockIdx.x != 0) return;
+    const bool ok = grid_barrier(count);
+    if (threadIdx.x == 0) *result = ok ? 2ull : 1ull;
+}
+
+// Inner Algorithm 3 lines 3-8 in FP32 as one cooperative launch: the residual
+// update of k_update_r32, a grid barrier (where block partials of
+// (r32, r32)_w and block 0's alpha become visible to all blocks), then the
+// direction update of k_update_dp32.  Each block's threads own the same
+// entries in both halves, so the direction half re-reads r32 that the same
+// thread just wrote; its first items of p32 and d32 (and of the diagonal) are
+// prefetched into L2 while the barrier waits.  Same arithmetic, same order
+// and the same bits as the two kernels.  A barrier that runs out records
+// SSG_E_TIMEOUT and stops the loop.
+template <bool PC>
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_rdp32(
+    int64_t N, float *__restrict__ r, const float *__restrict__ q, float *__restrict__ d,
+    float *__restrict__ p, const uint8_t *__restrict__ mult, const float *__restrict__ wtab,
+    const uint8_t *__restrict__ gflag128, const double *part_pq, int G1, double *part_rr, Scal *si, Scal *so,
+    cudaGraphConditionalHandle h, int use_cond, const float *__restrict__ dinv32, double *part_rz,
+    unsigned long long *bar) {
+    if (!update_r32_step<PC>(N, r, q, mult, wtab, gflag128, part_pq, G1, part_rr, si, so, h, use_cond, dinv32,
+                             part_rz))
+        return;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    const int64_t N4 = N >> 2;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x + u * stride;
+        if (i < N4) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 4 * i));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(d + 4 * i));
+            if (PC) asm volatile("prefetch.global.L2 [%0];" ::"l"(dinv32 + 4 * i));
+        }
+    }
+    if (!grid_barrier(bar)) {
+        if (threadIdx.x == 0) {
+            si->status = SSG_E_TIMEOUT;
+            si->brk = 1;
+            stop_loop(si, h, use_cond);
+        }
+        return;
+    }
+    // written by block 0 before the barrier: read from L2, not a stale L1 line
+    update_dp32_step<PC>(N, d, p, r, part_rr, gridDim.x, si, so, h, use_cond, dinv32, part_rz,
+                         __ldcg(&si->iter_b), __ldcg(&si->alpha32), __ldcg(&si->total_b) + 1,
+                         __ldcg(&si->rho_b));
+}
+
 // x64 <- x64 + (double) d32 (the refinement update).
 __global__ void __launch_bounds__(kBlock) k_ir_correct(int64_t N, double *__restrict__ x, const float *__restrict__ d) {
     const int64_t stride = (int64_t)gridDim.x * kBlock;
@@ -1065,7 +1197,9 @@ __global__ void __launch_bounds__(kBlock) k_ir_residual(int64_t N, const double 
             so->iter += 1;
             so->relres = so->bnorm > 0.0 ? sqrt(tot) / so->bnorm : 0.0;
             int stop = 1;
-            if (sqrt(tot) <= so->rtol * so->bnorm) {
+            if (si->status == SSG_E_TIMEOUT) {
+                so->status = SSG_E_TIMEOUT;  // the inner iterate is not to be trusted
+            } else if (sqrt(tot) <= so->rtol * so->bnorm) {
                 so->status = SSG_OK;
             } else if (si->status == SSG_E_BREAKDOWN) {
                 so->status = SSG_E_BREAKDOWN;

@@ -44,6 +44,8 @@ EXPORTS = (
     "ssg_set_mixed",
     "ssg_set_rhs_block",
     "ssg_set_pdl",
+    "ssg_set_fused",
+    "ssg_check_barrier_timeout",
     "ssg_destroy",
     "ssg_partition",
     "ssg_partition_fe",
@@ -173,6 +175,8 @@ def lib():
         L.ssg_set_mixed.argtypes = [vp, C.c_double, C.c_int32]
         L.ssg_set_rhs_block.argtypes = [vp, C.c_int32]
         L.ssg_set_pdl.argtypes = [vp, C.c_int]
+        L.ssg_set_fused.argtypes = [vp, C.c_int]
+        L.ssg_check_barrier_timeout.argtypes = [vp]
         L.ssg_destroy.argtypes = [vp]
         L.ssg_partition.argtypes = [vp, i32, vp, vp, vp, vp, i32, C.POINTER(vp)]
         L.ssg_partition_batch.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]
@@ -268,6 +272,15 @@ def ssg_set_rhs_block(ctx, kmax: int):
 
 def ssg_set_pdl(ctx, enable: bool):
     return _check(lib().ssg_set_pdl(ctx, int(bool(enable))), "ssg_set_pdl")
+
+
+def ssg_set_fused(ctx, enable: bool):
+    return _check(lib().ssg_set_fused(ctx, int(bool(enable))), "ssg_set_fused")
+
+
+def ssg_check_barrier_timeout(ctx) -> int:
+    """Raw status of the grid-barrier timeout probe (SSG_E_TIMEOUT expected)."""
+    return lib().ssg_check_barrier_timeout(ctx)
 
 
 def ssg_destroy(ctx):
@@ -545,6 +558,9 @@ class Context:
 
     def set_pdl(self, enable: bool):
         ssg_set_pdl(self.h, enable)
+
+    def set_fused(self, enable: bool):
+        ssg_set_fused(self.h, enable)
 
     def set_mixed(self, inner_rtol: float = 1e-4, max_outer: int = 30):
         ssg_set_mixed(self.h, inner_rtol, max_outer)
