@@ -101,19 +101,31 @@ int ssg_set_driver(ssg_ctx *ctx, int driver);
  * GB300: no gain in SSG_MIXED, 13 us per iteration lost in SSG_FP64).
  * Applies to systems partitioned on this context afterwards. */
 int ssg_set_pdl(ssg_ctx *ctx, int enable);
-/* Run the FP32 residual update and the direction update of each inner
- * iteration of SSG_MIXED / SSG_MIXED_JACOBI (Algorithm 3 lines 3-8 inside
- * iterative refinement) as one cooperative kernel with a grid barrier
- * between them, instead of two kernels.  Same operations in the same order:
- * results are bit-identical either way.  enable != 0: on; default off
- * (measured on GB300, 128^3 system: 44.5 us per inner iteration fused against
- * 41.2 us with two kernels; the barrier costs more than the kernel boundary
- * it replaces).
- * Applies to systems partitioned on this context afterwards; a device or
- * driver that cannot co-schedule the grid, or capture a cooperative kernel
- * inside the loop graph, gets the two kernels.  A grid barrier that does not
- * complete within about a second ends the solve with SSG_E_TIMEOUT. */
-int ssg_set_fused(ssg_ctx *ctx, int enable);
+/* How the FP32 inner iteration of SSG_MIXED / SSG_MIXED_JACOBI (Algorithm 3
+ * inside iterative refinement) is split into kernels.  Every form runs the
+ * same operations in the same order on the same work partition: results are
+ * bit-identical whichever is chosen.
+ *   SSG_FUSE_NONE  three kernels: product (line 2, with (p, S p)_w), residual
+ *                  update (lines 3, 5), direction update (lines 4, 7, 8).
+ *   SSG_FUSE_GRID  product, then the two updates as one cooperative kernel
+ *                  with a grid barrier between them.  Measured on GB300 (128^3
+ *                  system): 44.5 us per inner iteration against 41.2 us for
+ *                  three kernels.  A device or driver that cannot co-schedule
+ *                  the grid or capture a cooperative kernel inside the loop
+ *                  graph gets three kernels; a barrier that does not complete
+ *                  within about a second ends the solve with SSG_E_TIMEOUT.
+ *   SSG_FUSE_SPMV  the direction update of iteration k-1 folded into the
+ *                  product of iteration k (it forms p_k where it gathers, from
+ *                  p_{k-1} and z_k, and stores p_k and d at the rows it owns;
+ *                  p alternates between two buffers), then the residual
+ *                  update: two kernels per inner iteration and one more
+ *                  product launch per refinement, which only completes d.
+ * Default SSG_FUSE_NONE.  Applies to systems partitioned on this context
+ * afterwards. */
+#define SSG_FUSE_NONE 0
+#define SSG_FUSE_GRID 1
+#define SSG_FUSE_SPMV 2
+int ssg_set_fused(ssg_ctx *ctx, int mode);
 /* Runs the fused update's grid barrier once in a two-block cooperative
  * launch in which one block never arrives: the other's wait gives up after
  * about a second and the call returns SSG_E_TIMEOUT (SSG_OK would mean the

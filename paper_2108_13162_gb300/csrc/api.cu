@@ -56,6 +56,8 @@ struct ssg_system {
     double *d_xg = nullptr, *d_bg = nullptr;  // global staging for ssg_solve_host
     bool pdl = false;  // loop-body kernels use programmatic dependent launch
     bool fuse = false;  // FP32 inner updates as one cooperative launch (k_update_rdp32)
+    bool fdir = false;  // FP32 direction update folded into the next product (k_spmv_fd)
+    float *d_p32b = nullptr;  // the second direction buffer of the folded form
     unsigned long long *d_gbar = nullptr;  // its grid barrier's arrival counter, zeroed before each solve
     int grid_spmv = 0;
     int grid_spmv32 = 0;
@@ -459,6 +461,19 @@ int launch_inner_init(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
 int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const int64_t N = S->maps.nloc;
     const cudaGraphConditionalHandle h = S->cond_in[pc];
+    if (S->fdir) {
+        const bool b5 = kSpmv32Variants[S->var32].bps == 5;
+        auto fd = pc ? (b5 ? k_spmv_fd<true, 5> : k_spmv_fd<true, 4>) : (b5 ? k_spmv_fd<false, 5> : k_spmv_fd<false, 4>);
+        fd<<<S->grid_spmv32, kSpmvThreads, 0, st>>>(S->op32, N, S->d_r32, S->d_dinv32, S->d_p32, S->d_p32b, S->d_d32,
+                                                    S->d_q32, part_pq(S), part_rr(S), part_rz(S), S->grid_vec,
+                                                    S->d_scal_in, S->d_scal, h, use_cond);
+        SSG_CUDA_TRY(cudaGetLastError());
+        SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_r32<true, true> : k_update_r32<false, true>, S->grid_vec, kBlock,
+                              st, N, S->d_r32, S->d_q32, S->op.mult, S->op.wtab32, S->op.gflag128,
+                              (const double *)part_pq(S), S->grid_spmv32, part_rr(S), S->d_scal_in,
+                              (const Scal *)S->d_scal, h, use_cond, (const float *)S->d_dinv32, part_rz(S)));
+        return SSG_OK;
+    }
     SSG_CUDA_TRY(launch_k(false, kSpmv32Variants[S->var32].part, S->grid_spmv32, kSpmvThreads, st, S->op32,
                           S->d_p32, S->d_q32, part_pq(S), S->d_scal_in, (double *)nullptr, h, use_cond));
     if (S->fuse) {
@@ -745,6 +760,7 @@ int upload(ssg_system *S) {
     size_t i_ival32 = add(ival32.data(), sizeof(float) * ival32.size());
     size_t i_r32 = add(nullptr, sizeof(float) * N);
     size_t i_p32 = add(nullptr, sizeof(float) * N);
+    size_t i_p32b = add(nullptr, sizeof(float) * N);
     size_t i_q32 = add(nullptr, sizeof(float) * N);
     size_t i_d32 = add(nullptr, sizeof(float) * N);
     size_t i_scal_in = add(nullptr, sizeof(Scal));
@@ -817,6 +833,7 @@ int upload(ssg_system *S) {
     S->op.ival32 = static_cast<const float *>(at(i_ival32));
     S->d_r32 = static_cast<float *>(at(i_r32));
     S->d_p32 = static_cast<float *>(at(i_p32));
+    S->d_p32b = static_cast<float *>(at(i_p32b));
     S->d_q32 = static_cast<float *>(at(i_q32));
     S->d_d32 = static_cast<float *>(at(i_d32));
     S->d_scal_in = static_cast<Scal *>(at(i_scal_in));
@@ -950,7 +967,7 @@ int run_host_mixed(ssg_system *S, int64_t *launches, bool pc) {
                 rc = launch_inner_body(S, s, 0, pc);
                 if (rc != SSG_OK) return rc;
             }
-            *launches += (S->fuse ? 2 : 3) * kHostChunk;
+            *launches += (S->fuse || S->fdir ? 2 : 3) * kHostChunk;
         }
         rc = launch_outer_tail(S, s, 0, pc);
         if (rc != SSG_OK) return rc;
@@ -1029,8 +1046,11 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     float ms = 0.f;
     SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
     if (C->driver == SSG_DRIVER_GRAPH) {
-        if (mixed)  // init, per refinement: inner init + 3 tail kernels, 3 (fused: 2) per inner iteration
-            launches += 1 + 4 * static_cast<int64_t>(h.iter) + (S->fuse ? 2 : 3) * static_cast<int64_t>(h.total);
+        if (mixed)  // init, per refinement: inner init + 3 tail kernels, 3 per inner iteration (fused: 2;
+                    // folded: 2 per inner iteration and per refinement, whose last product only ends d)
+            launches += 1 + 4 * static_cast<int64_t>(h.iter) +
+                        (S->fdir ? 2 * (static_cast<int64_t>(h.total) + h.iter)
+                                 : (S->fuse ? 2 : 3) * static_cast<int64_t>(h.total));
         else  // init, 3 per iteration (a breakdown ends after the SpMV and residual kernels of one more)
             launches += 1 + 3 * static_cast<int64_t>(h.iter) + (h.status == SSG_E_BREAKDOWN ? 3 : 0);
     }
@@ -1630,12 +1650,12 @@ int ssg_set_pdl(ssg_ctx *ctx, int enable) {
     return SSG_OK;
 }
 
-int ssg_set_fused(ssg_ctx *ctx, int enable) {
-    if (!ctx) {
-        set_error("null context");
+int ssg_set_fused(ssg_ctx *ctx, int mode) {
+    if (!ctx || (mode != SSG_FUSE_NONE && mode != SSG_FUSE_GRID && mode != SSG_FUSE_SPMV)) {
+        set_error("ssg_set_fused: null context, or mode not SSG_FUSE_NONE / SSG_FUSE_GRID / SSG_FUSE_SPMV");
         return SSG_E_INVALID;
     }
-    ctx->fuse = enable ? 1 : 0;
+    ctx->fuse = mode;
     return SSG_OK;
 }
 
@@ -1713,7 +1733,8 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
     if (ctx) {
         ctx->live_systems++;
         S->pdl = ctx->pdl != 0;
-        S->fuse = ctx->fuse != 0;
+        S->fuse = ctx->fuse == SSG_FUSE_GRID;
+        S->fdir = ctx->fuse == SSG_FUSE_SPMV;
         rc = upload(S);
         if (rc != SSG_OK) {
             ssg_system_destroy(S);
@@ -1744,7 +1765,8 @@ int ssg_partition_fe(ssg_ctx *ctx, int32_t n, int32_t ne, int32_t nv, const int3
     if (ctx) {
         ctx->live_systems++;
         S->pdl = ctx->pdl != 0;
-        S->fuse = ctx->fuse != 0;
+        S->fuse = ctx->fuse == SSG_FUSE_GRID;
+        S->fdir = ctx->fuse == SSG_FUSE_SPMV;
         rc = upload(S);
         if (rc != SSG_OK) {
             ssg_system_destroy(S);
@@ -1787,7 +1809,8 @@ int make_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off, const in
     S->ctx = ctx;
     ctx->live_systems++;
     S->pdl = ctx->pdl != 0;
-    S->fuse = ctx->fuse != 0;
+    S->fuse = ctx->fuse == SSG_FUSE_GRID;
+    S->fdir = ctx->fuse == SSG_FUSE_SPMV;
     rc = upload(S);
     if (rc != SSG_OK) {
         ssg_system_destroy(S);

@@ -851,8 +851,12 @@ __global__ void __launch_bounds__(kBlock) k_inner_init(int64_t N, const double *
 // sums in FP32).  A warp covers the 128 entries of flag group i >> 5 (float4
 // per lane); groups without interface copies skip the weights.
 // The block's part of it; false when the loop has stopped (every block
-// returns at the same point: all read the same state and partials).
-template <bool PC>
+// returns at the same point: all read the same state and partials).  FD:
+// the direction update runs inside the next product (k_spmv_fd), which
+// hands the iteration number over in iter_b; this kernel then advances iter
+// and relays a stop that the product raised (halt[(k + 1) & 1]) to
+// halt[k & 1], the flag every later kernel of the loop reads.
+template <bool PC, bool FD = false>
 __device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r, const float *__restrict__ q,
                                                 const uint8_t *__restrict__ mult, const float *__restrict__ wtab,
                                                 const uint8_t *__restrict__ gflag128, const double *part_pq, int G1,
@@ -861,10 +865,19 @@ __device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r
                                                 const float *__restrict__ dinv32, double *part_rz) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         si->rho_b = si->rho;
-        si->iter_b = si->iter;
+        if (!FD) si->iter_b = si->iter;
         si->total_b = so->total;
     }
-    if (si->brk || si->halt[si->iter & 1]) return false;
+    const int k = FD ? si->iter_b : si->iter;
+    if (FD) {
+        const bool held = si->halt[(k + 1) & 1] != 0;
+        if (si->brk || si->halt[k & 1] || held) {
+            if (held && blockIdx.x == 0 && threadIdx.x == 0) si->halt[k & 1] = 1;
+            return false;
+        }
+    } else if (si->brk || si->halt[k & 1]) {
+        return false;
+    }
     double pq = 0.0, alpha_d = 0.0;
     float alpha = 0.f;
     float acc = 0.f, acz = 0.f;
@@ -952,12 +965,13 @@ __device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r
             si->alpha = alpha_d;
             si->alpha32 = alpha;
             si->pq = pq;
+            if (FD) si->iter = k + 1;
         }
     }
     return true;
 }
 
-template <bool PC>
+template <bool PC, bool FD = false>
 __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
                                                        const uint8_t *__restrict__ mult, const float *__restrict__ wtab,
                                                        const uint8_t *__restrict__ gflag128, const double *part_pq, int G1,
@@ -965,7 +979,8 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
                                                        cudaGraphConditionalHandle h, int use_cond,
                                                        const float *__restrict__ dinv32, double *part_rz) {
     pdl_enter();
-    update_r32_step<PC>(N, r, q, mult, wtab, gflag128, part_pq, G1, part_rr, si, so, h, use_cond, dinv32, part_rz);
+    update_r32_step<PC, FD>(N, r, q, mult, wtab, gflag128, part_pq, G1, part_rr, si, so, h, use_cond, dinv32,
+                            part_rz);
 }
 
 // Inner Algorithm 3 lines 4, 7, 8 in FP32: every block sums the partials of
@@ -1055,6 +1070,194 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t
     if (si->brk || si->halt[k & 1]) return;
     update_dp32_step<PC>(N, d, p, r, part_rr, G2, si, so, h, use_cond, dinv32, part_rz, k, si->alpha32,
                          si->total_b + 1, si->rho_b);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 product with the previous iteration's direction update folded in
+// (k_spmv_fd).  Inner Algorithm 3 lines 7-8 of iteration k-1 (beta, d += alpha
+// p, p = z + beta p) and line 2 of iteration k (q = S p with the weighted dot)
+// as one launch: the product forms p_k at every column it gathers from p_{k-1}
+// and z_k (the value the direction update would have stored, bit for bit),
+// and the lane that owns a row stores p_k and d there.  p_{k-1} and p_k live in
+// two buffers used in turn (P[k & 1] holds p_k), so no block reads an entry
+// another block writes.
+
+// x = p_k entry j from p_{k-1} and z_k = r_k (M^-1 r_k with the preconditioner).
+template <bool PC>
+struct DirX {
+    const float *__restrict__ pold;
+    const float *__restrict__ r;
+    const float *__restrict__ dinv;
+    float beta;
+    __device__ __forceinline__ float operator()(int j) const {
+        const float z = PC ? __ldg(r + j) * __ldg(dinv + j) : __ldg(r + j);
+        return fmaf(beta, __ldg(pold + j), z);
+    }
+};
+// x = p_0 as the refinement's first kernel stored it.
+struct PlainX {
+    const float *__restrict__ x;
+    __device__ __forceinline__ float operator()(int j) const { return __ldg(x + j); }
+};
+
+template <int N, typename X>
+__device__ __forceinline__ float fd_chunk(const float *__restrict__ sv, const int32_t *__restrict__ sc,
+                                          const X &xf, int base, int k0, float acc) {
+    float vv[N], xv[N];
+    int cc[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        vv[j] = __ldcs(sv + base + (k0 + j) * kSliceRows);
+        cc[j] = __ldcs(sc + base + (k0 + j) * kSliceRows);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) xv[j] = xf(cc[j]);
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc = fmaf(vv[j], xv[j], acc);
+    return acc;
+}
+
+template <typename X>
+__device__ __forceinline__ float fd_row(const float *__restrict__ sv, const int32_t *__restrict__ sc, const X &xf,
+                                        int off, int w, int lane) {
+    const int base = off + lane;
+    float acc = 0.f;
+    int k = 0;
+    for (; k + 4 <= w; k += 4) acc = fd_chunk<4>(sv, sc, xf, base, k, acc);
+    switch (w - k) {
+        case 1: return fd_chunk<1>(sv, sc, xf, base, k, acc);
+        case 2: return fd_chunk<2>(sv, sc, xf, base, k, acc);
+        case 3: return fd_chunk<3>(sv, sc, xf, base, k, acc);
+        default: return acc;
+    }
+}
+
+// Row `row`'s own entry: y = S p_k there, p_k and d stored (UPD), and its
+// share of (p_k, S p_k)_w (weight w).
+template <bool UPD, typename X>
+__device__ __forceinline__ void fd_store(const X &xf, int row, float yv, float w, bool weighted,
+                                         const float *__restrict__ pold, float *__restrict__ pnew,
+                                         float *__restrict__ d, float alpha, float *__restrict__ y, float &dot) {
+    const float pk = xf(row);
+    y[row] = yv;
+    if (UPD) {
+        pnew[row] = pk;
+        d[row] = fmaf(alpha, __ldg(pold + row), d[row]);
+    }
+    dot = fmaf(weighted ? w * pk : pk, yv, dot);
+}
+
+template <bool UPD, typename X>
+__device__ __forceinline__ float fd_items(const DevOp &A, const X &xf, const float *__restrict__ pold,
+                                          float *__restrict__ pnew, float *__restrict__ d, float alpha,
+                                          float *__restrict__ y) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int2 range = A.warp_range[blockIdx.x * kSpmvWarps + warp];
+    const float *__restrict__ sv = A.sval32;
+    float dot = 0.f;
+    for (int it = range.x; it < range.y; ++it) {
+        const WorkItem W = A.items[it];
+        if (W.kind == kItemSlice || W.kind == kItemIfaceSlice) {
+            const float acc = fd_row(sv, A.scol, xf, W.e0, W.e1, lane);
+            if (W.kind == kItemSlice) {
+                const int r = W.a + lane;
+                if (r < W.b) fd_store<UPD>(xf, r, acc, 1.f, false, pold, pnew, d, alpha, y, dot);
+            } else {
+                const int c = W.a + lane;
+                const bool valid = c < W.b;
+                const int seg = valid ? __ldg(A.sseg + c) : 0;
+                const int l0 = seg & 0xff, m = seg >> 8;
+                const int mmax = __reduce_max_sync(0xffffffffu, m);
+                float S = 0.f;
+                for (int t = 0; t < mmax; ++t) {
+                    const float v = __shfl_sync(0xffffffffu, acc, (l0 + t) & 31);
+                    if (t < m) S += v;
+                }
+                if (valid)
+                    fd_store<UPD>(xf, __ldg(A.icopy + c), S, __ldg(A.wtab32 + m), true, pold, pnew, d, alpha, y,
+                                  dot);
+            }
+        } else if (W.kind == kItemLongRow) {
+            float acc = 0.f;
+            for (int k = W.e0 + lane; k < W.e1; k += 32) acc = fmaf(A.val32[k], xf(A.col[k]), acc);
+            const float racc = float(warp_sum(double(acc)));
+            if (lane == 0) fd_store<UPD>(xf, W.a, racc, 1.f, false, pold, pnew, d, alpha, y, dot);
+        } else {
+            float S = 0.f;
+            for (int c = W.c0; c < W.c1; ++c) {
+                float acc = 0.f;
+                for (int k = A.irp[c] + lane; k < A.irp[c + 1]; k += 32) acc = fmaf(A.ival32[k], xf(A.icol[k]), acc);
+                S += float(warp_sum(double(acc)));  // valid in lane 0
+            }
+            if (lane == 0) {
+                const float w = __ldg(A.wtab32 + (W.c1 - W.c0));
+                for (int c = W.c0; c < W.c1; ++c) fd_store<UPD>(xf, A.icopy[c], S, w, true, pold, pnew, d, alpha, y, dot);
+            }
+        }
+    }
+    return dot;
+}
+
+// Iteration k of the FP32 inner CG (k = si->iter).  k = 0: q = S p_0 from the
+// stored p_0.  k >= 1: every block sums the residual kernel's partials of
+// (r_k, r_k)_w (and (r_k, z_k)_w), forms beta = rho_k / rho_{k-1} once, takes
+// the stopping decision of iteration k-1 (sqrt(rho) <= tau sqrt(rho0), or the
+// summed inner iterations reach max_iter); on a stop it applies d += alpha
+// p_{k-1} alone (grid-stride) and raises halt[(k + 1) & 1], else it runs the
+// product on p_k as above.  Block 0 records rho, beta and the summed count.
+// BPS: resident blocks per SM of the launch (the grid and warp ranges of
+// the FP32 product instance in use, so both forms partition the work alike).
+template <bool PC, int BPS>
+__global__ void __launch_bounds__(kSpmvThreads, BPS)
+    k_spmv_fd(DevOp A, int64_t N, const float *__restrict__ r, const float *__restrict__ dinv32, float *p0,
+              float *p1, float *__restrict__ d, float *__restrict__ y, double *part_pq, const double *part_rr,
+              const double *part_rz, int G2, Scal *si, Scal *so, cudaGraphConditionalHandle h, int use_cond) {
+    const int k = si->iter;
+    if (blockIdx.x == 0 && threadIdx.x == 0) si->iter_b = k;
+    if (si->brk || si->halt[k & 1]) return;
+    float *pnew = (k & 1) ? p1 : p0;
+    const float *pold = (k & 1) ? p0 : p1;
+    float dot;
+    if (k == 0) {
+        dot = fd_items<false>(A, PlainX{pnew}, pold, pnew, d, 0.f, y);
+    } else {
+        const double rr = all_sum_partials(part_rr, G2);
+        const double rz = PC ? all_sum_partials(part_rz, G2) : rr;
+        float beta = 0.f;
+        const double beta_d = block_quotient(rz, si->rho_b, &beta);
+        const float alpha = si->alpha32;
+        const int total1 = si->total_b + 1;
+        const bool stop = sqrt(rr) <= si->tau * sqrt(si->rho0) || total1 >= so->max_iter;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            si->rho = rz;
+            si->rr = rr;
+            si->beta = beta_d;
+            si->beta32 = beta;
+            so->total = total1;
+            if (stop) {
+                si->halt[(k + 1) & 1] = 1;
+                stop_loop(si, h, use_cond);
+            }
+        }
+        if (stop) {
+            const int64_t stride = (int64_t)gridDim.x * kSpmvThreads;
+            for (int64_t i = (int64_t)blockIdx.x * kSpmvThreads + threadIdx.x; i < N; i += stride)
+                d[i] = fmaf(alpha, pold[i], d[i]);
+            return;
+        }
+        dot = fd_items<true>(A, DirX<PC>{pold, r, dinv32, beta}, pold, pnew, d, alpha, y);
+    }
+    __shared__ double wsum[kSpmvWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double wv = double(warp_sumf(dot));
+    if (lane == 0) wsum[warp] = wv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bs = wsum[0];
+#pragma unroll
+        for (int w = 1; w < kSpmvWarps; ++w) bs += wsum[w];
+        part_pq[blockIdx.x] = bs;
+    }
 }
 
 // Bounds of the grid barrier's wait: about one second of %globaltimer, or

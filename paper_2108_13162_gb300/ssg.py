@@ -35,6 +35,9 @@ SSG_BAND_ROW = 0
 SSG_BAND_COL = 1
 SSG_BAND_AUTO = 0
 SSG_BAND_STAGED = -1
+SSG_FUSE_NONE = 0
+SSG_FUSE_GRID = 1
+SSG_FUSE_SPMV = 2
 
 # every entry point declared in include/ssg.h
 EXPORTS = (
@@ -274,8 +277,8 @@ def ssg_set_pdl(ctx, enable: bool):
     return _check(lib().ssg_set_pdl(ctx, int(bool(enable))), "ssg_set_pdl")
 
 
-def ssg_set_fused(ctx, enable: bool):
-    return _check(lib().ssg_set_fused(ctx, int(bool(enable))), "ssg_set_fused")
+def ssg_set_fused(ctx, mode: int):
+    return _check(lib().ssg_set_fused(ctx, int(mode)), "ssg_set_fused")
 
 
 def ssg_check_barrier_timeout(ctx) -> int:
@@ -559,8 +562,9 @@ class Context:
     def set_pdl(self, enable: bool):
         ssg_set_pdl(self.h, enable)
 
-    def set_fused(self, enable: bool):
-        ssg_set_fused(self.h, enable)
+    def set_fused(self, mode: int):
+        """SSG_FUSE_NONE, SSG_FUSE_GRID or SSG_FUSE_SPMV (systems partitioned afterwards)."""
+        ssg_set_fused(self.h, mode)
 
     def set_mixed(self, inner_rtol: float = 1e-4, max_outer: int = 30):
         ssg_set_mixed(self.h, inner_rtol, max_outer)

@@ -11,8 +11,9 @@ inner FP32 sums are ordered differently on each side):
     (kappa from the Lanczos coefficients of the FP64 oracle run);
   * both drivers (graph, host loop) give the same bits; the parameters are
     validated; a one-refinement cap stops with SSG_E_NOT_CONVERGED;
-  * the fused FP32 update (one cooperative kernel with a grid barrier) gives
-    the bits of the two-kernel form; its barrier's bounded wait times out.
+  * the fused kernel splits of the FP32 iteration (SSG_FUSE_GRID,
+    SSG_FUSE_SPMV) give the bits of the three-kernel form; the grid
+    barrier's bounded wait times out.
 """
 
 import json
@@ -156,16 +157,27 @@ def test_mixed_full_size_128cube(ctx):
     assert _rel(xg, p.xstar[:, 0]) <= 2 * kap * 1e-8
 
 
-def _fused_pair(ctx, p):
+def _fused_pair(ctx, p, mode):
+    from paper_2108_13162_gb300 import ssg
     from paper_2108_13162_gb300.ssg import System
 
-    S0 = System(ctx, p.A, p.part, p.P)  # the default: two kernels
-    ctx.set_fused(True)
+    S0 = System(ctx, p.A, p.part, p.P)  # the default: three kernels
+    ctx.set_fused(mode)
     try:
         S1 = System(ctx, p.A, p.part, p.P)
     finally:
-        ctx.set_fused(False)
+        ctx.set_fused(ssg.SSG_FUSE_NONE)
     return S0, S1
+
+
+def _launch_saving(mode, st):
+    """Kernels a fused form saves in one graph solve against three per inner
+    iteration: one per inner iteration, less, for the folded form, the two
+    kernels of the extra loop pass of every refinement (its product only
+    completes d)."""
+    from paper_2108_13162_gb300 import ssg
+
+    return st["iters"] - (2 * st["outer"] if mode == ssg.SSG_FUSE_SPMV else 0)
 
 
 FUSED_CASES = [
@@ -174,16 +186,18 @@ FUSED_CASES = [
 ]
 
 
+@pytest.mark.parametrize("fuse", [1, 2], ids=["grid", "spmv"])
 @pytest.mark.parametrize("name,mk", FUSED_CASES, ids=[c[0] for c in FUSED_CASES])
-def test_mixed_fused_update_same_bits(ctx, name, mk):
-    """The FP32 residual and direction updates as one cooperative kernel with
-    a grid barrier give the bits, iteration counts and refinements of the
-    two-kernel form (the default), in both modes and with both drivers, and
-    launches one kernel fewer per inner iteration."""
+def test_mixed_fused_update_same_bits(ctx, name, mk, fuse):
+    """The fused kernel splits (SSG_FUSE_GRID: both updates as one
+    cooperative kernel with a grid barrier; SSG_FUSE_SPMV: the direction
+    update folded into the next product) give the bits, iteration counts and
+    refinements of the three-kernel form (the default), in both modes and
+    with both drivers, and launch fewer kernels."""
     from paper_2108_13162_gb300 import ssg
 
     p = mk()
-    S0, S1 = _fused_pair(ctx, p)
+    S0, S1 = _fused_pair(ctx, p, fuse)
     b = _t(p.b[:, 0])
     for mode in (ssg.SSG_MIXED, ssg.SSG_MIXED_JACOBI):
         for driver in (ssg.SSG_DRIVER_GRAPH, ssg.SSG_DRIVER_HOST):
@@ -197,20 +211,22 @@ def test_mixed_fused_update_same_bits(ctx, name, mk):
             assert (s1[0]["iters"], s1[0]["outer"]) == (s0[0]["iters"], s0[0]["outer"])
             assert np.array_equal(x1.cpu().numpy(), x0.cpu().numpy()), (mode, driver)
             if driver == ssg.SSG_DRIVER_GRAPH:
-                assert s0[0]["kernel_launches"] - s1[0]["kernel_launches"] == s1[0]["iters"]
+                assert s0[0]["kernel_launches"] - s1[0]["kernel_launches"] == _launch_saving(fuse, s1[0])
             else:
                 assert s1[0]["kernel_launches"] < s0[0]["kernel_launches"]
     S0.close()
     S1.close()
 
 
-def test_mixed_fused_update_same_bits_128cube(ctx):
+@pytest.mark.parametrize("fuse", [1, 2], ids=["grid", "spmv"])
+def test_mixed_fused_update_same_bits_128cube(ctx, fuse):
     """The benchmark's system (several float4 items per thread, the full
-    608-block grid): fused and two-kernel forms agree bit for bit."""
+    608-block grid): the fused forms and the three-kernel form agree bit for
+    bit."""
     from paper_2108_13162_gb300 import ssg
 
     p = config_problem(2)
-    S0, S1 = _fused_pair(ctx, p)
+    S0, S1 = _fused_pair(ctx, p, fuse)
     b = _t(p.b[:, 0])
     for mode in (ssg.SSG_MIXED, ssg.SSG_MIXED_JACOBI):
         x0, rc0, s0 = S0.solve(b, rtol=1e-8, mode=mode)
@@ -218,7 +234,7 @@ def test_mixed_fused_update_same_bits_128cube(ctx):
         assert rc0 == rc1 == ssg.SSG_OK
         assert (s1[0]["iters"], s1[0]["outer"]) == (s0[0]["iters"], s0[0]["outer"])
         assert np.array_equal(x1.cpu().numpy(), x0.cpu().numpy()), mode
-        assert s0[0]["kernel_launches"] - s1[0]["kernel_launches"] == s1[0]["iters"]
+        assert s0[0]["kernel_launches"] - s1[0]["kernel_launches"] == _launch_saving(fuse, s1[0])
     S0.close()
     S1.close()
 
