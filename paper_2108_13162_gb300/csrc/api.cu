@@ -182,6 +182,17 @@ const SpmvVariant<float> kSpmv32Variants[kSpmvVariants] = {
     {4, 2, k_spmv_asm<kEpiPartials, float, 4, 2>, k_spmv_asm<kEpiStore, float, 4, 2>},
 };
 
+// The folded-direction FP32 product (SSG_FUSE_SPMV) for each entry of
+// kSpmv32Variants (same blocks per SM and L2 prefetch distance), without and
+// with the diagonal preconditioner.
+using SpmvFdFn = void (*)(DevOp, int64_t, const float *, const float *, float *, float *, float *, float *,
+                          double *, const double *, const double *, int, Scal *, Scal *,
+                          cudaGraphConditionalHandle, int);
+const SpmvFdFn kSpmvFdVariants[2][kSpmvVariants] = {
+    {k_spmv_fd<false, 5, 1>, k_spmv_fd<false, 5, 0>, k_spmv_fd<false, 4, 1>, k_spmv_fd<false, 4, 2>},
+    {k_spmv_fd<true, 5, 1>, k_spmv_fd<true, 5, 0>, k_spmv_fd<true, 4, 1>, k_spmv_fd<true, 4, 2>},
+};
+
 // SpMV work list (see WorkItem in kernels.cuh) and the sliced-ELL copy of
 // the local matrices it streams.  Interior slices: up to 32 consecutive
 // interior rows of one subdomain, width = their longest row; a row longer
@@ -462,8 +473,7 @@ int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const int64_t N = S->maps.nloc;
     const cudaGraphConditionalHandle h = S->cond_in[pc];
     if (S->fdir) {
-        const bool b5 = kSpmv32Variants[S->var32].bps == 5;
-        auto fd = pc ? (b5 ? k_spmv_fd<true, 5> : k_spmv_fd<true, 4>) : (b5 ? k_spmv_fd<false, 5> : k_spmv_fd<false, 4>);
+        auto fd = kSpmvFdVariants[pc][S->var32];
         fd<<<S->grid_spmv32, kSpmvThreads, 0, st>>>(S->op32, N, S->d_r32, S->d_dinv32, S->d_p32, S->d_p32b, S->d_d32,
                                                     S->d_q32, part_pq(S), part_rr(S), part_rz(S), S->grid_vec,
                                                     S->d_scal_in, S->d_scal, h, use_cond);

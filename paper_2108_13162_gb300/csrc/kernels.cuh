@@ -1123,11 +1123,15 @@ __device__ __forceinline__ float fd_row(const float *__restrict__ sv, const int3
     const int base = off + lane;
     float acc = 0.f;
     int k = 0;
-    for (; k + 4 <= w; k += 4) acc = fd_chunk<4>(sv, sc, xf, base, k, acc);
+    for (; k + 8 <= w; k += 8) acc = fd_chunk<8>(sv, sc, xf, base, k, acc);
     switch (w - k) {
         case 1: return fd_chunk<1>(sv, sc, xf, base, k, acc);
         case 2: return fd_chunk<2>(sv, sc, xf, base, k, acc);
         case 3: return fd_chunk<3>(sv, sc, xf, base, k, acc);
+        case 4: return fd_chunk<4>(sv, sc, xf, base, k, acc);
+        case 5: return fd_chunk<5>(sv, sc, xf, base, k, acc);
+        case 6: return fd_chunk<6>(sv, sc, xf, base, k, acc);
+        case 7: return fd_chunk<7>(sv, sc, xf, base, k, acc);
         default: return acc;
     }
 }
@@ -1147,7 +1151,7 @@ __device__ __forceinline__ void fd_store(const X &xf, int row, float yv, float w
     dot = fmaf(weighted ? w * pk : pk, yv, dot);
 }
 
-template <bool UPD, typename X>
+template <bool UPD, int AHEAD, typename X>
 __device__ __forceinline__ float fd_items(const DevOp &A, const X &xf, const float *__restrict__ pold,
                                           float *__restrict__ pnew, float *__restrict__ d, float alpha,
                                           float *__restrict__ y) {
@@ -1157,6 +1161,14 @@ __device__ __forceinline__ float fd_items(const DevOp &A, const X &xf, const flo
     float dot = 0.f;
     for (int it = range.x; it < range.y; ++it) {
         const WorkItem W = A.items[it];
+        if (AHEAD > 0 && it + AHEAD < range.y) {
+            // the value and column lines of a slice further ahead, one line per lane
+            const WorkItem Wp = A.items[it + AHEAD];
+            if ((Wp.kind == kItemSlice || Wp.kind == kItemIfaceSlice) && lane < Wp.e1) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(sv + Wp.e0 + lane * kSliceRows));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
+            }
+        }
         if (W.kind == kItemSlice || W.kind == kItemIfaceSlice) {
             const float acc = fd_row(sv, A.scol, xf, W.e0, W.e1, lane);
             if (W.kind == kItemSlice) {
@@ -1205,9 +1217,10 @@ __device__ __forceinline__ float fd_items(const DevOp &A, const X &xf, const flo
 // summed inner iterations reach max_iter); on a stop it applies d += alpha
 // p_{k-1} alone (grid-stride) and raises halt[(k + 1) & 1], else it runs the
 // product on p_k as above.  Block 0 records rho, beta and the summed count.
-// BPS: resident blocks per SM of the launch (the grid and warp ranges of
-// the FP32 product instance in use, so both forms partition the work alike).
-template <bool PC, int BPS>
+// BPS, AHEAD: resident blocks per SM of the launch and slices ahead
+// prefetched into L2, those of the FP32 product instance in use (so both
+// forms partition the work alike).
+template <bool PC, int BPS, int AHEAD>
 __global__ void __launch_bounds__(kSpmvThreads, BPS)
     k_spmv_fd(DevOp A, int64_t N, const float *__restrict__ r, const float *__restrict__ dinv32, float *p0,
               float *p1, float *__restrict__ d, float *__restrict__ y, double *part_pq, const double *part_rr,
@@ -1219,7 +1232,7 @@ __global__ void __launch_bounds__(kSpmvThreads, BPS)
     const float *pold = (k & 1) ? p0 : p1;
     float dot;
     if (k == 0) {
-        dot = fd_items<false>(A, PlainX{pnew}, pold, pnew, d, 0.f, y);
+        dot = fd_items<false, AHEAD>(A, PlainX{pnew}, pold, pnew, d, 0.f, y);
     } else {
         const double rr = all_sum_partials(part_rr, G2);
         const double rz = PC ? all_sum_partials(part_rz, G2) : rr;
@@ -1245,7 +1258,7 @@ __global__ void __launch_bounds__(kSpmvThreads, BPS)
                 d[i] = fmaf(alpha, pold[i], d[i]);
             return;
         }
-        dot = fd_items<true>(A, DirX<PC>{pold, r, dinv32, beta}, pold, pnew, d, alpha, y);
+        dot = fd_items<true, AHEAD>(A, DirX<PC>{pold, r, dinv32, beta}, pold, pnew, d, alpha, y);
     }
     __shared__ double wsum[kSpmvWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
