@@ -60,6 +60,7 @@ def parse_args(argv=None):
                          "Both stop on an FP64 relative residual of 1e-8; the other mode is timed too and reported")
     ap.add_argument("--pdl", choices=("on", "off"), default="off",
                     help="programmatic dependent launch for the per-iteration update kernels")
+    ap.add_argument("--unroll", type=int, default=4, help="CG iterations per pass of the loop graph's body")
     ap.add_argument("--fuse", choices=("none", "grid", "spmv"), default="none",
                     help="kernel split of the FP32 inner iteration: three kernels; the two updates as one "
                          "cooperative kernel (grid barrier); the direction update folded into the next product")
@@ -702,6 +703,7 @@ def run_ours(args, dist):
     if args.driver == "host":
         ctx.set_driver(ssg.SSG_DRIVER_HOST)
     ctx.set_pdl(args.pdl == "on")
+    ctx.set_unroll(args.unroll)
     ctx.set_fused({"none": ssg.SSG_FUSE_NONE, "grid": ssg.SSG_FUSE_GRID, "spmv": ssg.SSG_FUSE_SPMV}[args.fuse])
     S = System(ctx, prob.A, prob.part, prob.P)
     b = torch.from_numpy(prob.b[:, 0].copy()).to("cuda:%d" % dev)
@@ -852,6 +854,7 @@ def run_ours(args, dist):
             "driver": args.driver,
             "pdl": args.pdl,
             "fuse": args.fuse,
+            "unroll": args.unroll,
         },
         "roofline": roof[dominant],
         "roofline_other": roof["fp64" if dominant == "fp32" else "fp32"],

@@ -126,6 +126,15 @@ int ssg_set_pdl(ssg_ctx *ctx, int enable);
 #define SSG_FUSE_GRID 1
 #define SSG_FUSE_SPMV 2
 int ssg_set_fused(ssg_ctx *ctx, int mode);
+/* CG iterations per pass of the body of a single-vector solve's loop graph
+ * (1..8, default 4): the body holds that many copies of one iteration's
+ * kernels; once the loop has stopped, the later copies of the last pass
+ * return at once (the host-loop driver relies on the same flags).  Results
+ * are unchanged.  Each pass of a conditional loop costs about 1.9 us on
+ * GB300: on the 128^3 system 4 copies per pass take 39.7 us per mixed inner
+ * iteration and 73.0 us per FP64 iteration, against 41.5 and 74.7 with one.
+ * Applies to systems partitioned on this context afterwards. */
+int ssg_set_unroll(ssg_ctx *ctx, int32_t iters);
 /* Runs the fused update's grid barrier once in a two-block cooperative
  * launch in which one block never arrives: the other's wait gives up after
  * about a second and the call returns SSG_E_TIMEOUT (SSG_OK would mean the

@@ -57,6 +57,7 @@ struct ssg_system {
     bool pdl = false;  // loop-body kernels use programmatic dependent launch
     bool fuse = false;  // FP32 inner updates as one cooperative launch (k_update_rdp32)
     bool fdir = false;  // FP32 direction update folded into the next product (k_spmv_fd)
+    int unroll = 4;     // iterations per pass of the single-vector loop bodies
     float *d_p32b = nullptr;  // the second direction buffer of the folded form
     unsigned long long *d_gbar = nullptr;  // its grid barrier's arrival counter, zeroed before each solve
     int grid_spmv = 0;
@@ -481,7 +482,7 @@ int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
         SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_r32<true, true> : k_update_r32<false, true>, S->grid_vec, kBlock,
                               st, N, S->d_r32, S->d_q32, S->op.mult, S->op.wtab32, S->op.gflag128,
                               (const double *)part_pq(S), S->grid_spmv32, part_rr(S), S->d_scal_in,
-                              (const Scal *)S->d_scal, h, use_cond, (const float *)S->d_dinv32, part_rz(S)));
+                              S->d_scal, h, use_cond, (const float *)S->d_dinv32, part_rz(S)));
         return SSG_OK;
     }
     SSG_CUDA_TRY(launch_k(false, kSpmv32Variants[S->var32].part, S->grid_spmv32, kSpmvThreads, st, S->op32,
@@ -496,7 +497,7 @@ int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     }
     SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_r32<true> : k_update_r32<false>, S->grid_vec, kBlock, st, N,
                           S->d_r32, S->d_q32, S->op.mult, S->op.wtab32, S->op.gflag128, (const double *)part_pq(S),
-                          S->grid_spmv32, part_rr(S), S->d_scal_in, (const Scal *)S->d_scal, h, use_cond,
+                          S->grid_spmv32, part_rr(S), S->d_scal_in, S->d_scal, h, use_cond,
                           (const float *)S->d_dinv32, part_rz(S)));
     SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_dp32<true> : k_update_dp32<false>, S->grid_vec, kBlock, st, N,
                           S->d_d32, S->d_p32, S->d_r32, (const double *)part_rr(S), S->grid_vec, S->d_scal_in,
@@ -588,7 +589,11 @@ int build_graph_once(ssg_system *S, bool pc) {
     if (e == cudaSuccess && rc == SSG_OK) e = last_node(graph, &init_node);
     if (e == cudaSuccess && rc == SSG_OK) e = add_while(graph, &init_node, cond, &loop_node, &body);
     if (e == cudaSuccess && rc == SSG_OK)
-        e = capture_into(cap, body, nullptr, 0, [&](cudaStream_t c) { return launch_body(S, c, 1, pc); }, &rc);
+        e = capture_into(cap, body, nullptr, 0, [&](cudaStream_t c) {
+                int r = SSG_OK;
+                for (int u = 0; u < S->unroll && r == SSG_OK; ++u) r = launch_body(S, c, 1, pc);
+                return r;
+            }, &rc);
     if (e == cudaSuccess && rc == SSG_OK) e = cudaGraphInstantiate(&exec, graph, 0);
     cudaStreamDestroy(cap);
     if (rc != SSG_OK) return rc;
@@ -643,7 +648,11 @@ int build_graph_mixed_once(ssg_system *S, bool pc) {
     if (e == cudaSuccess && rc == SSG_OK) e = last_node(body_out, &n_iinit);
     if (e == cudaSuccess && rc == SSG_OK) e = add_while(body_out, &n_iinit, S->cond_in[pc], &n_inner, &body_in);
     if (e == cudaSuccess && rc == SSG_OK)
-        e = capture_into(cap, body_in, nullptr, 0, [&](cudaStream_t c) { return launch_inner_body(S, c, 1, pc); },
+        e = capture_into(cap, body_in, nullptr, 0, [&](cudaStream_t c) {
+                int r = SSG_OK;
+                for (int u = 0; u < S->unroll && r == SSG_OK; ++u) r = launch_inner_body(S, c, 1, pc);
+                return r;
+            },
                          &rc);
     if (e == cudaSuccess && rc == SSG_OK)
         e = capture_into(cap, body_out, &n_inner, 1,
@@ -1056,13 +1065,12 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     float ms = 0.f;
     SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
     if (C->driver == SSG_DRIVER_GRAPH) {
-        if (mixed)  // init, per refinement: inner init + 3 tail kernels, 3 per inner iteration (fused: 2;
-                    // folded: 2 per inner iteration and per refinement, whose last product only ends d)
-            launches += 1 + 4 * static_cast<int64_t>(h.iter) +
-                        (S->fdir ? 2 * (static_cast<int64_t>(h.total) + h.iter)
-                                 : (S->fuse ? 2 : 3) * static_cast<int64_t>(h.total));
-        else  // init, 3 per iteration (a breakdown ends after the SpMV and residual kernels of one more)
-            launches += 1 + 3 * static_cast<int64_t>(h.iter) + (h.status == SSG_E_BREAKDOWN ? 3 : 0);
+        // every copy of an iteration in a loop pass launches all its kernels;
+        // the device counts the residual-update launches (h.passes)
+        if (mixed)  // init, per refinement: inner init + 3 tail kernels; 3 per inner copy (fused forms: 2)
+            launches += 1 + 4 * static_cast<int64_t>(h.iter) + (S->fuse || S->fdir ? 2 : 3) * int64_t(h.passes);
+        else  // init, 3 per copy
+            launches += 1 + 3 * static_cast<int64_t>(h.passes);
     }
     if (st) {
         st->status = h.status;
@@ -1669,6 +1677,15 @@ int ssg_set_fused(ssg_ctx *ctx, int mode) {
     return SSG_OK;
 }
 
+int ssg_set_unroll(ssg_ctx *ctx, int32_t iters) {
+    if (!ctx || iters < 1 || iters > 8) {
+        set_error("ssg_set_unroll: null context, or iterations per loop pass not in 1..8");
+        return SSG_E_INVALID;
+    }
+    ctx->unroll = iters;
+    return SSG_OK;
+}
+
 int ssg_check_barrier_timeout(ssg_ctx *ctx) {
     if (!ctx) {
         set_error("null context");
@@ -1745,6 +1762,7 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
         S->pdl = ctx->pdl != 0;
         S->fuse = ctx->fuse == SSG_FUSE_GRID;
         S->fdir = ctx->fuse == SSG_FUSE_SPMV;
+        S->unroll = ctx->unroll;
         rc = upload(S);
         if (rc != SSG_OK) {
             ssg_system_destroy(S);
@@ -1777,6 +1795,7 @@ int ssg_partition_fe(ssg_ctx *ctx, int32_t n, int32_t ne, int32_t nv, const int3
         S->pdl = ctx->pdl != 0;
         S->fuse = ctx->fuse == SSG_FUSE_GRID;
         S->fdir = ctx->fuse == SSG_FUSE_SPMV;
+        S->unroll = ctx->unroll;
         rc = upload(S);
         if (rc != SSG_OK) {
             ssg_system_destroy(S);
@@ -1821,6 +1840,7 @@ int make_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off, const in
     S->pdl = ctx->pdl != 0;
     S->fuse = ctx->fuse == SSG_FUSE_GRID;
     S->fdir = ctx->fuse == SSG_FUSE_SPMV;
+    S->unroll = ctx->unroll;
     rc = upload(S);
     if (rc != SSG_OK) {
         ssg_system_destroy(S);

@@ -84,7 +84,7 @@ struct Scal {
     int32_t total_b;
     int32_t halt[2];
     int32_t brk;     // (S p, p) <= 0 seen: every later kernel returns at once
-    int32_t pad2;
+    int32_t passes;  // launches of the residual update (one per iteration copy the loop ran)
 };
 
 enum { kTicketSpmv = 0, kTicketR = 1, kTicketXP = 2, kTicketMisc = 3 };
@@ -497,6 +497,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r(int64_t N,
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         s->rho_b = s->rho;
         s->iter_b = s->iter;
+        s->passes += 1;
     }
     if (s->brk || s->halt[s->iter & 1]) return;
     double pq = 0.0, alpha = 0.0;
@@ -699,6 +700,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t N, const double *__r
             s->bnorm = sqrt(bb);
             s->iter = 0;
             s->total = 0;
+            s->passes = 0;
             s->done = 0;
             s->stop_after_xp = 0;
             s->brk = 0;
@@ -860,13 +862,14 @@ template <bool PC, bool FD = false>
 __device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r, const float *__restrict__ q,
                                                 const uint8_t *__restrict__ mult, const float *__restrict__ wtab,
                                                 const uint8_t *__restrict__ gflag128, const double *part_pq, int G1,
-                                                double *part_rr, Scal *si, const Scal *so,
+                                                double *part_rr, Scal *si, Scal *so,
                                                 cudaGraphConditionalHandle h, int use_cond,
                                                 const float *__restrict__ dinv32, double *part_rz) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         si->rho_b = si->rho;
         if (!FD) si->iter_b = si->iter;
         si->total_b = so->total;
+        so->passes += 1;
     }
     const int k = FD ? si->iter_b : si->iter;
     if (FD) {
@@ -975,7 +978,7 @@ template <bool PC, bool FD = false>
 __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
                                                        const uint8_t *__restrict__ mult, const float *__restrict__ wtab,
                                                        const uint8_t *__restrict__ gflag128, const double *part_pq, int G1,
-                                                       double *part_rr, Scal *si, const Scal *so,
+                                                       double *part_rr, Scal *si, Scal *so,
                                                        cudaGraphConditionalHandle h, int use_cond,
                                                        const float *__restrict__ dinv32, double *part_rz) {
     pdl_enter();

@@ -21,6 +21,7 @@ struct ssg_ctx {
     double inner_rtol = 1e-4;  // SSG_MIXED: inner FP32 CG tolerance
     int32_t max_outer = 30;    // SSG_MIXED: refinement steps cap
     int32_t rhs_block = 16;    // right-hand sides solved together (1, 2, 4, 8 or 16)
+    int32_t unroll = 4;        // CG iterations per pass of a single-vector loop graph's body (measured: 4 beats 1)
 };
 
 namespace ssg {

@@ -48,6 +48,7 @@ EXPORTS = (
     "ssg_set_rhs_block",
     "ssg_set_pdl",
     "ssg_set_fused",
+    "ssg_set_unroll",
     "ssg_check_barrier_timeout",
     "ssg_destroy",
     "ssg_partition",
@@ -179,6 +180,7 @@ def lib():
         L.ssg_set_rhs_block.argtypes = [vp, C.c_int32]
         L.ssg_set_pdl.argtypes = [vp, C.c_int]
         L.ssg_set_fused.argtypes = [vp, C.c_int]
+        L.ssg_set_unroll.argtypes = [vp, C.c_int32]
         L.ssg_check_barrier_timeout.argtypes = [vp]
         L.ssg_destroy.argtypes = [vp]
         L.ssg_partition.argtypes = [vp, i32, vp, vp, vp, vp, i32, C.POINTER(vp)]
@@ -279,6 +281,10 @@ def ssg_set_pdl(ctx, enable: bool):
 
 def ssg_set_fused(ctx, mode: int):
     return _check(lib().ssg_set_fused(ctx, int(mode)), "ssg_set_fused")
+
+
+def ssg_set_unroll(ctx, iters: int):
+    return _check(lib().ssg_set_unroll(ctx, int(iters)), "ssg_set_unroll")
 
 
 def ssg_check_barrier_timeout(ctx) -> int:
@@ -561,6 +567,10 @@ class Context:
 
     def set_pdl(self, enable: bool):
         ssg_set_pdl(self.h, enable)
+
+    def set_unroll(self, iters: int):
+        """CG iterations per pass of a single-vector loop graph's body (systems partitioned afterwards)."""
+        ssg_set_unroll(self.h, iters)
 
     def set_fused(self, mode: int):
         """SSG_FUSE_NONE, SSG_FUSE_GRID or SSG_FUSE_SPMV (systems partitioned afterwards)."""

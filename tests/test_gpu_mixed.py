@@ -27,6 +27,8 @@ from synth import CSR, config_problem
 
 pytestmark = pytest.mark.gpu
 
+UNROLL_DEFAULT = 4  # CG iterations per loop pass unless ssg_set_unroll says otherwise
+
 
 @pytest.fixture(scope="module")
 def ctx():
@@ -161,12 +163,15 @@ def _fused_pair(ctx, p, mode):
     from paper_2108_13162_gb300 import ssg
     from paper_2108_13162_gb300.ssg import System
 
-    S0 = System(ctx, p.A, p.part, p.P)  # the default: three kernels
-    ctx.set_fused(mode)
+    # one iteration per loop pass, so that the launch counts below are exact
+    ctx.set_unroll(1)
     try:
+        S0 = System(ctx, p.A, p.part, p.P)  # the default split: three kernels
+        ctx.set_fused(mode)
         S1 = System(ctx, p.A, p.part, p.P)
     finally:
         ctx.set_fused(ssg.SSG_FUSE_NONE)
+        ctx.set_unroll(UNROLL_DEFAULT)
     return S0, S1
 
 
@@ -258,3 +263,43 @@ def test_grid_barrier_wait_times_out(ctx):
     x, rc, st = S.solve(_t(p.b[:, 0]), rtol=1e-8, mode=ssg.SSG_MIXED)
     assert rc == ssg.SSG_OK
     S.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3], ids=["fp64", "mixed", "fp64_jacobi", "mixed_jacobi"])
+def test_loop_unroll_same_bits(ctx, mode):
+    """Several copies of an iteration per pass of the loop graph (the later
+    copies of the last pass return at once) give the bits and counts of one
+    copy per pass; the launch counts grow by the copies that ran idle (exact
+    for the FP64 modes: u ceil(k / u) - k copies; whole copies, at most u - 1
+    per refinement, for the mixed ones)."""
+    import math
+
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    with pytest.raises(ssg.SSGError):
+        ctx.set_unroll(0)
+    with pytest.raises(ssg.SSGError):
+        ctx.set_unroll(9)
+    p = config_problem(2, scale=24)
+    b = _t(p.b[:, 0])
+    out = {}
+    for u in (1, 3, 4, 8):
+        ctx.set_unroll(u)
+        try:
+            S = System(ctx, p.A, p.part, p.P)
+        finally:
+            ctx.set_unroll(UNROLL_DEFAULT)
+        x, rc, st = S.solve(b, rtol=1e-8, mode=mode)
+        assert rc == ssg.SSG_OK
+        out[u] = (x.cpu().numpy(), st[0])
+        S.close()
+    x1, s1 = out[1]
+    for u, (x, st) in out.items():
+        assert np.array_equal(x, x1), u
+        assert (st["iters"], st["outer"]) == (s1["iters"], s1["outer"]), u
+        extra = st["kernel_launches"] - s1["kernel_launches"]
+        if mode in (ssg.SSG_FP64, ssg.SSG_FP64_JACOBI):
+            assert extra == 3 * (u * math.ceil(s1["iters"] / u) - s1["iters"]), u
+        else:
+            assert extra % 3 == 0 and 0 <= extra <= 3 * (u - 1) * s1["outer"], u
