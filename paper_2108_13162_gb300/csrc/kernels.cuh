@@ -989,7 +989,7 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t 
 // Inner Algorithm 3 lines 4, 7, 8 in FP32: every block sums the partials of
 // (r32, r32)_w, forms beta, and d32 <- d32 + alpha p32, p32 <- r32 + beta p32;
 // block 0 records the iteration and the inner stopping decision
-// (sqrt(rho) <= tau sqrt(rho0), or the inner iterations summed over
+// (sqrt((r, r)_w) <= tau sqrt(rho0), or the inner iterations summed over
 // refinements reach max_iter).
 // The block's part of it for iteration k, with alpha (FP32), the summed
 // inner iteration count and rho_k handed in by the caller.
@@ -1216,7 +1216,7 @@ __device__ __forceinline__ float fd_items(const DevOp &A, const X &xf, const flo
 // Iteration k of the FP32 inner CG (k = si->iter).  k = 0: q = S p_0 from the
 // stored p_0.  k >= 1: every block sums the residual kernel's partials of
 // (r_k, r_k)_w (and (r_k, z_k)_w), forms beta = rho_k / rho_{k-1} once, takes
-// the stopping decision of iteration k-1 (sqrt(rho) <= tau sqrt(rho0), or the
+// the stopping decision of iteration k-1 (sqrt((r, r)_w) <= tau sqrt(rho0), or the
 // summed inner iterations reach max_iter); on a stop it applies d += alpha
 // p_{k-1} alone (grid-stride) and raises halt[(k + 1) & 1], else it runs the
 // product on p_k as above.  Block 0 records rho, beta and the summed count.
