@@ -409,15 +409,18 @@ int ssg_system_destroy(ssg_system *sys);
 /*
  * Interface-weighted dot, (u, v)_w = sum_k w_k u_k v_k with w_k = 1/mult_loc[k],
  * for callers that cannot let a library allocate device memory (this call
- * has no counterpart in the paper).  Such callers: code running while a CUDA
- * graph is being captured, where cudaMalloc is not allowed; programs whose
- * own allocator owns the device memory under a fixed budget; loops that must
- * not take the implicit device synchronisation cudaMalloc/cudaFree can cause.
+ * has no counterpart in the paper).  Such callers: programs whose own
+ * allocator owns the device memory under a fixed budget, where an allocation
+ * made behind its back can fail or starve it; loops that must not take the
+ * implicit device synchronisation cudaMalloc/cudaFree can cause.
  *
  * No system is needed.  All arguments are device pointers owned by the
  * caller: u_loc, v_loc (nloc doubles), mult_loc (nloc bytes, the multiplicity
- * 1..255 of each local entry's node, i.e. mult[l2g[k]] from ssg_copy_maps),
- * result_dev (one double, written on the device).  Work goes to `stream`
+ * 1..255 of each local entry's node, i.e. mult[l2g[k]] from ssg_copy_maps;
+ * an entry with multiplicity 0 gets weight 0, as in the system path),
+ * result_dev (one double, written on the device).  The library cannot see
+ * the buffers' lengths: each must hold nloc elements (result_dev one) on the
+ * current device, or the kernel reads out of bounds.  Work goes to `stream`
  * (cudaStream_t or NULL) on the calling thread's current device.
  * Scratch: a 64 KB static __device__ array that every GPU loading this
  * library keeps until the process exits; nothing is allocated or freed.

@@ -1,9 +1,9 @@
 // Interface-weighted dot product that allocates no device memory.
 //
-// Some callers cannot let a library call cudaMalloc: code running while a
-// CUDA graph is being captured (allocation is not allowed there), programs
-// whose device memory is owned by their own caching allocator with a fixed
-// budget, and latency-critical loops that must not hit the implicit device
+// Some callers cannot let a library call cudaMalloc: programs whose device
+// memory is owned by their own caching allocator under a fixed budget (a
+// library allocation outside it can fail or push the program out of memory),
+// and latency-critical loops that must not take the implicit device
 // synchronisation cudaMalloc/cudaFree can cause.  ssg_wdot_noalloc serves
 // them: its only scratch (the per-block partial sums and the last-block
 // ticket) lives in one file-scope __device__ array that every GPU loading
@@ -60,7 +60,9 @@ __device__ __forceinline__ double na_block_sum(double v) {
 }
 
 // Same arithmetic as the weighted dot of the system path (w = 1/m, one FMA per
-// entry, fixed-order block and last-block sums), one chunk per block.
+// entry, fixed-order block and last-block sums), one chunk per block.  A
+// multiplicity of 0 (no node has it) gets weight 0, as in the system path's
+// weight table, so such an entry adds nothing instead of a non-finite value.
 __global__ void __launch_bounds__(kBlock) k_wdot_noalloc(int64_t n, const double *__restrict__ u,
                                                          const double *__restrict__ v,
                                                          const uint8_t *__restrict__ mult, NoAllocScratch *sc,
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(kBlock) k_wdot_noalloc(int64_t n, const double
         const int64_t i = base + j;
         if (i < n) {
             const unsigned int m = mult[i];
-            const double w = (m == 1u) ? 1.0 : 1.0 / static_cast<double>(m);
+            const double w = (m == 1u) ? 1.0 : (m == 0u ? 0.0 : 1.0 / static_cast<double>(m));
             acc = fma(w * u[i], v[i], acc);
         }
     }

@@ -509,15 +509,45 @@ def ssg_solve_host(sys, k, b_host, x_host, x_is_guess=False, rtol=1e-8, max_iter
     return rc, [st[i].as_dict() for i in range(k)]
 
 
-def ssg_wdot_noalloc(u_loc, v_loc, mult_loc, out, stream=None):
-    """Weighted dot with no device allocation in the library (see ssg.h)."""
+def noalloc_wdot_args(u_loc, v_loc, mult_loc, out):
+    """Checks the arguments of ssg_wdot_noalloc before anything reaches the
+    library, which cannot see buffer lengths or devices: u_loc, v_loc (float64)
+    and mult_loc (uint8) must be contiguous with one common length, out a
+    float64 tensor of at least one element, and all four on the current CUDA
+    device.  Raises TypeError (wrong kind of tensor) or ValueError (lengths,
+    layout, device); returns nloc."""
     import torch
 
-    if not (isinstance(mult_loc, torch.Tensor) and mult_loc.is_cuda and mult_loc.dtype == torch.uint8):
-        raise TypeError("mult_loc must be a uint8 CUDA tensor")
+    named = (("u_loc", u_loc, torch.float64), ("v_loc", v_loc, torch.float64),
+             ("mult_loc", mult_loc, torch.uint8), ("out", out, torch.float64))
+    for name, t, dt in named:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("%s must be a torch tensor" % name)
+        if t.dtype != dt:
+            raise TypeError("%s must have dtype %s, not %s" % (name, dt, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    n = u_loc.numel()
+    if v_loc.numel() != n or mult_loc.numel() != n:
+        raise ValueError("u_loc, v_loc and mult_loc must have the same length (%d, %d, %d)"
+                         % (n, v_loc.numel(), mult_loc.numel()))
+    if out.numel() < 1:
+        raise ValueError("out must hold at least one element")
+    for name, t, _ in named:
+        if not t.is_cuda:
+            raise TypeError("%s must be a CUDA tensor" % name)
+    dev = torch.cuda.current_device()
+    for name, t, _ in named:
+        if t.device.index != dev:
+            raise ValueError("%s is on cuda:%d, the current device is cuda:%d" % (name, t.device.index, dev))
+    return n
+
+
+def ssg_wdot_noalloc(u_loc, v_loc, mult_loc, out, stream=None):
+    """Weighted dot with no device allocation in the library (see ssg.h)."""
+    n = noalloc_wdot_args(u_loc, v_loc, mult_loc, out)
     return _check(
-        lib().ssg_wdot_noalloc(_dev_f64(u_loc), _dev_f64(v_loc), mult_loc.data_ptr(), u_loc.numel(),
-                               _dev_f64(out), stream),
+        lib().ssg_wdot_noalloc(u_loc.data_ptr(), v_loc.data_ptr(), mult_loc.data_ptr(), n, out.data_ptr(), stream),
         "ssg_wdot_noalloc",
     )
 

@@ -172,3 +172,31 @@ def test_element_input_rejected():
     ids2[ids2 == 3] = 4
     with pytest.raises(ssg.SSGError):
         ssg.ssg_partition_fe(None, A.n, ids2, Ke, epart, P)
+
+
+def test_noalloc_dot_arguments_refused_before_launch(monkeypatch):
+    """ssg_wdot_noalloc cannot see buffer lengths or devices, so the binding
+    refuses mismatched lengths, non-contiguous buffers, an empty output, wrong
+    dtypes and non-CUDA tensors itself; the library is never reached."""
+    import torch
+
+    def no_library():
+        raise AssertionError("the library was called with arguments the binding must refuse")
+
+    monkeypatch.setattr(ssg, "lib", no_library)
+    u = torch.zeros(100, dtype=torch.float64)
+    v = torch.zeros(100, dtype=torch.float64)
+    m = torch.ones(100, dtype=torch.uint8)
+    out = torch.zeros(1, dtype=torch.float64)
+    bad = [
+        ((u, v[:99], m, out), ValueError),                       # v shorter than u
+        ((u, v, m[:50], out), ValueError),                       # mult shorter than u
+        ((u, v, m, torch.zeros(0, dtype=torch.float64)), ValueError),  # no room for the result
+        ((u, torch.zeros(200, dtype=torch.float64)[::2], m, out), ValueError),  # strided v
+        ((u, v, m.to(torch.int32), out), TypeError),             # mult not bytes
+        ((u.float(), v, m, out), TypeError),                     # u not float64
+        ((u, v, m, out), TypeError),                             # consistent, but host tensors
+    ]
+    for args, exc in bad:
+        with pytest.raises(exc):
+            ssg.ssg_wdot_noalloc(*args)
