@@ -23,6 +23,7 @@ from .problems import (  # noqa: F401
     fe_assemble,
     fe_element_problem,
     random_spd,
+    pair_blocks,
     box_partition_2d,
     box_partition_3d,
     rcb_partition,

@@ -336,6 +336,23 @@ def random_spd(n: int, avg_deg: float, rng: np.random.Generator, shift: float = 
     return CSR(n, S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(np.float64))
 
 
+def pair_blocks(blocks, nrep: int) -> CSR:
+    """Block-diagonal SPD matrix of 2x2 blocks [[a, b], [b, a]] on the node
+    pairs (2j, 2j+1), block j taking ``blocks[j % len(blocks)]``, repeated
+    until there are len(blocks) * nrep blocks.  Its eigenvalues are the
+    a - b and a + b of the blocks, so the number of distinct eigenvalues is
+    known by construction, and a partition that splits pairs gives interface
+    nodes."""
+    nb = len(blocks) * nrep
+    ab = np.array([blocks[j % len(blocks)] for j in range(nb)], dtype=np.float64)
+    n = 2 * nb
+    rowptr = np.arange(0, 2 * n + 1, 2, dtype=np.int32)
+    first = 2 * np.arange(nb)
+    colidx = np.stack([first, first + 1, first, first + 1], axis=1).ravel().astype(np.int32)
+    val = np.stack([ab[:, 0], ab[:, 1], ab[:, 1], ab[:, 0]], axis=1).ravel()
+    return CSR(n, rowptr, colidx, val)
+
+
 def box_partition_2d(nx: int, ny: int, px: int, py: int) -> np.ndarray:
     """part = bx + px*by with bx = floor(ix*px/nx), by = floor(iy*py/ny)."""
     ix, iy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")

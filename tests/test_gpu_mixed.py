@@ -6,7 +6,10 @@ inner FP32 sums are ordered differently on each side):
   * converged, and the FP64 true residual ||b - S x|| / ||b|| recomputed on
     the CPU with the oracle's global product is <= rtol;
   * the refinement count equals the oracle's (+-1) and the summed inner
-    iterations are within max(3 per refinement, 10 %) of the oracle's;
+    iterations are within max(3 per refinement, 10 %) of the oracle's (an
+    empirical tolerance, see the exact-count cases below);
+  * on matrices with d distinct eigenvalues every inner solve takes exactly d
+    iterations (finite termination): counts equal the oracle's exactly;
   * the solution is within 2 kappa rtol of x* and of the oracle's solution
     (kappa from the Lanczos coefficients of the FP64 oracle run);
   * both drivers (graph, host loop) give the same bits; the parameters are
@@ -84,6 +87,37 @@ def test_mixed_matches_oracle(ctx, name, mk, rtol):
     kap = oracle.cond_from_lanczos(r64.alpha, r64.beta)
     assert _rel(xg, p.xstar[:, 0]) <= 2 * kap * rtol
     assert _rel(xg, rm.x) <= 2 * kap * rtol
+
+
+# 2x2 blocks [[a, b], [b, a]] with d distinct eigenvalues: CG's finite
+# termination fixes every inner solve at d iterations, so the counts of the
+# GPU and of the oracle must agree exactly, not within a tolerance
+COUNT_CASES = [
+    ("d4_kappa27", [(14.0, 13.0), (6.0, 3.0)], 4),
+    ("d3_kappa16", [(2.5, 1.5), (10.0, 6.0)], 3),
+    ("d2_kappa4", [(5.0, 3.0)], 2),
+]
+
+
+@pytest.mark.parametrize("name,blocks,d", COUNT_CASES, ids=[c[0] for c in COUNT_CASES])
+def test_mixed_counts_exact_on_finite_termination(ctx, name, blocks, d):
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+    from synth import pair_blocks
+
+    for seed in range(2):
+        rng = np.random.default_rng(seed)
+        A = pair_blocks(blocks, 25)
+        b = rng.uniform(-1, 1, A.n)
+        part = rng.integers(0, 5, A.n).astype(np.int32)
+        rm = oracle.Partition(A, part, 5).cg_mixed(b, 1e-8, 1000, 1e-4, 30)
+        S = System(ctx, A, part, 5)
+        x, rc, st = S.solve(_t(b), rtol=1e-8, max_iter=1000, mode=ssg.SSG_MIXED)
+        assert rc == ssg.SSG_OK
+        assert (st[0]["iters"], st[0]["outer"]) == (rm.iters, rm.outer) == (2 * d, 2)
+        tr = np.linalg.norm(b - oracle.spmv(A, x.cpu().numpy())) / np.linalg.norm(b)
+        assert tr <= 1e-8
+        S.close()
 
 
 def test_mixed_drivers_agree_and_deterministic(ctx):
