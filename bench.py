@@ -4,14 +4,19 @@
 Workload: 3D 7-point variable-coefficient diffusion on 128^3 cells
 (kappa = exp(g), g ~ N(0,1) per cell, harmonic-mean faces), 4x4x4 box split
 into 64 subdomains, b = A x* with x* ~ U[-1,1], seeded.  One step = one
-complete solve (Algorithm 3, M = I) from x = 0 to a recursive relative
-residual of 1e-8, with b already resident on the device.
+complete solve (Algorithm 3, M = I, in FP64 by default) from x = 0 to a
+recursive relative residual of 1e-8, with b already resident on the device.
 
 Prints one JSON line.  Besides the time per solve it reports the roofline of
 the dominant kernel (fused sub-structured SpMV + interface assembly) measured
 live with CUDA events, the end-to-end time through the host-buffer C ABI
-call, the SM clocks sampled during the timed region, and (rank 0, one GPU)
-the FP64 CPU oracle timed on a bounded sample of the same solve.
+call, the SM clocks sampled during the timed region, each solution's error
+against x* and against the oracle's stored FP64 solution, the other modes
+(mixed precision, diagonal preconditioner) with their own rooflines, the
+other workloads (64^2 Poisson, 96^3 with 16 right-hand sides and gradients,
+the 1024^2 finite-element mesh, the 512-system batch, the band splittings)
+and, on rank 0 with one GPU, the FP64 CPU oracle timed on complete solves
+of the same system on all host cores and on one.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -54,10 +59,12 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--spmv-reps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU time budget of the oracle sample")
-    ap.add_argument("--mode", choices=("mixed", "fp64"), default="mixed",
-                    help="mixed: FP32 inner CG inside FP64 iterative refinement; fp64: Algorithm 3 in FP64. "
-                         "Both stop on an FP64 relative residual of 1e-8; the other mode is timed too and reported")
+    ap.add_argument("--mode", choices=("fp64", "mixed", "jacobi", "mixed_jacobi"), default="fp64",
+                    help="the headline mode: fp64 = Algorithm 3 in FP64 (the paper's precision); mixed = FP32 "
+                         "inner CG inside FP64 iterative refinement; jacobi / mixed_jacobi = the same with the "
+                         "diagonal preconditioner.  All stop on an FP64 relative residual of 1e-8; every mode "
+                         "is timed and reported")
+    ap.add_argument("--no-p2d", action="store_true", help="skip the 64x64 Poisson system (solve to 1e-10)")
     ap.add_argument("--pdl", choices=("on", "off"), default="off",
                     help="programmatic dependent launch for the per-iteration update kernels")
     ap.add_argument("--unroll", type=int, default=4, help="CG iterations per pass of the loop graph's body")
@@ -80,9 +87,10 @@ def parse_args(argv=None):
                     help="only run the band product of the 128^3 matrix (64 bands) spmv-reps times (for ncu)")
     ap.add_argument("--no-fe", action="store_true",
                     help="skip the 1024^2 P1 finite-element workload (256 RCB subdomains, autotuned SpMV)")
-    ap.add_argument("--batch", choices=("off", "small", "full"), default="small",
-                    help="many independent systems in one launch, reported beside the headline: small = 512 "
-                         "systems of side 32..128, full = 512 of side 32..512 (several minutes of host setup)")
+    ap.add_argument("--batch", choices=("off", "small", "full"), default="full",
+                    help="many independent systems in one launch, reported beside the headline: full = 512 "
+                         "systems of side 32..512 (44.3 M unknowns); small = 512 of side 32..128, also solved "
+                         "one after another for comparison")
     ap.add_argument("--driver", choices=("graph", "host"), default="graph",
                     help="graph: one CUDA graph per solve (timed default); host: same kernels launched from a "
                          "host loop (for profilers that cannot see kernels inside conditional graphs)")
@@ -574,51 +582,173 @@ def profiled_traffic(prec="fp64"):
         return None
 
 
-def golden_iters():
-    """Iterations the oracle needs for this solve at rtol 1e-8 (stored)."""
+def golden_samples():
+    """The oracle's stored results for the 128^3 workload (written by
+    tests/golden/make_oracle_golden.py, which calls only the oracle): the
+    sample indices, its FP64 solutions there (to 1e-8 and 1e-12) and its
+    iteration counts per mode."""
+    import numpy as np
+
     try:
         with open(GOLDEN) as f:
-            for rec in json.load(f)["solves"]:
-                if rec["rtol"] == RTOL:
-                    return int(rec["iters"])
+            d = json.load(f)
+        out = {"idx": np.array(d["sample_idx"], dtype=np.int64), "oracle_iters": {}}
+        for rec in d["solves"]:
+            out["fp64_%g" % rec["rtol"]] = np.array(rec["sample_x"])
+            if rec["rtol"] == RTOL:
+                out["oracle_iters"]["fp64"] = int(rec["iters"])
+        for m in ("mixed", "jacobi", "mixed_jacobi"):
+            if m in d:
+                out["oracle_iters"][m] = int(d[m]["iters"])
+        return out
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def bench_p2d(ctx, stream, reps):
+    """Workload 1: the 64x64 5-point Poisson system on 2x2 subdomains, plain
+    FP64 CG to 1e-10.  The whole system (0.33 MB) sits in L2, so launch
+    latency, not HBM, bounds it: the figures are the time per solve and per
+    iteration, with the error against the oracle's stored solution."""
+    import numpy as np
+    import torch
+
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+    from synth import config_problem
+
+    rtol = 1e-10
+    p = config_problem(1)
+    S = System(ctx, p.A, p.part, p.P)
+    b = torch.from_numpy(p.b[:, 0].copy()).cuda()
+    x = torch.zeros_like(b)
+    for _ in range(3):
+        x.zero_()
+        ssg.ssg_solve(S.h, 1, b, x, False, rtol, 0, ssg.SSG_FP64)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        x.zero_()
+        rc, st = ssg.ssg_solve(S.h, 1, b, x, False, rtol, 0, ssg.SSG_FP64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if rc != ssg.SSG_OK:
+        raise RuntimeError("64x64 solve did not converge")
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    xh = x.cpu().numpy()
+    xs = p.xstar[:, 0]
+    out = {"workload": "poisson2d_5pt_64x64_2x2_subdomains", "n": p.A.n, "nnz": p.A.nnz, "rtol": rtol,
+           "mode": "fp64", "s": t, "iters": st[0]["iters"], "us_per_iter": t * 1e6 / max(st[0]["iters"], 1),
+           "true_relres": st[0]["true_relres"],
+           "err_vs_xstar": float(np.linalg.norm(xh - xs) / np.linalg.norm(xs)),
+           "l2": "L2-resident (0.33 MB): latency-bound, no HBM roofline"}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_p2d_64_2x2.json")) as f:
+            g = json.load(f)
+        xo = np.array(g["x"])
+        out["err_vs_oracle_fp64"] = float(np.linalg.norm(xh - xo) / np.linalg.norm(xo))
+        out["oracle_iters"] = int(g["iters"])
     except (OSError, KeyError, ValueError):
         pass
-    return None
+    S.close()
+    return out
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(prob, iters_full, seconds):
-    """Time the FP64 oracle's sub-structured CG on a bounded number of
-    iterations of the same solve; returns (seconds per full solve, sample text)."""
+def cpu_info():
+    """Host CPU: logical cores (nproc) and the model name lscpu prints (or
+    /proc/cpuinfo's, or the platform's)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    if not model:
+        import platform
+
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def oracle_solves(part, b, count, threads):
+    """Complete FP64 solves of the oracle's sub-structured CG to RTOL from
+    x = 0: threads 1 = the plain single-threaded oracle (or_sub_cg), else
+    the subdomains shared among that many OpenMP threads (or_sub_cg_omp,
+    0 = all).  Returns (seconds of each solve, last result)."""
+    import oracle
+
+    times = []
+    r = None
+    for _ in range(count):
+        t0 = time.perf_counter()
+        if threads == 1:
+            r = part.cg(b, RTOL, 100000)
+        else:
+            r = part.cg_omp(b, RTOL, 100000, threads)
+        times.append(time.perf_counter() - t0)
+        if r.status != oracle.OK:
+            raise RuntimeError("oracle solve did not converge (status %d)" % r.status)
+    return times, r
+
+
+def cpu_baseline_leg(prob):
+    """The oracle on the host cores, one complete solve each: on every
+    OpenMP thread (the baseline's value) and on one thread."""
     import oracle
 
     part = oracle.Partition(prob.A, prob.part, prob.P)
     b = prob.b[:, 0]
-    t0 = time.perf_counter()
-    part.cg(b, 0.0, 3)
-    t_probe = (time.perf_counter() - t0) / 3
-    m = int(max(5, min(iters_full, seconds / max(t_probe, 1e-6))))
-    t0 = time.perf_counter()
-    r = part.cg(b, 0.0, m)
-    dt = time.perf_counter() - t0
-    per_iter = dt / max(r.iters, 1)
-    sample = ("oracle sub-structured CG (plain C, FP64, one thread): first %d of %d iterations of the same "
-              "128^3 solve, %.1f s, scaled to %d iterations" % (r.iters, iters_full, dt, iters_full))
-    return per_iter * iters_full, sample, r.iters, dt
+    nt = oracle.omp_max_threads()
+    t_all, r_all = oracle_solves(part, b, 1, 0)
+    t_one, r_one = oracle_solves(part, b, 1, 1)
+    info = cpu_info()
+    return {
+        "value": t_all[0], "unit": UNIT, "cores": nt, "kind": "oracle",
+        "sample": "one complete FP64 solve of the same 128^3 system to 1e-8 (%d iterations) by the oracle's "
+                  "sub-structured CG with the 64 subdomains shared among %d OpenMP threads; one thread: %.2f s "
+                  "(%d iterations)" % (r_all.iters, nt, t_one[0], r_one.iters),
+        "iters": r_all.iters,
+        "single_thread_s": t_one[0],
+        "single_thread_iters": r_one.iters,
+        **info,
+    }
 
 
 def run_reference(args, dist):
+    """The reference arm: the paper gives no code, so the FP64 oracle's
+    sub-structured CG (plain C, the subdomains shared among all host cores)
+    solves the same 128^3 system from x = 0 to 1e-8, one complete solve per
+    step, warm-up steps untimed."""
     if dist.rank != 0:
         return 0
+    import numpy as np
+
+    import oracle
+
     prob = make_workload()
-    iters_full = golden_iters() or 1065
-    per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
-    vals = []
-    for i in range(args.warmup + args.steps):
-        v, sample, m, dt = oracle_sample(prob, iters_full, per_step)
-        if i >= args.warmup:
-            vals.append(v)
-    value = statistics.mean(vals)
+    part = oracle.Partition(prob.A, prob.part, prob.P)
+    b = prob.b[:, 0]
+    nt = oracle.omp_max_threads()
+    oracle_solves(part, b, max(args.warmup, 0), 0)
+    times, r = oracle_solves(part, b, args.steps, 0)
+    value = statistics.mean(times)
+    info = cpu_info()
+    tr = float(np.linalg.norm(b - oracle.spmv(prob.A, r.x)) / np.linalg.norm(b))
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -633,13 +763,22 @@ def run_reference(args, dist):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": prob.A.n, "nnz": prob.A.nnz, "rtol": RTOL, "mode": "fp64",
-                   "parallelism": "replicas"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": reference_config(prob, dist.world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                         "sample": "%d complete FP64 solves to 1e-8 (%d iterations each) by the oracle's "
+                                   "sub-structured CG, 64 subdomains shared among %d OpenMP threads, after %d "
+                                   "untimed" % (args.steps, r.iters, nt, args.warmup),
+                         "iters": r.iters, "true_relres": tr, "step_s": times, **info},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def reference_config(prob, world):
+    """The config keys both arms print, with the same values."""
+    return {"workload": WORKLOAD, "n": prob.A.n, "nnz": prob.A.nnz, "subdomains": prob.P, "rtol": RTOL,
+            "mode": "fp64", "parallelism": "replicas" if world > 1 else "single"}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -710,6 +849,8 @@ def run_ours(args, dist):
     x = torch.zeros_like(b)
     modes = {"fp64": ssg.SSG_FP64, "mixed": ssg.SSG_MIXED, "jacobi": ssg.SSG_FP64_JACOBI,
              "mixed_jacobi": ssg.SSG_MIXED_JACOBI}
+    gold = golden_samples()
+    xstar = prob.xstar[:, 0]
 
     def solve(mode):
         x.zero_()
@@ -737,28 +878,31 @@ def run_ours(args, dist):
         ck = clocks.stop() if clocks else None
         return dist.max(e0.elapsed_time(e1) / steps), sts, ck
 
-    other = "fp64" if args.mode == "mixed" else "mixed"
-    for _ in range(max(args.warmup, 0)):
-        solve(args.mode)
-    ms_step, sts, ck = timed(args.mode, args.steps, ClockSampler(_device_index(dev)))
-    launches = sum(s["kernel_launches"] for s in sts)
-    iters = [s["iters"] for s in sts]
-    st = sts[-1]
-    true_res = st["true_relres"]
-    # the other mode on the same system, same protocol (reported, not the value)
-    for _ in range(max(args.warmup, 0)):
-        solve(other)
-    ms_other, sts_other, _ = timed(other, args.steps)
+    def accuracy(xg):
+        """Relative error of the GPU solution against x* (exact) and against
+        the oracle's FP64 solutions to 1e-8 and 1e-12 at the stored samples."""
+        xh = xg.cpu().numpy()
+        out = {"err_vs_xstar": float(np.linalg.norm(xh - xstar) / np.linalg.norm(xstar))}
+        if gold:
+            idx = gold["idx"]
+            for key in ("1e-08", "1e-12"):
+                ref = gold["fp64_" + key]
+                out["err_vs_oracle_fp64_%s_sampled" % key] = float(np.linalg.norm(xh[idx] - ref)
+                                                                     / np.linalg.norm(ref))
+        return out
 
-    # Algorithm 3 with the paper's diagonal preconditioner, same protocol (reported)
-    for _ in range(max(args.warmup, 0)):
-        x.zero_()
-        ssg.ssg_solve(S.h, 1, b, x, False, RTOL, 0, ssg.SSG_FP64_JACOBI)
-    ms_jac, sts_jac, _ = timed("jacobi", args.steps)
-    for _ in range(max(args.warmup, 0)):
-        x.zero_()
-        ssg.ssg_solve(S.h, 1, b, x, False, RTOL, 0, ssg.SSG_MIXED_JACOBI)
-    ms_mjac, sts_mjac, _ = timed("mixed_jacobi", args.steps)
+    # the headline: plain FP64 (the paper's precision), then the other modes
+    # on the same system with the same protocol
+    results = {}
+    for mode in ([args.mode] + [m for m in modes if m != args.mode]):
+        for _ in range(max(args.warmup, 0)):
+            solve(mode)
+        ms, sts, ck = timed(mode, args.steps, ClockSampler(_device_index(dev)) if mode == args.mode else None)
+        iters = [t["iters"] for t in sts]
+        results[mode] = {"ms": ms, "sts": sts, "clocks": ck, "iters": int(statistics.median(iters)),
+                         "accuracy": accuracy(x)}
+    head = results[args.mode]
+    launches = sum(t["kernel_launches"] for t in head["sts"])
 
     # end to end through the host-buffer C ABI call (pinned host memory)
     bh = torch.from_numpy(prob.b[:, 0].copy()).pin_memory().numpy()
@@ -770,8 +914,8 @@ def run_ours(args, dist):
         rc, _ = ssg.ssg_solve_host(S.h, 1, bh, xh, False, RTOL, 0, modes[args.mode])
     e2e_s = dist.max((time.perf_counter() - t0) / args.steps)
 
-    # roofline of the dominant kernel: the fused SpMV + interface assembly,
-    # CUDA events on the launching stream, matrix larger than L2
+    # roofline of the dominant kernel of each mode: the fused SpMV + interface
+    # assembly, CUDA events on the launching stream, matrix larger than L2
     peak, peak_src = measured_peaks()
     roof = {}
     for prec in ("fp64", "fp32"):
@@ -791,7 +935,18 @@ def run_ours(args, dist):
             "algorithmic_bytes": nbytes,
             "launch_us": spmv_s * 1e6,
         }
-    dominant = "fp32" if args.mode == "mixed" else "fp64"
+    prec_of = {"fp64": "fp64", "jacobi": "fp64", "mixed": "fp32", "mixed_jacobi": "fp32"}
+
+    def mode_record(mode):
+        r = results[mode]
+        st = r["sts"][-1]
+        rec = {"s": r["ms"] / 1e3, "iters": r["iters"], "outer": st["outer"], "true_relres": st["true_relres"],
+               "us_per_iter": r["ms"] * 1e3 / max(r["iters"], 1), **r["accuracy"]}
+        if gold and mode in gold["oracle_iters"]:
+            rec["oracle_iters"] = gold["oracle_iters"][mode]
+        rec["roofline"] = roof[prec_of[mode]]
+        return rec
+
     multi = None
     if not args.no_multi_rhs:
         multi = bench_multi_rhs(ctx, stream, max(1, min(args.steps, 3)), args.spmv_reps)
@@ -801,17 +956,35 @@ def run_ours(args, dist):
     bands = None
     if not args.no_bands:
         bands = bench_bands(ctx, stream, prob, max(1, min(args.steps, 3)), args.spmv_reps)
+    p2d = None
+    if not args.no_p2d:
+        p2d = bench_p2d(ctx, stream, max(args.steps, 5))
     batch = None
     if args.batch != "off":
-        batch = bench_batch(ctx, stream, max(1, min(args.steps, 3)), args.batch)
+        batch = bench_batch(ctx, stream, 1 if args.batch == "full" else max(1, min(args.steps, 3)), args.batch)
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        v, sample, m, dt = oracle_sample(prob, golden_iters() or int(statistics.median(iters)), args.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = cpu_baseline_leg(prob)
 
+    ms_step = head["ms"]
     value = ms_step / 1e3
-    fp64_iters = iters if args.mode == "fp64" else [s["iters"] for s in sts_other]
+    cfg = reference_config(prob, dist.world)
+    cfg["mode"] = args.mode
+    cfg.update({
+        "nloc": S.sizes.nloc,
+        "interface_nodes": S.sizes.ngamma,
+        "iters": head["iters"],
+        "outer": head["sts"][-1]["outer"],
+        "true_relres": head["sts"][-1]["true_relres"],
+        "us_per_iter": ms_step * 1e3 / head["iters"],
+        **head["accuracy"],
+        "l2": "inputs larger than L2 (175 MB matrix + 5 x 18 MB vectors > 129 MB)",
+        "driver": args.driver,
+        "unroll": args.unroll,
+    })
+    if gold and args.mode in gold["oracle_iters"]:
+        cfg["oracle_iters"] = gold["oracle_iters"][args.mode]
     line = {
         "metric": METRIC,
         "value": value,
@@ -823,45 +996,16 @@ def run_ours(args, dist):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32+f64" if args.mode == "mixed" else "f64",
+        "dtype": "f64" if args.mode in ("fp64", "jacobi") else "f32+f64",
         "data": "synthetic",
-        "config": {
-            "workload": WORKLOAD,
-            "n": prob.A.n,
-            "nnz": prob.A.nnz,
-            "nloc": S.sizes.nloc,
-            "interface_nodes": S.sizes.ngamma,
-            "subdomains": prob.P,
-            "rtol": RTOL,
-            "mode": args.mode,
-            "iters": int(statistics.median(iters)),
-            "outer": st["outer"],
-            "true_relres": true_res,
-            "us_per_iter": ms_step * 1e3 / statistics.median(iters),
-            other + "_s": ms_other / 1e3,
-            other + "_iters": sts_other[-1]["iters"],
-            other + "_true_relres": sts_other[-1]["true_relres"],
-            "fp64_us_per_iter": (ms_step if args.mode == "fp64" else ms_other) * 1e3 / statistics.median(fp64_iters),
-            "jacobi_s": ms_jac / 1e3,
-            "jacobi_iters": sts_jac[-1]["iters"],
-            "jacobi_true_relres": sts_jac[-1]["true_relres"],
-            "mixed_jacobi_s": ms_mjac / 1e3,
-            "mixed_jacobi_iters": sts_mjac[-1]["iters"],
-            "mixed_jacobi_outer": sts_mjac[-1]["outer"],
-            "mixed_jacobi_true_relres": sts_mjac[-1]["true_relres"],
-            "l2": "inputs larger than L2 (175 MB matrix + 5 x 18 MB vectors > 129 MB)",
-            "parallelism": "replicas" if dist.world > 1 else "single",
-            "driver": args.driver,
-            "pdl": args.pdl,
-            "fuse": args.fuse,
-            "unroll": args.unroll,
-        },
-        "roofline": roof[dominant],
-        "roofline_other": roof["fp64" if dominant == "fp32" else "fp32"],
+        "config": cfg,
+        "roofline": roof[prec_of[args.mode]],
         "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * prob.A.n, "d2h_bytes_per_step": 8 * prob.A.n},
         "gpu_launches": int(dist.sum(launches)),
-        "clocks": ck,
+        "clocks": head["clocks"],
         "cpu_baseline": cpu,
+        "modes": {m: mode_record(m) for m in modes if m != args.mode},
+        "p2d64": p2d,
         "multi_rhs": multi,
         "batch": batch,
         "fe2d": fe,

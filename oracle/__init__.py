@@ -31,14 +31,21 @@ _i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
 
 
+_CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c99"]
+
+
 def build(force: bool = False) -> str:
-    """Compile ssg_oracle.c into _build/liboracle.so (gcc, no FMA contraction)."""
+    """Compile ssg_oracle.c into _build/liboracle.so (gcc, no FMA contraction),
+    with OpenMP for or_sub_cg_omp where the compiler has it (without it that
+    function runs on one thread with the same results)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(
-            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c99", "-o", tmp, _SRC, "-lm"]
-        )
+        try:
+            subprocess.check_call(["gcc"] + _CFLAGS + ["-fopenmp", "-o", tmp, _SRC, "-lm"],
+                                  stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(["gcc"] + _CFLAGS + ["-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -51,9 +58,7 @@ def compile_variant(src_text: str, tag: str) -> str:
     out = os.path.join(_BUILD, "libvariant_%s_%d.so" % (tag, os.getpid()))
     with open(src, "w") as f:
         f.write(src_text)
-    subprocess.check_call(
-        ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c99", "-o", out, src, "-lm"]
-    )
+    subprocess.check_call(["gcc"] + _CFLAGS + ["-o", out, src, "-lm"])
     return out
 
 
@@ -127,6 +132,11 @@ def _bind(L):
         L.or_sub_pcg_mixed.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int32, C.c_double, C.c_int32,
                                        C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)]
         L.or_sub_pcg_mixed.restype = C.c_int
+        L.or_sub_cg_omp.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int32, C.c_int32,
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+        L.or_sub_cg_omp.restype = C.c_int
+        L.or_omp_max_threads.argtypes = []
+        L.or_omp_max_threads.restype = C.c_int
         L.or_cholesky_solve.argtypes = [C.c_int32, _f64p, _f64p, _f64p]
         L.or_cholesky_solve.restype = C.c_int
         i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
@@ -292,6 +302,26 @@ class Partition:
         st = self._L.or_sub_cg(self.h, b, x, rtol, max_iter, C.byref(it), C.byref(rr), pa, pb, pr)
         k = it.value
         return CGResult(x, st, k, rr.value, ha[:k].copy(), hb[:k].copy(), hr[:k].copy())
+
+
+def omp_max_threads() -> int:
+    """Threads or_sub_cg_omp uses by default (1 when built without OpenMP)."""
+    return int(lib().or_omp_max_threads())
+
+
+def _cg_omp(self, b, rtol, max_iter, nthreads=0, x0=None) -> CGResult:
+    """Sub-structured CG with the subdomains shared among OpenMP threads
+    (ssg_oracle.c: or_sub_cg_omp); nthreads 0 = all."""
+    b = _c(b, np.float64).ravel()
+    x = np.zeros(self.maps.n) if x0 is None else _c(x0, np.float64).ravel().copy()
+    it = C.c_int32()
+    rr = C.c_double()
+    st = self._L.or_sub_cg_omp(self.h, b, x, rtol, max_iter, int(nthreads), C.byref(it), C.byref(rr))
+    e = np.zeros(0)
+    return CGResult(x, st, it.value, rr.value, e, e, e)
+
+
+Partition.cg_omp = _cg_omp
 
 
 @dataclass

@@ -28,6 +28,8 @@
  *                    Sections 2.1 and 2.2 (Algorithms 1 and 2), one band at a time.
  *   or_band_row_spmv, or_band_col_spmv  y = A x through either splitting: each
  *                    band's block of y, or the sum of the bands' partial products.
+ *   or_sub_cg_omp    or_sub_cg with the subdomains shared among OpenMP threads
+ *                    (the CPU baseline on all host cores).
  *
  * Readings where the paper is silent (no tolerance, no initial guess, no
  * weights, no rule for splitting an assembled S_33) are stated at each function.
@@ -1167,4 +1169,128 @@ int or_band_col_spmv(int32_t n, const int32_t *rowptr, const int32_t *colidx, co
     }
     free(yp);
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* The sub-structured CG with the subdomains shared among CPU threads. */
+/* ------------------------------------------------------------------ */
+/*
+ * Baseline timing on all host cores (TEST INFRASTRUCTURE like the rest of
+ * this file).  Section 3.4.2 gives each subdomain to its own process; here
+ * threads stand in for the processes:
+ *   - the local products run subdomain by subdomain in parallel, and the
+ *     interface sums node by node in parallel (a node writes only its own
+ *     copies), each entry computed exactly as in or_sub_spmv;
+ *   - the vector updates run entry by entry in parallel, as in or_sub_cg;
+ *   - every weighted dot is formed the way the paper's processes form it:
+ *     each subdomain sums its own entries in order, then the subdomain sums
+ *     are added in ascending s.
+ * So the result does not depend on the number of threads, and it differs
+ * from or_sub_cg only in how the dot sums are grouped (one running sum
+ * there); with one subdomain the two compute the same bits.  nthreads <= 0
+ * uses every thread OpenMP offers.  Built without OpenMP, it runs on one
+ * thread with the same results.
+ */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int or_omp_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static void sub_spmv_par(const or_part *h, const double *xl, double *yl, int nt) {
+#pragma omp parallel num_threads(nt)
+    {
+#pragma omp for schedule(dynamic, 1)
+        for (int32_t s = 0; s < h->P; ++s) {
+            const int32_t o = h->off[s];
+            for (int32_t li = 0; li < h->off[s + 1] - o; ++li) {
+                double acc = 0.0;
+                for (int32_t k = h->lrowptr[o + li]; k < h->lrowptr[o + li + 1]; ++k)
+                    acc += h->lval[k] * xl[o + h->lcol[k]];
+                yl[o + li] = acc;
+            }
+        }
+#pragma omp for schedule(static)
+        for (int32_t g = 0; g < h->ngamma; ++g) {
+            double S = 0.0;
+            for (int32_t c = h->iptr[g]; c < h->iptr[g + 1]; ++c) S += yl[h->icopy[c]];
+            for (int32_t c = h->iptr[g]; c < h->iptr[g + 1]; ++c) yl[h->icopy[c]] = S;
+        }
+    }
+}
+
+static double wdot_by_subdomain(const or_part *h, const double *u, const double *v, double *part, int nt) {
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int32_t s = 0; s < h->P; ++s) {
+        double acc = 0.0;
+        for (int64_t k = h->off[s]; k < h->off[s + 1]; ++k) acc += h->w[k] * u[k] * v[k];
+        part[s] = acc;
+    }
+    double t = 0.0;
+    for (int32_t s = 0; s < h->P; ++s) t += part[s];
+    return t;
+}
+
+int or_sub_cg_omp(const or_part *h, const double *b, double *x, double rtol, int32_t max_iter, int32_t nthreads,
+                  int32_t *iters_out, double *relres_out) {
+    const int nt = nthreads > 0 ? nthreads : or_omp_max_threads();
+    size_t N = (size_t)(h->nloc > 0 ? h->nloc : 1);
+    double *bl = (double *)malloc(sizeof(double) * N);
+    double *xl = (double *)malloc(sizeof(double) * N);
+    double *r = (double *)malloc(sizeof(double) * N);
+    double *p = (double *)malloc(sizeof(double) * N);
+    double *q = (double *)malloc(sizeof(double) * N);
+    double *part = (double *)malloc(sizeof(double) * (size_t)(h->P > 0 ? h->P : 1));
+    if (!bl || !xl || !r || !p || !q || !part) {
+        free(bl); free(xl); free(r); free(p); free(q); free(part);
+        return OR_OOM;
+    }
+    const int64_t L = h->nloc;
+    or_scatter(h, b, bl);
+    or_scatter(h, x, xl);
+    sub_spmv_par(h, xl, q, nt);
+#pragma omp parallel for schedule(static) num_threads(nt)
+    for (int64_t k = 0; k < L; ++k) {
+        r[k] = bl[k] - q[k];
+        p[k] = r[k];
+    }
+    double rho = wdot_by_subdomain(h, r, r, part, nt);
+    double bnorm = sqrt(wdot_by_subdomain(h, bl, bl, part, nt));
+    int status = OR_NOT_CONVERGED;
+    int32_t it = 0;
+    double relres = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;
+    if (sqrt(rho) <= rtol * bnorm) status = OR_OK;
+    while (status == OR_NOT_CONVERGED && it < max_iter) {
+        sub_spmv_par(h, p, q, nt);
+        double pq = wdot_by_subdomain(h, q, p, part, nt);
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            status = OR_BREAKDOWN;
+            break;
+        }
+        double alpha = rho / pq;
+#pragma omp parallel for schedule(static) num_threads(nt)
+        for (int64_t k = 0; k < L; ++k) {
+            xl[k] = xl[k] + alpha * p[k];
+            r[k] = r[k] - alpha * q[k];
+        }
+        double rho_new = wdot_by_subdomain(h, r, r, part, nt);
+        double beta = rho_new / rho;
+#pragma omp parallel for schedule(static) num_threads(nt)
+        for (int64_t k = 0; k < L; ++k) p[k] = r[k] + beta * p[k];
+        rho = rho_new;
+        ++it;
+        relres = bnorm > 0.0 ? sqrt(rho) / bnorm : 0.0;
+        if (sqrt(rho) <= rtol * bnorm) status = OR_OK;
+    }
+    or_gather(h, xl, x);
+    *iters_out = it;
+    *relres_out = relres;
+    free(bl); free(xl); free(r); free(p); free(q); free(part);
+    return status;
 }

@@ -7,11 +7,14 @@ mixed-precision refinement (FP32 inner CG, FP64 residuals) to 1e-8,
 Algorithm 3 with the diagonal preconditioner to 1e-8, and the refinement with
 diagonal-preconditioned inner solves to 1e-8.  Stored per solve: the
 iteration count, final residuals, the Lanczos condition estimate (M = I) and
-the solution at 4096 seeded sample indices.  Calls only oracle/ and synth/;
-takes about three minutes of one CPU core.
+the solution at 4096 seeded sample indices.  Also writes
+tests/golden/oracle_p2d_64_2x2.json: the 64x64 Poisson system on 2x2
+subdomains solved to 1e-10, with its whole solution.  Calls only oracle/ and
+synth/; takes about three minutes of one CPU core.
 
     python tests/golden/make_oracle_golden.py            # everything
     python tests/golden/make_oracle_golden.py jacobi     # one part, merged into the file
+    python tests/golden/make_oracle_golden.py p2d        # the 64x64 Poisson system (its own file)
 """
 
 import json
@@ -28,12 +31,38 @@ import oracle  # noqa: E402
 from synth import config_problem  # noqa: E402
 
 OUT = os.path.join(HERE, "oracle_fv3d_128_4x4x4.json")
+OUT_P2D = os.path.join(HERE, "oracle_p2d_64_2x2.json")
 
 
-ALL = ("cg", "mixed", "jacobi", "mixed_jacobi")
+ALL = ("cg", "mixed", "jacobi", "mixed_jacobi", "p2d")
+
+
+def p2d():
+    """The 64x64 5-point Poisson system on 2x2 subdomains (x* ~ U[-1,1],
+    b = A x*) solved by the oracle's sub-structured CG (M = I) to 1e-10:
+    iterations, residuals and the whole solution (4096 values)."""
+    p = config_problem(1)
+    part = oracle.Partition(p.A, p.part, p.P)
+    b = p.b[:, 0]
+    r = part.cg(b, 1e-10, 20000)
+    assert r.status == oracle.OK
+    rec = {
+        "workload": p.name, "n": p.A.n, "nnz": p.A.nnz, "rtol": 1e-10, "iters": r.iters, "relres": r.relres,
+        "true_relres": float(np.linalg.norm(b - oracle.spmv(p.A, r.x)) / np.linalg.norm(b)),
+        "err_vs_xstar": float(np.linalg.norm(r.x - p.xstar[:, 0]) / np.linalg.norm(p.xstar[:, 0])),
+        "x": [float(v) for v in r.x],
+    }
+    with open(OUT_P2D, "w") as f:
+        json.dump(rec, f)
+    print("p2d: %d iterations; wrote %s" % (r.iters, OUT_P2D))
 
 
 def main(parts=ALL):
+    if "p2d" in parts:
+        p2d()
+        parts = tuple(q for q in parts if q != "p2d")
+        if not parts:
+            return
     p = config_problem(2)
     part = oracle.Partition(p.A, p.part, p.P)
     b = p.b[:, 0]

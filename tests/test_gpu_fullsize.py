@@ -2,8 +2,9 @@
 system (which test_gpu_solve / test_gpu_mixed / test_gpu_jacobi cover):
 
   * P1 finite elements on the jittered 1024^2 mesh, 256 RCB subdomains;
-  * the batch of 512 independent 2D systems (sides 32..128, the benchmark's
-    default batch), 4-16 subdomains and 1-8 right-hand sides each;
+  * the batch of 512 independent 2D systems, 4-16 subdomains and 1-8
+    right-hand sides each: sides 32..128 (3.5 M unknowns) and the stated
+    workload, sides 32..512 (44.3 M unknowns, the benchmark's default batch);
   * the 96^3 system with 16 right-hand sides iterating together.
 
 Element by element where the oracle finishes in seconds: the assembled
@@ -90,11 +91,14 @@ def test_fe_full_size_1024(ctx):
     S.close()
 
 
-def test_batch_full_size_512(ctx):
+@pytest.mark.parametrize("side_hi", [128, 512], ids=["side32-128", "side32-512"])
+def test_batch_full_size_512(ctx, side_hi):
+    """512 systems in one launch: sides 32..128 (3.5 M unknowns) and the
+    stated workload, sides 32..512 (44.3 M unknowns, 2322 right-hand sides)."""
     from paper_2108_13162_gb300 import ssg
     from paper_2108_13162_gb300.ssg import Batch
 
-    bp = batch_problem(512, 32, 128)
+    bp = batch_problem(512, 32, side_hi)
     B = Batch(ctx, [(A, pt, P, b.shape[0]) for A, pt, P, b in zip(bp.A, bp.part, bp.P, bp.b)])
     bb = _t(np.concatenate([b.ravel() for b in bp.b]))
 
