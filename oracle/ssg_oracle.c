@@ -1212,7 +1212,7 @@ static void sub_spmv_par(const or_part *h, const double *xl, double *yl, int nt)
             for (int32_t li = 0; li < h->off[s + 1] - o; ++li) {
                 double acc = 0.0;
                 for (int32_t k = h->lrowptr[o + li]; k < h->lrowptr[o + li + 1]; ++k)
-                    acc += h->lval[k] * xl[o + h->lcol[k]];
+                    acc = acc + h->lval[k] * xl[h->lcol[k] + o];
                 yl[o + li] = acc;
             }
         }
