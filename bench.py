@@ -65,12 +65,7 @@ def parse_args(argv=None):
                          "diagonal preconditioner.  All stop on an FP64 relative residual of 1e-8; every mode "
                          "is timed and reported")
     ap.add_argument("--no-p2d", action="store_true", help="skip the 64x64 Poisson system (solve to 1e-10)")
-    ap.add_argument("--pdl", choices=("on", "off"), default="off",
-                    help="programmatic dependent launch for the per-iteration update kernels")
     ap.add_argument("--unroll", type=int, default=4, help="CG iterations per pass of the loop graph's body")
-    ap.add_argument("--fuse", choices=("none", "grid", "spmv"), default="none",
-                    help="kernel split of the FP32 inner iteration: three kernels; the two updates as one "
-                         "cooperative kernel (grid barrier); the direction update folded into the next product")
     ap.add_argument("--profile-spmm", choices=("fp64", "fp32"), default=None,
                     help="only build the 96^3 16-right-hand-side workload and launch the 16-vector product "
                          "--spmv-reps times (for ncu); no JSON line")
@@ -841,9 +836,7 @@ def run_ours(args, dist):
         return 0
     if args.driver == "host":
         ctx.set_driver(ssg.SSG_DRIVER_HOST)
-    ctx.set_pdl(args.pdl == "on")
     ctx.set_unroll(args.unroll)
-    ctx.set_fused({"none": ssg.SSG_FUSE_NONE, "grid": ssg.SSG_FUSE_GRID, "spmv": ssg.SSG_FUSE_SPMV}[args.fuse])
     S = System(ctx, prob.A, prob.part, prob.P)
     b = torch.from_numpy(prob.b[:, 0].copy()).to("cuda:%d" % dev)
     x = torch.zeros_like(b)

@@ -95,37 +95,6 @@ int ssg_create(ssg_ctx **ctx, int device, void *stream);
 int ssg_set_stream(ssg_ctx *ctx, void *stream);
 /* Pick how ssg_solve drives the iteration (SSG_DRIVER_*); default GRAPH. */
 int ssg_set_driver(ssg_ctx *ctx, int driver);
-/* Launch the residual and direction updates of each iteration with
- * programmatic dependent launch (their launch overlaps the previous kernel's
- * tail; results are unchanged).  enable != 0: on; default off (measured on
- * GB300: no gain in SSG_MIXED, 13 us per iteration lost in SSG_FP64).
- * Applies to systems partitioned on this context afterwards. */
-int ssg_set_pdl(ssg_ctx *ctx, int enable);
-/* How the FP32 inner iteration of SSG_MIXED / SSG_MIXED_JACOBI (Algorithm 3
- * inside iterative refinement) is split into kernels.  Every form runs the
- * same operations in the same order on the same work partition: results are
- * bit-identical whichever is chosen.
- *   SSG_FUSE_NONE  three kernels: product (line 2, with (p, S p)_w), residual
- *                  update (lines 3, 5), direction update (lines 4, 7, 8).
- *   SSG_FUSE_GRID  product, then the two updates as one cooperative kernel
- *                  with a grid barrier between them.  Measured on GB300 (128^3
- *                  system): 44.5 us per inner iteration against 41.2 us for
- *                  three kernels.  A device or driver that cannot co-schedule
- *                  the grid or capture a cooperative kernel inside the loop
- *                  graph gets three kernels; a barrier that does not complete
- *                  within about a second ends the solve with SSG_E_TIMEOUT.
- *   SSG_FUSE_SPMV  the direction update of iteration k-1 folded into the
- *                  product of iteration k (it forms p_k where it gathers, from
- *                  p_{k-1} and z_k, and stores p_k and d at the rows it owns;
- *                  p alternates between two buffers), then the residual
- *                  update: two kernels per inner iteration and one more
- *                  product launch per refinement, which only completes d.
- * Default SSG_FUSE_NONE.  Applies to systems partitioned on this context
- * afterwards. */
-#define SSG_FUSE_NONE 0
-#define SSG_FUSE_GRID 1
-#define SSG_FUSE_SPMV 2
-int ssg_set_fused(ssg_ctx *ctx, int mode);
 /* CG iterations per pass of the body of a single-vector solve's loop graph
  * (1..8, default 4): the body holds that many copies of one iteration's
  * kernels; once the loop has stopped, the later copies of the last pass
@@ -135,12 +104,6 @@ int ssg_set_fused(ssg_ctx *ctx, int mode);
  * iteration and 73.0 us per FP64 iteration, against 41.5 and 74.7 with one.
  * Applies to systems partitioned on this context afterwards. */
 int ssg_set_unroll(ssg_ctx *ctx, int32_t iters);
-/* Runs the fused update's grid barrier once in a two-block cooperative
- * launch in which one block never arrives: the other's wait gives up after
- * about a second and the call returns SSG_E_TIMEOUT (SSG_OK would mean the
- * barrier completed, i.e. the failure path did not work).  The context stays
- * usable.  A test of failure detection without a GPU fault. */
-int ssg_check_barrier_timeout(ssg_ctx *ctx);
 /*
  * Parameters of SSG_MIXED solves on this context (not a method of the paper;
  * its experiments are FP64 only): the inner FP32 CG stops when its residual

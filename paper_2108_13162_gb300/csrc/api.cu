@@ -54,12 +54,7 @@ struct ssg_system {
     int diag_state = -1;        // host copy of *d_diag_bad: -1 not read since the values changed
     Scal *d_scal_op = nullptr;  // state for the stand-alone SpMV / dot calls
     double *d_xg = nullptr, *d_bg = nullptr;  // global staging for ssg_solve_host
-    bool pdl = false;  // loop-body kernels use programmatic dependent launch
-    bool fuse = false;  // FP32 inner updates as one cooperative launch (k_update_rdp32)
-    bool fdir = false;  // FP32 direction update folded into the next product (k_spmv_fd)
     int unroll = 4;     // iterations per pass of the single-vector loop bodies
-    float *d_p32b = nullptr;  // the second direction buffer of the folded form
-    unsigned long long *d_gbar = nullptr;  // its grid barrier's arrival counter, zeroed before each solve
     int grid_spmv = 0;
     int grid_spmv32 = 0;
     int grid_bps[6] = {0, 0, 0, 0, 0, 0};           // single-vector grids for 3, 4, 5 blocks per SM
@@ -126,37 +121,17 @@ namespace {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Launch with or without programmatic stream serialization (the kernel may
-// begin while its predecessor finishes; it waits in pdl_enter()).
+// Launch through a kernel pointer (one instance chosen at run time), with
+// the arguments converted to the kernel's parameter types.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+cudaError_t launch_k(void (*kern)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = pdl ? attr : nullptr;
-    cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
-// Cooperative launch: every block of the grid is resident at once (the
-// kernel holds a grid barrier).
-template <typename... KArgs, typename... Args>
-cudaError_t launch_coop(void (*kern)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
@@ -181,17 +156,6 @@ const SpmvVariant<float> kSpmv32Variants[kSpmvVariants] = {
     {5, 0, k_spmv_asm<kEpiPartials, float, 5, 0>, k_spmv_asm<kEpiStore, float, 5, 0>},
     {4, 1, k_spmv_asm<kEpiPartials, float, 4, 1>, k_spmv_asm<kEpiStore, float, 4, 1>},
     {4, 2, k_spmv_asm<kEpiPartials, float, 4, 2>, k_spmv_asm<kEpiStore, float, 4, 2>},
-};
-
-// The folded-direction FP32 product (SSG_FUSE_SPMV) for each entry of
-// kSpmv32Variants (same blocks per SM and L2 prefetch distance), without and
-// with the diagonal preconditioner.
-using SpmvFdFn = void (*)(DevOp, int64_t, const float *, const float *, float *, float *, float *, float *,
-                          double *, const double *, const double *, int, Scal *, Scal *,
-                          cudaGraphConditionalHandle, int);
-const SpmvFdFn kSpmvFdVariants[2][kSpmvVariants] = {
-    {k_spmv_fd<false, 5, 1>, k_spmv_fd<false, 5, 0>, k_spmv_fd<false, 4, 1>, k_spmv_fd<false, 4, 2>},
-    {k_spmv_fd<true, 5, 1>, k_spmv_fd<true, 5, 0>, k_spmv_fd<true, 4, 1>, k_spmv_fd<true, 4, 2>},
 };
 
 // SpMV work list (see WorkItem in kernels.cuh) and the sliced-ELL copy of
@@ -429,12 +393,12 @@ double *part_rz(ssg_system *S) { return S->d_partials + 2 * (S->n_partials / 3);
 int launch_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const int64_t N = S->maps.nloc;
     const cudaGraphConditionalHandle h = pc ? S->cond_pc : S->cond;
-    SSG_CUDA_TRY(launch_k(false, kSpmv64Variants[S->var64].part, S->grid_spmv, kSpmvThreads, st, S->op, S->d_p,
+    SSG_CUDA_TRY(launch_k(kSpmv64Variants[S->var64].part, S->grid_spmv, kSpmvThreads, st, S->op, S->d_p,
                           S->d_q, part_pq(S), S->d_scal, (double *)nullptr, h, use_cond));
-    SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_r<true> : k_update_r<false>, S->grid_vec, kBlock, st, N, S->d_r,
+    SSG_CUDA_TRY(launch_k(pc ? k_update_r<true> : k_update_r<false>, S->grid_vec, kBlock, st, N, S->d_r,
                           S->d_q, S->op.mult, S->op.wtab, S->op.gflag, (const double *)part_pq(S), S->grid_spmv,
                           part_rr(S), S->d_scal, h, use_cond, (const double *)S->d_dinv, part_rz(S)));
-    SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_xp<true> : k_update_xp<false>, S->grid_vec, kBlock, st, N, S->d_xl,
+    SSG_CUDA_TRY(launch_k(pc ? k_update_xp<true> : k_update_xp<false>, S->grid_vec, kBlock, st, N, S->d_xl,
                           S->d_p, S->d_r, (const double *)part_rr(S), S->grid_vec, S->d_scal, h, use_cond,
                           (const double *)S->d_dinv, (const double *)part_rz(S)));
     return SSG_OK;
@@ -453,7 +417,6 @@ int launch_init(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
 }
 
 int launch_mixed_init(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
-    SSG_CUDA_TRY(cudaMemsetAsync(S->d_gbar, 0, sizeof(unsigned long long) * kGridBarWords, st));
     k_cg_init<false><<<S->grid_vec, kBlock, 0, st>>>(S->maps.nloc, S->d_bl, S->d_q, S->d_r, nullptr, S->op.mult,
                                                      S->op.wtab, S->d_partials, S->d_scal, S->cond_out[pc], use_cond,
                                                      nullptr);
@@ -473,33 +436,13 @@ int launch_inner_init(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
 int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const int64_t N = S->maps.nloc;
     const cudaGraphConditionalHandle h = S->cond_in[pc];
-    if (S->fdir) {
-        auto fd = kSpmvFdVariants[pc][S->var32];
-        fd<<<S->grid_spmv32, kSpmvThreads, 0, st>>>(S->op32, N, S->d_r32, S->d_dinv32, S->d_p32, S->d_p32b, S->d_d32,
-                                                    S->d_q32, part_pq(S), part_rr(S), part_rz(S), S->grid_vec,
-                                                    S->d_scal_in, S->d_scal, h, use_cond);
-        SSG_CUDA_TRY(cudaGetLastError());
-        SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_r32<true, true> : k_update_r32<false, true>, S->grid_vec, kBlock,
-                              st, N, S->d_r32, S->d_q32, S->op.mult, S->op.wtab32, S->op.gflag128,
-                              (const double *)part_pq(S), S->grid_spmv32, part_rr(S), S->d_scal_in,
-                              S->d_scal, h, use_cond, (const float *)S->d_dinv32, part_rz(S)));
-        return SSG_OK;
-    }
-    SSG_CUDA_TRY(launch_k(false, kSpmv32Variants[S->var32].part, S->grid_spmv32, kSpmvThreads, st, S->op32,
+    SSG_CUDA_TRY(launch_k(kSpmv32Variants[S->var32].part, S->grid_spmv32, kSpmvThreads, st, S->op32,
                           S->d_p32, S->d_q32, part_pq(S), S->d_scal_in, (double *)nullptr, h, use_cond));
-    if (S->fuse) {
-        SSG_CUDA_TRY(launch_coop(pc ? k_update_rdp32<true> : k_update_rdp32<false>, S->grid_vec, kBlock, st, N,
-                                 S->d_r32, (const float *)S->d_q32, S->d_d32, S->d_p32, S->op.mult, S->op.wtab32,
-                                 S->op.gflag128, (const double *)part_pq(S), S->grid_spmv32, part_rr(S),
-                                 S->d_scal_in, S->d_scal, h, use_cond, (const float *)S->d_dinv32, part_rz(S),
-                                 S->d_gbar));
-        return SSG_OK;
-    }
-    SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_r32<true> : k_update_r32<false>, S->grid_vec, kBlock, st, N,
+    SSG_CUDA_TRY(launch_k(pc ? k_update_r32<true> : k_update_r32<false>, S->grid_vec, kBlock, st, N,
                           S->d_r32, S->d_q32, S->op.mult, S->op.wtab32, S->op.gflag128, (const double *)part_pq(S),
                           S->grid_spmv32, part_rr(S), S->d_scal_in, S->d_scal, h, use_cond,
                           (const float *)S->d_dinv32, part_rz(S)));
-    SSG_CUDA_TRY(launch_k(S->pdl, pc ? k_update_dp32<true> : k_update_dp32<false>, S->grid_vec, kBlock, st, N,
+    SSG_CUDA_TRY(launch_k(pc ? k_update_dp32<true> : k_update_dp32<false>, S->grid_vec, kBlock, st, N,
                           S->d_d32, S->d_p32, S->d_r32, (const double *)part_rr(S), S->grid_vec, S->d_scal_in,
                           S->d_scal, h, use_cond, (const float *)S->d_dinv32, (const double *)part_rz(S)));
     return SSG_OK;
@@ -559,22 +502,9 @@ cudaError_t add_while(cudaGraph_t g, const cudaGraphNode_t *dep, cudaGraphCondit
     return e;
 }
 
-int build_graph_once(ssg_system *S, bool pc);
-
-// Build the FP64 graph (with or without the diagonal preconditioner); if the
-// driver refuses programmatic edges inside the conditional body, rebuild it
-// with plain launches.
+// Build the FP64 graph (with or without the diagonal preconditioner).
 int build_graph(ssg_system *S, bool pc) {
     if (pc ? S->exec_pc : S->exec) return SSG_OK;
-    int rc = build_graph_once(S, pc);
-    if (rc != SSG_OK && S->pdl) {
-        S->pdl = false;
-        rc = build_graph_once(S, pc);
-    }
-    return rc;
-}
-
-int build_graph_once(ssg_system *S, bool pc) {
     cudaGraph_t &graph = pc ? S->graph_pc : S->graph;
     cudaGraphExec_t &exec = pc ? S->exec_pc : S->exec;
     cudaGraphConditionalHandle &cond = pc ? S->cond_pc : S->cond;
@@ -610,23 +540,8 @@ int build_graph_once(ssg_system *S, bool pc) {
 
 // SSG_MIXED graph: init -> WHILE(outer) { inner_init -> WHILE(inner) { FP32
 // SpMV, r update, d/p update } -> x += d -> FP64 SpMV -> residual + test }.
-int build_graph_mixed_once(ssg_system *S, bool pc);
-
 int build_graph_mixed(ssg_system *S, bool pc) {
     if (S->exec_m[pc]) return SSG_OK;
-    int rc = build_graph_mixed_once(S, pc);
-    if (rc != SSG_OK && S->fuse) {  // no cooperative kernel inside the loop body: two launches
-        S->fuse = false;
-        rc = build_graph_mixed_once(S, pc);
-    }
-    if (rc != SSG_OK && S->pdl) {
-        S->pdl = false;
-        rc = build_graph_mixed_once(S, pc);
-    }
-    return rc;
-}
-
-int build_graph_mixed_once(ssg_system *S, bool pc) {
     cudaGraph_t &gm = S->graph_m[pc];
     SSG_CUDA_TRY(cudaGraphCreate(&gm, 0));
     SSG_CUDA_TRY(cudaGraphConditionalHandleCreate(&S->cond_out[pc], gm, 0u, cudaGraphCondAssignDefault));
@@ -713,14 +628,6 @@ int upload(ssg_system *S) {
     S->grid_spmv32 = plan.grid_bps[kSpmv32Variants[0].bps];
     S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N / 2 + kBlock - 1) / kBlock), C->num_sms * kVecBlocksPerSM));
     S->n_partials = 3 * std::max(std::max(plan.grid_bps[3], std::max(plan.grid_bps[4], plan.grid_bps[5])), S->grid_vec);
-    if (S->fuse) {
-        // the fused FP32 update needs its whole grid resident at once
-        int coop = 0, nb0 = 0, nb1 = 0;
-        SSG_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, C->device));
-        SSG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, k_update_rdp32<false>, kBlock, 0));
-        SSG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb1, k_update_rdp32<true>, kBlock, 0));
-        S->fuse = coop != 0 && static_cast<int64_t>(std::min(nb0, nb1)) * C->num_sms >= S->grid_vec;
-    }
 
     struct Piece {
         const void *src;
@@ -779,7 +686,6 @@ int upload(ssg_system *S) {
     size_t i_ival32 = add(ival32.data(), sizeof(float) * ival32.size());
     size_t i_r32 = add(nullptr, sizeof(float) * N);
     size_t i_p32 = add(nullptr, sizeof(float) * N);
-    size_t i_p32b = add(nullptr, sizeof(float) * N);
     size_t i_q32 = add(nullptr, sizeof(float) * N);
     size_t i_d32 = add(nullptr, sizeof(float) * N);
     size_t i_scal_in = add(nullptr, sizeof(Scal));
@@ -830,7 +736,6 @@ int upload(ssg_system *S) {
     size_t i_part = add(nullptr, sizeof(double) * S->n_partials);
     size_t i_scal = add(nullptr, sizeof(Scal));
     size_t i_scal2 = add(nullptr, sizeof(Scal));
-    size_t i_gbar = add(nullptr, sizeof(unsigned long long) * kGridBarWords);
     size_t i_xg = add(nullptr, sizeof(double) * M.n);
     size_t i_bg = add(nullptr, sizeof(double) * M.n);
 
@@ -852,11 +757,9 @@ int upload(ssg_system *S) {
     S->op.ival32 = static_cast<const float *>(at(i_ival32));
     S->d_r32 = static_cast<float *>(at(i_r32));
     S->d_p32 = static_cast<float *>(at(i_p32));
-    S->d_p32b = static_cast<float *>(at(i_p32b));
     S->d_q32 = static_cast<float *>(at(i_q32));
     S->d_d32 = static_cast<float *>(at(i_d32));
     S->d_scal_in = static_cast<Scal *>(at(i_scal_in));
-    S->d_gbar = static_cast<unsigned long long *>(at(i_gbar));
     S->d_dmap = static_cast<int32_t *>(at(i_dmap));
     S->d_dinv = static_cast<double *>(at(i_dinv));
     S->d_dinv32 = static_cast<float *>(at(i_dinv32));
@@ -986,7 +889,7 @@ int run_host_mixed(ssg_system *S, int64_t *launches, bool pc) {
                 rc = launch_inner_body(S, s, 0, pc);
                 if (rc != SSG_OK) return rc;
             }
-            *launches += (S->fuse || S->fdir ? 2 : 3) * kHostChunk;
+            *launches += 3 * kHostChunk;
         }
         rc = launch_outer_tail(S, s, 0, pc);
         if (rc != SSG_OK) return rc;
@@ -1067,8 +970,8 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     if (C->driver == SSG_DRIVER_GRAPH) {
         // every copy of an iteration in a loop pass launches all its kernels;
         // the device counts the residual-update launches (h.passes)
-        if (mixed)  // init, per refinement: inner init + 3 tail kernels; 3 per inner copy (fused forms: 2)
-            launches += 1 + 4 * static_cast<int64_t>(h.iter) + (S->fuse || S->fdir ? 2 : 3) * int64_t(h.passes);
+        if (mixed)  // init, per refinement: inner init + 3 tail kernels; 3 per inner copy
+            launches += 1 + 4 * static_cast<int64_t>(h.iter) + 3 * int64_t(h.passes);
         else  // init, 3 per copy
             launches += 1 + 3 * static_cast<int64_t>(h.passes);
     }
@@ -1659,55 +1562,12 @@ int ssg_set_driver(ssg_ctx *ctx, int driver) {
     return SSG_OK;
 }
 
-int ssg_set_pdl(ssg_ctx *ctx, int enable) {
-    if (!ctx) {
-        set_error("null context");
-        return SSG_E_INVALID;
-    }
-    ctx->pdl = enable ? 1 : 0;
-    return SSG_OK;
-}
-
-int ssg_set_fused(ssg_ctx *ctx, int mode) {
-    if (!ctx || (mode != SSG_FUSE_NONE && mode != SSG_FUSE_GRID && mode != SSG_FUSE_SPMV)) {
-        set_error("ssg_set_fused: null context, or mode not SSG_FUSE_NONE / SSG_FUSE_GRID / SSG_FUSE_SPMV");
-        return SSG_E_INVALID;
-    }
-    ctx->fuse = mode;
-    return SSG_OK;
-}
-
 int ssg_set_unroll(ssg_ctx *ctx, int32_t iters) {
     if (!ctx || iters < 1 || iters > 8) {
         set_error("ssg_set_unroll: null context, or iterations per loop pass not in 1..8");
         return SSG_E_INVALID;
     }
     ctx->unroll = iters;
-    return SSG_OK;
-}
-
-int ssg_check_barrier_timeout(ssg_ctx *ctx) {
-    if (!ctx) {
-        set_error("null context");
-        return SSG_E_INVALID;
-    }
-    SSG_CUDA_TRY(cudaSetDevice(ctx->device));
-    SSG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    unsigned long long *buf = nullptr;  // barrier words, result
-    const size_t words = kGridBarWords + 1;
-    SSG_CUDA_TRY(cudaMalloc(&buf, words * sizeof(unsigned long long)));
-    unsigned long long res = 0;
-    cudaError_t e = cudaMemsetAsync(buf, 0, words * sizeof(unsigned long long), ctx->stream);
-    if (e == cudaSuccess) e = launch_coop(k_grid_barrier_probe, 2, kBlock, ctx->stream, buf, buf + kGridBarWords);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpy(&res, buf + kGridBarWords, sizeof(res), cudaMemcpyDeviceToHost);
-    cudaFree(buf);
-    if (e != cudaSuccess) {
-        set_error(std::string("grid barrier probe: ") + cudaGetErrorString(e));
-        return SSG_E_CUDA;
-    }
-    if (res == 1) return SSG_E_TIMEOUT;
-    set_error("grid barrier probe: the wait did not run out");
     return SSG_OK;
 }
 
@@ -1759,9 +1619,6 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
     S->ctx = ctx;
     if (ctx) {
         ctx->live_systems++;
-        S->pdl = ctx->pdl != 0;
-        S->fuse = ctx->fuse == SSG_FUSE_GRID;
-        S->fdir = ctx->fuse == SSG_FUSE_SPMV;
         S->unroll = ctx->unroll;
         rc = upload(S);
         if (rc != SSG_OK) {
@@ -1792,9 +1649,6 @@ int ssg_partition_fe(ssg_ctx *ctx, int32_t n, int32_t ne, int32_t nv, const int3
     S->ctx = ctx;
     if (ctx) {
         ctx->live_systems++;
-        S->pdl = ctx->pdl != 0;
-        S->fuse = ctx->fuse == SSG_FUSE_GRID;
-        S->fdir = ctx->fuse == SSG_FUSE_SPMV;
         S->unroll = ctx->unroll;
         rc = upload(S);
         if (rc != SSG_OK) {
@@ -1837,9 +1691,6 @@ int make_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off, const in
     }
     S->ctx = ctx;
     ctx->live_systems++;
-    S->pdl = ctx->pdl != 0;
-    S->fuse = ctx->fuse == SSG_FUSE_GRID;
-    S->fdir = ctx->fuse == SSG_FUSE_SPMV;
     S->unroll = ctx->unroll;
     rc = upload(S);
     if (rc != SSG_OK) {

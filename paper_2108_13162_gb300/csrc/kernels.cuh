@@ -200,15 +200,6 @@ __device__ __forceinline__ double sum_partials(const double *partials, int G) {
     return block_sum<NT>(v);
 }
 
-// Programmatic dependent launch: wait until the preceding kernel in the
-// stream has completed and its writes are visible (a no-op when this kernel
-// was launched without the attribute), then let the next kernel start its
-// launch so its scheduling overlaps this kernel's tail.
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // Every block sums the previous kernel's block partials in the same fixed
 // order (the partials are complete and visible at the kernel boundary), so
 // all blocks hold the bitwise same total without a ticket or a last block.
@@ -394,7 +385,6 @@ template <int EPI, typename T, int BPS = SpmvTraits<T>::kBlocksPerSM, int AHEAD 
 __global__ void __launch_bounds__(kSpmvThreads, BPS)
     k_spmv_asm(DevOp A, const T *__restrict__ x, T *__restrict__ y, double *partials, Scal *s, double *out,
                cudaGraphConditionalHandle h, int use_cond) {
-    pdl_enter();
     if (EPI == kEpiPartials && (s->brk || s->halt[s->iter & 1])) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 range = A.warp_range[blockIdx.x * kSpmvWarps + warp];
@@ -493,7 +483,6 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r(int64_t N,
                                                      int G1, double *part_rr, Scal *s, cudaGraphConditionalHandle h,
                                                      int use_cond, const double *__restrict__ dinv,
                                                      double *part_rz) {
-    pdl_enter();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         s->rho_b = s->rho;
         s->iter_b = s->iter;
@@ -593,7 +582,6 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_xp(int64_t N
                                                       const double *__restrict__ r, const double *part_rr, int G2,
                                                       Scal *s, cudaGraphConditionalHandle h, int use_cond,
                                                       const double *__restrict__ dinv, const double *part_rz) {
-    pdl_enter();
     const int k = s->iter_b;
     if (s->brk || s->halt[k & 1]) return;
     double rr = 0.0, rz = 0.0, beta = 0.0;
@@ -853,12 +841,8 @@ __global__ void __launch_bounds__(kBlock) k_inner_init(int64_t N, const double *
 // sums in FP32).  A warp covers the 128 entries of flag group i >> 5 (float4
 // per lane); groups without interface copies skip the weights.
 // The block's part of it; false when the loop has stopped (every block
-// returns at the same point: all read the same state and partials).  FD:
-// the direction update runs inside the next product (k_spmv_fd), which
-// hands the iteration number over in iter_b; this kernel then advances iter
-// and relays a stop that the product raised (halt[(k + 1) & 1]) to
-// halt[k & 1], the flag every later kernel of the loop reads.
-template <bool PC, bool FD = false>
+// returns at the same point: all read the same state and partials).
+template <bool PC>
 __device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r, const float *__restrict__ q,
                                                 const uint8_t *__restrict__ mult, const float *__restrict__ wtab,
                                                 const uint8_t *__restrict__ gflag128, const double *part_pq, int G1,
@@ -867,20 +851,12 @@ __device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r
                                                 const float *__restrict__ dinv32, double *part_rz) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         si->rho_b = si->rho;
-        if (!FD) si->iter_b = si->iter;
+        si->iter_b = si->iter;
         si->total_b = so->total;
         so->passes += 1;
     }
-    const int k = FD ? si->iter_b : si->iter;
-    if (FD) {
-        const bool held = si->halt[(k + 1) & 1] != 0;
-        if (si->brk || si->halt[k & 1] || held) {
-            if (held && blockIdx.x == 0 && threadIdx.x == 0) si->halt[k & 1] = 1;
-            return false;
-        }
-    } else if (si->brk || si->halt[k & 1]) {
-        return false;
-    }
+    const int k = si->iter;
+    if (si->brk || si->halt[k & 1]) return false;
     double pq = 0.0, alpha_d = 0.0;
     float alpha = 0.f;
     float acc = 0.f, acz = 0.f;
@@ -968,22 +944,19 @@ __device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r
             si->alpha = alpha_d;
             si->alpha32 = alpha;
             si->pq = pq;
-            if (FD) si->iter = k + 1;
         }
     }
     return true;
 }
 
-template <bool PC, bool FD = false>
+template <bool PC>
 __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
                                                        const uint8_t *__restrict__ mult, const float *__restrict__ wtab,
                                                        const uint8_t *__restrict__ gflag128, const double *part_pq, int G1,
                                                        double *part_rr, Scal *si, Scal *so,
                                                        cudaGraphConditionalHandle h, int use_cond,
                                                        const float *__restrict__ dinv32, double *part_rz) {
-    pdl_enter();
-    update_r32_step<PC, FD>(N, r, q, mult, wtab, gflag128, part_pq, G1, part_rr, si, so, h, use_cond, dinv32,
-                            part_rz);
+    update_r32_step<PC>(N, r, q, mult, wtab, gflag128, part_pq, G1, part_rr, si, so, h, use_cond, dinv32, part_rz);
 }
 
 // Inner Algorithm 3 lines 4, 7, 8 in FP32: every block sums the partials of
@@ -1068,323 +1041,10 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t
                                                         const float *__restrict__ r, const double *part_rr, int G2,
                                                         Scal *si, Scal *so, cudaGraphConditionalHandle h, int use_cond,
                                                         const float *__restrict__ dinv32, const double *part_rz) {
-    pdl_enter();
     const int k = si->iter_b;
     if (si->brk || si->halt[k & 1]) return;
     update_dp32_step<PC>(N, d, p, r, part_rr, G2, si, so, h, use_cond, dinv32, part_rz, k, si->alpha32,
                          si->total_b + 1, si->rho_b);
-}
-
-// ---------------------------------------------------------------------------
-// FP32 product with the previous iteration's direction update folded in
-// (k_spmv_fd).  Inner Algorithm 3 lines 7-8 of iteration k-1 (beta, d += alpha
-// p, p = z + beta p) and line 2 of iteration k (q = S p with the weighted dot)
-// as one launch: the product forms p_k at every column it gathers from p_{k-1}
-// and z_k (the value the direction update would have stored, bit for bit),
-// and the lane that owns a row stores p_k and d there.  p_{k-1} and p_k live in
-// two buffers used in turn (P[k & 1] holds p_k), so no block reads an entry
-// another block writes.
-
-// x = p_k entry j from p_{k-1} and z_k = r_k (M^-1 r_k with the preconditioner).
-template <bool PC>
-struct DirX {
-    const float *__restrict__ pold;
-    const float *__restrict__ r;
-    const float *__restrict__ dinv;
-    float beta;
-    __device__ __forceinline__ float operator()(int j) const {
-        const float z = PC ? __ldg(r + j) * __ldg(dinv + j) : __ldg(r + j);
-        return fmaf(beta, __ldg(pold + j), z);
-    }
-};
-// x = p_0 as the refinement's first kernel stored it.
-struct PlainX {
-    const float *__restrict__ x;
-    __device__ __forceinline__ float operator()(int j) const { return __ldg(x + j); }
-};
-
-template <int N, typename X>
-__device__ __forceinline__ float fd_chunk(const float *__restrict__ sv, const int32_t *__restrict__ sc,
-                                          const X &xf, int base, int k0, float acc) {
-    float vv[N], xv[N];
-    int cc[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        vv[j] = __ldcs(sv + base + (k0 + j) * kSliceRows);
-        cc[j] = __ldcs(sc + base + (k0 + j) * kSliceRows);
-    }
-#pragma unroll
-    for (int j = 0; j < N; ++j) xv[j] = xf(cc[j]);
-#pragma unroll
-    for (int j = 0; j < N; ++j) acc = fmaf(vv[j], xv[j], acc);
-    return acc;
-}
-
-template <typename X>
-__device__ __forceinline__ float fd_row(const float *__restrict__ sv, const int32_t *__restrict__ sc, const X &xf,
-                                        int off, int w, int lane) {
-    const int base = off + lane;
-    float acc = 0.f;
-    int k = 0;
-    for (; k + 8 <= w; k += 8) acc = fd_chunk<8>(sv, sc, xf, base, k, acc);
-    switch (w - k) {
-        case 1: return fd_chunk<1>(sv, sc, xf, base, k, acc);
-        case 2: return fd_chunk<2>(sv, sc, xf, base, k, acc);
-        case 3: return fd_chunk<3>(sv, sc, xf, base, k, acc);
-        case 4: return fd_chunk<4>(sv, sc, xf, base, k, acc);
-        case 5: return fd_chunk<5>(sv, sc, xf, base, k, acc);
-        case 6: return fd_chunk<6>(sv, sc, xf, base, k, acc);
-        case 7: return fd_chunk<7>(sv, sc, xf, base, k, acc);
-        default: return acc;
-    }
-}
-
-// Row `row`'s own entry: y = S p_k there, p_k and d stored (UPD), and its
-// share of (p_k, S p_k)_w (weight w).
-template <bool UPD, typename X>
-__device__ __forceinline__ void fd_store(const X &xf, int row, float yv, float w, bool weighted,
-                                         const float *__restrict__ pold, float *__restrict__ pnew,
-                                         float *__restrict__ d, float alpha, float *__restrict__ y, float &dot) {
-    const float pk = xf(row);
-    y[row] = yv;
-    if (UPD) {
-        pnew[row] = pk;
-        d[row] = fmaf(alpha, __ldg(pold + row), d[row]);
-    }
-    dot = fmaf(weighted ? w * pk : pk, yv, dot);
-}
-
-template <bool UPD, int AHEAD, typename X>
-__device__ __forceinline__ float fd_items(const DevOp &A, const X &xf, const float *__restrict__ pold,
-                                          float *__restrict__ pnew, float *__restrict__ d, float alpha,
-                                          float *__restrict__ y) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int2 range = A.warp_range[blockIdx.x * kSpmvWarps + warp];
-    const float *__restrict__ sv = A.sval32;
-    float dot = 0.f;
-    for (int it = range.x; it < range.y; ++it) {
-        const WorkItem W = A.items[it];
-        if (AHEAD > 0 && it + AHEAD < range.y) {
-            // the value and column lines of a slice further ahead, one line per lane
-            const WorkItem Wp = A.items[it + AHEAD];
-            if ((Wp.kind == kItemSlice || Wp.kind == kItemIfaceSlice) && lane < Wp.e1) {
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(sv + Wp.e0 + lane * kSliceRows));
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
-            }
-        }
-        if (W.kind == kItemSlice || W.kind == kItemIfaceSlice) {
-            const float acc = fd_row(sv, A.scol, xf, W.e0, W.e1, lane);
-            if (W.kind == kItemSlice) {
-                const int r = W.a + lane;
-                if (r < W.b) fd_store<UPD>(xf, r, acc, 1.f, false, pold, pnew, d, alpha, y, dot);
-            } else {
-                const int c = W.a + lane;
-                const bool valid = c < W.b;
-                const int seg = valid ? __ldg(A.sseg + c) : 0;
-                const int l0 = seg & 0xff, m = seg >> 8;
-                const int mmax = __reduce_max_sync(0xffffffffu, m);
-                float S = 0.f;
-                for (int t = 0; t < mmax; ++t) {
-                    const float v = __shfl_sync(0xffffffffu, acc, (l0 + t) & 31);
-                    if (t < m) S += v;
-                }
-                if (valid)
-                    fd_store<UPD>(xf, __ldg(A.icopy + c), S, __ldg(A.wtab32 + m), true, pold, pnew, d, alpha, y,
-                                  dot);
-            }
-        } else if (W.kind == kItemLongRow) {
-            float acc = 0.f;
-            for (int k = W.e0 + lane; k < W.e1; k += 32) acc = fmaf(A.val32[k], xf(A.col[k]), acc);
-            const float racc = float(warp_sum(double(acc)));
-            if (lane == 0) fd_store<UPD>(xf, W.a, racc, 1.f, false, pold, pnew, d, alpha, y, dot);
-        } else {
-            float S = 0.f;
-            for (int c = W.c0; c < W.c1; ++c) {
-                float acc = 0.f;
-                for (int k = A.irp[c] + lane; k < A.irp[c + 1]; k += 32) acc = fmaf(A.ival32[k], xf(A.icol[k]), acc);
-                S += float(warp_sum(double(acc)));  // valid in lane 0
-            }
-            if (lane == 0) {
-                const float w = __ldg(A.wtab32 + (W.c1 - W.c0));
-                for (int c = W.c0; c < W.c1; ++c) fd_store<UPD>(xf, A.icopy[c], S, w, true, pold, pnew, d, alpha, y, dot);
-            }
-        }
-    }
-    return dot;
-}
-
-// Iteration k of the FP32 inner CG (k = si->iter).  k = 0: q = S p_0 from the
-// stored p_0.  k >= 1: every block sums the residual kernel's partials of
-// (r_k, r_k)_w (and (r_k, z_k)_w), forms beta = rho_k / rho_{k-1} once, takes
-// the stopping decision of iteration k-1 (sqrt((r, r)_w) <= tau sqrt(rho0), or the
-// summed inner iterations reach max_iter); on a stop it applies d += alpha
-// p_{k-1} alone (grid-stride) and raises halt[(k + 1) & 1], else it runs the
-// product on p_k as above.  Block 0 records rho, beta and the summed count.
-// BPS, AHEAD: resident blocks per SM of the launch and slices ahead
-// prefetched into L2, those of the FP32 product instance in use (so both
-// forms partition the work alike).
-template <bool PC, int BPS, int AHEAD>
-__global__ void __launch_bounds__(kSpmvThreads, BPS)
-    k_spmv_fd(DevOp A, int64_t N, const float *__restrict__ r, const float *__restrict__ dinv32, float *p0,
-              float *p1, float *__restrict__ d, float *__restrict__ y, double *part_pq, const double *part_rr,
-              const double *part_rz, int G2, Scal *si, Scal *so, cudaGraphConditionalHandle h, int use_cond) {
-    const int k = si->iter;
-    if (blockIdx.x == 0 && threadIdx.x == 0) si->iter_b = k;
-    if (si->brk || si->halt[k & 1]) return;
-    float *pnew = (k & 1) ? p1 : p0;
-    const float *pold = (k & 1) ? p0 : p1;
-    float dot;
-    if (k == 0) {
-        dot = fd_items<false, AHEAD>(A, PlainX{pnew}, pold, pnew, d, 0.f, y);
-    } else {
-        const double rr = all_sum_partials(part_rr, G2);
-        const double rz = PC ? all_sum_partials(part_rz, G2) : rr;
-        float beta = 0.f;
-        const double beta_d = block_quotient(rz, si->rho_b, &beta);
-        const float alpha = si->alpha32;
-        const int total1 = si->total_b + 1;
-        const bool stop = sqrt(rr) <= si->tau * sqrt(si->rho0) || total1 >= so->max_iter;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            si->rho = rz;
-            si->rr = rr;
-            si->beta = beta_d;
-            si->beta32 = beta;
-            so->total = total1;
-            if (stop) {
-                si->halt[(k + 1) & 1] = 1;
-                stop_loop(si, h, use_cond);
-            }
-        }
-        if (stop) {
-            const int64_t stride = (int64_t)gridDim.x * kSpmvThreads;
-            for (int64_t i = (int64_t)blockIdx.x * kSpmvThreads + threadIdx.x; i < N; i += stride)
-                d[i] = fmaf(alpha, pold[i], d[i]);
-            return;
-        }
-        dot = fd_items<true, AHEAD>(A, DirX<PC>{pold, r, dinv32, beta}, pold, pnew, d, alpha, y);
-    }
-    __shared__ double wsum[kSpmvWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double wv = double(warp_sumf(dot));
-    if (lane == 0) wsum[warp] = wv;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double bs = wsum[0];
-#pragma unroll
-        for (int w = 1; w < kSpmvWarps; ++w) bs += wsum[w];
-        part_pq[blockIdx.x] = bs;
-    }
-}
-
-// Bounds of the grid barrier's wait: about one second of %globaltimer, or
-// this many polls, whichever ends first.
-constexpr uint64_t kGridWaitNs = 1000000000ull;
-constexpr uint32_t kGridWaitPolls = 1u << 26;
-
-__device__ __forceinline__ uint64_t timer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *a) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
-    return v;
-}
-
-// Barrier over every block of a cooperative launch (all blocks resident at
-// once).  bar[0] counts arrivals (zeroed before a solve, advanced by exactly
-// gridDim.x per barrier); bar[16], a cache line away, holds the number of
-// the last completed round.  Thread 0 of each block publishes the block's
-// earlier writes and arrives; the last arrival of a round publishes the
-// round number, the others poll for it (reads only, off the line the
-// arrivals update).  False when the wait ran out (no block may then rely on
-// the others' writes); every thread of the block gets the same answer.
-constexpr int kGridBarWords = 32;  // two 128-byte lines of 64-bit words
-__device__ __forceinline__ bool grid_barrier(unsigned long long *bar) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned long long G = gridDim.x;
-        unsigned long long *round_done = bar + 16;
-        __threadfence();
-        const unsigned long long old = atomicAdd(bar, 1ull);
-        const unsigned long long round = old / G + 1;
-        int good = 0;
-        if (old % G == G - 1) {
-            __threadfence();
-            atomicMax(round_done, round);
-            good = 1;
-        } else {
-            const uint64_t t0 = timer_ns();
-            for (uint32_t it = 0; it < kGridWaitPolls; ++it) {
-                if (ld_acquire(round_done) >= round) {
-                    good = 1;
-                    break;
-                }
-                if ((it & 63u) == 63u && timer_ns() - t0 > kGridWaitNs) break;
-                __nanosleep(100);
-            }
-        }
-        __threadfence();
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
-// Failure-path probe of grid_barrier: block 1 returns without arriving, so
-// block 0's wait runs out after about a second; *result = 1 then (2 if the
-// barrier had completed).
-__global__ void k_grid_barrier_probe(unsigned long long *count, unsigned long long *result) {
-    if (blockIdx.x != 0) return;
-    const bool ok = grid_barrier(count);
-    if (threadIdx.x == 0) *result = ok ? 2ull : 1ull;
-}
-
-// Inner Algorithm 3 lines 3-8 in FP32 as one cooperative launch: the residual
-// update of k_update_r32, a grid barrier (where block partials of
-// (r32, r32)_w and block 0's alpha become visible to all blocks), then the
-// direction update of k_update_dp32.  Each block's threads own the same
-// entries in both halves, so the direction half re-reads r32 that the same
-// thread just wrote; its first items of p32 and d32 (and of the diagonal) are
-// prefetched into L2 while the barrier waits.  Same arithmetic, same order
-// and the same bits as the two kernels.  A barrier that runs out records
-// SSG_E_TIMEOUT and stops the loop.
-template <bool PC>
-__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_rdp32(
-    int64_t N, float *__restrict__ r, const float *__restrict__ q, float *__restrict__ d,
-    float *__restrict__ p, const uint8_t *__restrict__ mult, const float *__restrict__ wtab,
-    const uint8_t *__restrict__ gflag128, const double *part_pq, int G1, double *part_rr, Scal *si, Scal *so,
-    cudaGraphConditionalHandle h, int use_cond, const float *__restrict__ dinv32, double *part_rz,
-    unsigned long long *bar) {
-    if (!update_r32_step<PC>(N, r, q, mult, wtab, gflag128, part_pq, G1, part_rr, si, so, h, use_cond, dinv32,
-                             part_rz))
-        return;
-    const int64_t stride = (int64_t)gridDim.x * kBlock;
-    const int64_t N4 = N >> 2;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x + u * stride;
-        if (i < N4) {
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 4 * i));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(d + 4 * i));
-            if (PC) asm volatile("prefetch.global.L2 [%0];" ::"l"(dinv32 + 4 * i));
-        }
-    }
-    if (!grid_barrier(bar)) {
-        if (threadIdx.x == 0) {
-            si->status = SSG_E_TIMEOUT;
-            si->brk = 1;
-            stop_loop(si, h, use_cond);
-        }
-        return;
-    }
-    // written by block 0 before the barrier: read from L2, not a stale L1 line
-    update_dp32_step<PC>(N, d, p, r, part_rr, gridDim.x, si, so, h, use_cond, dinv32, part_rz,
-                         __ldcg(&si->iter_b), __ldcg(&si->alpha32), __ldcg(&si->total_b) + 1,
-                         __ldcg(&si->rho_b));
 }
 
 // x64 <- x64 + (double) d32 (the refinement update).

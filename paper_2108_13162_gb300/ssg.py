@@ -35,9 +35,6 @@ SSG_BAND_ROW = 0
 SSG_BAND_COL = 1
 SSG_BAND_AUTO = 0
 SSG_BAND_STAGED = -1
-SSG_FUSE_NONE = 0
-SSG_FUSE_GRID = 1
-SSG_FUSE_SPMV = 2
 
 # every entry point declared in include/ssg.h
 EXPORTS = (
@@ -46,10 +43,7 @@ EXPORTS = (
     "ssg_set_driver",
     "ssg_set_mixed",
     "ssg_set_rhs_block",
-    "ssg_set_pdl",
-    "ssg_set_fused",
     "ssg_set_unroll",
-    "ssg_check_barrier_timeout",
     "ssg_destroy",
     "ssg_partition",
     "ssg_partition_fe",
@@ -178,10 +172,7 @@ def lib():
         L.ssg_set_driver.argtypes = [vp, C.c_int]
         L.ssg_set_mixed.argtypes = [vp, C.c_double, C.c_int32]
         L.ssg_set_rhs_block.argtypes = [vp, C.c_int32]
-        L.ssg_set_pdl.argtypes = [vp, C.c_int]
-        L.ssg_set_fused.argtypes = [vp, C.c_int]
         L.ssg_set_unroll.argtypes = [vp, C.c_int32]
-        L.ssg_check_barrier_timeout.argtypes = [vp]
         L.ssg_destroy.argtypes = [vp]
         L.ssg_partition.argtypes = [vp, i32, vp, vp, vp, vp, i32, C.POINTER(vp)]
         L.ssg_partition_batch.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, C.POINTER(vp)]
@@ -275,21 +266,8 @@ def ssg_set_rhs_block(ctx, kmax: int):
     return _check(lib().ssg_set_rhs_block(ctx, kmax), "ssg_set_rhs_block")
 
 
-def ssg_set_pdl(ctx, enable: bool):
-    return _check(lib().ssg_set_pdl(ctx, int(bool(enable))), "ssg_set_pdl")
-
-
-def ssg_set_fused(ctx, mode: int):
-    return _check(lib().ssg_set_fused(ctx, int(mode)), "ssg_set_fused")
-
-
 def ssg_set_unroll(ctx, iters: int):
     return _check(lib().ssg_set_unroll(ctx, int(iters)), "ssg_set_unroll")
-
-
-def ssg_check_barrier_timeout(ctx) -> int:
-    """Raw status of the grid-barrier timeout probe (SSG_E_TIMEOUT expected)."""
-    return lib().ssg_check_barrier_timeout(ctx)
 
 
 def ssg_destroy(ctx):
@@ -595,16 +573,9 @@ class Context:
     def set_driver(self, driver: int):
         ssg_set_driver(self.h, driver)
 
-    def set_pdl(self, enable: bool):
-        ssg_set_pdl(self.h, enable)
-
     def set_unroll(self, iters: int):
         """CG iterations per pass of a single-vector loop graph's body (systems partitioned afterwards)."""
         ssg_set_unroll(self.h, iters)
-
-    def set_fused(self, mode: int):
-        """SSG_FUSE_NONE, SSG_FUSE_GRID or SSG_FUSE_SPMV (systems partitioned afterwards)."""
-        ssg_set_fused(self.h, mode)
 
     def set_mixed(self, inner_rtol: float = 1e-4, max_outer: int = 30):
         ssg_set_mixed(self.h, inner_rtol, max_outer)

@@ -14,9 +14,7 @@ inner FP32 sums are ordered differently on each side):
     (kappa from the Lanczos coefficients of the FP64 oracle run);
   * both drivers (graph, host loop) give the same bits; the parameters are
     validated; a one-refinement cap stops with SSG_E_NOT_CONVERGED;
-  * the fused kernel splits of the FP32 iteration (SSG_FUSE_GRID,
-    SSG_FUSE_SPMV) give the bits of the three-kernel form; the grid
-    barrier's bounded wait times out.
+  * several iterations per loop pass give the bits of one.
 """
 
 import json
@@ -191,112 +189,6 @@ def test_mixed_full_size_128cube(ctx):
     idx = np.array(g["sample_idx"])
     assert _rel(xg[idx], np.array(gm["sample_x"])) <= 2 * kap * 1e-8
     assert _rel(xg, p.xstar[:, 0]) <= 2 * kap * 1e-8
-
-
-def _fused_pair(ctx, p, mode):
-    from paper_2108_13162_gb300 import ssg
-    from paper_2108_13162_gb300.ssg import System
-
-    # one iteration per loop pass, so that the launch counts below are exact
-    ctx.set_unroll(1)
-    try:
-        S0 = System(ctx, p.A, p.part, p.P)  # the default split: three kernels
-        ctx.set_fused(mode)
-        S1 = System(ctx, p.A, p.part, p.P)
-    finally:
-        ctx.set_fused(ssg.SSG_FUSE_NONE)
-        ctx.set_unroll(UNROLL_DEFAULT)
-    return S0, S1
-
-
-def _launch_saving(mode, st):
-    """Kernels a fused form saves in one graph solve against three per inner
-    iteration: one per inner iteration, less, for the folded form, the two
-    kernels of the extra loop pass of every refinement (its product only
-    completes d)."""
-    from paper_2108_13162_gb300 import ssg
-
-    return st["iters"] - (2 * st["outer"] if mode == ssg.SSG_FUSE_SPMV else 0)
-
-
-FUSED_CASES = [
-    ("fv3d_24", lambda: config_problem(2, scale=24)),  # one float4 item per thread
-    ("fe2d_64", lambda: config_problem(3, scale=64)),  # ragged tail: 4545 local entries
-]
-
-
-@pytest.mark.parametrize("fuse", [1, 2], ids=["grid", "spmv"])
-@pytest.mark.parametrize("name,mk", FUSED_CASES, ids=[c[0] for c in FUSED_CASES])
-def test_mixed_fused_update_same_bits(ctx, name, mk, fuse):
-    """The fused kernel splits (SSG_FUSE_GRID: both updates as one
-    cooperative kernel with a grid barrier; SSG_FUSE_SPMV: the direction
-    update folded into the next product) give the bits, iteration counts and
-    refinements of the three-kernel form (the default), in both modes and
-    with both drivers, and launch fewer kernels."""
-    from paper_2108_13162_gb300 import ssg
-
-    p = mk()
-    S0, S1 = _fused_pair(ctx, p, fuse)
-    b = _t(p.b[:, 0])
-    for mode in (ssg.SSG_MIXED, ssg.SSG_MIXED_JACOBI):
-        for driver in (ssg.SSG_DRIVER_GRAPH, ssg.SSG_DRIVER_HOST):
-            ctx.set_driver(driver)
-            try:
-                x0, rc0, s0 = S0.solve(b, rtol=1e-8, mode=mode)
-                x1, rc1, s1 = S1.solve(b, rtol=1e-8, mode=mode)
-            finally:
-                ctx.set_driver(ssg.SSG_DRIVER_GRAPH)
-            assert rc0 == rc1 == ssg.SSG_OK
-            assert (s1[0]["iters"], s1[0]["outer"]) == (s0[0]["iters"], s0[0]["outer"])
-            assert np.array_equal(x1.cpu().numpy(), x0.cpu().numpy()), (mode, driver)
-            if driver == ssg.SSG_DRIVER_GRAPH:
-                assert s0[0]["kernel_launches"] - s1[0]["kernel_launches"] == _launch_saving(fuse, s1[0])
-            else:
-                assert s1[0]["kernel_launches"] < s0[0]["kernel_launches"]
-    S0.close()
-    S1.close()
-
-
-@pytest.mark.parametrize("fuse", [1, 2], ids=["grid", "spmv"])
-def test_mixed_fused_update_same_bits_128cube(ctx, fuse):
-    """The benchmark's system (several float4 items per thread, the full
-    608-block grid): the fused forms and the three-kernel form agree bit for
-    bit."""
-    from paper_2108_13162_gb300 import ssg
-
-    p = config_problem(2)
-    S0, S1 = _fused_pair(ctx, p, fuse)
-    b = _t(p.b[:, 0])
-    for mode in (ssg.SSG_MIXED, ssg.SSG_MIXED_JACOBI):
-        x0, rc0, s0 = S0.solve(b, rtol=1e-8, mode=mode)
-        x1, rc1, s1 = S1.solve(b, rtol=1e-8, mode=mode)
-        assert rc0 == rc1 == ssg.SSG_OK
-        assert (s1[0]["iters"], s1[0]["outer"]) == (s0[0]["iters"], s0[0]["outer"])
-        assert np.array_equal(x1.cpu().numpy(), x0.cpu().numpy()), mode
-        assert s0[0]["kernel_launches"] - s1[0]["kernel_launches"] == _launch_saving(fuse, s1[0])
-    S0.close()
-    S1.close()
-
-
-def test_grid_barrier_wait_times_out(ctx):
-    """The fused update's grid barrier is bounded: with one block that never
-    arrives the other gives up after about a second and reports
-    SSG_E_TIMEOUT; the context keeps working afterwards."""
-    import time
-
-    from paper_2108_13162_gb300 import ssg
-    from paper_2108_13162_gb300.ssg import System
-
-    t0 = time.perf_counter()
-    rc = ssg.ssg_check_barrier_timeout(ctx.h)
-    dt = time.perf_counter() - t0
-    assert rc == ssg.SSG_E_TIMEOUT, rc
-    assert 0.5 <= dt <= 30.0, dt
-    p = config_problem(2, scale=16)
-    S = System(ctx, p.A, p.part, p.P)
-    x, rc, st = S.solve(_t(p.b[:, 0]), rtol=1e-8, mode=ssg.SSG_MIXED)
-    assert rc == ssg.SSG_OK
-    S.close()
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2, 3], ids=["fp64", "mixed", "fp64_jacobi", "mixed_jacobi"])
