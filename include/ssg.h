@@ -205,6 +205,15 @@ int ssg_partition_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off,
  * in that order.  max_iter <= 0 means the largest n_s.  Returns SSG_OK when
  * every right-hand side converged, else the first non-OK status.
  */
+/*
+ * How a batch whose systems fall into several column groups runs with the
+ * graph driver (not in the paper): one_graph != 0 (the default) launches one
+ * graph whose parallel branches are the groups' loops; 0 launches each
+ * group's own loop graph on a stream of its own, side by side.  The second
+ * form is also what a solve falls back to when the one-graph form cannot be
+ * built.  Both give the same bits.  SSG_E_INVALID for a null system.
+ */
+int ssg_set_batch_graph(ssg_system *sys, int32_t one_graph);
 int ssg_solve_batch(ssg_system *sys, const double *b, double *x, int32_t x_is_guess, double rtol, int32_t max_iter,
                     int32_t mode, ssg_stats *stats);
 int ssg_get_sizes(const ssg_system *sys, ssg_sizes *out);

@@ -1964,7 +1964,11 @@ int batch_classes_ready(ssg_system *S, int mode) {
         SSG_CUDA_TRY(cudaStreamSynchronize(C->ctx->stream));
     }
     if (classes_graph(S, mode) != SSG_OK) {
+        // the solve falls back to streams; the failed capture or
+        // instantiation left its (non-sticky) error behind, which the next
+        // launch check would otherwise report (the message stays set)
         S->classes_graph_refused[mode] = true;
+        cudaGetLastError();
         return SSG_E_CUDA;
     }
     return SSG_OK;
@@ -1973,6 +1977,15 @@ int batch_classes_ready(ssg_system *S, int mode) {
 }  // namespace
 
 extern "C" {
+
+int ssg_set_batch_graph(ssg_system *S, int32_t one_graph) {
+    if (!S) {
+        set_error("null system");
+        return SSG_E_INVALID;
+    }
+    for (bool &r : S->classes_graph_refused) r = one_graph == 0;
+    return SSG_OK;
+}
 
 int ssg_solve_batch(ssg_system *S, const double *b, double *x, int32_t x_is_guess, double rtol, int32_t max_iter,
                     int32_t mode, ssg_stats *stats) {

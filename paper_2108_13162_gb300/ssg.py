@@ -69,6 +69,7 @@ EXPORTS = (
     "ssg_error_string",
     "ssg_last_error",
     "ssg_wdot_noalloc",
+    "ssg_set_batch_graph",
     "ssg_band_split",
     "ssg_band_get",
     "ssg_band_spmv",
@@ -196,6 +197,7 @@ def lib():
         L.ssg_solve_host.argtypes = [vp, i32, vp, vp, i32, C.c_double, i32, i32, C.POINTER(ssg_stats)]
         L.ssg_system_destroy.argtypes = [vp]
         L.ssg_wdot_noalloc.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
+        L.ssg_set_batch_graph.argtypes = [vp, C.c_int32]
         L.ssg_band_split.argtypes = [vp, i32, i32, vp, vp, vp, i32, C.POINTER(vp)]
         L.ssg_band_get.argtypes = [vp, i32, vp, vp, vp, vp]
         L.ssg_band_spmv.argtypes = [vp, vp, vp]
@@ -528,6 +530,10 @@ def ssg_wdot_noalloc(u_loc, v_loc, mult_loc, out, stream=None):
         lib().ssg_wdot_noalloc(u_loc.data_ptr(), v_loc.data_ptr(), mult_loc.data_ptr(), n, out.data_ptr(), stream),
         "ssg_wdot_noalloc",
     )
+
+
+def ssg_set_batch_graph(sys, one_graph: bool):
+    return _check(lib().ssg_set_batch_graph(sys, int(bool(one_graph))), "ssg_set_batch_graph")
 
 
 def ssg_system_destroy(sys):

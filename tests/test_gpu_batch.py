@@ -142,6 +142,16 @@ def test_batch_drivers_agree(ctx, bp):
         assert rc1 == rc2 == ssg.SSG_OK
         assert np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
         assert [(a["iters"], a["outer"]) for a in s1] == [(a["iters"], a["outer"]) for a in s2]
+        # the column groups on streams of their own (the form a solve falls
+        # back to when the one-graph form cannot be built): the same bits
+        ssg.ssg_set_batch_graph(B.h, False)
+        try:
+            x3, rc3, s3 = B.solve(_b_all(bp), rtol=1e-8, mode=mode)
+        finally:
+            ssg.ssg_set_batch_graph(B.h, True)
+        assert rc3 == ssg.SSG_OK
+        assert np.array_equal(x1.cpu().numpy(), x3.cpu().numpy())
+        assert [(a["iters"], a["outer"]) for a in s1] == [(a["iters"], a["outer"]) for a in s3]
 
 
 def test_batch_rejects_bad_tables(ctx, bp):
