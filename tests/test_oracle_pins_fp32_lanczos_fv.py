@@ -27,10 +27,12 @@ Generators (cell-centred finite volumes, harmonic faces, boundary faces 2k):
   G3 fv3d_7pt on a line of three cells along x, y and z, three kappas.
   G4 fv2d_5pt on 2x2 cells and on a line of three cells.
 Mixed inner iterations:
-  M1 a matrix with d distinct eigenvalues (d <= 4, kappa <= 27): each FP32
-     inner solve ends after exactly d iterations (CG's finite termination), so
-     the refinement takes d x refinements inner iterations, two refinements
-     to 1e-8.
+  M1 a matrix with d distinct eigenvalues (d <= 4, kappa <= 27), refinement
+     capped at two steps and rtol 1e-13, so that both inner solves run to
+     the inner tolerance 1e-4 (rtol ||b|| / ||r|| stays below it): each FP32
+     inner solve ends after exactly d iterations (CG's finite termination),
+     2 d in all.  (Uncapped, the last refinement's tolerance rtol ||b|| / ||r||
+     is loose, and where it stops depends on rounding.)
 """
 
 import inspect
@@ -350,11 +352,11 @@ def count_case(blocks, seed, nrep=25, P=5):
 @pytest.mark.parametrize("case", COUNT_CASES, ids=[c[0] for c in COUNT_CASES])
 def test_mixed_inner_counts_finite_termination(case):
     _, blocks, d = case
-    for seed in range(3):
+    for seed in range(4):
         A, b, part, P = count_case(blocks, seed)
         Pt = oracle.Partition(A, part, P)
         assert Pt.maps.ngamma > 0  # the pairs are split across subdomains
-        r = Pt.cg_mixed(b, 1e-8, 1000, 1e-4, 30)
-        assert r.status == oracle.OK
-        assert r.outer == 2 and r.iters == d * r.outer, (seed, r.iters, r.outer)
-        assert np.linalg.norm(b - oracle.spmv(A, r.x)) <= 1e-8 * np.linalg.norm(b)
+        r = Pt.cg_mixed(b, 1e-13, 1000, 1e-4, 2)
+        assert r.status in (oracle.OK, oracle.NOT_CONVERGED)
+        assert r.outer == 2 and r.iters == 2 * d, (seed, r.iters, r.outer)
+        assert np.linalg.norm(b - oracle.spmv(A, r.x)) <= 1e-9 * np.linalg.norm(b)
