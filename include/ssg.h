@@ -214,6 +214,17 @@ int ssg_partition_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off,
  * built.  Both give the same bits.  SSG_E_INVALID for a null system.
  */
 int ssg_set_batch_graph(ssg_system *sys, int32_t one_graph);
+
+/*
+ * This GPU's FP64 fused multiply-add rate, measured (not in the paper): the
+ * denominator of the rooflines of FP64-bound kernels.  Eight 256-thread
+ * blocks per SM each keep 8 independent FMA chains per thread going for
+ * `iters` steps; the best of `reps` timed launches (CUDA events on the
+ * context's stream, after one untimed launch) gives *tflops (2 flops per FMA)
+ * and *best_ms (may be NULL).  Allocates and frees a small sink buffer.
+ * SSG_E_INVALID for a null context or result, iters or reps < 1.
+ */
+int ssg_measure_fp64_rate(ssg_ctx *ctx, int32_t iters, int32_t reps, double *tflops, double *best_ms);
 int ssg_solve_batch(ssg_system *sys, const double *b, double *x, int32_t x_is_guess, double rtol, int32_t max_iter,
                     int32_t mode, ssg_stats *stats);
 int ssg_get_sizes(const ssg_system *sys, ssg_sizes *out);

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libssg.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["api.cu", "noalloc.cu", "band.cu"]
+CU_SOURCES = ["api.cu", "noalloc.cu", "band.cu", "peak.cu"]
 CPP_SOURCES = ["partition.cpp"]
 
 

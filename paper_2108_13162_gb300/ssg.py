@@ -70,6 +70,7 @@ EXPORTS = (
     "ssg_last_error",
     "ssg_wdot_noalloc",
     "ssg_set_batch_graph",
+    "ssg_measure_fp64_rate",
     "ssg_band_split",
     "ssg_band_get",
     "ssg_band_spmv",
@@ -198,6 +199,8 @@ def lib():
         L.ssg_system_destroy.argtypes = [vp]
         L.ssg_wdot_noalloc.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
         L.ssg_set_batch_graph.argtypes = [vp, C.c_int32]
+        L.ssg_measure_fp64_rate.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double)]
         L.ssg_band_split.argtypes = [vp, i32, i32, vp, vp, vp, i32, C.POINTER(vp)]
         L.ssg_band_get.argtypes = [vp, i32, vp, vp, vp, vp]
         L.ssg_band_spmv.argtypes = [vp, vp, vp]
@@ -534,6 +537,14 @@ def ssg_wdot_noalloc(u_loc, v_loc, mult_loc, out, stream=None):
 
 def ssg_set_batch_graph(sys, one_graph: bool):
     return _check(lib().ssg_set_batch_graph(sys, int(bool(one_graph))), "ssg_set_batch_graph")
+
+
+def ssg_measure_fp64_rate(ctx, iters: int = 20000, reps: int = 3):
+    """(TFLOP/s, best launch ms) of the FP64 FMA rate probe (see ssg.h)."""
+    t = C.c_double()
+    ms = C.c_double()
+    _check(lib().ssg_measure_fp64_rate(ctx, int(iters), int(reps), C.byref(t), C.byref(ms)), "ssg_measure_fp64_rate")
+    return t.value, ms.value
 
 
 def ssg_system_destroy(sys):
