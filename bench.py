@@ -450,8 +450,10 @@ def bench_batch(ctx, stream, reps, size):
 
 def bench_fe(ctx, stream, reps):
     """Workload 3: P1 finite elements on the jittered 1024^2 mesh, 256 uneven
-    RCB subdomains: the SpMV instances chosen by ssg_autotune for this
-    irregular system, then time to 1e-8 in FP64, mixed and mixed + Jacobi."""
+    RCB subdomains: the slice layout the row-length rule picks (rows sorted
+    by length in windows) against the unsorted one, the SpMV instances chosen
+    by ssg_autotune, the product's roofline in FP64 and FP32, then time to
+    1e-8 in FP64, mixed and mixed + Jacobi."""
     import torch
 
     from paper_2108_13162_gb300 import ssg
@@ -459,11 +461,35 @@ def bench_fe(ctx, stream, reps):
     from synth import config_problem
 
     p = config_problem(3)
+    peak, peak_src = measured_peaks()
+
+    def spmv_roofline(Sx):
+        """The FE product in both precisions: launch time (CUDA events,
+        the autotuned instance) against the algorithmic bytes."""
+        rec = {}
+        for prec, vb in (("fp64", 8), ("fp32", 4)):
+            t = time_spmv(Sx, prec, stream, 50)
+            nb = spmv_algorithmic_bytes(Sx.sizes, vb)
+            rec[prec] = {"launch_us": t * 1e6, "algorithmic_bytes": nb, "achieved_gbs": nb / t / 1e9,
+                         "frac": nb / t / 1e9 / peak, "peak": peak, "peak_source": peak_src}
+        return rec
+
+    # the unsorted layout (32 consecutive rows per slice), for comparison
+    ctx.set_slice_sort(1)
+    try:
+        S1 = System(ctx, p.A, p.part, p.P)
+    finally:
+        ctx.set_slice_sort(0)
+    S1.autotune(reps=20)
+    unsorted = {"layout": S1.layout(), "spmv": spmv_roofline(S1)}
+    S1.close()
+    # the layout the row-length rule picks (the default)
     S = System(ctx, p.A, p.part, p.P)
     tune = S.autotune(reps=20)
     b = torch.from_numpy(p.b[:, 0].copy()).cuda()
     out = {"workload": "fe2d_p1_jittered_1024^2_rcb256", "n": p.A.n, "nnz": p.A.nnz, "subdomains": p.P,
-           "nloc": S.sizes.nloc, "rtol": RTOL, "autotune": tune}
+           "nloc": S.sizes.nloc, "rtol": RTOL, "autotune": tune, "layout": S.layout(),
+           "spmv": spmv_roofline(S), "unsorted": unsorted}
     for name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED), ("mixed_jacobi", ssg.SSG_MIXED_JACOBI)):
         x, rc, st = S.solve(b, rtol=RTOL, mode=mode)
         torch.cuda.synchronize()

@@ -104,6 +104,21 @@ int ssg_set_driver(ssg_ctx *ctx, int driver);
  * iteration and 73.0 us per FP64 iteration, against 41.5 and 74.7 with one.
  * Applies to systems partitioned on this context afterwards. */
 int ssg_set_unroll(ssg_ctx *ctx, int32_t iters);
+/* Layout of the local matrices' interior rows in the sliced-ELL copy the
+ * products stream (Section 3.4.1's local SpMV; the layout is this library's,
+ * the products are unchanged): a slice holds 32 rows, one per lane, padded
+ * to its longest row.  window = 1: a slice is 32 consecutive rows; > 1: each
+ * window of that many consecutive rows is ordered by decreasing length first
+ * (SELL-C-sigma), so rows of equal length share slices and padding shrinks,
+ * at the cost of a 4-byte row index per row; -1: the window is the whole
+ * subdomain; 0 (default): per subdomain, the window of {1, 128, 256, 512}
+ * rows whose slices move the fewest bytes by its row-length histogram,
+ * sorting only when it saves at least 2 %.  Each row's entries keep their
+ * order, so the product's entries are the same bits in every layout (the
+ * block partial sums of its weighted dot group rows differently).  Applies
+ * to systems partitioned on this context afterwards; SSG_E_INVALID for
+ * window < -1. */
+int ssg_set_slice_sort(ssg_ctx *ctx, int32_t window);
 /*
  * Parameters of SSG_MIXED solves on this context (not a method of the paper;
  * its experiments are FP64 only): the inner FP32 CG stops when its residual
@@ -144,8 +159,9 @@ int ssg_destroy(ssg_ctx *ctx);
  *   entry (i,i) belongs to S^(part(i)); entry (i,j), i != j, to
  *   S^(min(part(i), part(j))), so the local matrices sum exactly to S.
  *   Interface copies of a node are listed in ascending subdomain order.
- * With ctx == NULL only the host maps are built (ssg_get_sizes and
- * ssg_copy_maps work; device calls return SSG_E_INVALID).  Otherwise the
+ * With ctx == NULL only the host maps are built (ssg_get_sizes,
+ * ssg_copy_maps and ssg_get_layout, with the default layout rule, work;
+ * device calls return SSG_E_INVALID).  Otherwise the
  * device arena is allocated and filled on the context stream.
  * Errors: SSG_E_INVALID for any malformed input, SSG_E_OOM, SSG_E_CUDA.
  */
@@ -205,6 +221,8 @@ int ssg_partition_batch(ssg_ctx *ctx, int32_t nsys, const int32_t *sys_node_off,
  * in that order.  max_iter <= 0 means the largest n_s.  Returns SSG_OK when
  * every right-hand side converged, else the first non-OK status.
  */
+int ssg_solve_batch(ssg_system *sys, const double *b, double *x, int32_t x_is_guess, double rtol, int32_t max_iter,
+                    int32_t mode, ssg_stats *stats);
 /*
  * How a batch whose systems fall into several column groups runs with the
  * graph driver (not in the paper): one_graph != 0 (the default) launches one
@@ -225,9 +243,12 @@ int ssg_set_batch_graph(ssg_system *sys, int32_t one_graph);
  * SSG_E_INVALID for a null context or result, iters or reps < 1.
  */
 int ssg_measure_fp64_rate(ssg_ctx *ctx, int32_t iters, int32_t reps, double *tflops, double *best_ms);
-int ssg_solve_batch(ssg_system *sys, const double *b, double *x, int32_t x_is_guess, double rtol, int32_t max_iter,
-                    int32_t mode, ssg_stats *stats);
 int ssg_get_sizes(const ssg_system *sys, ssg_sizes *out);
+/* The interior slice layout a system got (ssg_set_slice_sort): out[0] =
+ * entries stored in interior slices (padding included), out[1] = nonzeros
+ * they hold, out[2] = subdomains whose slices are sorted by row length,
+ * out[3] = the largest sorting window (1: none).  Host memory, 4 int64. */
+int ssg_get_layout(const ssg_system *sys, int64_t *out);
 
 /*
  * Copy the sub-structure maps into caller host buffers (any pointer may be

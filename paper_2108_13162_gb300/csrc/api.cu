@@ -55,6 +55,10 @@ struct ssg_system {
     Scal *d_scal_op = nullptr;  // state for the stand-alone SpMV / dot calls
     double *d_xg = nullptr, *d_bg = nullptr;  // global staging for ssg_solve_host
     int unroll = 4;     // iterations per pass of the single-vector loop bodies
+    // the interior slice layout (make_plan): entries stored with padding, real
+    // entries, subdomains sorted by row length, the largest sorting window
+    int64_t slice_slots = 0, slice_entries = 0;
+    int32_t sorted_subdomains = 0, max_window = 1;
     int grid_spmv = 0;
     int grid_spmv32 = 0;
     int grid_bps[6] = {0, 0, 0, 0, 0, 0};           // single-vector grids for 3, 4, 5 blocks per SM
@@ -174,6 +178,11 @@ struct WorkPlan {
     std::vector<int32_t> isrc, ssrc;  // local entry each copy-row / sliced value copies (-1: padding)
     std::vector<double> sval;        // sliced-ELL values
     std::vector<int32_t> scol, sseg;
+    std::vector<int32_t> srow;       // sorted slices: the local row of each slot
+    int64_t slice_slots = 0;         // interior slice entries stored (padding included)
+    int64_t slice_entries = 0;       // interior nonzeros in slices
+    int32_t sorted_subdomains = 0;   // subdomains whose interior slices are sorted by row length
+    int32_t max_window = 1;          // the largest sorting window used
     std::vector<WorkItem> items;
     std::vector<int2> range_bps[6];  // per warp of a single-vector launch sized for 3, 4 or 5 blocks per SM
     std::vector<int2> warp_rangeB;   // per warp of the K-vector product: cut inside each segment
@@ -186,7 +195,7 @@ struct WorkPlan {
 
 double item_cost(const WorkItem &w) {
     double cost = 64.0;
-    if (w.kind == kItemSlice || w.kind == kItemIfaceSlice) cost += 32.0 * w.e1;
+    if (sliced_item(w.kind)) cost += 32.0 * w.e1;
     else cost += 4.0 * (w.e1 - w.e0);
     return cost;
 }
@@ -215,8 +224,57 @@ std::vector<int2> cut_ranges(const std::vector<WorkItem> &items, int blocks) {
     return R;
 }
 
-// seg_sub: subdomains of each segment (independent systems), [nseg + 1].
-WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &seg_sub) {
+// Interior slice entries stored for rows lens[0..n) (runs of rows no longer
+// than kSliceMaxWidth) cut into windows of `win` rows sorted by decreasing
+// length, 32 rows per slice (win <= 1: no sorting).
+int64_t slice_slots_for(const std::vector<int32_t> &lens, int win) {
+    int64_t slots = 0;
+    const int n = static_cast<int>(lens.size());
+    const int step = win <= 1 ? n : win;
+    std::vector<int32_t> w;
+    for (int w0 = 0; w0 < n; w0 += std::max(step, 1)) {
+        w.assign(lens.begin() + w0, lens.begin() + std::min(n, w0 + std::max(step, 1)));
+        if (win > 1) std::stable_sort(w.begin(), w.end(), [](int32_t x, int32_t y) { return x > y; });
+        for (size_t i = 0; i < w.size(); i += kSliceRows)
+            slots += static_cast<int64_t>(kSliceRows) *
+                     *std::max_element(w.begin() + i, w.begin() + std::min(w.size(), i + kSliceRows));
+    }
+    return slots;
+}
+
+// Sorting window of subdomain s's interior rows.  policy: 1 = none, > 1 = a
+// window of that many rows, -1 = the whole subdomain, 0 = chosen from the
+// row lengths: the window of {1, 128, 256, 512} rows whose slices move the
+// fewest bytes, counting 12 bytes per stored entry (value and column) and,
+// for a sorted layout, 4 bytes per row for its row index; sorting is taken
+// only when it saves at least 2 % (its row indices scatter the stores).
+// Windows of at most 512 rows keep each slice's column gathers within a few
+// grid lines of the subdomain.
+int slice_window(const HostMaps &M, int32_t s, int policy) {
+    if (policy == 1) return 1;
+    if (policy == -1) return std::max<int32_t>(M.nint[s], 2);
+    if (policy > 1) return policy;
+    std::vector<int32_t> lens;
+    for (int64_t r = M.off[s]; r < M.off[s] + M.nint[s]; ++r) {
+        const int32_t L = M.lrowptr[r + 1] - M.lrowptr[r];
+        if (L <= kSliceMaxWidth) lens.push_back(L);
+    }
+    const double base = 12.0 * static_cast<double>(slice_slots_for(lens, 1));
+    int best = 1;
+    double best_bytes = base;
+    for (int win : {128, 256, 512}) {
+        const double b = 12.0 * static_cast<double>(slice_slots_for(lens, win)) + 4.0 * lens.size();
+        if (b < best_bytes) {
+            best = win;
+            best_bytes = b;
+        }
+    }
+    return best_bytes <= 0.98 * base ? best : 1;
+}
+
+// seg_sub: subdomains of each segment (independent systems), [nseg + 1];
+// sort_policy: the sorting window of the interior slices (slice_window).
+WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &seg_sub, int sort_policy) {
     WorkPlan W;
     std::vector<int32_t> sub_of(static_cast<size_t>(M.nloc));
     for (int32_t s = 0; s < M.P; ++s)
@@ -236,35 +294,70 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
     }
     W.sseg.assign(static_cast<size_t>(M.ncopies), 0);
     std::vector<WorkItem> rows, iface;
-    // interior slices
+    // interior slices: the rows no longer than kSliceMaxWidth, in runs
+    // between long rows; unsorted (window 1), a slice is 32 consecutive rows
+    // of a run; sorted, each window of a run is ordered by decreasing row
+    // length (ties in row order) and sliced 32 rows at a time, so that short
+    // rows stop padding to a long neighbour's width (SELL-C-sigma); its lanes
+    // find their rows in srow.  Padding entries: value 0, a column of the
+    // same subdomain.
+    std::vector<int32_t> order;
+    auto emit_slice = [&](const int32_t *rws, int32_t cnt, int32_t o, bool sorted) {
+        int32_t w = 0;
+        for (int32_t i = 0; i < cnt; ++i) w = std::max(w, rlen(rws[i]));
+        const int32_t off = static_cast<int32_t>(W.sval.size());
+        for (int32_t k = 0; k < w; ++k)
+            for (int32_t lane = 0; lane < kSliceRows; ++lane) {
+                const int32_t row = lane < cnt ? rws[lane] : rws[0];
+                if (lane < cnt && k < rlen(row)) {
+                    const int32_t e = M.lrowptr[row] + k;
+                    W.sval.push_back(M.lval[e]);
+                    W.scol.push_back(o + M.lcol[e]);
+                    W.ssrc.push_back(e);
+                    W.slice_entries++;
+                } else {
+                    W.sval.push_back(0.0);
+                    W.scol.push_back(row);
+                    W.ssrc.push_back(-1);
+                }
+            }
+        W.slice_slots += static_cast<int64_t>(w) * kSliceRows;
+        if (sorted) {
+            const int32_t slot0 = static_cast<int32_t>(W.srow.size());
+            W.srow.insert(W.srow.end(), rws, rws + cnt);
+            rows.push_back({kItemSortedSlice, slot0, slot0 + cnt, off, w, 0, 0, 0});
+        } else {
+            rows.push_back({kItemSlice, rws[0], rws[0] + cnt, off, w, 0, 0, 0});
+        }
+    };
     for (int32_t s = 0; s < M.P; ++s) {
         int32_t r = M.off[s];
         const int32_t rend = M.off[s] + M.nint[s];
         const int32_t o = M.off[s];
+        const int win = slice_window(M, s, sort_policy);
+        if (win > 1 && rend > r) {
+            W.sorted_subdomains++;
+            W.max_window = std::max(W.max_window, win);
+        }
         while (r < rend) {
             if (rlen(r) > kSliceMaxWidth) {
                 rows.push_back({kItemLongRow, r, r + 1, M.lrowptr[r], M.lrowptr[r + 1], 0, 0, 0});
                 ++r;
                 continue;
             }
-            int32_t r1 = r, w = 0;
-            while (r1 < rend && r1 - r < kSliceRows && rlen(r1) <= kSliceMaxWidth) w = std::max(w, rlen(r1++));
-            const int32_t off = static_cast<int32_t>(W.sval.size());
-            for (int32_t k = 0; k < w; ++k)
-                for (int32_t lane = 0; lane < kSliceRows; ++lane) {
-                    const int32_t row = r + lane;
-                    if (row < r1 && k < rlen(row)) {
-                        const int32_t e = M.lrowptr[row] + k;
-                        W.sval.push_back(M.lval[e]);
-                        W.scol.push_back(o + M.lcol[e]);
-                        W.ssrc.push_back(e);
-                    } else {
-                        W.sval.push_back(0.0);
-                        W.scol.push_back(row < r1 ? row : r);
-                        W.ssrc.push_back(-1);
-                    }
-                }
-            rows.push_back({kItemSlice, r, r1, off, w, 0, 0, 0});
+            int32_t r1 = r;
+            while (r1 < rend && rlen(r1) <= kSliceMaxWidth) ++r1;
+            const int32_t step = win > 1 ? win : kSliceRows;
+            for (int32_t w0 = r; w0 < r1; w0 += step) {
+                const int32_t w1 = std::min(r1, w0 + step);
+                order.resize(static_cast<size_t>(w1 - w0));
+                for (int32_t i = w0; i < w1; ++i) order[i - w0] = i;
+                if (win > 1)
+                    std::stable_sort(order.begin(), order.end(),
+                                     [&](int32_t x, int32_t y) { return rlen(x) > rlen(y); });
+                for (int32_t i = 0; i < w1 - w0; i += kSliceRows)
+                    emit_slice(order.data() + i, std::min<int32_t>(kSliceRows, w1 - w0 - i), o, win > 1);
+            }
             r = r1;
         }
     }
@@ -320,6 +413,7 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
     // nrows / (niface+1)) of the segment
     auto item_seg = [&](const WorkItem &w) {
         if (w.kind == kItemSlice || w.kind == kItemLongRow) return seg_of_sub[sub_of[w.a]];
+        if (w.kind == kItemSortedSlice) return seg_of_sub[sub_of[W.srow[w.a]]];
         const int32_t c = w.kind == kItemIfaceSlice ? w.a : w.c0;
         return seg_of_sub[sub_of[M.icopy[c]]];
     };
@@ -600,7 +694,11 @@ int upload(ssg_system *S) {
         S->seg_rhs_off = {0};
     }
     S->nseg = static_cast<int32_t>(S->seg_sub.size()) - 1;
-    WorkPlan plan = make_plan(M, C->num_sms, S->seg_sub);
+    WorkPlan plan = make_plan(M, C->num_sms, S->seg_sub, C->slice_sort);
+    S->slice_slots = plan.slice_slots;
+    S->slice_entries = plan.slice_entries;
+    S->sorted_subdomains = plan.sorted_subdomains;
+    S->max_window = plan.max_window;
     const int64_t N = M.nloc;
     // concatenated column ids
     std::vector<int32_t> gcol(static_cast<size_t>(M.nnz));
@@ -659,6 +757,7 @@ int upload(ssg_system *S) {
     size_t i_sval32 = add(sval32.data(), sizeof(float) * sval32.size());
     size_t i_scol = add(plan.scol.data(), sizeof(int32_t) * plan.scol.size());
     size_t i_sseg = add(plan.sseg.data(), sizeof(int32_t) * plan.sseg.size());
+    size_t i_srow = add(plan.srow.data(), sizeof(int32_t) * plan.srow.size());
     size_t i_items = add(plan.items.data(), sizeof(WorkItem) * plan.items.size());
     size_t i_range_bps[6] = {0, 0, 0, 0, 0, 0};
     for (int bps = 3; bps <= 5; ++bps)
@@ -776,6 +875,7 @@ int upload(ssg_system *S) {
     S->op.sval32 = static_cast<const float *>(at(i_sval32));
     S->op.scol = static_cast<const int32_t *>(at(i_scol));
     S->op.sseg = static_cast<const int32_t *>(at(i_sseg));
+    S->op.srow = static_cast<const int32_t *>(at(i_srow));
     S->op.items = static_cast<const WorkItem *>(at(i_items));
     for (int bps = 3; bps <= 5; ++bps) S->range_bps[bps] = static_cast<const int2 *>(at(i_range_bps[bps]));
     S->op.warp_range = S->range_bps[kSpmv64Variants[0].bps];
@@ -1562,6 +1662,15 @@ int ssg_set_driver(ssg_ctx *ctx, int driver) {
     return SSG_OK;
 }
 
+int ssg_set_slice_sort(ssg_ctx *ctx, int32_t window) {
+    if (!ctx || window < -1) {
+        set_error("ssg_set_slice_sort: null context, or window < -1");
+        return SSG_E_INVALID;
+    }
+    ctx->slice_sort = window;
+    return SSG_OK;
+}
+
 int ssg_set_unroll(ssg_ctx *ctx, int32_t iters) {
     if (!ctx || iters < 1 || iters > 8) {
         set_error("ssg_set_unroll: null context, or iterations per loop pass not in 1..8");
@@ -1625,6 +1734,14 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
             ssg_system_destroy(S);
             return rc;
         }
+    } else {
+        // host only: the interior slice layout the row-length rule gives
+        // (ssg_get_layout), without a device
+        const WorkPlan plan = make_plan(S->maps, 1, {0, S->maps.P}, 0);
+        S->slice_slots = plan.slice_slots;
+        S->slice_entries = plan.slice_entries;
+        S->sorted_subdomains = plan.sorted_subdomains;
+        S->max_window = plan.max_window;
     }
     *sys = S;
     return SSG_OK;
@@ -2128,6 +2245,18 @@ int ssg_solve_batch(ssg_system *S, const double *b, double *x, int32_t x_is_gues
     }
     if (rc != SSG_OK && rc != SSG_E_CUDA && rc != SSG_E_OOM && rc != SSG_E_INVALID) set_error(ssg_error_string(rc));
     return rc;
+}
+
+int ssg_get_layout(const ssg_system *S, int64_t *out) {
+    if (!S || !out) {
+        set_error("null argument");
+        return SSG_E_INVALID;
+    }
+    out[0] = S->slice_slots;
+    out[1] = S->slice_entries;
+    out[2] = S->sorted_subdomains;
+    out[3] = S->max_window;
+    return SSG_OK;
 }
 
 int ssg_get_sizes(const ssg_system *S, ssg_sizes *o) {

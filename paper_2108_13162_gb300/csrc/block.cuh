@@ -233,13 +233,14 @@ __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ 
         const WorkItem W = A.items[it];
         if (SpmmTraits<T>::kL2Ahead > 0 && it + SpmmTraits<T>::kL2Ahead < range.y) {
             const WorkItem Wp = A.items[it + SpmmTraits<T>::kL2Ahead];
-            if ((Wp.kind == kItemSlice || Wp.kind == kItemIfaceSlice) && lane < Wp.e1) {
+            if (sliced_item(Wp.kind) && lane < Wp.e1) {
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(sv + Wp.e0 + lane * kSliceRows));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
             }
         }
-        if (W.kind == kItemSlice || W.kind == kItemIfaceSlice) {
+        if (sliced_item(W.kind)) {
             const bool iface = W.kind == kItemIfaceSlice;
+            const bool sorted = W.kind == kItemSortedSlice;
             constexpr int NC = (sizeof(T) == 8 && K >= 8) ? 1 : 2;
             T acc[LPR][VW];
 #pragma unroll
@@ -255,8 +256,9 @@ __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ 
             for (int pass = 0; pass < LPR; ++pass) {
                 const int sr = pass * RPP + rl;
                 if (!iface) {
-                    const int r = W.a + sr;
-                    if (r < W.b) {
+                    const int slot = W.a + sr;
+                    if (slot < W.b) {
+                        const int r = sorted ? __ldg(A.srow + slot) : slot;
                         store_vec<VW>(Y + (size_t)r * K + col0, acc[pass]);
                         if (DOTS) {
                             T xr[VW];

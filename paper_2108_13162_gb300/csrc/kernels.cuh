@@ -97,11 +97,19 @@ enum { kTicketSpmv = 0, kTicketR = 1, kTicketXP = 2, kTicketMisc = 3 };
 //           nodes only, sliced-ELL data at e0, width e1
 //   kind 2: one interior row a longer than kSliceMaxWidth, CSR nonzeros [e0, e1)
 //   kind 3: one interface node a, copies [c0, c1), whose copy rows are too long
+//   kind 4: slice of interior rows taken from a window of one subdomain's
+//           rows sorted by length (SELL-C-sigma): lane l holds row srow[a + l]
+//           for a + l < b; sliced-ELL data at e0, width e1, as kind 0
 struct WorkItem {
     int32_t kind, a, b, e0, e1, c0, c1, pad;
 };
 
-enum { kItemSlice = 0, kItemIfaceSlice = 1, kItemLongRow = 2, kItemLongIface = 3 };
+enum { kItemSlice = 0, kItemIfaceSlice = 1, kItemLongRow = 2, kItemLongIface = 3, kItemSortedSlice = 4 };
+
+// Items streamed as sliced ELL (one row per lane).
+__host__ __device__ __forceinline__ bool sliced_item(int kind) {
+    return kind == kItemSlice || kind == kItemIfaceSlice || kind == kItemSortedSlice;
+}
 
 // Matrix-side arrays on the device (one arena, see api.cu).
 struct DevOp {
@@ -119,6 +127,7 @@ struct DevOp {
     const float *sval32;    // the same rounded to FP32
     const int32_t *scol;    // sliced-ELL columns (concatenated local index)
     const int32_t *sseg;    // interface slices, per copy: (lane of the node's first copy) | (m << 8)
+    const int32_t *srow;    // sorted slices: the local row of each slot
     const WorkItem *items;  // SpMV work list
     const int2 *warp_range;  // [grid * kSpmvWarps] contiguous item range of each warp
     const uint8_t *mult;    // [nloc] multiplicity of each local entry's node
@@ -358,6 +367,12 @@ __device__ __forceinline__ void finish_slice(const DevOp &A, const WorkItem &W, 
             y[r] = acc;
             dot = fma(__ldg(x + r), acc, dot);
         }
+    } else if (W.kind == kItemSortedSlice) {
+        if (W.a + lane < W.b) {
+            const int r = __ldg(A.srow + W.a + lane);
+            y[r] = acc;
+            dot = fma(__ldg(x + r), acc, dot);
+        }
     } else {
         const int c = W.a + lane;
         const bool valid = c < W.b;
@@ -398,12 +413,12 @@ __global__ void __launch_bounds__(kSpmvThreads, BPS)
         if (AHEAD > 0 && it + AHEAD < range.y) {
             // the value and column lines of a slice further ahead, one line per lane
             const WorkItem Wp = A.items[it + AHEAD];
-            if ((Wp.kind == kItemSlice || Wp.kind == kItemIfaceSlice) && lane < Wp.e1) {
+            if (sliced_item(Wp.kind) && lane < Wp.e1) {
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(sv + Wp.e0 + lane * kSliceRows));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
             }
         }
-        if (W.kind == kItemSlice || W.kind == kItemIfaceSlice) {
+        if (sliced_item(W.kind)) {
             const T acc = slice_row<T>(sv, A.scol, x, W.e0, W.e1, lane);
             finish_slice(A, W, acc, x, y, lane, dot);
         } else if (W.kind == kItemLongRow) {

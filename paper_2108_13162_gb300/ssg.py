@@ -71,6 +71,8 @@ EXPORTS = (
     "ssg_wdot_noalloc",
     "ssg_set_batch_graph",
     "ssg_measure_fp64_rate",
+    "ssg_set_slice_sort",
+    "ssg_get_layout",
     "ssg_band_split",
     "ssg_band_get",
     "ssg_band_spmv",
@@ -199,6 +201,8 @@ def lib():
         L.ssg_system_destroy.argtypes = [vp]
         L.ssg_wdot_noalloc.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
         L.ssg_set_batch_graph.argtypes = [vp, C.c_int32]
+        L.ssg_set_slice_sort.argtypes = [vp, C.c_int32]
+        L.ssg_get_layout.argtypes = [vp, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")]
         L.ssg_measure_fp64_rate.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                             C.POINTER(C.c_double)]
         L.ssg_band_split.argtypes = [vp, i32, i32, vp, vp, vp, i32, C.POINTER(vp)]
@@ -547,6 +551,18 @@ def ssg_measure_fp64_rate(ctx, iters: int = 20000, reps: int = 3):
     return t.value, ms.value
 
 
+def ssg_set_slice_sort(ctx, window: int):
+    return _check(lib().ssg_set_slice_sort(ctx, int(window)), "ssg_set_slice_sort")
+
+
+def ssg_get_layout(sys) -> dict:
+    """The interior slice layout of a system (see ssg.h)."""
+    out = np.zeros(4, np.int64)
+    _check(lib().ssg_get_layout(sys, out), "ssg_get_layout")
+    return {"slice_slots": int(out[0]), "slice_entries": int(out[1]), "sorted_subdomains": int(out[2]),
+            "max_window": int(out[3]), "padding_ratio": float(out[0]) / max(int(out[1]), 1)}
+
+
 def ssg_system_destroy(sys):
     return lib().ssg_system_destroy(sys)
 
@@ -593,6 +609,11 @@ class Context:
     def set_unroll(self, iters: int):
         """CG iterations per pass of a single-vector loop graph's body (systems partitioned afterwards)."""
         ssg_set_unroll(self.h, iters)
+
+    def set_slice_sort(self, window: int = 0):
+        """Interior slice layout: 0 auto, 1 none, > 1 sorting window, -1 whole subdomain
+        (systems partitioned afterwards)."""
+        ssg_set_slice_sort(self.h, window)
 
     def set_mixed(self, inner_rtol: float = 1e-4, max_outer: int = 30):
         ssg_set_mixed(self.h, inner_rtol, max_outer)
@@ -734,6 +755,9 @@ class System:
         out = self._empty_loc() if out is None else out
         ssg_spmv_assembled(self.h, x_loc, out, xSx)
         return out
+
+    def layout(self):
+        return ssg_get_layout(self.h)
 
     def autotune(self, reps=20):
         """Pick the fastest single-vector SpMV instances for this system."""

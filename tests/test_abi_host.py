@@ -200,3 +200,34 @@ def test_noalloc_dot_arguments_refused_before_launch(monkeypatch):
     for args, exc in bad:
         with pytest.raises(exc):
             ssg.ssg_wdot_noalloc(*args)
+
+
+def test_slice_layout_rule_from_row_lengths():
+    """The interior slice layout chosen from the row-length histogram (host
+    only): the jittered P1 mesh (rows of 3-9 entries) gets its rows sorted
+    by length in windows, which cuts the padding of 32-row slices from about
+    27 % to a few % (2 % on the 1024^2 mesh); the finite-volume and Poisson grids (rows of equal
+    length but at the boundary) stay unsorted."""
+    p = config_problem(3, scale=96)
+    S = ssg.System(None, p.A, p.part, p.P)
+    lay = S.layout()
+    assert lay["sorted_subdomains"] == p.P and lay["max_window"] in (128, 256, 512)
+    # (at this size a subdomain holds about 290 rows, and the part-empty
+    # last slice of each window weighs; the 1024^2 mesh gets about 1.02)
+    assert lay["slice_entries"] == _interior_nnz(p) and lay["padding_ratio"] < 1.10
+    S.close()
+    for q in (config_problem(2, scale=24), config_problem(1)):
+        S = ssg.System(None, q.A, q.part, q.P)
+        lay = S.layout()
+        assert lay["sorted_subdomains"] == 0 and lay["max_window"] == 1
+        assert lay["slice_entries"] == _interior_nnz(q) and lay["padding_ratio"] < 1.10
+        S.close()
+
+
+def _interior_nnz(p):
+    """Stored entries of the interior (multiplicity 1) rows of the local
+    matrices, from the oracle's maps."""
+    m = oracle.Partition(p.A, p.part, p.P).maps
+    lens = np.diff(m.lrowptr)
+    interior = np.concatenate([np.arange(m.off[s], m.off[s] + m.nint[s]) for s in range(m.P)])
+    return int(lens[interior].sum())

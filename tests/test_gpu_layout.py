@@ -1,0 +1,158 @@
+"""Interior slice layouts (ssg_set_slice_sort) through the C ABI: 32
+consecutive rows per slice, rows sorted by length in windows of 128 or 256
+rows or over a whole subdomain (SELL-C-sigma), and the row-length rule's
+choice.  Cases: the jittered P1 mesh (rows of 3-9 entries, uneven RCB
+subdomains), a random sparse matrix with irregular rows and a random
+partition, the same with a hub row longer than a slice, and the
+finite-volume grid.
+
+In every layout: the FP64 product within 4 (L_i + m_i) u (|A||x|)_i of the
+oracle's on every local entry (Section 3.4.1), and the FP64, FP32 and
+4-vector products bit-identical to the unsorted layout's (each row's entries
+keep their order, each interface node's copies their ascending order); a
+solve's first six iterates within 1e-10 of the oracle's, its iteration
+count at 1e-8 within max(2, 3 %) of the oracle's, and the mixed mode's FP64
+true residual <= rtol.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import CSR, config_problem, random_spd
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0**-53
+WINDOWS = [1, 128, 256, -1, 0]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    from paper_2108_13162_gb300 import build as ssg_build
+    from paper_2108_13162_gb300.ssg import Context
+
+    ssg_build.build()
+    c = Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def _t(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _hub(rng, n=3000):
+    """Random SPD rows plus one node coupled to 200 others (a row longer
+    than a slice: an item of its own in every layout)."""
+    A = random_spd(n, 7.0, rng)
+    import scipy.sparse as sp
+
+    M = A.to_scipy().tolil()
+    for j in range(1, 201):
+        M[0, 10 * j] = M[10 * j, 0] = -0.01
+        M[10 * j, 10 * j] += 0.01
+    M[0, 0] += 2.0
+    M = M.tocsr()
+    M.sort_indices()
+    return CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64))
+
+
+def _cases():
+    rng = np.random.default_rng(31)
+    out = []
+    p = config_problem(3, scale=128)
+    out.append(("fe2d_128_rcb64", p.A, p.part, p.P))
+    A = random_spd(4000, 8.0, rng)
+    out.append(("rand4000_P9", A, rng.integers(0, 9, A.n).astype(np.int32), 9))
+    A = _hub(rng)
+    out.append(("hub3000_P4", A, rng.integers(0, 4, A.n).astype(np.int32), 4))
+    p = config_problem(2, scale=24)
+    out.append(("fv3d_24", p.A, p.part, p.P))
+    return out
+
+
+CASES = _cases()
+
+
+def _systems(ctx, A, part, P):
+    from paper_2108_13162_gb300.ssg import System
+
+    out = {}
+    try:
+        for w in WINDOWS:
+            ctx.set_slice_sort(w)
+            out[w] = System(ctx, A, part, P)
+    finally:
+        ctx.set_slice_sort(0)
+    return out
+
+
+@pytest.mark.parametrize("name,A,part,P", CASES, ids=[c[0] for c in CASES])
+def test_layouts_same_products(ctx, name, A, part, P):
+    import torch
+
+    Ss = _systems(ctx, A, part, P)
+    ref = oracle.Partition(A, part, P)
+    m = ref.maps
+    rng = np.random.default_rng(7)
+    x = rng.uniform(-1, 1, A.n)
+    xl = ref.scatter(x)
+    X4 = np.stack([ref.scatter(rng.uniform(-1, 1, A.n)) for _ in range(4)], axis=1)
+    absAx = abs(A.to_scipy()) @ np.abs(x)
+    L = np.zeros(A.n)
+    np.maximum.at(L, m.l2g, np.diff(m.lrowptr))
+    bound = 4.0 * (L[m.l2g] + m.mult[m.l2g]) * U * absAx[m.l2g]
+    y_ref = ref.spmv(xl)
+    base = None
+    for w, S in Ss.items():
+        lay = S.layout()
+        if w == 1:
+            assert lay["sorted_subdomains"] == 0
+        elif w != 0:
+            assert lay["max_window"] >= 2 or lay["slice_entries"] == 0
+        y = S.spmv(_t(xl)).cpu().numpy()
+        assert np.all(np.abs(y - y_ref) <= bound), (w, float(np.max(np.abs(y - y_ref) - bound)))
+        y32 = torch.empty(S.sizes.nloc, dtype=torch.float32, device="cuda")
+        S.spmv_prec(_t(xl.astype(np.float32)), y32, "fp32")
+        Y = S.spmm(_t(X4)).cpu().numpy()
+        got = (y, y32.cpu().numpy(), Y)
+        if base is None:
+            base = got
+        else:
+            for a, b in zip(got, base):
+                assert np.array_equal(a, b), (name, w)
+    for S in Ss.values():
+        S.close()
+
+
+@pytest.mark.parametrize("name,A,part,P", CASES[:2], ids=[c[0] for c in CASES[:2]])
+def test_layouts_solves(ctx, name, A, part, P):
+    from paper_2108_13162_gb300 import ssg
+
+    Ss = _systems(ctx, A, part, P)
+    ref = oracle.Partition(A, part, P)
+    b = np.random.default_rng(9).uniform(-1, 1, A.n)
+    x6 = ref.cg(b, 0.0, 6).x
+    r8 = ref.cg(b, 1e-8, 100000)
+    for w, S in Ss.items():
+        x, rc, st = S.solve(_t(b), rtol=0.0, max_iter=6)
+        assert _rel(x.cpu().numpy(), x6) <= 1e-10, w
+        x, rc, st = S.solve(_t(b), rtol=1e-8, max_iter=100000)
+        assert rc == ssg.SSG_OK
+        assert abs(st[0]["iters"] - r8.iters) <= max(2, 0.03 * r8.iters), (w, st[0]["iters"], r8.iters)
+        x, rc, st = S.solve(_t(b), rtol=1e-8, max_iter=100000, mode=ssg.SSG_MIXED)
+        assert rc == ssg.SSG_OK
+        tr = np.linalg.norm(b - oracle.spmv(A, x.cpu().numpy())) / np.linalg.norm(b)
+        assert tr <= 1.0001e-8, w
+    for S in Ss.values():
+        S.close()
