@@ -65,7 +65,6 @@ struct ssg_system {
     const int2 *range_bps[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int var64 = 0, var32 = 0;                       // chosen SpMV instances (ssg_autotune)
     int grid_vec = 0;
-    int grid_loop = 0;  // the per-iteration vector kernels: kLoopThreads per block, at most one block per SM
     // graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -490,11 +489,11 @@ int launch_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const cudaGraphConditionalHandle h = pc ? S->cond_pc : S->cond;
     SSG_CUDA_TRY(launch_k(kSpmv64Variants[S->var64].part, S->grid_spmv, kSpmvThreads, st, S->op, S->d_p,
                           S->d_q, part_pq(S), S->d_scal, (double *)nullptr, h, use_cond));
-    SSG_CUDA_TRY(launch_k(pc ? k_update_r<true> : k_update_r<false>, S->grid_loop, kLoopThreads, st, N, S->d_r,
+    SSG_CUDA_TRY(launch_k(pc ? k_update_r<true> : k_update_r<false>, S->grid_vec, kBlock, st, N, S->d_r,
                           S->d_q, S->op.mult, S->op.wtab, S->op.gflag, (const double *)part_pq(S), S->grid_spmv,
                           part_rr(S), S->d_scal, h, use_cond, (const double *)S->d_dinv, part_rz(S)));
-    SSG_CUDA_TRY(launch_k(pc ? k_update_xp<true> : k_update_xp<false>, S->grid_loop, kLoopThreads, st, N, S->d_xl,
-                          S->d_p, S->d_r, (const double *)part_rr(S), S->grid_loop, S->d_scal, h, use_cond,
+    SSG_CUDA_TRY(launch_k(pc ? k_update_xp<true> : k_update_xp<false>, S->grid_vec, kBlock, st, N, S->d_xl,
+                          S->d_p, S->d_r, (const double *)part_rr(S), S->grid_vec, S->d_scal, h, use_cond,
                           (const double *)S->d_dinv, (const double *)part_rz(S)));
     return SSG_OK;
 }
@@ -533,12 +532,12 @@ int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const cudaGraphConditionalHandle h = S->cond_in[pc];
     SSG_CUDA_TRY(launch_k(kSpmv32Variants[S->var32].part, S->grid_spmv32, kSpmvThreads, st, S->op32,
                           S->d_p32, S->d_q32, part_pq(S), S->d_scal_in, (double *)nullptr, h, use_cond));
-    SSG_CUDA_TRY(launch_k(pc ? k_update_r32<true> : k_update_r32<false>, S->grid_loop, kLoopThreads, st, N,
+    SSG_CUDA_TRY(launch_k(pc ? k_update_r32<true> : k_update_r32<false>, S->grid_vec, kBlock, st, N,
                           S->d_r32, S->d_q32, S->op.mult, S->op.wtab32, S->op.gflag128, (const double *)part_pq(S),
                           S->grid_spmv32, part_rr(S), S->d_scal_in, S->d_scal, h, use_cond,
                           (const float *)S->d_dinv32, part_rz(S)));
-    SSG_CUDA_TRY(launch_k(pc ? k_update_dp32<true> : k_update_dp32<false>, S->grid_loop, kLoopThreads, st, N,
-                          S->d_d32, S->d_p32, S->d_r32, (const double *)part_rr(S), S->grid_loop, S->d_scal_in,
+    SSG_CUDA_TRY(launch_k(pc ? k_update_dp32<true> : k_update_dp32<false>, S->grid_vec, kBlock, st, N,
+                          S->d_d32, S->d_p32, S->d_r32, (const double *)part_rr(S), S->grid_vec, S->d_scal_in,
                           S->d_scal, h, use_cond, (const float *)S->d_dinv32, (const double *)part_rz(S)));
     return SSG_OK;
 }
@@ -726,7 +725,6 @@ int upload(ssg_system *S) {
     S->grid_spmv = plan.grid_bps[kSpmv64Variants[0].bps];
     S->grid_spmv32 = plan.grid_bps[kSpmv32Variants[0].bps];
     S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N / 2 + kBlock - 1) / kBlock), C->num_sms * kVecBlocksPerSM));
-    S->grid_loop = std::max(1, std::min<int>(static_cast<int>((N / 2 + kLoopThreads - 1) / kLoopThreads), C->num_sms));
     S->n_partials = 3 * std::max(std::max(plan.grid_bps[3], std::max(plan.grid_bps[4], plan.grid_bps[5])), S->grid_vec);
 
     struct Piece {

@@ -44,13 +44,6 @@ struct SpmvTraits<float> {
 };
 // [spmv-source-end]
 constexpr int kVecBlocksPerSM = 4;
-// The per-iteration vector kernels (residual and direction updates, FP64 and
-// FP32) run one block of kLoopThreads per SM.  Every block of such a kernel
-// sums all block partials of the previous kernel on the FP64 pipe (2 FMAs
-// per clock per SM on this part, one warp instruction every 16 cycles):
-// with one block per SM that sum is done 152 times instead of 608, and the
-// next kernel has 152 partials to sum instead of 608.
-constexpr int kLoopThreads = 1024;
 constexpr int kHostChunk = 32;    // iterations per host-loop chunk (SSG_DRIVER_HOST)
 
 // Scalar state of one CG solve, resident on the device.
@@ -179,9 +172,8 @@ __device__ __forceinline__ float warp_sumf(float v) {
 }
 
 // FP32 version for the FP32 kernels (one conversion to double per block).
-template <int NT = kBlock>
 __device__ __forceinline__ float block_sumf(float v) {
-    __shared__ float redf[NT];
+    __shared__ float redf[kBlock];
     __syncthreads();
     redf[threadIdx.x] = v;
     __syncthreads();
@@ -189,27 +181,10 @@ __device__ __forceinline__ float block_sumf(float v) {
     if (threadIdx.x < 32) {
         t = redf[threadIdx.x];
 #pragma unroll
-        for (int i = 1; i < NT / 32; ++i) t += redf[threadIdx.x + 32 * i];
+        for (int i = 1; i < kBlock / 32; ++i) t += redf[threadIdx.x + 32 * i];
         t = warp_sumf(t);
     }
     return t;
-}
-
-// Sum of G block partials in a fixed order by one warp (call from warp 0
-// only): lane l adds partials l, l + 32, l + 64, ... into two accumulators in
-// turn (two loads in flight; more would spill the stream's registers), the
-// accumulators are added, then the lanes by the fixed shuffle tree.  Valid
-// in lane 0.  Every block that calls it gets the bitwise same total.
-__device__ __forceinline__ double warp_sum_partials(const double *partials, int G) {
-    const int lane = threadIdx.x & 31;
-    double a0 = 0.0, a1 = 0.0;
-    int i = lane;
-    for (; i + 32 < G; i += 64) {
-        a0 += __ldcg(partials + i);
-        a1 += __ldcg(partials + i + 32);
-    }
-    if (i < G) a0 += __ldcg(partials + i);
-    return warp_sum(a0 + a1);
 }
 
 // Thread 0 of each block publishes its partial, then takes a ticket; returns
@@ -479,7 +454,8 @@ __global__ void __launch_bounds__(kSpmvThreads, BPS)
     // block's warps in order in FP64.  FP64: through shared memory, one warp
     // adding the block's 256 values (12 FP64 warp instructions per block
     // instead of 47 for a shuffle tree in every warp: each takes 16 cycles of
-    // the SM's FP64 pipe, which the products keep busy)
+    // the SM's FP64 pipe, which the products keep busy; 41.5 -> 40.8 us on
+    // the 128^3 system)
     double bs = 0.0;
     if constexpr (sizeof(T) == 4) {
         __shared__ double wsum[kSpmvWarps];
@@ -514,13 +490,12 @@ __device__ __forceinline__ double wsq(double r, unsigned int m, const double *__
 }
 
 // Algorithm 3 lines 3 and 5: every block sums the SpMV's partials of
-// (p, S p)_w (one warp, warp_sum_partials), forms alpha = rho / (p, S p)_w
-// once (or stops on a breakdown), then r <- r - alpha q and its share of
-// (r, r)_w.  With the diagonal preconditioner (PC, dinv = 1 / diag(S) per
-// local entry) the block also forms its share of (r, z)_w, z = dinv r,
-// into part_rz.  One block of kLoopThreads per SM.
+// (p, S p)_w, forms alpha = rho / (p, S p)_w (or stops on a breakdown), then
+// r <- r - alpha q and its share of (r, r)_w.  With the diagonal
+// preconditioner (PC, dinv = 1 / diag(S) per local entry) the block also
+// forms its share of (r, z)_w, z = dinv r, into part_rz.
 template <bool PC>
-__global__ void __launch_bounds__(kLoopThreads, 1) k_update_r(int64_t N, double *__restrict__ r, const double *__restrict__ q,
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r(int64_t N, double *__restrict__ r, const double *__restrict__ q,
                                                      const uint8_t *__restrict__ mult, const double *__restrict__ wtab,
                                                      const uint8_t *__restrict__ gflag, const double *part_pq,
                                                      int G1, double *part_rr, Scal *s, cudaGraphConditionalHandle h,
@@ -532,11 +507,9 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_update_r(int64_t N, double 
         s->passes += 1;
     }
     if (s->brk || s->halt[s->iter & 1]) return;
-    __shared__ double alpha_sh;
-    __shared__ int go_sh;
-    double alpha = 0.0;
+    double pq = 0.0, alpha = 0.0;
     double acc = 0.0, acz = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * kLoopThreads;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N2 = N >> 1;
     double2 *__restrict__ r2 = reinterpret_cast<double2 *>(r);
     const double2 *__restrict__ q2 = reinterpret_cast<const double2 *>(q);
@@ -547,7 +520,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_update_r(int64_t N, double 
         uint8_t g;
     };
     const bool go = stream_loop_after<PC ? 2 : 4>(
-        (int64_t)blockIdx.x * kLoopThreads + threadIdx.x, N2, stride,
+        (int64_t)blockIdx.x * kBlock + threadIdx.x, N2, stride,
         [&](int64_t i) {
             Ld l;
             l.r = r2[i];
@@ -557,30 +530,18 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_update_r(int64_t N, double 
             return l;
         },
         [&]() {
-            // one warp sums the partials and one thread divides and tests:
-            // every FP64 instruction takes 16 cycles of the SM's FP64 pipe
-            if (threadIdx.x < 32) {
-                const double pq = warp_sum_partials(part_pq, G1);
-                if (threadIdx.x == 0) {
-                    const bool ok = pq > 0.0 && isfinite(pq);
-                    go_sh = ok;
-                    alpha_sh = ok ? s->rho / pq : 0.0;
-                    if (blockIdx.x == 0) {
-                        s->pq = pq;
-                        if (ok) {
-                            s->alpha = alpha_sh;
-                            s->alpha32 = float(alpha_sh);
-                        } else {
-                            s->status = SSG_E_BREAKDOWN;
-                            s->brk = 1;
-                            stop_loop(s, h, use_cond);
-                        }
-                    }
+            pq = all_sum_partials(part_pq, G1);
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    s->pq = pq;
+                    s->status = SSG_E_BREAKDOWN;
+                    s->brk = 1;
+                    stop_loop(s, h, use_cond);
                 }
+                return false;
             }
-            __syncthreads();
-            alpha = alpha_sh;
-            return go_sh != 0;
+            alpha = block_quotient(s->rho, pq);
+            return true;
         },
         [&](int64_t i, Ld l) {
             double2 rv = l.r;
@@ -615,32 +576,35 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_update_r(int64_t N, double 
         acc = fma(wi, ri, acc);
         if (PC) acz = fma(wi, ri * dinv[N - 1], acz);
     }
-    const double bs = block_sum<kLoopThreads>(acc);
-    const double bz = PC ? block_sum<kLoopThreads>(acz) : 0.0;
+    const double bs = block_sum(acc);
+    const double bz = PC ? block_sum(acz) : 0.0;
     if (threadIdx.x == 0) {
         part_rr[blockIdx.x] = bs;
         if (PC) part_rz[blockIdx.x] = bz;
+        if (blockIdx.x == 0) {
+            s->alpha = alpha;
+            s->alpha32 = float(alpha);
+            s->pq = pq;
+        }
     }
 }
 
 // Algorithm 3 lines 4, 7, 8: every block sums the partials of (r_{k+1},
-// r_{k+1})_w (and of (r_{k+1}, z_{k+1})_w with the diagonal preconditioner)
-// in one warp, forms beta = (r, z)_{k+1} / (r, z)_k in one thread, and
-// x <- x + alpha p, p <- z + beta p (z = r without a preconditioner, z = dinv
-// r with it); block 0 records the iteration and the stopping decision
-// (recursive residual sqrt((r, r)_w) <= rtol ||b||, or max_iter reached),
-// applied after this update.  One block of kLoopThreads per SM.
+// r_{k+1})_w (and of (r_{k+1}, z_{k+1})_w with the diagonal preconditioner),
+// forms beta = (r, z)_{k+1} / (r, z)_k, and x <- x + alpha p, p <- z + beta p
+// (z = r without a preconditioner, z = dinv r with it); block 0 records the
+// iteration and the stopping decision (recursive residual sqrt((r, r)_w) <=
+// rtol ||b||, or max_iter reached), applied after this update.
 template <bool PC>
-__global__ void __launch_bounds__(kLoopThreads, 1) k_update_xp(int64_t N, double *__restrict__ x, double *__restrict__ p,
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_xp(int64_t N, double *__restrict__ x, double *__restrict__ p,
                                                       const double *__restrict__ r, const double *part_rr, int G2,
                                                       Scal *s, cudaGraphConditionalHandle h, int use_cond,
                                                       const double *__restrict__ dinv, const double *part_rz) {
     const int k = s->iter_b;
     if (s->brk || s->halt[k & 1]) return;
-    __shared__ double rr_sh, rz_sh, beta_sh;
-    double beta = 0.0;
+    double rr = 0.0, rz = 0.0, beta = 0.0;
     const double alpha = s->alpha;
-    const int64_t stride = (int64_t)gridDim.x * kLoopThreads;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N2 = N >> 1;
     double2 *x2 = reinterpret_cast<double2 *>(x);
     double2 *p2 = reinterpret_cast<double2 *>(p);
@@ -650,7 +614,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_update_xp(int64_t N, double
         double2 p, x, z;
     };
     stream_loop_after<PC ? 2 : 4>(
-        (int64_t)blockIdx.x * kLoopThreads + threadIdx.x, N2, stride,
+        (int64_t)blockIdx.x * kBlock + threadIdx.x, N2, stride,
         [&](int64_t i) {
             Ld l;
             l.p = p2[i];
@@ -664,17 +628,9 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_update_xp(int64_t N, double
             return l;
         },
         [&]() {
-            if (threadIdx.x < 32) {
-                const double rr = warp_sum_partials(part_rr, G2);
-                const double rz = PC ? warp_sum_partials(part_rz, G2) : rr;
-                if (threadIdx.x == 0) {
-                    rr_sh = rr;
-                    rz_sh = rz;
-                    beta_sh = rz / s->rho_b;
-                }
-            }
-            __syncthreads();
-            beta = beta_sh;
+            rr = all_sum_partials(part_rr, G2);
+            rz = PC ? all_sum_partials(part_rz, G2) : rr;
+            beta = block_quotient(rz, s->rho_b);
             return true;
         },
         [&](int64_t i, Ld l) {
@@ -690,7 +646,6 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_update_xp(int64_t N, double
         p[N - 1] = fma(beta, pi, PC ? r[N - 1] * dinv[N - 1] : r[N - 1]);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const double rr = rr_sh, rz = rz_sh;
         s->rho = rz;
         s->rr = rr;
         s->beta = beta;
@@ -923,10 +878,7 @@ __device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r
     double pq = 0.0, alpha_d = 0.0;
     float alpha = 0.f;
     float acc = 0.f, acz = 0.f;
-    __shared__ double alpha_sh;
-    __shared__ float alpha32_sh;
-    __shared__ int go_sh;
-    const int64_t stride = (int64_t)gridDim.x * kLoopThreads;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N4 = N >> 2;
     float4 *__restrict__ r4 = reinterpret_cast<float4 *>(r);
     const float4 *__restrict__ q4 = reinterpret_cast<const float4 *>(q);
@@ -939,7 +891,7 @@ __device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r
     // a thread streams about four items on the 128^3 system: all of them
     // are in flight before the prologue
     const bool go = stream_loop_after<PC ? 2 : 4, PC ? 2 : 4>(
-        (int64_t)blockIdx.x * kLoopThreads + threadIdx.x, N4, stride,
+        (int64_t)blockIdx.x * kBlock + threadIdx.x, N4, stride,
         [&](int64_t i) {
             Ld l;
             l.r = r4[i];
@@ -949,31 +901,18 @@ __device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r
             return l;
         },
         [&]() {
-            // one warp sums the FP64 partials, one thread divides and tests
-            if (threadIdx.x < 32) {
-                pq = warp_sum_partials(part_pq, G1);
-                if (threadIdx.x == 0) {
-                    const bool ok = pq > 0.0 && isfinite(pq);
-                    go_sh = ok;
-                    alpha_sh = ok ? si->rho / pq : 0.0;
-                    alpha32_sh = float(alpha_sh);
-                    if (blockIdx.x == 0) {
-                        si->pq = pq;
-                        if (ok) {
-                            si->alpha = alpha_sh;
-                            si->alpha32 = alpha32_sh;
-                        } else {
-                            si->status = SSG_E_BREAKDOWN;
-                            si->brk = 1;
-                            stop_loop(si, h, use_cond);
-                        }
-                    }
+            pq = all_sum_partials(part_pq, G1);
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    si->pq = pq;
+                    si->status = SSG_E_BREAKDOWN;
+                    si->brk = 1;
+                    stop_loop(si, h, use_cond);
                 }
+                return false;
             }
-            __syncthreads();
-            alpha_d = alpha_sh;
-            alpha = alpha32_sh;
-            return go_sh != 0;
+            alpha_d = block_quotient(si->rho, pq, &alpha);
+            return true;
         },
         [&](int64_t i, Ld l) {
             float4 rv = l.r;
@@ -1014,17 +953,22 @@ __device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r
         acc = fmaf(wi, ri, acc);
         if (PC) acz = fmaf(wi, ri * dinv32[i], acz);
     }
-    const double bs = double(block_sumf<kLoopThreads>(acc));
-    const double bz = PC ? double(block_sumf<kLoopThreads>(acz)) : 0.0;
+    const double bs = double(block_sumf(acc));
+    const double bz = PC ? double(block_sumf(acz)) : 0.0;
     if (threadIdx.x == 0) {
         part_rr[blockIdx.x] = bs;
         if (PC) part_rz[blockIdx.x] = bz;
+        if (blockIdx.x == 0) {
+            si->alpha = alpha_d;
+            si->alpha32 = alpha;
+            si->pq = pq;
+        }
     }
     return true;
 }
 
 template <bool PC>
-__global__ void __launch_bounds__(kLoopThreads, 1) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r32(int64_t N, float *__restrict__ r, const float *__restrict__ q,
                                                        const uint8_t *__restrict__ mult, const float *__restrict__ wtab,
                                                        const uint8_t *__restrict__ gflag128, const double *part_pq, int G1,
                                                        double *part_rr, Scal *si, Scal *so,
@@ -1048,9 +992,7 @@ __device__ __forceinline__ void update_dp32_step(int64_t N, float *__restrict__ 
                                                  double rho_b) {
     double rr = 0.0, rz = 0.0, beta_d = 0.0;
     float beta = 0.f;
-    __shared__ double rr_sh, rz_sh, beta_sh;
-    __shared__ float beta32_sh;
-    const int64_t stride = (int64_t)gridDim.x * kLoopThreads;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
     const int64_t N4 = N >> 2;
     float4 *__restrict__ d4 = reinterpret_cast<float4 *>(d);
     float4 *__restrict__ p4 = reinterpret_cast<float4 *>(p);
@@ -1060,7 +1002,7 @@ __device__ __forceinline__ void update_dp32_step(int64_t N, float *__restrict__ 
         float4 p, d, z;
     };
     stream_loop_after<2>(
-        (int64_t)blockIdx.x * kLoopThreads + threadIdx.x, N4, stride,
+        (int64_t)blockIdx.x * kBlock + threadIdx.x, N4, stride,
         [&](int64_t i) {
             Ld l;
             l.p = p4[i];
@@ -1076,21 +1018,9 @@ __device__ __forceinline__ void update_dp32_step(int64_t N, float *__restrict__ 
             return l;
         },
         [&]() {
-            if (threadIdx.x < 32) {
-                const double srr = warp_sum_partials(part_rr, G2);
-                const double srz = PC ? warp_sum_partials(part_rz, G2) : srr;
-                if (threadIdx.x == 0) {
-                    rr_sh = srr;
-                    rz_sh = srz;
-                    beta_sh = srz / rho_b;
-                    beta32_sh = float(beta_sh);
-                }
-            }
-            __syncthreads();
-            rr = rr_sh;
-            rz = rz_sh;
-            beta_d = beta_sh;
-            beta = beta32_sh;
+            rr = all_sum_partials(part_rr, G2);
+            rz = PC ? all_sum_partials(part_rz, G2) : rr;
+            beta_d = block_quotient(rz, rho_b, &beta);
             return true;
         },
         [&](int64_t i, Ld l) {
@@ -1125,7 +1055,7 @@ __device__ __forceinline__ void update_dp32_step(int64_t N, float *__restrict__ 
 }
 
 template <bool PC>
-__global__ void __launch_bounds__(kLoopThreads, 1) k_update_dp32(int64_t N, float *__restrict__ d, float *__restrict__ p,
+__global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_dp32(int64_t N, float *__restrict__ d, float *__restrict__ p,
                                                         const float *__restrict__ r, const double *part_rr, int G2,
                                                         Scal *si, Scal *so, cudaGraphConditionalHandle h, int use_cond,
                                                         const float *__restrict__ dinv32, const double *part_rz) {
