@@ -301,15 +301,16 @@ int ssg_spmv_assembled_f32(ssg_system *sys, const float *x_loc, float *y_loc, do
 /* Result of ssg_autotune: per precision, the launch shape (blocks per SM)
  * and L2 prefetch distance of every candidate, its mean launch time, and the
  * index chosen. */
+#define SSG_TUNE_CANDIDATES 6
 typedef struct {
     int32_t fp64_choice, fp32_choice;
-    int32_t fp64_blocks_per_sm[4], fp64_l2_ahead[4];
-    int32_t fp32_blocks_per_sm[4], fp32_l2_ahead[4];
-    double fp64_us[4], fp32_us[4];
+    int32_t fp64_blocks_per_sm[SSG_TUNE_CANDIDATES], fp64_l2_ahead[SSG_TUNE_CANDIDATES];
+    int32_t fp32_blocks_per_sm[SSG_TUNE_CANDIDATES], fp32_l2_ahead[SSG_TUNE_CANDIDATES];
+    double fp64_us[SSG_TUNE_CANDIDATES], fp32_us[SSG_TUNE_CANDIDATES];
 } ssg_tune;
 /*
- * Time the single-vector SpMV instances (launch shapes of 3 to 5 blocks per
- * SM, L2 prefetch of the next slices on or off; four per precision) on this
+ * Time the single-vector SpMV instances (launch shapes of 3 to 6 blocks per
+ * SM, L2 prefetch of the next slices on or off; six per precision) on this
  * system as the solver loop launches them (block partials, no last-block
  * sum), reps launches each (reps <= 0: 20), and use the fastest for the
  * following solves and products.  The choice changes only the order of the

@@ -111,16 +111,19 @@ class ssg_stats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+TUNE_CANDIDATES = 6  # SSG_TUNE_CANDIDATES
+
+
 class ssg_tune(C.Structure):
     _fields_ = [
         ("fp64_choice", C.c_int32),
         ("fp32_choice", C.c_int32),
-        ("fp64_blocks_per_sm", C.c_int32 * 4),
-        ("fp64_l2_ahead", C.c_int32 * 4),
-        ("fp32_blocks_per_sm", C.c_int32 * 4),
-        ("fp32_l2_ahead", C.c_int32 * 4),
-        ("fp64_us", C.c_double * 4),
-        ("fp32_us", C.c_double * 4),
+        ("fp64_blocks_per_sm", C.c_int32 * TUNE_CANDIDATES),
+        ("fp64_l2_ahead", C.c_int32 * TUNE_CANDIDATES),
+        ("fp32_blocks_per_sm", C.c_int32 * TUNE_CANDIDATES),
+        ("fp32_l2_ahead", C.c_int32 * TUNE_CANDIDATES),
+        ("fp64_us", C.c_double * TUNE_CANDIDATES),
+        ("fp32_us", C.c_double * TUNE_CANDIDATES),
     ]
 
     def as_dict(self):

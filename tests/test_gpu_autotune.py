@@ -58,7 +58,8 @@ def test_autotuned_parity(ctx, case):
     _, A, part, P, b = case
     S = System(ctx, A, part, P)
     t = S.autotune(reps=5)
-    assert 0 <= t["fp64_choice"] < 4 and 0 <= t["fp32_choice"] < 4
+    assert 0 <= t["fp64_choice"] < ssg.TUNE_CANDIDATES and 0 <= t["fp32_choice"] < ssg.TUNE_CANDIDATES
+    assert len(t["fp64_us"]) == len(t["fp32_us"]) == ssg.TUNE_CANDIDATES
     assert all(v > 0 for v in t["fp64_us"] + t["fp32_us"])
     assert t["fp64_us"][t["fp64_choice"]] == min(t["fp64_us"])
     ref = oracle.Partition(A, part, P)
