@@ -222,16 +222,6 @@ __device__ __forceinline__ double all_sum_partials(const double *partials, int G
     return bc;
 }
 
-// Sum of G block partials by warp 0 alone (lane l adds partials l, l + 32,
-// ... in order, then the fixed shuffle tree; valid in lane 0), so that the
-// per-block sum takes G / 32 + 5 FP64 warp instructions and no barrier; every
-// block gets the bitwise same total.
-__device__ __forceinline__ double warp0_sum_partials(const double *partials, int G) {
-    double a = 0.0;
-    for (int i = threadIdx.x & 31; i < G; i += 32) a += __ldcg(partials + i);
-    return warp_sum(a);
-}
-
 // num / den formed once by thread 0 and handed to the block: an FP64 division
 // is a sequence of FP64 instructions, and every thread of every block
 // dividing on its own kept the FP64 pipe (2 operations per clock per SM)
@@ -540,29 +530,18 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_r(int64_t N,
             return l;
         },
         [&]() {
-            // warp 0 sums the partials, thread 0 tests and divides, one
-            // barrier hands alpha out (each FP64 instruction costs the SM's
-            // FP64 pipe 16 cycles, so none is repeated per thread)
-            __shared__ double alpha_sh;
-            __shared__ int go_sh;
-            if (threadIdx.x < 32) {
-                const double t = warp0_sum_partials(part_pq, G1);
-                if (threadIdx.x == 0) {
-                    const bool ok = t > 0.0 && isfinite(t);
-                    go_sh = ok;
-                    alpha_sh = ok ? s->rho / t : 0.0;
-                    if (!ok && blockIdx.x == 0) {
-                        s->pq = t;
-                        s->status = SSG_E_BREAKDOWN;
-                        s->brk = 1;
-                        stop_loop(s, h, use_cond);
-                    }
-                    pq = t;
+            pq = all_sum_partials(part_pq, G1);
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    s->pq = pq;
+                    s->status = SSG_E_BREAKDOWN;
+                    s->brk = 1;
+                    stop_loop(s, h, use_cond);
                 }
+                return false;
             }
-            __syncthreads();
-            alpha = alpha_sh;
-            return go_sh != 0;
+            alpha = block_quotient(s->rho, pq);
+            return true;
         },
         [&](int64_t i, Ld l) {
             double2 rv = l.r;
@@ -649,14 +628,9 @@ __global__ void __launch_bounds__(kBlock, kVecBlocksPerSM) k_update_xp(int64_t N
             return l;
         },
         [&]() {
-            __shared__ double beta_sh;
-            if (threadIdx.x < 32) {
-                rr = warp0_sum_partials(part_rr, G2);
-                rz = PC ? warp0_sum_partials(part_rz, G2) : rr;
-                if (threadIdx.x == 0) beta_sh = rz / s->rho_b;
-            }
-            __syncthreads();
-            beta = beta_sh;
+            rr = all_sum_partials(part_rr, G2);
+            rz = PC ? all_sum_partials(part_rz, G2) : rr;
+            beta = block_quotient(rz, s->rho_b);
             return true;
         },
         [&](int64_t i, Ld l) {
@@ -927,30 +901,18 @@ __device__ __forceinline__ bool update_r32_step(int64_t N, float *__restrict__ r
             return l;
         },
         [&]() {
-            // warp 0 sums the FP64 partials, thread 0 tests and divides
-            __shared__ double alpha_sh;
-            __shared__ float alpha32_sh;
-            __shared__ int go_sh;
-            if (threadIdx.x < 32) {
-                const double t = warp0_sum_partials(part_pq, G1);
-                if (threadIdx.x == 0) {
-                    const bool ok = t > 0.0 && isfinite(t);
-                    go_sh = ok;
-                    alpha_sh = ok ? si->rho / t : 0.0;
-                    alpha32_sh = float(alpha_sh);
-                    if (!ok && blockIdx.x == 0) {
-                        si->pq = t;
-                        si->status = SSG_E_BREAKDOWN;
-                        si->brk = 1;
-                        stop_loop(si, h, use_cond);
-                    }
-                    pq = t;
+            pq = all_sum_partials(part_pq, G1);
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    si->pq = pq;
+                    si->status = SSG_E_BREAKDOWN;
+                    si->brk = 1;
+                    stop_loop(si, h, use_cond);
                 }
+                return false;
             }
-            __syncthreads();
-            alpha_d = alpha_sh;
-            alpha = alpha32_sh;
-            return go_sh != 0;
+            alpha_d = block_quotient(si->rho, pq, &alpha);
+            return true;
         },
         [&](int64_t i, Ld l) {
             float4 rv = l.r;
@@ -1056,19 +1018,9 @@ __device__ __forceinline__ void update_dp32_step(int64_t N, float *__restrict__ 
             return l;
         },
         [&]() {
-            __shared__ double beta_sh;
-            __shared__ float beta32_sh;
-            if (threadIdx.x < 32) {
-                rr = warp0_sum_partials(part_rr, G2);
-                rz = PC ? warp0_sum_partials(part_rz, G2) : rr;
-                if (threadIdx.x == 0) {
-                    beta_sh = rz / rho_b;
-                    beta32_sh = float(beta_sh);
-                }
-            }
-            __syncthreads();
-            beta_d = beta_sh;
-            beta = beta32_sh;
+            rr = all_sum_partials(part_rr, G2);
+            rz = PC ? all_sum_partials(part_rz, G2) : rr;
+            beta_d = block_quotient(rz, rho_b, &beta);
             return true;
         },
         [&](int64_t i, Ld l) {
