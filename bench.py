@@ -325,7 +325,8 @@ def bench_multi_rhs(ctx, stream, reps, spmv_reps, fp64_peak=None):
     B = torch.from_numpy(p.b.T.copy()).cuda()
     X = torch.zeros_like(B)
     out = {"workload": "fv3d_7pt_96^3_kappa=exp(N(0,1))_3x3x3_subdomains_16rhs", "n": p.A.n, "nnz": p.A.nnz,
-           "nloc": S.sizes.nloc, "rhs": B.shape[0], "rtol": RTOL}
+           "nloc": S.sizes.nloc, "rhs": B.shape[0], "rtol": RTOL,
+           "autotune_block": S.autotune_block(16, reps=10)}
     for mode_name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED), ("jacobi", ssg.SSG_FP64_JACOBI),
                             ("mixed_jacobi", ssg.SSG_MIXED_JACOBI)):
         for kb in (16, 1):
@@ -410,11 +411,12 @@ def bench_batch(ctx, stream, reps, size):
     t0 = time.perf_counter()
     B = Batch(ctx, [(A, pt, P, b.shape[0]) for A, pt, P, b in zip(bp.A, bp.part, bp.P, bp.b)])
     setup_s = time.perf_counter() - t0
+    tune = B.autotune_block(reps=10)
     bb = torch.from_numpy(np.concatenate([b.ravel() for b in bp.b])).cuda()
     out = {"workload": "fv2d_5pt_batch512_side32-%d_sigma0.5_4-16subdomains_1-8rhs" % hi,
            "systems": len(bp.A), "unknowns": int(sum(A.n for A in bp.A)), "nnz": int(sum(A.nnz for A in bp.A)),
            "rhs": int(sum(b.shape[0] for b in bp.b)), "subdomains": int(sum(bp.P)), "rtol": RTOL,
-           "setup_s": setup_s}
+           "setup_s": setup_s, "autotune_block": tune}
     for mode_name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED), ("mixed_jacobi", ssg.SSG_MIXED_JACOBI)):
         x, rc, st = B.solve(bb, rtol=RTOL, mode=mode)
         torch.cuda.synchronize()

@@ -321,6 +321,30 @@ typedef struct {
  */
 int ssg_autotune(ssg_system *sys, int32_t reps, ssg_tune *out);
 
+/* Result of ssg_autotune_block: the column count tuned for, each
+ * candidate's entries loaded at once and L2 look-ahead, its mean launch time
+ * per precision, and the index chosen. */
+#define SSG_TUNE_BLOCK_CANDIDATES 6
+typedef struct {
+    int32_t k;
+    int32_t fp64_choice, fp32_choice;
+    int32_t nc[SSG_TUNE_BLOCK_CANDIDATES], l2_ahead[SSG_TUNE_BLOCK_CANDIDATES];
+    double fp64_us[SSG_TUNE_BLOCK_CANDIDATES], fp32_us[SSG_TUNE_BLOCK_CANDIDATES];
+} ssg_tune_block;
+/*
+ * Tune the product with k vectors (Section 3.4.1's SpMV with several
+ * right-hand sides; not in the paper) as ssg_solve and ssg_solve_batch launch
+ * it: sliced entries loaded at once per lane (1 or 2) x slices ahead whose
+ * lines are prefetched into L2 (0, 1, 2), timed in FP64 and FP32 (reps
+ * launches each, reps <= 0: 20), the fastest kept for the following solves
+ * with that k.  Neither changes the arithmetic: results are the same bits
+ * with every candidate.  A batch of systems tunes every column group for its
+ * own K (k is then ignored) and reports the group with the most columns.
+ * Allocates the K-column vectors if needed; blocks until done; graphs built
+ * earlier are rebuilt on the next solve.  SSG_E_INVALID for another k.
+ */
+int ssg_autotune_block(ssg_system *sys, int32_t k, int32_t reps, ssg_tune_block *out);
+
 /*
  * The sub-structured product of ssg_spmv_assembled with k vectors at once
  * (k = 2, 4, 8 or 16): x_loc and y_loc are device blocks of nloc*k doubles,

@@ -85,6 +85,10 @@ struct ssg_system {
     // several right-hand sides and independent systems together (block.cuh):
     // segments = independent systems (one for a system from ssg_partition)
     DevOp opB64{}, opB32{};  // K-vector product launches (warp ranges cut inside each segment)
+    // the K-vector product's entries loaded at once (1 or 2) and L2 look-ahead
+    // per precision (0: FP64, 1: FP32) and log2 K - 1 (ssg_autotune_block)
+    int8_t spmm_nc[2][4] = {{2, 2, 1, 1}, {2, 2, 2, 2}};
+    int8_t spmm_ahead[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
     int grid_spmmB = 0;
     int32_t nseg = 1, nchunks = 0;
     std::vector<int32_t> seg_sub, seg_node, seg_nrhs;  // [nseg+1], [nseg+1], [nseg]
@@ -1185,10 +1189,25 @@ int launch_initB(ssg_system *S, cudaStream_t st, double *p, cudaGraphConditional
     return SSG_OK;
 }
 
+constexpr int log2_cols(int K) { return K == 2 ? 0 : K == 4 ? 1 : K == 8 ? 2 : 3; }
+
+// The K-vector product of the solves with the chunk depth and L2 look-ahead
+// chosen for (precision, K); segs given: frozen segments' blocks return.
+template <typename T, int K, bool DOTS>
+void spmm_seg(ssg_system *S, cudaStream_t st, const T *X, T *Y, double *part, const ScalB *segs) {
+    const int pi = sizeof(T) == 8 ? 0 : 1, lk = log2_cols(K);
+    DevOp A = pi == 0 ? S->opB64 : S->opB32;
+    A.l2_ahead = S->spmm_ahead[pi][lk];
+    if (S->spmm_nc[pi][lk] == 1)
+        k_spmm_seg<T, K, DOTS, 1><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(A, X, Y, part, S->tab, segs);
+    else
+        k_spmm_seg<T, K, DOTS, 2><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(A, X, Y, part, S->tab, segs);
+}
+
 template <int K, bool PC>
 int launch_bodyB64(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
-    k_spmm_seg<double, K, true><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(S->opB64, B.p, B.q, B.part_a, S->tab, B.so);
+    spmm_seg<double, K, true>(S, st, B.p, B.q, B.part_a, B.so);
     k_update_rB<K, PC><<<S->nchunks, kBlockV, 0, st>>>(B.q, B.r, S->op.mult, S->op.wtab, S->op.gflag, B.part_a,
                                                       B.part_b, S->tab, B.so, S->d_dinv);
     k_update_xpB<K, PC><<<S->nchunks, kBlockV, 0, st>>>(B.xl, B.p, B.r, B.part_b, S->tab, B.so, S->d_dinv);
@@ -1211,8 +1230,7 @@ int launch_inner_initB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandl
 template <int K, bool PC>
 int launch_inner_bodyB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
     ssg_system::BlockState &B = S->blk;
-    k_spmm_seg<float, K, true><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(S->opB32, B.p32, B.q32, B.part_a, S->tab,
-                                                                        B.si);
+    spmm_seg<float, K, true>(S, st, B.p32, B.q32, B.part_a, B.si);
     k_update_r32B<K, PC><<<S->nchunks, kBlockV, 0, st>>>(B.q32, B.r32, S->op.mult, S->op.wtab32, S->op.gflag128,
                                                         B.part_a, B.part_b, S->tab, B.si, S->d_dinv32);
     k_update_dp32B<K, PC><<<S->nchunks, kBlockV, 0, st>>>(B.d32, B.p32, B.r32, B.part_b, S->tab, B.si, B.so,
@@ -1227,7 +1245,7 @@ int launch_outer_tailB(ssg_system *S, cudaStream_t st, cudaGraphConditionalHandl
     ssg_system::BlockState &B = S->blk;
     const int64_t N = S->maps.nloc;
     k_ir_correct<<<grid_for(N * K, S->ctx->num_sms), kBlock, 0, st>>>(N * K, B.xl, B.d32);
-    k_spmm_seg<double, K, false><<<S->grid_spmmB, kSpmvThreads, 0, st>>>(S->opB64, B.xl, B.q, nullptr, S->tab, B.so);
+    spmm_seg<double, K, false>(S, st, B.xl, B.q, nullptr, B.so);
     k_residualB<K><<<S->nchunks, kBlockV, 0, st>>>(B.bl, B.q, B.r, nullptr, S->op.mult, S->op.wtab, B.part_a, S->tab,
                                                   1, 0);
     k_outer_finB<K><<<S->nseg, kBlock, 0, st>>>(B.part_a, S->tab, B.so, B.si, 0);
@@ -1401,8 +1419,7 @@ int block_pre(ssg_system *S, int nr_single, const double *b_glob, double *x_glob
     launches += 2;
     if (guess) {
         k_scatterB<K><<<S->nchunks, kBlockV, 0, s>>>(S->d_l2g, x_glob, B.xl, S->tab);
-        k_spmm_seg<double, K, false><<<S->grid_spmmB, kSpmvThreads, 0, s>>>(S->opB64, B.xl, B.q, nullptr, S->tab,
-                                                                             nullptr);
+        spmm_seg<double, K, false>(S, s, B.xl, B.q, nullptr, nullptr);
         launches += 2;
     } else {
         SSG_CUDA_TRY(cudaMemsetAsync(B.xl, 0, sizeof(double) * N * K, s));
@@ -1418,8 +1435,7 @@ int block_post(ssg_system *S, int nr_single, double *x_glob, int mode, cudaStrea
     ssg_system::BlockState &B = S->blk;
     k_gatherB<K><<<S->nchunks, kBlockV, 0, s>>>(S->d_l2g, S->d_own, B.xl, x_glob, S->tab);
     // true residuals ||b_j - S x_j||_w in FP64
-    k_spmm_seg<double, K, false><<<S->grid_spmmB, kSpmvThreads, 0, s>>>(S->opB64, B.xl, B.q, nullptr, S->tab,
-                                                                         nullptr);
+    spmm_seg<double, K, false>(S, s, B.xl, B.q, nullptr, nullptr);
     k_residualB<K><<<S->nchunks, kBlockV, 0, s>>>(B.bl, B.q, nullptr, nullptr, S->op.mult, S->op.wtab, B.part_a,
                                                  S->tab, 1, 0);
     k_outer_finB<K><<<S->nseg, kBlock, 0, s>>>(B.part_a, S->tab, B.so, B.si, 1);
@@ -2097,9 +2113,114 @@ int batch_classes_ready(ssg_system *S, int mode) {
     return SSG_OK;
 }
 
+// K-vector product candidates of ssg_autotune_block: entries loaded at once
+// (1 or 2) x slices ahead prefetched into L2 (0, 1, 2).
+constexpr int kBlockTuneCands = SSG_TUNE_BLOCK_CANDIDATES;
+const int kCandNc[kBlockTuneCands] = {1, 1, 1, 2, 2, 2};
+const int kCandAhead[kBlockTuneCands] = {0, 1, 2, 0, 1, 2};
+
+// Times every candidate as the solves launch the product (with the block
+// partials of (x, S x)_w, every segment active) and keeps the fastest.
+template <typename T, int K>
+int tune_spmm(ssg_system *S, int reps, double *us, int32_t *choice) {
+    ssg_system::BlockState &B = S->blk;
+    const int pi = sizeof(T) == 8 ? 0 : 1, lk = log2_cols(K);
+    const T *X;
+    T *Y;
+    if constexpr (sizeof(T) == 8) {
+        X = B.p;
+        Y = B.q;
+    } else {
+        X = B.p32;
+        Y = B.q32;
+    }
+    cudaStream_t st = S->ctx->stream;
+    double best = 1e30;
+    for (int c = 0; c < kBlockTuneCands; ++c) {
+        S->spmm_nc[pi][lk] = static_cast<int8_t>(kCandNc[c]);
+        S->spmm_ahead[pi][lk] = static_cast<int8_t>(kCandAhead[c]);
+        for (int i = 0; i < 3; ++i) spmm_seg<T, K, true>(S, st, X, Y, B.part_a, nullptr);
+        SSG_CUDA_TRY(cudaEventRecord(S->ev0, st));
+        for (int i = 0; i < reps; ++i) spmm_seg<T, K, true>(S, st, X, Y, B.part_a, nullptr);
+        SSG_CUDA_TRY(cudaEventRecord(S->ev1, st));
+        SSG_CUDA_TRY(cudaGetLastError());
+        SSG_CUDA_TRY(cudaEventSynchronize(S->ev1));
+        float ms = 0.f;
+        SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
+        us[c] = 1e3 * ms / reps;
+        if (us[c] < best) {
+            best = us[c];
+            *choice = c;
+        }
+    }
+    S->spmm_nc[pi][lk] = static_cast<int8_t>(kCandNc[*choice]);
+    S->spmm_ahead[pi][lk] = static_cast<int8_t>(kCandAhead[*choice]);
+    return SSG_OK;
+}
+
+// Tune one (non-batch, or one column group's) system for K columns; its block
+// graphs, which hold the previous launches, are rebuilt on demand.
+int tune_block_system(ssg_system *S, int K, int reps, ssg_tune_block *t) {
+    int rc = ensure_block(S, K);
+    if (rc != SSG_OK) return rc;
+    t->k = K;
+    for (int c = 0; c < kBlockTuneCands; ++c) {
+        t->nc[c] = kCandNc[c];
+        t->l2_ahead[c] = kCandAhead[c];
+    }
+    switch (K) {
+        case 2: rc = tune_spmm<double, 2>(S, reps, t->fp64_us, &t->fp64_choice); break;
+        case 4: rc = tune_spmm<double, 4>(S, reps, t->fp64_us, &t->fp64_choice); break;
+        case 8: rc = tune_spmm<double, 8>(S, reps, t->fp64_us, &t->fp64_choice); break;
+        default: rc = tune_spmm<double, 16>(S, reps, t->fp64_us, &t->fp64_choice); break;
+    }
+    if (rc != SSG_OK) return rc;
+    switch (K) {
+        case 2: rc = tune_spmm<float, 2>(S, reps, t->fp32_us, &t->fp32_choice); break;
+        case 4: rc = tune_spmm<float, 4>(S, reps, t->fp32_us, &t->fp32_choice); break;
+        case 8: rc = tune_spmm<float, 8>(S, reps, t->fp32_us, &t->fp32_choice); break;
+        default: rc = tune_spmm<float, 16>(S, reps, t->fp32_us, &t->fp32_choice); break;
+    }
+    if (rc != SSG_OK) return rc;
+    SSG_CUDA_TRY(cudaStreamSynchronize(S->ctx->stream));
+    destroy_block_graphs(S);
+    return SSG_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int ssg_autotune_block(ssg_system *S, int32_t k, int32_t reps, ssg_tune_block *out) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (reps <= 0) reps = 20;
+    ssg_tune_block t{};
+    if (S->kclass.empty()) {
+        if (!(k == 2 || k == 4 || k == 8 || k == 16)) {
+            set_error("ssg_autotune_block: k must be 2, 4, 8 or 16");
+            return SSG_E_INVALID;
+        }
+        rc = tune_block_system(S, k, reps, &t);
+        if (rc != SSG_OK) return rc;
+    } else {
+        // a batch: every column group for its own K; the group with the most
+        // columns is reported
+        for (ssg_system *C : S->kclass) {
+            ssg_tune_block tc{};
+            rc = tune_block_system(C, pow2_columns(C->batch_k), reps, &tc);
+            if (rc != SSG_OK) return rc;
+            if (tc.k >= t.k) t = tc;
+        }
+        for (ssg_system::BlockGraph &G : S->classes_graph) {
+            if (G.exec) cudaGraphExecDestroy(G.exec);
+            if (G.g) cudaGraphDestroy(G.g);
+            G = ssg_system::BlockGraph{};
+        }
+    }
+    if (out) *out = t;
+    return SSG_OK;
+}
 
 int ssg_set_batch_graph(ssg_system *S, int32_t one_graph) {
     if (!S) {

@@ -72,13 +72,19 @@ struct SpmmTraits;
 template <>
 struct SpmmTraits<double> {
     static constexpr int kBlocksPerSM = 2;  // K FP64 accumulators and two entries' rows in flight per lane
-    static constexpr int kL2Ahead = 0;      // slices ahead whose value and column lines go to L2 (0: none)
 };
 template <>
 struct SpmmTraits<float> {
     static constexpr int kBlocksPerSM = 4;
-    static constexpr int kL2Ahead = 0;
 };
+
+// Sliced-ELL entries a lane loads at once in the K-vector product (before
+// their x rows), the default of the autotuner (ssg_autotune_block times 1
+// and 2): one with K >= 8 FP64 columns (register room), else two.
+template <typename T, int K>
+constexpr int spmm_nc_default() {
+    return (sizeof(T) == 8 && K >= 8) ? 1 : 2;
+}
 
 // K contiguous values of one local entry.
 template <int K>
@@ -213,8 +219,9 @@ __device__ __forceinline__ void slice_chunk_v(const T *__restrict__ sv, const in
 // block's partial of (x_j, y_j)_w at partials[block * K + j].  The work list
 // and the summation orders (CSR order inside a row, ascending subdomain at
 // an interface node) are those of the single-vector kernel, so every column
-// is bit-identical to it.
-template <typename T, int K, bool DOTS>
+// is bit-identical to it.  NC: sliced entries loaded at once; A.l2_ahead:
+// slices ahead prefetched into L2 (neither changes the arithmetic).
+template <typename T, int K, bool DOTS, int NC = spmm_nc_default<T, K>()>
 __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ X, T *__restrict__ Y,
                                           double *partials) {
     using Sh = SpmmShape<T, K>;
@@ -231,8 +238,8 @@ __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ 
     for (int u = 0; u < VW; ++u) dot[u] = T(0);
     for (int it = range.x; it < range.y; ++it) {
         const WorkItem W = A.items[it];
-        if (SpmmTraits<T>::kL2Ahead > 0 && it + SpmmTraits<T>::kL2Ahead < range.y) {
-            const WorkItem Wp = A.items[it + SpmmTraits<T>::kL2Ahead];
+        if (A.l2_ahead > 0 && it + A.l2_ahead < range.y) {
+            const WorkItem Wp = A.items[it + A.l2_ahead];
             if (sliced_item(Wp.kind) && lane < Wp.e1) {
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(sv + Wp.e0 + lane * kSliceRows));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
@@ -241,7 +248,6 @@ __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ 
         if (sliced_item(W.kind)) {
             const bool iface = W.kind == kItemIfaceSlice;
             const bool sorted = W.kind == kItemSortedSlice;
-            constexpr int NC = (sizeof(T) == 8 && K >= 8) ? 1 : 2;
             T acc[LPR][VW];
 #pragma unroll
             for (int p = 0; p < LPR; ++p)
@@ -410,12 +416,12 @@ __global__ void __launch_bounds__(kSpmvThreads, SpmmTraits<T>::kBlocksPerSM)
 
 // The K-vector product inside the solves: blocks of a segment whose columns
 // are all frozen (segs given) return at once.
-template <typename T, int K, bool DOTS>
+template <typename T, int K, bool DOTS, int NC>
 __global__ void __launch_bounds__(kSpmvThreads, SpmmTraits<T>::kBlocksPerSM)
     k_spmm_seg(DevOp A, const T *__restrict__ X, T *__restrict__ Y, double *partials, SegTab tab,
                const ScalB *segs) {
     if (segs && segs[tab.blk_seg[blockIdx.x]].act == 0) return;
-    spmm_body<T, K, DOTS>(A, X, Y, partials);
+    spmm_body<T, K, DOTS, NC>(A, X, Y, partials);
 }
 
 // Sums of each column's partials over blocks [b0, b1) of the previous kernel

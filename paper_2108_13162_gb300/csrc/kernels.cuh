@@ -135,6 +135,7 @@ struct DevOp {
     const float *wtab32;    // [256] 1/m rounded to FP32
     const uint8_t *gflag;   // [ceil(nloc / 64)] 1 if entries [64 g, 64 g + 64) hold an interface copy
     const uint8_t *gflag128;  // [ceil(nloc / 128)] the same for groups of 128 entries
+    int32_t l2_ahead;       // K-vector product: slices ahead whose lines are prefetched into L2 (0: none)
 };
 
 // kEpiStore: the (x, y)_w total is written to *out by the last block (ticket);

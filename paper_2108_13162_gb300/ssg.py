@@ -73,6 +73,7 @@ EXPORTS = (
     "ssg_measure_fp64_rate",
     "ssg_set_slice_sort",
     "ssg_get_layout",
+    "ssg_autotune_block",
     "ssg_band_split",
     "ssg_band_get",
     "ssg_band_spmv",
@@ -124,6 +125,25 @@ class ssg_tune(C.Structure):
         ("fp32_l2_ahead", C.c_int32 * TUNE_CANDIDATES),
         ("fp64_us", C.c_double * TUNE_CANDIDATES),
         ("fp32_us", C.c_double * TUNE_CANDIDATES),
+    ]
+
+    def as_dict(self):
+        return {f: (list(getattr(self, f)) if not isinstance(getattr(self, f), int) else getattr(self, f))
+                for f, _ in self._fields_}
+
+
+TUNE_BLOCK_CANDIDATES = 6  # SSG_TUNE_BLOCK_CANDIDATES
+
+
+class ssg_tune_block(C.Structure):
+    _fields_ = [
+        ("k", C.c_int32),
+        ("fp64_choice", C.c_int32),
+        ("fp32_choice", C.c_int32),
+        ("nc", C.c_int32 * TUNE_BLOCK_CANDIDATES),
+        ("l2_ahead", C.c_int32 * TUNE_BLOCK_CANDIDATES),
+        ("fp64_us", C.c_double * TUNE_BLOCK_CANDIDATES),
+        ("fp32_us", C.c_double * TUNE_BLOCK_CANDIDATES),
     ]
 
     def as_dict(self):
@@ -205,6 +225,7 @@ def lib():
         L.ssg_wdot_noalloc.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
         L.ssg_set_batch_graph.argtypes = [vp, C.c_int32]
         L.ssg_set_slice_sort.argtypes = [vp, C.c_int32]
+        L.ssg_autotune_block.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(ssg_tune_block)]
         L.ssg_get_layout.argtypes = [vp, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")]
         L.ssg_measure_fp64_rate.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                             C.POINTER(C.c_double)]
@@ -400,6 +421,12 @@ def ssg_spmv_assembled_f32(sys, x_loc, y_loc, xSx=None):
 def ssg_autotune(sys, reps=20):
     t = ssg_tune()
     _check(lib().ssg_autotune(sys, reps, C.byref(t)), "ssg_autotune")
+    return t.as_dict()
+
+
+def ssg_autotune_block(sys, k=16, reps=20):
+    t = ssg_tune_block()
+    _check(lib().ssg_autotune_block(sys, int(k), int(reps), C.byref(t)), "ssg_autotune_block")
     return t.as_dict()
 
 
@@ -659,6 +686,10 @@ class Batch:
         s = ssg_get_sizes(self.h)
         self.sizes = Sizes(s.n, s.P, s.nnz, s.nloc, s.ngamma, s.max_mult, s.ncopies)
 
+    def autotune_block(self, reps=20):
+        """Tune every column group's K-vector product."""
+        return ssg_autotune_block(self.h, 16, reps)
+
     def solve(self, b, x=None, rtol=1e-8, max_iter=0, mode=SSG_FP64):
         """b: float64 CUDA tensor of rhs_off[-1] values (system s's right-hand
         side j at rhs_off[s] + j * n_s); returns (x, status, stats)."""
@@ -761,6 +792,10 @@ class System:
 
     def layout(self):
         return ssg_get_layout(self.h)
+
+    def autotune_block(self, k=16, reps=20):
+        """Tune the k-vector product of the several-right-hand-side solves."""
+        return ssg_autotune_block(self.h, k, reps)
 
     def autotune(self, reps=20):
         """Pick the fastest single-vector SpMV instances for this system."""

@@ -253,3 +253,20 @@ def test_batch_jacobi(ctx, bp):
         assert abs(st[t]["outer"] - rm.outer) <= 1
         assert abs(st[t]["iters"] - rm.iters) <= max(3 * rm.outer, 0.10 * rm.iters)
         t += 1
+
+
+def test_batch_autotune_same_bits(ctx, bp):
+    """Tuning every column group's K-vector product keeps the bits of the
+    batch solve (FP64 and mixed)."""
+    from paper_2108_13162_gb300 import ssg
+
+    B = _make(ctx, bp)
+    before = [B.solve(_b_all(bp), rtol=1e-8, mode=m) for m in (ssg.SSG_FP64, ssg.SSG_MIXED)]
+    t = B.autotune_block(reps=3)
+    assert t["k"] == 8  # the batch's largest column group (1-8 right-hand sides)
+    after = [B.solve(_b_all(bp), rtol=1e-8, mode=m) for m in (ssg.SSG_FP64, ssg.SSG_MIXED)]
+    for (x0, rc0, s0), (x1, rc1, s1) in zip(before, after):
+        assert rc0 == rc1 == ssg.SSG_OK
+        assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy())
+        assert [(a["iters"], a["outer"]) for a in s0] == [(a["iters"], a["outer"]) for a in s1]
+    B.close()

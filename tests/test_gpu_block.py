@@ -259,3 +259,32 @@ def test_block_mixed_matches_oracle(ctx, fv20):
         r64 = ref.cg(B[j], 1e-8, 100000)
         kap = oracle.cond_from_lanczos(r64.alpha, r64.beta)
         assert _rel(X[j], rm.x) <= 2 * kap * 1e-8
+
+
+@pytest.mark.parametrize("k", [16, 4])
+def test_block_autotune_same_bits(ctx, k):
+    """ssg_autotune_block times six (entries at once, L2 look-ahead)
+    candidates of the K-vector product in both precisions and keeps the
+    fastest; none changes the arithmetic, so solves before and after tuning
+    give the same bits and counts (FP64 and mixed)."""
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    p = config_problem(5, scale=20)
+    B = _t(p.b.T[:k].copy())
+    S = System(ctx, p.A, p.part, p.P)
+    before = [S.solve(B, rtol=1e-8, mode=m) for m in (ssg.SSG_FP64, ssg.SSG_MIXED)]
+    t = S.autotune_block(k, reps=3)
+    assert t["k"] == k
+    assert 0 <= t["fp64_choice"] < ssg.TUNE_BLOCK_CANDIDATES and 0 <= t["fp32_choice"] < ssg.TUNE_BLOCK_CANDIDATES
+    assert all(v > 0 for v in t["fp64_us"] + t["fp32_us"])
+    assert t["fp32_us"][t["fp32_choice"]] == min(t["fp32_us"])
+    assert sorted(set(t["nc"])) == [1, 2] and sorted(set(t["l2_ahead"])) == [0, 1, 2]
+    after = [S.solve(B, rtol=1e-8, mode=m) for m in (ssg.SSG_FP64, ssg.SSG_MIXED)]
+    for (x0, rc0, s0), (x1, rc1, s1) in zip(before, after):
+        assert rc0 == rc1 == ssg.SSG_OK
+        assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy())
+        assert [(a["iters"], a["outer"]) for a in s0] == [(a["iters"], a["outer"]) for a in s1]
+    with pytest.raises(ssg.SSGError):
+        S.autotune_block(3)
+    S.close()
