@@ -77,6 +77,9 @@ def parse_args(argv=None):
     ap.add_argument("--profile-fe", choices=("fp64", "fp32"), default=None,
                     help="only build the 1024^2 finite-element workload (the default slice layout) and launch its "
                          "SpMV --spmv-reps times (for ncu); no JSON line")
+    ap.add_argument("--fe-windows", action="store_true",
+                    help="also time the 1024^2 finite-element product under every slice-sorting window "
+                         "(1, 128, 256, 512, whole subdomain), each autotuned, and report them in fe2d")
     ap.add_argument("--head-only", action="store_true",
                     help="time the headline mode only (not the other modes); for profiler launch lists")
     ap.add_argument("--no-multi-rhs", action="store_true",
@@ -455,7 +458,7 @@ def bench_batch(ctx, stream, reps, size):
     return out
 
 
-def bench_fe(ctx, stream, reps):
+def bench_fe(ctx, stream, reps, windows=False):
     """Workload 3: P1 finite elements on the jittered 1024^2 mesh, 256 uneven
     RCB subdomains: the slice layout the row-length rule picks (rows sorted
     by length in windows) against the unsorted one, the SpMV instances chosen
@@ -490,6 +493,18 @@ def bench_fe(ctx, stream, reps):
     S1.autotune(reps=20)
     unsorted = {"layout": S1.layout(), "spmv": spmv_roofline(S1)}
     S1.close()
+    by_window = None
+    if windows:
+        by_window = {}
+        for w in (128, 256, 512, -1):
+            ctx.set_slice_sort(w)
+            try:
+                Sw = System(ctx, p.A, p.part, p.P)
+            finally:
+                ctx.set_slice_sort(0)
+            Sw.autotune(reps=20)
+            by_window[str(w)] = {"layout": Sw.layout(), "spmv": spmv_roofline(Sw)}
+            Sw.close()
     # the layout the row-length rule picks (the default)
     S = System(ctx, p.A, p.part, p.P)
     tune = S.autotune(reps=20)
@@ -497,6 +512,8 @@ def bench_fe(ctx, stream, reps):
     out = {"workload": "fe2d_p1_jittered_1024^2_rcb256", "n": p.A.n, "nnz": p.A.nnz, "subdomains": p.P,
            "nloc": S.sizes.nloc, "rtol": RTOL, "autotune": tune, "layout": S.layout(),
            "spmv": spmv_roofline(S), "unsorted": unsorted}
+    if by_window is not None:
+        out["by_window"] = by_window
     for name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED), ("mixed_jacobi", ssg.SSG_MIXED_JACOBI)):
         x, rc, st = S.solve(b, rtol=RTOL, mode=mode)
         torch.cuda.synchronize()
@@ -1019,7 +1036,7 @@ def run_ours(args, dist):
         multi = bench_multi_rhs(ctx, stream, max(1, min(args.steps, 3)), args.spmv_reps, fp64_ok)
     fe = None
     if not args.no_fe:
-        fe = bench_fe(ctx, stream, max(1, min(args.steps, 3)))
+        fe = bench_fe(ctx, stream, max(1, min(args.steps, 3)), args.fe_windows)
     bands = None
     if not args.no_bands:
         bands = bench_bands(ctx, stream, prob, max(1, min(args.steps, 3)), args.spmv_reps)
