@@ -289,8 +289,8 @@ __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ 
                         const int l0 = seg & 0xff, m = seg >> 8;
                         T S[VW];
 #pragma unroll
-                        for (int u = 0; u < VW; ++u) S[u] = T(0);
-                        for (int t = 0; t < m; ++t)
+                        for (int u = 0; u < VW; ++u) S[u] = stage[warp][l0][col0 + u];
+                        for (int t = 1; t < m; ++t)
 #pragma unroll
                             for (int u = 0; u < VW; ++u) S[u] += stage[warp][l0 + t][col0 + u];
                         const int row = __ldg(A.icopy + c);

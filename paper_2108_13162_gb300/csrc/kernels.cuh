@@ -380,8 +380,11 @@ __device__ __forceinline__ void finish_slice(const DevOp &A, const WorkItem &W, 
         const int seg = valid ? __ldg(A.sseg + c) : 0;
         const int l0 = seg & 0xff, m = seg >> 8;
         const int mmax = __reduce_max_sync(0xffffffffu, m);
-        T S = T(0);
-        for (int t = 0; t < mmax; ++t) {
+        // the sum starts from the first copy, not from 0 (one FP64 add less
+        // per slice: a predicated-off add still takes its FP64 issue slot);
+        // the same sum in the same order, up to the sign of a zero total
+        T S = __shfl_sync(0xffffffffu, acc, l0 & 31);
+        for (int t = 1; t < mmax; ++t) {
             const T v = __shfl_sync(0xffffffffu, acc, (l0 + t) & 31);
             if (t < m) S += v;
         }
