@@ -396,6 +396,31 @@ def bench_multi_rhs(ctx, stream, reps, spmv_reps, fp64_peak=None):
     return out
 
 
+def batch_algorithmic_bytes(bp, st, mode_name):
+    """Bytes the batch solve must move: for every system, the iterations of
+    its K-column loop (the most any of its right-hand sides took; the K
+    columns, padding included, run together) times the bytes of one
+    iteration -- FP64: the matrix (12 per entry, 4 per row pointer) and 80
+    per entry and column (product: x read, y written; residual update: r, q
+    read, r written; x/p update: x, p, r read, x, p written); mixed (inner
+    FP32 iterations): 8 per matrix entry and 40 per entry and column.
+    Counted on the global sizes (interface copies left out), so a lower
+    bound."""
+    tot = 0
+    t = 0
+    for A, b in zip(bp.A, bp.b):
+        k = b.shape[0]
+        K = 2 if k <= 2 else 4 if k <= 4 else 8 if k <= 8 else 16
+        its = max(st[t + j]["iters"] for j in range(k))
+        t += k
+        if mode_name == "fp64":
+            per = 12 * A.nnz + 4 * (A.n + 1) + 80 * K * A.n
+        else:
+            per = 8 * A.nnz + 4 * (A.n + 1) + 40 * K * A.n
+        tot += its * per
+    return tot
+
+
 def bench_batch(ctx, stream, reps, size):
     """Workload 4: independent 2D finite-volume systems (4-16 box subdomains,
     1-8 right-hand sides each) solved together in one graph launch, FP64,
@@ -436,6 +461,11 @@ def bench_batch(ctx, stream, reps, size):
         out[mode_name + "_iters_max"] = max(t["iters"] for t in st)
         out[mode_name + "_true_relres_max"] = max(t["true_relres"] for t in st)
         out[mode_name + "_launches"] = st[0]["kernel_launches"]
+        nb = batch_algorithmic_bytes(bp, st, mode_name)
+        sec = out[mode_name + "_together_s"]
+        peak, _ = measured_peaks()
+        out[mode_name + "_roofline"] = {"algorithmic_bytes": nb, "achieved_gbs": nb / sec / 1e9,
+                                        "frac": nb / sec / 1e9 / peak, "peak": peak}
     B.close()
     # the same systems one after another (each with its right-hand sides together)
     if size != "full":
