@@ -701,9 +701,11 @@ def golden_samples():
 
 def bench_p2d(ctx, stream, reps):
     """Workload 1: the 64x64 5-point Poisson system on 2x2 subdomains, plain
-    FP64 CG to 1e-10.  The whole system (0.33 MB) sits in L2, so launch
-    latency, not HBM, bounds it: the figures are the time per solve and per
-    iteration, with the error against the oracle's stored solution."""
+    FP64 CG to 1e-10.  The whole system (0.33 MB) sits in L2, so latency, not
+    HBM, bounds it: the figures are the time per solve and per iteration,
+    with the error against the oracle's stored solution, for the one-cluster
+    solve (the default at this size: every iteration inside one launch) and
+    for the three-kernel loop graph."""
     import numpy as np
     import torch
 
@@ -716,36 +718,55 @@ def bench_p2d(ctx, stream, reps):
     S = System(ctx, p.A, p.part, p.P)
     b = torch.from_numpy(p.b[:, 0].copy()).cuda()
     x = torch.zeros_like(b)
-    for _ in range(3):
-        x.zero_()
-        ssg.ssg_solve(S.h, 1, b, x, False, rtol, 0, ssg.SSG_FP64)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        x.zero_()
-        rc, st = ssg.ssg_solve(S.h, 1, b, x, False, rtol, 0, ssg.SSG_FP64)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if rc != ssg.SSG_OK:
-        raise RuntimeError("64x64 solve did not converge")
-    t = e0.elapsed_time(e1) / 1e3 / reps
-    xh = x.cpu().numpy()
-    xs = p.xstar[:, 0]
-    out = {"workload": "poisson2d_5pt_64x64_2x2_subdomains", "n": p.A.n, "nnz": p.A.nnz, "rtol": rtol,
-           "mode": "fp64", "s": t, "iters": st[0]["iters"], "us_per_iter": t * 1e6 / max(st[0]["iters"], 1),
-           "true_relres": st[0]["true_relres"],
-           "err_vs_xstar": float(np.linalg.norm(xh - xs) / np.linalg.norm(xs)),
-           "l2": "L2-resident (0.33 MB): latency-bound, no HBM roofline"}
     try:
         with open(os.path.join(ROOT, "tests", "golden", "oracle_p2d_64_2x2.json")) as f:
             g = json.load(f)
-        xo = np.array(g["x"])
-        out["err_vs_oracle_fp64"] = float(np.linalg.norm(xh - xo) / np.linalg.norm(xo))
+    except (OSError, ValueError):
+        g = None
+    limit, ctas = ctx.cluster_solve()
+
+    def timed():
+        for _ in range(3):
+            x.zero_()
+            ssg.ssg_solve(S.h, 1, b, x, False, rtol, 0, ssg.SSG_FP64)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            x.zero_()
+            rc, st = ssg.ssg_solve(S.h, 1, b, x, False, rtol, 0, ssg.SSG_FP64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rc != ssg.SSG_OK:
+            raise RuntimeError("64x64 solve did not converge")
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        xh = x.cpu().numpy()
+        xs = p.xstar[:, 0]
+        r = {"s": t, "iters": st[0]["iters"], "us_per_iter": t * 1e6 / max(st[0]["iters"], 1),
+             "kernel_launches": st[0]["kernel_launches"], "true_relres": st[0]["true_relres"],
+             "err_vs_xstar": float(np.linalg.norm(xh - xs) / np.linalg.norm(xs))}
+        if g is not None:
+            xo = np.array(g["x"])
+            r["err_vs_oracle_fp64"] = float(np.linalg.norm(xh - xo) / np.linalg.norm(xo))
+        return r
+
+    out = {"workload": "poisson2d_5pt_64x64_2x2_subdomains", "n": p.A.n, "nnz": p.A.nnz,
+           "nloc": S.sizes.nloc, "rtol": rtol, "mode": "fp64",
+           "l2": "L2-resident (0.33 MB): latency-bound, no HBM roofline"}
+    if g is not None:
         out["oracle_iters"] = int(g["iters"])
-    except (OSError, KeyError, ValueError):
-        pass
+    try:
+        ctx.set_cluster_solve(0)
+        out["loop"] = timed()
+    finally:
+        ctx.set_cluster_solve(limit)
+    if ctas > 0 and S.sizes.nloc <= limit:
+        out["cluster"] = dict(timed(), ctas=ctas)
+    head = out.get("cluster", out["loop"])
+    for k in ("s", "iters", "us_per_iter", "true_relres", "err_vs_xstar", "err_vs_oracle_fp64"):
+        if k in head:
+            out[k] = head[k]
     S.close()
     return out
 

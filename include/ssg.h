@@ -120,6 +120,26 @@ int ssg_set_unroll(ssg_ctx *ctx, int32_t iters);
  * window < -1. */
 int ssg_set_slice_sort(ssg_ctx *ctx, int32_t window);
 /*
+ * One-cluster solve of small systems (Algorithm 3 of Section 3.4, the whole
+ * iteration loop in one kernel launch).  Under the graph driver, a
+ * single-right-hand-side SSG_FP64 or SSG_FP64_JACOBI solve of a system with
+ * at most max_nloc local entries (|V_1| + ... + |V_P|) runs as one thread-block
+ * cluster of up to 16 CTAs, one per SM, instead of three kernels per
+ * iteration.  Its CTAs exchange the weighted dots' per-CTA sums through
+ * distributed shared memory and add them in one fixed order in every CTA,
+ * and meet at three cluster barriers per iteration.  The product's rows and
+ * interface sums are the same bits as the multi-kernel loop's.  The dots'
+ * partial sums are grouped differently, so iterates agree to rounding and the
+ * iteration count may differ by a few.  max_nloc = 0 turns it off; default
+ * 65536.  Applies to solves issued afterwards, on systems partitioned on this
+ * context; SSG_E_INVALID for max_nloc < 0.
+ */
+int ssg_set_cluster_solve(ssg_ctx *ctx, int64_t max_nloc);
+/* The current limit, and the CTAs per cluster the device places (0: the
+ * one-cluster solve is unavailable and never used).  Either pointer may be
+ * NULL. */
+int ssg_get_cluster_solve(const ssg_ctx *ctx, int64_t *max_nloc, int32_t *ctas);
+/*
  * Parameters of SSG_MIXED solves on this context (not a method of the paper;
  * its experiments are FP64 only): the inner FP32 CG stops when its residual
  * has dropped by inner_rtol (or by the factor the outer test still needs, if

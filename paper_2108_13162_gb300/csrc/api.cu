@@ -16,6 +16,7 @@
 
 #include "adjoint.cuh"
 #include "block.cuh"
+#include "cluster.cuh"
 #include "kernels.cuh"
 #include "ssg_ctx.h"
 #include "ssg_internal.h"
@@ -65,6 +66,10 @@ struct ssg_system {
     const int2 *range_bps[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int var64 = 0, var32 = 0;                       // chosen SpMV instances (ssg_autotune)
     int grid_vec = 0;
+    // one-cluster solve: warp ranges for cluster_ctas CTAs (warp w of CTA c
+    // takes range w * cluster_ctas + c), the first cluster_nranges non-empty
+    const int2 *range_cluster = nullptr;
+    int32_t cluster_ctas = 0, cluster_nranges = 0;
     // graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -194,6 +199,8 @@ struct WorkPlan {
     std::vector<WorkItem> items;
     std::vector<int2> range_bps[7];  // per warp of a single-vector launch sized for 3 to 6 blocks per SM
     std::vector<int2> warp_rangeB;   // per warp of the K-vector product: cut inside each segment
+    std::vector<int2> range_cluster;  // per warp of the one-cluster solve (cluster_ctas CTAs)
+    int32_t cluster_nranges = 0;      // its non-empty ranges (a prefix)
     std::vector<int32_t> blk_seg, seg_blk;  // segment of each K-vector product block; blocks per segment
     std::vector<int4> chunk;                // vector-kernel chunks (segment, first entry, end entry, 0)
     std::vector<int32_t> seg_chunk;         // chunks per segment
@@ -282,7 +289,8 @@ int slice_window(const HostMaps &M, int32_t s, int policy) {
 
 // seg_sub: subdomains of each segment (independent systems), [nseg + 1];
 // sort_policy: the sorting window of the interior slices (slice_window).
-WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &seg_sub, int sort_policy) {
+WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &seg_sub, int sort_policy,
+                   int cluster_ctas) {
     WorkPlan W;
     std::vector<int32_t> sub_of(static_cast<size_t>(M.nloc));
     for (int32_t s = 0; s < M.P; ++s)
@@ -447,6 +455,12 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
     for (int bps = 3; bps <= 6; ++bps) {
         W.grid_bps[bps] = std::max(1, std::min(per, num_sms * bps));
         W.range_bps[bps] = cut_ranges(W.items, W.grid_bps[bps]);
+    }
+    if (cluster_ctas > 0) {
+        // kClusterWarps warps per CTA: cut for the equivalent number of
+        // kSpmvWarps-warp blocks
+        W.range_cluster = cut_ranges(W.items, cluster_ctas * kClusterWarps / kSpmvWarps);
+        for (const int2 &r : W.range_cluster) W.cluster_nranges += r.y > r.x ? 1 : 0;
     }
     // K-vector product: blocks shared out among the segments by cost, at
     // least one each, every block inside one segment
@@ -702,7 +716,7 @@ int upload(ssg_system *S) {
         S->seg_rhs_off = {0};
     }
     S->nseg = static_cast<int32_t>(S->seg_sub.size()) - 1;
-    WorkPlan plan = make_plan(M, C->num_sms, S->seg_sub, C->slice_sort);
+    WorkPlan plan = make_plan(M, C->num_sms, S->seg_sub, C->slice_sort, S->nseg == 1 ? C->cluster_ctas : 0);
     S->slice_slots = plan.slice_slots;
     S->slice_entries = plan.slice_entries;
     S->sorted_subdomains = plan.sorted_subdomains;
@@ -773,6 +787,7 @@ int upload(ssg_system *S) {
     for (int bps = 3; bps <= 6; ++bps)
         i_range_bps[bps] = add(plan.range_bps[bps].data(), sizeof(int2) * plan.range_bps[bps].size());
     size_t i_brangeB = add(plan.warp_rangeB.data(), sizeof(int2) * plan.warp_rangeB.size());
+    size_t i_rcluster = add(plan.range_cluster.data(), sizeof(int2) * plan.range_cluster.size());
     size_t i_blk_seg = add(plan.blk_seg.data(), sizeof(int32_t) * plan.blk_seg.size());
     size_t i_seg_blk = add(plan.seg_blk.data(), sizeof(int32_t) * plan.seg_blk.size());
     size_t i_chunk = add(plan.chunk.data(), sizeof(int4) * plan.chunk.size());
@@ -916,6 +931,11 @@ int upload(ssg_system *S) {
     S->opB32 = S->op;
     S->opB32.warp_range = static_cast<const int2 *>(at(i_brangeB));
     S->grid_spmmB = plan.gridB;
+    if (!plan.range_cluster.empty()) {
+        S->range_cluster = static_cast<const int2 *>(at(i_rcluster));
+        S->cluster_ctas = C->cluster_ctas;
+        S->cluster_nranges = plan.cluster_nranges;
+    }
     S->nchunks = static_cast<int32_t>(plan.chunk.size());
     S->tab.blk_seg = static_cast<const int32_t *>(at(i_blk_seg));
     S->tab.seg_blk = static_cast<const int32_t *>(at(i_seg_blk));
@@ -1023,6 +1043,71 @@ int check_diag(ssg_system *S) {
     return SSG_OK;
 }
 
+// The one-cluster solve's CTAs per cluster: the largest of 16, 8, 4 and 2
+// for which the occupancy query places at least one cluster of both
+// instances (16 is beyond the portable cluster size and must be allowed per
+// kernel); 0 if none is placed or the query fails.
+int pick_cluster_ctas(cudaStream_t st) {
+    if (cudaFuncSetAttribute(k_cg_cluster<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(k_cg_cluster<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    for (int nc = kClusterMaxCtas; nc >= 2; nc /= 2) {
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = nc;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(nc);
+        cfg.blockDim = dim3(kClusterThreads);
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n0 = 0, n1 = 0;
+        const bool ok = cudaOccupancyMaxActiveClusters(&n0, k_cg_cluster<false>, &cfg) == cudaSuccess &&
+                        cudaOccupancyMaxActiveClusters(&n1, k_cg_cluster<true>, &cfg) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+        if (ok && n0 > 0 && n1 > 0) return nc;
+    }
+    return 0;
+}
+
+// Whether a single-vector FP64 solve of S runs as the one-cluster kernel.
+bool use_cluster(const ssg_system *S, bool mixed) {
+    const ssg_ctx *C = S->ctx;
+    return !mixed && C->driver == SSG_DRIVER_GRAPH && S->cluster_ctas > 0 && S->cluster_ctas == C->cluster_ctas &&
+           S->maps.nloc <= C->cluster_max_n && S->nseg == 1;
+}
+
+int launch_cluster_cg(ssg_system *S, cudaStream_t st, bool pc) {
+    const int nc = S->cluster_ctas;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = nc;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(nc);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    DevOp A = S->op;
+    A.warp_range = S->range_cluster;
+    const int64_t N = S->maps.nloc;
+    if (pc)
+        SSG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cg_cluster<true>, A, N, S->cluster_nranges,
+                                        static_cast<const double *>(S->d_bl), S->d_xl, S->d_r, S->d_p, S->d_q,
+                                        static_cast<const double *>(S->d_dinv), S->d_scal));
+    else
+        SSG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cg_cluster<false>, A, N, S->cluster_nranges,
+                                        static_cast<const double *>(S->d_bl), S->d_xl, S->d_r, S->d_p, S->d_q,
+                                        static_cast<const double *>(S->d_dinv), S->d_scal));
+    return SSG_OK;
+}
+
 // One right-hand side: b_glob/x_glob are device pointers (length n).
 int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, double rtol, int32_t max_iter,
               int mode, ssg_stats *st) {
@@ -1055,7 +1140,12 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     }
     SSG_CUDA_TRY(cudaGetLastError());
     int rc = SSG_OK;
-    if (C->driver == SSG_DRIVER_GRAPH) {
+    const bool cluster = use_cluster(S, mixed);
+    if (cluster) {
+        rc = launch_cluster_cg(S, s, pc);
+        if (rc != SSG_OK) return rc;
+        ++launches;
+    } else if (C->driver == SSG_DRIVER_GRAPH) {
         rc = mixed ? build_graph_mixed(S, pc) : build_graph(S, pc);
         if (rc != SSG_OK) return rc;
         SSG_CUDA_TRY(cudaGraphLaunch(mixed ? S->exec_m[pc] : pc ? S->exec_pc : S->exec, s));
@@ -1077,7 +1167,7 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     if (rc != SSG_OK) return rc;
     float ms = 0.f;
     SSG_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev0, S->ev1));
-    if (C->driver == SSG_DRIVER_GRAPH) {
+    if (C->driver == SSG_DRIVER_GRAPH && !cluster) {
         // every copy of an iteration in a loop pass launches all its kernels;
         // the device counts the residual-update launches (h.passes)
         if (mixed)  // init, per refinement: inner init + 3 tail kernels; 3 per inner copy
@@ -1665,6 +1755,7 @@ int ssg_create(ssg_ctx **ctx, int device, void *stream) {
         set_error(std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
         return SSG_E_CUDA;
     }
+    c->cluster_ctas = pick_cluster_ctas(c->stream);
     *ctx = c;
     return SSG_OK;
 }
@@ -1690,6 +1781,25 @@ int ssg_set_slice_sort(ssg_ctx *ctx, int32_t window) {
         return SSG_E_INVALID;
     }
     ctx->slice_sort = window;
+    return SSG_OK;
+}
+
+int ssg_set_cluster_solve(ssg_ctx *ctx, int64_t max_nloc) {
+    if (!ctx || max_nloc < 0) {
+        set_error("ssg_set_cluster_solve: null context, or max_nloc < 0");
+        return SSG_E_INVALID;
+    }
+    ctx->cluster_max_n = max_nloc;
+    return SSG_OK;
+}
+
+int ssg_get_cluster_solve(const ssg_ctx *ctx, int64_t *max_nloc, int32_t *ctas) {
+    if (!ctx) {
+        set_error("ssg_get_cluster_solve: null context");
+        return SSG_E_INVALID;
+    }
+    if (max_nloc) *max_nloc = ctx->cluster_max_n;
+    if (ctas) *ctas = ctx->cluster_ctas;
     return SSG_OK;
 }
 
@@ -1759,7 +1869,7 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
     } else {
         // host only: the interior slice layout the row-length rule gives
         // (ssg_get_layout), without a device
-        const WorkPlan plan = make_plan(S->maps, 1, {0, S->maps.P}, 0);
+        const WorkPlan plan = make_plan(S->maps, 1, {0, S->maps.P}, 0, 0);
         S->slice_slots = plan.slice_slots;
         S->slice_entries = plan.slice_entries;
         S->sorted_subdomains = plan.sorted_subdomains;

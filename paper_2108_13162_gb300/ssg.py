@@ -72,6 +72,8 @@ EXPORTS = (
     "ssg_set_batch_graph",
     "ssg_measure_fp64_rate",
     "ssg_set_slice_sort",
+    "ssg_set_cluster_solve",
+    "ssg_get_cluster_solve",
     "ssg_get_layout",
     "ssg_autotune_block",
     "ssg_band_split",
@@ -225,6 +227,8 @@ def lib():
         L.ssg_wdot_noalloc.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
         L.ssg_set_batch_graph.argtypes = [vp, C.c_int32]
         L.ssg_set_slice_sort.argtypes = [vp, C.c_int32]
+        L.ssg_set_cluster_solve.argtypes = [vp, C.c_int64]
+        L.ssg_get_cluster_solve.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.ssg_autotune_block.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(ssg_tune_block)]
         L.ssg_get_layout.argtypes = [vp, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")]
         L.ssg_measure_fp64_rate.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double),
@@ -585,6 +589,18 @@ def ssg_set_slice_sort(ctx, window: int):
     return _check(lib().ssg_set_slice_sort(ctx, int(window)), "ssg_set_slice_sort")
 
 
+def ssg_set_cluster_solve(ctx, max_nloc: int):
+    return _check(lib().ssg_set_cluster_solve(ctx, int(max_nloc)), "ssg_set_cluster_solve")
+
+
+def ssg_get_cluster_solve(ctx) -> tuple:
+    """(max_nloc, CTAs per cluster) of the one-cluster solve (see ssg.h)."""
+    n = C.c_int64(0)
+    c = C.c_int32(0)
+    _check(lib().ssg_get_cluster_solve(ctx, C.byref(n), C.byref(c)), "ssg_get_cluster_solve")
+    return int(n.value), int(c.value)
+
+
 def ssg_get_layout(sys) -> dict:
     """The interior slice layout of a system (see ssg.h)."""
     out = np.zeros(4, np.int64)
@@ -644,6 +660,15 @@ class Context:
         """Interior slice layout: 0 auto, 1 none, > 1 sorting window, -1 whole subdomain
         (systems partitioned afterwards)."""
         ssg_set_slice_sort(self.h, window)
+
+    def set_cluster_solve(self, max_nloc: int = 65536):
+        """Single-vector FP64 solves of systems with at most max_nloc local entries
+        run as one thread-block cluster (0: never)."""
+        ssg_set_cluster_solve(self.h, max_nloc)
+
+    def cluster_solve(self) -> tuple:
+        """(max_nloc, CTAs per cluster; 0 when the device places none)."""
+        return ssg_get_cluster_solve(self.h)
 
     def set_mixed(self, inner_rtol: float = 1e-4, max_outer: int = 30):
         ssg_set_mixed(self.h, inner_rtol, max_outer)

@@ -94,11 +94,17 @@ def test_jacobi_fewer_iterations_and_drivers_agree(ctx):
     _, _, s0 = S.solve(b, rtol=1e-8)
     x1, rc1, s1 = S.solve(b, rtol=1e-8, mode=ssg.SSG_FP64_JACOBI)
     assert rc1 == ssg.SSG_OK and s1[0]["iters"] < 0.7 * s0[0]["iters"]
-    ctx.set_driver(ssg.SSG_DRIVER_HOST)
+    # the graph-driven and the host-driven loop (the one-cluster solve off):
+    # the same kernels, the same bits
+    limit = ctx.cluster_solve()[0]
+    ctx.set_cluster_solve(0)
     try:
+        x1, rc1, s1 = S.solve(b, rtol=1e-8, mode=ssg.SSG_FP64_JACOBI)
+        ctx.set_driver(ssg.SSG_DRIVER_HOST)
         x2, rc2, s2 = S.solve(b, rtol=1e-8, mode=ssg.SSG_FP64_JACOBI)
     finally:
         ctx.set_driver(ssg.SSG_DRIVER_GRAPH)
+        ctx.set_cluster_solve(limit)
     assert s2[0]["iters"] == s1[0]["iters"]
     assert np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
     # several right-hand sides iterate together (K = 2), each column against the oracle

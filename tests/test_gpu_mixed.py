@@ -216,13 +216,18 @@ def test_loop_unroll_same_bits(ctx, mode):
     p = config_problem(2, scale=24)
     b = _t(p.b[:, 0])
     out = {}
+    limit = ctx.cluster_solve()[0]
     for u in (1, 3, 4, 8):
         ctx.set_unroll(u)
         try:
             S = System(ctx, p.A, p.part, p.P)
         finally:
             ctx.set_unroll(UNROLL_DEFAULT)
-        x, rc, st = S.solve(b, rtol=1e-8, mode=mode)
+        ctx.set_cluster_solve(0)  # the loop graph, not the one-cluster kernel
+        try:
+            x, rc, st = S.solve(b, rtol=1e-8, mode=mode)
+        finally:
+            ctx.set_cluster_solve(limit)
         assert rc == ssg.SSG_OK
         out[u] = (x.cpu().numpy(), st[0])
         S.close()

@@ -17,6 +17,8 @@ iterate by ~3e-5 relative, although the two converged solutions agree to
   edge cases: b = 0, A = I, exact initial guess, max_iter reached, an
   indefinite matrix (breakdown), several right-hand sides, the host-loop
   driver, host buffers.
+Each test runs twice: small single-vector solves as the one-cluster kernel,
+then as the three-kernel loop.
 """
 
 import numpy as np
@@ -28,8 +30,10 @@ from synth import CSR, config_problem, laplace1d, poisson2d_5pt, random_spd
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["cluster", "loop"])
+def ctx(request):
+    """Every test once with small single-vector FP64 solves run as the
+    one-cluster kernel (the default) and once with the three-kernel loop."""
     import torch
 
     from paper_2108_13162_gb300 import build as ssg_build
@@ -37,9 +41,24 @@ def ctx():
 
     ssg_build.build()
     c = Context(0)
+    if request.param == "cluster" and c.cluster_solve()[1] == 0:
+        c.close()
+        pytest.skip("the device places no cluster for the one-cluster solve")
+    if request.param == "loop":
+        c.set_cluster_solve(0)
+    c.path = request.param
     yield c
     torch.cuda.synchronize()
     c.close()
+
+
+def _cluster_runs(ctx, S):
+    return ctx.path == "cluster" and S.sizes.nloc <= ctx.cluster_solve()[0]
+
+
+def _loop_only(ctx):
+    if ctx.path == "cluster":
+        pytest.skip("larger than the one-cluster limit: the three-kernel loop runs in both passes")
 
 
 def _t(a):
@@ -101,7 +120,11 @@ def test_solve_to_tolerance(ctx, name, mk, rtol):
     tr = np.linalg.norm(b - p.A.to_scipy() @ xg) / np.linalg.norm(b)
     assert abs(st[0]["true_relres"] - tr) <= 1e-6 * tr + 1e-15
     assert st[0]["relres"] <= rtol
-    assert st[0]["kernel_launches"] >= 3 * st[0]["iters"]
+    if _cluster_runs(ctx, S):
+        # scatter, parameters, the cluster kernel, gather, true residual (2)
+        assert st[0]["kernel_launches"] == 6
+    else:
+        assert st[0]["kernel_launches"] >= 3 * st[0]["iters"]
 
 
 @pytest.mark.parametrize("name,mk,rtol", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
@@ -125,11 +148,17 @@ def test_deterministic_and_drivers_agree(ctx):
     x1, _, s1 = S.solve(b, rtol=1e-8)
     x2, _, s2 = S.solve(b, rtol=1e-8)
     assert np.array_equal(x1.cpu().numpy(), x2.cpu().numpy())
-    ctx.set_driver(ssg.SSG_DRIVER_HOST)
+    # the host-loop driver runs the loop's kernels: the same bits as the
+    # graph-driven loop
+    limit = ctx.cluster_solve()[0]
+    ctx.set_cluster_solve(0)
     try:
+        x1, _, s1 = S.solve(b, rtol=1e-8)
+        ctx.set_driver(ssg.SSG_DRIVER_HOST)
         x3, rc3, s3 = S.solve(b, rtol=1e-8)
     finally:
         ctx.set_driver(ssg.SSG_DRIVER_GRAPH)
+        ctx.set_cluster_solve(limit)
     assert rc3 == ssg.SSG_OK and s3[0]["iters"] == s1[0]["iters"]
     assert np.array_equal(x3.cpu().numpy(), x1.cpu().numpy())
 
@@ -246,6 +275,7 @@ def test_full_size_solve_128cube(ctx):
     the iteration count and the 2 kappa rtol solution bound, the 1e-12 solve
     the 1e-10 solution parity on 4096 sampled entries.  Early iterates are
     compared with the oracle live."""
+    _loop_only(ctx)
     p = config_problem(2)
     S = _sys(ctx, p.A, p.part, p.P)
     b = p.b[:, 0]
@@ -277,6 +307,7 @@ def test_full_size_solve_128cube_every_entry(ctx):
     per subdomain; a few seconds on all host cores): relative 2-norm error
     <= 1e-10 (the FP64 bound of converged solutions) and every entry within
     1e-9 of the largest."""
+    _loop_only(ctx)
     p = config_problem(2)
     S = _sys(ctx, p.A, p.part, p.P)
     b = p.b[:, 0]
