@@ -127,15 +127,17 @@ int ssg_set_slice_sort(ssg_ctx *ctx, int32_t window);
  * cluster of up to 16 CTAs, one per SM, instead of three kernels per
  * iteration.  Its CTAs exchange the weighted dots' per-CTA sums through
  * distributed shared memory and add them in one fixed order in every CTA,
- * and meet at three cluster barriers per iteration.  The product's rows and
+ * and meet at two cluster barriers per iteration.  The product's rows and
  * interface sums are the same bits as the multi-kernel loop's.  The dots'
  * partial sums are grouped differently, so iterates agree to rounding and the
  * iteration count may differ by a few.  max_nloc = 0 turns it off; default
- * 65536.  Applies to solves issued afterwards, on systems partitioned on this
- * context; SSG_E_INVALID for max_nloc < 0.
+ * 65536.  ctas: CTAs per cluster (2, 4, 8 or 16, capped at what the device
+ * places), or 0 for the device's largest.  max_nloc applies to solves issued
+ * afterwards; ctas to systems partitioned on this context afterwards.
+ * SSG_E_INVALID for max_nloc < 0 or another ctas.
  */
-int ssg_set_cluster_solve(ssg_ctx *ctx, int64_t max_nloc);
-/* The current limit, and the CTAs per cluster the device places (0: the
+int ssg_set_cluster_solve(ssg_ctx *ctx, int64_t max_nloc, int32_t ctas);
+/* The current limit, and the most CTAs per cluster the device places (0: the
  * one-cluster solve is unavailable and never used).  Either pointer may be
  * NULL. */
 int ssg_get_cluster_solve(const ssg_ctx *ctx, int64_t *max_nloc, int32_t *ctas);

@@ -287,6 +287,14 @@ int slice_window(const HostMaps &M, int32_t s, int policy) {
     return best_bytes <= 0.98 * base ? best : 1;
 }
 
+// CTAs per cluster of a system's one-cluster solve: the count asked for on
+// the context, else the most the device places.
+int cluster_ctas_for(const ssg_ctx *C, int64_t nloc) {
+    (void)nloc;
+    if (C->cluster_ctas <= 0) return 0;
+    return C->cluster_ctas_set > 0 ? std::min(C->cluster_ctas_set, C->cluster_ctas) : C->cluster_ctas;
+}
+
 // seg_sub: subdomains of each segment (independent systems), [nseg + 1];
 // sort_policy: the sorting window of the interior slices (slice_window).
 WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &seg_sub, int sort_policy,
@@ -716,7 +724,8 @@ int upload(ssg_system *S) {
         S->seg_rhs_off = {0};
     }
     S->nseg = static_cast<int32_t>(S->seg_sub.size()) - 1;
-    WorkPlan plan = make_plan(M, C->num_sms, S->seg_sub, C->slice_sort, S->nseg == 1 ? C->cluster_ctas : 0);
+    const int cl_ctas = S->nseg == 1 ? cluster_ctas_for(C, M.nloc) : 0;
+    WorkPlan plan = make_plan(M, C->num_sms, S->seg_sub, C->slice_sort, cl_ctas);
     S->slice_slots = plan.slice_slots;
     S->slice_entries = plan.slice_entries;
     S->sorted_subdomains = plan.sorted_subdomains;
@@ -933,7 +942,7 @@ int upload(ssg_system *S) {
     S->grid_spmmB = plan.gridB;
     if (!plan.range_cluster.empty()) {
         S->range_cluster = static_cast<const int2 *>(at(i_rcluster));
-        S->cluster_ctas = C->cluster_ctas;
+        S->cluster_ctas = cl_ctas;
         S->cluster_nranges = plan.cluster_nranges;
     }
     S->nchunks = static_cast<int32_t>(plan.chunk.size());
@@ -1077,8 +1086,8 @@ int pick_cluster_ctas(cudaStream_t st) {
 // Whether a single-vector FP64 solve of S runs as the one-cluster kernel.
 bool use_cluster(const ssg_system *S, bool mixed) {
     const ssg_ctx *C = S->ctx;
-    return !mixed && C->driver == SSG_DRIVER_GRAPH && S->cluster_ctas > 0 && S->cluster_ctas == C->cluster_ctas &&
-           S->maps.nloc <= C->cluster_max_n && S->nseg == 1;
+    return !mixed && C->driver == SSG_DRIVER_GRAPH && S->cluster_ctas > 0 && S->maps.nloc <= C->cluster_max_n &&
+           S->nseg == 1;
 }
 
 int launch_cluster_cg(ssg_system *S, cudaStream_t st, bool pc) {
@@ -1784,12 +1793,13 @@ int ssg_set_slice_sort(ssg_ctx *ctx, int32_t window) {
     return SSG_OK;
 }
 
-int ssg_set_cluster_solve(ssg_ctx *ctx, int64_t max_nloc) {
-    if (!ctx || max_nloc < 0) {
-        set_error("ssg_set_cluster_solve: null context, or max_nloc < 0");
+int ssg_set_cluster_solve(ssg_ctx *ctx, int64_t max_nloc, int32_t ctas) {
+    if (!ctx || max_nloc < 0 || (ctas != 0 && ctas != 2 && ctas != 4 && ctas != 8 && ctas != 16)) {
+        set_error("ssg_set_cluster_solve: null context, max_nloc < 0, or ctas not 0, 2, 4, 8 or 16");
         return SSG_E_INVALID;
     }
     ctx->cluster_max_n = max_nloc;
+    ctx->cluster_ctas_set = ctas;
     return SSG_OK;
 }
 

@@ -4,7 +4,7 @@
 // On a system whose vectors and matrix sit in L2 (tens of thousands of
 // local entries) an iteration of the three-kernel loop costs the latency of
 // three kernel boundaries, not bandwidth.  Here the CTAs of one cluster (up
-// to 16, one per SM) run the iteration with three cluster barriers instead:
+// to 16, one per SM) run the iteration with two cluster barriers instead:
 // the product's work items are split among the cluster's warps (the same
 // items, rows in the same order and interface copies summed in the same
 // order as the multi-block product), each CTA sums its share of a dot in a
@@ -76,21 +76,43 @@ __device__ __forceinline__ void cluster_sums(cooperative_groups::cluster_group &
     __syncthreads();
 }
 
+// The direction the product gathers in iteration k, formed where it is
+// read: p_k[j] = z_k[j] + beta_{k-1} p_{k-1}[j] (Algorithm 3 line 8, z = r,
+// or dinv r with the diagonal preconditioner), the same FMA on the same
+// operands as the update that stores p_k, so the same bits.  r and p are
+// rewritten by other CTAs between products and are read through L2.
+template <bool PC>
+struct PNext {
+    const double *r, *p, *dinv;
+    double beta;
+    __device__ __forceinline__ double operator()(int j) const {
+        const double rj = __ldcg(r + j);
+        return fma(beta, __ldcg(p + j), PC ? rj * __ldg(dinv + j) : rj);
+    }
+};
+
 // One solve of S x = b on the concatenated local vectors.  The caller has
 // scattered b into b, x holds x_1 (zero, or the scattered guess) and, with a
 // guess, q = S x_1.  Launched as one cluster of gridDim.x CTAs.  Product
 // items: warp w of CTA c takes A.warp_range[w * gridDim.x + c] (ranges cut
 // for the whole cluster, dealt out to the CTAs in turn); the non-empty
 // ranges are the first `nranges`.  Vector entries: CTA c takes a contiguous
-// run of whole warps' worth.  The setup, the stopping rule (recursive
-// residual sqrt((r, r)_w) <= rtol ||b||_w after an iteration, or max_iter),
-// the breakdown test and the state written to s at the end are those of the
-// three-kernel loop.
+// run of whole warps' worth.
+//
+// Iteration k: q = S p_k with p_k formed as the product gathers it (PNext),
+// then one cluster-wide sum gives alpha_k; each CTA stores p_k on its
+// entries (the product's gathers of p_{k-1} are over: they precede that
+// sum), x <- x + alpha_k p_k, r <- r - alpha_k q, and a second cluster-wide
+// sum gives (r, r)_w (and (r, z)_w), beta_k and the stopping test.  Two
+// cluster barriers per iteration; the operations and their operands are
+// those of the three-kernel loop, in its order for every entry.  The setup,
+// the stopping rule (recursive residual sqrt((r, r)_w) <= rtol ||b||_w after
+// an iteration, or max_iter), the breakdown test and the state written to s
+// at the end are the loop's; p is left holding the last p_k, not p_{k+1}.
 template <bool PC>
 __global__ void __launch_bounds__(kClusterThreads, 1)
     k_cg_cluster(DevOp A, int64_t N, int nranges, const double *__restrict__ b, double *__restrict__ x,
-                 double *__restrict__ r, double *__restrict__ p, double *__restrict__ q,
-                 const double *__restrict__ dinv, Scal *s) {
+                 double *r, double *p, double *q, const double *__restrict__ dinv, Scal *s) {
     namespace cgr = cooperative_groups;
     constexpr int NZ = PC ? 2 : 1;  // sums after the residual update: (r, r)_w [, (r, z)_w]
     cgr::cluster_group cl = cgr::this_cluster();
@@ -132,6 +154,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         cs.rr = t[0];
         cs.rho = PC ? t[2] : t[0];
         cs.bnorm = sqrt(t[1]);
+        // p_0 = z_0 = fma(0, p, z_0): the gather's form with beta = 0
         cs.pq = cs.alpha = cs.beta = 0.0;
         cs.k = 0;
         cs.status = SSG_E_NOT_CONVERGED;
@@ -145,9 +168,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     });
     // every CTA reads the same cs.run after the same barrier
     while (cs.run) {
-        // lines 2-3: q = S p (p complete in every CTA: the previous cluster
-        // barrier), alpha = rho / (p, S p)_w
-        const double v1[1] = {spmv_items<double, 0, true>(A, range, p, q, lane)};
+        // lines 2-3: q = S p_k, alpha = rho / (p_k, S p_k)_w; r and p complete
+        // in every CTA (the previous cluster barrier)
+        const double beta = cs.beta;
+        const double v1[1] = {spmv_items<double, 0, false>(A, range, PNext<PC>{r, p, dinv, beta}, q, lane)};
         cluster_sums<1>(cl, red, slot, phase++, wspmv, v1, [&](const double(&t)[1]) {
             cs.pq = t[0];
             if (!(cs.pq > 0.0) || !isfinite(cs.pq)) {
@@ -158,12 +182,17 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
             }
         });
         if (!cs.run) break;
-        // line 5: r <- r - alpha q and (r, r)_w (and (r, z)_w); q was written
-        // by other CTAs' warps and is read through L2
+        // lines 4-5 and this CTA's share of line 8's p_k: p_k = z_k + beta
+        // p_{k-1}, x <- x + alpha p_k, r <- r - alpha q and (r, r)_w (and
+        // (r, z)_w); q was written by other CTAs' warps and is read through L2
         const double alpha = cs.alpha;
         double acc = 0.0, acz = 0.0;
         for (int64_t i = e0 + threadIdx.x; i < e1; i += kClusterThreads) {
-            const double ri = fma(-alpha, __ldcg(q + i), r[i]);
+            const double r0 = r[i];
+            const double pk = fma(beta, p[i], PC ? r0 * dinv[i] : r0);
+            p[i] = pk;
+            x[i] = fma(alpha, pk, x[i]);
+            const double ri = fma(-alpha, __ldcg(q + i), r0);
             r[i] = ri;
             const unsigned int m = mult[i];
             const double wi = m == 1u ? ri : __ldg(wtab + m) * ri;
@@ -187,15 +216,6 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
                 cs.run = 0;
             }
         });
-        // lines 4, 7, 8: x <- x + alpha p, p <- z + beta p (this CTA's entries)
-        const double beta = cs.beta;
-        for (int64_t i = e0 + threadIdx.x; i < e1; i += kClusterThreads) {
-            const double pi = p[i];
-            x[i] = fma(alpha, pi, x[i]);
-            p[i] = fma(beta, pi, PC ? r[i] * dinv[i] : r[i]);
-        }
-        // p complete in every CTA before the next product gathers it
-        if (cs.run) cl.sync();
     }
     // no CTA exits while another may still read its shared memory
     cl.sync();

@@ -313,31 +313,39 @@ template <>
 __device__ __forceinline__ float wtab_of<float>(const DevOp &A, int m) { return __ldg(A.wtab32 + m); }
 
 // [spmv-source-begin] the single-vector SpMV kernel and its helpers
-// Gathers of the product's input x: through the read-only path when x stays
-// constant for the whole kernel (every product launch), or L2-coherent
-// (COH) when the same kernel rewrites x between products (the one-cluster
-// solve, whose direction vector changes every iteration).
-template <bool COH, typename T>
-__device__ __forceinline__ T ldx(const T *p) {
-    if constexpr (COH) return __ldcg(p);
+// The product's input x_j, gathered by column: through the read-only path,
+// x being constant for the whole kernel (every product launch).  The
+// one-cluster solve passes its own gather instead (cluster.cuh).
+template <typename T>
+struct XRead {
+    const T *__restrict__ x;
+    __device__ __forceinline__ T operator()(int j) const { return __ldg(x + j); }
+};
+
+// Matrix loads: streamed with L2 evict-first (every product launch: the
+// matrix is read once per launch), or through L1 (STREAM = false: the
+// one-cluster solve, whose CTAs read the same slices every iteration).
+template <bool STREAM, typename U>
+__device__ __forceinline__ U ldm(const U *p) {
+    if constexpr (STREAM) return __ldcs(p);
     else return __ldg(p);
 }
 
 // N consecutive entries (k0 .. k0+N-1) of a lane's sliced-ELL row: all
 // loads first (the value and column loads of a warp are contiguous and
 // coalesced, streamed with L2 evict-first), then the FMA chain in order.
-template <int N, bool COH, typename T>
-__device__ __forceinline__ T slice_chunk(const T *__restrict__ sv, const int32_t *__restrict__ sc,
-                                         const T *__restrict__ x, int base, int k0, T acc) {
+template <int N, bool STREAM, typename T, typename XL>
+__device__ __forceinline__ T slice_chunk(const T *__restrict__ sv, const int32_t *__restrict__ sc, const XL &X,
+                                         int base, int k0, T acc) {
     T vv[N], xv[N];
     int cc[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-        vv[j] = __ldcs(sv + base + (k0 + j) * kSliceRows);
-        cc[j] = __ldcs(sc + base + (k0 + j) * kSliceRows);
+        vv[j] = ldm<STREAM>(sv + base + (k0 + j) * kSliceRows);
+        cc[j] = ldm<STREAM>(sc + base + (k0 + j) * kSliceRows);
     }
 #pragma unroll
-    for (int j = 0; j < N; ++j) xv[j] = ldx<COH>(x + cc[j]);
+    for (int j = 0; j < N; ++j) xv[j] = X(cc[j]);
 #pragma unroll
     for (int j = 0; j < N; ++j) acc = fma(vv[j], xv[j], acc);
     return acc;
@@ -348,41 +356,41 @@ __device__ __forceinline__ T slice_chunk(const T *__restrict__ sv, const int32_t
 // zero-valued padding, which leaves the sum unchanged.  Every lane runs
 // exactly w FMAs: on this part a predicated-off FP64 instruction still takes
 // its issue slot, so nothing here is predicated.
-template <bool COH, typename T>
-__device__ __forceinline__ T slice_row(const T *__restrict__ sv, const int32_t *__restrict__ sc,
-                                       const T *__restrict__ x, int off, int w, int lane) {
+template <bool STREAM, typename T, typename XL>
+__device__ __forceinline__ T slice_row(const T *__restrict__ sv, const int32_t *__restrict__ sc, const XL &X,
+                                       int off, int w, int lane) {
     const int base = off + lane;
     T acc = T(0);
     int k = 0;
-    for (; k + 8 <= w; k += 8) acc = slice_chunk<8, COH>(sv, sc, x, base, k, acc);
+    for (; k + 8 <= w; k += 8) acc = slice_chunk<8, STREAM>(sv, sc, X, base, k, acc);
     switch (w - k) {
-        case 1: return slice_chunk<1, COH>(sv, sc, x, base, k, acc);
-        case 2: return slice_chunk<2, COH>(sv, sc, x, base, k, acc);
-        case 3: return slice_chunk<3, COH>(sv, sc, x, base, k, acc);
-        case 4: return slice_chunk<4, COH>(sv, sc, x, base, k, acc);
-        case 5: return slice_chunk<5, COH>(sv, sc, x, base, k, acc);
-        case 6: return slice_chunk<6, COH>(sv, sc, x, base, k, acc);
-        case 7: return slice_chunk<7, COH>(sv, sc, x, base, k, acc);
+        case 1: return slice_chunk<1, STREAM>(sv, sc, X, base, k, acc);
+        case 2: return slice_chunk<2, STREAM>(sv, sc, X, base, k, acc);
+        case 3: return slice_chunk<3, STREAM>(sv, sc, X, base, k, acc);
+        case 4: return slice_chunk<4, STREAM>(sv, sc, X, base, k, acc);
+        case 5: return slice_chunk<5, STREAM>(sv, sc, X, base, k, acc);
+        case 6: return slice_chunk<6, STREAM>(sv, sc, X, base, k, acc);
+        case 7: return slice_chunk<7, STREAM>(sv, sc, X, base, k, acc);
         default: return acc;
     }
 }
 
 // Writes of one slice's results: interior rows, or interface copy rows whose
 // node sums are formed by shuffles in ascending subdomain order.
-template <bool COH, typename T>
-__device__ __forceinline__ void finish_slice(const DevOp &A, const WorkItem &W, T acc, const T *__restrict__ x,
+template <typename T, typename XL>
+__device__ __forceinline__ void finish_slice(const DevOp &A, const WorkItem &W, T acc, const XL &X,
                                              T *__restrict__ y, int lane, T &dot) {
     if (W.kind == kItemSlice) {
         const int r = W.a + lane;
         if (r < W.b) {
             y[r] = acc;
-            dot = fma(ldx<COH>(x + r), acc, dot);
+            dot = fma(X(r), acc, dot);
         }
     } else if (W.kind == kItemSortedSlice) {
         if (W.a + lane < W.b) {
             const int r = __ldg(A.srow + W.a + lane);
             y[r] = acc;
-            dot = fma(ldx<COH>(x + r), acc, dot);
+            dot = fma(X(r), acc, dot);
         }
     } else {
         const int c = W.a + lane;
@@ -401,17 +409,17 @@ __device__ __forceinline__ void finish_slice(const DevOp &A, const WorkItem &W, 
         if (valid) {
             const int row = __ldg(A.icopy + c);
             y[row] = S;
-            dot = fma(wtab_of<T>(A, m) * ldx<COH>(x + row), S, dot);
+            dot = fma(wtab_of<T>(A, m) * X(row), S, dot);
         }
     }
 }
 
 // The work items [range.x, range.y) of one warp: y = S x on their rows, the
-// interface sums, and the lane's share of (x, y)_w returned.  AHEAD: slices
-// ahead whose value and column lines are prefetched into L2 (0: none).
-template <typename T, int AHEAD, bool COH = false>
-__device__ __forceinline__ T spmv_items(const DevOp &A, int2 range, const T *__restrict__ x, T *__restrict__ y,
-                                        int lane) {
+// interface sums, and the lane's share of (x, y)_w returned; x_j = X(j).
+// AHEAD: slices ahead whose value and column lines are prefetched into L2
+// (0: none); STREAM: how the slices are loaded (ldm).
+template <typename T, int AHEAD, bool STREAM = true, typename XL>
+__device__ __forceinline__ T spmv_items(const DevOp &A, int2 range, const XL &X, T *__restrict__ y, int lane) {
     const T *__restrict__ sv = slice_vals<T>(A);
     const T *__restrict__ val = row_vals<T>(A);
     const T *__restrict__ ival = copy_vals<T>(A);
@@ -428,16 +436,16 @@ __device__ __forceinline__ T spmv_items(const DevOp &A, int2 range, const T *__r
             }
         }
         if (sliced_item(W.kind)) {
-            const T acc = slice_row<COH, T>(sv, A.scol, x, W.e0, W.e1, lane);
-            finish_slice<COH>(A, W, acc, x, y, lane, dot);
+            const T acc = slice_row<STREAM, T>(sv, A.scol, X, W.e0, W.e1, lane);
+            finish_slice<T>(A, W, acc, X, y, lane, dot);
         } else if (W.kind == kItemLongRow) {
             // one long row: lane-strided partial sums, fixed warp tree
             T acc = T(0);
-            for (int k = W.e0 + lane; k < W.e1; k += 32) acc = fma(val[k], ldx<COH>(x + A.col[k]), acc);
+            for (int k = W.e0 + lane; k < W.e1; k += 32) acc = fma(val[k], X(A.col[k]), acc);
             const T racc = T(warp_sum(double(acc)));
             if (lane == 0) {
                 y[W.a] = racc;
-                dot = fma(ldx<COH>(x + W.a), racc, dot);
+                dot = fma(X(W.a), racc, dot);
             }
         } else {
             // one interface node with long copy rows: each copy row reduced by
@@ -446,7 +454,7 @@ __device__ __forceinline__ T spmv_items(const DevOp &A, int2 range, const T *__r
             for (int c = W.c0; c < W.c1; ++c) {
                 T acc = T(0);
                 for (int k = A.irp[c] + lane; k < A.irp[c + 1]; k += 32)
-                    acc = fma(ival[k], ldx<COH>(x + A.icol[k]), acc);
+                    acc = fma(ival[k], X(A.icol[k]), acc);
                 S += T(warp_sum(double(acc)));  // valid in lane 0
             }
             if (lane == 0) {
@@ -454,7 +462,7 @@ __device__ __forceinline__ T spmv_items(const DevOp &A, int2 range, const T *__r
                 for (int c = W.c0; c < W.c1; ++c) {
                     const int row = A.icopy[c];
                     y[row] = S;
-                    dot = fma(w * ldx<COH>(x + row), S, dot);
+                    dot = fma(w * X(row), S, dot);
                 }
             }
         }
@@ -473,7 +481,7 @@ __global__ void __launch_bounds__(kSpmvThreads, BPS)
     if (EPI == kEpiPartials && (s->brk || s->halt[s->iter & 1])) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 range = A.warp_range[blockIdx.x * kSpmvWarps + warp];
-    const T dot = spmv_items<T, AHEAD>(A, range, x, y, lane);
+    const T dot = spmv_items<T, AHEAD>(A, range, XRead<T>{x}, y, lane);
     // fixed-order reduction.  FP32: lanes of each warp in FP32, then the
     // block's warps in order in FP64.  FP64: through shared memory, one warp
     // adding the block's 256 values (12 FP64 warp instructions per block

@@ -227,7 +227,7 @@ def lib():
         L.ssg_wdot_noalloc.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
         L.ssg_set_batch_graph.argtypes = [vp, C.c_int32]
         L.ssg_set_slice_sort.argtypes = [vp, C.c_int32]
-        L.ssg_set_cluster_solve.argtypes = [vp, C.c_int64]
+        L.ssg_set_cluster_solve.argtypes = [vp, C.c_int64, C.c_int32]
         L.ssg_get_cluster_solve.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.ssg_autotune_block.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(ssg_tune_block)]
         L.ssg_get_layout.argtypes = [vp, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")]
@@ -589,8 +589,8 @@ def ssg_set_slice_sort(ctx, window: int):
     return _check(lib().ssg_set_slice_sort(ctx, int(window)), "ssg_set_slice_sort")
 
 
-def ssg_set_cluster_solve(ctx, max_nloc: int):
-    return _check(lib().ssg_set_cluster_solve(ctx, int(max_nloc)), "ssg_set_cluster_solve")
+def ssg_set_cluster_solve(ctx, max_nloc: int, ctas: int = 0):
+    return _check(lib().ssg_set_cluster_solve(ctx, int(max_nloc), int(ctas)), "ssg_set_cluster_solve")
 
 
 def ssg_get_cluster_solve(ctx) -> tuple:
@@ -661,10 +661,11 @@ class Context:
         (systems partitioned afterwards)."""
         ssg_set_slice_sort(self.h, window)
 
-    def set_cluster_solve(self, max_nloc: int = 65536):
+    def set_cluster_solve(self, max_nloc: int = 65536, ctas: int = 0):
         """Single-vector FP64 solves of systems with at most max_nloc local entries
-        run as one thread-block cluster (0: never)."""
-        ssg_set_cluster_solve(self.h, max_nloc)
+        run as one thread-block cluster (0: never) of ctas CTAs (0: the device's
+        largest; systems partitioned afterwards)."""
+        ssg_set_cluster_solve(self.h, max_nloc, ctas)
 
     def cluster_solve(self) -> tuple:
         """(max_nloc, CTAs per cluster; 0 when the device places none)."""

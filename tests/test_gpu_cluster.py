@@ -274,4 +274,6 @@ def test_cluster_setting_checked(ctx):
     with pytest.raises(ssg.SSGError):
         ctx.set_cluster_solve(-1)
     limit, ctas = ctx.cluster_solve()
+    with pytest.raises(ssg.SSGError):
+        ctx.set_cluster_solve(limit, 3)
     assert limit == 65536 and ctas in (2, 4, 8, 16)
