@@ -38,6 +38,7 @@ def ctx():
     if c.cluster_solve()[1] == 0:
         c.close()
         pytest.skip("the device places no cluster for the one-cluster solve")
+    c.set_cluster_solve(FORCE)  # every case here through the cluster, whatever its size
     yield c
     torch.cuda.synchronize()
     c.close()
@@ -55,6 +56,8 @@ def _rel(a, b):
 
 # scatter, parameters, the cluster kernel, gather, true residual (product + dot)
 CLUSTER_LAUNCHES = 6
+DEFAULT_LIMIT = 12288  # local entries (ssg_set_cluster_solve's default)
+FORCE = 1 << 20
 
 
 def _hub(rng, n=3000):
@@ -105,7 +108,6 @@ def test_cluster_matches_oracle(ctx, name, A, part, P, mode):
     from paper_2108_13162_gb300.ssg import System
 
     S = System(ctx, A, part, P)
-    assert S.sizes.nloc <= ctx.cluster_solve()[0]
     ref = oracle.Partition(A, part, P)
     b = np.random.default_rng(5).uniform(-1, 1, A.n)
     run = ref.pcg if mode == ssg.SSG_FP64_JACOBI else ref.cg
@@ -271,9 +273,14 @@ def test_cluster_guess_and_edges(ctx):
 def test_cluster_setting_checked(ctx):
     from paper_2108_13162_gb300 import ssg
 
+    from paper_2108_13162_gb300.ssg import Context
+
     with pytest.raises(ssg.SSGError):
         ctx.set_cluster_solve(-1)
     limit, ctas = ctx.cluster_solve()
     with pytest.raises(ssg.SSGError):
         ctx.set_cluster_solve(limit, 3)
-    assert limit == 65536 and ctas in (2, 4, 8, 16)
+    assert limit == FORCE and ctas in (2, 4, 8, 16)
+    c = Context(0)
+    assert c.cluster_solve()[0] == DEFAULT_LIMIT
+    c.close()

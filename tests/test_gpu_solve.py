@@ -44,8 +44,9 @@ def ctx(request):
     if request.param == "cluster" and c.cluster_solve()[1] == 0:
         c.close()
         pytest.skip("the device places no cluster for the one-cluster solve")
-    if request.param == "loop":
-        c.set_cluster_solve(0)
+    # the cluster pass runs every small system through the cluster, whatever
+    # its size; the loop pass turns it off
+    c.set_cluster_solve(1 << 20 if request.param == "cluster" else 0)
     c.path = request.param
     yield c
     torch.cuda.synchronize()
