@@ -119,17 +119,6 @@ int ssg_set_unroll(ssg_ctx *ctx, int32_t iters);
  * to systems partitioned on this context afterwards; SSG_E_INVALID for
  * window < -1. */
 int ssg_set_slice_sort(ssg_ctx *ctx, int32_t window);
-/* Column indices of the sliced-ELL copy the products stream (a layout of
- * this library, not of the paper; the products are the same bits either
- * way).  bits = 0 (default): when every subdomain holds at most 65536 local
- * entries, each column is stored as a 16-bit offset from the first local
- * entry of its row's subdomain (a slice of interior rows lies in one
- * subdomain and carries that base; an interface slice takes each copy's
- * base from a per-copy table), so a stored entry moves 10 bytes in FP64 and
- * 6 in FP32 instead of 12 and 8; otherwise 32-bit concatenated indices.
- * bits = 32: always 32-bit.  Applies to systems partitioned on this context
- * afterwards; SSG_E_INVALID for other values. */
-int ssg_set_col_index(ssg_ctx *ctx, int32_t bits);
 /*
  * One-cluster solve of small systems (Algorithm 3 of Section 3.4, the whole
  * iteration loop in one kernel launch).  Under the graph driver, a
@@ -279,11 +268,10 @@ int ssg_set_batch_graph(ssg_system *sys, int32_t one_graph);
  */
 int ssg_measure_fp64_rate(ssg_ctx *ctx, int32_t iters, int32_t reps, double *tflops, double *best_ms);
 int ssg_get_sizes(const ssg_system *sys, ssg_sizes *out);
-/* The interior slice layout a system got (ssg_set_slice_sort,
- * ssg_set_col_index): out[0] = entries stored in interior slices (padding
- * included), out[1] = nonzeros they hold, out[2] = subdomains whose slices
- * are sorted by row length, out[3] = the largest sorting window (1: none),
- * out[4] = bytes per stored column index (2 or 4).  Host memory, 5 int64. */
+/* The interior slice layout a system got (ssg_set_slice_sort): out[0] =
+ * entries stored in interior slices (padding included), out[1] = nonzeros
+ * they hold, out[2] = subdomains whose slices are sorted by row length,
+ * out[3] = the largest sorting window (1: none).  Host memory, 4 int64. */
 int ssg_get_layout(const ssg_system *sys, int64_t *out);
 
 /*

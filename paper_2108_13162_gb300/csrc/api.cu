@@ -60,7 +60,6 @@ struct ssg_system {
     // entries, subdomains sorted by row length, the largest sorting window
     int64_t slice_slots = 0, slice_entries = 0;
     int32_t sorted_subdomains = 0, max_window = 1;
-    int32_t col_bytes = 4;  // bytes per sliced-ELL column (2: 16-bit offsets from the subdomain base)
     int grid_spmv = 0;
     int grid_spmv32 = 0;
     int grid_bps[7] = {0, 0, 0, 0, 0, 0, 0};        // single-vector grids for 3 to 6 blocks per SM
@@ -192,11 +191,6 @@ struct WorkPlan {
     std::vector<int32_t> isrc, ssrc;  // local entry each copy-row / sliced value copies (-1: padding)
     std::vector<double> sval;        // sliced-ELL values
     std::vector<int32_t> scol, sseg;
-    // 16-bit columns (col16): offsets from the row's subdomain base, and the
-    // base of each interface copy's subdomain
-    bool col16 = false;
-    std::vector<uint16_t> scol16;
-    std::vector<int32_t> cbase;
     std::vector<int32_t> srow;       // sorted slices: the local row of each slot
     int64_t slice_slots = 0;         // interior slice entries stored (padding included)
     int64_t slice_entries = 0;       // interior nonzeros in slices
@@ -302,16 +296,12 @@ int cluster_ctas_for(const ssg_ctx *C) {
 
 // seg_sub: subdomains of each segment (independent systems), [nseg + 1];
 // sort_policy: the sorting window of the interior slices (slice_window).
-// col_bits: 32 for 32-bit slice columns always, else 16-bit offsets from the
-// subdomain base when every subdomain has at most 65536 local entries.
 WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &seg_sub, int sort_policy,
-                   int cluster_ctas, int col_bits) {
+                   int cluster_ctas) {
     WorkPlan W;
     std::vector<int32_t> sub_of(static_cast<size_t>(M.nloc));
     for (int32_t s = 0; s < M.P; ++s)
         for (int64_t r = M.off[s]; r < M.off[s + 1]; ++r) sub_of[r] = s;
-    W.col16 = col_bits != 32;
-    for (int32_t s = 0; s < M.P; ++s) W.col16 = W.col16 && M.off[s + 1] - M.off[s] <= 65536;
     auto rlen = [&](int32_t r) { return M.lrowptr[r + 1] - M.lrowptr[r]; };
     // interface copy rows in (node, copy) order, columns as concatenated index
     W.irp.assign(static_cast<size_t>(M.ncopies) + 1, 0);
@@ -353,15 +343,14 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
                     W.scol.push_back(row);
                     W.ssrc.push_back(-1);
                 }
-                if (W.col16) W.scol16.push_back(static_cast<uint16_t>(W.scol.back() - o));
             }
         W.slice_slots += static_cast<int64_t>(w) * kSliceRows;
         if (sorted) {
             const int32_t slot0 = static_cast<int32_t>(W.srow.size());
             W.srow.insert(W.srow.end(), rws, rws + cnt);
-            rows.push_back({kItemSortedSlice, slot0, slot0 + cnt, off, w, 0, 0, o});
+            rows.push_back({kItemSortedSlice, slot0, slot0 + cnt, off, w, 0, 0, 0});
         } else {
-            rows.push_back({kItemSlice, rws[0], rws[0] + cnt, off, w, 0, 0, o});
+            rows.push_back({kItemSlice, rws[0], rws[0] + cnt, off, w, 0, 0, 0});
         }
     };
     for (int32_t s = 0; s < M.P; ++s) {
@@ -439,20 +428,9 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
                     W.scol.push_back(M.icopy[c < c1 ? c : c0]);
                     W.ssrc.push_back(-1);
                 }
-                // 16-bit: offset from the copy's subdomain base; lanes past
-                // the slice's copies (base 0) gather entry 0 for their
-                // discarded padding
-                if (W.col16)
-                    W.scol16.push_back(c < c1 ? static_cast<uint16_t>(W.scol.back() - M.off[sub_of[M.icopy[c]]]) : 0);
             }
         iface.push_back({kItemIfaceSlice, c0, c1, off, w, 0, 0, 0});
         g = g1;
-    }
-    if (W.col16) {
-        W.cbase.resize(static_cast<size_t>(M.ncopies));
-        for (int64_t c = 0; c < M.ncopies; ++c) W.cbase[c] = M.off[sub_of[M.icopy[c]]];
-        W.scol.clear();
-        W.scol.shrink_to_fit();
     }
     // per segment, interface item j goes after interior item floor((j+1) *
     // nrows / (niface+1)) of the segment
@@ -746,12 +724,11 @@ int upload(ssg_system *S) {
     }
     S->nseg = static_cast<int32_t>(S->seg_sub.size()) - 1;
     const int cl_ctas = S->nseg == 1 ? cluster_ctas_for(C) : 0;
-    WorkPlan plan = make_plan(M, C->num_sms, S->seg_sub, C->slice_sort, cl_ctas, C->col_bits);
+    WorkPlan plan = make_plan(M, C->num_sms, S->seg_sub, C->slice_sort, cl_ctas);
     S->slice_slots = plan.slice_slots;
     S->slice_entries = plan.slice_entries;
     S->sorted_subdomains = plan.sorted_subdomains;
     S->max_window = plan.max_window;
-    S->col_bytes = plan.col16 ? 2 : 4;
     const int64_t N = M.nloc;
     // concatenated column ids
     std::vector<int32_t> gcol(static_cast<size_t>(M.nnz));
@@ -811,8 +788,6 @@ int upload(ssg_system *S) {
     size_t i_sval = add(plan.sval.data(), sizeof(double) * plan.sval.size());
     size_t i_sval32 = add(sval32.data(), sizeof(float) * sval32.size());
     size_t i_scol = add(plan.scol.data(), sizeof(int32_t) * plan.scol.size());
-    size_t i_scol16 = add(plan.scol16.data(), sizeof(uint16_t) * plan.scol16.size());
-    size_t i_cbase = add(plan.cbase.data(), sizeof(int32_t) * plan.cbase.size());
     size_t i_sseg = add(plan.sseg.data(), sizeof(int32_t) * plan.sseg.size());
     size_t i_srow = add(plan.srow.data(), sizeof(int32_t) * plan.srow.size());
     size_t i_items = add(plan.items.data(), sizeof(WorkItem) * plan.items.size());
@@ -931,10 +906,7 @@ int upload(ssg_system *S) {
     S->op.ival = static_cast<const double *>(at(i_ival));
     S->op.sval = static_cast<const double *>(at(i_sval));
     S->op.sval32 = static_cast<const float *>(at(i_sval32));
-    S->op.scol = plan.col16 ? nullptr : static_cast<const int32_t *>(at(i_scol));
-    S->op.scol16 = plan.col16 ? static_cast<const uint16_t *>(at(i_scol16)) : nullptr;
-    S->op.cbase = plan.col16 ? static_cast<const int32_t *>(at(i_cbase)) : nullptr;
-    S->col_bytes = plan.col16 ? 2 : 4;
+    S->op.scol = static_cast<const int32_t *>(at(i_scol));
     S->op.sseg = static_cast<const int32_t *>(at(i_sseg));
     S->op.srow = static_cast<const int32_t *>(at(i_srow));
     S->op.items = static_cast<const WorkItem *>(at(i_items));
@@ -1820,15 +1792,6 @@ int ssg_set_slice_sort(ssg_ctx *ctx, int32_t window) {
     return SSG_OK;
 }
 
-int ssg_set_col_index(ssg_ctx *ctx, int32_t bits) {
-    if (!ctx || (bits != 0 && bits != 32)) {
-        set_error("ssg_set_col_index: null context, or bits not 0 or 32");
-        return SSG_E_INVALID;
-    }
-    ctx->col_bits = bits;
-    return SSG_OK;
-}
-
 int ssg_set_cluster_solve(ssg_ctx *ctx, int64_t max_nloc, int32_t ctas) {
     if (!ctx || max_nloc < 0 || (ctas != 0 && ctas != 2 && ctas != 4 && ctas != 8 && ctas != 16)) {
         set_error("ssg_set_cluster_solve: null context, max_nloc < 0, or ctas not 0, 2, 4, 8 or 16");
@@ -1915,12 +1878,11 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
     } else {
         // host only: the interior slice layout the row-length rule gives
         // (ssg_get_layout), without a device
-        const WorkPlan plan = make_plan(S->maps, 1, {0, S->maps.P}, 0, 0, 0);
+        const WorkPlan plan = make_plan(S->maps, 1, {0, S->maps.P}, 0, 0);
         S->slice_slots = plan.slice_slots;
         S->slice_entries = plan.slice_entries;
         S->sorted_subdomains = plan.sorted_subdomains;
         S->max_window = plan.max_window;
-        S->col_bytes = plan.col16 ? 2 : 4;
     }
     *sys = S;
     return SSG_OK;
@@ -2540,7 +2502,6 @@ int ssg_get_layout(const ssg_system *S, int64_t *out) {
     out[1] = S->slice_entries;
     out[2] = S->sorted_subdomains;
     out[3] = S->max_window;
-    out[4] = S->col_bytes;
     return SSG_OK;
 }
 

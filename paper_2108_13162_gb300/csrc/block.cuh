@@ -188,12 +188,11 @@ __device__ __forceinline__ void store_vec(float *__restrict__ p, const float (&v
 // NC consecutive sliced-ELL entries for the lane's LPR rows of a slice (row
 // p * RPP + rl in pass p) and its VW columns: value and column loads
 // (broadcast within a row's lanes), then the NC * LPR x pieces, then the FMAs
-// in CSR order.  Columns: 32-bit concatenated indices (CT = int32_t), or
-// 16-bit offsets from the base cb[p] of pass p's row (CT = uint16_t).
-template <int NC, int LPR, int RPP, int VW, int K, typename T, typename CT>
-__device__ __forceinline__ void slice_chunk_v(const T *__restrict__ sv, const CT *__restrict__ sc,
-                                              const int (&cb)[LPR], const T *__restrict__ X, int base, int k0,
-                                              int col0, T (&acc)[LPR][VW]) {
+// in CSR order.
+template <int NC, int LPR, int RPP, int VW, int K, typename T>
+__device__ __forceinline__ void slice_chunk_v(const T *__restrict__ sv, const int32_t *__restrict__ sc,
+                                              const T *__restrict__ X, int base, int k0, int col0,
+                                              T (&acc)[LPR][VW]) {
     T v[NC][LPR];
     int c[NC][LPR];
 #pragma unroll
@@ -201,8 +200,7 @@ __device__ __forceinline__ void slice_chunk_v(const T *__restrict__ sv, const CT
 #pragma unroll
         for (int p = 0; p < LPR; ++p) {
             v[e][p] = __ldcs(sv + base + p * RPP + (k0 + e) * kSliceRows);
-            c[e][p] = static_cast<int>(__ldcs(sc + base + p * RPP + (k0 + e) * kSliceRows));
-            if constexpr (sizeof(CT) == 2) c[e][p] += cb[p];  // 16-bit offsets from the subdomain base
+            c[e][p] = __ldcs(sc + base + p * RPP + (k0 + e) * kSliceRows);
         }
     T xv[NC][LPR][VW];
 #pragma unroll
@@ -244,10 +242,7 @@ __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ 
             const WorkItem Wp = A.items[it + A.l2_ahead];
             if (sliced_item(Wp.kind) && lane < Wp.e1) {
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(sv + Wp.e0 + lane * kSliceRows));
-                if (A.scol16)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol16 + Wp.e0 + lane * kSliceRows));
-                else
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
             }
         }
         if (sliced_item(W.kind)) {
@@ -259,25 +254,10 @@ __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ 
 #pragma unroll
                 for (int u = 0; u < VW; ++u) acc[p][u] = T(0);
             const int base = W.e0 + rl;
-            int cb[LPR];
-#pragma unroll
-            for (int p = 0; p < LPR; ++p) cb[p] = 0;
-            auto rows = [&](const auto *sc) {
-                int k = 0;
-                for (; k + NC <= W.e1; k += NC)
-                    slice_chunk_v<NC, LPR, RPP, VW, K, T>(sv, sc, cb, X, base, k, col0, acc);
-                for (; k < W.e1; ++k) slice_chunk_v<1, LPR, RPP, VW, K, T>(sv, sc, cb, X, base, k, col0, acc);
-            };
-            if (A.scol16) {
-#pragma unroll
-                for (int p = 0; p < LPR; ++p) {
-                    const int c = W.a + p * RPP + rl;
-                    cb[p] = !iface ? W.pad : c < W.b ? __ldg(A.cbase + c) : 0;
-                }
-                rows(A.scol16);
-            } else {
-                rows(A.scol);
-            }
+            int k = 0;
+            for (; k + NC <= W.e1; k += NC)
+                slice_chunk_v<NC, LPR, RPP, VW, K, T>(sv, A.scol, X, base, k, col0, acc);
+            for (; k < W.e1; ++k) slice_chunk_v<1, LPR, RPP, VW, K, T>(sv, A.scol, X, base, k, col0, acc);
 #pragma unroll
             for (int pass = 0; pass < LPR; ++pass) {
                 const int sr = pass * RPP + rl;

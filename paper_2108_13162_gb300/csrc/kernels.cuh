@@ -100,8 +100,6 @@ enum { kTicketSpmv = 0, kTicketR = 1, kTicketXP = 2, kTicketMisc = 3 };
 //   kind 4: slice of interior rows taken from a window of one subdomain's
 //           rows sorted by length (SELL-C-sigma): lane l holds row srow[a + l]
 //           for a + l < b; sliced-ELL data at e0, width e1, as kind 0
-// Kinds 0 and 4 lie in one subdomain, whose first local entry is in pad
-// (the base of its 16-bit columns, DevOp::scol16).
 struct WorkItem {
     int32_t kind, a, b, e0, e1, c0, c1, pad;
 };
@@ -127,13 +125,7 @@ struct DevOp {
     const int32_t *icopy;   // [ncopies] concatenated local index of each copy
     const double *sval;     // sliced-ELL values: slice k-th entries of its 32 rows contiguous
     const float *sval32;    // the same rounded to FP32
-    const int32_t *scol;    // sliced-ELL columns (concatenated local index); null with scol16
-    // sliced-ELL columns as 16-bit offsets from the first local entry of the
-    // row's subdomain (every subdomain then holds <= 65536 local entries):
-    // interior slices add the item's base (WorkItem::pad), interface slices
-    // the base of each copy's subdomain (cbase); null: 32-bit scol
-    const uint16_t *scol16;
-    const int32_t *cbase;   // [ncopies] first local entry of each copy's subdomain (with scol16)
+    const int32_t *scol;    // sliced-ELL columns (concatenated local index)
     const int32_t *sseg;    // interface slices, per copy: (lane of the node's first copy) | (m << 8)
     const int32_t *srow;    // sorted slices: the local row of each slot
     const WorkItem *items;  // SpMV work list
@@ -339,38 +331,18 @@ __device__ __forceinline__ U ldm(const U *p) {
     else return __ldg(p);
 }
 
-// Column readers of a lane's sliced-ELL row: 32-bit concatenated indices,
-// or 16-bit offsets from the row's subdomain base.
-template <bool STREAM>
-struct Col32 {
-    const int32_t *__restrict__ sc;
-    __device__ __forceinline__ int operator()(int i) const { return ldm<STREAM>(sc + i); }
-};
-template <bool STREAM>
-struct Col16 {
-    const uint16_t *__restrict__ sc;
-    int base;
-    __device__ __forceinline__ int operator()(int i) const { return base + static_cast<int>(ldm<STREAM>(sc + i)); }
-};
-
-// The 16-bit column base of lane `lane`'s row in sliced item W.
-__device__ __forceinline__ int slice_col_base(const DevOp &A, const WorkItem &W, int lane) {
-    if (W.kind != kItemIfaceSlice) return W.pad;
-    return W.a + lane < W.b ? __ldg(A.cbase + W.a + lane) : 0;
-}
-
 // N consecutive entries (k0 .. k0+N-1) of a lane's sliced-ELL row: all
 // loads first (the value and column loads of a warp are contiguous and
 // coalesced, streamed with L2 evict-first), then the FMA chain in order.
-template <int N, bool STREAM, typename T, typename CL, typename XL>
-__device__ __forceinline__ T slice_chunk(const T *__restrict__ sv, const CL &C, const XL &X, int base, int k0,
-                                         T acc) {
+template <int N, bool STREAM, typename T, typename XL>
+__device__ __forceinline__ T slice_chunk(const T *__restrict__ sv, const int32_t *__restrict__ sc, const XL &X,
+                                         int base, int k0, T acc) {
     T vv[N], xv[N];
     int cc[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         vv[j] = ldm<STREAM>(sv + base + (k0 + j) * kSliceRows);
-        cc[j] = C(base + (k0 + j) * kSliceRows);
+        cc[j] = ldm<STREAM>(sc + base + (k0 + j) * kSliceRows);
     }
 #pragma unroll
     for (int j = 0; j < N; ++j) xv[j] = X(cc[j]);
@@ -384,9 +356,9 @@ __device__ __forceinline__ T slice_chunk(const T *__restrict__ sv, const CL &C, 
 // zero-valued padding, which leaves the sum unchanged.  Every lane runs
 // exactly w FMAs: on this part a predicated-off FP64 instruction still takes
 // its issue slot, so nothing here is predicated.
-template <bool STREAM, typename T, typename CL, typename XL>
-__device__ __forceinline__ T slice_row(const T *__restrict__ sv, const CL &sc, const XL &X, int off, int w,
-                                       int lane) {
+template <bool STREAM, typename T, typename XL>
+__device__ __forceinline__ T slice_row(const T *__restrict__ sv, const int32_t *__restrict__ sc, const XL &X,
+                                       int off, int w, int lane) {
     const int base = off + lane;
     T acc = T(0);
     int k = 0;
@@ -460,16 +432,11 @@ __device__ __forceinline__ T spmv_items(const DevOp &A, int2 range, const XL &X,
             const WorkItem Wp = A.items[it + AHEAD];
             if (sliced_item(Wp.kind) && lane < Wp.e1) {
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(sv + Wp.e0 + lane * kSliceRows));
-                if (A.scol16)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol16 + Wp.e0 + lane * kSliceRows));
-                else
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
             }
         }
         if (sliced_item(W.kind)) {
-            const T acc = A.scol16 ? slice_row<STREAM, T>(sv, Col16<STREAM>{A.scol16, slice_col_base(A, W, lane)}, X,
-                                                          W.e0, W.e1, lane)
-                                   : slice_row<STREAM, T>(sv, Col32<STREAM>{A.scol}, X, W.e0, W.e1, lane);
+            const T acc = slice_row<STREAM, T>(sv, A.scol, X, W.e0, W.e1, lane);
             finish_slice<T>(A, W, acc, X, y, lane, dot);
         } else if (W.kind == kItemLongRow) {
             // one long row: lane-strided partial sums, fixed warp tree

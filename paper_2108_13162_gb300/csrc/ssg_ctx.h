@@ -21,7 +21,6 @@ struct ssg_ctx {
     int32_t rhs_block = 16;    // right-hand sides solved together (1, 2, 4, 8 or 16)
     int32_t unroll = 4;        // CG iterations per pass of a single-vector loop graph's body (measured: 4 beats 1)
     int32_t slice_sort = 0;    // interior slice sorting window: 0 auto (row lengths), 1 none, > 1 rows, -1 subdomain
-    int32_t col_bits = 0;      // slice columns: 0 16-bit offsets where every subdomain fits, 32 always 32-bit
     // one-cluster solve (cluster.cuh): the most CTAs per cluster this device
     // places (0: none), the count asked for (0: automatic), and the largest
     // system (local entries) solved that way

@@ -72,7 +72,6 @@ EXPORTS = (
     "ssg_set_batch_graph",
     "ssg_measure_fp64_rate",
     "ssg_set_slice_sort",
-    "ssg_set_col_index",
     "ssg_set_cluster_solve",
     "ssg_get_cluster_solve",
     "ssg_get_layout",
@@ -228,7 +227,6 @@ def lib():
         L.ssg_wdot_noalloc.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
         L.ssg_set_batch_graph.argtypes = [vp, C.c_int32]
         L.ssg_set_slice_sort.argtypes = [vp, C.c_int32]
-        L.ssg_set_col_index.argtypes = [vp, C.c_int32]
         L.ssg_set_cluster_solve.argtypes = [vp, C.c_int64, C.c_int32]
         L.ssg_get_cluster_solve.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.ssg_autotune_block.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(ssg_tune_block)]
@@ -605,15 +603,10 @@ def ssg_get_cluster_solve(ctx) -> tuple:
 
 def ssg_get_layout(sys) -> dict:
     """The interior slice layout of a system (see ssg.h)."""
-    out = np.zeros(5, np.int64)
+    out = np.zeros(4, np.int64)
     _check(lib().ssg_get_layout(sys, out), "ssg_get_layout")
     return {"slice_slots": int(out[0]), "slice_entries": int(out[1]), "sorted_subdomains": int(out[2]),
-            "max_window": int(out[3]), "padding_ratio": float(out[0]) / max(int(out[1]), 1),
-            "col_bytes": int(out[4])}
-
-
-def ssg_set_col_index(ctx, bits: int):
-    return _check(lib().ssg_set_col_index(ctx, int(bits)), "ssg_set_col_index")
+            "max_window": int(out[3]), "padding_ratio": float(out[0]) / max(int(out[1]), 1)}
 
 
 def ssg_system_destroy(sys):
@@ -667,11 +660,6 @@ class Context:
         """Interior slice layout: 0 auto, 1 none, > 1 sorting window, -1 whole subdomain
         (systems partitioned afterwards)."""
         ssg_set_slice_sort(self.h, window)
-
-    def set_col_index(self, bits: int = 0):
-        """Slice column indices: 0 16-bit offsets where every subdomain fits, 32
-        always 32-bit (systems partitioned afterwards)."""
-        ssg_set_col_index(self.h, bits)
 
     def set_cluster_solve(self, max_nloc: int = 12288, ctas: int = 0):
         """Single-vector FP64 solves of systems with at most max_nloc local entries

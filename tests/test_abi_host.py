@@ -224,24 +224,6 @@ def test_slice_layout_rule_from_row_lengths():
         S.close()
 
 
-def test_column_index_width_rule():
-    """Slice columns are 16-bit offsets from the subdomain base exactly when
-    every subdomain holds at most 65536 local entries (host only)."""
-    from synth import laplace1d
-
-    for n, P, want in ((65536, 1, 2), (65537, 1, 4), (2 * 65536 + 2, 2, 4), (2 * 65536 - 2, 2, 2)):
-        A = laplace1d(n)
-        part = (np.arange(n) * P // n).astype(np.int32)
-        S = ssg.System(None, A, part, P)
-        nloc_max = max(np.bincount(part, minlength=P)) + (P > 1)  # one interface copy per side
-        assert S.layout()["col_bytes"] == want, (n, P, nloc_max)
-        S.close()
-    p = config_problem(2, scale=24)
-    S = ssg.System(None, p.A, p.part, p.P)
-    assert S.layout()["col_bytes"] == 2
-    S.close()
-
-
 def _interior_nnz(p):
     """Stored entries of the interior (multiplicity 1) rows of the local
     matrices, from the oracle's maps."""

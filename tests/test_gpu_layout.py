@@ -6,8 +6,7 @@ subdomains), a random sparse matrix with irregular rows and a random
 partition, the same with a hub row longer than a slice, and the
 finite-volume grid.
 
-With 16-bit and with 32-bit slice columns: the same bits.  In every
-layout: the FP64 product within 4 (L_i + m_i) u (|A||x|)_i of the
+In every layout: the FP64 product within 4 (L_i + m_i) u (|A||x|)_i of the
 oracle's on every local entry (Section 3.4.1), and the FP64, FP32 and
 4-vector products bit-identical to the unsorted layout's (each row's entries
 keep their order, each interface node's copies their ascending order); a
@@ -134,43 +133,6 @@ def test_layouts_same_products(ctx, name, A, part, P):
                 assert np.array_equal(a, b), (name, w)
     for S in Ss.values():
         S.close()
-
-
-@pytest.mark.parametrize("name,A,part,P", CASES, ids=[c[0] for c in CASES])
-def test_column_index_widths_same_products(ctx, name, A, part, P):
-    """16-bit column offsets from the subdomain base and 32-bit concatenated
-    columns (ssg_set_col_index) gather the same entries: the FP64, FP32 and
-    4-vector products and the solves are bit-identical, in the unsorted and
-    the sorted layouts."""
-    import torch
-
-    from paper_2108_13162_gb300.ssg import System
-
-    ref = oracle.Partition(A, part, P)
-    rng = np.random.default_rng(11)
-    xl = ref.scatter(rng.uniform(-1, 1, A.n))
-    X4 = np.stack([ref.scatter(rng.uniform(-1, 1, A.n)) for _ in range(4)], axis=1)
-    b = rng.uniform(-1, 1, A.n)
-    for window in (1, -1):
-        got = {}
-        for bits in (0, 32):
-            ctx.set_slice_sort(window)
-            ctx.set_col_index(bits)
-            try:
-                S = System(ctx, A, part, P)
-            finally:
-                ctx.set_slice_sort(0)
-                ctx.set_col_index(0)
-            assert S.layout()["col_bytes"] == (2 if bits == 0 else 4)
-            y = S.spmv(_t(xl)).cpu().numpy()
-            y32 = torch.empty(S.sizes.nloc, dtype=torch.float32, device="cuda")
-            S.spmv_prec(_t(xl.astype(np.float32)), y32, "fp32")
-            Y = S.spmm(_t(X4)).cpu().numpy()
-            x, rc, st = S.solve(_t(b), rtol=1e-10, max_iter=100000)
-            got[bits] = (y, y32.cpu().numpy(), Y, x.cpu().numpy())
-            S.close()
-        for a, c in zip(got[0], got[32]):
-            assert np.array_equal(a, c), (name, window)
 
 
 @pytest.mark.parametrize("name,A,part,P", CASES[:2], ids=[c[0] for c in CASES[:2]])
