@@ -77,6 +77,9 @@ def parse_args(argv=None):
     ap.add_argument("--profile-fe", choices=("fp64", "fp32"), default=None,
                     help="only build the 1024^2 finite-element workload (the default slice layout) and launch its "
                          "SpMV --spmv-reps times (for ncu); no JSON line")
+    ap.add_argument("--profile-p2d", choices=("cluster", "loop"), default=None,
+                    help="only build the 64x64 Poisson workload and run --spmv-reps FP64 solves to 1e-10 as the "
+                         "one-cluster kernel or the three-kernel loop (for ncu); no JSON line")
     ap.add_argument("--fe-windows", action="store_true",
                     help="also time the 1024^2 finite-element product under every slice-sorting window "
                          "(1, 128, 256, 512, whole subdomain), each autotuned, and report them in fe2d")
@@ -937,6 +940,24 @@ def run_ours(args, dist):
         S.close()
         ctx.close()
         return 0
+    if args.profile_p2d:
+        from synth import config_problem
+
+        p1 = config_problem(1)
+        if args.profile_p2d == "loop":
+            ctx.set_cluster_solve(0)
+        S = System(ctx, p1.A, p1.part, p1.P)
+        b1 = torch.from_numpy(p1.b[:, 0].copy()).cuda()
+        x1 = torch.zeros_like(b1)
+        for _ in range(args.spmv_reps):
+            x1.zero_()
+            rc, st = ssg.ssg_solve(S.h, 1, b1, x1, False, 1e-10, 0, ssg.SSG_FP64)
+        torch.cuda.synchronize()
+        print("64x64 solve (%s): rc %d, %d iterations, %d launches, %.3f ms" % (
+            args.profile_p2d, rc, st[0]["iters"], st[0]["kernel_launches"], st[0]["solve_ms"]))
+        S.close()
+        ctx.close()
+        return 0 if rc == ssg.SSG_OK else 1
     prob = make_workload()
     if args.profile_band:
         from paper_2108_13162_gb300.ssg import Band
