@@ -333,7 +333,7 @@ typedef struct {
     double fp64_us[SSG_TUNE_CANDIDATES], fp32_us[SSG_TUNE_CANDIDATES];
 } ssg_tune;
 /*
- * Time the single-vector SpMV instances (launch shapes of 4 to 8 blocks per
+ * Time the single-vector SpMV instances (launch shapes of 3 to 6 blocks per
  * SM, L2 prefetch of the next slices on or off; six per precision) on this
  * system as the solver loop launches them (block partials, no last-block
  * sum), reps launches each (reps <= 0: 20), and use the fastest for the

@@ -62,8 +62,8 @@ struct ssg_system {
     int32_t sorted_subdomains = 0, max_window = 1;
     int grid_spmv = 0;
     int grid_spmv32 = 0;
-    int grid_bps[kMaxBps + 1] = {};                 // single-vector grids for 3 to kMaxBps blocks per SM
-    const int2 *range_bps[kMaxBps + 1] = {};
+    int grid_bps[7] = {0, 0, 0, 0, 0, 0, 0};        // single-vector grids for 3 to 6 blocks per SM
+    const int2 *range_bps[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int var64 = 0, var32 = 0;                       // chosen SpMV instances (ssg_autotune)
     int grid_vec = 0;
     // one-cluster solve: warp ranges for cluster_ctas CTAs (warp w of CTA c
@@ -161,16 +161,16 @@ constexpr int kSpmvVariants = SSG_TUNE_CANDIDATES;
 const SpmvVariant<double> kSpmv64Variants[kSpmvVariants] = {
     {4, 0, k_spmv_asm<kEpiPartials, double, 4, 0>, k_spmv_asm<kEpiStore, double, 4, 0>},
     {4, 1, k_spmv_asm<kEpiPartials, double, 4, 1>, k_spmv_asm<kEpiStore, double, 4, 1>},
-    {6, 0, k_spmv_asm<kEpiPartials, double, 6, 0>, k_spmv_asm<kEpiStore, double, 6, 0>},
-    {8, 0, k_spmv_asm<kEpiPartials, double, 8, 0>, k_spmv_asm<kEpiStore, double, 8, 0>},
+    {3, 0, k_spmv_asm<kEpiPartials, double, 3, 0>, k_spmv_asm<kEpiStore, double, 3, 0>},
+    {3, 1, k_spmv_asm<kEpiPartials, double, 3, 1>, k_spmv_asm<kEpiStore, double, 3, 1>},
     {5, 0, k_spmv_asm<kEpiPartials, double, 5, 0>, k_spmv_asm<kEpiStore, double, 5, 0>},
     {5, 1, k_spmv_asm<kEpiPartials, double, 5, 1>, k_spmv_asm<kEpiStore, double, 5, 1>},
 };
 const SpmvVariant<float> kSpmv32Variants[kSpmvVariants] = {
     {5, 1, k_spmv_asm<kEpiPartials, float, 5, 1>, k_spmv_asm<kEpiStore, float, 5, 1>},
     {5, 0, k_spmv_asm<kEpiPartials, float, 5, 0>, k_spmv_asm<kEpiStore, float, 5, 0>},
-    {7, 1, k_spmv_asm<kEpiPartials, float, 7, 1>, k_spmv_asm<kEpiStore, float, 7, 1>},
-    {8, 1, k_spmv_asm<kEpiPartials, float, 8, 1>, k_spmv_asm<kEpiStore, float, 8, 1>},
+    {4, 1, k_spmv_asm<kEpiPartials, float, 4, 1>, k_spmv_asm<kEpiStore, float, 4, 1>},
+    {4, 2, k_spmv_asm<kEpiPartials, float, 4, 2>, k_spmv_asm<kEpiStore, float, 4, 2>},
     {6, 1, k_spmv_asm<kEpiPartials, float, 6, 1>, k_spmv_asm<kEpiStore, float, 6, 1>},
     {6, 2, k_spmv_asm<kEpiPartials, float, 6, 2>, k_spmv_asm<kEpiStore, float, 6, 2>},
 };
@@ -197,14 +197,14 @@ struct WorkPlan {
     int32_t sorted_subdomains = 0;   // subdomains whose interior slices are sorted by row length
     int32_t max_window = 1;          // the largest sorting window used
     std::vector<WorkItem> items;
-    std::vector<int2> range_bps[kMaxBps + 1];  // per warp of a single-vector launch sized for 3 to kMaxBps blocks per SM
+    std::vector<int2> range_bps[7];  // per warp of a single-vector launch sized for 3 to 6 blocks per SM
     std::vector<int2> warp_rangeB;   // per warp of the K-vector product: cut inside each segment
     std::vector<int2> range_cluster;  // per warp of the one-cluster solve (cluster_ctas CTAs)
     int32_t cluster_nranges = 0;      // its non-empty ranges (a prefix)
     std::vector<int32_t> blk_seg, seg_blk;  // segment of each K-vector product block; blocks per segment
     std::vector<int4> chunk;                // vector-kernel chunks (segment, first entry, end entry, 0)
     std::vector<int32_t> seg_chunk;         // chunks per segment
-    int grid_bps[kMaxBps + 1] = {};
+    int grid_bps[7] = {0, 0, 0, 0, 0, 0, 0};
     int gridB = 0;
 };
 
@@ -459,7 +459,7 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
     }
     const int n = static_cast<int>(W.items.size());
     const int per = (n + kSpmvWarps - 1) / kSpmvWarps;
-    for (int bps = 3; bps <= kMaxBps; ++bps) {
+    for (int bps = 3; bps <= 6; ++bps) {
         W.grid_bps[bps] = std::max(1, std::min(per, num_sms * bps));
         W.range_bps[bps] = cut_ranges(W.items, W.grid_bps[bps]);
     }
@@ -751,12 +751,12 @@ int upload(ssg_system *S) {
         wtab32[m] = static_cast<float>(wtab[m]);
     }
 
-    for (int bps = 3; bps <= kMaxBps; ++bps) S->grid_bps[bps] = plan.grid_bps[bps];
+    for (int bps = 3; bps <= 6; ++bps) S->grid_bps[bps] = plan.grid_bps[bps];
     S->grid_spmv = plan.grid_bps[kSpmv64Variants[0].bps];
     S->grid_spmv32 = plan.grid_bps[kSpmv32Variants[0].bps];
     S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N / 2 + kBlock - 1) / kBlock), C->num_sms * kVecBlocksPerSM));
     int max_grid = S->grid_vec;
-    for (int bps = 3; bps <= kMaxBps; ++bps) max_grid = std::max(max_grid, plan.grid_bps[bps]);
+    for (int bps = 3; bps <= 6; ++bps) max_grid = std::max(max_grid, plan.grid_bps[bps]);
     S->n_partials = 3 * max_grid;
 
     struct Piece {
@@ -791,8 +791,8 @@ int upload(ssg_system *S) {
     size_t i_sseg = add(plan.sseg.data(), sizeof(int32_t) * plan.sseg.size());
     size_t i_srow = add(plan.srow.data(), sizeof(int32_t) * plan.srow.size());
     size_t i_items = add(plan.items.data(), sizeof(WorkItem) * plan.items.size());
-    size_t i_range_bps[kMaxBps + 1] = {};
-    for (int bps = 3; bps <= kMaxBps; ++bps)
+    size_t i_range_bps[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int bps = 3; bps <= 6; ++bps)
         i_range_bps[bps] = add(plan.range_bps[bps].data(), sizeof(int2) * plan.range_bps[bps].size());
     size_t i_brangeB = add(plan.warp_rangeB.data(), sizeof(int2) * plan.warp_rangeB.size());
     size_t i_rcluster = add(plan.range_cluster.data(), sizeof(int2) * plan.range_cluster.size());
@@ -910,7 +910,7 @@ int upload(ssg_system *S) {
     S->op.sseg = static_cast<const int32_t *>(at(i_sseg));
     S->op.srow = static_cast<const int32_t *>(at(i_srow));
     S->op.items = static_cast<const WorkItem *>(at(i_items));
-    for (int bps = 3; bps <= kMaxBps; ++bps) S->range_bps[bps] = static_cast<const int2 *>(at(i_range_bps[bps]));
+    for (int bps = 3; bps <= 6; ++bps) S->range_bps[bps] = static_cast<const int2 *>(at(i_range_bps[bps]));
     S->op.warp_range = S->range_bps[kSpmv64Variants[0].bps];
     S->op32 = S->op;  // filled below once the op is complete
     S->op.iptr = static_cast<const int32_t *>(at(i_iptr));

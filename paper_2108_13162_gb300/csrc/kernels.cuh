@@ -43,7 +43,6 @@ struct SpmvTraits<float> {
     static constexpr int kL2Ahead = 1;      // measured on the 128^3 system: 28.9 us (0: 31.8, 2: 29.9, 4: 31.7)
 };
 // [spmv-source-end]
-constexpr int kMaxBps = 8;  // most resident blocks per SM of a single-vector product launch shape
 constexpr int kVecBlocksPerSM = 4;
 constexpr int kHostChunk = 32;    // iterations per host-loop chunk (SSG_DRIVER_HOST)
 
