@@ -33,17 +33,28 @@ struct ClusterScal {
     int status, k, run;
 };
 
+// Sum over the first 16 lanes of a warp (the CTAs of a cluster), by the
+// fixed tree of offsets 8, 4, 2, 1; valid in lane 0.
+__device__ __forceinline__ double warp_sum16(double v) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Cluster-wide sums of NV <= 3 values per thread, in every CTA; thread 0 then
 // runs fin(tot) with the NV totals (red: the CTA's [3][kClusterThreads]
-// staging buffer).  Each CTA adds its warps [0, wact) (the others
-// hold no entry) lane by lane in warp order, then the 32 lanes by the fixed
-// shuffle tree, into slot[phase & 1] of its shared memory.  The cluster
-// barrier (release / acquire at cluster scope: it also publishes the phase's
-// global-memory writes to the other CTAs), then lane r of warp 0 reads CTA
-// r's sums through distributed shared memory and the lanes are added by the
-// same tree.  The slots alternate: a CTA writes a slot again only after the
-// next cluster barrier, which no CTA passes before every CTA has read this
-// phase's sums.  Ends with a block barrier (fin's results visible).
+// staging buffer).  Each CTA adds its warps [0, wact) (the others hold no
+// entry) lane by lane, warp w into chain w mod 4, the four chains then
+// pairwise, then the 32 lanes by the fixed shuffle tree, into slot[phase &
+// 1] of its shared memory.  (On this part a dependent FP64 add costs about
+// 80 cycles: the four chains cut the critical path of 32 warps from 31 adds
+// to 9.)  The cluster barrier (release / acquire at cluster scope: it also
+// publishes the phase's global-memory writes to the other CTAs), then lane r
+// of warp 0 reads CTA r's sums through distributed shared memory and the 16
+// lanes are added by a fixed tree.  The slots alternate: a CTA writes a slot
+// again only after the next cluster barrier, which no CTA passes before every
+// CTA has read this phase's sums.  Ends with a block barrier (fin's results
+// visible).
 template <int NV, typename F>
 __device__ __forceinline__ void cluster_sums(cooperative_groups::cluster_group &cl, double (*red)[kClusterThreads],
                                              double (*slot)[4], int phase, int wact, const double (&v)[NV], F fin) {
@@ -52,12 +63,19 @@ __device__ __forceinline__ void cluster_sums(cooperative_groups::cluster_group &
     for (int j = 0; j < NV; ++j) red[j][threadIdx.x] = v[j];
     __syncthreads();
     if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
-            double t = wact > 0 ? red[j][threadIdx.x] : 0.0;
-            for (int w = 1; w < wact; ++w) t += red[j][threadIdx.x + 32 * w];
-            t = warp_sum(t);
-            if (threadIdx.x == 0) mine[j] = t;
+            double a[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a[c] = c < wact ? red[j][l + 32 * c] : 0.0;
+            for (int w = 4; w < wact; w += 4) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (w + c < wact) a[c] += red[j][l + 32 * (w + c)];
+            }
+            const double t = warp_sum((a[0] + a[1]) + (a[2] + a[3]));
+            if (l == 0) mine[j] = t;
         }
     }
     cl.sync();
@@ -69,12 +87,37 @@ __device__ __forceinline__ void cluster_sums(cooperative_groups::cluster_group &
         for (int j = 0; j < NV; ++j) {
             double t = 0.0;
             if (lane < n) t = cl.map_shared_rank(mine, lane)[j];
-            tot[j] = warp_sum(t);
+            tot[j] = warp_sum16(t);
         }
         if (lane == 0) fin(tot);
     }
     __syncthreads();
 }
+
+// The stopping test of Algorithm 3 as the loop takes it, sqrt(rr) <= t,
+// without the square root (a chain of dependent FP64 operations) when rr is
+// clearly on one side of t^2: lo and hi bracket t^2 by a relative 2^-48,
+// far beyond the rounding of t^2 and of the square root, so outside
+// [lo, hi] the answer is that of the correctly rounded square root; inside,
+// and whenever t^2 is not a normal number, the square root decides.
+struct StopTest {
+    double t, lo, hi;
+    bool bracket;
+    __device__ __forceinline__ void init(double t_) {
+        t = t_;
+        const double T = t_ * t_;
+        bracket = isfinite(T) && T >= 0x1p-1000;
+        lo = T * (1.0 - 0x1p-48);
+        hi = T * (1.0 + 0x1p-48);
+    }
+    __device__ __forceinline__ bool operator()(double rr) const {
+        if (bracket) {
+            if (rr <= lo) return true;
+            if (rr > hi) return false;
+        }
+        return sqrt(rr) <= t;
+    }
+};
 
 // The direction the product gathers in iteration k, formed where it is
 // read: p_k[j] = z_k[j] + beta_{k-1} p_{k-1}[j] (Algorithm 3 line 8, z = r,
@@ -119,6 +162,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     __shared__ double red[3][kClusterThreads];
     __shared__ double slot[2][4];
     __shared__ ClusterScal cs;
+    __shared__ StopTest stop;  // read by thread 0 only
     const int nc = static_cast<int>(cl.num_blocks());
     const int rank = static_cast<int>(cl.block_rank());
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -154,12 +198,13 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         cs.rr = t[0];
         cs.rho = PC ? t[2] : t[0];
         cs.bnorm = sqrt(t[1]);
+        stop.init(rtol * cs.bnorm);
         // p_0 = z_0 = fma(0, p, z_0): the gather's form with beta = 0
         cs.pq = cs.alpha = cs.beta = 0.0;
         cs.k = 0;
         cs.status = SSG_E_NOT_CONVERGED;
         cs.run = 1;
-        if (sqrt(cs.rr) <= rtol * cs.bnorm) {
+        if (stop(cs.rr)) {
             cs.status = SSG_OK;
             cs.run = 0;
         } else if (max_iter <= 0) {
@@ -209,7 +254,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
             cs.beta = rz / cs.rho;
             cs.rho = rz;
             cs.k += 1;
-            if (sqrt(cs.rr) <= rtol * cs.bnorm) {
+            if (stop(cs.rr)) {
                 cs.status = SSG_OK;
                 cs.run = 0;
             } else if (cs.k >= max_iter) {
