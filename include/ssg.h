@@ -131,7 +131,7 @@ int ssg_set_slice_sort(ssg_ctx *ctx, int32_t window);
  * interface sums are the same bits as the multi-kernel loop's.  The dots'
  * partial sums are grouped differently, so iterates agree to rounding and the
  * iteration count may differ by a few.  max_nloc = 0 turns it off; default
- * 12288 (on GB300 the one-cluster solve takes 7.4 us per FP64 iteration on
+ * 12288 (on GB300 the one-cluster solve takes 7.1 us per FP64 iteration on
  * the 64 x 64 Poisson system against 13.3 for the loop; its 16 SMs' FP64
  * rate makes it the slower one beyond about 12-16 thousand entries).  ctas: CTAs per cluster (2, 4, 8 or 16, capped at what the device
  * places), or 0 for the device's largest.  max_nloc applies to solves issued
