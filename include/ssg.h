@@ -385,11 +385,32 @@ int ssg_spmm_assembled_f32(ssg_system *sys, int32_t k, const float *x_loc, float
 
 /*
  * Interface-weighted dot of Section 3.4.2: result = sum_k w_k u_k v_k over the
- * nloc local entries with w_k = 1/m of the entry's node (equals the global dot
+ * nloc local entries with w_k the system's weight of entry k (ssg_set_weights:
+ * 1/m of the entry's node by default; either weighting equals the global dot
  * for consistent vectors).  Device pointers; *result_dev is written on the
  * device.  Deterministic for a given system.
  */
 int ssg_wdot(ssg_system *sys, const double *u_loc, const double *v_loc, double *result_dev);
+
+/* weightings of the weighted dots (ssg_set_weights) */
+#define SSG_WEIGHT_INV_MULT 0 /* w = 1/m on each of a node's m copies (the default) */
+#define SSG_WEIGHT_OWNER 1    /* w = 1 on the node's owner copy, 0 on its other copies */
+/*
+ * The weights of every weighted dot the system forms (Section 3.4.2 combines
+ * the subdomains' sums with weights it does not give): the solves' (r, r)_w,
+ * (r, z)_w, (p, S p)_w and ||b||_w, the true residual and ssg_wdot.
+ * SSG_WEIGHT_INV_MULT: w = 1/m on each copy of a node of multiplicity m.
+ * SSG_WEIGHT_OWNER: the owner mask, w = 1 on the node's owner copy (the copy
+ * ssg_copy_maps reports in own: in subdomain part(i) for ssg_partition, in the
+ * lowest subdomain for ssg_partition_fe) and 0 on its other copies, so that
+ * each node is counted once with no division.  Both sum to 1 over a node's
+ * copies: for consistent vectors both dots are the global dot in exact
+ * arithmetic, and the solves' iterates agree to rounding.  Applies to later
+ * calls (loop graphs built before are rebuilt; for a batch, every column
+ * group); blocks until the context's stream is idle.  SSG_E_INVALID for
+ * another mode or a system without device data.
+ */
+int ssg_set_weights(ssg_system *sys, int32_t mode);
 
 /*
  * Solve S x = b for k right-hand sides with Algorithm 3 (M = I) on the

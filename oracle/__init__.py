@@ -24,6 +24,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
 OK, INVALID, OOM, BREAKDOWN, NOT_CONVERGED = 0, 1, 2, 4, 5
+WEIGHT_INV_MULT, WEIGHT_OWNER = 0, 1  # weights of the weighted dots (Partition.set_weights)
 
 _lib = None
 
@@ -115,6 +116,8 @@ def _bind(L):
         L.or_sub_spmv.argtypes = [C.c_void_p, _f64p, _f64p]
         L.or_wdot.argtypes = [C.c_void_p, _f64p, _f64p]
         L.or_wdot.restype = C.c_double
+        L.or_set_weights.argtypes = [C.c_void_p, C.c_int]
+        L.or_set_weights.restype = C.c_int
         L.or_sub_cg.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int32, C.POINTER(C.c_int32),
                                 C.POINTER(C.c_double), dp, dp, dp]
         L.or_sub_cg.restype = C.c_int
@@ -289,6 +292,13 @@ class Partition:
 
     def wdot(self, u, v) -> float:
         return float(self._L.or_wdot(self.h, _c(u, np.float64), _c(v, np.float64)))
+
+    def set_weights(self, mode: int):
+        """Weights of every weighted dot of this partition (or_set_weights):
+        WEIGHT_INV_MULT (1/m, the default) or WEIGHT_OWNER (1 on the owner copy,
+        0 on the others)."""
+        if self._L.or_set_weights(self.h, int(mode)) != 0:
+            raise ValueError("weight mode must be WEIGHT_INV_MULT or WEIGHT_OWNER")
 
     def cg(self, b, rtol, max_iter, x0=None) -> CGResult:
         """Sub-structured CG (Algorithm 3, M = I) on global b / x."""

@@ -21,7 +21,8 @@
  *   or_sub_spmv      the two-step sub-structured SpMV of Section 3.4.1: local
  *                    products, then assembly of interface contributions
  *                    (Algorithms 4 and 5, every copy receives the same sum).
- *   or_wdot          the interface-weighted dot of Section 3.4.2, w = 1/m.
+ *   or_wdot          the interface-weighted dot of Section 3.4.2, w = 1/m
+ *                    (or the owner mask, or_set_weights).
  *   or_sub_cg        Algorithm 3 with the sub-structured SpMV and weighted dots.
  *   or_cholesky_solve  textbook dense Cholesky (second opinion on tiny systems).
  *   or_band_row, or_band_col  the band-row and band-column splittings of
@@ -416,6 +417,29 @@ double or_wdot(const or_part *h, const double *u, const double *v) {
     double s = 0.0;
     for (int64_t k = 0; k < h->nloc; ++k) s += h->w[k] * u[k] * v[k];
     return s;
+}
+
+/*
+ * The weights of every weighted dot (Section 3.4.2 asks for a weighted
+ * combination of the subdomains' sums without giving the weights).  mode 0:
+ * w = 1/m on every copy of a node (the default set by or_partition); mode 1,
+ * the owner mask: w = 1 on the node's owner copy own[i] (its copy in
+ * subdomain part(i); for element sub-structures, in the lowest subdomain) and
+ * w = 0 on its other copies.  Either set sums to 1 over the copies of each
+ * node, so for a consistent vector both dots are the global dot in exact
+ * arithmetic.  Returns OR_OK, or OR_INVALID for another mode.
+ */
+int or_set_weights(or_part *h, int mode) {
+    if (mode == 0) {
+        for (int64_t k = 0; k < h->nloc; ++k) h->w[k] = 1.0 / (double)h->mult[h->l2g[k]];
+        return OR_OK;
+    }
+    if (mode == 1) {
+        for (int64_t k = 0; k < h->nloc; ++k) h->w[k] = 0.0;
+        for (int32_t i = 0; i < h->n; ++i) h->w[h->own[i]] = 1.0;
+        return OR_OK;
+    }
+    return OR_INVALID;
 }
 
 /*

@@ -65,6 +65,10 @@ struct ssg_system {
     int grid_bps[7] = {0, 0, 0, 0, 0, 0, 0};        // single-vector grids for 3 to 6 blocks per SM
     const int2 *range_bps[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int var64 = 0, var32 = 0;                       // chosen SpMV instances (ssg_autotune)
+    // weights of the weighted dots (ssg_set_weights): the multiplicity codes
+    // (w = 1/m) and the owner-mask codes; the operators read one of them
+    const uint8_t *d_mult = nullptr, *d_wown = nullptr;
+    int32_t weight_mode = SSG_WEIGHT_INV_MULT;
     int grid_vec = 0;
     // one-cluster solve: warp ranges for cluster_ctas CTAs (warp w of CTA c
     // takes range w * cluster_ctas + c), the first cluster_nranges non-empty
@@ -737,6 +741,10 @@ int upload(ssg_system *S) {
             for (int32_t k = M.lrowptr[r]; k < M.lrowptr[r + 1]; ++k) gcol[k] = M.off[s] + M.lcol[k];
     std::vector<uint8_t> mloc(static_cast<size_t>(N));
     for (int64_t k = 0; k < N; ++k) mloc[k] = static_cast<uint8_t>(M.mult[M.l2g[k]]);
+    // owner-mask weight codes (ssg_set_weights): 1 on a node's owner copy
+    // (every interior entry is one), 0 on its other copies
+    std::vector<uint8_t> wown(static_cast<size_t>(N), 0);
+    for (int32_t i = 0; i < M.n; ++i) wown[M.own[i]] = 1;
     // group flags: 1 when any of the 64 entries of a group is an interface copy
     std::vector<uint8_t> gflag(static_cast<size_t>((N + 63) / 64), 0);
     for (int64_t k = 0; k < N; ++k)
@@ -806,6 +814,7 @@ int upload(ssg_system *S) {
     size_t i_iptr = add(M.iptr.data(), sizeof(int32_t) * (M.ngamma + 1));
     size_t i_icopy = add(M.icopy.data(), sizeof(int32_t) * M.ncopies);
     size_t i_mult = add(mloc.data(), N);
+    size_t i_wown = add(wown.data(), N);
     size_t i_wtab = add(wtab.data(), sizeof(double) * 256);
     size_t i_gflag = add(gflag.data(), gflag.size());
     size_t i_gflag128 = add(gflag128.data(), gflag128.size());
@@ -916,6 +925,8 @@ int upload(ssg_system *S) {
     S->op.iptr = static_cast<const int32_t *>(at(i_iptr));
     S->op.icopy = static_cast<const int32_t *>(at(i_icopy));
     S->op.mult = static_cast<const uint8_t *>(at(i_mult));
+    S->d_mult = S->op.mult;
+    S->d_wown = static_cast<const uint8_t *>(at(i_wown));
     S->op.wtab = static_cast<const double *>(at(i_wtab));
     S->op.gflag = static_cast<const uint8_t *>(at(i_gflag));
     S->op.gflag128 = static_cast<const uint8_t *>(at(i_gflag128));
@@ -2306,6 +2317,50 @@ int tune_block_system(ssg_system *S, int K, int reps, ssg_tune_block *t) {
     return SSG_OK;
 }
 
+// Single-vector loop graphs hold the operators by value: dropped here, built
+// again by the next solve.
+void destroy_single_graphs(ssg_system *S) {
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    if (S->exec_pc) cudaGraphExecDestroy(S->exec_pc);
+    if (S->graph_pc) cudaGraphDestroy(S->graph_pc);
+    S->exec = nullptr;
+    S->graph = nullptr;
+    S->exec_pc = nullptr;
+    S->graph_pc = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        if (S->exec_m[i]) cudaGraphExecDestroy(S->exec_m[i]);
+        if (S->graph_m[i]) cudaGraphDestroy(S->graph_m[i]);
+        S->exec_m[i] = nullptr;
+        S->graph_m[i] = nullptr;
+    }
+}
+
+// Point every operator of S (and of its column classes) at the weight codes
+// of `mode`; every graph holding the previous operators is dropped.
+int apply_weights(ssg_system *S, int mode) {
+    SSG_CUDA_TRY(cudaStreamSynchronize(S->ctx->stream));
+    const uint8_t *codes = mode == SSG_WEIGHT_OWNER ? S->d_wown : S->d_mult;
+    const uint8_t *wsel = mode == SSG_WEIGHT_OWNER ? S->d_wown : nullptr;
+    for (DevOp *A : {&S->op, &S->op32, &S->opB64, &S->opB32}) {
+        A->mult = codes;
+        A->wsel = wsel;
+    }
+    S->weight_mode = mode;
+    destroy_single_graphs(S);
+    destroy_block_graphs(S);
+    for (ssg_system *C : S->kclass) {
+        const int rc = apply_weights(C, mode);
+        if (rc != SSG_OK) return rc;
+    }
+    for (ssg_system::BlockGraph &G : S->classes_graph) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        if (G.g) cudaGraphDestroy(G.g);
+        G = ssg_system::BlockGraph{};
+    }
+    return SSG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2670,22 +2725,19 @@ int ssg_autotune(ssg_system *S, int32_t reps, ssg_tune *out) {
     S->grid_spmv = S->grid_bps[kSpmv64Variants[S->var64].bps];
     S->op32.warp_range = S->range_bps[kSpmv32Variants[S->var32].bps];
     S->grid_spmv32 = S->grid_bps[kSpmv32Variants[S->var32].bps];
-    if (S->exec) cudaGraphExecDestroy(S->exec);
-    if (S->graph) cudaGraphDestroy(S->graph);
-    if (S->exec_pc) cudaGraphExecDestroy(S->exec_pc);
-    if (S->graph_pc) cudaGraphDestroy(S->graph_pc);
-    S->exec = nullptr;
-    S->graph = nullptr;
-    S->exec_pc = nullptr;
-    S->graph_pc = nullptr;
-    for (int i = 0; i < 2; ++i) {
-        if (S->exec_m[i]) cudaGraphExecDestroy(S->exec_m[i]);
-        if (S->graph_m[i]) cudaGraphDestroy(S->graph_m[i]);
-        S->exec_m[i] = nullptr;
-        S->graph_m[i] = nullptr;
-    }
+    destroy_single_graphs(S);
     if (out) *out = t;
     return SSG_OK;
+}
+
+int ssg_set_weights(ssg_system *S, int32_t mode) {
+    int rc = check_dev(S);
+    if (rc != SSG_OK) return rc;
+    if (mode != SSG_WEIGHT_INV_MULT && mode != SSG_WEIGHT_OWNER) {
+        set_error("ssg_set_weights: mode must be SSG_WEIGHT_INV_MULT or SSG_WEIGHT_OWNER");
+        return SSG_E_INVALID;
+    }
+    return apply_weights(S, mode);
 }
 
 int ssg_spmm_assembled(ssg_system *S, int32_t k, const double *x_loc, double *y_loc) {

@@ -296,7 +296,7 @@ __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ 
                         const int row = __ldg(A.icopy + c);
                         store_vec<VW>(Y + (size_t)row * K + col0, S);
                         if (DOTS) {
-                            const T w = wtab_of<T>(A, m);
+                            const T w = copy_weight<T>(A, m, row);
                             T xr[VW];
                             load_vec<VW>(X + (size_t)row * K + col0, xr);
 #pragma unroll
@@ -364,7 +364,6 @@ __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ 
                 }
             }
             __syncwarp();
-            const T w = wtab_of<T>(A, W.c1 - W.c0);
             if (rl == 0) {
                 T Sv[VW];
 #pragma unroll
@@ -373,6 +372,7 @@ __device__ __forceinline__ void spmm_body(const DevOp &A, const T *__restrict__ 
                     const int row = A.icopy[c];
                     store_vec<VW>(Y + (size_t)row * K + col0, Sv);
                     if (DOTS) {
+                        const T w = copy_weight<T>(A, W.c1 - W.c0, row);
                         T xr[VW];
                         load_vec<VW>(X + (size_t)row * K + col0, xr);
 #pragma unroll

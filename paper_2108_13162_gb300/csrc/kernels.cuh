@@ -130,7 +130,10 @@ struct DevOp {
     const int32_t *srow;    // sorted slices: the local row of each slot
     const WorkItem *items;  // SpMV work list
     const int2 *warp_range;  // [grid * kSpmvWarps] contiguous item range of each warp
-    const uint8_t *mult;    // [nloc] multiplicity of each local entry's node
+    const uint8_t *mult;    // [nloc] weight code of each local entry: its node's multiplicity m (w = wtab[m] = 1/m),
+                            // or with the owner mask 1 on owner copies and interior entries, 0 on other copies
+    const uint8_t *wsel;    // owner mask: the same codes, read by the product's interface dot; null: w = 1/m of the
+                            // node's copy count
     const double *wtab;     // [256] wtab[m] = 1/m
     const float *wtab32;    // [256] 1/m rounded to FP32
     const uint8_t *gflag;   // [ceil(nloc / 64)] 1 if entries [64 g, 64 g + 64) hold an interface copy
@@ -313,6 +316,13 @@ template <>
 __device__ __forceinline__ float wtab_of<float>(const DevOp &A, int m) { return __ldg(A.wtab32 + m); }
 
 // [spmv-source-begin] the single-vector SpMV kernel and its helpers
+// Weight of interface copy `row` (of a node with m copies) in the product's
+// weighted dot: 1/m, or the owner mask's 1 / 0 when the system uses it.
+template <typename T>
+__device__ __forceinline__ T copy_weight(const DevOp &A, int m, int row) {
+    return wtab_of<T>(A, A.wsel ? __ldg(A.wsel + row) : m);
+}
+
 // The product's input x_j, gathered by column: through the read-only path,
 // x being constant for the whole kernel (every product launch).  The
 // one-cluster solve passes its own gather instead (cluster.cuh).
@@ -409,7 +419,7 @@ __device__ __forceinline__ void finish_slice(const DevOp &A, const WorkItem &W, 
         if (valid) {
             const int row = __ldg(A.icopy + c);
             y[row] = S;
-            dot = fma(wtab_of<T>(A, m) * X(row), S, dot);
+            dot = fma(copy_weight<T>(A, m, row) * X(row), S, dot);
         }
     }
 }
@@ -458,11 +468,10 @@ __device__ __forceinline__ T spmv_items(const DevOp &A, int2 range, const XL &X,
                 S += T(warp_sum(double(acc)));  // valid in lane 0
             }
             if (lane == 0) {
-                const T w = wtab_of<T>(A, W.c1 - W.c0);
                 for (int c = W.c0; c < W.c1; ++c) {
                     const int row = A.icopy[c];
                     y[row] = S;
-                    dot = fma(w * X(row), S, dot);
+                    dot = fma(copy_weight<T>(A, W.c1 - W.c0, row) * X(row), S, dot);
                 }
             }
         }

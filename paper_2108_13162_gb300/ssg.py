@@ -29,6 +29,8 @@ SSG_FP64 = 0
 SSG_MIXED = 1
 SSG_FP64_JACOBI = 2
 SSG_MIXED_JACOBI = 3
+SSG_WEIGHT_INV_MULT = 0
+SSG_WEIGHT_OWNER = 1
 SSG_DRIVER_GRAPH = 0
 SSG_DRIVER_HOST = 1
 SSG_BAND_ROW = 0
@@ -72,6 +74,7 @@ EXPORTS = (
     "ssg_set_batch_graph",
     "ssg_measure_fp64_rate",
     "ssg_set_slice_sort",
+    "ssg_set_weights",
     "ssg_set_cluster_solve",
     "ssg_get_cluster_solve",
     "ssg_get_layout",
@@ -227,6 +230,7 @@ def lib():
         L.ssg_wdot_noalloc.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
         L.ssg_set_batch_graph.argtypes = [vp, C.c_int32]
         L.ssg_set_slice_sort.argtypes = [vp, C.c_int32]
+        L.ssg_set_weights.argtypes = [vp, C.c_int32]
         L.ssg_set_cluster_solve.argtypes = [vp, C.c_int64, C.c_int32]
         L.ssg_get_cluster_solve.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.ssg_autotune_block.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(ssg_tune_block)]
@@ -601,6 +605,10 @@ def ssg_get_cluster_solve(ctx) -> tuple:
     return int(n.value), int(c.value)
 
 
+def ssg_set_weights(sys, mode: int):
+    return _check(lib().ssg_set_weights(sys, int(mode)), "ssg_set_weights")
+
+
 def ssg_get_layout(sys) -> dict:
     """The interior slice layout of a system (see ssg.h)."""
     out = np.zeros(4, np.int64)
@@ -712,6 +720,10 @@ class Batch:
         s = ssg_get_sizes(self.h)
         self.sizes = Sizes(s.n, s.P, s.nnz, s.nloc, s.ngamma, s.max_mult, s.ncopies)
 
+    def set_weights(self, mode: int = SSG_WEIGHT_INV_MULT):
+        """Weights of the weighted dots of every system of the batch."""
+        ssg_set_weights(self.h, mode)
+
     def autotune_block(self, reps=20):
         """Tune every column group's K-vector product."""
         return ssg_autotune_block(self.h, 16, reps)
@@ -818,6 +830,10 @@ class System:
 
     def layout(self):
         return ssg_get_layout(self.h)
+
+    def set_weights(self, mode: int = SSG_WEIGHT_INV_MULT):
+        """Weights of the weighted dots: SSG_WEIGHT_INV_MULT (1/m) or SSG_WEIGHT_OWNER."""
+        ssg_set_weights(self.h, mode)
 
     def autotune_block(self, k=16, reps=20):
         """Tune the k-vector product of the several-right-hand-side solves."""
