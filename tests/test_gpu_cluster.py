@@ -284,3 +284,23 @@ def test_cluster_setting_checked(ctx):
     c = Context(0)
     assert c.cluster_solve()[0] == DEFAULT_LIMIT
     c.close()
+
+
+def test_cluster_not_under_host_driver(ctx):
+    """The host-loop driver always runs the three-kernel loop, whatever the
+    system's size; mixed precision too."""
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    p = config_problem(1)
+    S = System(ctx, p.A, p.part, p.P)
+    b = _t(p.b[:, 0])
+    ctx.set_driver(ssg.SSG_DRIVER_HOST)
+    try:
+        x, rc, st = S.solve(b, rtol=1e-10)
+    finally:
+        ctx.set_driver(ssg.SSG_DRIVER_GRAPH)
+    assert rc == ssg.SSG_OK and st[0]["kernel_launches"] >= 3 * st[0]["iters"]
+    x, rc, st = S.solve(b, rtol=1e-10, mode=ssg.SSG_MIXED)
+    assert rc == ssg.SSG_OK and st[0]["kernel_launches"] > CLUSTER_LAUNCHES
+    S.close()
