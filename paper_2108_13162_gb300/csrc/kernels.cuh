@@ -385,33 +385,27 @@ __device__ __forceinline__ T slice_row(const T *__restrict__ sv, const int32_t *
     }
 }
 
-// The output row of lane `lane` of sliced item W and, for an interface
-// slice, its copy's segment word (lane of the node's first copy | m << 8):
-// loaded when the item is read, so that these loads overlap the slice's
-// value, column and x loads instead of following its FMA chain.
-__device__ __forceinline__ int slice_out_row(const DevOp &A, const WorkItem &W, int lane, int &seg) {
-    const int i = W.a + lane;
-    seg = 0;
-    if (W.kind == kItemSlice) return i;
-    if (i >= W.b) return 0;
-    if (W.kind == kItemSortedSlice) return __ldg(A.srow + i);
-    seg = __ldg(A.sseg + i);
-    return __ldg(A.icopy + i);
-}
-
-// Writes of one slice's results (row, seg: slice_out_row): interior rows, or
-// interface copy rows whose node sums are formed by shuffles in ascending
-// subdomain order.
+// Writes of one slice's results: interior rows, or interface copy rows whose
+// node sums are formed by shuffles in ascending subdomain order.
 template <typename T, typename XL>
 __device__ __forceinline__ void finish_slice(const DevOp &A, const WorkItem &W, T acc, const XL &X,
-                                             T *__restrict__ y, int lane, int row, int seg, T &dot) {
-    const bool valid = W.a + lane < W.b;
-    if (W.kind != kItemIfaceSlice) {
-        if (valid) {
-            y[row] = acc;
-            dot = fma(X(row), acc, dot);
+                                             T *__restrict__ y, int lane, T &dot) {
+    if (W.kind == kItemSlice) {
+        const int r = W.a + lane;
+        if (r < W.b) {
+            y[r] = acc;
+            dot = fma(X(r), acc, dot);
+        }
+    } else if (W.kind == kItemSortedSlice) {
+        if (W.a + lane < W.b) {
+            const int r = __ldg(A.srow + W.a + lane);
+            y[r] = acc;
+            dot = fma(X(r), acc, dot);
         }
     } else {
+        const int c = W.a + lane;
+        const bool valid = c < W.b;
+        const int seg = valid ? __ldg(A.sseg + c) : 0;
         const int l0 = seg & 0xff, m = seg >> 8;
         const int mmax = __reduce_max_sync(0xffffffffu, m);
         // the sum starts from the first copy, not from 0 (one FP64 add less
@@ -423,6 +417,7 @@ __device__ __forceinline__ void finish_slice(const DevOp &A, const WorkItem &W, 
             if (t < m) S += v;
         }
         if (valid) {
+            const int row = __ldg(A.icopy + c);
             y[row] = S;
             dot = fma(copy_weight<T>(A, m, row) * X(row), S, dot);
         }
@@ -451,10 +446,8 @@ __device__ __forceinline__ T spmv_items(const DevOp &A, int2 range, const XL &X,
             }
         }
         if (sliced_item(W.kind)) {
-            int seg;
-            const int row = slice_out_row(A, W, lane, seg);
             const T acc = slice_row<STREAM, T>(sv, A.scol, X, W.e0, W.e1, lane);
-            finish_slice<T>(A, W, acc, X, y, lane, row, seg, dot);
+            finish_slice<T>(A, W, acc, X, y, lane, dot);
         } else if (W.kind == kItemLongRow) {
             // one long row: lane-strided partial sums, fixed warp tree
             T acc = T(0);
