@@ -498,7 +498,7 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
     W.gridB = W.seg_blk[nseg];
     // vector-kernel chunks: about one per SM in all, a multiple of 64
     // entries, at least one per segment
-    const int64_t ch = std::max<int64_t>(64, (M.nloc / (num_sms * kChunksPerSM) + 63) / 64 * 64);
+    const int64_t ch = std::max<int64_t>(64, (M.nloc / num_sms + 63) / 64 * 64);
     W.seg_chunk.assign(static_cast<size_t>(nseg) + 1, 0);
     for (int sg = 0; sg < nseg; ++sg) {
         const int64_t e0 = M.off[seg_sub[sg]], e1 = M.off[seg_sub[sg + 1]];

@@ -34,8 +34,7 @@ constexpr int kMaxRhs = 16;
 // block, about one block per SM): every block sums its segment's partials of
 // the previous kernel in FP64 (2 DFMA/clk/SM on this part), so fewer, larger
 // chunks keep that sum small next to the chunk's own streaming.
-constexpr int kBlockV = 512;
-constexpr int kChunksPerSM = 2;  // chunk-kernel blocks resident per SM (kBlockV threads each)
+constexpr int kBlockV = 1024;
 
 // State of K solves, resident on the device.  Bit j of `act` is set while
 // column j still iterates.
@@ -502,7 +501,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_cond(const ScalB *segs, int nseg
 // 1 / diag(S) per local entry, shared by the K columns) also the partials of
 // (r_j, z_j)_w, z = dinv r, at part_rr[(nchunks + chunk)*K + j].
 template <int K, bool PC = false>
-__global__ void __launch_bounds__(kBlockV, kChunksPerSM) k_update_rB(const double *__restrict__ q, double *__restrict__ r,
+__global__ void __launch_bounds__(kBlockV, 1) k_update_rB(const double *__restrict__ q, double *__restrict__ r,
                                                       const uint8_t *__restrict__ mult,
                                                       const double *__restrict__ wtab,
                                                       const uint8_t *__restrict__ gflag, const double *part_pq,
@@ -598,7 +597,7 @@ __global__ void __launch_bounds__(kBlockV, kChunksPerSM) k_update_rB(const doubl
 // beta_j p_j (alpha = beta = 0 for frozen columns); the segment's first chunk
 // records each column's iteration and stopping decision.
 template <int K, bool PC = false>
-__global__ void __launch_bounds__(kBlockV, kChunksPerSM) k_update_xpB(double *__restrict__ x, double *__restrict__ p,
+__global__ void __launch_bounds__(kBlockV, 1) k_update_xpB(double *__restrict__ x, double *__restrict__ p,
                                                        const double *__restrict__ r, const double *part_rr,
                                                        SegTab tab, ScalB *segs,
                                                        const double *__restrict__ dinv = nullptr) {
@@ -691,7 +690,7 @@ __global__ void __launch_bounds__(kBlockV, kChunksPerSM) k_update_xpB(double *__
 // residual of the refinement; with r == nullptr only the norms are formed
 // (the true residual at the end of a solve).
 template <int K, bool PC = false>
-__global__ void __launch_bounds__(kBlockV, kChunksPerSM) k_residualB(const double *__restrict__ b, const double *__restrict__ q,
+__global__ void __launch_bounds__(kBlockV, 1) k_residualB(const double *__restrict__ b, const double *__restrict__ q,
                                                       double *__restrict__ r, double *__restrict__ p,
                                                       const uint8_t *__restrict__ mult,
                                                       const double *__restrict__ wtab, double *part, SegTab tab,
@@ -806,7 +805,7 @@ __global__ void __launch_bounds__(kBlock) k_init_finB(const double *part, int nc
 // with PC of (r32, z32)_w at part[(nchunks + chunk)*K + j] (FP32 products and
 // block sums).
 template <int K, bool PC = false>
-__global__ void __launch_bounds__(kBlockV, kChunksPerSM) k_inner_initB(const double *__restrict__ r64, float *__restrict__ r32,
+__global__ void __launch_bounds__(kBlockV, 1) k_inner_initB(const double *__restrict__ r64, float *__restrict__ r32,
                                                         float *__restrict__ p32, float *__restrict__ d32,
                                                         const uint8_t *__restrict__ mult,
                                                         const float *__restrict__ wtab, double *part, SegTab tab,
@@ -879,7 +878,7 @@ __global__ void __launch_bounds__(kBlock) k_inner_finB(const double *part, int n
 // (alpha formed in FP64 from the FP64 sums of the partials, then rounded to
 // FP32 once).
 template <int K, bool PC = false>
-__global__ void __launch_bounds__(kBlockV, kChunksPerSM) k_update_r32B(const float *__restrict__ q, float *__restrict__ r,
+__global__ void __launch_bounds__(kBlockV, 1) k_update_r32B(const float *__restrict__ q, float *__restrict__ r,
                                                         const uint8_t *__restrict__ mult,
                                                         const float *__restrict__ wtab,
                                                         const uint8_t *__restrict__ gflag128, const double *part_pq,
@@ -990,7 +989,7 @@ __global__ void __launch_bounds__(kBlockV, kChunksPerSM) k_update_r32B(const flo
 // (sqrt(rho_j) <= tau_j sqrt(rho0_j), or its inner iterations summed reach
 // max_iter).
 template <int K, bool PC = false>
-__global__ void __launch_bounds__(kBlockV, kChunksPerSM) k_update_dp32B(float *__restrict__ d, float *__restrict__ p,
+__global__ void __launch_bounds__(kBlockV, 1) k_update_dp32B(float *__restrict__ d, float *__restrict__ p,
                                                          const float *__restrict__ r, const double *part_rr,
                                                          SegTab tab, ScalB *si, ScalB *so,
                                                          const float *__restrict__ dinv32 = nullptr) {
@@ -1131,7 +1130,7 @@ __global__ void __launch_bounds__(kBlock) k_outer_finB(const double *part, SegTa
 // rhs_off[sg] + j * n_sg, node g of the segment at offset g - node_off[sg];
 // columns nrhs..K-1 of the block are zero.
 template <int K>
-__global__ void __launch_bounds__(kBlockV, kChunksPerSM) k_scatterB(const int32_t *__restrict__ l2g, const double *__restrict__ xg,
+__global__ void __launch_bounds__(kBlockV, 1) k_scatterB(const int32_t *__restrict__ l2g, const double *__restrict__ xg,
                                                      double *__restrict__ xl, SegTab tab) {
     const int4 ch = tab.chunk[blockIdx.x];
     const int sg = ch.x;
@@ -1146,7 +1145,7 @@ __global__ void __launch_bounds__(kBlockV, kChunksPerSM) k_scatterB(const int32_
 
 // Owner copies of the local blocks -> global right-hand-side layout.
 template <int K>
-__global__ void __launch_bounds__(kBlockV, kChunksPerSM) k_gatherB(const int32_t *__restrict__ l2g, const int32_t *__restrict__ own,
+__global__ void __launch_bounds__(kBlockV, 1) k_gatherB(const int32_t *__restrict__ l2g, const int32_t *__restrict__ own,
                                                     const double *__restrict__ xl, double *__restrict__ xg,
                                                     SegTab tab) {
     const int4 ch = tab.chunk[blockIdx.x];
