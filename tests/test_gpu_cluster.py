@@ -304,3 +304,30 @@ def test_cluster_not_under_host_driver(ctx):
     x, rc, st = S.solve(b, rtol=1e-10, mode=ssg.SSG_MIXED)
     assert rc == ssg.SSG_OK and st[0]["kernel_launches"] > CLUSTER_LAUNCHES
     S.close()
+
+
+@pytest.mark.parametrize("ctas", [2, 4, 8, 16])
+def test_cluster_sizes(ctx, ctas):
+    """Clusters of 2, 4, 8 and 16 CTAs (work items dealt to the CTAs in turn,
+    vector entries in runs per CTA): the same parity with the oracle, the
+    plain and the preconditioned solve."""
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+
+    if ctas > ctx.cluster_solve()[1]:
+        pytest.skip("the device places no cluster of %d CTAs" % ctas)
+    p = config_problem(2, scale=16)
+    ctx.set_cluster_solve(FORCE, ctas)
+    try:
+        S = System(ctx, p.A, p.part, p.P)
+    finally:
+        ctx.set_cluster_solve(FORCE, 0)
+    ref = oracle.Partition(p.A, p.part, p.P)
+    b = p.b[:, 0]
+    for mode, run in ((ssg.SSG_FP64, ref.cg), (ssg.SSG_FP64_JACOBI, ref.pcg)):
+        x, rc, st = S.solve(_t(b), rtol=0.0, max_iter=6, mode=mode)
+        assert _launches_say_cluster(st[0])
+        assert _rel(x.cpu().numpy(), run(b, 0.0, 6).x) <= 1e-10
+        x, rc, st = S.solve(_t(b), rtol=1e-12, max_iter=100000, mode=mode)
+        assert rc == ssg.SSG_OK and _rel(x.cpu().numpy(), run(b, 1e-12, 100000).x) <= 1e-10
+    S.close()
