@@ -65,3 +65,31 @@ def test_algorithmic_bytes_formula():
 
     # 12 nnz + 4 (nloc+1) + 16 nloc + 4 ncopies + 4 (ngamma+1)
     assert bench.spmv_algorithmic_bytes(S) == 221615328
+
+
+def test_reference_arm_line(capsys, monkeypatch):
+    """Rank 0 of the reference arm: one JSON line with the contract's keys,
+    a complete FP64 oracle solve of the 128^3 system to 1e-8 timed on the
+    host cores (about 8 s here), the headline's workload and unit."""
+    import json
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0"]) == 0
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is False and d["dtype"] == "f64"
+    assert d["config"]["workload"] == "fv3d_7pt_128^3_kappa=exp(N(0,1))_4x4x4_subdomains"
+    assert d["config"]["mode"] == "fp64" and d["config"]["rtol"] == 1e-8
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert abs(cb["iters"] - 1055) <= 0.03 * 1055 and cb["true_relres"] <= 1.01e-8
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
