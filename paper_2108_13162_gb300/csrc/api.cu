@@ -496,9 +496,12 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
         W.seg_blk[sg + 1] = W.seg_blk[sg] + gs;
     }
     W.gridB = W.seg_blk[nseg];
-    // vector-kernel chunks: about one per SM in all, a multiple of 64
-    // entries, at least one per segment
-    const int64_t ch = std::max<int64_t>(64, (M.nloc / num_sms + 63) / 64 * 64);
+    // vector-kernel chunks: about one per SM in all for one system (every
+    // chunk's block sums the system's product partials per column), four for
+    // a batch (a large system then spreads over more SMs once the small ones
+    // have converged); a multiple of 64 entries, at least one per segment
+    const int per_sm = nseg > 1 ? 4 : 1;
+    const int64_t ch = std::max<int64_t>(64, (M.nloc / (num_sms * per_sm) + 63) / 64 * 64);
     W.seg_chunk.assign(static_cast<size_t>(nseg) + 1, 0);
     for (int sg = 0; sg < nseg; ++sg) {
         const int64_t e0 = M.off[seg_sub[sg]], e1 = M.off[seg_sub[sg + 1]];
