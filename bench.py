@@ -444,10 +444,16 @@ def bench_batch(ctx, stream, reps, size):
     setup_s = time.perf_counter() - t0
     tune = B.autotune_block(reps=10)
     bb = torch.from_numpy(np.concatenate([b.ravel() for b in bp.b])).cuda()
+    # mixed precision's inner tolerance for this workload: 1e-5 measured best
+    # on the batch (4.54 s against 4.75 at the library's default 1e-4; the
+    # single 128^3 and FE systems are indifferent, 16 right-hand sides 2 %
+    # slower), set for the batch's solves and restored afterwards
+    inner_rtol = 1e-5
+    ctx.set_mixed(inner_rtol, 30)
     out = {"workload": "fv2d_5pt_batch512_side32-%d_sigma0.5_4-16subdomains_1-8rhs" % hi,
            "systems": len(bp.A), "unknowns": int(sum(A.n for A in bp.A)), "nnz": int(sum(A.nnz for A in bp.A)),
            "rhs": int(sum(b.shape[0] for b in bp.b)), "subdomains": int(sum(bp.P)), "rtol": RTOL,
-           "setup_s": setup_s, "autotune_block": tune}
+           "mixed_inner_rtol": inner_rtol, "setup_s": setup_s, "autotune_block": tune}
     for mode_name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED), ("mixed_jacobi", ssg.SSG_MIXED_JACOBI)):
         x, rc, st = B.solve(bb, rtol=RTOL, mode=mode)
         torch.cuda.synchronize()
@@ -469,6 +475,7 @@ def bench_batch(ctx, stream, reps, size):
         peak, _ = measured_peaks()
         out[mode_name + "_roofline"] = {"algorithmic_bytes": nb, "achieved_gbs": nb / sec / 1e9,
                                         "frac": nb / sec / 1e9 / peak, "peak": peak}
+    ctx.set_mixed(1e-4, 30)
     B.close()
     # the same systems one after another (each with its right-hand sides together)
     if size != "full":
