@@ -501,7 +501,7 @@ int ssg_system_destroy(ssg_system *sys);
  * Limit: nloc <= 33,554,432 (8192 partial sums of 4096 entries); larger
  * nloc, a negative nloc or a null pointer returns SSG_E_INVALID.
  * The first call on a device looks up the scratch address on that device
- * (one runtime call; later calls on it make none).  Every call shares the one
+ * (cudaGetSymbolAddress); later calls on it reuse the address.  Every call shares the one
  * scratch array: calls that can overlap on the GPU (different streams, or
  * threads) race and must be serialised by the caller.
  */
