@@ -76,6 +76,53 @@ def test_host_maps_bit_exact_vs_oracle(case):
     assert np.array_equal(got["lval"].view(np.int64), ref.lval.view(np.int64))
 
 
+def _random_case(seed):
+    """A small random SPD system and partition: random, contiguous, with
+    more subdomains than nodes, or with every node in the top subdomain."""
+    import scipy.sparse as sp
+
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(1, 120))
+    if seed % 5 == 4:
+        # a diagonal-only (isolated) node block next to a coupled one
+        A = random_spd(max(n - 3, 1), float(rng.uniform(1.0, 6.0)), rng).to_scipy()
+        A = sp.block_diag([A, sp.diags(rng.uniform(1.0, 2.0, 3))]).tocsr()
+        A.sort_indices()
+        A = CSR(A.shape[0], A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float64))
+    else:
+        A = random_spd(n, float(rng.uniform(1.0, 8.0)), rng)
+    n = A.n
+    kind = seed % 4
+    P = int(rng.integers(1, 12))
+    if kind == 0:
+        part = rng.integers(0, P, n)
+    elif kind == 1:
+        part = np.arange(n) * P // n
+    elif kind == 2:
+        P = n + int(rng.integers(1, 5))  # more subdomains than nodes: some empty
+        part = rng.integers(0, P, n)
+    else:
+        part = np.full(n, P - 1)  # only the top id used
+    return A, part.astype(np.int32), P
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_host_maps_bit_exact_random(seed):
+    A, part, P = _random_case(seed)
+    sys_ = ssg.ssg_partition(None, A.n, A.rowptr, A.colidx, A.val, part, P)
+    try:
+        got = ssg.ssg_copy_maps(sys_)
+        sz = ssg.ssg_get_sizes(sys_)
+    finally:
+        ssg.ssg_system_destroy(sys_)
+    ref = oracle.Partition(A, part, P).maps
+    assert (sz.n, sz.P, sz.nnz, sz.nloc, sz.ngamma, sz.ncopies) == (
+        ref.n, ref.P, ref.nnz, ref.nloc, ref.ngamma, ref.ncopies)
+    for k in ("off", "nint", "l2g", "mult", "lrowptr", "lcol", "gamma", "iptr", "icopy", "own"):
+        assert np.array_equal(got[k], getattr(ref, k)), k
+    assert np.array_equal(got["lval"].view(np.int64), ref.lval.view(np.int64))
+
+
 def test_full_size_maps_bit_exact():
     """The 128^3 / 4x4x4 workload: counts and maps identical to the oracle's."""
     p = config_problem(2)
