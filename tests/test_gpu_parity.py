@@ -186,3 +186,42 @@ def test_spmv_deterministic(ctx):
     y2 = S.spmv(x)
     torch.cuda.synchronize()
     assert torch.equal(y1, y2)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_systems_product_and_iterates(ctx, seed):
+    """The 40 seeded random systems and partitions of the host-map sweep
+    (empty and unused subdomains, isolated nodes, one-node systems): the
+    product on every local entry within 4 (L_i + m_i) u (|A||x|)_i of the
+    oracle's, and a solve's first six iterates within 1e-10 of the oracle's,
+    through the one-cluster solve (the default at these sizes) and the loop."""
+    import torch
+
+    from paper_2108_13162_gb300.ssg import System
+    from tests.test_abi_host import _random_case
+
+    A, part, P = _random_case(seed)
+    S = System(ctx, A, part, P)
+    ref = oracle.Partition(A, part, P)
+    m = ref.maps
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-1, 1, A.n)
+    xl = ref.scatter(x)
+    y = S.spmv(torch.from_numpy(xl).cuda()).cpu().numpy()
+    absAx = abs(A.to_scipy()) @ np.abs(x)
+    L = np.zeros(A.n)
+    np.maximum.at(L, m.l2g, np.diff(m.lrowptr))
+    assert np.all(np.abs(y - ref.spmv(xl)) <= 4.0 * (L[m.l2g] + m.mult[m.l2g]) * U * absAx[m.l2g])
+    b = rng.uniform(-1, 1, A.n)
+    k = min(6, A.n)
+    r = ref.cg(b, 0.0, k)
+    limit = ctx.cluster_solve()[0]
+    for lim in (limit, 0):
+        ctx.set_cluster_solve(lim)
+        try:
+            xg, rc, st = S.solve(torch.from_numpy(b).cuda(), rtol=0.0, max_iter=k)
+        finally:
+            ctx.set_cluster_solve(limit)
+        rel = np.linalg.norm(xg.cpu().numpy() - r.x) / max(np.linalg.norm(r.x), 1e-300)
+        assert rel <= 1e-10, (lim, rel)
+    S.close()
