@@ -288,3 +288,31 @@ def test_block_autotune_same_bits(ctx, k):
     with pytest.raises(ssg.SSGError):
         S.autotune_block(3)
     S.close()
+
+
+@pytest.mark.parametrize("seed", range(0, 40, 3))
+def test_spmm_random_systems_bitwise(ctx, seed):
+    """The seeded random systems of the host-map sweep (empty and unused
+    subdomains, isolated nodes): every column of the 2-, 4-, 8- and
+    16-vector products, FP64 and FP32, bit-identical to the single-vector
+    product of that column."""
+    import torch
+
+    from paper_2108_13162_gb300.ssg import System
+    from tests.test_abi_host import _random_case
+
+    A, part, P = _random_case(seed)
+    S = System(ctx, A, part, P)
+    ref = oracle.Partition(A, part, P)
+    rng = np.random.default_rng(seed)
+    for k in (2, 4, 8, 16):
+        Xl = np.stack([ref.scatter(rng.uniform(-1, 1, A.n)) for _ in range(k)], axis=1)
+        for dt, prec in ((torch.float64, "fp64"), (torch.float32, "fp32")):
+            Xd = _t(Xl).to(dt)
+            Y = S.spmm(Xd).cpu().numpy()
+            for j in range(k):
+                col = Xd[:, j].contiguous()
+                y1 = torch.empty_like(col)
+                S.spmv_prec(col, y1, prec)
+                assert np.array_equal(Y[:, j], y1.cpu().numpy()), (k, prec, j)
+    S.close()
