@@ -215,3 +215,27 @@ def test_owner_element_substructures(ctx):
     x, rc, st = S.solve(_t(bb), rtol=1e-12, max_iter=100000)
     assert rc == ssg.SSG_OK and _rel(x.cpu().numpy(), ref.cg(bb, 1e-12, 100000).x) <= 1e-10
     S.close()
+
+
+@pytest.mark.parametrize("seed", range(0, 40, 4))
+def test_owner_dot_random_systems(ctx, seed):
+    """The owner-mask dot on the seeded random systems of the host-map sweep:
+    within the rounding bound of the oracle's, for arbitrary local vectors."""
+    from paper_2108_13162_gb300 import ssg
+    from paper_2108_13162_gb300.ssg import System
+    from tests.test_abi_host import _random_case
+
+    A, part, P = _random_case(seed)
+    S = System(ctx, A, part, P)
+    S.set_weights(ssg.SSG_WEIGHT_OWNER)
+    ref = oracle.Partition(A, part, P)
+    ref.set_weights(oracle.WEIGHT_OWNER)
+    m = ref.maps
+    rng = np.random.default_rng(seed)
+    ul = rng.uniform(-1, 1, m.nloc)
+    vl = rng.uniform(-1, 1, m.nloc)
+    own = np.zeros(m.nloc)
+    own[m.own] = 1.0
+    bound = 2 * m.nloc * U * float(np.sum(own * np.abs(ul * vl))) + 1e-300
+    assert abs(float(S.wdot(_t(ul), _t(vl)).cpu()) - ref.wdot(ul, vl)) <= bound
+    S.close()
