@@ -72,6 +72,9 @@ def parse_args(argv=None):
     ap.add_argument("--profile-block", choices=("fp64", "mixed"), default=None,
                     help="only build the 96^3 16-right-hand-side workload and run one solve of all 16 together "
                          "with the host-loop driver (for an ncu launch list); no JSON line")
+    ap.add_argument("--profile-batch", choices=("fp64", "mixed"), default=None,
+                    help="only build the 512-system batch of sides 32..128 and run one solve of all its "
+                         "right-hand sides with the host-loop driver (for an ncu launch list); no JSON line")
     ap.add_argument("--profile-spmv", choices=("fp64", "fp32"), default=None,
                     help="only build the workload and launch the SpMV --spmv-reps times (for ncu); no JSON line")
     ap.add_argument("--profile-fe", choices=("fp64", "fp32"), default=None,
@@ -938,6 +941,24 @@ def run_ours(args, dist):
         S.close()
         ctx.close()
         return 0
+    if args.profile_batch:
+        import numpy as np
+
+        from paper_2108_13162_gb300.ssg import Batch
+        from synth import batch_problem
+
+        bp = batch_problem(512, 32, 128)
+        Bt = Batch(ctx, [(A, pt, P, b.shape[0]) for A, pt, P, b in zip(bp.A, bp.part, bp.P, bp.b)])
+        ctx.set_driver(ssg.SSG_DRIVER_HOST)
+        bb = torch.from_numpy(np.concatenate([b.ravel() for b in bp.b])).cuda()
+        mode = ssg.SSG_MIXED if args.profile_batch == "mixed" else ssg.SSG_FP64
+        x, rc, st = Bt.solve(bb, rtol=RTOL, mode=mode)
+        torch.cuda.synchronize()
+        print("batch solve (%s): status %d, iterations %d, launches %d" % (
+            args.profile_batch, rc, max(t["iters"] for t in st), st[0]["kernel_launches"]))
+        Bt.close()
+        ctx.close()
+        return 0 if rc == ssg.SSG_OK else 1
     if args.profile_spmm:
         from synth import config_problem
 
