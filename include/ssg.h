@@ -273,6 +273,23 @@ int ssg_get_sizes(const ssg_system *sys, ssg_sizes *out);
  * they hold, out[2] = subdomains whose slices are sorted by row length,
  * out[3] = the largest sorting window (1: none).  Host memory, 4 int64. */
 int ssg_get_layout(const ssg_system *sys, int64_t *out);
+/* The interface layout of a system's products (Algorithms 4/5 fused into
+ * them).  Every product can read the interface copy rows as slices of whole
+ * nodes, up to 32 copy rows in (node, copy) order, one copy row per lane, the
+ * node sums formed by warp shuffles; a slice pads every copy row to its
+ * longest, and a node's copies in the lower subdomains hold only the entries
+ * those own (one on a face of the 7-point grids, against six in the owner's
+ * row).  The FP64 single-vector product can instead read groups of up to 32
+ * nodes of one multiplicity m, one node per lane, its m copy rows in m
+ * sub-slices padded rank by rank, the node sum formed in the lane (the same
+ * operations in the same order: the same products).  It takes the groups
+ * when they store at least 4 % of all its sliced entries fewer; the FP32
+ * and K-vector products and the one-cluster solve always read the slices.
+ * out[0] = entries stored in interface slices, out[1] = in interface groups
+ * (both with padding), out[2] = 1 if the FP64 single-vector product reads
+ * the groups.
+ * Host memory, 3 int64; SSG_E_INVALID for a null argument. */
+int ssg_get_iface_layout(const ssg_system *sys, int64_t *out);
 
 /*
  * Copy the sub-structure maps into caller host buffers (any pointer may be

@@ -60,10 +60,15 @@ struct ssg_system {
     // entries, subdomains sorted by row length, the largest sorting window
     int64_t slice_slots = 0, slice_entries = 0;
     int32_t sorted_subdomains = 0, max_window = 1;
+    // the interface layout: entries stored in interface slices and in
+    // interface groups (padding included)
+    int64_t iface_slots = 0, group_slots = 0;
     int grid_spmv = 0;
     int grid_spmv32 = 0;
     int grid_bps[7] = {0, 0, 0, 0, 0, 0, 0};        // single-vector grids for 3 to 6 blocks per SM
     const int2 *range_bps[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int grid_bps32[7] = {0, 0, 0, 0, 0, 0, 0};      // the same for the FP32 product (interface slices)
+    const int2 *range_bps32[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int var64 = 0, var32 = 0;                       // chosen SpMV instances (ssg_autotune)
     // weights of the weighted dots (ssg_set_weights): the multiplicity codes
     // (w = 1/m) and the owner-mask codes; the operators read one of them
@@ -87,13 +92,16 @@ struct ssg_system {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // new values for the same pattern (ssg_set_values): the input-CSR entry
     // each device value copies (-1: padding)
-    int32_t *d_vmap = nullptr, *d_imap = nullptr, *d_smap = nullptr;
+    int32_t *d_vmap = nullptr, *d_imap = nullptr, *d_smap = nullptr, *d_gmap = nullptr;
+    int64_t n_gval = 0;  // interface groups' sliced entries (d_gmap)
     int64_t n_ival = 0, n_sval = 0;
     int32_t *d_growptr = nullptr;  // 7-point grid row pointers (ssg_fv7_*), after the pattern check
     int fv7_dims[3] = {0, 0, 0};
     // several right-hand sides and independent systems together (block.cuh):
     // segments = independent systems (one for a system from ssg_partition)
     DevOp opB64{}, opB32{};  // K-vector product launches (warp ranges cut inside each segment)
+    const WorkItem *items_slices = nullptr;  // the item list with interface slices (kind 1)
+    bool iface_groups = false;               // op.items holds interface groups (kind 5) instead
     // the K-vector product's entries loaded at once (1 or 2) and L2 look-ahead
     // per precision (0: FP64, 1: FP32) and log2 K - 1 (ssg_autotune_block)
     int8_t spmm_nc[2][4] = {{2, 2, 1, 1}, {2, 2, 2, 2}};
@@ -170,6 +178,15 @@ const SpmvVariant<double> kSpmv64Variants[kSpmvVariants] = {
     {5, 0, k_spmv_asm<kEpiPartials, double, 5, 0>, k_spmv_asm<kEpiStore, double, 5, 0>},
     {5, 1, k_spmv_asm<kEpiPartials, double, 5, 1>, k_spmv_asm<kEpiStore, double, 5, 1>},
 };
+// the same instances reading interface groups (systems that use them)
+const SpmvVariant<double> kSpmv64VariantsG[kSpmvVariants] = {
+    {4, 0, k_spmv_asm<kEpiPartials, double, 4, 0, true>, k_spmv_asm<kEpiStore, double, 4, 0, true>},
+    {4, 1, k_spmv_asm<kEpiPartials, double, 4, 1, true>, k_spmv_asm<kEpiStore, double, 4, 1, true>},
+    {3, 0, k_spmv_asm<kEpiPartials, double, 3, 0, true>, k_spmv_asm<kEpiStore, double, 3, 0, true>},
+    {3, 1, k_spmv_asm<kEpiPartials, double, 3, 1, true>, k_spmv_asm<kEpiStore, double, 3, 1, true>},
+    {5, 0, k_spmv_asm<kEpiPartials, double, 5, 0, true>, k_spmv_asm<kEpiStore, double, 5, 0, true>},
+    {5, 1, k_spmv_asm<kEpiPartials, double, 5, 1, true>, k_spmv_asm<kEpiStore, double, 5, 1, true>},
+};
 const SpmvVariant<float> kSpmv32Variants[kSpmvVariants] = {
     {5, 1, k_spmv_asm<kEpiPartials, float, 5, 1>, k_spmv_asm<kEpiStore, float, 5, 1>},
     {5, 0, k_spmv_asm<kEpiPartials, float, 5, 0>, k_spmv_asm<kEpiStore, float, 5, 0>},
@@ -179,14 +196,21 @@ const SpmvVariant<float> kSpmv32Variants[kSpmvVariants] = {
     {6, 2, k_spmv_asm<kEpiPartials, float, 6, 2>, k_spmv_asm<kEpiStore, float, 6, 2>},
 };
 
+// The FP64 instances a system launches: reading its interface groups, or
+// its slices.
+const SpmvVariant<double> *v64(const ssg_system *S) { return S->iface_groups ? kSpmv64VariantsG : kSpmv64Variants; }
+
 // SpMV work list (see WorkItem in kernels.cuh) and the sliced-ELL copy of
 // the local matrices it streams.  Interior slices: up to 32 consecutive
 // interior rows of one subdomain, width = their longest row; a row longer
 // than kSliceMaxWidth is an item of its own (read from the CSR arrays).
 // Interface slices: whole interface nodes, up to 32 copy rows in (node,
 // copy) order; a node with more than 32 copies or a copy row longer than
-// kSliceMaxWidth is an item of its own.  Padding entries have value 0 and a
-// column inside the same subdomain.  Interface items are spread evenly among
+// kSliceMaxWidth is an item of its own.  The FP64 single-vector product may
+// take a second list in which interface groups replace the slices
+// (make_plan).
+// Padding entries have value 0 and a column inside the same subdomain.
+// Interface items are spread evenly among
 // the interior ones, and the list is cut into one contiguous slice of about
 // equal cost per warp.
 struct WorkPlan {
@@ -195,13 +219,20 @@ struct WorkPlan {
     std::vector<int32_t> isrc, ssrc;  // local entry each copy-row / sliced value copies (-1: padding)
     std::vector<double> sval;        // sliced-ELL values
     std::vector<int32_t> scol, sseg;
+    std::vector<int32_t> gcopy;      // interface groups: per group and copy rank, the 32 lanes' copy rows
+    std::vector<double> gval;        // interface groups' sliced values (their own arrays: the slices'
+    std::vector<int32_t> gcol, gsrc;  // stay as they are), columns, local entry (-1: padding)
     std::vector<int32_t> srow;       // sorted slices: the local row of each slot
     int64_t slice_slots = 0;         // interior slice entries stored (padding included)
     int64_t slice_entries = 0;       // interior nonzeros in slices
     int32_t sorted_subdomains = 0;   // subdomains whose interior slices are sorted by row length
     int32_t max_window = 1;          // the largest sorting window used
     std::vector<WorkItem> items;
+    std::vector<WorkItem> items_g;   // the same with interface groups (empty: the product keeps items)
+    int64_t iface_slots = 0;         // interface slice entries stored (padding included)
+    int64_t group_slots = 0;         // the same in interface groups
     std::vector<int2> range_bps[7];  // per warp of a single-vector launch sized for 3 to 6 blocks per SM
+    std::vector<int2> range_bps32[7];  // the same over the slices' list (the FP32 product)
     std::vector<int2> warp_rangeB;   // per warp of the K-vector product: cut inside each segment
     std::vector<int2> range_cluster;  // per warp of the one-cluster solve (cluster_ctas CTAs)
     int32_t cluster_nranges = 0;      // its non-empty ranges (a prefix)
@@ -209,12 +240,13 @@ struct WorkPlan {
     std::vector<int4> chunk;                // vector-kernel chunks (segment, first entry, end entry, 0)
     std::vector<int32_t> seg_chunk;         // chunks per segment
     int grid_bps[7] = {0, 0, 0, 0, 0, 0, 0};
+    int grid_bps32[7] = {0, 0, 0, 0, 0, 0, 0};
     int gridB = 0;
 };
 
 double item_cost(const WorkItem &w) {
     double cost = 64.0;
-    if (sliced_item(w.kind)) cost += 32.0 * w.e1;
+    if (sliced_item(w.kind) || w.kind == kItemIfaceGroup) cost += 32.0 * w.e1;
     else cost += 4.0 * (w.e1 - w.e0);
     return cost;
 }
@@ -434,38 +466,152 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
                 }
             }
         iface.push_back({kItemIfaceSlice, c0, c1, off, w, 0, 0, 0});
+        W.iface_slots += static_cast<int64_t>(w) * kSliceRows;
         g = g1;
+    }
+    // interface groups (kind 5), for the FP64 single-vector product only: a
+    // node with more than kGroupMaxCopies copies or a copy row longer than
+    // kSliceMaxWidth is an item of its own (kind 3); the others go in groups
+    // of up to 32 nodes of one multiplicity m, one node per lane, per
+    // segment.  A group's data holds m sub-slices, the r-th with the r-th
+    // copy rows of its nodes at the width of the longest, so that a node's
+    // copies meet in one lane and a short copy row (a node's copies in the
+    // lower subdomains hold only the entries those own: one on the faces of
+    // the 7-point grids) never pads to a long one's width.  Within windows
+    // of kGroupWindow nodes of one multiplicity the nodes are ordered by
+    // decreasing copy-row lengths (rank 0 first; ties in node order).  The
+    // groups are built, and the product takes them, only when they store at
+    // least kGroupGain of all the product's sliced entries fewer than the
+    // slices (measured on the 128^3 system, where they save 4.9 %: the FP64
+    // product 2 % and the FP64 solve 3 % faster; on the P1 mesh, 2.6 %: no
+    // gain.  The FP32 products, the K-vector products and the one-cluster
+    // solve, no faster or slower with them, keep the slices)
+    std::vector<WorkItem> iface_g;
+    constexpr double kGroupGain = 0.04;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool emit = pass == 1;
+        if (emit && !(W.iface_slots > W.group_slots &&
+                      static_cast<double>(W.iface_slots - W.group_slots) >=
+                          kGroupGain * static_cast<double>(W.slice_slots + W.iface_slots)))
+            break;
+        constexpr size_t kGroupWindow = 512;
+        auto clen = [&](int32_t c) { return W.irp[c + 1] - W.irp[c]; };
+        auto long_node_g = [&](int32_t gg) {
+            if (M.iptr[gg + 1] - M.iptr[gg] > kGroupMaxCopies) return true;
+            for (int32_t c = M.iptr[gg]; c < M.iptr[gg + 1]; ++c)
+                if (clen(c) > kSliceMaxWidth) return true;
+            return false;
+        };
+        std::vector<int32_t> by_mult[kGroupMaxCopies + 1];
+        g = 0;
+        while (g < M.ngamma) {
+            const int sg = node_seg(g);
+            int32_t g1 = g;
+            while (g1 < M.ngamma && node_seg(g1) == sg) ++g1;
+            for (std::vector<int32_t> &v : by_mult) v.clear();
+            for (int32_t gg = g; gg < g1; ++gg) {
+                if (long_node_g(gg)) {
+                    const int32_t c0 = M.iptr[gg], c1 = M.iptr[gg + 1];
+                    if (emit) iface_g.push_back({kItemLongIface, gg, gg + 1, W.irp[c0], W.irp[c1], c0, c1, 0});
+                } else {
+                    by_mult[M.iptr[gg + 1] - M.iptr[gg]].push_back(gg);
+                }
+            }
+            for (int m = 1; m <= kGroupMaxCopies; ++m) {
+                std::vector<int32_t> &nodes = by_mult[m];
+                for (size_t w0 = 0; w0 < nodes.size(); w0 += kGroupWindow) {
+                    const size_t w1 = std::min(nodes.size(), w0 + kGroupWindow);
+                    std::stable_sort(nodes.begin() + w0, nodes.begin() + w1, [&](int32_t x, int32_t y) {
+                        for (int r = 0; r < m; ++r) {
+                            const int32_t lx = clen(M.iptr[x] + r), ly = clen(M.iptr[y] + r);
+                            if (lx != ly) return lx > ly;
+                        }
+                        return false;
+                    });
+                }
+                for (size_t i0 = 0; i0 < nodes.size(); i0 += kSliceRows) {
+                    if (!emit) {
+                        for (int r = 0; r < m; ++r) {
+                            int32_t w = 0;
+                            for (size_t l = i0; l < std::min(nodes.size(), i0 + kSliceRows); ++l)
+                                w = std::max(w, clen(M.iptr[nodes[l]] + r));
+                            W.group_slots += static_cast<int64_t>(w) * kSliceRows;
+                        }
+                        continue;
+                    }
+                    const int cnt = static_cast<int>(std::min<size_t>(kSliceRows, nodes.size() - i0));
+                    const int32_t *nd = nodes.data() + i0;
+                    auto copy_of = [&](int lane, int r) { return M.iptr[nd[lane < cnt ? lane : 0]] + r; };
+                    const int32_t a = static_cast<int32_t>(W.gcopy.size());
+                    const int32_t off = static_cast<int32_t>(W.gval.size());
+                    int32_t wsum = 0;
+                    uint32_t wpack[2] = {0u, 0u};
+                    for (int r = 0; r < m; ++r) {
+                        int32_t w = 0;
+                        for (int l = 0; l < cnt; ++l) w = std::max(w, clen(copy_of(l, r)));
+                        wpack[r >> 2] |= static_cast<uint32_t>(w) << (8 * (r & 3));
+                        wsum += w;
+                        for (int l = 0; l < kSliceRows; ++l) W.gcopy.push_back(M.icopy[copy_of(l, r)]);
+                        for (int32_t k = 0; k < w; ++k)
+                            for (int l = 0; l < kSliceRows; ++l) {
+                                const int32_t c = copy_of(l, r);
+                                if (l < cnt && k < clen(c)) {
+                                    W.gval.push_back(W.ival[W.irp[c] + k]);
+                                    W.gcol.push_back(W.icol[W.irp[c] + k]);
+                                    W.gsrc.push_back(W.isrc[W.irp[c] + k]);
+                                } else {
+                                    W.gval.push_back(0.0);
+                                    W.gcol.push_back(M.icopy[c]);
+                                    W.gsrc.push_back(-1);
+                                }
+                            }
+                    }
+                    iface_g.push_back({kItemIfaceGroup, a, cnt, off, wsum, m, static_cast<int32_t>(wpack[0]),
+                                     static_cast<int32_t>(wpack[1])});
+                }
+            }
+            g = g1;
+        }
     }
     // per segment, interface item j goes after interior item floor((j+1) *
     // nrows / (niface+1)) of the segment
     auto item_seg = [&](const WorkItem &w) {
         if (w.kind == kItemSlice || w.kind == kItemLongRow) return seg_of_sub[sub_of[w.a]];
         if (w.kind == kItemSortedSlice) return seg_of_sub[sub_of[W.srow[w.a]]];
+        if (w.kind == kItemIfaceGroup) return seg_of_sub[sub_of[W.gcopy[w.a]]];
         const int32_t c = w.kind == kItemIfaceSlice ? w.a : w.c0;
         return seg_of_sub[sub_of[M.icopy[c]]];
     };
     std::vector<int32_t> seg_item(static_cast<size_t>(nseg) + 1, 0);
-    {
+    auto interleave = [&](const std::vector<WorkItem> &ifc, std::vector<WorkItem> &out) {
         size_t ir = 0, ii = 0;
         for (int sg = 0; sg < nseg; ++sg) {
             size_t r0 = ir, i0 = ii;
             while (ir < rows.size() && item_seg(rows[ir]) == sg) ++ir;
-            while (ii < iface.size() && item_seg(iface[ii]) == sg) ++ii;
+            while (ii < ifc.size() && item_seg(ifc[ii]) == sg) ++ii;
             const size_t nr = ir - r0, ni = ii - i0;
             size_t j = 0;
             for (size_t i = 0; i <= nr; ++i) {
-                while (j < ni && (j + 1) * nr <= i * (ni + 1)) W.items.push_back(iface[i0 + j++]);
-                if (i < nr) W.items.push_back(rows[r0 + i]);
+                while (j < ni && (j + 1) * nr <= i * (ni + 1)) out.push_back(ifc[i0 + j++]);
+                if (i < nr) out.push_back(rows[r0 + i]);
             }
-            while (j < ni) W.items.push_back(iface[i0 + j++]);
-            seg_item[sg + 1] = static_cast<int32_t>(W.items.size());
+            while (j < ni) out.push_back(ifc[i0 + j++]);
+            seg_item[sg + 1] = static_cast<int32_t>(out.size());
         }
-    }
-    const int n = static_cast<int>(W.items.size());
-    const int per = (n + kSpmvWarps - 1) / kSpmvWarps;
-    for (int bps = 3; bps <= 6; ++bps) {
-        W.grid_bps[bps] = std::max(1, std::min(per, num_sms * bps));
-        W.range_bps[bps] = cut_ranges(W.items, W.grid_bps[bps]);
+    };
+    if (!iface_g.empty()) interleave(iface_g, W.items_g);
+    interleave(iface, W.items);  // last: seg_item is this list's
+    // single-vector launches: FP64 the list with interface groups when
+    // built, FP32 the slices (latency-bound, it gains nothing from them:
+    // measured slower on the 96^3 system)
+    for (int prec = 0; prec < 2; ++prec) {
+        const std::vector<WorkItem> &items1 = prec == 0 && !W.items_g.empty() ? W.items_g : W.items;
+        const int per = (static_cast<int>(items1.size()) + kSpmvWarps - 1) / kSpmvWarps;
+        for (int bps = 3; bps <= 6; ++bps) {
+            int &grid = prec == 0 ? W.grid_bps[bps] : W.grid_bps32[bps];
+            grid = std::max(1, std::min(per, num_sms * bps));
+            (prec == 0 ? W.range_bps[bps] : W.range_bps32[bps]) = cut_ranges(items1, grid);
+        }
     }
     if (cluster_ctas > 0) {
         // kClusterWarps warps per CTA: cut for the equivalent number of
@@ -484,7 +630,8 @@ WorkPlan make_plan(const HostMaps &M, int num_sms, const std::vector<int32_t> &s
     constexpr int kSpmmBlocks = SpmmTraits<double>::kBlocksPerSM > SpmmTraits<float>::kBlocksPerSM
                                     ? SpmmTraits<double>::kBlocksPerSM
                                     : SpmmTraits<float>::kBlocksPerSM;
-    const int target = std::max(1, std::min(per, num_sms * kSpmmBlocks * (nseg > 1 ? 4 : 1)));
+    const int perB = (static_cast<int>(W.items.size()) + kSpmvWarps - 1) / kSpmvWarps;
+    const int target = std::max(1, std::min(perB, num_sms * kSpmmBlocks * (nseg > 1 ? 4 : 1)));
     W.seg_blk.assign(static_cast<size_t>(nseg) + 1, 0);
     for (int sg = 0; sg < nseg; ++sg) {
         const int nit = seg_item[sg + 1] - seg_item[sg];
@@ -523,7 +670,7 @@ double *part_rz(ssg_system *S) { return S->d_partials + 2 * (S->n_partials / 3);
 int launch_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const int64_t N = S->maps.nloc;
     const cudaGraphConditionalHandle h = pc ? S->cond_pc : S->cond;
-    SSG_CUDA_TRY(launch_k(kSpmv64Variants[S->var64].part, S->grid_spmv, kSpmvThreads, st, S->op, S->d_p,
+    SSG_CUDA_TRY(launch_k(v64(S)[S->var64].part, S->grid_spmv, kSpmvThreads, st, S->op, S->d_p,
                           S->d_q, part_pq(S), S->d_scal, (double *)nullptr, h, use_cond));
     SSG_CUDA_TRY(launch_k(pc ? k_update_r<true> : k_update_r<false>, S->grid_vec, kBlock, st, N, S->d_r,
                           S->d_q, S->op.mult, S->op.wtab, S->op.gflag, (const double *)part_pq(S), S->grid_spmv,
@@ -581,7 +728,7 @@ int launch_inner_body(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
 int launch_outer_tail(ssg_system *S, cudaStream_t st, int use_cond, bool pc) {
     const int64_t N = S->maps.nloc;
     k_ir_correct<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_xl, S->d_d32);
-    kSpmv64Variants[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, st>>>(
+    v64(S)[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, st>>>(
         S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
     k_ir_residual<<<S->grid_vec, kBlock, 0, st>>>(N, S->d_bl, S->d_q, S->d_r, S->op.mult, S->op.wtab, S->d_partials,
                                                   S->d_scal, S->d_scal_in, S->cond_out[pc], use_cond);
@@ -736,6 +883,8 @@ int upload(ssg_system *S) {
     S->slice_entries = plan.slice_entries;
     S->sorted_subdomains = plan.sorted_subdomains;
     S->max_window = plan.max_window;
+    S->iface_slots = plan.iface_slots;
+    S->group_slots = plan.group_slots;
     const int64_t N = M.nloc;
     // concatenated column ids
     std::vector<int32_t> gcol(static_cast<size_t>(M.nnz));
@@ -762,12 +911,15 @@ int upload(ssg_system *S) {
         wtab32[m] = static_cast<float>(wtab[m]);
     }
 
-    for (int bps = 3; bps <= 6; ++bps) S->grid_bps[bps] = plan.grid_bps[bps];
+    for (int bps = 3; bps <= 6; ++bps) {
+        S->grid_bps[bps] = plan.grid_bps[bps];
+        S->grid_bps32[bps] = plan.grid_bps32[bps];
+    }
     S->grid_spmv = plan.grid_bps[kSpmv64Variants[0].bps];
-    S->grid_spmv32 = plan.grid_bps[kSpmv32Variants[0].bps];
+    S->grid_spmv32 = plan.grid_bps32[kSpmv32Variants[0].bps];
     S->grid_vec = std::max(1, std::min<int>(static_cast<int>((N / 2 + kBlock - 1) / kBlock), C->num_sms * kVecBlocksPerSM));
     int max_grid = S->grid_vec;
-    for (int bps = 3; bps <= 6; ++bps) max_grid = std::max(max_grid, plan.grid_bps[bps]);
+    for (int bps = 3; bps <= 6; ++bps) max_grid = std::max({max_grid, plan.grid_bps[bps], plan.grid_bps32[bps]});
     S->n_partials = 3 * max_grid;
 
     struct Piece {
@@ -791,7 +943,7 @@ int upload(ssg_system *S) {
     size_t i_irp = add(plan.irp.data(), sizeof(int32_t) * plan.irp.size());
     size_t i_icol = add(plan.icol.data(), sizeof(int32_t) * plan.icol.size());
     size_t i_ival = add(plan.ival.data(), sizeof(double) * plan.ival.size());
-    if (plan.sval.size() > static_cast<size_t>(INT32_MAX)) {
+    if (plan.sval.size() > static_cast<size_t>(INT32_MAX) || plan.gval.size() > static_cast<size_t>(INT32_MAX)) {
         set_error("sliced matrix larger than 2^31 entries");
         return SSG_E_INVALID;
     }
@@ -802,9 +954,13 @@ int upload(ssg_system *S) {
     size_t i_sseg = add(plan.sseg.data(), sizeof(int32_t) * plan.sseg.size());
     size_t i_srow = add(plan.srow.data(), sizeof(int32_t) * plan.srow.size());
     size_t i_items = add(plan.items.data(), sizeof(WorkItem) * plan.items.size());
-    size_t i_range_bps[7] = {0, 0, 0, 0, 0, 0, 0};
+    size_t i_items_g = add(plan.items_g.data(), sizeof(WorkItem) * plan.items_g.size());
+    size_t i_gcopy = add(plan.gcopy.data(), sizeof(int32_t) * plan.gcopy.size());
+    size_t i_range_bps[7] = {0, 0, 0, 0, 0, 0, 0}, i_range_bps32[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int bps = 3; bps <= 6; ++bps)
         i_range_bps[bps] = add(plan.range_bps[bps].data(), sizeof(int2) * plan.range_bps[bps].size());
+    for (int bps = 3; bps <= 6; ++bps)
+        i_range_bps32[bps] = add(plan.range_bps32[bps].data(), sizeof(int2) * plan.range_bps32[bps].size());
     size_t i_brangeB = add(plan.warp_rangeB.data(), sizeof(int2) * plan.warp_rangeB.size());
     size_t i_rcluster = add(plan.range_cluster.data(), sizeof(int2) * plan.range_cluster.size());
     size_t i_blk_seg = add(plan.blk_seg.data(), sizeof(int32_t) * plan.blk_seg.size());
@@ -882,6 +1038,15 @@ int upload(ssg_system *S) {
     size_t i_scal2 = add(nullptr, sizeof(Scal));
     size_t i_xg = add(nullptr, sizeof(double) * M.n);
     size_t i_bg = add(nullptr, sizeof(double) * M.n);
+    // the interface groups' sliced data (the small tables sit beside the
+    // other item lists: every launch reads them first)
+    std::vector<float> gval32(plan.gval.begin(), plan.gval.end());
+    std::vector<int32_t> gmap(plan.gsrc.size());
+    for (size_t i = 0; i < gmap.size(); ++i) gmap[i] = plan.gsrc[i] >= 0 ? vmap[plan.gsrc[i]] : -1;
+    size_t i_gval = add(plan.gval.data(), sizeof(double) * plan.gval.size());
+    size_t i_gval32 = add(gval32.data(), sizeof(float) * gval32.size());
+    size_t i_gcol = add(plan.gcol.data(), sizeof(int32_t) * plan.gcol.size());
+    size_t i_gmap = add(gmap.data(), sizeof(int32_t) * gmap.size());
 
     cudaError_t e = cudaMalloc(&S->arena, total);
     if (e != cudaSuccess) {
@@ -921,8 +1086,21 @@ int upload(ssg_system *S) {
     S->op.scol = static_cast<const int32_t *>(at(i_scol));
     S->op.sseg = static_cast<const int32_t *>(at(i_sseg));
     S->op.srow = static_cast<const int32_t *>(at(i_srow));
-    S->op.items = static_cast<const WorkItem *>(at(i_items));
-    for (int bps = 3; bps <= 6; ++bps) S->range_bps[bps] = static_cast<const int2 *>(at(i_range_bps[bps]));
+    S->op.gcopy = static_cast<const int32_t *>(at(i_gcopy));
+    S->op.gval = static_cast<const double *>(at(i_gval));
+    S->op.gval32 = static_cast<const float *>(at(i_gval32));
+    S->op.gcol = static_cast<const int32_t *>(at(i_gcol));
+    S->d_gmap = static_cast<int32_t *>(at(i_gmap));
+    S->n_gval = static_cast<int64_t>(gmap.size());
+    // single-vector products: the list with interface groups when built;
+    // the K-vector products and the one-cluster solve: the slices
+    S->items_slices = static_cast<const WorkItem *>(at(i_items));
+    S->op.items = plan.items_g.empty() ? S->items_slices : static_cast<const WorkItem *>(at(i_items_g));
+    S->iface_groups = !plan.items_g.empty();
+    for (int bps = 3; bps <= 6; ++bps) {
+        S->range_bps[bps] = static_cast<const int2 *>(at(i_range_bps[bps]));
+        S->range_bps32[bps] = static_cast<const int2 *>(at(i_range_bps32[bps]));
+    }
     S->op.warp_range = S->range_bps[kSpmv64Variants[0].bps];
     S->op32 = S->op;  // filled below once the op is complete
     S->op.iptr = static_cast<const int32_t *>(at(i_iptr));
@@ -947,11 +1125,12 @@ int upload(ssg_system *S) {
     S->d_xg = static_cast<double *>(at(i_xg));
     S->d_bg = static_cast<double *>(at(i_bg));
     S->op32 = S->op;
-    S->op32.warp_range = S->range_bps[kSpmv32Variants[0].bps];
+    S->op32.items = S->items_slices;
+    S->op32.warp_range = S->range_bps32[kSpmv32Variants[0].bps];
     S->opB64 = S->op;
+    S->opB64.items = S->items_slices;
     S->opB64.warp_range = static_cast<const int2 *>(at(i_brangeB));
-    S->opB32 = S->op;
-    S->opB32.warp_range = static_cast<const int2 *>(at(i_brangeB));
+    S->opB32 = S->opB64;
     S->grid_spmmB = plan.gridB;
     if (!plan.range_cluster.empty()) {
         S->range_cluster = static_cast<const int2 *>(at(i_rcluster));
@@ -1117,6 +1296,7 @@ int launch_cluster_cg(ssg_system *S, cudaStream_t st, bool pc) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     DevOp A = S->op;
+    A.items = S->items_slices;
     A.warp_range = S->range_cluster;
     const int64_t N = S->maps.nloc;
     if (pc)
@@ -1148,7 +1328,7 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     ++launches;
     if (guess) {
         k_scatter<<<grid_for(N, C->num_sms), kBlock, 0, s>>>(N, S->d_l2g, x_glob, S->d_xl);
-        kSpmv64Variants[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, s>>>(
+        v64(S)[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, s>>>(
             S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
         launches += 2;
     } else {
@@ -1177,7 +1357,7 @@ int solve_one(ssg_system *S, const double *b_glob, double *x_glob, int guess, do
     }
     k_gather<<<grid_for(S->maps.n, C->num_sms), kBlock, 0, s>>>(S->maps.n, S->d_own, S->d_xl, x_glob);
     // true residual ||b - S x||_w in FP64
-    kSpmv64Variants[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, s>>>(
+    v64(S)[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, s>>>(
         S->op, S->d_xl, S->d_q, S->d_partials, S->d_scal_op, nullptr, 0, 0);
     k_wdot<true><<<S->grid_vec, kBlock, 0, s>>>(N, S->d_bl, S->d_q, S->op.mult, S->op.wtab, S->d_partials,
                                                 S->d_scal_op, &S->d_scal->aux);
@@ -1897,6 +2077,9 @@ int ssg_partition(ssg_ctx *ctx, int32_t n, const int32_t *rowptr, const int32_t 
         S->slice_entries = plan.slice_entries;
         S->sorted_subdomains = plan.sorted_subdomains;
         S->max_window = plan.max_window;
+        S->iface_slots = plan.iface_slots;
+        S->group_slots = plan.group_slots;
+        S->iface_groups = !plan.items_g.empty();
     }
     *sys = S;
     return SSG_OK;
@@ -2563,6 +2746,17 @@ int ssg_get_layout(const ssg_system *S, int64_t *out) {
     return SSG_OK;
 }
 
+int ssg_get_iface_layout(const ssg_system *S, int64_t *out) {
+    if (!S || !out) {
+        set_error("null argument");
+        return SSG_E_INVALID;
+    }
+    out[0] = S->iface_slots;
+    out[1] = S->group_slots;
+    out[2] = S->iface_groups ? 1 : 0;
+    return SSG_OK;
+}
+
 int ssg_get_sizes(const ssg_system *S, ssg_sizes *o) {
     if (!S || !o) {
         set_error("null argument");
@@ -2638,10 +2832,10 @@ int ssg_spmv_assembled(ssg_system *S, const double *x_loc, double *y_loc, double
     // without xSx the loop's instance (block partials only); with it the one
     // whose last block sums the partials (a ticket, a few microseconds more)
     if (xSx_dev)
-        kSpmv64Variants[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, S->ctx->stream>>>(
+        v64(S)[S->var64].store<<<S->grid_spmv, kSpmvThreads, 0, S->ctx->stream>>>(
             S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, xSx_dev, 0, 0);
     else
-        kSpmv64Variants[S->var64].part<<<S->grid_spmv, kSpmvThreads, 0, S->ctx->stream>>>(
+        v64(S)[S->var64].part<<<S->grid_spmv, kSpmvThreads, 0, S->ctx->stream>>>(
             S->op, x_loc, y_loc, S->d_partials, S->d_scal_op, nullptr, 0, 0);
     SSG_CUDA_TRY(cudaGetLastError());
     return SSG_OK;
@@ -2674,7 +2868,7 @@ int ssg_autotune(ssg_system *S, int32_t reps, ssg_tune *out) {
     // as the loop launches them (block partials, no last-block sum)
     double best = 1e30;
     for (int v = 0; v < kSpmvVariants; ++v) {
-        const SpmvVariant<double> &V = kSpmv64Variants[v];
+        const SpmvVariant<double> &V = v64(S)[v];
         DevOp A = S->op;
         A.warp_range = S->range_bps[V.bps];
         const int grid = S->grid_bps[V.bps];
@@ -2700,8 +2894,8 @@ int ssg_autotune(ssg_system *S, int32_t reps, ssg_tune *out) {
     for (int v = 0; v < kSpmvVariants; ++v) {
         const SpmvVariant<float> &V = kSpmv32Variants[v];
         DevOp A = S->op32;
-        A.warp_range = S->range_bps[V.bps];
-        const int grid = S->grid_bps[V.bps];
+        A.warp_range = S->range_bps32[V.bps];
+        const int grid = S->grid_bps32[V.bps];
         for (int i = 0; i < 3; ++i)
             V.part<<<grid, kSpmvThreads, 0, st>>>(A, S->d_p32, S->d_q32, S->d_partials, S->d_scal_op, nullptr, 0, 0);
         SSG_CUDA_TRY(cudaEventRecord(S->ev0, st));
@@ -2726,8 +2920,8 @@ int ssg_autotune(ssg_system *S, int32_t reps, ssg_tune *out) {
     S->var32 = t.fp32_choice;
     S->op.warp_range = S->range_bps[kSpmv64Variants[S->var64].bps];
     S->grid_spmv = S->grid_bps[kSpmv64Variants[S->var64].bps];
-    S->op32.warp_range = S->range_bps[kSpmv32Variants[S->var32].bps];
-    S->grid_spmv32 = S->grid_bps[kSpmv32Variants[S->var32].bps];
+    S->op32.warp_range = S->range_bps32[kSpmv32Variants[S->var32].bps];
+    S->grid_spmv32 = S->grid_bps32[kSpmv32Variants[S->var32].bps];
     destroy_single_graphs(S);
     if (out) *out = t;
     return SSG_OK;
@@ -2792,6 +2986,10 @@ int ssg_set_values(ssg_system *S, const double *val) {
         k_gather_vals<<<grid_for(S->n_sval, ns), kBlock, 0, st>>>(S->n_sval, S->d_smap, val,
                                                                   const_cast<double *>(S->op.sval),
                                                                   const_cast<float *>(S->op.sval32));
+    if (S->n_gval)
+        k_gather_vals<<<grid_for(S->n_gval, ns), kBlock, 0, st>>>(S->n_gval, S->d_gmap, val,
+                                                                  const_cast<double *>(S->op.gval),
+                                                                  const_cast<float *>(S->op.gval32));
     SSG_CUDA_TRY(cudaMemsetAsync(S->d_diag_bad, 0, sizeof(int), st));
     k_dinv<<<grid_for(S->maps.nloc, ns), kBlock, 0, st>>>(S->maps.nloc, S->d_dmap, S->op.val, S->d_dinv, S->d_dinv32,
                                                            S->d_diag_bad);

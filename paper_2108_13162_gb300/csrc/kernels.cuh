@@ -28,6 +28,7 @@ constexpr int kSpmvWarps = 8;               // warps per SpMV block
 constexpr int kSpmvThreads = 32 * kSpmvWarps;
 constexpr int kSliceRows = 32;              // rows (or interface copy rows) per slice: one per lane
 constexpr int kSliceMaxWidth = 64;          // longer rows are handled one per warp from the CSR arrays
+constexpr int kGroupMaxCopies = 8;          // interface nodes with more copies are handled one per warp
 // [spmv-source-begin] traits of the single-vector SpMV
 template <typename T>
 struct SpmvTraits;  // resident blocks per SM; slices ahead prefetched into L2
@@ -96,17 +97,38 @@ enum { kTicketSpmv = 0, kTicketR = 1, kTicketXP = 2, kTicketMisc = 3 };
 //   kind 1: slice of interface copy rows [a, b) in (node, copy) order, whole
 //           nodes only, sliced-ELL data at e0, width e1
 //   kind 2: one interior row a longer than kSliceMaxWidth, CSR nonzeros [e0, e1)
-//   kind 3: one interface node a, copies [c0, c1), whose copy rows are too long
+//   kind 3: one interface node a, copies [c0, c1), whose copy rows are too
+//           long (in the list of kind-5 groups also: more than
+//           kGroupMaxCopies copies)
 //   kind 4: slice of interior rows taken from a window of one subdomain's
 //           rows sorted by length (SELL-C-sigma): lane l holds row srow[a + l]
 //           for a + l < b; sliced-ELL data at e0, width e1, as kind 0
+//   kind 5: group of b <= 32 interface nodes of one multiplicity m = c0 <=
+//           kGroupMaxCopies, one node per lane: the group's sliced-ELL data
+//           at e0 of gval / gcol holds m sub-slices, the r-th with the lanes' r-th copy rows
+//           (ascending subdomain) at width group_width(W, r) (8 bits each,
+//           ranks 0-3 in c1, 4-7 in pad), e1 = their total width; lane l's
+//           r-th copy is the local row gcopy[a + 32 r + l]
+// A system carries its interface copy rows in both forms: kind 1 in the
+// item list of every product, kind 5 in a second list that the FP64
+// single-vector product takes when the groups store enough fewer padding
+// entries (api.cu, make_plan).
 struct WorkItem {
     int32_t kind, a, b, e0, e1, c0, c1, pad;
 };
 
-enum { kItemSlice = 0, kItemIfaceSlice = 1, kItemLongRow = 2, kItemLongIface = 3, kItemSortedSlice = 4 };
+enum {
+    kItemSlice = 0,
+    kItemIfaceSlice = 1,
+    kItemLongRow = 2,
+    kItemLongIface = 3,
+    kItemSortedSlice = 4,
+    kItemIfaceGroup = 5
+};
 
-// Items streamed as sliced ELL (one row per lane).
+// Items streamed as sliced ELL (one row per lane); interface groups (kind
+// 5, one node per lane) are sliced too, but only the single-vector product
+// reads them and tests for them first.
 __host__ __device__ __forceinline__ bool sliced_item(int kind) {
     return kind == kItemSlice || kind == kItemIfaceSlice || kind == kItemSortedSlice;
 }
@@ -127,6 +149,10 @@ struct DevOp {
     const float *sval32;    // the same rounded to FP32
     const int32_t *scol;    // sliced-ELL columns (concatenated local index)
     const int32_t *sseg;    // interface slices, per copy: (lane of the node's first copy) | (m << 8)
+    const int32_t *gcopy;   // interface groups: per group and copy rank, the 32 lanes' copy rows
+    const double *gval;     // interface groups' sliced-ELL values (sub-slice layout as sval)
+    const float *gval32;    // the same rounded to FP32
+    const int32_t *gcol;    // their columns (concatenated local index)
     const int32_t *srow;    // sorted slices: the local row of each slot
     const WorkItem *items;  // SpMV work list
     const int2 *warp_range;  // [grid * kSpmvWarps] contiguous item range of each warp
@@ -144,6 +170,11 @@ struct DevOp {
 // kEpiStore: the (x, y)_w total is written to *out by the last block (ticket);
 // kEpiPartials: each block only writes its partial, the next kernel sums them.
 enum { kEpiStore = 0, kEpiPartials = 1 };
+
+// Width of copy rank r's sub-slice in an interface group (kind 5).
+__host__ __device__ __forceinline__ int group_width(const WorkItem &W, int r) {
+    return static_cast<int>((static_cast<uint32_t>(r < 4 ? W.c1 : W.pad) >> (8 * (r & 3))) & 0xffu);
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -296,6 +327,12 @@ __device__ __forceinline__ const double *slice_vals<double>(const DevOp &A) { re
 template <>
 __device__ __forceinline__ const float *slice_vals<float>(const DevOp &A) { return A.sval32; }
 template <typename T>
+__device__ __forceinline__ const T *group_vals(const DevOp &A);
+template <>
+__device__ __forceinline__ const double *group_vals<double>(const DevOp &A) { return A.gval; }
+template <>
+__device__ __forceinline__ const float *group_vals<float>(const DevOp &A) { return A.gval32; }
+template <typename T>
 __device__ __forceinline__ const T *row_vals(const DevOp &A);
 template <>
 __device__ __forceinline__ const double *row_vals<double>(const DevOp &A) { return A.val; }
@@ -424,11 +461,101 @@ __device__ __forceinline__ void finish_slice(const DevOp &A, const WorkItem &W, 
     }
 }
 
+// N consecutive entries (k0 .. k0+N-1) of the lane's rows in an interface
+// group (kind 5): loads first, then the FMAs in order, where entry kend
+// starts the next copy row: the finished row's product joins the node sum
+// S (the first one is S), and the next row's chain starts from 0.  kend is
+// the same in every lane (sub-slice boundaries), so the branch is uniform.
+template <int N, bool STREAM, typename T, typename XL>
+__device__ __forceinline__ void group_chunk(const T *__restrict__ sv, const int32_t *__restrict__ sc, const XL &X,
+                                            const WorkItem &W, int base, int k0, int &r, int &kend, T &S, T &acc) {
+    T vv[N], xv[N];
+    int cc[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        vv[j] = ldm<STREAM>(sv + base + (k0 + j) * kSliceRows);
+        cc[j] = ldm<STREAM>(sc + base + (k0 + j) * kSliceRows);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) xv[j] = X(cc[j]);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        while (k0 + j == kend) {
+            if (r == 0) S = acc;
+            else S += acc;
+            acc = T(0);
+            kend += group_width(W, ++r);
+        }
+        acc = fma(vv[j], xv[j], acc);
+    }
+}
+
+// One interface group (kind 5), Algorithms 4/5 for its nodes: lane l's node
+// has its m copy rows in sub-slices 0..m-1 (ascending subdomain); each row's
+// product is an FMA chain over its nonzeros in CSR order (then zero-valued
+// padding), the products are summed in ascending subdomain order starting
+// from the first, and every copy receives the sum: the copy rows of one node
+// meet in one lane, with no shuffle and no padding to another rank's width.
+// The lane's copies' share of (x, y)_w is added to dot.  GC: entries loaded
+// at once (8, or 4 where the node sum and the rank bookkeeping beside eight
+// loads would spill: 48 registers a thread).
+template <int GC, bool STREAM, typename T, typename XL>
+__device__ __forceinline__ void iface_group(const DevOp &A, const WorkItem &W, const XL &X,
+                                            T *__restrict__ y, int lane, T &dot) {
+    const T *__restrict__ gv = group_vals<T>(A);
+    const int base = W.e0 + lane, wsum = W.e1, m = W.c0;
+    // the lane's first two copy rows, loaded before the chains so that their
+    // latency overlaps them (most interface nodes have two copies)
+    const int row0 = __ldg(A.gcopy + W.a + lane);
+    const int row1 = m > 1 ? __ldg(A.gcopy + W.a + kSliceRows + lane) : row0;
+    int r = 0, kend = group_width(W, 0);
+    T S = T(0), acc = T(0);
+    int k = 0;
+    for (; k + GC <= wsum; k += GC) group_chunk<GC, STREAM>(gv, A.gcol, X, W, base, k, r, kend, S, acc);
+    switch (wsum - k) {
+        case 1: group_chunk<1, STREAM>(gv, A.gcol, X, W, base, k, r, kend, S, acc); break;
+        case 2: group_chunk<2, STREAM>(gv, A.gcol, X, W, base, k, r, kend, S, acc); break;
+        case 3: group_chunk<3, STREAM>(gv, A.gcol, X, W, base, k, r, kend, S, acc); break;
+        case 4: if constexpr (GC > 4) group_chunk<4, STREAM>(gv, A.gcol, X, W, base, k, r, kend, S, acc); break;
+        case 5: if constexpr (GC > 5) group_chunk<5, STREAM>(gv, A.gcol, X, W, base, k, r, kend, S, acc); break;
+        case 6: if constexpr (GC > 6) group_chunk<6, STREAM>(gv, A.gcol, X, W, base, k, r, kend, S, acc); break;
+        case 7: if constexpr (GC > 7) group_chunk<7, STREAM>(gv, A.gcol, X, W, base, k, r, kend, S, acc); break;
+        default: break;
+    }
+    // the last row (and any empty ones after it)
+    for (; r < m; ++r) {
+        if (r == 0) S = acc;
+        else S += acc;
+        acc = T(0);
+    }
+    if (lane < W.b) {
+        const T x0 = X(row0), w0 = copy_weight<T>(A, m, row0);
+        T x1 = T(0), w1 = T(0);
+        if (m > 1) {
+            x1 = X(row1);
+            w1 = copy_weight<T>(A, m, row1);
+        }
+        y[row0] = S;
+        dot = fma(w0 * x0, S, dot);
+        if (m > 1) {
+            y[row1] = S;
+            dot = fma(w1 * x1, S, dot);
+        }
+        for (int c = 2; c < m; ++c) {
+            const int row = __ldg(A.gcopy + W.a + c * kSliceRows + lane);
+            y[row] = S;
+            dot = fma(copy_weight<T>(A, m, row) * X(row), S, dot);
+        }
+    }
+}
+
 // The work items [range.x, range.y) of one warp: y = S x on their rows, the
 // interface sums, and the lane's share of (x, y)_w returned; x_j = X(j).
 // AHEAD: slices ahead whose value and column lines are prefetched into L2
-// (0: none); STREAM: how the slices are loaded (ldm).
-template <typename T, int AHEAD, bool STREAM = true, typename XL>
+// (0: none); STREAM: how the slices are loaded (ldm); GROUPS: whether the
+// list may hold interface groups (kind 5), GC their entries loaded at once
+// (iface_group).
+template <typename T, int AHEAD, bool STREAM = true, bool GROUPS = false, int GC = 8, typename XL>
 __device__ __forceinline__ T spmv_items(const DevOp &A, int2 range, const XL &X, T *__restrict__ y, int lane) {
     const T *__restrict__ sv = slice_vals<T>(A);
     const T *__restrict__ val = row_vals<T>(A);
@@ -443,9 +570,14 @@ __device__ __forceinline__ T spmv_items(const DevOp &A, int2 range, const XL &X,
             if (sliced_item(Wp.kind) && lane < Wp.e1) {
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(sv + Wp.e0 + lane * kSliceRows));
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(A.scol + Wp.e0 + lane * kSliceRows));
+            } else if (GROUPS && Wp.kind == kItemIfaceGroup && lane < Wp.e1) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(group_vals<T>(A) + Wp.e0 + lane * kSliceRows));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(A.gcol + Wp.e0 + lane * kSliceRows));
             }
         }
-        if (sliced_item(W.kind)) {
+        if (GROUPS && W.kind == kItemIfaceGroup) {
+            iface_group<GC, STREAM, T>(A, W, X, y, lane, dot);
+        } else if (sliced_item(W.kind)) {
             const T acc = slice_row<STREAM, T>(sv, A.scol, X, W.e0, W.e1, lane);
             finish_slice<T>(A, W, acc, X, y, lane, dot);
         } else if (W.kind == kItemLongRow) {
@@ -483,14 +615,21 @@ __device__ __forceinline__ T spmv_items(const DevOp &A, int2 range, const XL &X,
 // register budget); AHEAD: slices ahead whose value and column lines are
 // prefetched into L2 (0: none).  The defaults are the measured best on the
 // 128^3 system; ssg_autotune times the other instances on a given system.
-template <int EPI, typename T, int BPS = SpmvTraits<T>::kBlocksPerSM, int AHEAD = SpmvTraits<T>::kL2Ahead>
+// GROUPS: the work list holds interface groups (kind 5) instead of slices.
+template <int EPI, typename T, int BPS = SpmvTraits<T>::kBlocksPerSM, int AHEAD = SpmvTraits<T>::kL2Ahead,
+          bool GROUPS = false>
 __global__ void __launch_bounds__(kSpmvThreads, BPS)
     k_spmv_asm(DevOp A, const T *__restrict__ x, T *__restrict__ y, double *partials, Scal *s, double *out,
                cudaGraphConditionalHandle h, int use_cond) {
     if (EPI == kEpiPartials && (s->brk || s->halt[s->iter & 1])) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int2 range = A.warp_range[blockIdx.x * kSpmvWarps + warp];
-    const T dot = spmv_items<T, AHEAD>(A, range, XRead<T>{x}, y, lane);
+    // GROUPS: the list holds interface groups (FP64 instances of systems
+    // that use them; the group path, merely compiled in, slowed the slices:
+    // FP32 8 % on 128^3, the FP64 loop of the 64^2 Poisson system 4 %)
+    static_assert(!GROUPS || sizeof(T) == 8, "interface groups are read by the FP64 product only");
+    constexpr int GC = BPS >= 5 ? 4 : 8;
+    const T dot = spmv_items<T, AHEAD, true, GROUPS, GC>(A, range, XRead<T>{x}, y, lane);
     // fixed-order reduction.  FP32: lanes of each warp in FP32, then the
     // block's warps in order in FP64.  FP64: through shared memory, one warp
     // adding the block's 256 values (12 FP64 warp instructions per block

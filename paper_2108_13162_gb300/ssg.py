@@ -78,6 +78,7 @@ EXPORTS = (
     "ssg_set_cluster_solve",
     "ssg_get_cluster_solve",
     "ssg_get_layout",
+    "ssg_get_iface_layout",
     "ssg_autotune_block",
     "ssg_band_split",
     "ssg_band_get",
@@ -235,6 +236,7 @@ def lib():
         L.ssg_get_cluster_solve.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.ssg_autotune_block.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(ssg_tune_block)]
         L.ssg_get_layout.argtypes = [vp, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")]
+        L.ssg_get_iface_layout.argtypes = [vp, np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")]
         L.ssg_measure_fp64_rate.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                             C.POINTER(C.c_double)]
         L.ssg_band_split.argtypes = [vp, i32, i32, vp, vp, vp, i32, C.POINTER(vp)]
@@ -617,6 +619,13 @@ def ssg_get_layout(sys) -> dict:
             "max_window": int(out[3]), "padding_ratio": float(out[0]) / max(int(out[1]), 1)}
 
 
+def ssg_get_iface_layout(sys) -> dict:
+    """The interface layout of a system's products (see ssg.h)."""
+    out = np.zeros(3, np.int64)
+    _check(lib().ssg_get_iface_layout(sys, out), "ssg_get_iface_layout")
+    return {"iface_slots": int(out[0]), "group_slots": int(out[1]), "groups": bool(out[2])}
+
+
 def ssg_system_destroy(sys):
     return lib().ssg_system_destroy(sys)
 
@@ -830,6 +839,9 @@ class System:
 
     def layout(self):
         return ssg_get_layout(self.h)
+
+    def iface_layout(self):
+        return ssg_get_iface_layout(self.h)
 
     def set_weights(self, mode: int = SSG_WEIGHT_INV_MULT):
         """Weights of the weighted dots: SSG_WEIGHT_INV_MULT (1/m) or SSG_WEIGHT_OWNER."""

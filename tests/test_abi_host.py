@@ -271,6 +271,59 @@ def test_slice_layout_rule_from_row_lengths():
         S.close()
 
 
+def _iface_slots(m):
+    """Entries the two interface layouts store, recomputed from the oracle's
+    maps: slices of whole nodes in ascending node order (up to 32 copy rows,
+    each padded to the slice's longest) and groups of up to 32 nodes of one
+    multiplicity (in windows of 512 nodes ordered by decreasing copy-row
+    lengths, rank by rank; each rank padded to the group's longest).  Nodes
+    with a copy row longer than 64, or more copies than a layout takes (32,
+    8), are left to items of their own."""
+    clen = np.diff(m.lrowptr)[m.icopy]
+    mult = np.diff(m.iptr)
+    long_row = np.array([clen[m.iptr[g]:m.iptr[g + 1]].max() > 64 for g in range(m.ngamma)], bool)
+    slots, g = 0, 0
+    while g < m.ngamma:
+        if mult[g] > 32 or long_row[g]:
+            g += 1
+            continue
+        c0, g1, w = m.iptr[g], g, 0
+        while g1 < m.ngamma and not (mult[g1] > 32 or long_row[g1]) and m.iptr[g1 + 1] - c0 <= 32:
+            w = max(w, int(clen[m.iptr[g1]:m.iptr[g1 + 1]].max()))
+            g1 += 1
+        slots += 32 * w
+        g = g1
+    gslots = 0
+    for mm in range(1, 9):
+        nodes = [g for g in range(m.ngamma) if mult[g] == mm and not long_row[g]]
+        for w0 in range(0, len(nodes), 512):
+            win = sorted(nodes[w0:w0 + 512], key=lambda g: tuple(-int(clen[m.iptr[g] + r]) for r in range(mm)))
+            for i in range(0, len(win), 32):
+                grp = win[i:i + 32]
+                gslots += sum(32 * max(int(clen[m.iptr[g] + r]) for g in grp) for r in range(mm))
+    return slots, gslots
+
+
+def test_iface_layout_rule():
+    """The interface layout (host only): the entries both layouts store match
+    a recomputation from the oracle's maps, and the single-vector product
+    takes the groups exactly when they store at least 4 % of all its sliced
+    entries fewer: on the finite-volume boxes (a node's copy in the lower
+    subdomain holds one entry, the owner's six) but not on the Poisson square
+    or the P1 mesh."""
+    for q, want in ((config_problem(2, scale=24), True), (config_problem(1), False),
+                    (config_problem(3, scale=96), None)):
+        S = ssg.System(None, q.A, q.part, q.P)
+        lay, il = S.layout(), S.iface_layout()
+        slots, gslots = _iface_slots(oracle.Partition(q.A, q.part, q.P).maps)
+        assert (il["iface_slots"], il["group_slots"]) == (slots, gslots)
+        rule = slots > gslots and slots - gslots >= 0.04 * (lay["slice_slots"] + slots)
+        assert il["groups"] == rule
+        if want is not None:
+            assert il["groups"] == want
+        S.close()
+
+
 def _interior_nnz(p):
     """Stored entries of the interior (multiplicity 1) rows of the local
     matrices, from the oracle's maps."""

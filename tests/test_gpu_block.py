@@ -68,6 +68,9 @@ def test_spmm_bitwise_vs_spmv_and_oracle_bound(ctx, fv20, k, prec):
 
     p, ref = fv20
     S = System(ctx, p.A, p.part, p.P)
+    # the single-vector product reads the interface groups here, the
+    # K-vector product the interface slices: two layouts, the same bits
+    assert S.iface_layout()["groups"]
     m = ref.maps
     rng = np.random.default_rng(40 + k)
     Xg = rng.uniform(-1, 1, (p.A.n, k))
