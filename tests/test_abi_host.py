@@ -324,6 +324,21 @@ def test_iface_layout_rule():
         S.close()
 
 
+@pytest.mark.parametrize("seed", range(0, 40, 3))
+def test_iface_layout_random_systems(seed):
+    """The interface layout's entry counts and choice on the seeded random
+    systems (random degrees: multiplicities up to the subdomain count,
+    nodes with more copies than a group takes, empty subdomains), against the
+    recomputation from the oracle's maps."""
+    A, part, P = _random_case(seed)
+    S = ssg.System(None, A, part, P)
+    lay, il = S.layout(), S.iface_layout()
+    slots, gslots = _iface_slots(oracle.Partition(A, part, P).maps)
+    assert (il["iface_slots"], il["group_slots"]) == (slots, gslots)
+    assert il["groups"] == (slots > gslots and slots - gslots >= 0.04 * (lay["slice_slots"] + slots))
+    S.close()
+
+
 def _interior_nnz(p):
     """Stored entries of the interior (multiplicity 1) rows of the local
     matrices, from the oracle's maps."""
