@@ -176,6 +176,26 @@ def test_host_only_system_refuses_device_calls():
         ssg.ssg_system_destroy(sys_)
 
 
+def test_layout_reports_refuse_null_arguments():
+    """The layout reports take a system and a host buffer; a null either is
+    SSG_E_INVALID with a message, and nothing is written."""
+    import ctypes as C
+
+    L = ssg.lib()
+    buf = (C.c_int64 * 4)()
+    for fn in (L.ssg_get_layout, L.ssg_get_iface_layout):
+        f = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p)(C.cast(fn, C.c_void_p).value)
+        assert f(None, C.addressof(buf)) == ssg.SSG_E_INVALID
+        assert "null" in ssg.last_error()
+    A = poisson2d_5pt(4, 4)
+    sys_ = ssg.ssg_partition(None, A.n, A.rowptr, A.colidx, A.val, (np.arange(A.n) % 2).astype(np.int32), 2)
+    try:
+        f = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p)(C.cast(L.ssg_get_iface_layout, C.c_void_p).value)
+        assert f(sys_, None) == ssg.SSG_E_INVALID
+    finally:
+        ssg.ssg_system_destroy(sys_)
+
+
 def test_error_strings():
     for code in range(7):
         assert ssg.ssg_error_string(code)
