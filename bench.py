@@ -554,7 +554,7 @@ def bench_fe(ctx, stream, reps, windows=False):
     b = torch.from_numpy(p.b[:, 0].copy()).cuda()
     out = {"workload": "fe2d_p1_jittered_1024^2_rcb256", "n": p.A.n, "nnz": p.A.nnz, "subdomains": p.P,
            "nloc": S.sizes.nloc, "rtol": RTOL, "autotune": tune, "layout": S.layout(),
-           "spmv": spmv_roofline(S), "unsorted": unsorted}
+           "iface_layout": S.iface_layout(), "spmv": spmv_roofline(S), "unsorted": unsorted}
     if by_window is not None:
         out["by_window"] = by_window
     for name, mode in (("fp64", ssg.SSG_FP64), ("mixed", ssg.SSG_MIXED), ("mixed_jacobi", ssg.SSG_MIXED_JACOBI)):
@@ -1169,6 +1169,8 @@ def run_ours(args, dist):
         "driver": args.driver,
         "unroll": args.unroll,
         "autotune": tune,
+        # interface slices or groups in the FP64 product (ssg_get_iface_layout)
+        "iface_layout": S.iface_layout(),
     })
     if gold and args.mode in gold["oracle_iters"]:
         cfg["oracle_iters"] = gold["oracle_iters"][args.mode]
